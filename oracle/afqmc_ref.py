@@ -1,0 +1,455 @@
+"""CPU oracle for the phaseless-AFQMC walker step (test infrastructure only).
+
+This module is the slow, plain FP64 statement of what the walker step of
+large-time-step ph-AFQMC computes (Sukurma et al., "Towards Large-Scale AFQMC
+Calculations: Large Time Step Auxiliary-Field Quantum Monte Carlo").  It is
+used only by the tests, by the smoke check and by the CPU-baseline leg of the
+benchmark; the product path never imports it.  It shares no code with the CUDA
+library: every quantity is written from its definition with PyTorch CPU
+primitives (matmul, solve, slogdet, eigh, eig, matrix_exp), in float64 /
+complex128, walker by walker where the method is per walker.
+
+Conventions.
+  * A walker is psi [N, na+nb] complex; columns [0, na) hold the alpha
+    orbitals, [na, na+nb) the beta orbitals.  Batches carry a leading walker
+    axis: psi [Nw, N, na+nb].
+  * trial [N, na+nb] real, same column split.
+  * L [G, N, N] real symmetric Cholesky vectors, <pq|rs> = sum_g L_g,pr L_g,qs
+    (Sec. II.A).
+  * logovl = sum_sigma log det(trial_sigma^T psi_sigma) (complex; the
+    imaginary part is defined modulo 2 pi).
+
+Readings of the paper used here (the paper is silent or ambiguous on them):
+  R1  The mean-field shift L_bar_g enters as an operator constant:
+      H = h'' + 1/2 sum_g (L_g - L_bar_g)^2 + E_c' with
+      h'' = h - 1/2 sum_g L_g L_g + sum_g L_bar_g L_g and
+      E_c' = E_const - 1/2 sum_g L_bar_g^2.  e^{-tau h''/2} is the Split-2
+      half step; the shift contributes one scalar factor
+      s = exp(-tau E_c' - i sqrt(tau) sum_g c_g L_bar_g) per walker to the
+      overlap ratio.
+  R5  Krylov = Arnoldi with one modified Gram-Schmidt pass per vector; an
+      invariant subspace is declared when the new subdiagonal entry is
+      <= 1e-12 ||A||_F (the basis vectors are unit vectors).
+  R6  The small exponential e^{A_k} is torch.linalg.matrix_exp.
+  R7  E_0 is a caller-supplied scalar.
+  R8  Population control: comb with caller-supplied uniform u.
+  R9  Threshold tests use the strict inequalities printed in Sec. V.
+  R11 The mixed estimator and the energy window use Re E_L.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import torch
+
+RT = torch.float64
+CT = torch.complex128
+
+__all__ = [
+    "Hamiltonian", "make_hamiltonian", "overlap", "greens_function",
+    "log_overlap", "theta", "mean_field_shift", "mixed_L_expectation",
+    "force_bias", "propagation_h1", "half_step_propagator", "field_matrix",
+    "taylor_action", "krylov_action", "exact_action", "expm_action",
+    "split2_propagate", "local_energy", "energy_window", "mixed_energy",
+    "mgs_qr", "reorthonormalise", "weight_update", "step", "init_walkers",
+    "free_projection_step", "comb", "StepInfo",
+]
+
+
+# --------------------------------------------------------------------------
+# Hamiltonian data (Sec. II.A, Eq. mbham and the Cholesky decomposition)
+# --------------------------------------------------------------------------
+@dataclass
+class Hamiltonian:
+    h1: torch.Tensor        # [N, N] real symmetric one-body matrix h_pq
+    L: torch.Tensor         # [G, N, N] Cholesky vectors L_g,pq
+    trial: torch.Tensor     # [N, na+nb] real trial orbitals
+    na: int
+    nb: int
+    e_const: float = 0.0
+
+    @property
+    def N(self):
+        return self.h1.shape[0]
+
+    @property
+    def G(self):
+        return self.L.shape[0]
+
+    def spins(self):
+        """Column slices of the two spin blocks."""
+        return (slice(0, self.na), slice(self.na, self.na + self.nb))
+
+
+def make_hamiltonian(h1, L, trial, na, nb, e_const=0.0) -> Hamiltonian:
+    return Hamiltonian(torch.as_tensor(h1, dtype=RT), torch.as_tensor(L, dtype=RT),
+                       torch.as_tensor(trial, dtype=RT), int(na), int(nb), float(e_const))
+
+
+# --------------------------------------------------------------------------
+# Overlaps and the mixed one-particle density (Sec. II.A, Eqs. force_shift,
+# hyben, eloc)
+# --------------------------------------------------------------------------
+def overlap(trial_s, psi_s):
+    """O = <Psi_T|Psi> matrix for one spin: O = trial^T psi  ([..., n, n])."""
+    return trial_s.to(psi_s.dtype).transpose(-1, -2) @ psi_s
+
+
+def log_overlap(ham: Hamiltonian, psi):
+    """log <Psi_T|Psi> = sum_sigma log det(trial_sigma^T psi_sigma)."""
+    total = 0
+    for sl in ham.spins():
+        if sl.stop == sl.start:
+            continue
+        sign, logabs = torch.linalg.slogdet(overlap(ham.trial[:, sl], psi[..., sl]))
+        total = total + logabs + 1j * torch.angle(sign)
+    return total
+
+
+def theta(trial_s, psi_s):
+    """Theta = psi (trial^T psi)^{-1}, the N x n factor of the mixed density."""
+    O = overlap(trial_s, psi_s)
+    # Theta O = psi  <=>  O^T Theta^T = psi^T
+    return torch.linalg.solve(O.transpose(-1, -2), psi_s.transpose(-1, -2)).transpose(-1, -2)
+
+
+def greens_function(trial_s, psi_s):
+    """Mixed one-particle density G_pq = <Psi_T|a+_p a_q|Psi>/<Psi_T|Psi>.
+
+    For Slater determinants G_pq = [psi (trial^T psi)^{-1} trial^T]_{qp}.
+    """
+    M = theta(trial_s, psi_s) @ trial_s.to(psi_s.dtype).transpose(-1, -2)
+    return M.transpose(-1, -2)
+
+
+def mixed_L_expectation(ham: Hamiltonian, psi):
+    """<Psi_T|L_g|Psi>/<Psi_T|Psi> = sum_sigma sum_pq L_g,pq G^sigma_pq  ([..., G])."""
+    out = 0
+    for sl in ham.spins():
+        if sl.stop == sl.start:
+            continue
+        Gs = greens_function(ham.trial[:, sl], psi[..., sl])
+        out = out + torch.einsum("gpq,...pq->...g", ham.L.to(Gs.dtype), Gs)
+    return out
+
+
+def mean_field_shift(ham: Hamiltonian):
+    """L_bar_g = <Psi_T|L_g|Psi_T>/<Psi_T|Psi_T> (Eq. force_shift, first line)."""
+    return mixed_L_expectation(ham, ham.trial.to(CT)).real
+
+
+# --------------------------------------------------------------------------
+# Force bias and the effective interaction (Eqs. heffTOT, force_shift;
+# force-bias capping of Sec. V.C)
+# --------------------------------------------------------------------------
+def force_bias(ham: Hamiltonian, psi, tau, L_bar=None):
+    """f_g = -i sqrt(tau) (<L_g>_mixed - L_bar_g), components with |f_g| >= 1 set to 0.
+
+    Returns (f_capped, f_uncapped).
+    """
+    if L_bar is None:
+        L_bar = mean_field_shift(ham)
+    f = -1j * math.sqrt(tau) * (mixed_L_expectation(ham, psi) - L_bar)
+    capped = torch.where(f.abs() < 1.0, f, torch.zeros_like(f))
+    return capped, f
+
+
+def propagation_h1(ham: Hamiltonian, L_bar=None):
+    """h'' and E_c' of reading R1.
+
+    1/2 sum_pqrs V a+a+aa = 1/2 sum_g L_g^2 - 1/2 sum_g (L_g L_g)_pq a+_p a_q,
+    and 1/2 sum_g L_g^2 = 1/2 sum_g (L_g - L_bar_g)^2 + sum_g L_bar_g L_g
+    - 1/2 sum_g L_bar_g^2.
+    """
+    if L_bar is None:
+        L_bar = mean_field_shift(ham)
+    LL = torch.einsum("gpr,grq->pq", ham.L, ham.L)
+    hpp = ham.h1 - 0.5 * LL + torch.einsum("g,gpq->pq", L_bar, ham.L)
+    ec = ham.e_const - 0.5 * float((L_bar * L_bar).sum())
+    return hpp, ec
+
+
+def half_step_propagator(hpp, tau):
+    """B = exp(-tau h''/2), exact by diagonalisation (Sec. III.B)."""
+    lam, V = torch.linalg.eigh(hpp)
+    return (V * torch.exp(-0.5 * tau * lam)[None, :]) @ V.T
+
+
+def field_matrix(ham: Hamiltonian, c, tau):
+    """A = -tau H_int (Sec. IV) without the L_bar delta term (reading R1).
+
+    H_int,pq = -(i/sqrt(tau)) sum_g c_g L_g,pq with c_g = x_g - f_g, so
+    A = i sqrt(tau) sum_g c_g L_g.  c: [..., G] complex -> A [..., N, N].
+    """
+    return 1j * math.sqrt(tau) * torch.einsum("...g,gpq->...pq", c, ham.L.to(CT))
+
+
+# --------------------------------------------------------------------------
+# Action of the exponential (Sec. IV)
+# --------------------------------------------------------------------------
+def taylor_action(A, psi, k):
+    """taylor_k{A, Psi} = sum_{n=0}^{k} A^n / n! Psi  (Eq. taylor)."""
+    term = psi
+    acc = psi
+    for n in range(1, k + 1):
+        term = (A @ term) / n
+        acc = acc + term
+    return acc
+
+
+def _arnoldi_column(A, psi_col, k, normA):
+    """Krylov approximation of e^A psi for one orbital vector (Eqs. krylovsub-krylov)."""
+    N = A.shape[-1]
+    beta = torch.linalg.vector_norm(psi_col)
+    if float(beta) == 0.0:
+        return torch.zeros_like(psi_col), 0
+    kk = min(k, N)
+    basis = [psi_col / beta]                                 # b_1 = psi/||psi||
+    H = torch.zeros(kk, kk, dtype=psi_col.dtype)
+    k_eff = kk
+    for j in range(kk):
+        w = A @ basis[j]
+        for i in range(j + 1):                               # modified Gram-Schmidt
+            H[i, j] = torch.vdot(basis[i], w)                # b_i^dagger w
+            w = w - H[i, j] * basis[i]
+        if j + 1 < kk:
+            h = torch.linalg.vector_norm(w)
+            if float(h) <= 1e-12 * float(normA):             # invariant subspace (R5)
+                k_eff = j + 1
+                break
+            H[j + 1, j] = h
+            basis.append(w / h)
+    y = torch.linalg.matrix_exp(H[:k_eff, :k_eff])[:, 0] * beta   # e^{A_k} e_1 ||psi||
+    out = torch.zeros_like(psi_col)
+    for i in range(k_eff):
+        out = out + y[i] * basis[i]                          # B_k y
+    return out, k_eff
+
+
+def krylov_action(A, psi, k):
+    """krylov_k{A, psi} = B_k e^{A_k} e_1 ||psi|| for every orbital column."""
+    if psi.dim() == 3:
+        return torch.stack([krylov_action(A[w], psi[w], k) for w in range(psi.shape[0])])
+    normA = torch.linalg.matrix_norm(A)
+    cols = [_arnoldi_column(A, psi[:, j], k, normA)[0] for j in range(psi.shape[1])]
+    return torch.stack(cols, dim=1)
+
+
+def exact_action(A, psi):
+    """e^A Psi by (non-Hermitian) diagonalisation, A = V diag(l) V^{-1} (Sec. IV)."""
+    lam, V = torch.linalg.eig(A.to(CT))
+    return V @ (torch.exp(lam)[..., :, None] * torch.linalg.solve(V, psi.to(CT)))
+
+
+def expm_action(A, psi, method, k):
+    if method == "taylor":
+        return taylor_action(A, psi, k)
+    if method == "krylov":
+        return krylov_action(A, psi, k)
+    if method == "exact":
+        return exact_action(A, psi)
+    raise ValueError(method)
+
+
+def split2_propagate(B, A, psi, method, k):
+    """U_S2 Psi = e^{-tau H1/2} e^{A} e^{-tau H1/2} Psi (Sec. III.B)."""
+    Bc = B.to(CT)
+    return Bc @ expm_action(A, Bc @ psi, method, k)
+
+
+# --------------------------------------------------------------------------
+# Local energy and the mixed estimator (Eq. eloc; Sec. V.A capping)
+# --------------------------------------------------------------------------
+def local_energy(ham: Hamiltonian, psi):
+    """E_L = <Psi_T|H|Psi>/<Psi_T|Psi> by Wick's theorem with the mixed density.
+
+    E_L = E_const + sum_s sum_pq h_pq G^s_pq
+          + 1/2 sum_pqrs V_pqrs [sum_{s,s'} G^s_pr G^s'_qs - sum_s G^s_ps G^s_qr],
+    V_pqrs = sum_g L_g,pr L_g,qs, so the direct term is 1/2 sum_g (sum_s
+    tr(L_g G^s^T))^2 and the exchange term 1/2 sum_g sum_s tr(L_g G^sT L_g G^sT).
+    """
+    if psi.dim() == 3 and psi.shape[0] * ham.G * ham.N * ham.N > (1 << 22):
+        # bound the [walkers, G, N, N] temporaries: evaluate walker by walker
+        return torch.stack([local_energy(ham, psi[w]) for w in range(psi.shape[0])])
+    e = torch.full(psi.shape[:-2], ham.e_const, dtype=CT)
+    direct = 0
+    exch = 0
+    L = ham.L.to(CT)
+    for sl in ham.spins():
+        if sl.stop == sl.start:
+            continue
+        Gs = greens_function(ham.trial[:, sl], psi[..., sl])
+        e = e + torch.einsum("pq,...pq->...", ham.h1.to(CT), Gs)
+        direct = direct + torch.einsum("gpr,...pr->...g", L, Gs)
+        GT = Gs.transpose(-1, -2)
+        M = torch.einsum("gpr,...rq->...gpq", L, GT)          # L_g G^T
+        exch = exch + torch.einsum("...gpq,...gqp->...", M, M)
+    return e + 0.5 * ((direct * direct).sum(-1) - exch)
+
+
+def energy_window(e_loc, e0, tau, n_elec):
+    """Capped local energy of Eq. enwin, DeltaE = 1/2 sqrt(N_e/tau) + sqrt(N_e tau)."""
+    dE = 0.5 * math.sqrt(n_elec / tau) + math.sqrt(n_elec * tau)
+    return torch.clamp(e_loc.real, e0 - dE, e0 + dE)
+
+
+def mixed_energy(W, e_loc_capped):
+    """E_k = sum_w W^w E_L^w / sum_w W^w over live walkers (Sec. II.A)."""
+    live = W > 0
+    Wl = torch.where(live, W, torch.zeros_like(W))
+    El = torch.where(live, e_loc_capped, torch.zeros_like(e_loc_capped))
+    return float((Wl * El).sum() / Wl.sum()), float(Wl.sum())
+
+
+# --------------------------------------------------------------------------
+# Re-orthonormalisation (Sec. IV.D: orbitals must be orthogonalised under
+# imaginary-time propagation)
+# --------------------------------------------------------------------------
+def mgs_qr(X):
+    """Modified Gram-Schmidt QR of the columns of X ([N, n]) -> (Q, R)."""
+    N, n = X.shape
+    Q = X.clone()
+    R = torch.zeros(n, n, dtype=X.dtype)
+    for j in range(n):
+        for i in range(j):
+            R[i, j] = torch.vdot(Q[:, i], Q[:, j])
+            Q[:, j] = Q[:, j] - R[i, j] * Q[:, i]
+        R[j, j] = torch.linalg.vector_norm(Q[:, j])
+        Q[:, j] = Q[:, j] / R[j, j]
+    return Q, R
+
+
+def reorthonormalise(ham: Hamiltonian, psi):
+    """Per walker and spin Psi_sigma <- Q of its MGS QR; returns (psi, logovl)."""
+    out = psi.clone()
+    batch = psi.shape[0] if psi.dim() == 3 else None
+    for w in (range(batch) if batch is not None else [None]):
+        for sl in ham.spins():
+            if sl.stop == sl.start:
+                continue
+            X = psi[w][:, sl] if w is not None else psi[:, sl]
+            Q, _ = mgs_qr(X)
+            if w is not None:
+                out[w][:, sl] = Q
+            else:
+                out[:, sl] = Q
+    return out, log_overlap(ham, out)
+
+
+# --------------------------------------------------------------------------
+# Weights (Eqs. wupdate, hyben, phaseless, theta; Sec. V.B)
+# --------------------------------------------------------------------------
+@dataclass
+class StepInfo:
+    f: torch.Tensor          # capped force bias [Nw, G]
+    n_fcap: torch.Tensor     # number of removed force-bias components [Nw]
+    log_ratio: torch.Tensor  # log of the overlap ratio incl. the scalar s [Nw]
+    log_I: torch.Tensor      # log of the importance factor [Nw]
+    e_hybrid: torch.Tensor   # E_H [Nw] complex
+    dtheta: torch.Tensor     # phase change in (-pi, pi] [Nw]
+    factor: torch.Tensor     # capped reweighting factor [Nw]
+
+
+def weight_update(W, log_ratio, log_I, tau, e0):
+    """Phaseless update W' = W exp(-tau(Re E_H - E0)) max(0, cos dtheta).
+
+    E_H = -(1/tau) log(ratio I) (Eq. hyben); dtheta = Im log ratio (Eq.
+    theta), wrapped to (-pi, pi]; the reweighting factor is set to 0 unless
+    it is < 10 (Sec. V.B).
+    """
+    e_h = -(log_ratio + log_I) / tau
+    dth = torch.remainder(log_ratio.imag + math.pi, 2 * math.pi) - math.pi
+    dth = torch.where(dth == -math.pi, torch.full_like(dth, math.pi), dth)
+    fac = torch.exp(-tau * (e_h.real - e0))
+    fac = torch.where(fac < 10.0, fac, torch.zeros_like(fac))
+    Wn = W * fac * torch.clamp(torch.cos(dth), min=0.0)
+    Wn = torch.where(torch.isfinite(Wn) & torch.isfinite(e_h.real), Wn, torch.zeros_like(Wn))
+    return Wn, e_h, dth, fac
+
+
+# --------------------------------------------------------------------------
+# The walker step
+# --------------------------------------------------------------------------
+def init_walkers(ham: Hamiltonian, n_walkers):
+    """Psi_0 = Psi_T, W_0 = 1, logovl_0 = log <Psi_T|Psi_T> (Sec. II.A)."""
+    psi = ham.trial.to(CT).unsqueeze(0).repeat(n_walkers, 1, 1)
+    W = torch.ones(n_walkers, dtype=RT)
+    return psi, log_overlap(ham, psi), W
+
+
+def step(ham: Hamiltonian, psi, logovl, W, x, tau, e0, method="krylov", k=10,
+         reortho=False, B=None, L_bar=None, ec=None):
+    """One phaseless walker step with the Split-2 propagator.
+
+    psi [Nw, N, na+nb] complex, logovl [Nw] complex, W [Nw] real, x [Nw, G]
+    real standard-normal fields.  Walkers with W = 0 are kept as they are.
+    Returns (psi', logovl', W', StepInfo).
+    """
+    if L_bar is None:
+        L_bar = mean_field_shift(ham)
+    if B is None or ec is None:
+        hpp, ec = propagation_h1(ham, L_bar)
+        B = half_step_propagator(hpp, tau)
+    x = torch.as_tensor(x, dtype=RT)
+    f, f_raw = force_bias(ham, psi, tau, L_bar)                     # Eq. force_shift
+    c = x.to(CT) - f
+    A = field_matrix(ham, c, tau)                                   # Eq. heffTOT
+    psi_new = split2_propagate(B, A, psi, method, k)                # Eq. psiupdate
+    logovl_new = log_overlap(ham, psi_new)
+    log_s = -tau * ec - 1j * math.sqrt(tau) * (c @ L_bar.to(CT))
+    log_ratio = logovl_new - logovl + log_s
+    log_I = (x.to(CT) * f - 0.5 * f * f).sum(-1)                    # importance factor
+    W_new, e_h, dth, fac = weight_update(W, log_ratio, log_I, tau, e0)
+    if reortho:
+        psi_new, logovl_new = reorthonormalise(ham, psi_new)
+    alive = W > 0
+    psi_out = torch.where(alive[:, None, None], psi_new, psi)
+    logovl_out = torch.where(alive, logovl_new, logovl)
+    W_out = torch.where(alive, W_new, W)
+    info = StepInfo(f=f, n_fcap=(f_raw.abs() >= 1.0).sum(-1), log_ratio=log_ratio,
+                    log_I=log_I, e_hybrid=e_h, dtheta=dth, factor=fac)
+    return psi_out, logovl_out, W_out, info
+
+
+def free_projection_step(ham: Hamiltonian, psi, logovl, weight, x, tau, e0,
+                         method="taylor", k=6, B=None, L_bar=None, ec=None):
+    """Free-projection step (Eqs. psiupdate, wupdate): complex weight, no phaseless cut.
+
+    weight' = weight * ratio * I * e^{tau E0} = weight e^{-tau(E_H - E0)}.
+    """
+    if L_bar is None:
+        L_bar = mean_field_shift(ham)
+    if B is None or ec is None:
+        hpp, ec = propagation_h1(ham, L_bar)
+        B = half_step_propagator(hpp, tau)
+    x = torch.as_tensor(x, dtype=RT)
+    f, _ = force_bias(ham, psi, tau, L_bar)
+    c = x.to(CT) - f
+    A = field_matrix(ham, c, tau)
+    psi_new = split2_propagate(B, A, psi, method, k)
+    logovl_new = log_overlap(ham, psi_new)
+    log_s = -tau * ec - 1j * math.sqrt(tau) * (c @ L_bar.to(CT))
+    log_ratio = logovl_new - logovl + log_s
+    log_I = (x.to(CT) * f - 0.5 * f * f).sum(-1)
+    return psi_new, logovl_new, weight * torch.exp(log_ratio + log_I + tau * e0)
+
+
+# --------------------------------------------------------------------------
+# Population control (the paper is silent; reading R8)
+# --------------------------------------------------------------------------
+def comb(W, u):
+    """Comb resampling: Nw teeth at (u + j) sum(W)/Nw; tooth j picks the walker whose
+    cumulative-weight interval [C_{w-1}, C_w) contains it.  Returns indices [Nw]."""
+    W = torch.as_tensor(W, dtype=RT)
+    n = W.shape[0]
+    total = float(W.sum())
+    cum = torch.cumsum(W, 0)
+    idx = []
+    w = 0
+    for j in range(n):
+        tooth = (u + j) * total / n
+        while w < n - 1 and not (tooth < float(cum[w])):
+            w += 1
+        idx.append(w)
+    return torch.tensor(idx, dtype=torch.int64)

@@ -1,0 +1,461 @@
+"""Pins of the CPU oracle against facts fixed by the paper and by mathematics.
+
+Every oracle function is checked here against something other than itself:
+library routines (matrix_exp, eigh, qr, det), closed forms, invariants,
+special cases, brute-force FCI (second quantisation, in fci_bruteforce.py) and
+finite differences.  No GPU is needed.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import fci_bruteforce as fci
+from oracle import afqmc_ref as R
+from paper_2403_02542_gb300.inputs import make_fields, make_system
+
+CT = torch.complex128
+RT = torch.float64
+
+
+def _rand_c(gen, *shape):
+    return (torch.randn(*shape, generator=gen, dtype=RT)
+            + 1j * torch.randn(*shape, generator=gen, dtype=RT)).to(CT)
+
+
+def _small_ham(N=6, n=2, G=10, rho=0.6, seed=3, lambda0=1.0):
+    s = make_system(N, n, n, G, rho=rho, seed=seed, lambda0=lambda0)
+    return s, R.make_hamiltonian(s.h1, s.L, s.trial, s.na, s.nb, s.e_const)
+
+
+# ---------------------------------------------------------------- exponentials
+def test_taylor_within_truncation_bound():
+    """Eq. taylor: ||taylor_k - e^A psi|| <= ||A||^{k+1} e^{||A||} / (k+1)! ||psi||."""
+    g = torch.Generator().manual_seed(1)
+    for N in (4, 6, 8):
+        A = 0.3 * _rand_c(g, N, N)
+        psi = _rand_c(g, N, 3)
+        ref = torch.linalg.matrix_exp(A) @ psi
+        nA = float(torch.linalg.matrix_norm(A, ord=2))
+        for k in (2, 4, 6, 10):
+            err = float(torch.linalg.matrix_norm(R.taylor_action(A, psi, k) - ref, ord=2))
+            bound = nA ** (k + 1) * math.exp(nA) / math.factorial(k + 1) * float(
+                torch.linalg.matrix_norm(psi, ord=2))
+            assert err <= bound * (1 + 1e-9) + 1e-14
+
+
+def test_taylor_order_zero_and_one():
+    g = torch.Generator().manual_seed(2)
+    A = _rand_c(g, 5, 5)
+    psi = _rand_c(g, 5, 2)
+    assert torch.equal(R.taylor_action(A, psi, 0), psi)
+    assert torch.allclose(R.taylor_action(A, psi, 1), psi + A @ psi, atol=1e-15)
+
+
+def test_exact_action_matches_matrix_exp():
+    g = torch.Generator().manual_seed(3)
+    A = _rand_c(g, 7, 7)
+    psi = _rand_c(g, 7, 3)
+    ref = torch.linalg.matrix_exp(A) @ psi
+    assert torch.allclose(R.exact_action(A, psi), ref, rtol=1e-10, atol=1e-10)
+
+
+def test_krylov_full_dimension_is_exact():
+    """k = N: the Krylov space is the whole space, so e^A psi is exact to roundoff."""
+    g = torch.Generator().manual_seed(4)
+    for N in (3, 5, 8):
+        A = 0.5 * _rand_c(g, N, N)
+        psi = _rand_c(g, N, 2)
+        ref = torch.linalg.matrix_exp(A) @ psi
+        out = R.krylov_action(A, psi, N)
+        assert torch.allclose(out, ref, rtol=1e-11, atol=1e-12)
+        # k > N is clamped to N
+        assert torch.allclose(R.krylov_action(A, psi, N + 3), ref, rtol=1e-11, atol=1e-12)
+
+
+def test_krylov_eigenvector_exact_at_k1():
+    """psi an eigenvector of A: K_1 is invariant and krylov_1 = e^lambda psi."""
+    g = torch.Generator().manual_seed(5)
+    N = 6
+    A = _rand_c(g, N, N)
+    lam, V = torch.linalg.eig(A)
+    psi = V[:, :2] * 3.0
+    out = R.krylov_action(A, psi, 1)
+    assert torch.allclose(out, psi * torch.exp(lam[:2])[None, :], rtol=1e-10, atol=1e-12)
+    # and a higher k detects the invariant subspace (happy breakdown) without harm
+    out5 = R.krylov_action(A, psi, 5)
+    assert torch.allclose(out5, psi * torch.exp(lam[:2])[None, :], rtol=1e-9, atol=1e-11)
+
+
+def test_krylov_error_decreases_with_k():
+    g = torch.Generator().manual_seed(6)
+    N = 12
+    A = 0.15 * _rand_c(g, N, N)
+    psi = _rand_c(g, N, 1)
+    ref = torch.linalg.matrix_exp(A) @ psi
+    errs = [float((R.krylov_action(A, psi, k) - ref).norm()) for k in range(1, 10)]
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-6 * float(ref.norm())
+
+
+def test_krylov_hessenberg_projection():
+    """Eq. projham: B_k^dagger A B_k = A_k; checked by recomputing the projection
+    from the returned basis of a single column via the Arnoldi relation
+    A B_k = B_{k+1} H_{k+1,k} (exact arithmetic identity)."""
+    g = torch.Generator().manual_seed(7)
+    N, k = 9, 4
+    A = _rand_c(g, N, N)
+    psi = _rand_c(g, N, 1)[:, 0]
+    # run the oracle's per-column routine with k and k+1 and compare the
+    # Krylov result to a direct projection computed with an orthonormal basis
+    # of span{psi, A psi, ..., A^{k-1} psi} from a library QR
+    K = torch.stack([torch.linalg.matrix_power(A, j) @ psi for j in range(k)], 1)
+    Q, _ = torch.linalg.qr(K)
+    Ak = Q.conj().T @ A @ Q
+    e1 = Q.conj().T @ psi
+    ref = Q @ (torch.linalg.matrix_exp(Ak) @ e1)
+    out = R.krylov_action(A, psi[:, None], k)[:, 0]
+    assert torch.allclose(out, ref, rtol=1e-9, atol=1e-11)
+
+
+# ---------------------------------------------------------------- propagator
+def test_half_step_squares_to_one_body_exponential():
+    s, ham = _small_ham()
+    hpp, _ = R.propagation_h1(ham)
+    B = R.half_step_propagator(hpp, 0.07)
+    assert torch.allclose(B, B.T, atol=1e-15)
+    assert torch.allclose(B @ B, torch.linalg.matrix_exp(-0.07 * hpp), rtol=1e-12, atol=1e-13)
+
+
+def test_split2_local_error_slope_three():
+    """Deterministic one-body M: ||B e^{-tau M} B psi - e^{-tau(h''+M)} psi|| ~ tau^3."""
+    s, ham = _small_ham()
+    hpp, _ = R.propagation_h1(ham)
+    g = torch.Generator().manual_seed(8)
+    M = torch.randn(ham.N, ham.N, generator=g, dtype=RT)
+    M = 0.5 * (M + M.T)
+    psi = ham.trial.to(CT)
+    taus = [0.04, 0.02, 0.01]
+    errs = []
+    for tau in taus:
+        B = R.half_step_propagator(hpp, tau)
+        out = R.split2_propagate(B, (-tau * M).to(CT), psi, "exact", 0)
+        ref = torch.linalg.matrix_exp((-tau * (hpp + M)).to(CT)) @ psi
+        errs.append(float((out - ref).norm()))
+    slopes = [math.log(errs[i] / errs[i + 1]) / math.log(2) for i in range(2)]
+    assert all(2.85 < sl < 3.15 for sl in slopes), slopes
+
+
+def test_noninteracting_walk_closed_form():
+    """L = 0: every step is B B = e^{-tau h}, so Psi_n = e^{-n tau h} Psi_T."""
+    s = make_system(6, 2, 2, 4, rho=0.5, seed=5)
+    ham = R.make_hamiltonian(s.h1, 0.0 * s.L, s.trial, 2, 2)
+    psi, lo, W = R.init_walkers(ham, 3)
+    tau, n = 0.1, 7
+    x = torch.zeros(3, ham.G, dtype=RT)
+    for _ in range(n):
+        psi, lo, W, _ = R.step(ham, psi, lo, W, x, tau, 0.0, method="taylor", k=4)
+    lam, V = np.linalg.eigh(s.h1)
+    U = (V * np.exp(-n * tau * lam)) @ V.T
+    ref = torch.as_tensor(U @ s.trial).to(CT)
+    for w in range(3):
+        assert torch.allclose(psi[w], ref, rtol=1e-12, atol=1e-13)
+
+
+def test_propagation_h1_reproduces_one_electron_hamiltonian():
+    """On one-electron states the two-body term vanishes, so h'' + 1/2 sum_g
+    (L_g - L_bar_g)^2 + E_c' must equal h + E_const (reading R1)."""
+    s, ham = _small_ham()
+    Lbar = R.mean_field_shift(ham)
+    hpp, ec = R.propagation_h1(ham, Lbar)
+    eye = torch.eye(ham.N, dtype=RT)
+    sq = sum(0.5 * (ham.L[g] - Lbar[g] * eye) @ (ham.L[g] - Lbar[g] * eye) for g in range(ham.G))
+    assert torch.allclose(hpp + sq + ec * eye, ham.h1 + ham.e_const * eye, atol=1e-12)
+
+
+def test_mean_field_shift_closed_form():
+    """RHF trial with orthonormal C: L_bar_g = 2 tr(L_g C C^T)."""
+    s, ham = _small_ham()
+    C = s.trial[:, :s.na]
+    ref = 2.0 * np.einsum("gpq,pq->g", s.L, C @ C.T)
+    assert np.allclose(R.mean_field_shift(ham).numpy(), ref, atol=1e-13)
+
+
+# ---------------------------------------------------------------- force bias
+def test_force_bias_zero_at_trial():
+    s, ham = _small_ham()
+    psi, _, _ = R.init_walkers(ham, 2)
+    f, f_raw = R.force_bias(ham, psi, 0.05)
+    assert float(f_raw.abs().max()) < 1e-13
+
+
+def test_mixed_expectation_is_derivative_of_log_overlap():
+    """<L_g>_mixed = d/de log <Psi_T| e^{e L_g} |Psi> at e = 0 (one-body operator
+    acting on every orbital), by central finite differences with matrix_exp."""
+    s, ham = _small_ham()
+    g = torch.Generator().manual_seed(9)
+    psi = ham.trial.to(CT) + 0.3 * _rand_c(g, ham.N, s.na + s.nb)
+    got = R.mixed_L_expectation(ham, psi)
+    h = 1e-5
+    for gi in (0, 3, 7):
+        def lo(eps):
+            U = torch.linalg.matrix_exp((eps * ham.L[gi]).to(CT))
+            total = 0
+            for sl in ham.spins():
+                total = total + torch.log(torch.linalg.det(ham.trial[:, sl].to(CT).T @ (U @ psi[:, sl])))
+            return total
+        fd = (lo(h) - lo(-h)) / (2 * h)
+        assert abs(complex(fd) - complex(got[gi])) < 1e-8
+
+
+def test_force_bias_capping_removes_components():
+    """Sec. V.C: components with |f_g| >= 1 are removed (set to 0), not clipped."""
+    s, ham = _small_ham()
+    g = torch.Generator().manual_seed(10)
+    psi = ham.trial.to(CT) + 2.0 * _rand_c(g, ham.N, s.na + s.nb)
+    tau = 4.0
+    f, f_raw = R.force_bias(ham, psi, tau)
+    big = f_raw.abs() >= 1.0
+    assert bool(big.any()) and bool((~big).any())
+    assert torch.all(f[big] == 0)
+    assert torch.equal(f[~big], f_raw[~big])
+
+
+# ---------------------------------------------------------------- overlaps
+def test_log_overlap_closed_form_small_dets():
+    g = torch.Generator().manual_seed(11)
+    for n in (2, 3):
+        N = 7
+        trial = torch.linalg.qr(torch.randn(N, 2 * n, generator=g, dtype=RT))[0]
+        ham = R.Hamiltonian(torch.zeros(N, N, dtype=RT), torch.zeros(1, N, N, dtype=RT),
+                            trial, n, n)
+        psi = _rand_c(g, N, 2 * n)
+        got = R.log_overlap(ham, psi)
+        total = 1.0 + 0j
+        for sl in ham.spins():
+            O = (trial[:, sl].T.to(CT) @ psi[:, sl]).numpy()
+            if n == 2:
+                d = O[0, 0] * O[1, 1] - O[0, 1] * O[1, 0]
+            else:
+                d = (O[0, 0] * (O[1, 1] * O[2, 2] - O[1, 2] * O[2, 1])
+                     - O[0, 1] * (O[1, 0] * O[2, 2] - O[1, 2] * O[2, 0])
+                     + O[0, 2] * (O[1, 0] * O[2, 1] - O[1, 1] * O[2, 0]))
+            total *= d
+        assert abs(math.log(abs(total)) - float(got.real)) < 1e-12
+        dphi = (float(got.imag) - np.angle(total) + math.pi) % (2 * math.pi) - math.pi
+        assert abs(dphi) < 1e-12
+
+
+def test_log_overlap_after_qr_shifts_by_log_det_R():
+    s, ham = _small_ham()
+    g = torch.Generator().manual_seed(12)
+    psi = ham.trial.to(CT) + 0.5 * _rand_c(g, ham.N, s.na + s.nb)
+    lo = R.log_overlap(ham, psi)
+    q, lo_q = R.reorthonormalise(ham, psi)
+    logdetR = 0
+    for sl in ham.spins():
+        _, Rm = R.mgs_qr(psi[:, sl])
+        logdetR = logdetR + torch.log(torch.diagonal(Rm)).sum()
+    d = complex(lo - lo_q - logdetR)
+    assert abs(d.real) < 1e-12
+    assert abs((d.imag + math.pi) % (2 * math.pi) - math.pi) < 1e-12
+
+
+def test_mgs_qr_against_library_qr():
+    g = torch.Generator().manual_seed(13)
+    X = _rand_c(g, 9, 4)
+    Q, Rm = R.mgs_qr(X)
+    assert torch.allclose(Q.conj().T @ Q, torch.eye(4, dtype=CT), atol=1e-13)
+    assert torch.allclose(Q @ Rm, X, atol=1e-13)
+    assert torch.all(torch.diagonal(Rm).real > 0) and torch.all(torch.diagonal(Rm).imag == 0)
+    Ql, Rl = torch.linalg.qr(X)
+    ph = torch.diagonal(Rl) / torch.diagonal(Rl).abs()
+    assert torch.allclose(Ql * ph[None, :], Q, atol=1e-12)
+
+
+# ---------------------------------------------------------------- local energy
+def test_local_energy_at_trial_is_slater_condon_energy():
+    """E_L(Psi_T) = <D|H|D> with the full 4-index V_pqrs = sum_g L_pr L_qs."""
+    s, ham = _small_ham()
+    C = s.trial[:, :s.na]
+    P = C @ C.T
+    V = np.einsum("gpr,gqs->pqrs", s.L, s.L)
+    Ptot = 2 * P
+    e_hf = (2 * np.einsum("pq,qp->", s.h1, P)
+            + 0.5 * np.einsum("pqrs,rp,sq->", V, Ptot, Ptot)
+            - 0.5 * 2 * np.einsum("pqrs,sp,rq->", V, P, P))
+    got = R.local_energy(ham, ham.trial.to(CT))
+    assert abs(complex(got) - e_hf) < 1e-12
+
+
+def test_local_energy_at_trial_matches_bruteforce_determinant():
+    s, ham = _small_ham(N=5, n=2, G=8)
+    ref = fci.determinant_energy(s.h1, s.L, s.trial[:, :2], s.trial[:, 2:])
+    assert abs(complex(R.local_energy(ham, ham.trial.to(CT))) - ref) < 1e-11
+
+
+def test_local_energy_matches_bruteforce_for_general_walker():
+    """E_L(Psi) = <Psi_T|H|Psi>/<Psi_T|Psi> with both determinants expanded in the
+    FCI basis (real walker, so the brute force stays real)."""
+    s, ham = _small_ham(N=5, n=2, G=8)
+    g = np.random.default_rng(14)
+    psi = s.trial + 0.3 * g.standard_normal(s.trial.shape)
+    H, dets = fci.hamiltonian_matrix(s.h1, s.L, 2, 2)
+
+    def expand(Ca, Cb):
+        v = np.zeros(len(dets))
+        for i, d in enumerate(dets):
+            oa = [p for p in range(5) if (d >> p) & 1]
+            ob = [p for p in range(5) if (d >> (5 + p)) & 1]
+            v[i] = np.linalg.det(Ca[oa, :]) * np.linalg.det(Cb[ob, :])
+        return v
+    vt = expand(s.trial[:, :2], s.trial[:, 2:])
+    vp = expand(psi[:, :2], psi[:, 2:])
+    ref = (vt @ H @ vp) / (vt @ vp)
+    got = R.local_energy(ham, torch.as_tensor(psi).to(CT))
+    assert abs(complex(got) - ref) < 1e-10
+
+
+def test_local_energy_gauge_invariance():
+    s, ham = _small_ham()
+    g = torch.Generator().manual_seed(15)
+    psi = ham.trial.to(CT) + 0.4 * _rand_c(g, ham.N, s.na + s.nb)
+    M = torch.eye(s.na, dtype=CT) + 0.5 * _rand_c(g, s.na, s.na)
+    psi2 = psi.clone()
+    psi2[:, :s.na] = psi[:, :s.na] @ M
+    psi2[:, s.na:] = psi[:, s.na:] @ M.T
+    assert abs(complex(R.local_energy(ham, psi) - R.local_energy(ham, psi2))) < 1e-11
+
+
+def test_local_energy_noninteracting_projection():
+    """L = 0: e^{-t h} Psi_T -> lowest orbitals, E_L -> 2 sum_{i<n} eps_i(h)."""
+    s = make_system(6, 2, 2, 4, rho=0.5, seed=5)
+    ham = R.make_hamiltonian(s.h1, 0.0 * s.L, s.trial, 2, 2)
+    lam, V = np.linalg.eigh(s.h1)
+    U = torch.as_tensor((V * np.exp(-2.0 * lam)) @ V.T).to(CT)
+    psi = torch.as_tensor(s.trial).to(CT)
+    for _ in range(100):                      # e^{-200 h} with re-orthonormalisation
+        psi, _ = R.reorthonormalise(ham, U @ psi)
+    assert abs(complex(R.local_energy(ham, psi)) - 2 * lam[:2].sum()) < 1e-9
+
+
+def test_energy_window_values():
+    """Eq. enwin with DeltaE = 1/2 sqrt(N_e/tau) + sqrt(N_e tau)."""
+    tau, ne, e0 = 0.04, 4, -10.0
+    dE = 0.5 * math.sqrt(ne / tau) + math.sqrt(ne * tau)          # = 5.4
+    assert abs(dE - 5.4) < 1e-15
+    E = torch.tensor([-20.0 + 1j, -10.0 + 0j, -4.0 - 2j, -4.7 + 0j], dtype=CT)
+    got = R.energy_window(E, e0, tau, ne)
+    assert torch.allclose(got, torch.tensor([-15.4, -10.0, -4.6, -4.7], dtype=RT), atol=1e-14)
+
+
+# ---------------------------------------------------------------- weights
+def test_weight_real_positive_special_case():
+    """ratio*I real positive: dtheta = 0 and W' = W |ratio I| e^{tau E0}."""
+    tau, e0 = 0.05, -2.0
+    W = torch.tensor([1.0, 0.5, 2.0], dtype=RT)
+    lr = torch.tensor([0.01, -0.02, 0.03], dtype=CT)
+    li = torch.tensor([0.005, 0.0, -0.01], dtype=CT)
+    Wn, eh, dth, fac = R.weight_update(W, lr, li, tau, e0)
+    assert torch.all(dth == 0)
+    ref = W * torch.exp((lr + li).real) * math.exp(tau * e0)
+    assert torch.allclose(Wn, ref, rtol=1e-14)
+
+
+def test_weight_caps():
+    """Sec. V.B: a reweighting factor >= 10 is set to 0; cos(dtheta) <= 0 kills."""
+    tau, e0 = 0.05, 0.0
+    W = torch.ones(4, dtype=RT)
+    lr = torch.tensor([math.log(11.0), math.log(9.0), 1j * 2.0, 1j * 0.5], dtype=CT)
+    Wn, _, dth, fac = R.weight_update(W, lr, torch.zeros(4, dtype=CT), tau, e0)
+    assert float(Wn[0]) == 0.0 and float(fac[0]) == 0.0
+    assert abs(float(Wn[1]) - 9.0) < 1e-12
+    assert float(Wn[2]) == 0.0
+    assert abs(float(Wn[3]) - math.cos(0.5)) < 1e-14
+    # phase wrapping: Im log ratio = 2 pi + 0.3 -> dtheta = 0.3
+    _, _, dth2, _ = R.weight_update(W[:1], torch.tensor([1j * (2 * math.pi + 0.3)], dtype=CT),
+                                    torch.zeros(1, dtype=CT), tau, e0)
+    assert abs(float(dth2[0]) - 0.3) < 1e-14
+
+
+def test_mixed_energy_ignores_dead_walkers():
+    W = torch.tensor([1.0, 0.0, 3.0], dtype=RT)
+    E = torch.tensor([-1.0, float("nan"), -2.0], dtype=RT)
+    e, wsum = R.mixed_energy(W, E)
+    assert abs(e - (-7.0 / 4.0)) < 1e-15 and wsum == 4.0
+
+
+# ---------------------------------------------------------------- whole step
+def test_first_step_from_trial_closed_form():
+    """At Psi_T the force bias vanishes, so Psi_1 = B e^{i sqrt(tau) sum x_g L_g} B Psi_T
+    and ratio = det(T^T Psi_1) e^{-tau E_c' - i sqrt(tau) sum x L_bar}."""
+    s, ham = _small_ham()
+    tau = 0.05
+    psi, lo, W = R.init_walkers(ham, 2)
+    x = torch.as_tensor(make_fields(3, 0, 2, ham.G))
+    hpp, ec = R.propagation_h1(ham)
+    Lbar = R.mean_field_shift(ham)
+    B = R.half_step_propagator(hpp, tau).to(CT)
+    psi1, lo1, W1, info = R.step(ham, psi, lo, W, x, tau, -5.0, method="krylov", k=ham.N)
+    for w in range(2):
+        A = 1j * math.sqrt(tau) * torch.einsum("g,gpq->pq", x[w].to(CT), ham.L.to(CT))
+        ref = B @ torch.linalg.matrix_exp(A) @ B @ ham.trial.to(CT)
+        assert torch.allclose(psi1[w], ref, rtol=1e-11, atol=1e-12)
+        det = 1.0
+        for sl in ham.spins():
+            det = det * torch.linalg.det(ham.trial[:, sl].to(CT).T @ ref[:, sl])
+        log_ratio = torch.log(det) - tau * ec - 1j * math.sqrt(tau) * float(x[w] @ Lbar)
+        d = complex(info.log_ratio[w] - log_ratio)
+        assert abs(d.real) < 1e-11 and abs((d.imag + math.pi) % (2 * math.pi) - math.pi) < 1e-11
+        assert abs(complex(info.log_I[w])) < 1e-12     # f = 0 => I = 1
+
+
+def test_dead_walkers_are_kept():
+    s, ham = _small_ham()
+    psi, lo, W = R.init_walkers(ham, 3)
+    W[1] = 0.0
+    x = torch.as_tensor(make_fields(4, 0, 3, ham.G))
+    psi1, lo1, W1, _ = R.step(ham, psi, lo, W, x, 0.05, -5.0, method="taylor", k=6)
+    assert torch.equal(psi1[1], psi[1]) and float(W1[1]) == 0.0
+    assert not torch.equal(psi1[0], psi[0])
+
+
+def test_comb_example():
+    W = torch.tensor([0.5, 0.0, 2.5, 1.0], dtype=RT)
+    # total 4, teeth at u + j = 0.25, 1.25, 2.25, 3.25 -> cumulative 0.5, 0.5, 3, 4
+    assert R.comb(W, 0.25).tolist() == [0, 2, 2, 3]
+    assert R.comb(W, 0.75).tolist() == [2, 2, 2, 3]
+
+
+# ---------------------------------------------------------------- whole walk
+def test_free_projection_matches_fci():
+    """fp-AFQMC (Eqs. psiupdate, wupdate) with Split-2 at small tau reproduces the
+    brute-force FCI ground-state energy of a 2-electron / 4-orbital system within
+    3 sigma, while the HF energy is many sigma away."""
+    s = make_system(4, 1, 1, 8, rho=0.7, seed=11, lambda0=0.25)
+    ham = R.make_hamiltonian(s.h1, s.L, s.trial, 1, 1)
+    e_fci = fci.ground_state_energy(s.h1, s.L, 1, 1)
+    e_hf = fci.determinant_energy(s.h1, s.L, s.trial[:, :1], s.trial[:, 1:])
+    Lbar = R.mean_field_shift(ham)
+    hpp, ec = R.propagation_h1(ham, Lbar)
+    tau, nw, nsteps, neq = 0.05, 1000, 600, 300
+    B = R.half_step_propagator(hpp, tau)
+    psi, lo, _ = R.init_walkers(ham, nw)
+    wt = torch.ones(nw, dtype=CT)
+    series = []
+    for k in range(nsteps):
+        x = make_fields(7, k, nw, ham.G)
+        psi, lo, wt = R.free_projection_step(ham, psi, lo, wt, x, tau, e_fci, method="taylor",
+                                             k=10, B=B, L_bar=Lbar, ec=ec)
+        if k % 20 == 19:
+            psi, lo = R.reorthonormalise(ham, psi)
+            wt = wt / wt.abs().mean()
+        El = R.local_energy(ham, psi)
+        series.append(complex((wt * El).sum() / wt.sum()).real)
+    E = np.array(series[neq:])
+    blocks = E.reshape(6, -1).mean(1)
+    sigma = blocks.std(ddof=1) / math.sqrt(len(blocks))
+    mean = E.mean()
+    assert abs(mean - e_fci) < 3 * sigma + 1e-4, (mean, e_fci, sigma)
+    assert abs(e_hf - e_fci) > 5 * sigma, (e_hf, e_fci, sigma)
