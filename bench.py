@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Walker-steps/s of the ph-AFQMC walker step (Split-2 + Krylov + E_loc).
+
+Workload (large-step plain method): synthetic Hamiltonian with N=128 orbitals,
+20+20 electrons, 640 Cholesky vectors (lambda_g = rho^g, rho = 1e-5^(1/640)),
+RHF trial, 1024 walkers per GPU, tau = 0.05, Split-2 with the Krylov action
+of dimension 10, local energy and mixed estimator every step, modified
+Gram-Schmidt every 5 steps.  One step = one pass of the whole walker step over
+all walkers.  Multi-GPU (torchrun): every rank propagates its own walkers
+(weak scaling, no collective on the data path).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
+  python bench.py --impl reference ...   # the CPU oracle, timed on host cores
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "walker-steps/s (Split-2+Krylov+E_loc), mixed vs FP64 at ≤1e-4 Ha/walker"
+WORKLOAD = ("large-step plain method: N=128, Na=Nb=20, N_gamma=640 (decay rho=1e-5^(1/640)), "
+            "1024 walkers/GPU, tau=0.05, Split-2 + Krylov dim 10, E_loc every step, MGS every 5 steps")
+NW, TAU, KDIM, REORTHO = 1024, 0.05, 10, 5
+# peaks for the roofline denominators
+NOMINAL_FP64_TFLOPS = 1.25          # GB300 FP64 (recipe table)
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0  # recipe table
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-walkers", type=int, default=4)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.strip().split(",") for r in self.f.read().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def oracle_rate(system, n_walkers: int, n_steps: int, precision_note: str):
+    """Time the CPU oracle as it stands on a bounded sample of the workload."""
+    import numpy as np
+    import torch
+
+    from oracle import afqmc_ref as R
+    from paper_2403_02542_gb300.inputs import make_fields
+
+    ham = R.make_hamiltonian(system.h1, system.L, system.trial, system.na, system.nb)
+    Lbar = R.mean_field_shift(ham)
+    hpp, ec = R.propagation_h1(ham, Lbar)
+    B = R.half_step_propagator(hpp, TAU)
+    psi, lo, W = R.init_walkers(ham, n_walkers)
+    e0 = float(R.local_energy(ham, psi[:1]).real[0])
+    t0 = time.perf_counter()
+    per_step = []
+    for k in range(n_steps):
+        ts = time.perf_counter()
+        x = make_fields(99, k, n_walkers, ham.G)
+        psi, lo, W, _ = R.step(ham, psi, lo, W, x, TAU, e0, method="krylov", k=KDIM,
+                               reortho=(k + 1) % REORTHO == 0, B=B, L_bar=Lbar, ec=ec)
+        El = R.local_energy(ham, psi)
+        R.mixed_energy(W, R.energy_window(El, e0, TAU, ham.na + ham.nb))
+        per_step.append(time.perf_counter() - ts)
+    dt = time.perf_counter() - t0
+    return dict(value=n_walkers * n_steps / dt, unit="walker-steps/s", cores=torch.get_num_threads(),
+                kind="oracle",
+                sample=f"{n_walkers} walkers x {n_steps} steps of the same workload (FP64 oracle, "
+                       f"walker-by-walker Krylov), {dt:.1f} s"), per_step
+
+
+def config_dict(precision: str, world: int):
+    return {"workload": WORKLOAD, "walkers_per_gpu": NW, "N": 128, "na": 20, "nb": 20, "G": 640,
+            "tau": TAU, "expm": "krylov", "krylov_dim": KDIM, "reortho_every": REORTHO,
+            "precision": precision, "parallelism": f"walkers sharded over {world} GPU(s)",
+            "l2": "working set larger than L2 (walkers, Krylov basis, A_w > 129 MB)"}
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import torch
+
+    from paper_2403_02542_gb300.inputs import config_system
+    system = config_system("large")
+    nwalk = 2
+    total_steps = args.warmup + args.steps
+    _, per_step = oracle_rate(system, nwalk, total_steps, "")
+    timed = per_step[args.warmup:]
+    t = sum(timed)
+    value = nwalk * len(timed) / t
+    line = {
+        "metric": METRIC, "value": value, "unit": "walker-steps/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t / len(timed),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Hamiltonian, Gaussian fields)", "impl": "reference",
+        "config": config_dict("fp64 oracle", 1),
+        "cpu_baseline": {"value": value, "unit": "walker-steps/s", "cores": torch.get_num_threads(),
+                         "kind": "oracle",
+                         "sample": f"{nwalk} walkers per step of the same workload, {args.steps} "
+                                   f"timed steps after {args.warmup} warm-up steps"},
+        "e2e": {"value": value, "unit": "walker-steps/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2403_02542_gb300 import build as B
+    if not B.up_to_date():
+        if rank == 0:
+            B.build()
+        if world > 1:
+            dist.barrier()
+    from paper_2403_02542_gb300.api import Context
+    from paper_2403_02542_gb300.inputs import config_system
+
+    system = config_system("large")
+    N, G, na, nb = system.N, system.G, system.na, system.nb
+    ctx = Context(system.h1, system.L, system.trial, na, nb, system.e_const,
+                  precision=args.precision, device=dev)
+    w = ctx.new_walkers(NW)
+    ctx.init_walkers(w)
+    e_loc = torch.empty(NW, 2, dtype=torch.float64, device=dev)
+    e_mix = torch.empty(4, dtype=torch.float64, device=dev)
+    ctx.local_energy(w, 0.0, TAU, e_loc, e_mix)
+    e0 = float(e_loc[0, 0])
+
+    K, Wm = args.steps, args.warmup
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234 + rank)
+    fields = torch.randn(Wm + K, NW, G, dtype=torch.float64, device=dev, generator=gen)
+    step_idx = 0
+
+    def one(x):
+        nonlocal step_idx
+        step_idx += 1
+        ctx.step(w, x, TAU, e0, expm="krylov", order=KDIM, reortho=(step_idx % REORTHO == 0),
+                 measure=True, e_loc=e_loc, e_mix=e_mix)
+
+    for i in range(Wm):
+        one(fields[i])
+    torch.cuda.synchronize()
+
+    # -------- device-timed region: inputs resident in HBM
+    stream = torch.cuda.current_stream(dev)
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    l0 = ctx.launch_count
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(K):
+        one(fields[Wm + i])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = ctx.launch_count - l0
+    ctx.profile(False)
+    prof = ctx.profile_read()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t[0])
+    value = world * NW * K / (ms / 1000.0)
+    emix_final = float(e_mix[2])
+
+    # -------- end to end through the API with host buffers
+    rng = np.random.default_rng(4321 + rank)
+    host_fields = torch.from_numpy(rng.standard_normal((K, NW, G))).pin_memory()
+    x_dev = torch.empty(NW, G, dtype=torch.float64, device=dev)
+    emix_host = torch.empty(4, dtype=torch.float64).pin_memory()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(K):
+        x_dev.copy_(host_fields[i], non_blocking=True)
+        one(x_dev)
+        emix_host.copy_(e_mix, non_blocking=True)
+        stream.synchronize()
+        _ = float(emix_host[2])
+    torch.cuda.synchronize()
+    te = time.perf_counter() - t0
+    tt = torch.tensor([te], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        dist.barrier()
+    e2e = world * NW * K / float(tt[0])
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    # -------- roofline of the dominant kernel (exchange contraction of E_L)
+    ex_ms, ex_n = prof["exchange"]
+    flop_walker = G * 4 * (na * na + nb * nb) * N
+    ex_flop = flop_walker * NW
+    if args.precision == "fp64":
+        peak, bound, unit = NOMINAL_FP64_TFLOPS, "alu", "TFLOP/s"
+        peak_note = "FP64 nominal 1.25 TFLOP/s (recipe table); own FMA probe measured 1.19"
+    else:
+        peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+        bound, unit = "alu", "TFLOP/s"
+        peak_note = "FP32 ALU 152 SMs x 128 lanes x 2 x 2.07 GHz (recipe unit counts and clock)"
+    achieved = (ex_flop / (ex_ms / ex_n / 1000.0)) / 1e12 if ex_n else None
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu, _ = oracle_rate(system, args.cpu_sample_walkers, 2, "")
+    total_prof = sum(v[0] for v in prof.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": "walker-steps/s", "n_gpus": world,
+        "steps": K, "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.precision == "fp64" else "f32+f64 (mixed)",
+        "data": "synthetic (seeded Hamiltonian, Gaussian fields)",
+        "config": config_dict(args.precision, world),
+        "roofline": {"kernel": "exchange_kernel (Coulomb+exchange contraction of E_L)",
+                     "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "flop_per_launch": ex_flop, "avg_launch_ms": ex_ms / ex_n if ex_n else None,
+                     "peak_source": peak_note,
+                     "share_of_step": ex_ms / total_prof if total_prof else None},
+        "kernel_ms_per_step": {k: v[0] / K for k, v in prof.items()},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e, "unit": "walker-steps/s",
+                "h2d_bytes_per_step": NW * G * 8, "d2h_bytes_per_step": 4 * 8},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "e_mix_last": emix_final,
+    }
+    print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

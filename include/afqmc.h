@@ -1,0 +1,213 @@
+/*
+ * afqmc.h -- C ABI of the GB300 walker step of large-time-step phaseless AFQMC
+ * (Sukurma, Schlipf, Humer, Taheridehkordi, Kresse: "Towards Large-Scale AFQMC
+ * Calculations: Large Time Step Auxiliary-Field Quantum Monte Carlo").
+ *
+ * The library propagates a population of walkers.  A walker is a pair of
+ * complex Slater determinants (alpha: N x na, beta: N x nb), a real weight W,
+ * the complex log-overlap log <Psi_T|Psi> and a status word (Sec. II.A,
+ * Eq. wavefun_rep).  One call of afqmc_step performs, for every walker:
+ *   force bias with capping         (Eq. force_shift; Sec. V.C)
+ *   field assembly                  (Eq. heffTOT)
+ *   Split-2 propagation             (Sec. III.B) with the Taylor (Eq. taylor)
+ *                                   or Krylov (Eqs. krylovsub-krylov) action
+ *                                   of the one-body exponential
+ *   overlap ratio, hybrid energy    (Eqs. hyben, theta)
+ *   phaseless weight with capping   (Eq. phaseless; Sec. V.B)
+ *   optional re-orthonormalisation  (modified Gram-Schmidt; Sec. IV.D)
+ *   optional local energy, capping  (Eq. eloc, Eq. enwin) and the mixed
+ *   and mixed estimator              estimator E_k (Sec. II.A).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Sizes: N orbitals, na/nb electrons per spin (nc = na + nb columns),
+ *    G Cholesky vectors, Nw walkers.  1 <= N <= 512, 0 <= na, nb <= 80,
+ *    1 <= na + nb <= N, 1 <= G; otherwise AFQMC_EINVAL.
+ *  - Host matrices are row-major double.  h1[N*N] is the one-body matrix h_pq,
+ *    L[G*N*N] the Cholesky vectors L_g,pq with <pq|rs> = sum_g L_g,pr L_g,qs
+ *    (Sec. II.A), trial[nc*N] the trial orbitals stored orbital by orbital:
+ *    trial[j*N + p] is coefficient p of orbital j; orbitals [0, na) are
+ *    alpha, [na, nc) beta.  Host inputs are copied; the caller keeps
+ *    ownership and may free them after the call returns.
+ *  - Walker and field buffers are caller-owned DEVICE memory (for example
+ *    PyTorch tensors); the library never frees them and uses them
+ *    asynchronously on the context's stream.  The caller keeps them alive and
+ *    unmodified until that stream has been synchronised.
+ *  - psi[w][j][p] (w < Nw, j < nc, p < N) is interleaved complex: double2 for
+ *    an AFQMC_FP64 context, float2 for an AFQMC_MIXED context; 16-byte
+ *    (double) or 8-byte (float) alignment.
+ *  - Every call returns a status; nothing throws, aborts or traps.  Numerical
+ *    failure of a single walker (singular overlap, non-finite weight) sets its
+ *    status bits and its weight to 0 instead of failing the call.
+ */
+#ifndef AFQMC_H
+#define AFQMC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct afqmc_ctx afqmc_ctx;  /* opaque; owned by the library */
+
+typedef enum {
+  AFQMC_OK = 0,
+  AFQMC_EINVAL = 1,   /* null pointer, size out of range, unsupported value   */
+  AFQMC_EDOM = 2,     /* non-finite host input (h1, L, trial, tau, e_const)    */
+  AFQMC_ENOMEM = 3,   /* a device or host allocation failed                     */
+  AFQMC_ECUDA = 4,    /* a CUDA runtime call failed; afqmc_last_cuda_error()    */
+  AFQMC_ENOTSUP = 5,  /* propagator / exponential / precision not implemented   */
+  AFQMC_ESTATE = 6    /* call out of order (e.g. a step before afqmc_set_tau)   */
+} afqmc_status;
+
+/* Propagators (Sec. III).  Only Split-2, the paper's recommended one, is built. */
+enum { AFQMC_SPLIT2 = 0 };
+
+/* Action of the one-body exponential (Sec. IV). */
+enum { AFQMC_EXPM_TAYLOR = 0, AFQMC_EXPM_KRYLOV = 1 };
+
+/* Arithmetic of a context.
+ * AFQMC_FP64:  complex128 walkers, every step in FP64.
+ * AFQMC_MIXED: complex64 walkers; force bias, field assembly, B*Psi, A*Psi and
+ *              the exchange energy in FP32 (tensor cores where the kernel
+ *              says so); overlaps, log-determinants, LU, Gram-Schmidt, Krylov
+ *              coefficients, the small exponential, weights and all
+ *              reductions in FP64. */
+enum { AFQMC_FP64 = 0, AFQMC_MIXED = 1 };
+
+/* Per-walker status bits, OR-ed into status[w] (never cleared by the library). */
+#define AFQMC_W_FCAP      0x1u  /* at least one force-bias component removed      */
+#define AFQMC_W_REWEIGHT  0x2u  /* reweighting factor >= 10 set to 0 (Sec. V.B)  */
+#define AFQMC_W_PHASE     0x4u  /* cos(dtheta) <= 0: killed by the phaseless cut */
+#define AFQMC_W_NONFINITE 0x8u  /* non-finite ratio/energy/weight: weight set 0  */
+#define AFQMC_W_SINGULAR  0x10u /* zero pivot in the overlap matrix              */
+
+/* Walker population: caller-owned device buffers.
+ *   psi     [Nw][nc][N] complex (see above)
+ *   weight  [Nw] double, W >= 0; walkers with W == 0 are left untouched
+ *   logovl  [Nw][2] double, (Re, Im) of sum_sigma log det(trial_s^T psi_s);
+ *           the imaginary part is defined modulo 2*pi
+ *   status  [Nw] uint32, AFQMC_W_* bits */
+typedef struct {
+  int n_walkers;
+  void* psi;
+  double* weight;
+  double* logovl;
+  uint32_t* status;
+} afqmc_walkers;
+
+/* Parameters of one step.
+ *   tau         time step (> 0)
+ *   e0          best estimate of the ground-state energy E_0 (Eq. imag_prop)
+ *   propagator  AFQMC_SPLIT2
+ *   expm        AFQMC_EXPM_TAYLOR (order = Taylor order k >= 0) or
+ *               AFQMC_EXPM_KRYLOV (order = Krylov dimension 1 <= k <= 32)
+ *   reortho     nonzero: re-orthonormalise every determinant (modified
+ *               Gram-Schmidt) after the weight update and recompute logovl
+ *   measure     nonzero: evaluate E_L at the new walkers (see
+ *               afqmc_local_energy for the outputs) */
+typedef struct {
+  double tau;
+  double e0;
+  int propagator;
+  int expm;
+  int order;
+  int reortho;
+  int measure;
+} afqmc_step_params;
+
+/* Create a context for one Hamiltonian (Sec. II.A, Eq. mbham in Cholesky form)
+ * and trial determinant.  Computes on the device the mean-field shift
+ * L_bar_g = <Psi_T|L_g|Psi_T> (Eq. force_shift), the half-rotated vectors
+ * trial^T L_g, trial^T h1, the propagation one-body matrix
+ * h'' = h1 - 1/2 sum_g L_g L_g + sum_g L_bar_g L_g and its eigendecomposition
+ * (host, FP64 Jacobi), used for e^{-tau h''/2} (Sec. III.B).
+ *   out        receives the context
+ *   precision  AFQMC_FP64 or AFQMC_MIXED
+ *   stream     cudaStream_t to run on (NULL = legacy default stream)
+ * Errors: EINVAL (sizes/pointers), EDOM (non-finite input), ENOMEM, ECUDA. */
+afqmc_status afqmc_create(afqmc_ctx** out, int N, int n_alpha, int n_beta, int n_chol,
+                          const double* h1, const double* L, const double* trial,
+                          double e_const, int precision, void* stream);
+
+/* Set the time step: uploads B = e^{-tau h''/2} (Sec. III.B, computed exactly
+ * from the eigendecomposition).  afqmc_step calls it itself when its tau
+ * differs from the current one; call it before capturing steps in a CUDA
+ * graph.  Errors: EINVAL/EDOM (tau <= 0 or non-finite), ECUDA. */
+afqmc_status afqmc_set_tau(afqmc_ctx* ctx, double tau);
+
+/* Run subsequent work on another stream (cudaStream_t). */
+afqmc_status afqmc_set_stream(afqmc_ctx* ctx, void* stream);
+
+/* Psi_0 = Psi_T, W_0 = 1, logovl = log <Psi_T|Psi_T>, status = 0 (Sec. II.A). */
+afqmc_status afqmc_walkers_init(afqmc_ctx* ctx, const afqmc_walkers* w);
+
+/* One phaseless walker step of the whole population (see the file comment).
+ *   fields   device [Nw][G] double, standard-normal auxiliary fields x_g^w
+ *            (Eq. hstrafo); read only
+ *   e_loc    device [Nw][2] double (Re, Im of E_L) or NULL; written when
+ *            p->measure is nonzero
+ *   e_mix    device [4] double or NULL; written when p->measure is nonzero:
+ *            { sum_w W E_L_capped, sum_w W, E_k = ratio, live walkers }
+ * The context keeps scratch space sized for the largest Nw seen; a larger Nw
+ * reallocates it (do that before any graph capture).
+ * Errors: EINVAL, ENOTSUP (propagator/expm/order), ECUDA, ENOMEM. */
+afqmc_status afqmc_step(afqmc_ctx* ctx, const afqmc_walkers* w, const double* fields,
+                        const afqmc_step_params* p, double* e_loc, double* e_mix);
+
+/* Local energy E_L = <Psi_T|H|Psi>/<Psi_T|Psi> of every walker (Eq. eloc),
+ * the capped value of Eq. enwin with DeltaE = 1/2 sqrt(N_e/tau) + sqrt(N_e tau)
+ * around e0, and the mixed estimator E_k = sum W E_L_capped / sum W over
+ * walkers with W > 0 (Sec. II.A).  Outputs as for afqmc_step.
+ * Errors: EINVAL, ECUDA, ENOMEM. */
+afqmc_status afqmc_local_energy(afqmc_ctx* ctx, const afqmc_walkers* w, double e0, double tau,
+                                double* e_loc, double* e_mix);
+
+/* Block until the context's stream is idle; returns ECUDA on a pending error. */
+afqmc_status afqmc_sync(afqmc_ctx* ctx);
+
+/* Kernel classes of the per-class timer. */
+enum {
+  AFQMC_K_EXCHANGE = 0,   /* Coulomb + exchange contraction of E_L            */
+  AFQMC_K_FIELD = 1,      /* field assembly A = i sqrt(tau) sum_g c_g L_g      */
+  AFQMC_K_EXPM = 2,       /* products A*V of the Taylor / Krylov action        */
+  AFQMC_K_FORCEBIAS = 3,  /* <L_g>_mixed contraction                           */
+  AFQMC_K_HALFSTEP = 4,   /* B*Psi, B = e^{-tau h''/2}                         */
+  AFQMC_K_OVERLAP = 5,    /* overlap, LU, log det, Theta                       */
+  AFQMC_K_OTHER = 6,      /* everything else                                   */
+  AFQMC_K_COUNT = 7
+};
+
+/* Per-class launch timing.  enable != 0 clears the accumulators and starts
+ * recording a CUDA event before and after every launch on the context's
+ * stream (at most 32768 launches; later ones are not recorded); enable == 0
+ * stops.  afqmc_profile_read synchronises the stream, folds the recorded
+ * event pairs into the accumulators and returns, per class, the summed
+ * milliseconds ms[AFQMC_K_COUNT] and the number of launches n[AFQMC_K_COUNT].
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+afqmc_status afqmc_profile(afqmc_ctx* ctx, int enable);
+afqmc_status afqmc_profile_read(afqmc_ctx* ctx, double* ms, uint64_t* n);
+
+/* Number of kernel launches the context has issued so far. */
+uint64_t afqmc_launch_count(const afqmc_ctx* ctx);
+
+/* Release the context and its device memory (NULL is ignored). */
+void afqmc_destroy(afqmc_ctx* ctx);
+
+const char* afqmc_strerror(afqmc_status s);
+
+/* Host utility: eigendecomposition of a real symmetric n x n matrix a
+ * (row-major, not modified) by cyclic Jacobi rotations in FP64; on return
+ * evals[k] and column k of evecs (row-major n x n) form an eigenpair.  The
+ * contexts use it for h'' when building e^{-tau h''/2} (Sec. III.B, "computed
+ * exactly by diagonalisation").  Errors: EINVAL (n < 1, null), EDOM. */
+afqmc_status afqmc_host_eigh(int n, const double* a, double* evals, double* evecs);
+
+/* Text of the last CUDA error seen on the calling thread. */
+const char* afqmc_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AFQMC_H */

@@ -1,0 +1,161 @@
+"""Python face of the walker-step library: device buffers from PyTorch,
+everything else through the C ABI (include/afqmc.h)."""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    return None if t is None else t.data_ptr()
+
+
+@dataclass
+class WalkerSet:
+    """Caller-owned device buffers of a walker population.
+
+    psi     [Nw, nc, N] complex128 (FP64 context) or complex64 (mixed);
+            psi[w, j, p] is coefficient p of orbital j (alpha j < na).
+    weight  [Nw] float64
+    logovl  [Nw, 2] float64 (Re, Im of log <Psi_T|Psi>)
+    status  [Nw] int32 (AFQMC_W_* bits)
+    """
+
+    psi: torch.Tensor
+    weight: torch.Tensor
+    logovl: torch.Tensor
+    status: torch.Tensor
+
+    @property
+    def n(self) -> int:
+        return self.psi.shape[0]
+
+    def c_struct(self) -> L.Walkers:
+        return L.Walkers(self.n, _ptr(self.psi), _ptr(self.weight), _ptr(self.logovl),
+                         _ptr(self.status))
+
+
+class Context:
+    """One Hamiltonian + trial determinant on one GPU (afqmc_create)."""
+
+    def __init__(self, h1, chol, trial, na: int, nb: int, e_const: float = 0.0,
+                 precision: str = "fp64", device: str | torch.device = "cuda",
+                 stream: torch.cuda.Stream | None = None):
+        self.device = torch.device(device)
+        if self.device.type != "cuda":
+            raise ValueError("the walker step runs on a CUDA device only")
+        h1 = np.ascontiguousarray(h1, dtype=np.float64)
+        chol = np.ascontiguousarray(chol, dtype=np.float64)
+        # trial arrives as [N, na+nb] (columns = orbitals); the ABI wants orbital-major
+        trial_om = np.ascontiguousarray(np.asarray(trial, dtype=np.float64).T)
+        self.N = h1.shape[0]
+        self.G = chol.shape[0]
+        self.na, self.nb = int(na), int(nb)
+        self.nc = self.na + self.nb
+        self.precision = precision
+        self.ctype = torch.complex128 if precision == "fp64" else torch.complex64
+        prec = {"fp64": L.AFQMC_FP64, "mixed": L.AFQMC_MIXED}[precision]
+        self._stream = stream
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = L.lib().afqmc_create(ctypes.byref(handle), self.N, self.na, self.nb, self.G,
+                                      h1.ctypes.data, chol.ctypes.data, trial_om.ctypes.data,
+                                      float(e_const), prec, self._stream_ptr())
+        L.check(st, "afqmc_create")
+        self._h = handle
+
+    def _stream_ptr(self):
+        s = self._stream if self._stream is not None else torch.cuda.current_stream(self.device)
+        return s.cuda_stream
+
+    def _bind_stream(self):
+        L.check(L.lib().afqmc_set_stream(self._h, self._stream_ptr()), "afqmc_set_stream")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            L.lib().afqmc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------
+    def new_walkers(self, n: int) -> WalkerSet:
+        d = self.device
+        return WalkerSet(
+            psi=torch.empty(n, self.nc, self.N, dtype=self.ctype, device=d),
+            weight=torch.empty(n, dtype=torch.float64, device=d),
+            logovl=torch.empty(n, 2, dtype=torch.float64, device=d),
+            status=torch.zeros(n, dtype=torch.int32, device=d),
+        )
+
+    def set_tau(self, tau: float):
+        L.check(L.lib().afqmc_set_tau(self._h, float(tau)), "afqmc_set_tau")
+
+    def init_walkers(self, w: WalkerSet):
+        self._bind_stream()
+        cw = w.c_struct()
+        L.check(L.lib().afqmc_walkers_init(self._h, ctypes.byref(cw)), "afqmc_walkers_init")
+
+    def step(self, w: WalkerSet, fields: torch.Tensor, tau: float, e0: float,
+             expm: str = "krylov", order: int = 10, reortho: bool = False,
+             measure: bool = False, e_loc: torch.Tensor | None = None,
+             e_mix: torch.Tensor | None = None):
+        """One walker step (afqmc_step).  fields: device [Nw, G] float64."""
+        assert fields.dtype == torch.float64 and fields.is_cuda and fields.is_contiguous()
+        self._bind_stream()
+        p = L.StepParams(float(tau), float(e0), L.AFQMC_SPLIT2,
+                         {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV}[expm],
+                         int(order), int(bool(reortho)), int(bool(measure)))
+        cw = w.c_struct()
+        L.check(L.lib().afqmc_step(self._h, ctypes.byref(cw), fields.data_ptr(), ctypes.byref(p),
+                                   _ptr(e_loc), _ptr(e_mix)), "afqmc_step")
+
+    def local_energy(self, w: WalkerSet, e0: float, tau: float, e_loc=None, e_mix=None):
+        """E_L per walker [Nw, 2] and (sum W E_cap, sum W, E_k, live) [4]."""
+        if e_loc is None:
+            e_loc = torch.empty(w.n, 2, dtype=torch.float64, device=self.device)
+        if e_mix is None:
+            e_mix = torch.empty(4, dtype=torch.float64, device=self.device)
+        self._bind_stream()
+        cw = w.c_struct()
+        L.check(L.lib().afqmc_local_energy(self._h, ctypes.byref(cw), float(e0), float(tau),
+                                           e_loc.data_ptr(), e_mix.data_ptr()), "afqmc_local_energy")
+        return e_loc, e_mix
+
+    def sync(self):
+        L.check(L.lib().afqmc_sync(self._h), "afqmc_sync")
+
+    def profile(self, enable: bool):
+        """Start (clearing) or stop per-kernel-class event timing (afqmc_profile)."""
+        L.check(L.lib().afqmc_profile(self._h, int(bool(enable))), "afqmc_profile")
+
+    def profile_read(self) -> dict:
+        """{class: (total ms, launches)} accumulated since profile(True)."""
+        ms = (ctypes.c_double * 7)()
+        n = (ctypes.c_uint64 * 7)()
+        L.check(L.lib().afqmc_profile_read(self._h, ms, n), "afqmc_profile_read")
+        return {name: (ms[i], int(n[i])) for i, name in enumerate(L.KERNEL_CLASSES)}
+
+    @property
+    def launch_count(self) -> int:
+        return int(L.lib().afqmc_launch_count(self._h))
+
+
+def host_eigh(a: np.ndarray):
+    """afqmc_host_eigh: (evals, evecs) of a real symmetric matrix."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    n = a.shape[0]
+    ev = np.empty(n)
+    V = np.empty((n, n))
+    L.check(L.lib().afqmc_host_eigh(n, a.ctypes.data, ev.ctypes.data, V.ctypes.data),
+            "afqmc_host_eigh")
+    return ev, V

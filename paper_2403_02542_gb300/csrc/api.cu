@@ -1,0 +1,632 @@
+// C ABI of the walker-step library: context set-up and the step schedule.
+//
+// Set-up (once per Hamiltonian): half-rotated Cholesky vectors trial^T L_g,
+// the mean-field shift L_bar_g (Eq. force_shift), h'' = h1 - 1/2 sum_g L_g L_g
+// + sum_g L_bar_g L_g with E_c' = E_const - 1/2 sum_g L_bar_g^2, and the
+// eigendecomposition of h'' (host Jacobi) from which B = e^{-tau h''/2} is
+// built exactly for any tau (Sec. III.B).
+//
+// Step schedule (all on the context's stream):
+//   overlap/Theta -> force-bias GEMM -> bias finalisation -> field GEMM
+//   -> B Psi -> Taylor or Arnoldi/Krylov -> B Psi -> new overlap -> weights
+//   -> commit -> [MGS -> overlap] -> [overlap -> local energy -> E_k]
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace afq {
+cudaError_t launch_lsq(const double* L, double* LL, int N, int G, cudaStream_t s);
+cudaError_t launch_lbar(const double* Lh, const double* thT, double* Lbar, int G, size_t per, cudaStream_t s);
+cudaError_t launch_to_float(const double* a, float* b, size_t n, cudaStream_t s);
+}  // namespace afq
+
+using namespace afq;
+
+static thread_local char g_cuda_err[256] = "no error";
+
+static afqmc_status cuda_fail(cudaError_t e) {
+  snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+  if (e == cudaErrorMemoryAllocation) return AFQMC_ENOMEM;
+  return AFQMC_ECUDA;
+}
+
+#define CK(expr)                                     \
+  do {                                               \
+    cudaError_t _e = (expr);                         \
+    if (_e != cudaSuccess) return cuda_fail(_e);     \
+  } while (0)
+
+static bool all_finite(const double* a, size_t n) {
+  for (size_t i = 0; i < n; ++i)
+    if (!std::isfinite(a[i])) return false;
+  return true;
+}
+
+// ---------------------------------------------------------------- host eigh
+// Cyclic Jacobi for a real symmetric matrix (row-major, destroyed).  On
+// return evals[k] and column k of evecs (row-major n x n) are an eigenpair.
+static void jacobi_eigh(int n, double* a, double* evals, double* evecs) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) evecs[(size_t)i * n + j] = (i == j) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int p = 0; p < n; ++p) {
+      diag += a[(size_t)p * n + p] * a[(size_t)p * n + p];
+      for (int q = p + 1; q < n; ++q) off += a[(size_t)p * n + q] * a[(size_t)p * n + q];
+    }
+    if (off <= 1e-34 * (diag + off) || off == 0.0) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = a[(size_t)p * n + q];
+        if (apq == 0.0) continue;
+        const double app = a[(size_t)p * n + p], aqq = a[(size_t)q * n + q];
+        const double theta = (aqq - app) / (2.0 * apq);
+        double t;
+        if (std::fabs(theta) > 1e150)
+          t = 0.5 / theta;
+        else
+          t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double cth = 1.0 / std::sqrt(t * t + 1.0), sth = t * cth;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          const double akp = a[(size_t)k * n + p], akq = a[(size_t)k * n + q];
+          a[(size_t)k * n + p] = cth * akp - sth * akq;
+          a[(size_t)k * n + q] = sth * akp + cth * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          const double apk = a[(size_t)p * n + k], aqk = a[(size_t)q * n + k];
+          a[(size_t)p * n + k] = cth * apk - sth * aqk;
+          a[(size_t)q * n + k] = sth * apk + cth * aqk;
+        }
+        a[(size_t)p * n + q] = 0.0;
+        a[(size_t)q * n + p] = 0.0;
+        for (int k = 0; k < n; ++k) {
+          const double vkp = evecs[(size_t)k * n + p], vkq = evecs[(size_t)k * n + q];
+          evecs[(size_t)k * n + p] = cth * vkp - sth * vkq;
+          evecs[(size_t)k * n + q] = sth * vkp + cth * vkq;
+        }
+      }
+  }
+  for (int i = 0; i < n; ++i) evals[i] = a[(size_t)i * n + i];
+}
+
+// Invert a small real SPD matrix by Gauss-Jordan with partial pivoting.
+static bool small_inverse(int n, std::vector<double> m, std::vector<double>& inv) {
+  inv.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
+  for (int k = 0; k < n; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(m[(size_t)i * n + k]) > std::fabs(m[(size_t)piv * n + k])) piv = i;
+    if (m[(size_t)piv * n + k] == 0.0) return false;
+    if (piv != k)
+      for (int j = 0; j < n; ++j) {
+        std::swap(m[(size_t)k * n + j], m[(size_t)piv * n + j]);
+        std::swap(inv[(size_t)k * n + j], inv[(size_t)piv * n + j]);
+      }
+    const double d = m[(size_t)k * n + k];
+    for (int j = 0; j < n; ++j) { m[(size_t)k * n + j] /= d; inv[(size_t)k * n + j] /= d; }
+    for (int i = 0; i < n; ++i) {
+      if (i == k) continue;
+      const double f = m[(size_t)i * n + k];
+      if (f == 0.0) continue;
+      for (int j = 0; j < n; ++j) {
+        m[(size_t)i * n + j] -= f * m[(size_t)k * n + j];
+        inv[(size_t)i * n + j] -= f * inv[(size_t)k * n + j];
+      }
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------- workspace
+static void ws_free(Workspace& ws) {
+  void* ptrs[] = {ws.theta, ws.t, ws.c, ws.A, ws.psi_b, ws.term0, ws.term1, ws.acc, ws.psi_new, ws.basis,
+                  ws.hess, ws.beta, ws.scal, ws.logdet, ws.epart, ws.eloc, ws.ecap, ws.emix, ws.alive};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  ws = Workspace();
+}
+
+static afqmc_status ws_ensure(afqmc_ctx* c, int Nw, int kmax) {
+  if (Nw <= c->ws.n_walkers && kmax <= c->ws.kmax) return AFQMC_OK;
+  const int nw = Nw > c->ws.n_walkers ? Nw : c->ws.n_walkers;
+  const int km = kmax > c->ws.kmax ? kmax : c->ws.kmax;
+  CK(cudaStreamSynchronize(c->stream));
+  ws_free(c->ws);
+  Workspace& ws = c->ws;
+  const size_t cs = c->prec == AFQMC_FP64 ? 16 : 8;  // complex storage bytes
+  const size_t per = (size_t)c->nc * c->N;
+  CK(cudaMalloc(&ws.theta, nw * per * cs));
+  CK(cudaMalloc(&ws.t, (size_t)nw * c->G * cs));
+  CK(cudaMalloc(&ws.c, (size_t)nw * c->G * cs));
+  CK(cudaMalloc(&ws.A, (size_t)nw * c->N * c->N * cs));
+  CK(cudaMalloc(&ws.psi_b, nw * per * cs));
+  CK(cudaMalloc(&ws.term0, nw * per * cs));
+  CK(cudaMalloc(&ws.term1, nw * per * cs));
+  CK(cudaMalloc(&ws.acc, nw * per * cs));
+  CK(cudaMalloc(&ws.psi_new, nw * per * cs));
+  if (km > 0) {
+    CK(cudaMalloc(&ws.basis, (size_t)km * nw * per * cs));
+    CK(cudaMalloc(&ws.hess, (size_t)nw * c->nc * km * km * 2 * sizeof(double)));
+    CK(cudaMalloc(&ws.beta, (size_t)nw * c->nc * sizeof(double)));
+  }
+  CK(cudaMalloc(&ws.scal, (size_t)nw * SC_COUNT * sizeof(double)));
+  CK(cudaMalloc(&ws.logdet, (size_t)nw * 4 * sizeof(double)));
+  CK(cudaMalloc(&ws.epart, (size_t)nw * c->G * 8 * sizeof(double)));
+  CK(cudaMalloc(&ws.eloc, (size_t)nw * 2 * sizeof(double)));
+  CK(cudaMalloc(&ws.ecap, (size_t)nw * sizeof(double)));
+  CK(cudaMalloc(&ws.emix, 4 * sizeof(double)));
+  CK(cudaMalloc(&ws.alive, (size_t)nw));
+  ws.n_walkers = nw;
+  ws.kmax = km;
+  return AFQMC_OK;
+}
+
+// ---------------------------------------------------------------- profiler
+namespace afq {
+void prof_mark(afqmc_ctx* c, int cls, bool begin, cudaStream_t s) {
+  Prof& p = c->prof;
+  if (!p.on) return;
+  if (begin) {
+    if (p.used >= p.cap) { p.open_cls = -1; return; }
+    cudaEventRecord(p.pool[2 * p.used], s);
+    p.cls[p.used] = cls;
+    p.open_cls = cls;
+  } else {
+    if (p.open_cls < 0) return;
+    cudaEventRecord(p.pool[2 * p.used + 1], s);
+    ++p.used;
+    p.open_cls = -1;
+  }
+}
+}  // namespace afq
+
+static void prof_release(Prof& p) {
+  if (p.pool)
+    for (int i = 0; i < 2 * p.cap; ++i) cudaEventDestroy(p.pool[i]);
+  free(p.pool);
+  free(p.cls);
+  p = Prof();
+}
+
+// ---------------------------------------------------------------- set-up
+static void ctx_free(afqmc_ctx* c) {
+  if (!c) return;
+  prof_release(c->prof);
+  ws_free(c->ws);
+  void* ptrs[] = {c->d_L, c->d_Lh, c->d_trial, c->d_hhalf, c->d_Lbar, c->d_B, c->f_L, c->f_Lh, c->f_B};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  free(c->h_evals);
+  free(c->h_evecs);
+  delete c;
+}
+
+static afqmc_status ctx_setup(afqmc_ctx* c, const double* h1, const double* L, const double* trial) {
+  const int N = c->N, nc = c->nc, G = c->G;
+  const size_t NN = (size_t)N * N;
+  cudaStream_t s = c->stream;
+  CK(cudaMalloc(&c->d_L, (size_t)G * NN * sizeof(double)));
+  CK(cudaMalloc(&c->d_Lh, (size_t)G * nc * N * sizeof(double)));
+  CK(cudaMalloc(&c->d_trial, (size_t)nc * N * sizeof(double)));
+  CK(cudaMalloc(&c->d_hhalf, (size_t)nc * N * sizeof(double)));
+  CK(cudaMalloc(&c->d_Lbar, (size_t)G * sizeof(double)));
+  CK(cudaMalloc(&c->d_B, NN * sizeof(double)));
+  if (c->prec == AFQMC_MIXED) {
+    CK(cudaMalloc(&c->f_L, (size_t)G * NN * sizeof(float)));
+    CK(cudaMalloc(&c->f_Lh, (size_t)G * nc * N * sizeof(float)));
+    CK(cudaMalloc(&c->f_B, NN * sizeof(float)));
+  }
+  CK(cudaMemcpyAsync(c->d_L, L, (size_t)G * NN * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(c->d_trial, trial, (size_t)nc * N * sizeof(double), cudaMemcpyHostToDevice, s));
+
+  // h_half[j][q] = sum_p trial[j][p] h1[p][q]
+  std::vector<double> hh((size_t)nc * N, 0.0);
+  for (int j = 0; j < nc; ++j)
+    for (int p = 0; p < N; ++p) {
+      const double t = trial[(size_t)j * N + p];
+      if (t == 0.0) continue;
+      for (int q = 0; q < N; ++q) hh[(size_t)j * N + q] += t * h1[(size_t)p * N + q];
+    }
+  CK(cudaMemcpyAsync(c->d_hhalf, hh.data(), hh.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+
+  // Theta_T = trial (trial_s^T trial_s)^{-1} per spin (orthonormal trial: Theta_T = trial)
+  std::vector<double> thT((size_t)nc * N, 0.0);
+  for (int spin = 0; spin < 2; ++spin) {
+    const int n = spin ? c->nb : c->na, off = spin ? c->na : 0;
+    if (n == 0) continue;
+    std::vector<double> S((size_t)n * n, 0.0), Si;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        double v = 0.0;
+        for (int p = 0; p < N; ++p) v += trial[(size_t)(off + i) * N + p] * trial[(size_t)(off + j) * N + p];
+        S[(size_t)i * n + j] = v;
+      }
+    if (!small_inverse(n, S, Si)) return AFQMC_EINVAL;
+    for (int j = 0; j < n; ++j)
+      for (int p = 0; p < N; ++p) {
+        double v = 0.0;
+        for (int i = 0; i < n; ++i) v += trial[(size_t)(off + i) * N + p] * Si[(size_t)i * n + j];
+        thT[(size_t)(off + j) * N + p] = v;
+      }
+  }
+  double *d_thT = nullptr, *d_LL = nullptr;
+  CK(cudaMalloc(&d_thT, thT.size() * sizeof(double)));
+  CK(cudaMalloc(&d_LL, NN * sizeof(double)));
+  CK(cudaMemcpyAsync(d_thT, thT.data(), thT.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(launch_setup(c, s));
+  CK(launch_lbar(c->d_Lh, d_thT, c->d_Lbar, G, (size_t)nc * N, s));
+  CK(launch_lsq(c->d_L, d_LL, N, G, s));
+  c->launches += (c->prec == AFQMC_MIXED ? 3 : 1) + 2;
+  std::vector<double> LL(NN), Lbar(G);
+  CK(cudaMemcpyAsync(LL.data(), d_LL, NN * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaMemcpyAsync(Lbar.data(), c->d_Lbar, G * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  cudaFree(d_thT);
+  cudaFree(d_LL);
+
+  // h'' and E_c' (mean-field shift as an operator constant)
+  std::vector<double> hpp(NN);
+  for (size_t e = 0; e < NN; ++e) hpp[e] = h1[e] - 0.5 * LL[e];
+  double lb2 = 0.0;
+  for (int g = 0; g < G; ++g) {
+    const double lb = Lbar[g];
+    lb2 += lb * lb;
+    const double* Lg = L + (size_t)g * NN;
+    for (size_t e = 0; e < NN; ++e) hpp[e] += lb * Lg[e];
+  }
+  for (int p = 0; p < N; ++p)  // symmetrise against rounding
+    for (int q = p + 1; q < N; ++q) {
+      const double v = 0.5 * (hpp[(size_t)p * N + q] + hpp[(size_t)q * N + p]);
+      hpp[(size_t)p * N + q] = hpp[(size_t)q * N + p] = v;
+    }
+  c->ec_prime = c->e_const - 0.5 * lb2;
+  c->h_evals = (double*)malloc(N * sizeof(double));
+  c->h_evecs = (double*)malloc(NN * sizeof(double));
+  if (!c->h_evals || !c->h_evecs) return AFQMC_ENOMEM;
+  jacobi_eigh(N, hpp.data(), c->h_evals, c->h_evecs);
+  return AFQMC_OK;
+}
+
+// ---------------------------------------------------------------- step
+#define PK(cls, expr)                    \
+  do {                                   \
+    prof_mark(c, (cls), true, s);        \
+    CK(expr);                            \
+    prof_mark(c, (cls), false, s);       \
+  } while (0)
+
+template <typename R>
+static const R* pick(const double* d, const float* f);
+template <>
+const double* pick<double>(const double* d, const float*) { return d; }
+template <>
+const float* pick<float>(const double*, const float* f) { return f; }
+
+template <typename R>
+static afqmc_status run_energy(afqmc_ctx* c, const afqmc_walkers* w, double e0, double tau, double* e_loc,
+                               double* e_mix) {
+  cudaStream_t s = c->stream;
+  const int Nw = w->n_walkers;
+  PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, w->psi, c->ws.theta, c->ws.logdet, w->status, s));
+  int nl = 0;
+  CK(launch_energy<R>(c, Nw, w->weight, e0, tau, e_loc ? e_loc : c->ws.eloc, e_mix ? e_mix : c->ws.emix, s, &nl));
+  c->launches += 2 + nl;
+  return AFQMC_OK;
+}
+
+template <typename R>
+static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double* x, const afqmc_step_params* p,
+                             double* e_loc, double* e_mix) {
+  cudaStream_t s = c->stream;
+  const int Nw = w->n_walkers, N = c->N, nc = c->nc, G = c->G;
+  const long long per = (long long)nc * N, NN = (long long)N * N;
+  const double st = std::sqrt(p->tau);
+  const R* Lh = pick<R>(c->d_Lh, c->f_Lh);
+  const R* L = pick<R>(c->d_L, c->f_L);
+  const R* B = pick<R>(c->d_B, c->f_B);
+  Workspace& ws = c->ws;
+  const size_t cs = sizeof(typename C2<R>::t);
+
+  // Theta at the current walkers
+  PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, w->psi, ws.theta, ws.logdet, w->status, s));
+  // <L_g>_mixed = sum_{jq} Lh[g][j][q] Theta[w][j][q]
+  GemmArgs g{};
+  g.M = G; g.Nn = Nw; g.K = (int)per; g.batch = 1;
+  g.A = Lh; g.sa_m = per; g.sa_k = 1; g.sa_b = 0;
+  g.B = ws.theta; g.sb_n = per; g.sb_k = 1; g.sb_b = 0;
+  g.C = ws.t; g.sc_m = 1; g.sc_n = G; g.sc_b = 0;
+  g.alpha_re = 1.0; g.alpha_im = 0.0;
+  PK(AFQMC_K_FORCEBIAS, gemm<R>(g, false, EPI_STORE, s));
+  PK(AFQMC_K_OTHER, launch_bias_finalize<R>(c, Nw, x, st, s));
+  // A_w = i sqrt(tau) sum_g c_wg L_g
+  g = GemmArgs{};
+  g.M = (int)NN; g.Nn = Nw; g.K = G; g.batch = 1;
+  g.A = L; g.sa_m = 1; g.sa_k = NN;
+  g.B = ws.c; g.sb_n = G; g.sb_k = 1;
+  g.C = ws.A; g.sc_m = 1; g.sc_n = NN;
+  g.alpha_re = 0.0; g.alpha_im = st;
+  PK(AFQMC_K_FIELD, gemm<R>(g, false, EPI_STORE, s));
+  // psi_b = B psi
+  g = GemmArgs{};
+  g.M = N; g.Nn = Nw * nc; g.K = N; g.batch = 1;
+  g.A = B; g.sa_m = N; g.sa_k = 1;
+  g.B = w->psi; g.sb_n = N; g.sb_k = 1;
+  g.C = ws.psi_b; g.sc_m = 1; g.sc_n = N;
+  g.alpha_re = 1.0;
+  PK(AFQMC_K_HALFSTEP, gemm<R>(g, false, EPI_STORE, s));
+  c->launches += 5;
+
+  // per-walker products with A_w
+  GemmArgs ga{};
+  ga.M = N; ga.Nn = nc; ga.K = N; ga.batch = Nw;
+  ga.A = ws.A; ga.sa_m = N; ga.sa_k = 1; ga.sa_b = NN;
+  ga.sb_n = N; ga.sb_k = 1; ga.sb_b = per;
+  ga.sc_m = 1; ga.sc_n = N; ga.sc_b = per;
+  if (p->expm == AFQMC_EXPM_TAYLOR) {
+    CK(cudaMemcpyAsync(ws.acc, ws.psi_b, (size_t)Nw * per * cs, cudaMemcpyDeviceToDevice, s));
+    const void* cur = ws.psi_b;
+    for (int n = 1; n <= p->order; ++n) {
+      void* nxt = (n & 1) ? ws.term0 : ws.term1;
+      ga.B = cur; ga.C = nxt; ga.D = ws.acc;
+      ga.alpha_re = 1.0 / n; ga.alpha_im = 0.0;
+      PK(AFQMC_K_EXPM, gemm<R>(ga, true, EPI_STORE_ADD, s));
+      cur = nxt;
+    }
+    c->launches += p->order;
+  } else {
+    const int k = p->order;
+    const size_t bstride = (size_t)ws.n_walkers * per;
+    PK(AFQMC_K_OTHER, launch_normA<R>(c, Nw, s));
+    PK(AFQMC_K_OTHER, launch_krylov_init<R>(c, Nw, s));
+    for (int it = 0; it < k; ++it) {
+      ga.B = static_cast<char*>(ws.basis) + it * bstride * cs;
+      ga.C = ws.term0; ga.D = nullptr;
+      ga.alpha_re = 1.0; ga.alpha_im = 0.0;
+      PK(AFQMC_K_EXPM, gemm<R>(ga, true, EPI_STORE, s));
+      PK(AFQMC_K_OTHER, launch_krylov_orth<R>(c, Nw, it, k, s));
+    }
+    PK(AFQMC_K_OTHER, launch_krylov_finish<R>(c, Nw, k, s));
+    c->launches += 2 + 2 * k + 2;
+  }
+  // psi_new = B acc
+  g = GemmArgs{};
+  g.M = N; g.Nn = Nw * nc; g.K = N; g.batch = 1;
+  g.A = B; g.sa_m = N; g.sa_k = 1;
+  g.B = ws.acc; g.sb_n = N; g.sb_k = 1;
+  g.C = ws.psi_new; g.sc_m = 1; g.sc_n = N;
+  g.alpha_re = 1.0;
+  PK(AFQMC_K_HALFSTEP, gemm<R>(g, false, EPI_STORE, s));
+  // new overlap, weights, commit
+  PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, ws.psi_new, nullptr, ws.logdet, w->status, s));
+  PK(AFQMC_K_OTHER, launch_weights<R>(c, w, p->tau, p->e0, s));
+  PK(AFQMC_K_OTHER, launch_commit<R>(c, w, p->reortho, s));
+  c->launches += 4;
+  if (p->reortho) {
+    PK(AFQMC_K_OTHER, launch_mgs<R>(c, Nw, w->psi, ws.alive, s));
+    PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, w->psi, nullptr, ws.logdet, w->status, s));
+    PK(AFQMC_K_OTHER, launch_logovl_from_logdet(c, w, ws.alive, s));
+    c->launches += 3;
+  }
+  if (p->measure) return run_energy<R>(c, w, p->e0, p->tau, e_loc, e_mix);
+  return AFQMC_OK;
+}
+
+// ---------------------------------------------------------------- ABI
+extern "C" {
+
+const char* afqmc_strerror(afqmc_status s) {
+  switch (s) {
+    case AFQMC_OK: return "ok";
+    case AFQMC_EINVAL: return "invalid argument";
+    case AFQMC_EDOM: return "non-finite input";
+    case AFQMC_ENOMEM: return "out of memory";
+    case AFQMC_ECUDA: return "CUDA error";
+    case AFQMC_ENOTSUP: return "not supported";
+    case AFQMC_ESTATE: return "call out of order";
+  }
+  return "unknown status";
+}
+
+const char* afqmc_last_cuda_error(void) { return g_cuda_err; }
+
+afqmc_status afqmc_create(afqmc_ctx** out, int N, int n_alpha, int n_beta, int n_chol, const double* h1,
+                          const double* L, const double* trial, double e_const, int precision, void* stream) {
+  if (!out || !h1 || !L || !trial) return AFQMC_EINVAL;
+  *out = nullptr;
+  if (N < 1 || N > 512 || n_alpha < 0 || n_beta < 0 || n_alpha > 80 || n_beta > 80 || n_alpha + n_beta < 1 ||
+      n_alpha > N || n_beta > N || n_chol < 1)
+    return AFQMC_EINVAL;
+  if (precision != AFQMC_FP64 && precision != AFQMC_MIXED) return AFQMC_EINVAL;
+  const size_t NN = (size_t)N * N, nc = (size_t)(n_alpha + n_beta);
+  if (!std::isfinite(e_const) || !all_finite(h1, NN) || !all_finite(L, (size_t)n_chol * NN) ||
+      !all_finite(trial, nc * N))
+    return AFQMC_EDOM;
+  afqmc_ctx* c = new (std::nothrow) afqmc_ctx();
+  if (!c) return AFQMC_ENOMEM;
+  c->N = N; c->na = n_alpha; c->nb = n_beta; c->nc = (int)nc; c->G = n_chol; c->prec = precision;
+  c->e_const = e_const;
+  c->stream = static_cast<cudaStream_t>(stream);
+  afqmc_status st = ctx_setup(c, h1, L, trial);
+  if (st != AFQMC_OK) {
+    ctx_free(c);
+    return st;
+  }
+  *out = c;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_set_tau(afqmc_ctx* c, double tau) {
+  if (!c) return AFQMC_EINVAL;
+  if (!std::isfinite(tau)) return AFQMC_EDOM;
+  if (!(tau > 0.0)) return AFQMC_EINVAL;
+  const int N = c->N;
+  std::vector<double> Bh((size_t)N * N, 0.0), ex(N);
+  for (int k = 0; k < N; ++k) ex[k] = std::exp(-0.5 * tau * c->h_evals[k]);
+  for (int p = 0; p < N; ++p)
+    for (int q = 0; q < N; ++q) {
+      double v = 0.0;
+      for (int k = 0; k < N; ++k) v += c->h_evecs[(size_t)p * N + k] * ex[k] * c->h_evecs[(size_t)q * N + k];
+      Bh[(size_t)p * N + q] = v;
+    }
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(c->d_B, Bh.data(), Bh.size() * sizeof(double), cudaMemcpyHostToDevice));
+  if (c->prec == AFQMC_MIXED) {
+    CK(launch_to_float(c->d_B, c->f_B, Bh.size(), c->stream));
+    c->launches += 1;
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  c->tau = tau;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_set_stream(afqmc_ctx* c, void* stream) {
+  if (!c) return AFQMC_EINVAL;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return AFQMC_OK;
+}
+
+static afqmc_status check_walkers(const afqmc_ctx* c, const afqmc_walkers* w) {
+  if (!c || !w || w->n_walkers < 0 || w->n_walkers > (1 << 24)) return AFQMC_EINVAL;
+  if (w->n_walkers > 0 && (!w->psi || !w->weight || !w->logovl || !w->status)) return AFQMC_EINVAL;
+  const size_t align = c->prec == AFQMC_FP64 ? 16 : 8;
+  if (((uintptr_t)w->psi) % align || ((uintptr_t)w->weight) % 8 || ((uintptr_t)w->logovl) % 8 ||
+      ((uintptr_t)w->status) % 4)
+    return AFQMC_EINVAL;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_walkers_init(afqmc_ctx* c, const afqmc_walkers* w) {
+  afqmc_status st = check_walkers(c, w);
+  if (st != AFQMC_OK) return st;
+  if (w->n_walkers == 0) return AFQMC_OK;
+  st = ws_ensure(c, w->n_walkers, c->ws.kmax);
+  if (st != AFQMC_OK) return st;
+  if (c->prec == AFQMC_FP64) {
+    CK(launch_init_walkers<double>(c, w, c->stream));
+    CK(launch_overlap<double>(c, w->n_walkers, w->psi, nullptr, c->ws.logdet, w->status, c->stream));
+  } else {
+    CK(launch_init_walkers<float>(c, w, c->stream));
+    CK(launch_overlap<float>(c, w->n_walkers, w->psi, nullptr, c->ws.logdet, w->status, c->stream));
+  }
+  CK(launch_logovl_from_logdet(c, w, nullptr, c->stream));
+  c->launches += 3;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_step(afqmc_ctx* c, const afqmc_walkers* w, const double* fields, const afqmc_step_params* p,
+                        double* e_loc, double* e_mix) {
+  afqmc_status st = check_walkers(c, w);
+  if (st != AFQMC_OK) return st;
+  if (!p || (!fields && w->n_walkers > 0)) return AFQMC_EINVAL;
+  if (!std::isfinite(p->tau) || !std::isfinite(p->e0)) return AFQMC_EDOM;
+  if (!(p->tau > 0.0)) return AFQMC_EINVAL;
+  if (p->propagator != AFQMC_SPLIT2) return AFQMC_ENOTSUP;
+  if (p->expm == AFQMC_EXPM_TAYLOR) {
+    if (p->order < 0 || p->order > 64) return AFQMC_ENOTSUP;
+  } else if (p->expm == AFQMC_EXPM_KRYLOV) {
+    if (p->order < 1 || p->order > 32) return AFQMC_ENOTSUP;
+  } else {
+    return AFQMC_ENOTSUP;
+  }
+  if (w->n_walkers == 0) return AFQMC_OK;
+  if (p->tau != c->tau) {
+    st = afqmc_set_tau(c, p->tau);
+    if (st != AFQMC_OK) return st;
+  }
+  const int k = p->expm == AFQMC_EXPM_KRYLOV ? (p->order < c->N ? p->order : c->N) : 0;
+  st = ws_ensure(c, w->n_walkers, k);
+  if (st != AFQMC_OK) return st;
+  afqmc_step_params q = *p;
+  q.order = p->expm == AFQMC_EXPM_KRYLOV ? k : p->order;
+  if (c->prec == AFQMC_FP64) return run_step<double>(c, w, fields, &q, e_loc, e_mix);
+  return run_step<float>(c, w, fields, &q, e_loc, e_mix);
+}
+
+afqmc_status afqmc_local_energy(afqmc_ctx* c, const afqmc_walkers* w, double e0, double tau, double* e_loc,
+                                double* e_mix) {
+  afqmc_status st = check_walkers(c, w);
+  if (st != AFQMC_OK) return st;
+  if (!std::isfinite(tau) || !std::isfinite(e0)) return AFQMC_EDOM;
+  if (!(tau > 0.0)) return AFQMC_EINVAL;
+  if (w->n_walkers == 0) return AFQMC_OK;
+  st = ws_ensure(c, w->n_walkers, c->ws.kmax);
+  if (st != AFQMC_OK) return st;
+  if (c->prec == AFQMC_FP64) return run_energy<double>(c, w, e0, tau, e_loc, e_mix);
+  return run_energy<float>(c, w, e0, tau, e_loc, e_mix);
+}
+
+afqmc_status afqmc_sync(afqmc_ctx* c) {
+  if (!c) return AFQMC_EINVAL;
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaGetLastError());
+  return AFQMC_OK;
+}
+
+uint64_t afqmc_launch_count(const afqmc_ctx* c) { return c ? c->launches : 0; }
+
+afqmc_status afqmc_profile(afqmc_ctx* c, int enable) {
+  if (!c) return AFQMC_EINVAL;
+  Prof& p = c->prof;
+  if (enable) {
+    if (!p.pool) {
+      const int cap = 32768;
+      p.pool = (cudaEvent_t*)calloc((size_t)2 * cap, sizeof(cudaEvent_t));
+      p.cls = (int*)calloc(cap, sizeof(int));
+      if (!p.pool || !p.cls) { prof_release(p); return AFQMC_ENOMEM; }
+      for (int i = 0; i < 2 * cap; ++i) {
+        cudaError_t e = cudaEventCreate(&p.pool[i]);
+        if (e != cudaSuccess) {
+          p.cap = i / 2;
+          prof_release(p);
+          return cuda_fail(e);
+        }
+        p.cap = (i + 1) / 2;
+      }
+    }
+    CK(cudaStreamSynchronize(c->stream));
+    p.used = 0;
+    p.open_cls = -1;
+    for (int k = 0; k < AFQMC_K_COUNT; ++k) { p.ms[k] = 0.0; p.n[k] = 0; }
+    p.on = true;
+  } else {
+    p.on = false;
+  }
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_profile_read(afqmc_ctx* c, double* ms, uint64_t* n) {
+  if (!c || !ms || !n) return AFQMC_EINVAL;
+  Prof& p = c->prof;
+  CK(cudaStreamSynchronize(c->stream));
+  for (int i = 0; i < p.used; ++i) {
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, p.pool[2 * i], p.pool[2 * i + 1]));
+    p.ms[p.cls[i]] += t;
+    p.n[p.cls[i]] += 1;
+  }
+  p.used = 0;
+  for (int k = 0; k < AFQMC_K_COUNT; ++k) { ms[k] = p.ms[k]; n[k] = p.n[k]; }
+  return AFQMC_OK;
+}
+
+void afqmc_destroy(afqmc_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  ctx_free(c);
+}
+
+afqmc_status afqmc_host_eigh(int n, const double* a, double* evals, double* evecs) {
+  if (n < 1 || !a || !evals || !evecs) return AFQMC_EINVAL;
+  if (!all_finite(a, (size_t)n * n)) return AFQMC_EDOM;
+  std::vector<double> m(a, a + (size_t)n * n);
+  jacobi_eigh(n, m.data(), evals, evecs);
+  return AFQMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,175 @@
+// Internal declarations of the GB300 walker-step library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstddef>
+
+#include "../../include/afqmc.h"
+
+namespace afq {
+
+// ---------------------------------------------------------------- complex
+// Storage type of a complex number for real type R (interleaved re, im).
+template <typename R> struct C2;
+template <> struct C2<double> { typedef double2 t; };
+template <> struct C2<float> { typedef float2 t; };
+
+// FP64 complex used for all sensitive arithmetic.
+struct cd {
+  double re, im;
+};
+__host__ __device__ __forceinline__ cd mk(double r, double i) { return cd{r, i}; }
+__host__ __device__ __forceinline__ cd operator+(cd a, cd b) { return cd{a.re + b.re, a.im + b.im}; }
+__host__ __device__ __forceinline__ cd operator-(cd a, cd b) { return cd{a.re - b.re, a.im - b.im}; }
+__host__ __device__ __forceinline__ cd operator*(cd a, cd b) {
+  return cd{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__host__ __device__ __forceinline__ cd operator*(double s, cd a) { return cd{s * a.re, s * a.im}; }
+__host__ __device__ __forceinline__ cd conj(cd a) { return cd{a.re, -a.im}; }
+__host__ __device__ __forceinline__ double abs2(cd a) { return a.re * a.re + a.im * a.im; }
+__device__ __forceinline__ cd cdiv(cd a, cd b) {
+  // Smith's algorithm keeps the intermediate magnitudes bounded.
+  if (fabs(b.re) >= fabs(b.im)) {
+    double r = b.im / b.re, den = b.re + b.im * r;
+    return cd{(a.re + a.im * r) / den, (a.im - a.re * r) / den};
+  } else {
+    double r = b.re / b.im, den = b.re * r + b.im;
+    return cd{(a.re * r + a.im) / den, (a.im * r - a.re) / den};
+  }
+}
+__device__ __forceinline__ cd ld(const double2* p) { double2 v = *p; return cd{v.x, v.y}; }
+__device__ __forceinline__ cd ld(const float2* p) { float2 v = *p; return cd{(double)v.x, (double)v.y}; }
+__device__ __forceinline__ void st(double2* p, cd v) { *p = make_double2(v.re, v.im); }
+__device__ __forceinline__ void st(float2* p, cd v) { *p = make_float2((float)v.re, (float)v.im); }
+
+// ---------------------------------------------------------------- GEMM
+// C[b][m][n] = alpha * sum_k A[b][m][k] * B[b][n][k]  (strides in elements),
+// A real or complex, B complex; the epilogue mode decides what is stored.
+enum GemmEpi { EPI_STORE = 0, EPI_STORE_ADD = 1 };
+struct GemmArgs {
+  int M, Nn, K, batch;
+  const void* A;
+  long long sa_m, sa_k, sa_b;
+  const void* B;
+  long long sb_n, sb_k, sb_b;
+  void* C;
+  long long sc_m, sc_n, sc_b;
+  void* D;  // EPI_STORE_ADD: D += result (same strides as C)
+  double alpha_re, alpha_im;
+};
+template <typename R>
+cudaError_t gemm(const GemmArgs& a, bool a_complex, int epi, cudaStream_t s);
+
+// ---------------------------------------------------------------- context
+struct Workspace {
+  int n_walkers = 0;  // capacity
+  int kmax = 0;       // Krylov basis capacity
+  void* theta = nullptr;     // [Nw][nc][N] C2<R>
+  void* t = nullptr;         // [Nw][G] C2<R>   mixed <L_g> (force bias input)
+  void* c = nullptr;         // [Nw][G] C2<R>   c_g = x_g - f_g
+  void* A = nullptr;         // [Nw][N][N] C2<R>
+  void* psi_b = nullptr;     // [Nw][nc][N]
+  void* term0 = nullptr;     // [Nw][nc][N]
+  void* term1 = nullptr;     // [Nw][nc][N]
+  void* acc = nullptr;       // [Nw][nc][N]
+  void* psi_new = nullptr;   // [Nw][nc][N]
+  void* basis = nullptr;     // [kmax][Nw][nc][N]
+  double* hess = nullptr;    // [Nw*nc][kmax][kmax][2]
+  double* beta = nullptr;    // [Nw*nc]
+  double* scal = nullptr;    // [Nw][16] per-walker scalars (see SC_*)
+  double* logdet = nullptr;  // [Nw][2 spins][2]
+  double* epart = nullptr;   // [Nw][G][2 spins][4]  (tr re, tr im, exch re, exch im)
+  double* eloc = nullptr;    // [Nw][2]  scratch E_L when the caller passes none
+  double* ecap = nullptr;    // [Nw]     capped Re E_L
+  double* emix = nullptr;    // [4]
+  uint8_t* alive = nullptr;  // [Nw]     W > 0 at the start of the step
+};
+
+// per-walker scalar slots in Workspace::scal
+enum {
+  SC_LOGI_RE = 0, SC_LOGI_IM = 1,   // log I = sum_g x_g f_g - f_g^2/2
+  SC_CL_RE = 2, SC_CL_IM = 3,       // sum_g c_g L_bar_g
+  SC_NFCAP = 4,                     // removed force-bias components
+  SC_NORMA = 5,                     // ||A||_F
+  SC_E1_RE = 6, SC_E1_IM = 7,       // one-body energy sum_sigma tr(h_half Theta)
+  SC_COUNT = 16
+};
+
+}  // namespace afq
+
+namespace afq {
+// Kernel-class event profiler (see afqmc_profile in the header).
+struct Prof {
+  bool on = false;
+  cudaEvent_t* pool = nullptr;  // 2 events per recorded launch
+  int* cls = nullptr;           // class of each recorded launch
+  int cap = 0, used = 0, open_cls = -1;
+  double ms[AFQMC_K_COUNT] = {0};
+  uint64_t n[AFQMC_K_COUNT] = {0};
+};
+}  // namespace afq
+
+struct afqmc_ctx {
+  int N, na, nb, nc, G, prec;
+  double e_const = 0.0, ec_prime = 0.0, tau = -1.0;
+  cudaStream_t stream = nullptr;
+  // FP64 device constants
+  double* d_L = nullptr;      // [G][N][N]
+  double* d_Lh = nullptr;     // [G][nc][N]  Lh[g][j][q] = sum_p trial[j][p] L[g][p][q]
+  double* d_trial = nullptr;  // [nc][N]
+  double* d_hhalf = nullptr;  // [nc][N]     sum_p trial[j][p] h1[p][q]
+  double* d_Lbar = nullptr;   // [G]
+  double* d_B = nullptr;      // [N][N]
+  // FP32 copies for mixed contexts
+  float* f_L = nullptr;
+  float* f_Lh = nullptr;
+  float* f_B = nullptr;
+  // eigendecomposition of h'' (host, for B at any tau)
+  double* h_evals = nullptr;  // [N]
+  double* h_evecs = nullptr;  // [N][N], column k is eigenvector k
+  afq::Workspace ws;
+  afq::Prof prof;
+  uint64_t launches = 0;
+};
+
+namespace afq {
+
+// Record the start (begin=true) or end of a launch of class `cls` when the
+// context's profiler is on.
+void prof_mark(afqmc_ctx* c, int cls, bool begin, cudaStream_t s);
+
+// kernels (launch wrappers); every wrapper returns the launch error
+template <typename R>
+cudaError_t launch_overlap(const afqmc_ctx* c, int Nw, const void* psi, void* theta,
+                           double* logdet, uint32_t* status, cudaStream_t s);
+template <typename R>
+cudaError_t launch_bias_finalize(const afqmc_ctx* c, int Nw, const double* x, double sqrt_tau,
+                                 cudaStream_t s);
+template <typename R>
+cudaError_t launch_normA(const afqmc_ctx* c, int Nw, cudaStream_t s);
+template <typename R>
+cudaError_t launch_krylov_init(const afqmc_ctx* c, int Nw, cudaStream_t s);
+template <typename R>
+cudaError_t launch_krylov_orth(const afqmc_ctx* c, int Nw, int it, int k, cudaStream_t s);
+template <typename R>
+cudaError_t launch_krylov_finish(const afqmc_ctx* c, int Nw, int k, cudaStream_t s);
+template <typename R>
+cudaError_t launch_weights(const afqmc_ctx* c, const afqmc_walkers* w, double tau, double e0,
+                           cudaStream_t s);
+template <typename R>
+cudaError_t launch_commit(const afqmc_ctx* c, const afqmc_walkers* w, int reortho, cudaStream_t s);
+template <typename R>
+cudaError_t launch_mgs(const afqmc_ctx* c, int Nw, void* psi, const uint8_t* mask, cudaStream_t s);
+template <typename R>
+cudaError_t launch_energy(afqmc_ctx* c, int Nw, const double* weight, double e0, double tau,
+                          double* e_loc, double* e_mix, cudaStream_t s, int* n_launch);
+template <typename R>
+cudaError_t launch_init_walkers(const afqmc_ctx* c, const afqmc_walkers* w, cudaStream_t s);
+cudaError_t launch_setup(afqmc_ctx* c, cudaStream_t s);
+cudaError_t launch_logovl_from_logdet(const afqmc_ctx* c, const afqmc_walkers* w,
+                                      const uint8_t* mask, cudaStream_t s);
+cudaError_t launch_copy_alive(const afqmc_ctx* c, const afqmc_walkers* w, cudaStream_t s);
+
+}  // namespace afq

@@ -1,0 +1,407 @@
+// Per-walker FP64 linear algebra of the walker step:
+//  * overlap matrix O = trial^T Psi, LU with partial pivoting, log det O and
+//    Theta = Psi O^{-1} (the factor of the mixed density used by the force
+//    bias, Eq. force_shift, and the local energy, Eq. eloc);
+//  * modified Gram-Schmidt re-orthonormalisation of each determinant;
+//  * Arnoldi (one MGS pass) for the Krylov action of e^A (Eqs. krylovsub,
+//    projham, krylov) and the small exponential e^{A_k} e_1 (Sec. IV.C).
+// All arithmetic is FP64 whatever the storage type R of the walkers.
+#include <math_constants.h>
+
+#include "internal.cuh"
+
+namespace afq {
+
+namespace {
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Deterministic block sum of two doubles (fixed tree); every thread gets the result.
+template <int NT>
+__device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  a = warp_sum(a);
+  b = warp_sum(b);
+  __syncthreads();
+  if (lane == 0) { sh[2 * wid] = a; sh[2 * wid + 1] = b; }
+  __syncthreads();
+  double ra = 0.0, rb = 0.0;
+#pragma unroll
+  for (int i = 0; i < NT / 32; ++i) { ra += sh[2 * i]; rb += sh[2 * i + 1]; }
+  a = ra;
+  b = rb;
+}
+
+// ---------------------------------------------------------------- overlap
+// grid (Nw, 2 spins), block 128.  Shared: LU [n][n] and O^{-1} [n][n], FP64 complex.
+template <typename R>
+__global__ void __launch_bounds__(128) overlap_kernel(const typename C2<R>::t* __restrict__ psi,
+                                                      const double* __restrict__ trial, int N, int na,
+                                                      int nb, typename C2<R>::t* __restrict__ theta,
+                                                      double* __restrict__ logdet,
+                                                      uint32_t* __restrict__ status) {
+  extern __shared__ double smem_ov[];
+  const int w = blockIdx.x, spin = blockIdx.y;
+  const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double* ldw = logdet + (size_t)w * 4 + spin * 2;
+  if (n == 0) {
+    if (tid == 0) { ldw[0] = 0.0; ldw[1] = 0.0; }
+    return;
+  }
+  cd* LU = reinterpret_cast<cd*>(smem_ov);  // [n][n] row-major
+  cd* Inv = LU + n * n;                     // [n][n]
+  __shared__ int perm[128];
+  __shared__ int s_piv, s_swaps, s_sing;
+  const typename C2<R>::t* P = psi + ((size_t)w * nc + off) * N;
+
+  // O[i][j] = sum_p trial[off+i][p] psi[off+j][p]
+  for (int e = tid; e < n * n; e += nt) {
+    const int i = e / n, j = e % n;
+    const double* T = trial + (size_t)(off + i) * N;
+    const typename C2<R>::t* X = P + (size_t)j * N;
+    double sr = 0.0, si = 0.0;
+    for (int p = 0; p < N; ++p) {
+      cd x = ld(X + p);
+      sr = fma(T[p], x.re, sr);
+      si = fma(T[p], x.im, si);
+    }
+    LU[e] = mk(sr, si);
+  }
+  if (tid < n) perm[tid] = tid;
+  if (tid == 0) { s_swaps = 0; s_sing = 0; }
+  __syncthreads();
+
+  // LU with partial pivoting: (P O) = L U, row i of PO is row perm[i] of O
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      int piv = k;
+      double best = abs2(LU[k * n + k]);
+      for (int i = k + 1; i < n; ++i) {
+        double v = abs2(LU[i * n + k]);
+        if (v > best) { best = v; piv = i; }
+      }
+      s_piv = piv;
+      if (!(best > 0.0)) s_sing = 1;
+      if (piv != k) {
+        s_swaps ^= 1;
+        int t = perm[k]; perm[k] = perm[piv]; perm[piv] = t;
+      }
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    if (piv != k)
+      for (int j = tid; j < n; j += nt) {
+        cd t = LU[k * n + j]; LU[k * n + j] = LU[piv * n + j]; LU[piv * n + j] = t;
+      }
+    __syncthreads();
+    const cd pk = LU[k * n + k];
+    for (int i = k + 1 + tid; i < n; i += nt) LU[i * n + k] = cdiv(LU[i * n + k], pk);
+    __syncthreads();
+    const int rem = n - k - 1;
+    for (int e = tid; e < rem * rem; e += nt) {
+      const int i = k + 1 + e / rem, j = k + 1 + e % rem;
+      LU[i * n + j] = LU[i * n + j] - LU[i * n + k] * LU[k * n + j];
+    }
+    __syncthreads();
+  }
+
+  if (tid == 0) {
+    double lr = 0.0, li = s_swaps ? M_PI : 0.0;
+    for (int k = 0; k < n; ++k) {
+      cd u = LU[k * n + k];
+      lr += 0.5 * log(abs2(u));
+      li += atan2(u.im, u.re);
+    }
+    if (s_sing) { lr = CUDART_NAN; li = CUDART_NAN; }
+    ldw[0] = lr;
+    ldw[1] = li;
+    if (s_sing && status) atomicOr(status + w, (uint32_t)AFQMC_W_SINGULAR);
+  }
+  if (!theta) return;
+
+  // O^{-1} column j: L y = P e_j, U x = y.  (P e_j)_i = [perm[i] == j]
+  for (int j = tid; j < n; j += nt) {
+    for (int i = 0; i < n; ++i) {
+      cd y = mk(perm[i] == j ? 1.0 : 0.0, 0.0);
+      for (int k = 0; k < i; ++k) y = y - LU[i * n + k] * Inv[k * n + j];
+      Inv[i * n + j] = y;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+      cd x = Inv[i * n + j];
+      for (int k = i + 1; k < n; ++k) x = x - LU[i * n + k] * Inv[k * n + j];
+      Inv[i * n + j] = cdiv(x, LU[i * n + i]);
+    }
+  }
+  __syncthreads();
+
+  // Theta[j][p] = sum_i psi[i][p] Oinv[i][j]
+  typename C2<R>::t* Th = theta + ((size_t)w * nc + off) * N;
+  for (int e = tid; e < n * N; e += nt) {
+    const int j = e / N, p = e % N;
+    cd s = mk(0.0, 0.0);
+    for (int i = 0; i < n; ++i) s = s + ld(P + (size_t)i * N + p) * Inv[i * n + j];
+    st(Th + (size_t)j * N + p, s);
+  }
+}
+
+// ---------------------------------------------------------------- MGS QR
+// grid (Nw, 2 spins), block 256; one determinant per block, columns in order.
+template <typename R>
+__global__ void __launch_bounds__(256) mgs_kernel(typename C2<R>::t* __restrict__ psi, int N, int na,
+                                                  int nb, const uint8_t* __restrict__ mask) {
+  extern __shared__ double smem_q[];  // current column, FP64 complex [N]
+  __shared__ double red[2 * 8];
+  const int w = blockIdx.x, spin = blockIdx.y;
+  if (mask && !mask[w]) return;
+  const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
+  cd* q = reinterpret_cast<cd*>(smem_q);
+  typename C2<R>::t* P = psi + ((size_t)w * nc + off) * N;
+  for (int j = 0; j < n; ++j) {
+    for (int p = threadIdx.x; p < N; p += 256) q[p] = ld(P + (size_t)j * N + p);
+    __syncthreads();
+    for (int i = 0; i < j; ++i) {
+      const typename C2<R>::t* Qi = P + (size_t)i * N;
+      double dr = 0.0, di = 0.0;
+      for (int p = threadIdx.x; p < N; p += 256) {
+        cd a = ld(Qi + p), b = q[p];
+        dr += a.re * b.re + a.im * b.im;  // conj(a) b
+        di += a.re * b.im - a.im * b.re;
+      }
+      block_sum2<256>(dr, di, red);
+      const cd r = mk(dr, di);
+      for (int p = threadIdx.x; p < N; p += 256) q[p] = q[p] - r * ld(Qi + p);
+      __syncthreads();
+    }
+    double s2 = 0.0, dummy = 0.0;
+    for (int p = threadIdx.x; p < N; p += 256) s2 += abs2(q[p]);
+    block_sum2<256>(s2, dummy, red);
+    const double inv = 1.0 / sqrt(s2);
+    for (int p = threadIdx.x; p < N; p += 256) st(P + (size_t)j * N + p, inv * q[p]);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- Krylov
+// One warp per orbital column (walker w, column j); columns are numbered
+// col = w * nc + j and all column vectors are contiguous [N].
+template <typename R>
+__global__ void krylov_init_kernel(const typename C2<R>::t* __restrict__ x, typename C2<R>::t* __restrict__ v0,
+                                   double* __restrict__ beta, double* __restrict__ hess, int kmax, int N,
+                                   int ncols) {
+  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (col >= ncols) return;
+  // the Hessenberg block starts at zero: entries below the subdiagonal are never written
+  double* H = hess + (size_t)col * kmax * kmax * 2;
+  for (int e = lane; e < kmax * kmax * 2; e += 32) H[e] = 0.0;
+  const typename C2<R>::t* X = x + (size_t)col * N;
+  double s = 0.0;
+  for (int p = lane; p < N; p += 32) s += abs2(ld(X + p));
+  s = warp_sum(s);
+  const double b = sqrt(s);
+  const double inv = b > 0.0 ? 1.0 / b : 0.0;
+  for (int p = lane; p < N; p += 32) st(v0 + (size_t)col * N + p, inv * ld(X + p));
+  if (lane == 0) beta[col] = b;
+}
+
+// Step `it` of Arnoldi: w = A b_it is in `wv`; MGS against b_0..b_it, then the
+// next basis vector (or zero after an invariant subspace was found).
+template <typename R>
+__global__ void krylov_orth_kernel(typename C2<R>::t* __restrict__ wv, typename C2<R>::t* __restrict__ basis,
+                                   double* __restrict__ hess, const double* __restrict__ scal, int N,
+                                   int nc, int ncols, int it, int k, int kmax, size_t bstride) {
+  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (col >= ncols) return;
+  typename C2<R>::t* W = wv + (size_t)col * N;
+  double* H = hess + (size_t)col * kmax * kmax * 2;  // H[i][j] at (i*kmax + j)*2
+  for (int i = 0; i <= it; ++i) {
+    const typename C2<R>::t* V = basis + i * bstride + (size_t)col * N;
+    double dr = 0.0, di = 0.0;
+    for (int p = lane; p < N; p += 32) {
+      cd a = ld(V + p), b = ld(W + p);
+      dr += a.re * b.re + a.im * b.im;
+      di += a.re * b.im - a.im * b.re;
+    }
+    dr = warp_sum(dr);
+    di = warp_sum(di);
+    const cd h = mk(dr, di);
+    for (int p = lane; p < N; p += 32) st(W + p, ld(W + p) - h * ld(V + p));
+    __syncwarp();
+    if (lane == 0) { H[(i * kmax + it) * 2] = dr; H[(i * kmax + it) * 2 + 1] = di; }
+  }
+  if (it + 1 < k) {
+    double s = 0.0;
+    for (int p = lane; p < N; p += 32) s += abs2(ld(W + p));
+    s = warp_sum(s);
+    double hn = sqrt(s);
+    const double normA = scal[(size_t)(col / nc) * SC_COUNT + SC_NORMA];
+    const bool brk = !(hn > 1e-12 * normA);
+    const double inv = brk ? 0.0 : 1.0 / hn;
+    if (brk) hn = 0.0;
+    typename C2<R>::t* Vn = basis + (it + 1) * bstride + (size_t)col * N;
+    for (int p = lane; p < N; p += 32) st(Vn + p, inv * ld(W + p));
+    if (lane == 0) { H[((it + 1) * kmax + it) * 2] = hn; H[((it + 1) * kmax + it) * 2 + 1] = 0.0; }
+  }
+}
+
+// y = beta e^{H_k} e_1 by sub-stepping: (e^{H/m})^m e_1, each factor a Taylor
+// series on the vector summed until its terms fall below 1e-18 of the sum
+// (m chosen so that ||H/m||_1 <= 1/2).  Then psi_out = B_k y.
+// One thread per column for the small exponential; then a warp per column.
+template <typename R>
+__global__ void krylov_expm_kernel(double* __restrict__ hess, const double* __restrict__ beta, int ncols,
+                                   int k, int kmax) {
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= ncols) return;
+  double* H = hess + (size_t)col * kmax * kmax * 2;
+  cd v[32], t[32], u[32];
+  double n1 = 0.0;
+  for (int j = 0; j < k; ++j) {
+    double cs = 0.0;
+    for (int i = 0; i < k; ++i) cs += sqrt(abs2(mk(H[(i * kmax + j) * 2], H[(i * kmax + j) * 2 + 1])));
+    n1 = fmax(n1, cs);
+  }
+  int m = (int)ceil(n1 / 0.5);
+  if (m < 1) m = 1;
+  if (m > 4096) m = 4096;
+  const double sc = 1.0 / m;
+  for (int i = 0; i < k; ++i) v[i] = mk(i == 0 ? 1.0 : 0.0, 0.0);
+  for (int s = 0; s < m; ++s) {
+    for (int i = 0; i < k; ++i) { t[i] = v[i]; }
+    for (int d = 1; d <= 40; ++d) {
+      double tn = 0.0, an = 0.0;
+      for (int i = 0; i < k; ++i) {
+        cd a = mk(0.0, 0.0);
+        for (int j = 0; j < k; ++j) a = a + mk(H[(i * kmax + j) * 2], H[(i * kmax + j) * 2 + 1]) * t[j];
+        u[i] = (sc / d) * a;
+      }
+      for (int i = 0; i < k; ++i) {
+        t[i] = u[i];
+        v[i] = v[i] + u[i];
+        tn += abs2(u[i]);
+        an += abs2(v[i]);
+      }
+      if (tn <= 1e-36 * an) break;
+    }
+  }
+  // store y in column 0 of H (no longer needed)
+  const double b = beta[col];
+  for (int i = 0; i < k; ++i) {
+    H[(i * kmax + 0) * 2] = b * v[i].re;
+    H[(i * kmax + 0) * 2 + 1] = b * v[i].im;
+  }
+}
+
+template <typename R>
+__global__ void krylov_combine_kernel(const double* __restrict__ hess, const typename C2<R>::t* __restrict__ basis,
+                                      typename C2<R>::t* __restrict__ out, int N, int ncols, int k, int kmax,
+                                      size_t bstride) {
+  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (col >= ncols) return;
+  const double* H = hess + (size_t)col * kmax * kmax * 2;
+  for (int p = lane; p < N; p += 32) {
+    cd s = mk(0.0, 0.0);
+    for (int i = 0; i < k; ++i) {
+      const cd y = mk(H[(i * kmax) * 2], H[(i * kmax) * 2 + 1]);
+      s = s + y * ld(basis + i * bstride + (size_t)col * N + p);
+    }
+    st(out + (size_t)col * N + p, s);
+  }
+}
+
+template <typename R>
+__global__ void init_walkers_kernel(typename C2<R>::t* __restrict__ psi, const double* __restrict__ trial,
+                                    double* __restrict__ weight, uint32_t* __restrict__ status, int N, int nc,
+                                    int Nw) {
+  const size_t per = (size_t)nc * N;
+  const size_t total = per * Nw;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    st(psi + e, mk(trial[e % per], 0.0));
+    if (e % per == 0) {
+      const size_t w = e / per;
+      weight[w] = 1.0;
+      status[w] = 0u;
+    }
+  }
+}
+
+}  // namespace
+
+template <typename R>
+cudaError_t launch_overlap(const afqmc_ctx* c, int Nw, const void* psi, void* theta, double* logdet,
+                           uint32_t* status, cudaStream_t s) {
+  const int nmax = c->na > c->nb ? c->na : c->nb;
+  const size_t shm = (size_t)2 * nmax * nmax * sizeof(cd);
+  cudaError_t e = cudaFuncSetAttribute(overlap_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  if (e != cudaSuccess) return e;
+  overlap_kernel<R><<<dim3(Nw, 2), 128, shm, s>>>(static_cast<const typename C2<R>::t*>(psi), c->d_trial, c->N,
+                                                  c->na, c->nb, static_cast<typename C2<R>::t*>(theta), logdet,
+                                                  status);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_mgs(const afqmc_ctx* c, int Nw, void* psi, const uint8_t* mask, cudaStream_t s) {
+  const size_t shm = (size_t)c->N * sizeof(cd);
+  mgs_kernel<R><<<dim3(Nw, 2), 256, shm, s>>>(static_cast<typename C2<R>::t*>(psi), c->N, c->na, c->nb, mask);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_krylov_init(const afqmc_ctx* c, int Nw, cudaStream_t s) {
+  const int ncols = Nw * c->nc;
+  krylov_init_kernel<R><<<(ncols + 7) / 8, 256, 0, s>>>(
+      static_cast<const typename C2<R>::t*>(c->ws.psi_b), static_cast<typename C2<R>::t*>(c->ws.basis),
+      c->ws.beta, c->ws.hess, c->ws.kmax, c->N, ncols);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_krylov_orth(const afqmc_ctx* c, int Nw, int it, int k, cudaStream_t s) {
+  const int ncols = Nw * c->nc;
+  const size_t bstride = (size_t)c->ws.n_walkers * c->nc * c->N;
+  krylov_orth_kernel<R><<<(ncols + 7) / 8, 256, 0, s>>>(
+      static_cast<typename C2<R>::t*>(c->ws.term0), static_cast<typename C2<R>::t*>(c->ws.basis), c->ws.hess,
+      c->ws.scal, c->N, c->nc, ncols, it, k, c->ws.kmax, bstride);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_krylov_finish(const afqmc_ctx* c, int Nw, int k, cudaStream_t s) {
+  const int ncols = Nw * c->nc;
+  const size_t bstride = (size_t)c->ws.n_walkers * c->nc * c->N;
+  krylov_expm_kernel<R><<<(ncols + 127) / 128, 128, 0, s>>>(c->ws.hess, c->ws.beta, ncols, k, c->ws.kmax);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  krylov_combine_kernel<R><<<(ncols + 7) / 8, 256, 0, s>>>(
+      c->ws.hess, static_cast<const typename C2<R>::t*>(c->ws.basis), static_cast<typename C2<R>::t*>(c->ws.acc),
+      c->N, ncols, k, c->ws.kmax, bstride);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_init_walkers(const afqmc_ctx* c, const afqmc_walkers* w, cudaStream_t s) {
+  const size_t total = (size_t)w->n_walkers * c->nc * c->N;
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 152 * 32) blocks = 152 * 32;
+  init_walkers_kernel<R><<<blocks, 256, 0, s>>>(static_cast<typename C2<R>::t*>(w->psi), c->d_trial, w->weight,
+                                                w->status, c->N, c->nc, w->n_walkers);
+  return cudaGetLastError();
+}
+
+#define AFQ_INST(R)                                                                                       \
+  template cudaError_t launch_overlap<R>(const afqmc_ctx*, int, const void*, void*, double*, uint32_t*,   \
+                                         cudaStream_t);                                                    \
+  template cudaError_t launch_mgs<R>(const afqmc_ctx*, int, void*, const uint8_t*, cudaStream_t);          \
+  template cudaError_t launch_krylov_init<R>(const afqmc_ctx*, int, cudaStream_t);                         \
+  template cudaError_t launch_krylov_orth<R>(const afqmc_ctx*, int, int, int, cudaStream_t);               \
+  template cudaError_t launch_krylov_finish<R>(const afqmc_ctx*, int, int, cudaStream_t);                  \
+  template cudaError_t launch_init_walkers<R>(const afqmc_ctx*, const afqmc_walkers*, cudaStream_t);
+AFQ_INST(double)
+AFQ_INST(float)
+
+}  // namespace afq
