@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-walkers", type=int, default=4)
+    ap.add_argument("--walkers", type=int, default=NW,
+                    help="walkers per GPU (the workload has 1024; fewer only for small profiling cases)")
     return ap.parse_args()
 
 
@@ -135,7 +137,8 @@ def oracle_rate(system, n_walkers: int, n_steps: int, precision_note: str):
 
 
 def config_dict(precision: str, world: int):
-    return {"workload": WORKLOAD, "walkers_per_gpu": NW, "N": 128, "na": 20, "nb": 20, "G": 640,
+    wl = WORKLOAD if NW == 1024 else WORKLOAD.replace("1024 walkers/GPU", f"{NW} walkers/GPU (reduced)")
+    return {"workload": wl, "walkers_per_gpu": NW, "N": 128, "na": 20, "nb": 20, "G": 640,
             "tau": TAU, "expm": "krylov", "krylov_dim": KDIM, "reortho_every": REORTHO,
             "precision": precision, "parallelism": f"walkers sharded over {world} GPU(s)",
             "l2": "working set larger than L2 (walkers, Krylov basis, A_w > 129 MB)"}
@@ -179,6 +182,8 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
+    global NW
+    NW = args.walkers
     rank, world, local = dist_env()
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
