@@ -1,0 +1,73 @@
+"""Mixed-precision CUDA path (complex64 walkers; FP32 contractions; FP64
+overlaps, log-determinants, Krylov coefficients, small exponential, weights)
+against the FP64 CPU oracle.
+
+Bound (per step, from a common FP64 state produced by the oracle):
+|E_L(mixed) - E_L(oracle)| <= 1e-4 Ha per walker.  Weights, log-overlaps and
+walkers are reported with looser relative bounds that follow from complex64
+storage (unit roundoff 6e-8) amplified by the step."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import afqmc_ref as R
+from paper_2403_02542_gb300.inputs import config_system, make_fields, make_system
+from walk_helpers import oracle_walk
+
+pytestmark = pytest.mark.gpu
+E_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2403_02542_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _mixed_step_from_oracle_state(s, nw, n_pre, tau, k, seed, expm="krylov"):
+    from paper_2403_02542_gb300.api import Context
+    ham = R.make_hamiltonian(s.h1, s.L, s.trial, s.na, s.nb)
+    e0 = float(R.local_energy(ham, ham.trial.to(torch.complex128)).real)
+    ref, ties = oracle_walk(s, nw, n_pre + 1, tau, e0, expm, k, 0, seed=seed)
+    assert ties == 0
+    state, nxt = ref[n_pre - 1], ref[n_pre]
+    ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, precision="mixed")
+    w = ctx.new_walkers(nw)
+    w.psi.copy_(state["psi"].transpose(1, 2).to(torch.complex64))
+    w.weight.copy_(state["W"])
+    w.logovl.copy_(torch.stack([state["lo"].real, state["lo"].imag], 1))
+    w.status.zero_()
+    x = torch.as_tensor(make_fields(seed, n_pre, nw, s.G), device=ctx.device)
+    e_loc = torch.empty(nw, 2, dtype=torch.float64, device=ctx.device)
+    e_mix = torch.empty(4, dtype=torch.float64, device=ctx.device)
+    ctx.step(w, x, tau, e0, expm=expm, order=k, measure=True, e_loc=e_loc, e_mix=e_mix)
+    torch.cuda.synchronize()
+    El = torch.complex(e_loc[:, 0], e_loc[:, 1]).cpu()
+    live = nxt["W"] > 0
+    dE = (El - nxt["El"]).abs()[live]
+    dW = ((w.weight.cpu() - nxt["W"]).abs() / nxt["W"])[live]
+    g = w.psi.cpu().to(torch.complex128).transpose(1, 2)
+    dpsi = ((g - nxt["psi"]).flatten(1).norm(dim=1) / nxt["psi"].flatten(1).norm(dim=1))[live]
+    ctx.close()
+    return float(dE.max()), float(dW.max()), float(dpsi.max())
+
+
+def test_mixed_step_large_workload():
+    """N=128, 20+20 electrons, 640 vectors, Krylov 10, tau=0.05."""
+    s = config_system("large")
+    dE, dW, dpsi = _mixed_step_from_oracle_state(s, 6, 3, 0.05, 10, seed=77)
+    print(f"mixed vs oracle, large workload: max|dE_L| = {dE:.2e} Ha, "
+          f"max rel dW = {dW:.2e}, max rel dPsi = {dpsi:.2e}")
+    assert dE <= E_TOL
+    assert dW <= 1e-4 and dpsi <= 1e-4
+
+
+def test_mixed_step_taylor_ragged():
+    s = make_system(72, 5, 5, 150, rho=1e-5 ** (1 / 150), seed=4242)
+    dE, dW, dpsi = _mixed_step_from_oracle_state(s, 9, 2, 0.05, 6, seed=8, expm="taylor")
+    print(f"mixed vs oracle, N=72 Taylor-6: max|dE_L| = {dE:.2e} Ha, "
+          f"max rel dW = {dW:.2e}, max rel dPsi = {dpsi:.2e}")
+    assert dE <= E_TOL
+    assert dW <= 1e-4 and dpsi <= 1e-4
