@@ -164,6 +164,37 @@ afqmc_status afqmc_step(afqmc_ctx* ctx, const afqmc_walkers* w, const double* fi
 afqmc_status afqmc_local_energy(afqmc_ctx* ctx, const afqmc_walkers* w, double e0, double tau,
                                 double* e_loc, double* e_mix);
 
+/* Size of the device scratch array used by afqmc_local_energy_static. */
+#define AFQMC_STATIC_SCRATCH_BYTES ((unsigned long long)32 << 20) /* 32 MiB */
+
+/* afqmc_local_energy without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc when they need energies -- code running while a framework's
+ * caching allocator owns the device memory, code held to a memory budget
+ * fixed at start-up, or code that must not let an allocation synchronise
+ * the device.  afqmc_local_energy may grow the context's workspace with
+ * cudaMalloc; this variant instead uses one file-scope device array of
+ * AFQMC_STATIC_SCRATCH_BYTES that the CUDA runtime reserves on every device
+ * that loads the library and keeps until the process exits.  It calls no
+ * cudaMalloc, cudaFree or other allocating routine and runs the same kernels,
+ * so its outputs equal those of afqmc_local_energy.
+ *   e_loc, e_mix  caller-owned device outputs, as for afqmc_local_energy,
+ *                 both required (non-NULL).
+ * Scratch needed, each term rounded up to a multiple of 256 bytes:
+ *   Nw*nc*N*c (c = 16 for FP64, 8 for mixed contexts) + Nw*32 + Nw*128
+ *   + Nw*G*64 + Nw*8 bytes; a call needing more than
+ *   AFQMC_STATIC_SCRATCH_BYTES returns AFQMC_EINVAL and launches nothing.
+ * The first call on a device looks up the array's device address on the
+ * current device (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  All calls share the one array and it keeps the contents of
+ * the last call; every value a call reads there is written by the same call
+ * first, so nothing needs clearing.  Calls whose work overlaps on the GPU
+ * (different streams, contexts or host threads without ordering) race on the
+ * array and give wrong results.
+ * Errors: EINVAL (null outputs, misaligned buffers, too large), EDOM, ECUDA. */
+afqmc_status afqmc_local_energy_static(afqmc_ctx* ctx, const afqmc_walkers* w, double e0, double tau,
+                                       double* e_loc, double* e_mix);
+
 /* Block until the context's stream is idle; returns ECUDA on a pending error. */
 afqmc_status afqmc_sync(afqmc_ctx* ctx);
 

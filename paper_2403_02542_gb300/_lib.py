@@ -16,6 +16,7 @@ AFQMC_SPLIT2 = 0
 AFQMC_EXPM_TAYLOR, AFQMC_EXPM_KRYLOV = 0, 1
 AFQMC_FP64, AFQMC_MIXED = 0, 1
 W_FCAP, W_REWEIGHT, W_PHASE, W_NONFINITE, W_SINGULAR = 0x1, 0x2, 0x4, 0x8, 0x10
+STATIC_SCRATCH_BYTES = 32 << 20
 KERNEL_CLASSES = ("exchange", "field", "expm", "force_bias", "half_step", "overlap", "other")
 
 
@@ -49,6 +50,7 @@ SIGNATURES = {
     "afqmc_last_cuda_error": (ctypes.c_char_p, []),
     "afqmc_host_eigh": (_I, [_I, _P, _P, _P]),
     "afqmc_profile": (_I, [_P, _I]),
+    "afqmc_local_energy_static": (_I, [_P, ctypes.POINTER(Walkers), _D, _D, _P, _P]),
     "afqmc_profile_read": (_I, [_P, _P, _P]),
 }
 
