@@ -182,7 +182,9 @@ afqmc_status afqmc_local_energy(afqmc_ctx* ctx, const afqmc_walkers* w, double e
  *                 both required (non-NULL).
  * Scratch needed, each term rounded up to a multiple of 256 bytes:
  *   Nw*nc*N*c (c = 16 for FP64, 8 for mixed contexts) + Nw*32 + Nw*128
- *   + Nw*G*64 + Nw*8 bytes; a call needing more than
+ *   + Nw*G*64 + Nw*8 bytes, plus 2 * (8*Nw*na*Kp) bytes (Kp = N rounded up to
+ *   a multiple of 64) for mixed contexts whose exchange term runs on the
+ *   tensor cores (na == nb <= 64, N <= 128); a call needing more than
  *   AFQMC_STATIC_SCRATCH_BYTES returns AFQMC_EINVAL and launches nothing.
  * The first call on a device looks up the array's device address on the
  * current device (cudaGetSymbolAddress); make that first call before any

@@ -164,6 +164,7 @@ static afqmc_status ws_ensure(afqmc_ctx* c, int Nw, int kmax) {
   CK(cudaMalloc(&ws.alive, (size_t)nw));
   ws.n_walkers = nw;
   ws.kmax = km;
+  if (c->tc.ok) CK(tc_exchange_ws(c));
   return AFQMC_OK;
 }
 
@@ -198,8 +199,9 @@ static void prof_release(Prof& p) {
 static void ctx_free(afqmc_ctx* c) {
   if (!c) return;
   prof_release(c->prof);
+  tc_exchange_free(c);
   ws_free(c->ws);
-  void* ptrs[] = {c->d_L, c->d_Lh, c->d_trial, c->d_hhalf, c->d_Lbar, c->d_B, c->f_L, c->f_Lh, c->f_B};
+  void* ptrs[] = {c->d_L, c->d_Lh, c->d_trial, c->d_hhalf, c->d_Lbar, c->d_B, c->f_L, c->f_Lh, c->f_B, c->f_trial};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free(c->h_evals);
@@ -221,6 +223,7 @@ static afqmc_status ctx_setup(afqmc_ctx* c, const double* h1, const double* L, c
     CK(cudaMalloc(&c->f_L, (size_t)G * NN * sizeof(float)));
     CK(cudaMalloc(&c->f_Lh, (size_t)G * nc * N * sizeof(float)));
     CK(cudaMalloc(&c->f_B, NN * sizeof(float)));
+    CK(cudaMalloc(&c->f_trial, (size_t)nc * N * sizeof(float)));
   }
   CK(cudaMemcpyAsync(c->d_L, L, (size_t)G * NN * sizeof(double), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->d_trial, trial, (size_t)nc * N * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -260,6 +263,10 @@ static afqmc_status ctx_setup(afqmc_ctx* c, const double* h1, const double* L, c
   CK(cudaMalloc(&d_LL, NN * sizeof(double)));
   CK(cudaMemcpyAsync(d_thT, thT.data(), thT.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   CK(launch_setup(c, s));
+  if (c->prec == AFQMC_MIXED) {
+    CK(launch_to_float(c->d_trial, c->f_trial, (size_t)nc * N, s));
+    c->launches += 1;
+  }
   CK(launch_lbar(c->d_Lh, d_thT, c->d_Lbar, G, (size_t)nc * N, s));
   CK(launch_lsq(c->d_L, d_LL, N, G, s));
   c->launches += (c->prec == AFQMC_MIXED ? 3 : 1) + 2;
@@ -290,6 +297,11 @@ static afqmc_status ctx_setup(afqmc_ctx* c, const double* h1, const double* L, c
   c->h_evecs = (double*)malloc(NN * sizeof(double));
   if (!c->h_evals || !c->h_evecs) return AFQMC_ENOMEM;
   jacobi_eigh(N, hpp.data(), c->h_evals, c->h_evecs);
+  if (c->prec == AFQMC_MIXED && tc_exchange_plan(c)) {
+    CK(tc_exchange_setup(c, s));
+    c->launches += 1;
+    CK(cudaStreamSynchronize(s));
+  }
   return AFQMC_OK;
 }
 
@@ -565,6 +577,14 @@ afqmc_status afqmc_sync(afqmc_ctx* c) {
   if (!c) return AFQMC_EINVAL;
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaGetLastError());
+  if (c->tc.err) {  // a bounded wait of the tensor-core kernel gave up
+    int flag = 0;
+    CK(cudaMemcpy(&flag, c->tc.err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+      snprintf(g_cuda_err, sizeof g_cuda_err, "tensor-core exchange: pipeline wait timed out (code %d)", flag);
+      return AFQMC_ECUDA;
+    }
+  }
   return AFQMC_OK;
 }
 

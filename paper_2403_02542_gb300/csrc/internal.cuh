@@ -111,6 +111,23 @@ struct Prof {
 };
 }  // namespace afq
 
+namespace afq {
+// Plan and buffers of the tensor-core exchange contraction (mixed contexts).
+struct TcPlan {
+  bool ok = false;
+  int n = 0, gpt = 0, T = 0, Kp = 0, KC = 0, Wc = 0, NB = 0, S = 0, b_cap = 0;
+  void* a_hi = nullptr;  // [2 spins][T][128][Kp] bf16, Lh split hi/lo
+  void* a_lo = nullptr;
+  void* b_hi = nullptr;  // [2 spins][cap][re,im][n][Kp] bf16, Theta split hi/lo
+  void* b_lo = nullptr;
+  void* err = nullptr;   // device int: nonzero after a bounded wait timed out
+  alignas(64) unsigned char map_a_hi[128];
+  alignas(64) unsigned char map_a_lo[128];
+  alignas(64) unsigned char map_b_hi[128];
+  alignas(64) unsigned char map_b_lo[128];
+};
+}  // namespace afq
+
 struct afqmc_ctx {
   int N, na, nb, nc, G, prec;
   double e_const = 0.0, ec_prime = 0.0, tau = -1.0;
@@ -126,11 +143,13 @@ struct afqmc_ctx {
   float* f_L = nullptr;
   float* f_Lh = nullptr;
   float* f_B = nullptr;
+  float* f_trial = nullptr;  // [nc][N]
   // eigendecomposition of h'' (host, for B at any tau)
   double* h_evals = nullptr;  // [N]
   double* h_evecs = nullptr;  // [N][N], column k is eigenvector k
   afq::Workspace ws;
   afq::Prof prof;
+  afq::TcPlan tc;
   uint64_t launches = 0;
 };
 
@@ -171,5 +190,14 @@ cudaError_t launch_setup(afqmc_ctx* c, cudaStream_t s);
 cudaError_t launch_logovl_from_logdet(const afqmc_ctx* c, const afqmc_walkers* w,
                                       const uint8_t* mask, cudaStream_t s);
 cudaError_t launch_copy_alive(const afqmc_ctx* c, const afqmc_walkers* w, cudaStream_t s);
+
+// tensor-core exchange (k_exchange_tc.cu)
+bool tc_exchange_plan(afqmc_ctx* c);
+cudaError_t tc_exchange_setup(afqmc_ctx* c, cudaStream_t s);
+cudaError_t tc_exchange_ws(afqmc_ctx* c);
+size_t tc_exchange_plane_bytes(const TcPlan& P, int cap);
+cudaError_t tc_exchange_bind(TcPlan& P, void* b_hi, void* b_lo, int cap);
+void tc_exchange_free(afqmc_ctx* c);
+cudaError_t tc_exchange_launch(afqmc_ctx* c, int Nw, const void* theta, double* epart, cudaStream_t s);
 
 }  // namespace afq

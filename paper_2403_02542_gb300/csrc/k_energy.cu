@@ -176,6 +176,7 @@ __global__ void __launch_bounds__(256) onebody_kernel(const typename C2<R>::t* _
 // MAXE entries of T in registers; q is staged through shared memory in
 // slabs of QT.  Outputs epart[w][g][spin] = (tr T, sum_ij T_ij T_ji).
 constexpr int EX_NT = 256, EX_QT = 32, EX_GCHUNK = 16;
+constexpr int EX_QS = EX_QT + 1;  // padded row stride: rows j of a slab fall in distinct banks
 template <typename R, int MAXE>
 __global__ void __launch_bounds__(EX_NT) exchange_kernel(const typename C2<R>::t* __restrict__ theta,
                                                          const R* __restrict__ Lh, double* __restrict__ epart,
@@ -194,9 +195,9 @@ __global__ void __launch_bounds__(EX_NT) exchange_kernel(const typename C2<R>::t
     return;
   }
   R* sL = reinterpret_cast<R*>(smem_ex);                 // [n][QT]
-  R* sTr = sL + n * EX_QT;                               // [n][QT]
-  R* sTi = sTr + n * EX_QT;                              // [n][QT]
-  cd* sT = reinterpret_cast<cd*>(smem_ex + (3 * n * EX_QT * sizeof(R) + 7) / 8);  // [n][n]
+  R* sTr = sL + n * EX_QS;                               // [n][QS]
+  R* sTi = sTr + n * EX_QS;                              // [n][QS]
+  cd* sT = reinterpret_cast<cd*>(smem_ex + (3 * n * EX_QS * sizeof(R) + 7) / 8);  // [n][n]
   const int nn = n * n;
   const typename C2<R>::t* Th = theta + ((size_t)w * nc + off) * N;
   for (int g = g0; g < g1; ++g) {
@@ -215,9 +216,9 @@ __global__ void __launch_bounds__(EX_NT) exchange_kernel(const typename C2<R>::t
           tr = v.x;
           ti = v.y;
         }
-        sL[l] = lv;
-        sTr[l] = tr;
-        sTi[l] = ti;
+        sL[i * EX_QS + qq] = lv;
+        sTr[i * EX_QS + qq] = tr;
+        sTi[i * EX_QS + qq] = ti;
       }
       __syncthreads();
 #pragma unroll
@@ -225,9 +226,9 @@ __global__ void __launch_bounds__(EX_NT) exchange_kernel(const typename C2<R>::t
         const int idx = threadIdx.x + e * EX_NT;
         if (idx < nn) {
           const int i = idx / n, j = idx % n;
-          const R* a = sL + i * EX_QT;
-          const R* br = sTr + j * EX_QT;
-          const R* bi = sTi + j * EX_QT;
+          const R* a = sL + i * EX_QS;
+          const R* br = sTr + j * EX_QS;
+          const R* bi = sTi + j * EX_QS;
           R sr = ar[e], si = ai[e];
 #pragma unroll 8
           for (int qq = 0; qq < EX_QT; ++qq) {
@@ -417,7 +418,7 @@ cudaError_t launch_energy(afqmc_ctx* c, int Nw, const double* weight, double e0,
   if (e != cudaSuccess) return e;
   const int nmax = c->na > c->nb ? c->na : c->nb;
   const int nn = nmax * nmax;
-  const size_t shm = ((3 * nmax * EX_QT * sizeof(R) + 7) / 8) * 8 + (size_t)nn * sizeof(cd);
+  const size_t shm = ((3 * nmax * EX_QS * sizeof(R) + 7) / 8) * 8 + (size_t)nn * sizeof(cd);
   const dim3 grid(Nw, 2, (c->G + EX_GCHUNK - 1) / EX_GCHUNK);
   const R* Lh = std::is_same<R, double>::value ? reinterpret_cast<const R*>(c->d_Lh)
                                                : reinterpret_cast<const R*>(c->f_Lh);
@@ -430,7 +431,13 @@ cudaError_t launch_energy(afqmc_ctx* c, int Nw, const double* weight, double e0,
     exchange_kernel<R, ME><<<grid, EX_NT, shm, s>>>(th, Lh, c->ws.epart, c->N, c->na, c->nb, c->G);       \
     prof_mark(c, AFQMC_K_EXCHANGE, false, s);                                                            \
   } while (0)
-  if (nn <= 4 * EX_NT)
+  if (std::is_same<R, float>::value && c->tc.ok) {
+    // complex64 walkers: the contraction runs on the tensor cores (BF16x3)
+    prof_mark(c, AFQMC_K_EXCHANGE, true, s);
+    e = tc_exchange_launch(c, Nw, c->ws.theta, c->ws.epart, s);
+    prof_mark(c, AFQMC_K_EXCHANGE, false, s);
+    if (e != cudaSuccess) return e;
+  } else if (nn <= 4 * EX_NT)
     AFQ_EX(4);
   else if (nn <= 16 * EX_NT)
     AFQ_EX(16);

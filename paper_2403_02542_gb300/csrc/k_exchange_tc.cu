@@ -1,0 +1,584 @@
+// Coulomb and exchange contractions of the local energy on the 5th-generation
+// tensor cores (mixed-precision contexts).
+//
+// For every walker w, spin s and Cholesky vector g the local energy (Eq. eloc
+// with <pq|rs> = sum_g L_g,pr L_g,qs) needs T = Lh_gs Theta_ws^T (n x n,
+// K = N), its trace and sum_ij T_ij T_ji.  Across walkers and g this is one
+// dense contraction with a block-diagonal epilogue:
+//   rows    (g, i)        : the half-rotated Cholesky vectors Lh (operand A),
+//   columns (w, re/im, j) : Theta split into real and imaginary planes (B),
+//   K       q             : the orbital index.
+// Precision: both operands are split x = hi + lo into bfloat16 pairs and
+// T = A_hi B_hi + A_hi B_lo + A_lo B_hi is accumulated in FP32 (three
+// kind::f16 MMAs per K step); the dropped lo*lo term is below 2^-16 relative.
+//
+// Work decomposition: one work item = (spin, group of Wc walkers); its B tile
+// (Wc * 2n rows x K) stays in shared memory while the A tiles (128 rows =
+// gpt g's x n rows, all K) stream through a TMA ring.  A persistent grid of
+// one CTA per SM walks the items.  Warp roles:
+//   warp 0      TMA producer (one elected lane)
+//   warp 1      TMEM allocator and MMA issuer (one elected lane)
+//   warps 2..9  two epilogue warpgroups; each reads its walkers' columns of the
+//               TMEM accumulator, transposes the n x n blocks through shared
+//               memory and writes (tr T, sum T_ij T_ji) per (w, g, s).
+// The accumulator is double-buffered in TMEM so the epilogue of one A tile
+// overlaps the MMAs of the next.  Every mbarrier wait is bounded; on a
+// timeout the kernel raises an error flag, stops issuing work and frees its
+// TMEM.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstring>
+
+#include "internal.cuh"
+
+namespace afq {
+
+namespace {
+
+constexpr int TC_EPI_WG = 2;                       // epilogue warpgroups
+constexpr int TC_THREADS = 64 + 128 * TC_EPI_WG;   // 10 warps
+constexpr int TC_TMEM_COLS = 512;
+constexpr long long TC_WAIT_CYCLES = 4000000000LL;  // ~2 s at 2 GHz
+
+struct TcArgs {
+  int n, gpt, T, KC, NB, Wc, WG, Nw, cap, G, S, n_items;
+  uint32_t sB_bytes, sA_stage_bytes, staging_floats;
+  double* epart;
+  int* err;
+};
+
+__device__ __forceinline__ uint32_t sa(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sa(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sa(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
+}
+// Wait for the phase with the given parity to complete; false after the cycle limit.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+  const uint32_t a = sa(b);
+  const long long t0 = clock64();
+  while (true) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if (clock64() - t0 > TC_WAIT_CYCLES) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          sa(dst)),
+      "l"((uint64_t)map), "r"(x), "r"(y), "r"(sa(bar))
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// groups 1024 bytes apart (tcgen05 descriptor version 1).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // version
+  d |= (uint64_t)2 << 61;            // SWIZZLE_128B
+  return d;
+}
+// Instruction descriptor of kind::f16: BF16 x BF16 -> F32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sa(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void named_bar(int id, int n) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory"); }
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    exchange_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
+                       const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
+                       const TcArgs p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned base for the swizzled tiles
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* sB = base;                                   // [hi,lo][KC][NB][64] bf16
+  unsigned char* sA = sB + p.sB_bytes;                        // [S][hi,lo][128][64] bf16
+  float* stg = reinterpret_cast<float*>(sA + (size_t)p.S * p.sA_stage_bytes);  // [WG][128][2n+1]
+  float* pbuf = stg + (size_t)TC_EPI_WG * p.staging_floats;  // [WG][128][4]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(pbuf + TC_EPI_WG * 128 * 4);
+  uint64_t* full = bars;                 // [S]
+  uint64_t* empty = bars + p.S;          // [S]
+  uint64_t* bfull = bars + 2 * p.S;      // [1]
+  uint64_t* bempty = bfull + 1;          // [1]
+  uint64_t* tfull = bempty + 1;          // [2]
+  uint64_t* tempty = tfull + 2;          // [2]
+  uint64_t* drain = tempty + 2;          // [1] completion of every MMA this CTA issued
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* epi_ok = abort_flag + 1;  // [TC_EPI_WG] wait result broadcast inside a warpgroup
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n = p.n, two_n = 2 * n;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.S; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(bfull, 1);
+    mbar_init(bempty, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull + b, 1);
+      mbar_init(tempty + b, 128 * TC_EPI_WG);  // every epilogue thread arrives
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa((const void*)tmem_slot)),
+                 "r"(TC_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t tiles_per_item = (uint32_t)p.T;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t ph = 0, bph = 0;
+      uint32_t last_ph[8];  // parity of the last load issued into each stage (S <= 8)
+      bool issued[8] = {false, false, false, false, false, false, false, false};
+      bool b_issued = false;
+      const uint32_t a_bytes = 2u * 128u * 128u;  // hi + lo, 128 rows x 64 bf16
+      const uint32_t b_bytes = 2u * (uint32_t)p.KC * (uint32_t)p.NB * 128u;
+      for (int item = blockIdx.x; item < p.n_items && !*abort_flag; item += gridDim.x) {
+        const int spin = item / p.WG, wg = item % p.WG;
+        if (!mbar_wait(bempty, bph ^ 1)) { atomicOr(p.err, 1); *abort_flag = 1; break; }
+        bph ^= 1;
+        mbar_expect_tx(bfull, b_bytes);
+        b_issued = true;
+        const int brow = (spin * p.cap + wg * p.Wc) * two_n;
+        for (int kc = 0; kc < p.KC; ++kc) {
+          tma_load_2d(sB + (size_t)(0 * p.KC + kc) * p.NB * 128, &tmB_hi, kc * 64, brow, bfull);
+          tma_load_2d(sB + (size_t)(1 * p.KC + kc) * p.NB * 128, &tmB_lo, kc * 64, brow, bfull);
+        }
+        for (uint32_t t = 0; t < tiles_per_item && !*abort_flag; ++t) {
+          const int arow = (spin * p.T + (int)t) * 128;
+          for (int kc = 0; kc < p.KC; ++kc) {
+            if (!mbar_wait(empty + stage, ph ^ 1)) { atomicOr(p.err, 2); *abort_flag = 1; break; }
+            mbar_expect_tx(full + stage, a_bytes);
+            unsigned char* dst = sA + (size_t)stage * p.sA_stage_bytes;
+            tma_load_2d(dst, &tmA_hi, kc * 64, arow, full + stage);
+            tma_load_2d(dst + 128 * 128, &tmA_lo, kc * 64, arow, full + stage);
+            issued[stage] = true;
+            last_ph[stage] = ph;
+            if (++stage == p.S) { stage = 0; ph ^= 1; }
+          }
+        }
+      }
+      // let every copy this thread issued land before the CTA can exit (bounded)
+      for (int s2 = 0; s2 < p.S; ++s2)
+        if (issued[s2]) mbar_wait(full + s2, last_ph[s2]);
+      if (b_issued) mbar_wait(bfull, bph ^ 1);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int stage = 0, buf = 0;
+      uint32_t ph = 0, bph = 0, tph[2] = {0, 0};
+      const uint32_t idesc = idesc_bf16(128, p.NB);
+      for (int item = blockIdx.x; item < p.n_items && !*abort_flag; item += gridDim.x) {
+        if (!mbar_wait(bfull, bph)) { atomicOr(p.err, 4); *abort_flag = 1; break; }
+        bph ^= 1;
+        tc_fence_after();
+        for (uint32_t t = 0; t < tiles_per_item && !*abort_flag; ++t) {
+          if (!mbar_wait(tempty + buf, tph[buf] ^ 1)) { atomicOr(p.err, 8); *abort_flag = 1; break; }
+          tc_fence_after();
+          const uint32_t d = tmem + (uint32_t)(buf * p.NB);
+          for (int kc = 0; kc < p.KC; ++kc) {
+            if (!mbar_wait(full + stage, ph)) { atomicOr(p.err, 16); *abort_flag = 1; break; }
+            tc_fence_after();
+            const uint32_t a_hi = sa(sA + (size_t)stage * p.sA_stage_bytes);
+            const uint32_t a_lo = a_hi + 128 * 128;
+            const uint32_t b_hi = sa(sB + (size_t)(0 * p.KC + kc) * p.NB * 128);
+            const uint32_t b_lo = sa(sB + (size_t)(1 * p.KC + kc) * p.NB * 128);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {  // 4 x K=16 inside the 128-byte swizzle row
+              const uint32_t off = k * 32;
+              umma(d, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, (kc > 0 || k > 0) ? 1u : 0u);
+              umma(d, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
+              umma(d, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
+            }
+            umma_commit(empty + stage);  // the A stage is free once these MMAs complete
+            if (++stage == p.S) { stage = 0; ph ^= 1; }
+          }
+          umma_commit(tfull + buf);  // accumulator ready for the epilogue
+          tph[buf] ^= 1;
+          buf ^= 1;
+        }
+        umma_commit(bempty);  // B may be overwritten once every MMA of the item is done
+      }
+      // every MMA issued by this thread has completed before TMEM is released (bounded)
+      umma_commit(drain);
+      if (!mbar_wait(drain, 0)) atomicOr(p.err, 64);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int ewg = (warp - 2) >> 2;                 // epilogue warpgroup 0 / 1
+    const int quad = warp & 3;                       // TMEM lane quadrant this warp may read
+    const int r = quad * 32 + lane;                  // accumulator row = (g_local, i)
+    const int gl = r / n, i = r % n;
+    const bool row_ok = gl < p.gpt;
+    const int SP = two_n + 1;
+    float* st = stg + (size_t)ewg * p.staging_floats;
+    float* pb = pbuf + ewg * 128 * 4;
+    const int bar_id = 1 + ewg;
+    int buf = 0;
+    uint32_t tph[2] = {0, 0};
+    bool go = true;
+    for (int item = blockIdx.x; item < p.n_items && go; item += gridDim.x) {
+      const int spin = item / p.WG, wg = item % p.WG;
+      for (uint32_t t = 0; t < tiles_per_item; ++t) {
+        // one thread waits for the accumulator; the warpgroup follows its verdict
+        if (r == 0) {
+          const bool ok = mbar_wait(tfull + buf, tph[buf]);
+          if (!ok) { atomicOr(p.err, 32); *abort_flag = 1; }
+          epi_ok[ewg] = ok ? 1 : 0;
+        }
+        named_bar(bar_id, 128);
+        const int ok = epi_ok[ewg];
+        named_bar(bar_id, 128);  // every thread has read the verdict before it can be rewritten
+        if (!ok) { go = false; break; }
+        tc_fence_after();
+        const int g = (int)t * p.gpt + gl;
+        const bool valid = row_ok && g < p.G;
+        for (int wl = ewg; wl < p.Wc; wl += TC_EPI_WG) {
+          const int w = wg * p.Wc + wl;
+          if (w >= p.Nw) break;
+          // this walker's 2n accumulator columns: Re T[i][0..n), Im T[i][0..n)
+          const uint32_t col0 = (uint32_t)(buf * p.NB + wl * two_n);
+          for (int c0 = 0; c0 < two_n; c0 += 8) {
+            uint32_t v[8];
+            tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + col0 + (uint32_t)c0, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              if (c0 + e < two_n) st[r * SP + c0 + e] = __uint_as_float(v[e]);
+          }
+          named_bar(bar_id, 128);
+          float tr = 0.f, ti = 0.f, er = 0.f, ei = 0.f;
+          if (valid) {
+            tr = st[r * SP + i];
+            ti = st[r * SP + n + i];
+            const int rb = gl * n;  // first row of this g block
+            for (int j = 0; j < n; ++j) {
+              const float ar = st[r * SP + j], ai = st[r * SP + n + j];              // T_ij
+              const float br = st[(rb + j) * SP + i], bi = st[(rb + j) * SP + n + i];  // T_ji
+              er = fmaf(ar, br, er);
+              er = fmaf(-ai, bi, er);
+              ei = fmaf(ar, bi, ei);
+              ei = fmaf(ai, br, ei);
+            }
+          }
+          pb[r * 4 + 0] = tr;
+          pb[r * 4 + 1] = ti;
+          pb[r * 4 + 2] = er;
+          pb[r * 4 + 3] = ei;
+          named_bar(bar_id, 128);
+          if (r < p.gpt) {  // one thread per g block sums its n rows in fixed order
+            const int gg = (int)t * p.gpt + r;
+            if (gg < p.G) {
+              float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+              for (int ii = 0; ii < n; ++ii) {
+                const float* q = pb + (r * n + ii) * 4;
+                s0 += q[0]; s1 += q[1]; s2 += q[2]; s3 += q[3];
+              }
+              double* o = p.epart + (((size_t)w * p.G + gg) * 2 + spin) * 4;
+              o[0] = s0; o[1] = s1; o[2] = s2; o[3] = s3;
+            }
+          }
+          named_bar(bar_id, 128);
+        }
+        tc_fence_before();
+        mbar_arrive(tempty + buf);
+        tph[buf] ^= 1;
+        buf ^= 1;
+      }
+    }
+  }
+  // ------------------------------------------------------------ teardown
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_TMEM_COLS) : "memory");
+  }
+}
+
+// Split a real FP64/FP32 value into bfloat16 hi + lo.
+__device__ __forceinline__ void split_bf16(double x, __nv_bfloat16& hi, __nv_bfloat16& lo) {
+  hi = __double2bfloat16(x);
+  lo = __double2bfloat16(x - (double)__bfloat162float(hi));
+}
+
+// A operand: [2 spins][T][128 rows][Kp] from Lh[G][nc][N] (rows gg*n + i).
+__global__ void build_lh_tiles_kernel(const double* __restrict__ Lh, __nv_bfloat16* __restrict__ hi,
+                                      __nv_bfloat16* __restrict__ lo, int N, int n, int nc, int G, int gpt, int T,
+                                      int Kp) {
+  const size_t total = (size_t)2 * T * 128 * Kp;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int q = e % Kp;
+    const int r = (e / Kp) % 128;
+    const int t = (e / ((size_t)Kp * 128)) % T;
+    const int spin = (int)(e / ((size_t)Kp * 128 * T));
+    const int gg = r / n, i = r % n, g = t * gpt + gg;
+    double x = 0.0;
+    if (gg < gpt && g < G && q < N) x = Lh[((size_t)g * nc + spin * n + i) * N + q];
+    split_bf16(x, hi[e], lo[e]);
+  }
+}
+
+// B operand: [2 spins][Nw][re,im][n][Kp] from Theta[Nw][nc][N] (complex64).
+__global__ void build_theta_planes_kernel(const float2* __restrict__ theta, __nv_bfloat16* __restrict__ hi,
+                                          __nv_bfloat16* __restrict__ lo, int N, int n, int Nw, int cap, int Kp) {
+  const size_t per_w = (size_t)2 * n * Kp;  // one walker, one spin: [re,im][n][Kp]
+  const size_t total = (size_t)2 * Nw * per_w;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int q = e % Kp;
+    const int j = (e / Kp) % n;
+    const int c = (e / ((size_t)Kp * n)) % 2;
+    const size_t w = (e / per_w) % Nw;
+    const int spin = (int)(e / (per_w * Nw));
+    float x = 0.f;
+    if (q < N) {
+      const float2 v = theta[(w * 2 * n + spin * n + j) * N + q];
+      x = c ? v.y : v.x;
+    }
+    const __nv_bfloat16 h = __float2bfloat16(x);
+    const size_t o = ((size_t)spin * cap + w) * per_w + e % per_w;
+    hi[o] = h;
+    lo[o] = __float2bfloat16(x - __bfloat162float(h));
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// 2D bf16 tensor [rows][Kp], box {64, box_rows}, 128-byte swizzle.
+bool make_map(CUtensorMap* m, const void* ptr, size_t rows, int Kp, int box_rows) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)Kp * 2};
+  cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+  cuuint32_t es[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+inline int grid_for(size_t n) {
+  size_t b = (n + 255) / 256;
+  return (int)(b > 152 * 64 ? 152 * 64 : (b == 0 ? 1 : b));
+}
+
+size_t tc_smem_bytes(int KC, int NB, int S, int n) {
+  const size_t stg = (size_t)TC_EPI_WG * 128 * (2 * n + 1) * 4;
+  return 1024 + (size_t)2 * KC * NB * 128 + (size_t)S * 2 * 128 * 128 + stg + (size_t)TC_EPI_WG * 128 * 4 * 4 +
+         (size_t)(2 * S + 7) * 8 + 16 + 4 * TC_EPI_WG;
+}
+
+}  // namespace
+
+// Plan the tensor-core exchange for a context; false when the shape is outside
+// what the kernel handles (then the SIMT kernel runs).
+bool tc_exchange_plan(afqmc_ctx* c) {
+  TcPlan& P = c->tc;
+  P = TcPlan();
+  if (c->prec != AFQMC_MIXED || c->na != c->nb || c->na < 1) return false;
+  const int n = c->na;
+  const int Kp = ((c->N + 63) / 64) * 64;
+  const int KC = Kp / 64;
+  if (KC > 2 || n > 64) return false;
+  const int gpt = 128 / n;
+  int best_wc = 0, best_nb = 0, best_s = 0;
+  for (int S = 3; S >= 2 && !best_wc; --S)
+    for (int wc = 256 / (2 * n); wc >= 1; --wc) {
+      const int nb = ((wc * 2 * n + 15) / 16) * 16;
+      if (nb > 240) continue;  // two accumulators plus the 8-column read granularity stay inside 512 columns
+      if (tc_smem_bytes(KC, nb, S, n) <= 232448 - 1024) {
+        best_wc = wc;
+        best_nb = nb;
+        best_s = S;
+        break;
+      }
+    }
+  if (!best_wc) return false;
+  P.ok = true;
+  P.n = n;
+  P.gpt = gpt;
+  P.T = (c->G + gpt - 1) / gpt;
+  P.Kp = Kp;
+  P.KC = KC;
+  P.Wc = best_wc;
+  P.NB = best_nb;
+  P.S = best_s;
+  return true;
+}
+
+// Build the split A tiles (once per context) and their tensor maps.
+cudaError_t tc_exchange_setup(afqmc_ctx* c, cudaStream_t s) {
+  TcPlan& P = c->tc;
+  const size_t elems = (size_t)2 * P.T * 128 * P.Kp;
+  cudaError_t e = cudaMalloc(&P.a_hi, elems * 2);
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&P.a_lo, elems * 2);
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&P.err, sizeof(int));
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(P.err, 0, sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  build_lh_tiles_kernel<<<grid_for(elems), 256, 0, s>>>(c->d_Lh, static_cast<__nv_bfloat16*>(P.a_hi),
+                                                        static_cast<__nv_bfloat16*>(P.a_lo), c->N, P.n, c->nc, c->G,
+                                                        P.gpt, P.T, P.Kp);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (!make_map(reinterpret_cast<CUtensorMap*>(P.map_a_hi), P.a_hi, (size_t)2 * P.T * 128, P.Kp, 128) ||
+      !make_map(reinterpret_cast<CUtensorMap*>(P.map_a_lo), P.a_lo, (size_t)2 * P.T * 128, P.Kp, 128))
+    return cudaErrorInvalidValue;
+  return cudaSuccess;
+}
+
+// Bytes of one split Theta plane (hi or lo) for `cap` walkers.
+size_t tc_exchange_plane_bytes(const TcPlan& P, int cap) { return (size_t)2 * cap * 2 * P.n * P.Kp * 2; }
+
+// Point the plan at caller-provided Theta planes for `cap` walkers and encode
+// their tensor maps (no allocation).
+cudaError_t tc_exchange_bind(TcPlan& P, void* b_hi, void* b_lo, int cap) {
+  P.b_hi = b_hi;
+  P.b_lo = b_lo;
+  P.b_cap = 0;
+  if (!make_map(reinterpret_cast<CUtensorMap*>(P.map_b_hi), b_hi, (size_t)2 * cap * 2 * P.n, P.Kp, P.NB) ||
+      !make_map(reinterpret_cast<CUtensorMap*>(P.map_b_lo), b_lo, (size_t)2 * cap * 2 * P.n, P.Kp, P.NB))
+    return cudaErrorInvalidValue;
+  P.b_cap = cap;
+  return cudaSuccess;
+}
+
+// (Re)allocate the split Theta planes for the workspace's walker capacity.
+cudaError_t tc_exchange_ws(afqmc_ctx* c) {
+  TcPlan& P = c->tc;
+  if (P.b_hi) cudaFree(P.b_hi);
+  if (P.b_lo) cudaFree(P.b_lo);
+  P.b_hi = P.b_lo = nullptr;
+  P.b_cap = 0;
+  const int cap = c->ws.n_walkers;
+  void *hi = nullptr, *lo = nullptr;
+  cudaError_t e = cudaMalloc(&hi, tc_exchange_plane_bytes(P, cap));
+  if (e != cudaSuccess) return e;
+  P.b_hi = hi;
+  e = cudaMalloc(&lo, tc_exchange_plane_bytes(P, cap));
+  if (e != cudaSuccess) return e;
+  P.b_lo = lo;
+  return tc_exchange_bind(P, hi, lo, cap);
+}
+
+void tc_exchange_free(afqmc_ctx* c) {
+  TcPlan& P = c->tc;
+  void* ptrs[] = {P.a_hi, P.a_lo, P.b_hi, P.b_lo, P.err};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  P = TcPlan();
+}
+
+// Theta planes + the tensor-core contraction for Nw walkers; writes epart.
+cudaError_t tc_exchange_launch(afqmc_ctx* c, int Nw, const void* theta, double* epart, cudaStream_t s) {
+  TcPlan& P = c->tc;
+  // the B tensor map spans the allocated capacity; planes beyond Nw are ignored
+  if (Nw > P.b_cap) return cudaErrorInvalidValue;
+  const size_t elems = (size_t)2 * Nw * 2 * P.n * P.Kp;
+  build_theta_planes_kernel<<<grid_for(elems), 256, 0, s>>>(static_cast<const float2*>(theta),
+                                                            static_cast<__nv_bfloat16*>(P.b_hi),
+                                                            static_cast<__nv_bfloat16*>(P.b_lo), c->N, P.n, Nw,
+                                                            P.b_cap, P.Kp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  TcArgs a;
+  a.n = P.n;
+  a.gpt = P.gpt;
+  a.T = P.T;
+  a.KC = P.KC;
+  a.NB = P.NB;
+  a.Wc = P.Wc;
+  a.WG = (Nw + P.Wc - 1) / P.Wc;
+  a.Nw = Nw;
+  a.cap = P.b_cap;
+  a.G = c->G;
+  a.S = P.S;
+  a.n_items = 2 * a.WG;
+  a.sB_bytes = (uint32_t)(2 * P.KC * P.NB * 128);
+  a.sA_stage_bytes = 2 * 128 * 128;
+  a.staging_floats = (uint32_t)(128 * (2 * P.n + 1));
+  a.epart = epart;
+  a.err = static_cast<int*>(P.err);
+  const size_t shm = tc_smem_bytes(P.KC, P.NB, P.S, P.n);
+  e = cudaFuncSetAttribute(exchange_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
+  if (e != cudaSuccess) return e;
+  int sms = 152;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = a.n_items < sms ? a.n_items : sms;
+  CUtensorMap mah, mal, mbh, mbl;
+  memcpy(&mah, P.map_a_hi, sizeof(CUtensorMap));
+  memcpy(&mal, P.map_a_lo, sizeof(CUtensorMap));
+  memcpy(&mbh, P.map_b_hi, sizeof(CUtensorMap));
+  memcpy(&mbl, P.map_b_lo, sizeof(CUtensorMap));
+  exchange_tc_kernel<<<grid, TC_THREADS, shm, s>>>(mah, mal, mbh, mbl, a);
+  return cudaGetLastError();
+}
+
+}  // namespace afq

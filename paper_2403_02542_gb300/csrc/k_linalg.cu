@@ -8,6 +8,8 @@
 // All arithmetic is FP64 whatever the storage type R of the walkers.
 #include <math_constants.h>
 
+#include <type_traits>
+
 #include "internal.cuh"
 
 namespace afq {
@@ -40,7 +42,8 @@ __device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
 // grid (Nw, 2 spins), block 128.  Shared: LU [n][n] and O^{-1} [n][n], FP64 complex.
 template <typename R>
 __global__ void __launch_bounds__(128) overlap_kernel(const typename C2<R>::t* __restrict__ psi,
-                                                      const double* __restrict__ trial, int N, int na,
+                                                      const double* __restrict__ trial,
+                                                      const float* __restrict__ trial_f, int N, int na,
                                                       int nb, typename C2<R>::t* __restrict__ theta,
                                                       double* __restrict__ logdet,
                                                       uint32_t* __restrict__ status) {
@@ -62,13 +65,29 @@ __global__ void __launch_bounds__(128) overlap_kernel(const typename C2<R>::t* _
   // O[i][j] = sum_p trial[off+i][p] psi[off+j][p]
   for (int e = tid; e < n * n; e += nt) {
     const int i = e / n, j = e % n;
-    const double* T = trial + (size_t)(off + i) * N;
     const typename C2<R>::t* X = P + (size_t)j * N;
     double sr = 0.0, si = 0.0;
-    for (int p = 0; p < N; ++p) {
-      cd x = ld(X + p);
-      sr = fma(T[p], x.re, sr);
-      si = fma(T[p], x.im, si);
+    if constexpr (std::is_same<R, float>::value) {
+      // complex64 walkers: FP32 products summed in slabs of 16, slabs summed in FP64
+      const float* T = trial_f + (size_t)(off + i) * N;
+      for (int p0 = 0; p0 < N; p0 += 16) {
+        float fr = 0.f, fi = 0.f;
+        const int p1 = min(N, p0 + 16);
+        for (int p = p0; p < p1; ++p) {
+          const float2 x = X[p];
+          fr = fmaf(T[p], x.x, fr);
+          fi = fmaf(T[p], x.y, fi);
+        }
+        sr += fr;
+        si += fi;
+      }
+    } else {
+      const double* T = trial + (size_t)(off + i) * N;
+      for (int p = 0; p < N; ++p) {
+        cd x = ld(X + p);
+        sr = fma(T[p], x.re, sr);
+        si = fma(T[p], x.im, si);
+      }
     }
     LU[e] = mk(sr, si);
   }
@@ -141,11 +160,30 @@ __global__ void __launch_bounds__(128) overlap_kernel(const typename C2<R>::t* _
 
   // Theta[j][p] = sum_i psi[i][p] Oinv[i][j]
   typename C2<R>::t* Th = theta + ((size_t)w * nc + off) * N;
-  for (int e = tid; e < n * N; e += nt) {
-    const int j = e / N, p = e % N;
-    cd s = mk(0.0, 0.0);
-    for (int i = 0; i < n; ++i) s = s + ld(P + (size_t)i * N + p) * Inv[i * n + j];
-    st(Th + (size_t)j * N + p, s);
+  if constexpr (std::is_same<R, float>::value) {
+    // complex64 walkers: O^{-1} rounded to complex64, product in FP32
+    float2* InvF = reinterpret_cast<float2*>(LU);
+    for (int e = tid; e < n * n; e += nt) InvF[e] = make_float2((float)Inv[e].re, (float)Inv[e].im);
+    __syncthreads();
+    for (int e = tid; e < n * N; e += nt) {
+      const int j = e / N, p = e % N;
+      float sr = 0.f, si = 0.f;
+      for (int i = 0; i < n; ++i) {
+        const float2 x = P[(size_t)i * N + p], y = InvF[i * n + j];
+        sr = fmaf(x.x, y.x, sr);
+        sr = fmaf(-x.y, y.y, sr);
+        si = fmaf(x.x, y.y, si);
+        si = fmaf(x.y, y.x, si);
+      }
+      Th[(size_t)j * N + p] = make_float2(sr, si);
+    }
+  } else {
+    for (int e = tid; e < n * N; e += nt) {
+      const int j = e / N, p = e % N;
+      cd s = mk(0.0, 0.0);
+      for (int i = 0; i < n; ++i) s = s + ld(P + (size_t)i * N + p) * Inv[i * n + j];
+      st(Th + (size_t)j * N + p, s);
+    }
   }
 }
 
@@ -161,28 +199,64 @@ __global__ void __launch_bounds__(256) mgs_kernel(typename C2<R>::t* __restrict_
   const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
   cd* q = reinterpret_cast<cd*>(smem_q);
   typename C2<R>::t* P = psi + ((size_t)w * nc + off) * N;
-  for (int j = 0; j < n; ++j) {
-    for (int p = threadIdx.x; p < N; p += 256) q[p] = ld(P + (size_t)j * N + p);
-    __syncthreads();
-    for (int i = 0; i < j; ++i) {
-      const typename C2<R>::t* Qi = P + (size_t)i * N;
-      double dr = 0.0, di = 0.0;
-      for (int p = threadIdx.x; p < N; p += 256) {
-        cd a = ld(Qi + p), b = q[p];
-        dr += a.re * b.re + a.im * b.im;  // conj(a) b
-        di += a.re * b.im - a.im * b.re;
+  if constexpr (std::is_same<R, float>::value) {
+    // complex64 walkers: products and updates in FP32, every reduction in FP64
+    float2* qf = reinterpret_cast<float2*>(smem_q);
+    for (int j = 0; j < n; ++j) {
+      for (int p = threadIdx.x; p < N; p += 256) qf[p] = P[(size_t)j * N + p];
+      __syncthreads();
+      for (int i = 0; i < j; ++i) {
+        const float2* Qi = P + (size_t)i * N;
+        float fr = 0.f, fi = 0.f;
+        for (int p = threadIdx.x; p < N; p += 256) {
+          const float2 a = Qi[p], b = qf[p];
+          fr += a.x * b.x + a.y * b.y;  // conj(a) b
+          fi += a.x * b.y - a.y * b.x;
+        }
+        double dr = fr, di = fi;
+        block_sum2<256>(dr, di, red);
+        const float rr = (float)dr, ri = (float)di;
+        for (int p = threadIdx.x; p < N; p += 256) {
+          const float2 a = Qi[p];
+          float2 b = qf[p];
+          b.x -= rr * a.x - ri * a.y;
+          b.y -= rr * a.y + ri * a.x;
+          qf[p] = b;
+        }
+        __syncthreads();
       }
-      block_sum2<256>(dr, di, red);
-      const cd r = mk(dr, di);
-      for (int p = threadIdx.x; p < N; p += 256) q[p] = q[p] - r * ld(Qi + p);
+      float f2 = 0.f;
+      for (int p = threadIdx.x; p < N; p += 256) f2 += qf[p].x * qf[p].x + qf[p].y * qf[p].y;
+      double s2 = f2, dummy = 0.0;
+      block_sum2<256>(s2, dummy, red);
+      const float inv = (float)(1.0 / sqrt(s2));
+      for (int p = threadIdx.x; p < N; p += 256) P[(size_t)j * N + p] = make_float2(inv * qf[p].x, inv * qf[p].y);
       __syncthreads();
     }
-    double s2 = 0.0, dummy = 0.0;
-    for (int p = threadIdx.x; p < N; p += 256) s2 += abs2(q[p]);
-    block_sum2<256>(s2, dummy, red);
-    const double inv = 1.0 / sqrt(s2);
-    for (int p = threadIdx.x; p < N; p += 256) st(P + (size_t)j * N + p, inv * q[p]);
-    __syncthreads();
+  } else {
+    for (int j = 0; j < n; ++j) {
+      for (int p = threadIdx.x; p < N; p += 256) q[p] = ld(P + (size_t)j * N + p);
+      __syncthreads();
+      for (int i = 0; i < j; ++i) {
+        const typename C2<R>::t* Qi = P + (size_t)i * N;
+        double dr = 0.0, di = 0.0;
+        for (int p = threadIdx.x; p < N; p += 256) {
+          cd a = ld(Qi + p), b = q[p];
+          dr += a.re * b.re + a.im * b.im;  // conj(a) b
+          di += a.re * b.im - a.im * b.re;
+        }
+        block_sum2<256>(dr, di, red);
+        const cd r = mk(dr, di);
+        for (int p = threadIdx.x; p < N; p += 256) q[p] = q[p] - r * ld(Qi + p);
+        __syncthreads();
+      }
+      double s2 = 0.0, dummy = 0.0;
+      for (int p = threadIdx.x; p < N; p += 256) s2 += abs2(q[p]);
+      block_sum2<256>(s2, dummy, red);
+      const double inv = 1.0 / sqrt(s2);
+      for (int p = threadIdx.x; p < N; p += 256) st(P + (size_t)j * N + p, inv * q[p]);
+      __syncthreads();
+    }
   }
 }
 
@@ -218,24 +292,53 @@ __global__ void krylov_orth_kernel(typename C2<R>::t* __restrict__ wv, typename 
   if (col >= ncols) return;
   typename C2<R>::t* W = wv + (size_t)col * N;
   double* H = hess + (size_t)col * kmax * kmax * 2;  // H[i][j] at (i*kmax + j)*2
+  constexpr bool F32 = std::is_same<R, float>::value;
   for (int i = 0; i <= it; ++i) {
     const typename C2<R>::t* V = basis + i * bstride + (size_t)col * N;
     double dr = 0.0, di = 0.0;
-    for (int p = lane; p < N; p += 32) {
-      cd a = ld(V + p), b = ld(W + p);
-      dr += a.re * b.re + a.im * b.im;
-      di += a.re * b.im - a.im * b.re;
+    if constexpr (F32) {  // complex64: FP32 lane partials, FP64 reduction
+      float fr = 0.f, fi = 0.f;
+      for (int p = lane; p < N; p += 32) {
+        const float2 a = V[p], b = W[p];
+        fr += a.x * b.x + a.y * b.y;
+        fi += a.x * b.y - a.y * b.x;
+      }
+      dr = fr;
+      di = fi;
+    } else {
+      for (int p = lane; p < N; p += 32) {
+        cd a = ld(V + p), b = ld(W + p);
+        dr += a.re * b.re + a.im * b.im;
+        di += a.re * b.im - a.im * b.re;
+      }
     }
     dr = warp_sum(dr);
     di = warp_sum(di);
     const cd h = mk(dr, di);
-    for (int p = lane; p < N; p += 32) st(W + p, ld(W + p) - h * ld(V + p));
+    if constexpr (F32) {
+      const float hr = (float)dr, hi = (float)di;
+      for (int p = lane; p < N; p += 32) {
+        const float2 a = V[p];
+        float2 b = W[p];
+        b.x -= hr * a.x - hi * a.y;
+        b.y -= hr * a.y + hi * a.x;
+        W[p] = b;
+      }
+    } else {
+      for (int p = lane; p < N; p += 32) st(W + p, ld(W + p) - h * ld(V + p));
+    }
     __syncwarp();
     if (lane == 0) { H[(i * kmax + it) * 2] = dr; H[(i * kmax + it) * 2 + 1] = di; }
   }
   if (it + 1 < k) {
     double s = 0.0;
-    for (int p = lane; p < N; p += 32) s += abs2(ld(W + p));
+    if constexpr (F32) {
+      float f = 0.f;
+      for (int p = lane; p < N; p += 32) { const float2 b = W[p]; f += b.x * b.x + b.y * b.y; }
+      s = f;
+    } else {
+      for (int p = lane; p < N; p += 32) s += abs2(ld(W + p));
+    }
     s = warp_sum(s);
     double hn = sqrt(s);
     const double normA = scal[(size_t)(col / nc) * SC_COUNT + SC_NORMA];
@@ -250,7 +353,7 @@ __global__ void krylov_orth_kernel(typename C2<R>::t* __restrict__ wv, typename 
 
 // y = beta e^{H_k} e_1 by sub-stepping: (e^{H/m})^m e_1, each factor a Taylor
 // series on the vector summed until its terms fall below 1e-18 of the sum
-// (m chosen so that ||H/m||_1 <= 1/2).  Then psi_out = B_k y.
+// (m chosen so that ||H/m||_1 <= 1).  Then psi_out = B_k y.
 // One thread per column for the small exponential; then a warp per column.
 template <typename R>
 __global__ void krylov_expm_kernel(double* __restrict__ hess, const double* __restrict__ beta, int ncols,
@@ -265,7 +368,7 @@ __global__ void krylov_expm_kernel(double* __restrict__ hess, const double* __re
     for (int i = 0; i < k; ++i) cs += sqrt(abs2(mk(H[(i * kmax + j) * 2], H[(i * kmax + j) * 2 + 1])));
     n1 = fmax(n1, cs);
   }
-  int m = (int)ceil(n1 / 0.5);
+  int m = (int)ceil(n1);
   if (m < 1) m = 1;
   if (m > 4096) m = 4096;
   const double sc = 1.0 / m;
@@ -274,9 +377,10 @@ __global__ void krylov_expm_kernel(double* __restrict__ hess, const double* __re
     for (int i = 0; i < k; ++i) { t[i] = v[i]; }
     for (int d = 1; d <= 40; ++d) {
       double tn = 0.0, an = 0.0;
-      for (int i = 0; i < k; ++i) {
+      for (int i = 0; i < k; ++i) {  // upper Hessenberg: H[i][j] = 0 for j < i - 1
         cd a = mk(0.0, 0.0);
-        for (int j = 0; j < k; ++j) a = a + mk(H[(i * kmax + j) * 2], H[(i * kmax + j) * 2 + 1]) * t[j];
+        for (int j = (i > 0 ? i - 1 : 0); j < k; ++j)
+          a = a + mk(H[(i * kmax + j) * 2], H[(i * kmax + j) * 2 + 1]) * t[j];
         u[i] = (sc / d) * a;
       }
       for (int i = 0; i < k; ++i) {
@@ -303,13 +407,26 @@ __global__ void krylov_combine_kernel(const double* __restrict__ hess, const typ
   const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (col >= ncols) return;
   const double* H = hess + (size_t)col * kmax * kmax * 2;
-  for (int p = lane; p < N; p += 32) {
-    cd s = mk(0.0, 0.0);
-    for (int i = 0; i < k; ++i) {
-      const cd y = mk(H[(i * kmax) * 2], H[(i * kmax) * 2 + 1]);
-      s = s + y * ld(basis + i * bstride + (size_t)col * N + p);
+  if constexpr (std::is_same<R, float>::value) {  // complex64: y rounded, FP32 sum
+    for (int p = lane; p < N; p += 32) {
+      float sr = 0.f, si = 0.f;
+      for (int i = 0; i < k; ++i) {
+        const float yr = (float)H[(i * kmax) * 2], yi = (float)H[(i * kmax) * 2 + 1];
+        const float2 v = basis[i * bstride + (size_t)col * N + p];
+        sr += yr * v.x - yi * v.y;
+        si += yr * v.y + yi * v.x;
+      }
+      out[(size_t)col * N + p] = make_float2(sr, si);
     }
-    st(out + (size_t)col * N + p, s);
+  } else {
+    for (int p = lane; p < N; p += 32) {
+      cd s = mk(0.0, 0.0);
+      for (int i = 0; i < k; ++i) {
+        const cd y = mk(H[(i * kmax) * 2], H[(i * kmax) * 2 + 1]);
+        s = s + y * ld(basis + i * bstride + (size_t)col * N + p);
+      }
+      st(out + (size_t)col * N + p, s);
+    }
   }
 }
 
@@ -338,7 +455,8 @@ cudaError_t launch_overlap(const afqmc_ctx* c, int Nw, const void* psi, void* th
   const size_t shm = (size_t)2 * nmax * nmax * sizeof(cd);
   cudaError_t e = cudaFuncSetAttribute(overlap_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
   if (e != cudaSuccess) return e;
-  overlap_kernel<R><<<dim3(Nw, 2), 128, shm, s>>>(static_cast<const typename C2<R>::t*>(psi), c->d_trial, c->N,
+  overlap_kernel<R><<<dim3(Nw, 2), 128, shm, s>>>(static_cast<const typename C2<R>::t*>(psi), c->d_trial,
+                                                  c->f_trial, c->N,
                                                   c->na, c->nb, static_cast<typename C2<R>::t*>(theta), logdet,
                                                   status);
   return cudaGetLastError();

@@ -53,7 +53,9 @@ extern "C" afqmc_status afqmc_local_energy_static(afqmc_ctx* c, const afqmc_walk
   const size_t b_scal = up256(Nw * SC_COUNT * sizeof(double));
   const size_t b_epart = up256(Nw * (size_t)c->G * 8 * sizeof(double));
   const size_t b_ecap = up256(Nw * sizeof(double));
-  const size_t need = b_theta + b_logdet + b_scal + b_epart + b_ecap;
+  // split Theta planes of the tensor-core exchange (mixed contexts that use it)
+  const size_t b_plane = c->tc.ok ? up256(tc_exchange_plane_bytes(c->tc, w->n_walkers)) : 0;
+  const size_t need = b_theta + b_logdet + b_scal + b_epart + b_ecap + 2 * b_plane;
   if (need > kScratchBytes) return AFQMC_EINVAL;  // beyond AFQMC_STATIC_SCRATCH_BYTES
 
   // device address of the array on the current device, resolved once per device
@@ -83,6 +85,12 @@ extern "C" afqmc_status afqmc_local_energy_static(afqmc_ctx* c, const afqmc_walk
   tmp.ws.epart = reinterpret_cast<double*>(p);
   p += b_epart;
   tmp.ws.ecap = reinterpret_cast<double*>(p);
+  p += b_ecap;
+  if (c->tc.ok) {  // same tensor-core kernels, operand planes in the array (maps are host-side)
+    void* hi = p;
+    void* lo = p + b_plane;
+    if (tc_exchange_bind(tmp.tc, hi, lo, w->n_walkers) != cudaSuccess) return AFQMC_ECUDA;
+  }
 
   cudaStream_t s = c->stream;
   int nl = 0;
