@@ -164,6 +164,58 @@ afqmc_status afqmc_step(afqmc_ctx* ctx, const afqmc_walkers* w, const double* fi
 afqmc_status afqmc_local_energy(afqmc_ctx* ctx, const afqmc_walkers* w, double e0, double tau,
                                 double* e_loc, double* e_mix);
 
+/* Population control by comb resampling.  The paper does not describe one;
+ * the comb is the reading taken: with cumulative weights
+ * C_w = W_0 + ... + W_w summed in walker order in FP64, tooth j at
+ * (u + j) C_{Nw-1} / Nw selects the first walker w with C_w > tooth (walkers
+ * with W = 0 are never selected).  The population is replaced in place: slot j
+ * receives a copy of its selected walker (psi, logovl, status) and every
+ * weight becomes C_{Nw-1} / Nw, so the total weight is kept.
+ *   u          caller-supplied uniform number in [0, 1)
+ *   index_out  device [Nw] int32 or NULL: the source walker of every slot
+ * If the total weight is not positive and finite the walkers are left
+ * unchanged and index_out (when given) is filled with -1; the call itself
+ * runs asynchronously on the context's stream.
+ * Errors: EINVAL (u outside [0, 1), bad buffers), EDOM (u not finite), ECUDA. */
+afqmc_status afqmc_population_control(afqmc_ctx* ctx, const afqmc_walkers* w, double u, int32_t* index_out);
+
+/* Autotuner of the step's GEMM tile shapes.  Every walker-batched GEMM call
+ * site of afqmc_step (force bias, field assembly, half step B*Psi, products
+ * A*V of the exponential) has four output-tile variants (64x64, 128x32,
+ * 32x128, 64x32); this call times each variant at each site with CUDA events
+ * (one warm-up, three timed launches, minimum kept) for n_walkers walkers on
+ * the context's workspace and keeps the fastest.  Tile shape does not change
+ * the summation order, so results are bit-identical for every choice.
+ * Synchronises the context's stream.
+ *   table_out  host [4] int32 or NULL: the chosen variant per call site.
+ * afqmc_tune_set / afqmc_tune_get write / read that table (e.g. from a cache
+ * file).  Errors: EINVAL (bad table), ENOMEM, ECUDA. */
+afqmc_status afqmc_autotune(afqmc_ctx* ctx, int n_walkers, int32_t* table_out);
+afqmc_status afqmc_tune_set(afqmc_ctx* ctx, const int32_t* table);
+afqmc_status afqmc_tune_get(const afqmc_ctx* ctx, int32_t* table);
+
+/* A batch of independent systems (uneven N, electrons, G and walker counts)
+ * stepped together.  Each afqmc_batch_step runs afqmc_step for every system
+ * as one CUDA graph in which every system is a parallel branch between one
+ * fork and one join, so small systems share the GPU.  The graph is captured
+ * on the first call with a given set of arguments (walker buffers, field
+ * pointers, step parameters, output pointers; up to four such sets are
+ * cached) and replayed afterwards: to advance in time, write the next fields
+ * into the same field buffers.  A capture first sets the time step and sizes
+ * each context's workspace outside the capture.
+ *   ctxs     [n_sys] contexts (they must outlive the batch)
+ *   ws       [n_sys] walker sets; fields [n_sys] device pointers as for
+ *            afqmc_step; p [n_sys] step parameters; e_loc, e_mix: NULL or
+ *            [n_sys] device pointers (entries may be NULL)
+ *   stream   cudaStream_t on which the graph is launched
+ * Errors: as afqmc_step, plus ECUDA for a failed capture. */
+typedef struct afqmc_batch afqmc_batch;
+afqmc_status afqmc_batch_create(afqmc_batch** out, afqmc_ctx* const* ctxs, int n_sys);
+afqmc_status afqmc_batch_step(afqmc_batch* batch, const afqmc_walkers* ws, const double* const* fields,
+                              const afqmc_step_params* p, double* const* e_loc, double* const* e_mix,
+                              void* stream);
+void afqmc_batch_destroy(afqmc_batch* batch);
+
 /* Size of the device scratch array used by afqmc_local_energy_static. */
 #define AFQMC_STATIC_SCRATCH_BYTES ((unsigned long long)32 << 20) /* 32 MiB */
 

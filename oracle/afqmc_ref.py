@@ -53,7 +53,7 @@ __all__ = [
     "taylor_action", "krylov_action", "exact_action", "expm_action",
     "split2_propagate", "local_energy", "energy_window", "mixed_energy",
     "mgs_qr", "reorthonormalise", "weight_update", "step", "init_walkers",
-    "free_projection_step", "comb", "StepInfo",
+    "free_projection_step", "comb", "population_control", "StepInfo",
 ]
 
 
@@ -439,17 +439,34 @@ def free_projection_step(ham: Hamiltonian, psi, logovl, weight, x, tau, e0,
 # Population control (the paper is silent; reading R8)
 # --------------------------------------------------------------------------
 def comb(W, u):
-    """Comb resampling: Nw teeth at (u + j) sum(W)/Nw; tooth j picks the walker whose
-    cumulative-weight interval [C_{w-1}, C_w) contains it.  Returns indices [Nw]."""
-    W = torch.as_tensor(W, dtype=RT)
-    n = W.shape[0]
-    total = float(W.sum())
-    cum = torch.cumsum(W, 0)
+    """Comb resampling (reading R8): with cumulative weights C_w = W_0 + ... + W_w
+    summed in walker order, tooth j sits at (u + j) C_{Nw-1} / Nw and picks the
+    first walker whose C_w exceeds it (zero-weight walkers are never picked).
+    Returns the indices [Nw]."""
+    W = [float(x) for x in torch.as_tensor(W, dtype=RT)]
+    n = len(W)
+    cum = []
+    acc = 0.0
+    for x in W:
+        acc = acc + x
+        cum.append(acc)
+    total = cum[-1]
     idx = []
     w = 0
     for j in range(n):
         tooth = (u + j) * total / n
-        while w < n - 1 and not (tooth < float(cum[w])):
+        while w < n - 1 and not (tooth < cum[w]):
             w += 1
         idx.append(w)
     return torch.tensor(idx, dtype=torch.int64)
+
+
+def population_control(psi, logovl, W, u):
+    """Replace the population by Nw comb-selected copies, each of weight
+    C_{Nw-1} / Nw (the total weight is kept)."""
+    idx = comb(W, u)
+    total = 0.0
+    for x in torch.as_tensor(W, dtype=RT).tolist():
+        total = total + x
+    n = W.shape[0]
+    return psi[idx].clone(), logovl[idx].clone(), torch.full((n,), total / n, dtype=RT), idx

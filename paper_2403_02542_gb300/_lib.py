@@ -50,7 +50,14 @@ SIGNATURES = {
     "afqmc_last_cuda_error": (ctypes.c_char_p, []),
     "afqmc_host_eigh": (_I, [_I, _P, _P, _P]),
     "afqmc_profile": (_I, [_P, _I]),
+    "afqmc_population_control": (_I, [_P, ctypes.POINTER(Walkers), _D, _P]),
     "afqmc_local_energy_static": (_I, [_P, ctypes.POINTER(Walkers), _D, _D, _P, _P]),
+    "afqmc_autotune": (_I, [_P, _I, _P]),
+    "afqmc_tune_set": (_I, [_P, _P]),
+    "afqmc_tune_get": (_I, [_P, _P]),
+    "afqmc_batch_create": (_I, [ctypes.POINTER(_P), _P, _I]),
+    "afqmc_batch_step": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "afqmc_batch_destroy": (None, [_P]),
     "afqmc_profile_read": (_I, [_P, _P, _P]),
 }
 

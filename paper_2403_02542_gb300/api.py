@@ -3,6 +3,8 @@ everything else through the C ABI (include/afqmc.h)."""
 from __future__ import annotations
 
 import ctypes
+import json
+import os
 from dataclasses import dataclass
 
 import numpy as np
@@ -131,8 +133,49 @@ class Context:
                                            e_loc.data_ptr(), e_mix.data_ptr()), "afqmc_local_energy")
         return e_loc, e_mix
 
+    def population_control(self, w: WalkerSet, u: float, index_out: torch.Tensor | None = None):
+        """Comb resampling with uniform u in [0, 1) (afqmc_population_control)."""
+        self._bind_stream()
+        cw = w.c_struct()
+        L.check(L.lib().afqmc_population_control(self._h, ctypes.byref(cw), float(u), _ptr(index_out)),
+                "afqmc_population_control")
+
     def sync(self):
         L.check(L.lib().afqmc_sync(self._h), "afqmc_sync")
+
+    # ------------------------------------------------------------------ tuning
+    def tune_key(self, n_walkers: int) -> str:
+        return f"N{self.N}_na{self.na}_nb{self.nb}_G{self.G}_{self.precision}_w{n_walkers}"
+
+    def autotune(self, n_walkers: int, cache: str | None = None) -> list:
+        """Pick the GEMM tile variant of every call site (afqmc_autotune); with
+        `cache` (a JSON file) a table measured earlier for the same shape is reused."""
+        table = (ctypes.c_int32 * 4)()
+        key = self.tune_key(n_walkers)
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                known = json.load(f)
+            if key in known:
+                for i, v in enumerate(known[key]):
+                    table[i] = int(v)
+                L.check(L.lib().afqmc_tune_set(self._h, table), "afqmc_tune_set")
+                return list(table)
+        self._bind_stream()
+        L.check(L.lib().afqmc_autotune(self._h, int(n_walkers), table), "afqmc_autotune")
+        if cache:
+            known = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    known = json.load(f)
+            known[key] = list(table)
+            with open(cache, "w") as f:
+                json.dump(known, f, indent=1, sort_keys=True)
+        return list(table)
+
+    def tune_table(self) -> list:
+        table = (ctypes.c_int32 * 4)()
+        L.check(L.lib().afqmc_tune_get(self._h, table), "afqmc_tune_get")
+        return list(table)
 
     def profile(self, enable: bool):
         """Start (clearing) or stop per-kernel-class event timing (afqmc_profile)."""
@@ -159,3 +202,43 @@ def host_eigh(a: np.ndarray):
     L.check(L.lib().afqmc_host_eigh(n, a.ctypes.data, ev.ctypes.data, V.ctypes.data),
             "afqmc_host_eigh")
     return ev, V
+
+
+class Batch:
+    """Several contexts stepped as one CUDA graph (afqmc_batch_*)."""
+
+    def __init__(self, contexts: list):
+        self.contexts = list(contexts)
+        arr = (ctypes.c_void_p * len(self.contexts))(*[c._h.value for c in self.contexts])
+        h = ctypes.c_void_p()
+        L.check(L.lib().afqmc_batch_create(ctypes.byref(h), arr, len(self.contexts)), "afqmc_batch_create")
+        self._h = h
+
+    def step(self, walker_sets, fields, tau, e0, expm="krylov", order=10, reortho=False, measure=False,
+             e_loc=None, e_mix=None, stream: torch.cuda.Stream | None = None):
+        n = len(self.contexts)
+        taus = tau if isinstance(tau, (list, tuple)) else [tau] * n
+        e0s = e0 if isinstance(e0, (list, tuple)) else [e0] * n
+        ws = (L.Walkers * n)(*[w.c_struct() for w in walker_sets])
+        fp = (ctypes.c_void_p * n)(*[f.data_ptr() for f in fields])
+        ex = {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV}[expm]
+        ps = (L.StepParams * n)(*[L.StepParams(float(taus[i]), float(e0s[i]), L.AFQMC_SPLIT2, ex, int(order),
+                                               int(bool(reortho)), int(bool(measure))) for i in range(n)])
+        el = (ctypes.c_void_p * n)(*[None if e_loc is None or e_loc[i] is None else e_loc[i].data_ptr()
+                                     for i in range(n)])
+        em = (ctypes.c_void_p * n)(*[None if e_mix is None or e_mix[i] is None else e_mix[i].data_ptr()
+                                     for i in range(n)])
+        dev = self.contexts[0].device
+        s = stream if stream is not None else torch.cuda.current_stream(dev)
+        L.check(L.lib().afqmc_batch_step(self._h, ws, fp, ps, el, em, s.cuda_stream), "afqmc_batch_step")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            L.lib().afqmc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

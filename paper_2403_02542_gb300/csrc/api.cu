@@ -20,6 +20,9 @@
 #include "internal.cuh"
 
 namespace afq {
+template <typename R> cudaError_t prepare_overlap(const afqmc_ctx* c);
+template <typename R> cudaError_t prepare_energy(const afqmc_ctx* c);
+cudaError_t tc_exchange_prepare(const afqmc_ctx* c);
 cudaError_t launch_lsq(const double* L, double* LL, int N, int G, cudaStream_t s);
 cudaError_t launch_lbar(const double* Lh, const double* thT, double* Lbar, int G, size_t per, cudaStream_t s);
 cudaError_t launch_to_float(const double* a, float* b, size_t n, cudaStream_t s);
@@ -29,11 +32,19 @@ using namespace afq;
 
 static thread_local char g_cuda_err[256] = "no error";
 
-static afqmc_status cuda_fail(cudaError_t e) {
-  snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
+static afqmc_status cuda_fail(cudaError_t e, const char* where = nullptr) {
+  if (where)
+    snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s: %s", where, cudaGetErrorName(e), cudaGetErrorString(e));
+  else
+    snprintf(g_cuda_err, sizeof g_cuda_err, "%s: %s", cudaGetErrorName(e), cudaGetErrorString(e));
   if (e == cudaErrorMemoryAllocation) return AFQMC_ENOMEM;
   return AFQMC_ECUDA;
 }
+#define CKW(expr, where)                                 \
+  do {                                                   \
+    cudaError_t _e = (expr);                             \
+    if (_e != cudaSuccess) return cuda_fail(_e, where);  \
+  } while (0)
 
 #define CK(expr)                                     \
   do {                                               \
@@ -125,7 +136,7 @@ static bool small_inverse(int n, std::vector<double> m, std::vector<double>& inv
 
 // ---------------------------------------------------------------- workspace
 static void ws_free(Workspace& ws) {
-  void* ptrs[] = {ws.theta, ws.t, ws.c, ws.A, ws.psi_b, ws.term0, ws.term1, ws.acc, ws.psi_new, ws.basis,
+  void* ptrs[] = {ws.theta, ws.t, ws.c, ws.A, ws.psi_b, ws.term0, ws.term1, ws.acc, ws.psi_new, ws.splitk, ws.basis,
                   ws.hess, ws.beta, ws.scal, ws.logdet, ws.epart, ws.eloc, ws.ecap, ws.emix, ws.alive};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -150,6 +161,7 @@ static afqmc_status ws_ensure(afqmc_ctx* c, int Nw, int kmax) {
   CK(cudaMalloc(&ws.term1, nw * per * cs));
   CK(cudaMalloc(&ws.acc, nw * per * cs));
   CK(cudaMalloc(&ws.psi_new, nw * per * cs));
+  CK(cudaMalloc(&ws.splitk, (size_t)8 * nw * c->G * cs));
   if (km > 0) {
     CK(cudaMalloc(&ws.basis, (size_t)km * nw * per * cs));
     CK(cudaMalloc(&ws.hess, (size_t)nw * c->nc * km * km * 2 * sizeof(double)));
@@ -167,6 +179,28 @@ static afqmc_status ws_ensure(afqmc_ctx* c, int Nw, int kmax) {
   if (c->tc.ok) CK(tc_exchange_ws(c));
   return AFQMC_OK;
 }
+
+namespace afq {
+int max_dyn_smem() {
+  static int cached = 0;
+  if (!cached) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess && v > 0)
+      cached = v;
+    else
+      cached = 48 * 1024;
+  }
+  return cached;
+}
+
+cudaError_t prepare_kernels(afqmc_ctx* c) {
+  cudaError_t e = c->prec == AFQMC_FP64 ? prepare_overlap<double>(c) : prepare_overlap<float>(c);
+  if (e == cudaSuccess) e = c->prec == AFQMC_FP64 ? prepare_energy<double>(c) : prepare_energy<float>(c);
+  if (e == cudaSuccess) e = tc_exchange_prepare(c);
+  return e;
+}
+}  // namespace afq
 
 // ---------------------------------------------------------------- profiler
 namespace afq {
@@ -309,7 +343,7 @@ static afqmc_status ctx_setup(afqmc_ctx* c, const double* h1, const double* L, c
 #define PK(cls, expr)                    \
   do {                                   \
     prof_mark(c, (cls), true, s);        \
-    CK(expr);                            \
+    CKW(expr, #expr);                    \
     prof_mark(c, (cls), false, s);       \
   } while (0)
 
@@ -332,56 +366,80 @@ static afqmc_status run_energy(afqmc_ctx* c, const afqmc_walkers* w, double e0, 
   return AFQMC_OK;
 }
 
+// Arguments of the GEMM at one call site of the step (in -> out), tile variant
+// from the context's tuning table.
+template <typename R>
+static GemmArgs site_args(const afqmc_ctx* c, int site, int Nw, double sqrt_tau, const void* in, void* out) {
+  const int N = c->N, nc = c->nc, G = c->G;
+  const long long per = (long long)nc * N, NN = (long long)N * N;
+  GemmArgs g{};
+  g.variant = c->tune[site];
+  g.alpha_re = 1.0;
+  g.B = in;
+  g.C = out;
+  g.batch = 1;
+  switch (site) {
+    case SITE_FORCEBIAS: {  // <L_g>_mixed[w][g] = sum_{jq} Lh[g][j][q] Theta[w][j][q]
+      g.M = G; g.Nn = Nw; g.K = (int)per;
+      g.A = pick<R>(c->d_Lh, c->f_Lh); g.sa_m = per; g.sa_k = 1;
+      g.sb_n = per; g.sb_k = 1;
+      g.sc_m = 1; g.sc_n = G;
+      // few output tiles and a long K: split K over up to 8 slices (deterministic sum)
+      const long long tiles = (long long)((G + 63) / 64) * ((Nw + 63) / 64);
+      int sk = 1;
+      while (sk < 8 && tiles * sk < 4 * 152 && per / (2 * sk) >= 256) sk *= 2;
+      g.splitk = sk;
+      g.part = c->ws.splitk;
+      break;
+    }
+    case SITE_FIELD:  // A_w[pq] = i sqrt(tau) sum_g c_wg L_g[pq]
+      g.M = (int)NN; g.Nn = Nw; g.K = G;
+      g.A = pick<R>(c->d_L, c->f_L); g.sa_m = 1; g.sa_k = NN;
+      g.sb_n = G; g.sb_k = 1;
+      g.sc_m = 1; g.sc_n = NN;
+      g.alpha_re = 0.0; g.alpha_im = sqrt_tau;
+      break;
+    case SITE_HALFSTEP:  // out[w][j][p] = sum_q B[p][q] in[w][j][q]
+      g.M = N; g.Nn = Nw * nc; g.K = N;
+      g.A = pick<R>(c->d_B, c->f_B); g.sa_m = N; g.sa_k = 1;
+      g.sb_n = N; g.sb_k = 1;
+      g.sc_m = 1; g.sc_n = N;
+      break;
+    default:  // SITE_EXPM: out[w][j][p] = sum_q A_w[p][q] in[w][j][q], batched over walkers
+      g.M = N; g.Nn = nc; g.K = N; g.batch = Nw;
+      g.A = c->ws.A; g.sa_m = N; g.sa_k = 1; g.sa_b = NN;
+      g.sb_n = N; g.sb_k = 1; g.sb_b = per;
+      g.sc_m = 1; g.sc_n = N; g.sc_b = per;
+      break;
+  }
+  return g;
+}
+
 template <typename R>
 static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double* x, const afqmc_step_params* p,
                              double* e_loc, double* e_mix) {
   cudaStream_t s = c->stream;
-  const int Nw = w->n_walkers, N = c->N, nc = c->nc, G = c->G;
-  const long long per = (long long)nc * N, NN = (long long)N * N;
+  const int Nw = w->n_walkers, nc = c->nc, N = c->N;
+  const long long per = (long long)nc * N;
   const double st = std::sqrt(p->tau);
-  const R* Lh = pick<R>(c->d_Lh, c->f_Lh);
-  const R* L = pick<R>(c->d_L, c->f_L);
-  const R* B = pick<R>(c->d_B, c->f_B);
   Workspace& ws = c->ws;
   const size_t cs = sizeof(typename C2<R>::t);
 
   // Theta at the current walkers
   PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, w->psi, ws.theta, ws.logdet, w->status, s));
-  // <L_g>_mixed = sum_{jq} Lh[g][j][q] Theta[w][j][q]
-  GemmArgs g{};
-  g.M = G; g.Nn = Nw; g.K = (int)per; g.batch = 1;
-  g.A = Lh; g.sa_m = per; g.sa_k = 1; g.sa_b = 0;
-  g.B = ws.theta; g.sb_n = per; g.sb_k = 1; g.sb_b = 0;
-  g.C = ws.t; g.sc_m = 1; g.sc_n = G; g.sc_b = 0;
-  g.alpha_re = 1.0; g.alpha_im = 0.0;
-  PK(AFQMC_K_FORCEBIAS, gemm<R>(g, false, EPI_STORE, s));
+  // force bias (Eq. force_shift) and c_g = x_g - f_g
+  PK(AFQMC_K_FORCEBIAS, gemm<R>(site_args<R>(c, SITE_FORCEBIAS, Nw, st, ws.theta, ws.t), false, EPI_STORE, s));
   PK(AFQMC_K_OTHER, launch_bias_finalize<R>(c, Nw, x, st, s));
-  // A_w = i sqrt(tau) sum_g c_wg L_g
-  g = GemmArgs{};
-  g.M = (int)NN; g.Nn = Nw; g.K = G; g.batch = 1;
-  g.A = L; g.sa_m = 1; g.sa_k = NN;
-  g.B = ws.c; g.sb_n = G; g.sb_k = 1;
-  g.C = ws.A; g.sc_m = 1; g.sc_n = NN;
-  g.alpha_re = 0.0; g.alpha_im = st;
-  PK(AFQMC_K_FIELD, gemm<R>(g, false, EPI_STORE, s));
+  // A_w = i sqrt(tau) sum_g c_wg L_g (Eq. heffTOT)
+  PK(AFQMC_K_FIELD, gemm<R>(site_args<R>(c, SITE_FIELD, Nw, st, ws.c, ws.A), false, EPI_STORE, s));
   // psi_b = B psi
-  g = GemmArgs{};
-  g.M = N; g.Nn = Nw * nc; g.K = N; g.batch = 1;
-  g.A = B; g.sa_m = N; g.sa_k = 1;
-  g.B = w->psi; g.sb_n = N; g.sb_k = 1;
-  g.C = ws.psi_b; g.sc_m = 1; g.sc_n = N;
-  g.alpha_re = 1.0;
-  PK(AFQMC_K_HALFSTEP, gemm<R>(g, false, EPI_STORE, s));
+  PK(AFQMC_K_HALFSTEP, gemm<R>(site_args<R>(c, SITE_HALFSTEP, Nw, st, w->psi, ws.psi_b), false, EPI_STORE, s));
   c->launches += 5;
 
   // per-walker products with A_w
-  GemmArgs ga{};
-  ga.M = N; ga.Nn = nc; ga.K = N; ga.batch = Nw;
-  ga.A = ws.A; ga.sa_m = N; ga.sa_k = 1; ga.sa_b = NN;
-  ga.sb_n = N; ga.sb_k = 1; ga.sb_b = per;
-  ga.sc_m = 1; ga.sc_n = N; ga.sc_b = per;
+  GemmArgs ga = site_args<R>(c, SITE_EXPM, Nw, st, nullptr, nullptr);
   if (p->expm == AFQMC_EXPM_TAYLOR) {
-    CK(cudaMemcpyAsync(ws.acc, ws.psi_b, (size_t)Nw * per * cs, cudaMemcpyDeviceToDevice, s));
+    CKW(cudaMemcpyAsync(ws.acc, ws.psi_b, (size_t)Nw * per * cs, cudaMemcpyDeviceToDevice, s), "acc copy");
     const void* cur = ws.psi_b;
     for (int n = 1; n <= p->order; ++n) {
       void* nxt = (n & 1) ? ws.term0 : ws.term1;
@@ -407,13 +465,7 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
     c->launches += 2 + 2 * k + 2;
   }
   // psi_new = B acc
-  g = GemmArgs{};
-  g.M = N; g.Nn = Nw * nc; g.K = N; g.batch = 1;
-  g.A = B; g.sa_m = N; g.sa_k = 1;
-  g.B = ws.acc; g.sb_n = N; g.sb_k = 1;
-  g.C = ws.psi_new; g.sc_m = 1; g.sc_n = N;
-  g.alpha_re = 1.0;
-  PK(AFQMC_K_HALFSTEP, gemm<R>(g, false, EPI_STORE, s));
+  PK(AFQMC_K_HALFSTEP, gemm<R>(site_args<R>(c, SITE_HALFSTEP, Nw, st, ws.acc, ws.psi_new), false, EPI_STORE, s));
   // new overlap, weights, commit
   PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, ws.psi_new, nullptr, ws.logdet, w->status, s));
   PK(AFQMC_K_OTHER, launch_weights<R>(c, w, p->tau, p->e0, s));
@@ -427,6 +479,86 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
   }
   if (p->measure) return run_energy<R>(c, w, p->e0, p->tau, e_loc, e_mix);
   return AFQMC_OK;
+}
+
+// Time every tile variant of every GEMM call site on the workspace (contents
+// irrelevant for timing) and keep the fastest in the context.
+template <typename R>
+static afqmc_status autotune_impl(afqmc_ctx* c, int Nw, int order) {
+  cudaStream_t s = c->stream;
+  Workspace& ws = c->ws;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  const bool prof = c->prof.on;
+  c->prof.on = false;
+  afqmc_status rc = AFQMC_OK;
+  for (int site = 0; site < N_SITES && rc == AFQMC_OK; ++site) {
+    if (site == SITE_EXPM && order < 1) continue;
+    float best = 1e30f;
+    int best_v = 0;
+    for (int v = 0; v < GEMM_VARIANTS; ++v) {
+      c->tune[site] = v;
+      GemmArgs g;
+      bool ac = false;
+      if (site == SITE_FORCEBIAS) g = site_args<R>(c, site, Nw, 0.2, ws.theta, ws.t);
+      else if (site == SITE_FIELD) g = site_args<R>(c, site, Nw, 0.2, ws.c, ws.A);
+      else if (site == SITE_HALFSTEP) g = site_args<R>(c, site, Nw, 0.2, ws.psi_b, ws.psi_new);
+      else { g = site_args<R>(c, site, Nw, 0.2, ws.psi_b, ws.term0); ac = true; }
+      float tmin = 1e30f;
+      for (int rep = 0; rep < 4 && rc == AFQMC_OK; ++rep) {
+        cudaError_t e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = gemm<R>(g, ac, EPI_STORE, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) { rc = cuda_fail(e); break; }
+        if (rep > 0 && ms < tmin) tmin = ms;  // the first launch is a warm-up
+        c->launches += g.splitk > 1 ? 2 : 1;
+      }
+      if (tmin < best) { best = tmin; best_v = v; }
+    }
+    c->tune[site] = best_v;
+  }
+  c->prof.on = prof;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+// ---------------------------------------------------------------- batches
+namespace {
+constexpr int kBatchGraphs = 4;
+struct BatchGraph {
+  bool used = false;
+  uint64_t stamp = 0;
+  std::vector<unsigned char> key;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<uint64_t> launches;  // kernel launches per system in one replay
+};
+}  // namespace
+
+struct afqmc_batch {
+  std::vector<afqmc_ctx*> ctxs;
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> join;
+  cudaStream_t origin = nullptr;
+  cudaEvent_t fork = nullptr, done = nullptr;
+  BatchGraph graphs[kBatchGraphs];
+  uint64_t clock = 0;
+};
+
+static void batch_free(afqmc_batch* b) {
+  if (!b) return;
+  for (auto& g : b->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (auto s : b->branch) cudaStreamDestroy(s);
+  for (auto e : b->join) cudaEventDestroy(e);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
+  delete b;
 }
 
 // ---------------------------------------------------------------- ABI
@@ -573,6 +705,25 @@ afqmc_status afqmc_local_energy(afqmc_ctx* c, const afqmc_walkers* w, double e0,
   return run_energy<float>(c, w, e0, tau, e_loc, e_mix);
 }
 
+afqmc_status afqmc_population_control(afqmc_ctx* c, const afqmc_walkers* w, double u, int32_t* index_out) {
+  afqmc_status st = check_walkers(c, w);
+  if (st != AFQMC_OK) return st;
+  if (!std::isfinite(u)) return AFQMC_EDOM;
+  if (!(u >= 0.0 && u < 1.0)) return AFQMC_EINVAL;
+  if (index_out && ((uintptr_t)index_out) % 4) return AFQMC_EINVAL;
+  if (w->n_walkers == 0) return AFQMC_OK;
+  st = ws_ensure(c, w->n_walkers, c->ws.kmax);
+  if (st != AFQMC_OK) return st;
+  prof_mark(c, AFQMC_K_OTHER, true, c->stream);
+  if (c->prec == AFQMC_FP64)
+    CK(launch_comb<double>(c, w, u, index_out, c->stream));
+  else
+    CK(launch_comb<float>(c, w, u, index_out, c->stream));
+  prof_mark(c, AFQMC_K_OTHER, false, c->stream);
+  c->launches += 4;
+  return AFQMC_OK;
+}
+
 afqmc_status afqmc_sync(afqmc_ctx* c) {
   if (!c) return AFQMC_EINVAL;
   CK(cudaStreamSynchronize(c->stream));
@@ -639,6 +790,186 @@ void afqmc_destroy(afqmc_ctx* c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
   ctx_free(c);
+}
+
+afqmc_status afqmc_autotune(afqmc_ctx* c, int n_walkers, int32_t* table_out) {
+  if (!c || n_walkers < 1 || n_walkers > (1 << 24)) return AFQMC_EINVAL;
+  afqmc_status st = ws_ensure(c, n_walkers, c->ws.kmax);
+  if (st != AFQMC_OK) return st;
+  st = c->prec == AFQMC_FP64 ? autotune_impl<double>(c, n_walkers, 1) : autotune_impl<float>(c, n_walkers, 1);
+  if (st != AFQMC_OK) return st;
+  if (table_out)
+    for (int i = 0; i < N_SITES; ++i) table_out[i] = c->tune[i];
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_tune_set(afqmc_ctx* c, const int32_t* table) {
+  if (!c || !table) return AFQMC_EINVAL;
+  for (int i = 0; i < N_SITES; ++i)
+    if (table[i] < 0 || table[i] >= GEMM_VARIANTS) return AFQMC_EINVAL;
+  for (int i = 0; i < N_SITES; ++i) c->tune[i] = table[i];
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_tune_get(const afqmc_ctx* c, int32_t* table) {
+  if (!c || !table) return AFQMC_EINVAL;
+  for (int i = 0; i < N_SITES; ++i) table[i] = c->tune[i];
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_batch_create(afqmc_batch** out, afqmc_ctx* const* ctxs, int n_sys) {
+  if (!out || !ctxs || n_sys < 1 || n_sys > 4096) return AFQMC_EINVAL;
+  *out = nullptr;
+  for (int i = 0; i < n_sys; ++i)
+    if (!ctxs[i]) return AFQMC_EINVAL;
+  afqmc_batch* b = new (std::nothrow) afqmc_batch();
+  if (!b) return AFQMC_ENOMEM;
+  b->ctxs.assign(ctxs, ctxs + n_sys);
+  cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  for (int i = 0; i < n_sys && e == cudaSuccess; ++i) {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) b->branch.push_back(st);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) b->join.push_back(ev);
+  }
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return cuda_fail(e);
+  }
+  *out = b;
+  return AFQMC_OK;
+}
+
+void afqmc_batch_destroy(afqmc_batch* b) {
+  if (!b) return;
+  if (b->origin) cudaStreamSynchronize(b->origin);
+  batch_free(b);
+}
+
+static afqmc_status step_checks(afqmc_ctx* c, const afqmc_walkers* w, const double* fields,
+                                const afqmc_step_params* p) {
+  afqmc_status st = check_walkers(c, w);
+  if (st != AFQMC_OK) return st;
+  if (!p || (!fields && w->n_walkers > 0)) return AFQMC_EINVAL;
+  if (!std::isfinite(p->tau) || !std::isfinite(p->e0)) return AFQMC_EDOM;
+  if (!(p->tau > 0.0)) return AFQMC_EINVAL;
+  if (p->propagator != AFQMC_SPLIT2) return AFQMC_ENOTSUP;
+  if (p->expm == AFQMC_EXPM_TAYLOR) {
+    if (p->order < 0 || p->order > 64) return AFQMC_ENOTSUP;
+  } else if (p->expm == AFQMC_EXPM_KRYLOV) {
+    if (p->order < 1 || p->order > 32) return AFQMC_ENOTSUP;
+  } else {
+    return AFQMC_ENOTSUP;
+  }
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_batch_step(afqmc_batch* b, const afqmc_walkers* ws, const double* const* fields,
+                              const afqmc_step_params* p, double* const* e_loc, double* const* e_mix,
+                              void* stream) {
+  if (!b || !ws || !fields || !p) return AFQMC_EINVAL;
+  const int n = (int)b->ctxs.size();
+  std::vector<afqmc_step_params> q(p, p + n);
+  std::vector<unsigned char> key;
+  auto put = [&key](const void* src, size_t bytes) {
+    const unsigned char* c8 = static_cast<const unsigned char*>(src);
+    key.insert(key.end(), c8, c8 + bytes);
+  };
+  for (int i = 0; i < n; ++i) {
+    afqmc_ctx* c = b->ctxs[i];
+    afqmc_status st = step_checks(c, &ws[i], fields[i], &p[i]);
+    if (st != AFQMC_OK) return st;
+    if (p[i].expm == AFQMC_EXPM_KRYLOV) q[i].order = p[i].order < c->N ? p[i].order : c->N;
+    double* el = e_loc ? e_loc[i] : nullptr;
+    double* em = e_mix ? e_mix[i] : nullptr;
+    put(&ws[i], sizeof(afqmc_walkers));
+    put(&fields[i], sizeof(void*));
+    put(&q[i], sizeof(afqmc_step_params));
+    put(&el, sizeof(void*));
+    put(&em, sizeof(void*));
+  }
+  cudaStream_t user = static_cast<cudaStream_t>(stream);
+  BatchGraph* hit = nullptr;
+  for (auto& g : b->graphs)
+    if (g.used && g.key == key) hit = &g;
+  if (!hit) {
+    // prepare outside the capture: time step, workspace, kernel attributes
+    for (int i = 0; i < n; ++i) {
+      afqmc_ctx* c = b->ctxs[i];
+      if (ws[i].n_walkers == 0) continue;
+      if (p[i].tau != c->tau) {
+        afqmc_status st = afqmc_set_tau(c, p[i].tau);
+        if (st != AFQMC_OK) return st;
+      }
+      const int k = q[i].expm == AFQMC_EXPM_KRYLOV ? q[i].order : 0;
+      afqmc_status st = ws_ensure(c, ws[i].n_walkers, k);
+      if (st != AFQMC_OK) return st;
+      CKW(prepare_kernels(c), "prepare_kernels");
+      CKW(cudaStreamSynchronize(c->stream), "prepare sync");
+    }
+    // capture: one branch per system between a fork and a join
+    std::vector<cudaStream_t> saved(n);
+    std::vector<bool> saved_prof(n);
+    std::vector<uint64_t> launches(n, 0);
+    CKW(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    afqmc_status rc = AFQMC_OK;
+    cudaError_t e = cudaEventRecord(b->fork, b->origin);
+    for (int i = 0; i < n && e == cudaSuccess && rc == AFQMC_OK; ++i) {
+      afqmc_ctx* c = b->ctxs[i];
+      saved[i] = c->stream;
+      saved_prof[i] = c->prof.on;
+      e = cudaStreamWaitEvent(b->branch[i], b->fork, 0);
+      if (e != cudaSuccess) break;
+      c->stream = b->branch[i];
+      c->prof.on = false;
+      c->capturing = true;
+      const uint64_t l0 = c->launches;
+      if (ws[i].n_walkers > 0)
+        rc = c->prec == AFQMC_FP64
+                 ? run_step<double>(c, &ws[i], fields[i], &q[i], e_loc ? e_loc[i] : nullptr, e_mix ? e_mix[i] : nullptr)
+                 : run_step<float>(c, &ws[i], fields[i], &q[i], e_loc ? e_loc[i] : nullptr, e_mix ? e_mix[i] : nullptr);
+      launches[i] = c->launches - l0;
+      c->launches = l0;
+      c->stream = saved[i];
+      c->prof.on = saved_prof[i];
+      c->capturing = false;
+      if (e == cudaSuccess) e = cudaEventRecord(b->join[i], b->branch[i]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(b->origin, b->join[i], 0);
+    }
+    cudaGraph_t graph = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(b->origin, &graph);
+    if (rc != AFQMC_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess || ee != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return cuda_fail(e != cudaSuccess ? e : ee, e != cudaSuccess ? "capture fork/join" : "cudaStreamEndCapture");
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    BatchGraph* slot = &b->graphs[0];
+    for (auto& g : b->graphs) {
+      if (!g.used) { slot = &g; break; }
+      if (g.stamp < slot->stamp) slot = &g;
+    }
+    if (slot->exec) cudaGraphExecDestroy(slot->exec);
+    slot->used = true;
+    slot->key = key;
+    slot->exec = exec;
+    slot->launches = launches;
+    hit = slot;
+  }
+  hit->stamp = ++b->clock;
+  CKW(cudaGraphLaunch(hit->exec, user), "cudaGraphLaunch");
+  for (int i = 0; i < n; ++i) b->ctxs[i]->launches += hit->launches[i];
+  return AFQMC_OK;
 }
 
 afqmc_status afqmc_host_eigh(int n, const double* a, double* evals, double* evecs) {

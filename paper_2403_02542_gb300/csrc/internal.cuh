@@ -58,7 +58,15 @@ struct GemmArgs {
   long long sc_m, sc_n, sc_b;
   void* D;  // EPI_STORE_ADD: D += result (same strides as C)
   double alpha_re, alpha_im;
+  // split-K (batch == 1, EPI_STORE): `splitk` K-ranges write partial tiles to
+  // `part` [splitk][M][Nn] (complex, R), summed in fixed order afterwards
+  int splitk;
+  void* part;
+  int variant;  // output tile: 0 = 64x64, 1 = 128x32, 2 = 32x128, 3 = 64x32
 };
+constexpr int GEMM_VARIANTS = 4;
+// GEMM call sites of the step, each with its own tuned tile variant
+enum GemmSite { SITE_FORCEBIAS = 0, SITE_FIELD = 1, SITE_HALFSTEP = 2, SITE_EXPM = 3, N_SITES = 4 };
 template <typename R>
 cudaError_t gemm(const GemmArgs& a, bool a_complex, int epi, cudaStream_t s);
 
@@ -75,6 +83,7 @@ struct Workspace {
   void* term1 = nullptr;     // [Nw][nc][N]
   void* acc = nullptr;       // [Nw][nc][N]
   void* psi_new = nullptr;   // [Nw][nc][N]
+  void* splitk = nullptr;    // [8][Nw][G] partial force-bias tiles
   void* basis = nullptr;     // [kmax][Nw][nc][N]
   double* hess = nullptr;    // [Nw*nc][kmax][kmax][2]
   double* beta = nullptr;    // [Nw*nc]
@@ -150,10 +159,32 @@ struct afqmc_ctx {
   afq::Workspace ws;
   afq::Prof prof;
   afq::TcPlan tc;
+  int tune[afq::N_SITES] = {0, 0, 0, 0};  // GEMM tile variant per call site
+  bool capturing = false;                  // inside a graph capture (afqmc_batch_step)
   uint64_t launches = 0;
 };
 
 namespace afq {
+
+// True while the context's work is being captured into a graph (kernel
+// attributes were set before the capture and are not touched then).
+inline bool capturing(const afqmc_ctx* c);
+// Set the dynamic shared-memory limits of every kernel a context uses (before
+// any graph capture).  The limit is a per-kernel attribute shared by all
+// contexts, so it is always raised to the device's opt-in maximum (it permits
+// larger launches; it reserves nothing).
+cudaError_t prepare_kernels(afqmc_ctx* c);
+int max_dyn_smem();
+// Raise a kernel's dynamic shared-memory limit to the opt-in maximum minus its
+// static shared memory.
+template <typename F>
+cudaError_t raise_smem_limit(F* func) {
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, reinterpret_cast<const void*>(func));
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(reinterpret_cast<const void*>(func), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              max_dyn_smem() - (int)a.sharedSizeBytes);
+}
 
 // Record the start (begin=true) or end of a launch of class `cls` when the
 // context's profiler is on.
@@ -191,6 +222,10 @@ cudaError_t launch_logovl_from_logdet(const afqmc_ctx* c, const afqmc_walkers* w
                                       const uint8_t* mask, cudaStream_t s);
 cudaError_t launch_copy_alive(const afqmc_ctx* c, const afqmc_walkers* w, cudaStream_t s);
 
+// comb population control (k_population.cu)
+template <typename R>
+cudaError_t launch_comb(afqmc_ctx* c, const afqmc_walkers* w, double u, int* index_out, cudaStream_t s);
+
 // tensor-core exchange (k_exchange_tc.cu)
 bool tc_exchange_plan(afqmc_ctx* c);
 cudaError_t tc_exchange_setup(afqmc_ctx* c, cudaStream_t s);
@@ -200,4 +235,8 @@ cudaError_t tc_exchange_bind(TcPlan& P, void* b_hi, void* b_lo, int cap);
 void tc_exchange_free(afqmc_ctx* c);
 cudaError_t tc_exchange_launch(afqmc_ctx* c, int Nw, const void* theta, double* epart, cudaStream_t s);
 
+}  // namespace afq
+
+namespace afq {
+inline bool capturing(const afqmc_ctx* c) { return c->capturing; }
 }  // namespace afq

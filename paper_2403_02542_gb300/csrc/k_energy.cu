@@ -90,8 +90,12 @@ __global__ void __launch_bounds__(256) normA_kernel(const typename C2<R>::t* __r
                                                     size_t nn) {
   __shared__ double sh[8];
   const int w = blockIdx.x;
-  double v[1] = {0.0};
-  for (size_t e = threadIdx.x; e < nn; e += 256) v[0] += abs2(ld(A + (size_t)w * nn + e));
+  R part = R(0);  // per-thread partial in the storage precision
+  for (size_t e = threadIdx.x; e < nn; e += 256) {
+    const typename C2<R>::t a = A[(size_t)w * nn + e];
+    part += a.x * a.x + a.y * a.y;
+  }
+  double v[1] = {(double)part};
   block_sum<1>(v, sh);
   if (threadIdx.x == 0) scal[(size_t)w * SC_COUNT + SC_NORMA] = sqrt(v[0]);
 }
@@ -425,8 +429,10 @@ cudaError_t launch_energy(afqmc_ctx* c, int Nw, const double* weight, double e0,
   const typename C2<R>::t* th = static_cast<const typename C2<R>::t*>(c->ws.theta);
 #define AFQ_EX(ME)                                                                                       \
   do {                                                                                                   \
-    e = cudaFuncSetAttribute(exchange_kernel<R, ME>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm); \
-    if (e != cudaSuccess) return e;                                                                      \
+    if (!capturing(c)) {                                                                                 \
+      e = raise_smem_limit(exchange_kernel<R, ME>); \
+      if (e != cudaSuccess) return e;                                                                    \
+    }                                                                                                    \
     prof_mark(c, AFQMC_K_EXCHANGE, true, s);                                                             \
     exchange_kernel<R, ME><<<grid, EX_NT, shm, s>>>(th, Lh, c->ws.epart, c->N, c->na, c->nb, c->G);       \
     prof_mark(c, AFQMC_K_EXCHANGE, false, s);                                                            \
@@ -457,6 +463,18 @@ cudaError_t launch_energy(afqmc_ctx* c, int Nw, const double* weight, double e0,
   if (n_launch) *n_launch = 4;
   return cudaGetLastError();
 }
+
+template <typename R>
+cudaError_t prepare_energy(const afqmc_ctx*) {
+  cudaError_t e = raise_smem_limit(exchange_kernel<R, 4>);
+  if (e == cudaSuccess)
+    e = raise_smem_limit(exchange_kernel<R, 16>);
+  if (e == cudaSuccess)
+    e = raise_smem_limit(exchange_kernel<R, 26>);
+  return e;
+}
+template cudaError_t prepare_energy<double>(const afqmc_ctx*);
+template cudaError_t prepare_energy<float>(const afqmc_ctx*);
 
 cudaError_t launch_setup(afqmc_ctx* c, cudaStream_t s) {
   // device temporaries: Lh (FP64), LL, ThetaT

@@ -527,6 +527,12 @@ cudaError_t tc_exchange_ws(afqmc_ctx* c) {
   return tc_exchange_bind(P, hi, lo, cap);
 }
 
+cudaError_t tc_exchange_prepare(const afqmc_ctx* c) {
+  const TcPlan& P = c->tc;
+  if (!P.ok) return cudaSuccess;
+  return raise_smem_limit(exchange_tc_kernel);
+}
+
 void tc_exchange_free(afqmc_ctx* c) {
   TcPlan& P = c->tc;
   void* ptrs[] = {P.a_hi, P.a_lo, P.b_hi, P.b_lo, P.err};
@@ -566,8 +572,10 @@ cudaError_t tc_exchange_launch(afqmc_ctx* c, int Nw, const void* theta, double* 
   a.epart = epart;
   a.err = static_cast<int*>(P.err);
   const size_t shm = tc_smem_bytes(P.KC, P.NB, P.S, P.n);
-  e = cudaFuncSetAttribute(exchange_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-  if (e != cudaSuccess) return e;
+  if (!capturing(c)) {
+    e = raise_smem_limit(exchange_tc_kernel);
+    if (e != cudaSuccess) return e;
+  }
   int sms = 152;
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

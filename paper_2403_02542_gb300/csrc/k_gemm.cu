@@ -5,27 +5,34 @@
 // per-walker products A Psi of the Taylor and Krylov actions (Sec. IV).
 //
 // C[b][m][n] = alpha * sum_k A[b][m][k] B[b][n][k], strides in elements.
-// 64 x 64 output tile, K slab of 8 staged in shared memory, 256 threads with
-// a 4 x 4 register tile each.  The thread-to-output map follows the unit
-// stride of C so that the stores coalesce.
+// Output tile BM x BN (four variants: 64x64, 128x32, 32x128, 64x32, chosen per
+// call site by the autotuner), K slab of 8 staged in shared memory, 256
+// threads with a (BM/16) x (BN/16) register tile each.  The thread-to-output
+// map follows the unit stride of C so that the stores coalesce.
 #include "internal.cuh"
 
 namespace afq {
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 8, NT = 256;
+constexpr int BK = 8, NT = 256;
 
-template <typename R, bool ACPLX>
+template <typename R, bool ACPLX, int BM, int BN>
 __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g) {
+  constexpr int TM = BM / 16, TN = BN / 16;
   typedef typename C2<R>::t cplx;
   __shared__ R sAr[BK][BM];
   __shared__ R sAi[ACPLX ? BK : 1][ACPLX ? BM : 1];
   __shared__ R sBr[BK][BN];
   __shared__ R sBi[BK][BN];
 
-  const int b = blockIdx.z;
+  const bool split = g.splitk > 1;
+  const int b = split ? 0 : blockIdx.z;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  // K range of this block (the whole K unless split)
+  const int kchunk = split ? (((g.K + g.splitk - 1) / g.splitk + BK - 1) / BK) * BK : g.K;
+  const int kbeg = split ? blockIdx.z * kchunk : 0;
+  const int kend = split ? min(g.K, kbeg + kchunk) : g.K;
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const bool swap = (g.sc_m == 1);  // C contiguous along m: threads run along m
@@ -37,19 +44,19 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g) {
   const bool a_kc = (g.sa_k == 1);
   const bool b_kc = (g.sb_k == 1);
 
-  R accr[4][4], acci[4][4];
+  R accr[TM][TN], acci[TM][TN];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < TM; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = R(0);
+    for (int j = 0; j < TN; ++j) accr[i][j] = acci[i][j] = R(0);
 
-  for (int k0 = 0; k0 < g.K; k0 += BK) {
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
     for (int l = tid; l < BM * BK; l += NT) {
       int mm, kk;
       if (a_kc) { kk = l % BK; mm = l / BK; } else { mm = l % BM; kk = l / BM; }
       const int m = m0 + mm, k = k0 + kk;
       R vr = R(0), vi = R(0);
-      if (m < g.M && k < g.K) {
+      if (m < g.M && k < kend) {
         const long long off = (long long)m * g.sa_m + (long long)k * g.sa_k;
         if (ACPLX) {
           cplx v = reinterpret_cast<const cplx*>(A)[off];
@@ -67,28 +74,28 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g) {
       const int n = n0 + nn, k = k0 + kk;
       cplx v;
       v.x = R(0); v.y = R(0);
-      if (n < g.Nn && k < g.K) v = Bp[(long long)n * g.sb_n + (long long)k * g.sb_k];
+      if (n < g.Nn && k < kend) v = Bp[(long long)n * g.sb_n + (long long)k * g.sb_k];
       sBr[kk][nn] = v.x;
       sBi[kk][nn] = v.y;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      R ar[4], ai[4], br[4], bi[4];
+      R ar[TM], ai[TM], br[TN], bi[TN];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
+      for (int i = 0; i < TM; ++i) {
         ar[i] = sAr[kk][tm + 16 * i];
         ai[i] = ACPLX ? sAi[kk][tm + 16 * i] : R(0);
       }
 #pragma unroll
-      for (int j = 0; j < 4; ++j) {
+      for (int j = 0; j < TN; ++j) {
         br[j] = sBr[kk][tn + 16 * j];
         bi[j] = sBi[kk][tn + 16 * j];
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < TM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < TN; ++j) {
           accr[i][j] = fma(ar[i], br[j], accr[i][j]);
           acci[i][j] = fma(ar[i], bi[j], acci[i][j]);
           if (ACPLX) {
@@ -100,15 +107,33 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g) {
     __syncthreads();
   }
 
+  if (split) {  // partial tile, no scaling
+    cplx* Pp = static_cast<cplx*>(g.part) + (size_t)blockIdx.z * g.M * g.Nn;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int m = m0 + tm + 16 * i;
+      if (m >= g.M) continue;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int n = n0 + tn + 16 * j;
+        if (n >= g.Nn) continue;
+        cplx v;
+        v.x = accr[i][j];
+        v.y = acci[i][j];
+        Pp[(size_t)m * g.Nn + n] = v;
+      }
+    }
+    return;
+  }
   cplx* C = static_cast<cplx*>(g.C) + (long long)b * g.sc_b;
   cplx* D = g.D ? static_cast<cplx*>(g.D) + (long long)b * g.sc_b : nullptr;
   const R alr = (R)g.alpha_re, ali = (R)g.alpha_im;
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < TM; ++i) {
     const int m = m0 + tm + 16 * i;
     if (m >= g.M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < TN; ++j) {
       const int n = n0 + tn + 16 * j;
       if (n >= g.Nn) continue;
       cplx v;
@@ -126,19 +151,64 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g) {
   }
 }
 
+// Sum the split-K partials in fixed order, scale by alpha, store to C.
+template <typename R>
+__global__ void splitk_reduce_kernel(GemmArgs g) {
+  typedef typename C2<R>::t cplx;
+  const size_t MN = (size_t)g.M * g.Nn;
+  const cplx* Pp = static_cast<const cplx*>(g.part);
+  cplx* C = static_cast<cplx*>(g.C);
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < MN; e += (size_t)gridDim.x * blockDim.x) {
+    R sr = R(0), si = R(0);
+    for (int z = 0; z < g.splitk; ++z) {
+      const cplx v = Pp[(size_t)z * MN + e];
+      sr += v.x;
+      si += v.y;
+    }
+    const int m = (int)(e / g.Nn), n = (int)(e % g.Nn);
+    cplx o;
+    o.x = (R)g.alpha_re * sr - (R)g.alpha_im * si;
+    o.y = (R)g.alpha_re * si + (R)g.alpha_im * sr;
+    C[(long long)m * g.sc_m + (long long)n * g.sc_n] = o;
+  }
+}
+
 }  // namespace
+
+template <typename R, bool AC, int BM, int BN>
+cudaError_t gemm_launch(const GemmArgs& g, int zdim, cudaStream_t s) {
+  dim3 grid((g.M + BM - 1) / BM, (g.Nn + BN - 1) / BN, zdim);
+  gemm_kernel<R, AC, BM, BN><<<grid, NT, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+template <typename R, bool AC>
+cudaError_t gemm_variant(const GemmArgs& g, int zdim, cudaStream_t s) {
+  switch (g.variant) {
+    case 1: return gemm_launch<R, AC, 128, 32>(g, zdim, s);
+    case 2: return gemm_launch<R, AC, 32, 128>(g, zdim, s);
+    case 3: return gemm_launch<R, AC, 64, 32>(g, zdim, s);
+    default: return gemm_launch<R, AC, 64, 64>(g, zdim, s);
+  }
+}
 
 template <typename R>
 cudaError_t gemm(const GemmArgs& a, bool a_complex, int epi, cudaStream_t s) {
   if (a.M <= 0 || a.Nn <= 0 || a.batch <= 0) return cudaSuccess;
   GemmArgs g = a;
+  if (g.variant < 0 || g.variant >= GEMM_VARIANTS) g.variant = 0;
   if (epi != EPI_STORE_ADD) g.D = nullptr;
-  dim3 grid((a.M + BM - 1) / BM, (a.Nn + BN - 1) / BN, a.batch);
-  if (a_complex)
-    gemm_kernel<R, true><<<grid, NT, 0, s>>>(g);
-  else
-    gemm_kernel<R, false><<<grid, NT, 0, s>>>(g);
-  return cudaGetLastError();
+  if (g.splitk > 1 && g.part && g.batch == 1 && epi == EPI_STORE) {
+    cudaError_t e = a_complex ? gemm_variant<R, true>(g, g.splitk, s) : gemm_variant<R, false>(g, g.splitk, s);
+    if (e != cudaSuccess) return e;
+    const size_t MN = (size_t)a.M * a.Nn;
+    size_t blocks = (MN + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    splitk_reduce_kernel<R><<<(int)blocks, 256, 0, s>>>(g);
+    return cudaGetLastError();
+  }
+  g.splitk = 1;
+  return a_complex ? gemm_variant<R, true>(g, a.batch, s) : gemm_variant<R, false>(g, a.batch, s);
 }
 
 template cudaError_t gemm<double>(const GemmArgs&, bool, int, cudaStream_t);

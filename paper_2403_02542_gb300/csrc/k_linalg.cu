@@ -21,27 +21,16 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-
-// Deterministic block sum of two doubles (fixed tree); every thread gets the result.
-template <int NT>
-__device__ __forceinline__ void block_sum2(double& a, double& b, double* sh) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  a = warp_sum(a);
-  b = warp_sum(b);
-  __syncthreads();
-  if (lane == 0) { sh[2 * wid] = a; sh[2 * wid + 1] = b; }
-  __syncthreads();
-  double ra = 0.0, rb = 0.0;
+__device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
-  for (int i = 0; i < NT / 32; ++i) { ra += sh[2 * i]; rb += sh[2 * i + 1]; }
-  a = ra;
-  b = rb;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
 }
 
 // ---------------------------------------------------------------- overlap
-// grid (Nw, 2 spins), block 128.  Shared: LU [n][n] and O^{-1} [n][n], FP64 complex.
+// grid (Nw, 2 spins), block 256.  Shared: LU [n][n] and O^{-1} [n][n], FP64 complex.
 template <typename R>
-__global__ void __launch_bounds__(128) overlap_kernel(const typename C2<R>::t* __restrict__ psi,
+__global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* __restrict__ psi,
                                                       const double* __restrict__ trial,
                                                       const float* __restrict__ trial_f, int N, int na,
                                                       int nb, typename C2<R>::t* __restrict__ theta,
@@ -63,33 +52,38 @@ __global__ void __launch_bounds__(128) overlap_kernel(const typename C2<R>::t* _
   const typename C2<R>::t* P = psi + ((size_t)w * nc + off) * N;
 
   // O[i][j] = sum_p trial[off+i][p] psi[off+j][p]
-  for (int e = tid; e < n * n; e += nt) {
-    const int i = e / n, j = e % n;
-    const typename C2<R>::t* X = P + (size_t)j * N;
-    double sr = 0.0, si = 0.0;
-    if constexpr (std::is_same<R, float>::value) {
-      // complex64 walkers: FP32 products summed in slabs of 16, slabs summed in FP64
+  if constexpr (std::is_same<R, float>::value) {
+    // complex64 walkers: one warp per entry, lanes stride over p (coalesced),
+    // FP32 lane partials and FP32 tree; the entry is kept in FP64 from here on
+    const int wid = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
+    for (int e = wid; e < n * n; e += nwarp) {
+      const int i = e / n, j = e % n;
+      const float2* X = P + (size_t)j * N;
       const float* T = trial_f + (size_t)(off + i) * N;
-      for (int p0 = 0; p0 < N; p0 += 16) {
-        float fr = 0.f, fi = 0.f;
-        const int p1 = min(N, p0 + 16);
-        for (int p = p0; p < p1; ++p) {
-          const float2 x = X[p];
-          fr = fmaf(T[p], x.x, fr);
-          fi = fmaf(T[p], x.y, fi);
-        }
-        sr += fr;
-        si += fi;
+      float fr = 0.f, fi = 0.f;
+      for (int p = lane; p < N; p += 32) {
+        const float2 x = X[p];
+        fr = fmaf(T[p], x.x, fr);
+        fi = fmaf(T[p], x.y, fi);
       }
-    } else {
+      fr = warp_sum(fr);
+      fi = warp_sum(fi);
+      if (lane == 0) LU[e] = mk((double)fr, (double)fi);
+    }
+  } else {
+    // FP64: one thread per entry, sequential over p (fewest FP64 operations)
+    for (int e = tid; e < n * n; e += nt) {
+      const int i = e / n, j = e % n;
       const double* T = trial + (size_t)(off + i) * N;
+      const typename C2<R>::t* X = P + (size_t)j * N;
+      double sr = 0.0, si = 0.0;
       for (int p = 0; p < N; ++p) {
-        cd x = ld(X + p);
+        const cd x = ld(X + p);
         sr = fma(T[p], x.re, sr);
         si = fma(T[p], x.im, si);
       }
+      LU[e] = mk(sr, si);
     }
-    LU[e] = mk(sr, si);
   }
   if (tid < n) perm[tid] = tid;
   if (tid == 0) { s_swaps = 0; s_sing = 0; }
@@ -97,18 +91,26 @@ __global__ void __launch_bounds__(128) overlap_kernel(const typename C2<R>::t* _
 
   // LU with partial pivoting: (P O) = L U, row i of PO is row perm[i] of O
   for (int k = 0; k < n; ++k) {
-    if (tid == 0) {
+    if (tid < 32) {  // pivot: largest |LU[i][k]|, i >= k; ties keep the smaller row
       int piv = k;
-      double best = abs2(LU[k * n + k]);
-      for (int i = k + 1; i < n; ++i) {
-        double v = abs2(LU[i * n + k]);
+      double best = -1.0;
+      for (int i = k + tid; i < n; i += 32) {
+        const double v = abs2(LU[i * n + k]);
         if (v > best) { best = v; piv = i; }
       }
-      s_piv = piv;
-      if (!(best > 0.0)) s_sing = 1;
-      if (piv != k) {
-        s_swaps ^= 1;
-        int t = perm[k]; perm[k] = perm[piv]; perm[piv] = t;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, piv, o);
+        if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
+      }
+      if (tid == 0) {
+        s_piv = piv;
+        if (!(best > 0.0)) s_sing = 1;
+        if (piv != k) {
+          s_swaps ^= 1;
+          int t = perm[k]; perm[k] = perm[piv]; perm[piv] = t;
+        }
       }
     }
     __syncthreads();
@@ -188,75 +190,67 @@ __global__ void __launch_bounds__(128) overlap_kernel(const typename C2<R>::t* _
 }
 
 // ---------------------------------------------------------------- MGS QR
-// grid (Nw, 2 spins), block 256; one determinant per block, columns in order.
-template <typename R>
-__global__ void __launch_bounds__(256) mgs_kernel(typename C2<R>::t* __restrict__ psi, int N, int na,
-                                                  int nb, const uint8_t* __restrict__ mask) {
-  extern __shared__ double smem_q[];  // current column, FP64 complex [N]
-  __shared__ double red[2 * 8];
-  const int w = blockIdx.x, spin = blockIdx.y;
+// One warp per determinant (walker w, spin): columns in order, the current
+// column in registers (EPL elements per lane), projections reduced with warp
+// shuffles in FP64 (lane partials in the storage precision).
+template <typename R, int EPL>
+__global__ void mgs_kernel(typename C2<R>::t* __restrict__ psi, int N, int na, int nb, int Nw,
+                           const uint8_t* __restrict__ mask) {
+  typedef typename C2<R>::t cplx;
+  const int det = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (det >= 2 * Nw) return;
+  const int w = det >> 1, spin = det & 1;
   if (mask && !mask[w]) return;
   const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
-  cd* q = reinterpret_cast<cd*>(smem_q);
-  typename C2<R>::t* P = psi + ((size_t)w * nc + off) * N;
-  if constexpr (std::is_same<R, float>::value) {
-    // complex64 walkers: products and updates in FP32, every reduction in FP64
-    float2* qf = reinterpret_cast<float2*>(smem_q);
-    for (int j = 0; j < n; ++j) {
-      for (int p = threadIdx.x; p < N; p += 256) qf[p] = P[(size_t)j * N + p];
-      __syncthreads();
-      for (int i = 0; i < j; ++i) {
-        const float2* Qi = P + (size_t)i * N;
-        float fr = 0.f, fi = 0.f;
-        for (int p = threadIdx.x; p < N; p += 256) {
-          const float2 a = Qi[p], b = qf[p];
-          fr += a.x * b.x + a.y * b.y;  // conj(a) b
-          fi += a.x * b.y - a.y * b.x;
-        }
-        double dr = fr, di = fi;
-        block_sum2<256>(dr, di, red);
-        const float rr = (float)dr, ri = (float)di;
-        for (int p = threadIdx.x; p < N; p += 256) {
-          const float2 a = Qi[p];
-          float2 b = qf[p];
-          b.x -= rr * a.x - ri * a.y;
-          b.y -= rr * a.y + ri * a.x;
-          qf[p] = b;
-        }
-        __syncthreads();
+  cplx* P = psi + ((size_t)w * nc + off) * N;
+  for (int j = 0; j < n; ++j) {
+    R qr[EPL], qi[EPL];
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      const int p = lane + 32 * e;
+      qr[e] = R(0);
+      qi[e] = R(0);
+      if (p < N) {
+        const cplx v = P[(size_t)j * N + p];
+        qr[e] = v.x;
+        qi[e] = v.y;
       }
-      float f2 = 0.f;
-      for (int p = threadIdx.x; p < N; p += 256) f2 += qf[p].x * qf[p].x + qf[p].y * qf[p].y;
-      double s2 = f2, dummy = 0.0;
-      block_sum2<256>(s2, dummy, red);
-      const float inv = (float)(1.0 / sqrt(s2));
-      for (int p = threadIdx.x; p < N; p += 256) P[(size_t)j * N + p] = make_float2(inv * qf[p].x, inv * qf[p].y);
-      __syncthreads();
     }
-  } else {
-    for (int j = 0; j < n; ++j) {
-      for (int p = threadIdx.x; p < N; p += 256) q[p] = ld(P + (size_t)j * N + p);
-      __syncthreads();
-      for (int i = 0; i < j; ++i) {
-        const typename C2<R>::t* Qi = P + (size_t)i * N;
-        double dr = 0.0, di = 0.0;
-        for (int p = threadIdx.x; p < N; p += 256) {
-          cd a = ld(Qi + p), b = q[p];
-          dr += a.re * b.re + a.im * b.im;  // conj(a) b
-          di += a.re * b.im - a.im * b.re;
-        }
-        block_sum2<256>(dr, di, red);
-        const cd r = mk(dr, di);
-        for (int p = threadIdx.x; p < N; p += 256) q[p] = q[p] - r * ld(Qi + p);
-        __syncthreads();
+    for (int i = 0; i < j; ++i) {
+      const cplx* Qi = P + (size_t)i * N;
+      cplx a[EPL];
+      R pr = R(0), pi = R(0);
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) {
+        const int p = lane + 32 * e;
+        a[e].x = R(0);
+        a[e].y = R(0);
+        if (p < N) a[e] = Qi[p];
+        pr += a[e].x * qr[e] + a[e].y * qi[e];  // conj(q_i) q_j
+        pi += a[e].x * qi[e] - a[e].y * qr[e];
       }
-      double s2 = 0.0, dummy = 0.0;
-      for (int p = threadIdx.x; p < N; p += 256) s2 += abs2(q[p]);
-      block_sum2<256>(s2, dummy, red);
-      const double inv = 1.0 / sqrt(s2);
-      for (int p = threadIdx.x; p < N; p += 256) st(P + (size_t)j * N + p, inv * q[p]);
-      __syncthreads();
+      const R rr = warp_sum(pr), ri = warp_sum(pi);
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) {
+        qr[e] -= rr * a[e].x - ri * a[e].y;
+        qi[e] -= rr * a[e].y + ri * a[e].x;
+      }
     }
+    R ps = R(0);
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) ps += qr[e] * qr[e] + qi[e] * qi[e];
+    const R inv = (R)(1.0 / sqrt((double)warp_sum(ps)));
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      const int p = lane + 32 * e;
+      if (p < N) {
+        cplx o;
+        o.x = inv * qr[e];
+        o.y = inv * qi[e];
+        P[(size_t)j * N + p] = o;
+      }
+    }
+    __syncwarp();
   }
 }
 
@@ -273,80 +267,84 @@ __global__ void krylov_init_kernel(const typename C2<R>::t* __restrict__ x, type
   double* H = hess + (size_t)col * kmax * kmax * 2;
   for (int e = lane; e < kmax * kmax * 2; e += 32) H[e] = 0.0;
   const typename C2<R>::t* X = x + (size_t)col * N;
-  double s = 0.0;
-  for (int p = lane; p < N; p += 32) s += abs2(ld(X + p));
-  s = warp_sum(s);
-  const double b = sqrt(s);
+  R sp = R(0);
+  for (int p = lane; p < N; p += 32) {
+    const typename C2<R>::t v = X[p];
+    sp += v.x * v.x + v.y * v.y;
+  }
+  const double b = sqrt((double)warp_sum(sp));
   const double inv = b > 0.0 ? 1.0 / b : 0.0;
   for (int p = lane; p < N; p += 32) st(v0 + (size_t)col * N + p, inv * ld(X + p));
   if (lane == 0) beta[col] = b;
 }
 
 // Step `it` of Arnoldi: w = A b_it is in `wv`; MGS against b_0..b_it, then the
-// next basis vector (or zero after an invariant subspace was found).
-template <typename R>
-__global__ void krylov_orth_kernel(typename C2<R>::t* __restrict__ wv, typename C2<R>::t* __restrict__ basis,
+// next basis vector (or zero after an invariant subspace was found).  One warp
+// per column; w lives in registers (EPL elements per lane, N <= 32 * EPL).
+template <typename R, int EPL>
+__global__ void krylov_orth_kernel(const typename C2<R>::t* __restrict__ wv, typename C2<R>::t* __restrict__ basis,
                                    double* __restrict__ hess, const double* __restrict__ scal, int N,
                                    int nc, int ncols, int it, int k, int kmax, size_t bstride) {
+  typedef typename C2<R>::t cplx;
   const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (col >= ncols) return;
-  typename C2<R>::t* W = wv + (size_t)col * N;
+  const cplx* W = wv + (size_t)col * N;
   double* H = hess + (size_t)col * kmax * kmax * 2;  // H[i][j] at (i*kmax + j)*2
-  constexpr bool F32 = std::is_same<R, float>::value;
+  R wr[EPL], wi[EPL];
+#pragma unroll
+  for (int e = 0; e < EPL; ++e) {
+    const int p = lane + 32 * e;
+    wr[e] = R(0);
+    wi[e] = R(0);
+    if (p < N) {
+      const cplx v = W[p];
+      wr[e] = v.x;
+      wi[e] = v.y;
+    }
+  }
   for (int i = 0; i <= it; ++i) {
-    const typename C2<R>::t* V = basis + i * bstride + (size_t)col * N;
-    double dr = 0.0, di = 0.0;
-    if constexpr (F32) {  // complex64: FP32 lane partials, FP64 reduction
-      float fr = 0.f, fi = 0.f;
-      for (int p = lane; p < N; p += 32) {
-        const float2 a = V[p], b = W[p];
-        fr += a.x * b.x + a.y * b.y;
-        fi += a.x * b.y - a.y * b.x;
-      }
-      dr = fr;
-      di = fi;
-    } else {
-      for (int p = lane; p < N; p += 32) {
-        cd a = ld(V + p), b = ld(W + p);
-        dr += a.re * b.re + a.im * b.im;
-        di += a.re * b.im - a.im * b.re;
-      }
+    const cplx* V = basis + i * bstride + (size_t)col * N;
+    cplx vv[EPL];
+    R pr = R(0), pi = R(0);  // lane partial of b_i^H w (FP32 lanes for complex64 walkers)
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      const int p = lane + 32 * e;
+      vv[e].x = R(0);
+      vv[e].y = R(0);
+      if (p < N) vv[e] = V[p];
+      pr += vv[e].x * wr[e] + vv[e].y * wi[e];
+      pi += vv[e].x * wi[e] - vv[e].y * wr[e];
     }
-    dr = warp_sum(dr);
-    di = warp_sum(di);
-    const cd h = mk(dr, di);
-    if constexpr (F32) {
-      const float hr = (float)dr, hi = (float)di;
-      for (int p = lane; p < N; p += 32) {
-        const float2 a = V[p];
-        float2 b = W[p];
-        b.x -= hr * a.x - hi * a.y;
-        b.y -= hr * a.y + hi * a.x;
-        W[p] = b;
-      }
-    } else {
-      for (int p = lane; p < N; p += 32) st(W + p, ld(W + p) - h * ld(V + p));
+    const double dr = (double)warp_sum(pr), di = (double)warp_sum(pi);
+    const R hr = (R)dr, hi = (R)di;
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      wr[e] -= hr * vv[e].x - hi * vv[e].y;
+      wi[e] -= hr * vv[e].y + hi * vv[e].x;
     }
-    __syncwarp();
     if (lane == 0) { H[(i * kmax + it) * 2] = dr; H[(i * kmax + it) * 2 + 1] = di; }
   }
   if (it + 1 < k) {
-    double s = 0.0;
-    if constexpr (F32) {
-      float f = 0.f;
-      for (int p = lane; p < N; p += 32) { const float2 b = W[p]; f += b.x * b.x + b.y * b.y; }
-      s = f;
-    } else {
-      for (int p = lane; p < N; p += 32) s += abs2(ld(W + p));
-    }
-    s = warp_sum(s);
+    R ps = R(0);
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) ps += wr[e] * wr[e] + wi[e] * wi[e];
+    const double s = (double)warp_sum(ps);
     double hn = sqrt(s);
     const double normA = scal[(size_t)(col / nc) * SC_COUNT + SC_NORMA];
     const bool brk = !(hn > 1e-12 * normA);
-    const double inv = brk ? 0.0 : 1.0 / hn;
+    const R inv = brk ? R(0) : (R)(1.0 / hn);
     if (brk) hn = 0.0;
-    typename C2<R>::t* Vn = basis + (it + 1) * bstride + (size_t)col * N;
-    for (int p = lane; p < N; p += 32) st(Vn + p, inv * ld(W + p));
+    cplx* Vn = basis + (it + 1) * bstride + (size_t)col * N;
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      const int p = lane + 32 * e;
+      if (p < N) {
+        cplx o;
+        o.x = inv * wr[e];
+        o.y = inv * wi[e];
+        Vn[p] = o;
+      }
+    }
     if (lane == 0) { H[((it + 1) * kmax + it) * 2] = hn; H[((it + 1) * kmax + it) * 2 + 1] = 0.0; }
   }
 }
@@ -453,9 +451,11 @@ cudaError_t launch_overlap(const afqmc_ctx* c, int Nw, const void* psi, void* th
                            uint32_t* status, cudaStream_t s) {
   const int nmax = c->na > c->nb ? c->na : c->nb;
   const size_t shm = (size_t)2 * nmax * nmax * sizeof(cd);
-  cudaError_t e = cudaFuncSetAttribute(overlap_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm);
-  if (e != cudaSuccess) return e;
-  overlap_kernel<R><<<dim3(Nw, 2), 128, shm, s>>>(static_cast<const typename C2<R>::t*>(psi), c->d_trial,
+  if (!capturing(c)) {
+    cudaError_t e = raise_smem_limit(overlap_kernel<R>);
+    if (e != cudaSuccess) return e;
+  }
+  overlap_kernel<R><<<dim3(Nw, 2), 256, shm, s>>>(static_cast<const typename C2<R>::t*>(psi), c->d_trial,
                                                   c->f_trial, c->N,
                                                   c->na, c->nb, static_cast<typename C2<R>::t*>(theta), logdet,
                                                   status);
@@ -464,8 +464,15 @@ cudaError_t launch_overlap(const afqmc_ctx* c, int Nw, const void* psi, void* th
 
 template <typename R>
 cudaError_t launch_mgs(const afqmc_ctx* c, int Nw, void* psi, const uint8_t* mask, cudaStream_t s) {
-  const size_t shm = (size_t)c->N * sizeof(cd);
-  mgs_kernel<R><<<dim3(Nw, 2), 256, shm, s>>>(static_cast<typename C2<R>::t*>(psi), c->N, c->na, c->nb, mask);
+  const int dets = 2 * Nw;
+  typename C2<R>::t* P = static_cast<typename C2<R>::t*>(psi);
+  const dim3 grid((dets + 7) / 8);
+  if (c->N <= 128)
+    mgs_kernel<R, 4><<<grid, 256, 0, s>>>(P, c->N, c->na, c->nb, Nw, mask);
+  else if (c->N <= 256)
+    mgs_kernel<R, 8><<<grid, 256, 0, s>>>(P, c->N, c->na, c->nb, Nw, mask);
+  else
+    mgs_kernel<R, 16><<<grid, 256, 0, s>>>(P, c->N, c->na, c->nb, Nw, mask);
   return cudaGetLastError();
 }
 
@@ -482,9 +489,18 @@ template <typename R>
 cudaError_t launch_krylov_orth(const afqmc_ctx* c, int Nw, int it, int k, cudaStream_t s) {
   const int ncols = Nw * c->nc;
   const size_t bstride = (size_t)c->ws.n_walkers * c->nc * c->N;
-  krylov_orth_kernel<R><<<(ncols + 7) / 8, 256, 0, s>>>(
-      static_cast<typename C2<R>::t*>(c->ws.term0), static_cast<typename C2<R>::t*>(c->ws.basis), c->ws.hess,
-      c->ws.scal, c->N, c->nc, ncols, it, k, c->ws.kmax, bstride);
+  const typename C2<R>::t* W = static_cast<const typename C2<R>::t*>(c->ws.term0);
+  typename C2<R>::t* Bs = static_cast<typename C2<R>::t*>(c->ws.basis);
+  const dim3 grid((ncols + 7) / 8);
+  if (c->N <= 128)
+    krylov_orth_kernel<R, 4><<<grid, 256, 0, s>>>(W, Bs, c->ws.hess, c->ws.scal, c->N, c->nc, ncols, it, k,
+                                                  c->ws.kmax, bstride);
+  else if (c->N <= 256)
+    krylov_orth_kernel<R, 8><<<grid, 256, 0, s>>>(W, Bs, c->ws.hess, c->ws.scal, c->N, c->nc, ncols, it, k,
+                                                  c->ws.kmax, bstride);
+  else
+    krylov_orth_kernel<R, 16><<<grid, 256, 0, s>>>(W, Bs, c->ws.hess, c->ws.scal, c->N, c->nc, ncols, it, k,
+                                                   c->ws.kmax, bstride);
   return cudaGetLastError();
 }
 
@@ -510,6 +526,13 @@ cudaError_t launch_init_walkers(const afqmc_ctx* c, const afqmc_walkers* w, cuda
                                                 w->status, c->N, c->nc, w->n_walkers);
   return cudaGetLastError();
 }
+
+template <typename R>
+cudaError_t prepare_overlap(const afqmc_ctx*) {
+  return raise_smem_limit(overlap_kernel<R>);
+}
+template cudaError_t prepare_overlap<double>(const afqmc_ctx*);
+template cudaError_t prepare_overlap<float>(const afqmc_ctx*);
 
 #define AFQ_INST(R)                                                                                       \
   template cudaError_t launch_overlap<R>(const afqmc_ctx*, int, const void*, void*, double*, uint32_t*,   \

@@ -1,0 +1,154 @@
+"""Batched stepping of uneven systems as one CUDA graph, and the GEMM tile
+autotuner.  Parity: every system of the batch against the CPU oracle (FP64:
+1e-10 relative; mixed: 1e-4 Ha per walker on E_L).  Consistency: the graph
+replay and any tuned tile choice give results bit-identical to eager steps."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import afqmc_ref as R
+from paper_2403_02542_gb300.inputs import make_fields, make_system
+from walk_helpers import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    from paper_2403_02542_gb300 import build
+    build.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+SYSTEMS = [  # (N, n, G, rho, seed, walkers): uneven sizes and walker counts
+    (24, 3, 40, 0.8, 1, 7),
+    (40, 5, 90, 0.9, 2, 13),
+    (16, 2, 30, 0.7, 3, 5),
+]
+TAU, STEPS, ORDER = 0.05, 4, 6
+
+
+def _setup(precision):
+    from paper_2403_02542_gb300.api import Context
+    out = []
+    for N, n, G, rho, seed, nw in SYSTEMS:
+        s = make_system(N, n, n, G, rho=rho, seed=seed)
+        ham = R.make_hamiltonian(s.h1, s.L, s.trial, n, n)
+        e0 = float(R.local_energy(ham, ham.trial.to(torch.complex128)).real)
+        out.append((s, nw, e0, Context(s.h1, s.L, s.trial, n, n, precision=precision)))
+    return out
+
+
+def _record(w, e_loc, e_mix):
+    return dict(psi=w.psi.cpu().to(torch.complex128).transpose(1, 2).contiguous(),
+                lo=torch.complex(w.logovl[:, 0], w.logovl[:, 1]).cpu(), W=w.weight.cpu().clone(),
+                El=torch.complex(e_loc[:, 0], e_loc[:, 1]).cpu(), emix=e_mix.cpu().clone(),
+                raw=(w.psi.cpu().clone(), w.weight.cpu().clone(), w.logovl.cpu().clone(), e_loc.cpu().clone()))
+
+
+def _batch_walk(systems, expm="krylov"):
+    from paper_2403_02542_gb300.api import Batch
+    ctxs = [c for (_, _, _, c) in systems]
+    ws = [c.new_walkers(nw) for (_, nw, _, c) in systems]
+    for c, w in zip(ctxs, ws):
+        c.init_walkers(w)
+    fields = [torch.empty(nw, s.G, dtype=torch.float64, device=c.device) for (s, nw, _, c) in systems]
+    e_loc = [torch.empty(nw, 2, dtype=torch.float64, device=c.device) for (_, nw, _, c) in systems]
+    e_mix = [torch.empty(4, dtype=torch.float64, device=c.device) for (_, _, _, c) in systems]
+    batch = Batch(ctxs)
+    out = []
+    for k in range(STEPS):
+        for i, (s, nw, _, c) in enumerate(systems):
+            fields[i].copy_(torch.as_tensor(make_fields(100 + i, k, nw, s.G)))
+        batch.step(ws, fields, TAU, [e0 for (_, _, e0, _) in systems], expm=expm, order=ORDER,
+                   reortho=(k % 2 == 1), measure=True, e_loc=e_loc, e_mix=e_mix)
+        torch.cuda.synchronize()
+        out.append([_record(ws[i], e_loc[i], e_mix[i]) for i in range(len(systems))])
+    for c in ctxs:
+        c.sync()
+    batch.close()
+    return out
+
+
+def _eager_walk(systems, expm="krylov"):
+    out = []
+    ws = []
+    for (s, nw, e0, c) in systems:
+        w = c.new_walkers(nw)
+        c.init_walkers(w)
+        ws.append(w)
+    bufs = [(torch.empty(nw, 2, dtype=torch.float64, device=c.device), torch.empty(4, dtype=torch.float64,
+                                                                                   device=c.device))
+            for (_, nw, _, c) in systems]
+    for k in range(STEPS):
+        rec = []
+        for i, (s, nw, e0, c) in enumerate(systems):
+            x = torch.as_tensor(make_fields(100 + i, k, nw, s.G), device=c.device)
+            c.step(ws[i], x, TAU, e0, expm=expm, order=ORDER, reortho=(k % 2 == 1), measure=True,
+                   e_loc=bufs[i][0], e_mix=bufs[i][1])
+            torch.cuda.synchronize()
+            rec.append(_record(ws[i], bufs[i][0], bufs[i][1]))
+        out.append(rec)
+    return out
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_graph_matches_oracle(precision):
+    systems = _setup(precision)
+    got = _batch_walk(systems)
+    for i, (s, nw, e0, _) in enumerate(systems):
+        ref2, ties = _oracle_with_qr(s, nw, e0, i)
+        assert ties == 0
+        for k in range(STEPS):
+            if precision == "fp64":
+                compare(got[k][i], ref2[k], 1e-10, what=f"system {i} step {k}")
+            else:
+                live = ref2[k]["W"] > 0
+                dE = (got[k][i]["El"] - ref2[k]["El"]).abs()[live]
+                assert float(dE.max()) <= 1e-4, (i, k, float(dE.max()))
+
+
+def _oracle_with_qr(s, nw, e0, i):
+    """Oracle walk with QR after odd steps (the batch test's schedule)."""
+    from walk_helpers import near_ties, oracle_setup
+    ham, Lbar, ec, B = oracle_setup(s, TAU)
+    psi, lo, W = R.init_walkers(ham, nw)
+    out = []
+    ties = 0
+    for k in range(STEPS):
+        x = make_fields(100 + i, k, nw, s.G)
+        psi, lo, W, info = R.step(ham, psi, lo, W, x, TAU, e0, method="krylov", k=ORDER,
+                                  reortho=(k % 2 == 1), B=B, L_bar=Lbar, ec=ec)
+        ties += near_ties(info, TAU, e0)
+        El = R.local_energy(ham, psi)
+        out.append(dict(psi=psi.clone(), lo=lo.clone(), W=W.clone(), El=El))
+    return out, ties
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_batch_graph_is_bit_identical_to_eager_steps(precision):
+    got = _batch_walk(_setup(precision))
+    ref = _eager_walk(_setup(precision))
+    for k in range(STEPS):
+        for i in range(len(SYSTEMS)):
+            for a, b in zip(got[k][i]["raw"], ref[k][i]["raw"]):
+                assert torch.equal(a, b), (precision, k, i)
+
+
+def test_autotune_keeps_results_bit_identical(tmp_path):
+    systems = _setup("mixed")
+    ref = _eager_walk(systems)
+    tuned = _setup("mixed")
+    cache = str(tmp_path / "tune.json")
+    tables = [c.autotune(nw, cache=cache) for (_, nw, _, c) in tuned]
+    for t in tables:
+        assert len(t) == 4 and all(0 <= v < 4 for v in t)
+    # reloading from the cache gives the same table without timing
+    again = [c.autotune(nw, cache=cache) for (_, nw, _, c) in _setup("mixed")]
+    assert again == tables
+    got = _eager_walk(tuned)
+    for k in range(STEPS):
+        for i in range(len(SYSTEMS)):
+            for a, b in zip(got[k][i]["raw"], ref[k][i]["raw"]):
+                assert torch.equal(a, b)

@@ -426,6 +426,33 @@ def test_comb_example():
     # total 4, teeth at u + j = 0.25, 1.25, 2.25, 3.25 -> cumulative 0.5, 0.5, 3, 4
     assert R.comb(W, 0.25).tolist() == [0, 2, 2, 3]
     assert R.comb(W, 0.75).tolist() == [2, 2, 2, 3]
+    # a tooth exactly on a cumulative boundary belongs to the next walker
+    assert R.comb(torch.tensor([1.0, 1.0], dtype=RT), 0.0).tolist() == [0, 1]
+
+
+def test_comb_is_unbiased_on_average():
+    """E[number of copies of walker w] = Nw W_w / sum W for u ~ U[0,1)."""
+    g = np.random.default_rng(3)
+    W = torch.as_tensor(g.uniform(0, 2, 16))
+    W[5] = 0.0
+    counts = np.zeros(16)
+    us = (np.arange(4000) + 0.5) / 4000
+    for u in us:
+        counts += np.bincount(R.comb(W, float(u)).numpy(), minlength=16)
+    expect = 16 * W.numpy() / W.numpy().sum()
+    assert np.allclose(counts / len(us), expect, atol=2e-3)
+    assert counts[5] == 0
+
+
+def test_population_control_keeps_total_weight():
+    g = torch.Generator().manual_seed(4)
+    psi = _rand_c(g, 6, 5, 2)
+    lo = _rand_c(g, 6)
+    W = torch.tensor([0.3, 1.2, 0.0, 2.0, 0.5, 1.0], dtype=RT)
+    p2, l2, W2, idx = R.population_control(psi, lo, W, 0.4)
+    assert abs(float(W2.sum()) - float(W.sum())) < 1e-14
+    for j, i in enumerate(idx.tolist()):
+        assert torch.equal(p2[j], psi[i]) and l2[j] == lo[i]
 
 
 # ---------------------------------------------------------------- whole walk
