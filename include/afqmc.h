@@ -216,6 +216,25 @@ afqmc_status afqmc_batch_step(afqmc_batch* batch, const afqmc_walkers* ws, const
                               void* stream);
 void afqmc_batch_destroy(afqmc_batch* batch);
 
+/* Adjoint of the mixed energy estimator at fixed walkers and weights.  The
+ * paper has no gradients; this serves energy derivatives such as bond-length
+ * scans.  With M_ws = Theta_ws trial_s^T the local energy of Eq. eloc is
+ * E_const + sum_s tr(h1 M_ws) + 1/2 sum_g [(sum_s tr(L_g M_ws))^2
+ * - sum_s tr(L_g M_ws L_g M_ws)], so for E_k = sum_w W Ebar_L / sum_w W
+ * (Sec. II.A; dEbar/dRe E_L = 1 strictly inside the window of Eq. enwin,
+ * 0 outside; walkers with W = 0 excluded):
+ *   grad_h1  = dJ * Re sum_w c_w sum_s trial_s Theta_ws^T          [N][N]
+ *   grad_L_g = dJ * Re sum_w c_w sum_s trial_s (t_wg I - T_wgs^T) Theta_ws^T
+ * with c_w = W_w / sum W, T_wgs = trial_s^T L_g Theta_ws, t_wg = sum_s tr T_wgs.
+ * Derivatives are with respect to every entry of h1 and L_g (a symmetric
+ * direction dH gives sum_pq dH_pq grad_pq).  The trial is held fixed.
+ *   grad_h1  device [N][N] double, grad_L device [G][N][N] double (written)
+ * FP64 contexts only (AFQMC_ENOTSUP otherwise, and when na*na + na*N
+ * complex doubles exceed one block's shared memory).  Synchronises the stream.
+ * Errors: EINVAL, EDOM, ENOTSUP, ENOMEM, ECUDA. */
+afqmc_status afqmc_energy_backward(afqmc_ctx* ctx, const afqmc_walkers* w, double e0, double tau, double dJ,
+                                   double* grad_h1, double* grad_L);
+
 /* Size of the device scratch array used by afqmc_local_energy_static. */
 #define AFQMC_STATIC_SCRATCH_BYTES ((unsigned long long)32 << 20) /* 32 MiB */
 

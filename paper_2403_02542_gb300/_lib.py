@@ -53,6 +53,7 @@ SIGNATURES = {
     "afqmc_population_control": (_I, [_P, ctypes.POINTER(Walkers), _D, _P]),
     "afqmc_local_energy_static": (_I, [_P, ctypes.POINTER(Walkers), _D, _D, _P, _P]),
     "afqmc_autotune": (_I, [_P, _I, _P]),
+    "afqmc_energy_backward": (_I, [_P, ctypes.POINTER(Walkers), _D, _D, _D, _P, _P]),
     "afqmc_tune_set": (_I, [_P, _P]),
     "afqmc_tune_get": (_I, [_P, _P]),
     "afqmc_batch_create": (_I, [ctypes.POINTER(_P), _P, _I]),

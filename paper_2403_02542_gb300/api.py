@@ -143,6 +143,16 @@ class Context:
     def sync(self):
         L.check(L.lib().afqmc_sync(self._h), "afqmc_sync")
 
+    def energy_backward(self, w: WalkerSet, e0: float, tau: float, dJ: float = 1.0):
+        """(dE_k/dh1 [N,N], dE_k/dL [G,N,N]) at fixed walkers (afqmc_energy_backward)."""
+        gh = torch.empty(self.N, self.N, dtype=torch.float64, device=self.device)
+        gL = torch.empty(self.G, self.N, self.N, dtype=torch.float64, device=self.device)
+        self._bind_stream()
+        cw = w.c_struct()
+        L.check(L.lib().afqmc_energy_backward(self._h, ctypes.byref(cw), float(e0), float(tau), float(dJ),
+                                              gh.data_ptr(), gL.data_ptr()), "afqmc_energy_backward")
+        return gh, gL
+
     # ------------------------------------------------------------------ tuning
     def tune_key(self, n_walkers: int) -> str:
         return f"N{self.N}_na{self.na}_nb{self.nb}_G{self.G}_{self.precision}_w{n_walkers}"
@@ -242,3 +252,27 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class MixedEnergy(torch.autograd.Function):
+    """E_k(h1, L) at fixed walkers as a differentiable function: the forward
+    runs afqmc_local_energy on a context built from (h1, L), the backward
+    afqmc_energy_backward.  Inputs: h1 [N,N] and L [G,N,N] float64 tensors;
+    `walkers` a dict with psi [Nw, nc, N] complex128, weight [Nw], logovl
+    [Nw, 2] on the device; trial [N, nc]; na, nb; e0; tau."""
+
+    @staticmethod
+    def forward(ctx, h1, chol, walkers, trial, na, nb, e0, tau):
+        c = Context(h1.detach().cpu().numpy(), chol.detach().cpu().numpy(), trial, na, nb, precision="fp64",
+                    device=walkers["psi"].device)
+        w = WalkerSet(walkers["psi"], walkers["weight"], walkers["logovl"],
+                      torch.zeros(walkers["psi"].shape[0], dtype=torch.int32, device=walkers["psi"].device))
+        _, e_mix = c.local_energy(w, e0, tau)
+        ctx.state = (c, w, e0, tau)
+        return e_mix[2].detach().to(h1.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        c, w, e0, tau = ctx.state
+        gh, gL = c.energy_backward(w, e0, tau, float(grad_out))
+        return gh.to(grad_out.device), gL.to(grad_out.device), None, None, None, None, None, None

@@ -724,6 +724,38 @@ afqmc_status afqmc_population_control(afqmc_ctx* c, const afqmc_walkers* w, doub
   return AFQMC_OK;
 }
 
+afqmc_status afqmc_energy_backward(afqmc_ctx* c, const afqmc_walkers* w, double e0, double tau, double dJ,
+                                   double* grad_h1, double* grad_L) {
+  afqmc_status st = check_walkers(c, w);
+  if (st != AFQMC_OK) return st;
+  if (!grad_h1 || !grad_L || ((uintptr_t)grad_h1) % 8 || ((uintptr_t)grad_L) % 8) return AFQMC_EINVAL;
+  if (!std::isfinite(tau) || !std::isfinite(e0) || !std::isfinite(dJ)) return AFQMC_EDOM;
+  if (!(tau > 0.0)) return AFQMC_EINVAL;
+  if (c->prec != AFQMC_FP64) return AFQMC_ENOTSUP;
+  const int nmax = c->na > c->nb ? c->na : c->nb;
+  if ((size_t)(nmax * nmax + nmax * c->N) * 16 > (size_t)max_dyn_smem() - 1024) return AFQMC_ENOTSUP;
+  const size_t NN = (size_t)c->N * c->N;
+  if (w->n_walkers == 0) {
+    CK(cudaMemsetAsync(grad_h1, 0, NN * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(grad_L, 0, (size_t)c->G * NN * sizeof(double), c->stream));
+    return AFQMC_OK;
+  }
+  st = ws_ensure(c, w->n_walkers, c->ws.kmax);
+  if (st != AFQMC_OK) return st;
+  // Theta and E_L at the walkers (window mask), then the adjoint contractions
+  st = run_energy<double>(c, w, e0, tau, c->ws.eloc, c->ws.emix);
+  if (st != AFQMC_OK) return st;
+  double2* ys = nullptr;
+  CK(cudaMalloc(&ys, ((size_t)c->nc * c->N + (size_t)c->G * c->nc * c->N) * sizeof(double2)));
+  cudaError_t e = launch_energy_backward(c, w->n_walkers, w->weight, c->ws.eloc, e0, tau, dJ, grad_h1, grad_L, ys,
+                                         c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  cudaFree(ys);
+  if (e != cudaSuccess) return cuda_fail(e, "energy backward");
+  c->launches += 5;
+  return AFQMC_OK;
+}
+
 afqmc_status afqmc_sync(afqmc_ctx* c) {
   if (!c) return AFQMC_EINVAL;
   CK(cudaStreamSynchronize(c->stream));

@@ -226,6 +226,11 @@ cudaError_t launch_copy_alive(const afqmc_ctx* c, const afqmc_walkers* w, cudaSt
 template <typename R>
 cudaError_t launch_comb(afqmc_ctx* c, const afqmc_walkers* w, double u, int* index_out, cudaStream_t s);
 
+// adjoint of the mixed estimator (k_adjoint.cu)
+cudaError_t launch_energy_backward(afqmc_ctx* c, int Nw, const double* weight, const double* e_loc, double e0,
+                                   double tau, double dJ, double* grad_h1, double* grad_L, double2* yscratch,
+                                   cudaStream_t s);
+
 // tensor-core exchange (k_exchange_tc.cu)
 bool tc_exchange_plan(afqmc_ctx* c);
 cudaError_t tc_exchange_setup(afqmc_ctx* c, cudaStream_t s);

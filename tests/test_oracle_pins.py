@@ -486,3 +486,33 @@ def test_free_projection_matches_fci():
     mean = E.mean()
     assert abs(mean - e_fci) < 3 * sigma + 1e-4, (mean, e_fci, sigma)
     assert abs(e_hf - e_fci) > 5 * sigma, (e_hf, e_fci, sigma)
+
+
+# ---------------------------------------------------------------- gradients
+def test_oracle_energy_gradient_matches_central_differences():
+    """Reverse-mode autograd through the oracle's local energy and mixed
+    estimator agrees with central finite differences along random symmetric
+    directions (the CPU reference for the adjoint)."""
+    s, ham = _small_ham(N=8, n=2, G=10)
+    g = torch.Generator().manual_seed(21)
+    psi = ham.trial.to(CT).unsqueeze(0).repeat(3, 1, 1) + 0.3 * _rand_c(g, 3, 8, 4)
+    W = torch.tensor([1.0, 0.7, 1.3], dtype=RT)
+    e0, tau = float(R.local_energy(ham, ham.trial.to(CT)).real), 0.05
+
+    def J(h1, L):
+        hm = R.Hamiltonian(h1, L, ham.trial, 2, 2)
+        Ec = R.energy_window(R.local_energy(hm, psi), e0, tau, 4)
+        return (W * Ec).sum() / W.sum()
+
+    h1 = ham.h1.clone().requires_grad_(True)
+    L = ham.L.clone().requires_grad_(True)
+    J(h1, L).backward()
+    rng = np.random.default_rng(5)
+    dH = torch.as_tensor(rng.standard_normal((8, 8))); dH = 0.5 * (dH + dH.T)
+    dL = torch.as_tensor(rng.standard_normal((10, 8, 8))); dL = 0.5 * (dL + dL.transpose(1, 2))
+    eps = 1e-5
+    with torch.no_grad():
+        fd_h = (J(ham.h1 + eps * dH, ham.L) - J(ham.h1 - eps * dH, ham.L)) / (2 * eps)
+        fd_L = (J(ham.h1, ham.L + eps * dL) - J(ham.h1, ham.L - eps * dL)) / (2 * eps)
+    assert abs(float(fd_h) - float((h1.grad * dH).sum())) < 1e-8
+    assert abs(float(fd_L) - float((L.grad * dL).sum())) < 1e-8
