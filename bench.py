@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-fp64-compare", action="store_true",
+                    help="skip the FP64-path rate measured beside the mixed one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-walkers", type=int, default=4)
     ap.add_argument("--walkers", type=int, default=NW,
@@ -287,6 +289,63 @@ def run_ours(args):
         dist.barrier()
     e2e = world * NW * K / float(tt[0])
 
+    # -------- the same step replayed as a CUDA graph (one-system batch)
+    from paper_2403_02542_gb300.api import Batch
+    batch = Batch([ctx])
+    x_graph = torch.empty(NW, G, dtype=torch.float64, device=dev)
+    graph_steps = 0
+
+    def graph_step(i):
+        nonlocal graph_steps
+        graph_steps += 1
+        x_graph.copy_(fields[i % (Wm + K)])
+        batch.step([w], [x_graph], TAU, e0, expm="krylov", order=KDIM,
+                   reortho=(graph_steps % REORTHO == 0), measure=True, e_loc=[e_loc], e_mix=[e_mix])
+
+    for i in range(2 * REORTHO):  # capture both graphs (with and without MGS)
+        graph_step(i)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for i in range(K):
+        graph_step(i)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    tg = torch.tensor([g0.elapsed_time(g1)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(tg, op=dist.ReduceOp.MAX)
+    graph_value = world * NW * K / (float(tg[0]) / 1000.0)
+    batch.close()
+
+    # -------- the FP64 path on the same workload, for the mixed-vs-FP64 comparison
+    fp64_value = None
+    if args.precision == "mixed" and not args.no_fp64_compare:
+        c64 = Context(system.h1, system.L, system.trial, na, nb, system.e_const, precision="fp64", device=dev)
+        w64 = c64.new_walkers(NW)
+        c64.init_walkers(w64)
+        el64 = torch.empty(NW, 2, dtype=torch.float64, device=dev)
+        em64 = torch.empty(4, dtype=torch.float64, device=dev)
+        k64 = min(K, 3)
+        for i in range(2):
+            c64.step(w64, fields[i], TAU, e0, expm="krylov", order=KDIM, measure=True, e_loc=el64, e_mix=em64)
+        torch.cuda.synchronize()
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1e = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        for i in range(k64):
+            c64.step(w64, fields[2 + i], TAU, e0, expm="krylov", order=KDIM, reortho=((i + 3) % REORTHO == 0),
+                     measure=True, e_loc=el64, e_mix=em64)
+        h1e.record(stream)
+        torch.cuda.synchronize()
+        th = torch.tensor([h0.elapsed_time(h1e)], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(th, op=dist.ReduceOp.MAX)
+        fp64_value = world * NW * k64 / (float(th[0]) / 1000.0)
+        c64.close()
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -333,6 +392,9 @@ def run_ours(args):
         "e2e": {"value": e2e, "unit": "walker-steps/s",
                 "h2d_bytes_per_step": NW * G * 8, "d2h_bytes_per_step": 4 * 8},
         "gpu_launches": launches,
+        "graph_value": graph_value,
+        "fp64_value": fp64_value,
+        "mixed_over_fp64": (value / fp64_value) if fp64_value else None,
         "clocks": clk,
         "e_mix_last": emix_final,
     }
