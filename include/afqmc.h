@@ -147,7 +147,8 @@ afqmc_status afqmc_walkers_init(afqmc_ctx* ctx, const afqmc_walkers* w);
  *   fields   device [Nw][G] double, standard-normal auxiliary fields x_g^w
  *            (Eq. hstrafo); read only
  *   e_loc    device [Nw][2] double (Re, Im of E_L) or NULL; written when
- *            p->measure is nonzero
+ *            p->measure is nonzero (for walkers whose weight was already 0
+ *            before the step the value is unspecified)
  *   e_mix    device [4] double or NULL; written when p->measure is nonzero:
  *            { sum_w W E_L_capped, sum_w W, E_k = ratio, live walkers }
  * The context keeps scratch space sized for the largest Nw seen; a larger Nw
@@ -181,8 +182,10 @@ afqmc_status afqmc_population_control(afqmc_ctx* ctx, const afqmc_walkers* w, do
 
 /* Autotuner of the step's GEMM tile shapes.  Every walker-batched GEMM call
  * site of afqmc_step (force bias, field assembly, half step B*Psi, products
- * A*V of the exponential) has four output-tile variants (64x64, 128x32,
- * 32x128, 64x32); this call times each variant at each site with CUDA events
+ * A*V of the exponential) has output-tile variants 0..3 (64x64, 128x32,
+ * 32x128, 64x32) and variant 4, a per-walker kernel holding all orbital
+ * columns of a walker (used where it applies, i.e. for A*V; elsewhere it
+ * falls back to variant 0); this call times each variant at each site with CUDA events
  * (one warm-up, three timed launches, minimum kept) for n_walkers walkers on
  * the context's workspace and keeps the fastest.  Tile shape does not change
  * the summation order, so results are bit-identical for every choice.

@@ -356,10 +356,11 @@ const float* pick<float>(const double*, const float* f) { return f; }
 
 template <typename R>
 static afqmc_status run_energy(afqmc_ctx* c, const afqmc_walkers* w, double e0, double tau, double* e_loc,
-                               double* e_mix) {
+                               double* e_mix, bool theta_ready = false) {
   cudaStream_t s = c->stream;
   const int Nw = w->n_walkers;
-  PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, w->psi, c->ws.theta, c->ws.logdet, w->status, s));
+  if (!theta_ready)
+    PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, w->psi, c->ws.theta, c->ws.logdet, w->status, s));
   int nl = 0;
   CK(launch_energy<R>(c, Nw, w->weight, e0, tau, e_loc ? e_loc : c->ws.eloc, e_mix ? e_mix : c->ws.emix, s, &nl));
   c->launches += 2 + nl;
@@ -466,18 +467,23 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
   }
   // psi_new = B acc
   PK(AFQMC_K_HALFSTEP, gemm<R>(site_args<R>(c, SITE_HALFSTEP, Nw, st, ws.acc, ws.psi_new), false, EPI_STORE, s));
-  // new overlap, weights, commit
-  PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, ws.psi_new, nullptr, ws.logdet, w->status, s));
+  // new overlap (and Theta for the local energy when no re-orthonormalisation
+  // follows), weights, commit
+  void* th_new = (p->measure && !p->reortho) ? ws.theta : nullptr;
+  PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, ws.psi_new, th_new, ws.logdet, w->status, s));
   PK(AFQMC_K_OTHER, launch_weights<R>(c, w, p->tau, p->e0, s));
   PK(AFQMC_K_OTHER, launch_commit<R>(c, w, p->reortho, s));
   c->launches += 4;
   if (p->reortho) {
     PK(AFQMC_K_OTHER, launch_mgs<R>(c, Nw, w->psi, ws.alive, s));
-    PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, w->psi, nullptr, ws.logdet, w->status, s));
+    PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, w->psi, p->measure ? ws.theta : nullptr, ws.logdet, w->status, s));
     PK(AFQMC_K_OTHER, launch_logovl_from_logdet(c, w, ws.alive, s));
     c->launches += 3;
   }
-  if (p->measure) return run_energy<R>(c, w, p->e0, p->tau, e_loc, e_mix);
+  // Theta of every live walker is the one of its committed determinant (for
+  // walkers that were already dead it is that of the discarded proposal; their
+  // local energy is unspecified and they do not enter E_k)
+  if (p->measure) return run_energy<R>(c, w, p->e0, p->tau, e_loc, e_mix, true);
   return AFQMC_OK;
 }
 

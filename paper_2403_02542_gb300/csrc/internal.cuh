@@ -62,9 +62,9 @@ struct GemmArgs {
   // `part` [splitk][M][Nn] (complex, R), summed in fixed order afterwards
   int splitk;
   void* part;
-  int variant;  // output tile: 0 = 64x64, 1 = 128x32, 2 = 32x128, 3 = 64x32
+  int variant;  // output tile: 0 = 64x64, 1 = 128x32, 2 = 32x128, 3 = 64x32, 4 = per-walker A*V
 };
-constexpr int GEMM_VARIANTS = 4;
+constexpr int GEMM_VARIANTS = 5;
 // GEMM call sites of the step, each with its own tuned tile variant
 enum GemmSite { SITE_FORCEBIAS = 0, SITE_FIELD = 1, SITE_HALFSTEP = 2, SITE_EXPM = 3, N_SITES = 4 };
 template <typename R>
@@ -159,7 +159,7 @@ struct afqmc_ctx {
   afq::Workspace ws;
   afq::Prof prof;
   afq::TcPlan tc;
-  int tune[afq::N_SITES] = {0, 0, 0, 0};  // GEMM tile variant per call site
+  int tune[afq::N_SITES] = {0, 0, 0, 4};  // GEMM tile variant per call site
   bool capturing = false;                  // inside a graph capture (afqmc_batch_step)
   uint64_t launches = 0;
 };

@@ -6,7 +6,7 @@
 //
 // C[b][m][n] = alpha * sum_k A[b][m][k] B[b][n][k], strides in elements.
 // Output tile BM x BN (four variants: 64x64, 128x32, 32x128, 64x32, chosen per
-// call site by the autotuner), K slab of 8 staged in shared memory, 256
+// call site by the autotuner; a fifth, per-walker kernel for the products A*V), K slab of 8 staged in shared memory, 256
 // threads with a (BM/16) x (BN/16) register tile each.  The thread-to-output
 // map follows the unit stride of C so that the stores coalesce.
 #include "internal.cuh"
@@ -151,6 +151,103 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g) {
   }
 }
 
+// Per-walker product C[w][j][p] = alpha sum_q A[w][p][q] X[w][j][q] (complex A,
+// X, C; D += C when given): one block per (64-row tile of p, walker), all nc
+// columns of the walker in registers (JT per thread), K staged in slabs of 32.
+// The per-element FMA sequence equals gemm_kernel's, so results agree bit for bit.
+constexpr int WM_BM = 64;
+template <typename R, int JT>
+__global__ void __launch_bounds__(256) walker_gemm_kernel(GemmArgs g) {
+  typedef typename C2<R>::t cplx;
+  constexpr int WM_BK = sizeof(R) == 8 ? 16 : 32;  // static shared memory stays below 48 KB
+  __shared__ cplx sA[WM_BK][WM_BM];        // A[p][k] slab, p contiguous
+  __shared__ cplx sX[WM_BK][8 * JT];       // X[j][k] slab, j contiguous
+  const int w = blockIdx.y, m0 = blockIdx.x * WM_BM;
+  const int N = g.M, nc = g.Nn, K = g.K;
+  const int tid = threadIdx.x;
+  const int pg = tid & 31, jg = tid >> 5;  // rows m0 + 2 pg + {0,1}, columns jg + 8 t
+  const cplx* A = static_cast<const cplx*>(g.A) + (size_t)w * g.sa_b;
+  const cplx* X = static_cast<const cplx*>(g.B) + (size_t)w * g.sb_b;
+  R accr[2][JT], acci[2][JT];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int t = 0; t < JT; ++t) accr[i][t] = acci[i][t] = R(0);
+  for (int k0 = 0; k0 < K; k0 += WM_BK) {
+    for (int l = tid; l < WM_BM * WM_BK; l += 256) {  // coalesced along k (A[p][q], unit stride in q)
+      const int kk = l % WM_BK, mm = l / WM_BK;
+      const int m = m0 + mm, k = k0 + kk;
+      cplx v;
+      v.x = R(0); v.y = R(0);
+      if (m < N && k < K) v = A[(size_t)m * g.sa_m + k];
+      sA[kk][mm] = v;
+    }
+    for (int l = tid; l < 8 * JT * WM_BK; l += 256) {
+      const int kk = l % WM_BK, jj = l / WM_BK;
+      const int k = k0 + kk;
+      cplx v;
+      v.x = R(0); v.y = R(0);
+      if (jj < nc && k < K) v = X[(size_t)jj * g.sb_n + k];
+      sX[kk][jj] = v;
+    }
+    __syncthreads();
+    const int kn = min(WM_BK, K - k0);
+    for (int kk = 0; kk < kn; ++kk) {
+      const cplx a0 = sA[kk][2 * pg], a1 = sA[kk][2 * pg + 1];
+#pragma unroll
+      for (int t = 0; t < JT; ++t) {
+        const cplx b = sX[kk][jg + 8 * t];
+        accr[0][t] = fma(a0.x, b.x, accr[0][t]);
+        acci[0][t] = fma(a0.x, b.y, acci[0][t]);
+        accr[0][t] = fma(-a0.y, b.y, accr[0][t]);
+        acci[0][t] = fma(a0.y, b.x, acci[0][t]);
+        accr[1][t] = fma(a1.x, b.x, accr[1][t]);
+        acci[1][t] = fma(a1.x, b.y, acci[1][t]);
+        accr[1][t] = fma(-a1.y, b.y, accr[1][t]);
+        acci[1][t] = fma(a1.y, b.x, acci[1][t]);
+      }
+    }
+    __syncthreads();
+  }
+  cplx* C = static_cast<cplx*>(g.C) + (size_t)w * g.sc_b;
+  cplx* D = g.D ? static_cast<cplx*>(g.D) + (size_t)w * g.sc_b : nullptr;
+  const R alr = (R)g.alpha_re, ali = (R)g.alpha_im;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const int m = m0 + 2 * pg + i;
+    if (m >= N) continue;
+#pragma unroll
+    for (int t = 0; t < JT; ++t) {
+      const int j = jg + 8 * t;
+      if (j >= nc) continue;
+      cplx v;
+      v.x = alr * accr[i][t] - ali * acci[i][t];
+      v.y = alr * acci[i][t] + ali * accr[i][t];
+      const size_t off = (size_t)m + (size_t)j * g.sc_n;
+      C[off] = v;
+      if (D) {
+        cplx d = D[off];
+        d.x += v.x;
+        d.y += v.y;
+        D[off] = d;
+      }
+    }
+  }
+}
+
+template <typename R, int JT>
+cudaError_t walker_gemm_launch(const GemmArgs& g, cudaStream_t s) {
+  dim3 grid((g.M + WM_BM - 1) / WM_BM, g.batch);
+  walker_gemm_kernel<R, JT><<<grid, 256, 0, s>>>(g);
+  return cudaGetLastError();
+}
+
+// The walker kernel applies to complex A, per-walker batches with unit stride
+// along K for A and X and along p for C.
+bool walker_gemm_ok(const GemmArgs& g, bool a_complex) {
+  return a_complex && g.batch >= 1 && g.sa_k == 1 && g.sb_k == 1 && g.sc_m == 1 && g.Nn <= 96 && g.batch <= 65535;
+}
+
 // Sum the split-K partials in fixed order, scale by alpha, store to C.
 template <typename R>
 __global__ void splitk_reduce_kernel(GemmArgs g) {
@@ -197,6 +294,7 @@ cudaError_t gemm(const GemmArgs& a, bool a_complex, int epi, cudaStream_t s) {
   if (a.M <= 0 || a.Nn <= 0 || a.batch <= 0) return cudaSuccess;
   GemmArgs g = a;
   if (g.variant < 0 || g.variant >= GEMM_VARIANTS) g.variant = 0;
+  if (g.variant == 4 && (a.splitk > 1 || !walker_gemm_ok(g, a_complex))) g.variant = 0;
   if (epi != EPI_STORE_ADD) g.D = nullptr;
   if (g.splitk > 1 && g.part && g.batch == 1 && epi == EPI_STORE) {
     cudaError_t e = a_complex ? gemm_variant<R, true>(g, g.splitk, s) : gemm_variant<R, false>(g, g.splitk, s);
@@ -208,6 +306,13 @@ cudaError_t gemm(const GemmArgs& a, bool a_complex, int epi, cudaStream_t s) {
     return cudaGetLastError();
   }
   g.splitk = 1;
+  if (g.variant == 4 && walker_gemm_ok(g, a_complex)) {
+    if (g.Nn <= 16) return walker_gemm_launch<R, 2>(g, s);
+    if (g.Nn <= 40) return walker_gemm_launch<R, 5>(g, s);
+    if (g.Nn <= 64) return walker_gemm_launch<R, 8>(g, s);
+    return walker_gemm_launch<R, 12>(g, s);
+  }
+  if (g.variant >= 4) g.variant = 0;
   return a_complex ? gemm_variant<R, true>(g, a.batch, s) : gemm_variant<R, false>(g, a.batch, s);
 }
 

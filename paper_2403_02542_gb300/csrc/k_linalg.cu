@@ -28,7 +28,18 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 
 // ---------------------------------------------------------------- overlap
-// grid (Nw, 2 spins), block 256.  Shared: LU [n][n] and O^{-1} [n][n], FP64 complex.
+// grid (Nw, 2 spins), block 256.  Shared: LU [n][n], O^{-1} [n][n] + [n],
+// FP64 complex.  On this GPU an FP64 warp instruction occupies the FP64 pipe
+// for its full duration whatever the number of active lanes, so the FP64
+// parts are kept few and warp-wide: the LU (FP64), one reciprocal per pivot,
+// the log-determinant summed across a warp.  Complex64 walkers get Theta from
+// FP32 triangular solves on the rounded LU factors; FP64 walkers from the
+// FP64 inverse.
+__device__ __forceinline__ cd crecip(cd z) {  // 1/z = conj(z)/|z|^2
+  const double r = 1.0 / abs2(z);
+  return cd{z.re * r, -z.im * r};
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* __restrict__ psi,
                                                       const double* __restrict__ trial,
@@ -40,22 +51,24 @@ __global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* _
   const int w = blockIdx.x, spin = blockIdx.y;
   const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
   const int tid = threadIdx.x, nt = blockDim.x;
+  const int wid = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
   double* ldw = logdet + (size_t)w * 4 + spin * 2;
   if (n == 0) {
     if (tid == 0) { ldw[0] = 0.0; ldw[1] = 0.0; }
     return;
   }
   cd* LU = reinterpret_cast<cd*>(smem_ov);  // [n][n] row-major
-  cd* Inv = LU + n * n;                     // [n][n]
+  cd* Inv = LU + n * n;                     // [n][n] (+ [n] reciprocal diagonal)
   __shared__ int perm[128];
   __shared__ int s_piv, s_swaps, s_sing;
+  __shared__ cd s_rpk;
   const typename C2<R>::t* P = psi + ((size_t)w * nc + off) * N;
 
   // O[i][j] = sum_p trial[off+i][p] psi[off+j][p]
   if constexpr (std::is_same<R, float>::value) {
     // complex64 walkers: one warp per entry, lanes stride over p (coalesced),
-    // FP32 lane partials and FP32 tree; the entry is kept in FP64 from here on
-    const int wid = tid >> 5, lane = tid & 31, nwarp = nt >> 5;
+    // FP32 lane partials and tree; the FP32 entries are widened in one pass
+    float2* Of = reinterpret_cast<float2*>(Inv);  // scratch until the solves
     for (int e = wid; e < n * n; e += nwarp) {
       const int i = e / n, j = e % n;
       const float2* X = P + (size_t)j * N;
@@ -68,8 +81,10 @@ __global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* _
       }
       fr = warp_sum(fr);
       fi = warp_sum(fi);
-      if (lane == 0) LU[e] = mk((double)fr, (double)fi);
+      if (lane == 0) Of[e] = make_float2(fr, fi);
     }
+    __syncthreads();
+    for (int e = tid; e < n * n; e += nt) LU[e] = mk((double)Of[e].x, (double)Of[e].y);
   } else {
     // FP64: one thread per entry, sequential over p (fewest FP64 operations)
     for (int e = tid; e < n * n; e += nt) {
@@ -91,10 +106,10 @@ __global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* _
 
   // LU with partial pivoting: (P O) = L U, row i of PO is row perm[i] of O
   for (int k = 0; k < n; ++k) {
-    if (tid < 32) {  // pivot: largest |LU[i][k]|, i >= k; ties keep the smaller row
+    if (wid == 0) {  // pivot: largest |LU[i][k]|, i >= k; ties keep the smaller row
       int piv = k;
       double best = -1.0;
-      for (int i = k + tid; i < n; i += 32) {
+      for (int i = k + lane; i < n; i += 32) {
         const double v = abs2(LU[i * n + k]);
         if (v > best) { best = v; piv = i; }
       }
@@ -104,9 +119,10 @@ __global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* _
         const int op = __shfl_xor_sync(0xffffffffu, piv, o);
         if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
       }
-      if (tid == 0) {
+      if (lane == 0) {
         s_piv = piv;
         if (!(best > 0.0)) s_sing = 1;
+        s_rpk = crecip(LU[piv * n + k]);
         if (piv != k) {
           s_swaps ^= 1;
           int t = perm[k]; perm[k] = perm[piv]; perm[piv] = t;
@@ -120,8 +136,8 @@ __global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* _
         cd t = LU[k * n + j]; LU[k * n + j] = LU[piv * n + j]; LU[piv * n + j] = t;
       }
     __syncthreads();
-    const cd pk = LU[k * n + k];
-    for (int i = k + 1 + tid; i < n; i += nt) LU[i * n + k] = cdiv(LU[i * n + k], pk);
+    const cd rpk = s_rpk;
+    for (int i = k + 1 + tid; i < n; i += nt) LU[i * n + k] = LU[i * n + k] * rpk;
     __syncthreads();
     const int rem = n - k - 1;
     for (int e = tid; e < rem * rem; e += nt) {
@@ -131,60 +147,93 @@ __global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* _
     __syncthreads();
   }
 
-  if (tid == 0) {
-    double lr = 0.0, li = s_swaps ? M_PI : 0.0;
-    for (int k = 0; k < n; ++k) {
-      cd u = LU[k * n + k];
+  // log det = sum_i log U_ii + i pi [odd number of swaps], summed across warp 0
+  if (wid == 0) {
+    double lr = 0.0, li = 0.0;
+    for (int k = lane; k < n; k += 32) {
+      const cd u = LU[k * n + k];
       lr += 0.5 * log(abs2(u));
       li += atan2(u.im, u.re);
     }
-    if (s_sing) { lr = CUDART_NAN; li = CUDART_NAN; }
-    ldw[0] = lr;
-    ldw[1] = li;
-    if (s_sing && status) atomicOr(status + w, (uint32_t)AFQMC_W_SINGULAR);
+    lr = warp_sum(lr);
+    li = warp_sum(li);
+    if (lane == 0) {
+      li += s_swaps ? M_PI : 0.0;
+      if (s_sing) { lr = CUDART_NAN; li = CUDART_NAN; }
+      ldw[0] = lr;
+      ldw[1] = li;
+      if (s_sing && status) atomicOr(status + w, (uint32_t)AFQMC_W_SINGULAR);
+    }
   }
   if (!theta) return;
-
-  // O^{-1} column j: L y = P e_j, U x = y.  (P e_j)_i = [perm[i] == j]
-  for (int j = tid; j < n; j += nt) {
-    for (int i = 0; i < n; ++i) {
-      cd y = mk(perm[i] == j ? 1.0 : 0.0, 0.0);
-      for (int k = 0; k < i; ++k) y = y - LU[i * n + k] * Inv[k * n + j];
-      Inv[i * n + j] = y;
-    }
-    for (int i = n - 1; i >= 0; --i) {
-      cd x = Inv[i * n + j];
-      for (int k = i + 1; k < n; ++k) x = x - LU[i * n + k] * Inv[k * n + j];
-      Inv[i * n + j] = cdiv(x, LU[i * n + i]);
-    }
-  }
-  __syncthreads();
-
-  // Theta[j][p] = sum_i psi[i][p] Oinv[i][j]
   typename C2<R>::t* Th = theta + ((size_t)w * nc + off) * N;
+
   if constexpr (std::is_same<R, float>::value) {
-    // complex64 walkers: O^{-1} rounded to complex64, product in FP32
-    float2* InvF = reinterpret_cast<float2*>(LU);
-    for (int e = tid; e < n * n; e += nt) InvF[e] = make_float2((float)Inv[e].re, (float)Inv[e].im);
+    // Theta row p solves theta_p O = psi_p: with PO = LU, theta_p = u_p P where
+    // v U = psi_p (forward over columns of U) and u L = v (backward, unit L).
+    float2* Lf = reinterpret_cast<float2*>(Inv);  // rounded factors, [n][n]
+    __shared__ float2 s_rdiag[128];
+    for (int e = tid; e < n * n; e += nt) Lf[e] = make_float2((float)LU[e].re, (float)LU[e].im);
+    for (int i = tid; i < n; i += nt) {
+      const cd r = crecip(LU[i * n + i]);
+      s_rdiag[i] = make_float2((float)r.re, (float)r.im);
+    }
     __syncthreads();
-    for (int e = tid; e < n * N; e += nt) {
-      const int j = e / N, p = e % N;
-      float sr = 0.f, si = 0.f;
-      for (int i = 0; i < n; ++i) {
-        const float2 x = P[(size_t)i * N + p], y = InvF[i * n + j];
-        sr = fmaf(x.x, y.x, sr);
-        sr = fmaf(-x.y, y.y, sr);
-        si = fmaf(x.x, y.y, si);
-        si = fmaf(x.y, y.x, si);
+    float vr[80], vi[80];  // n <= 80
+    for (int p = tid; p < N; p += nt) {
+      for (int j = 0; j < n; ++j) {  // v U = psi_p
+        const float2 x = P[(size_t)j * N + p];
+        float ar = x.x, ai = x.y;
+        for (int i = 0; i < j; ++i) {
+          const float2 u = Lf[i * n + j];
+          ar -= vr[i] * u.x - vi[i] * u.y;
+          ai -= vr[i] * u.y + vi[i] * u.x;
+        }
+        const float2 d = s_rdiag[j];
+        vr[j] = ar * d.x - ai * d.y;
+        vi[j] = ar * d.y + ai * d.x;
       }
-      Th[(size_t)j * N + p] = make_float2(sr, si);
+      for (int i = n - 1; i >= 0; --i) {  // u L = v  (L unit lower: L[k][i], k > i)
+        float ar = vr[i], ai = vi[i];
+        for (int k = i + 1; k < n; ++k) {
+          const float2 l = Lf[k * n + i];
+          ar -= vr[k] * l.x - vi[k] * l.y;
+          ai -= vr[k] * l.y + vi[k] * l.x;
+        }
+        vr[i] = ar;
+        vi[i] = ai;
+      }
+      for (int i = 0; i < n; ++i) Th[(size_t)perm[i] * N + p] = make_float2(vr[i], vi[i]);
     }
   } else {
+    // O^{-1} column j: L y = P e_j, U x = y.  (P e_j)_i = [perm[i] == j], so y
+    // vanishes above row r = perm^{-1}(j); the diagonal of U is inverted once.
+    cd* rdiag = Inv + n * n;
+    for (int i = tid; i < n; i += nt) rdiag[i] = crecip(LU[i * n + i]);
+    __syncthreads();
+    for (int j = tid; j < n; j += nt) {
+      int r = 0;
+      while (perm[r] != j) ++r;
+      for (int i = 0; i < r; ++i) Inv[i * n + j] = mk(0.0, 0.0);
+      Inv[r * n + j] = mk(1.0, 0.0);
+      for (int i = r + 1; i < n; ++i) {
+        cd y = mk(0.0, 0.0);
+        for (int k = r; k < i; ++k) y = y - LU[i * n + k] * Inv[k * n + j];
+        Inv[i * n + j] = y;
+      }
+      for (int i = n - 1; i >= 0; --i) {
+        cd x = Inv[i * n + j];
+        for (int k = i + 1; k < n; ++k) x = x - LU[i * n + k] * Inv[k * n + j];
+        Inv[i * n + j] = x * rdiag[i];
+      }
+    }
+    __syncthreads();
+    // Theta[j][p] = sum_i psi[i][p] Oinv[i][j]
     for (int e = tid; e < n * N; e += nt) {
       const int j = e / N, p = e % N;
-      cd s = mk(0.0, 0.0);
-      for (int i = 0; i < n; ++i) s = s + ld(P + (size_t)i * N + p) * Inv[i * n + j];
-      st(Th + (size_t)j * N + p, s);
+      cd sacc = mk(0.0, 0.0);
+      for (int i = 0; i < n; ++i) sacc = sacc + ld(P + (size_t)i * N + p) * Inv[i * n + j];
+      st(Th + (size_t)j * N + p, sacc);
     }
   }
 }
@@ -387,7 +436,9 @@ __global__ void krylov_expm_kernel(double* __restrict__ hess, const double* __re
         tn += abs2(u[i]);
         an += abs2(v[i]);
       }
-      if (tn <= 1e-36 * an) break;
+      // complex64 walkers carry ~1e-7 relative error: terms below 1e-10 of the sum
+      // are dropped there; FP64 walkers sum to 1e-18
+      if (tn <= (std::is_same<R, float>::value ? 1e-20 : 1e-36) * an) break;
     }
   }
   // store y in column 0 of H (no longer needed)
@@ -450,7 +501,7 @@ template <typename R>
 cudaError_t launch_overlap(const afqmc_ctx* c, int Nw, const void* psi, void* theta, double* logdet,
                            uint32_t* status, cudaStream_t s) {
   const int nmax = c->na > c->nb ? c->na : c->nb;
-  const size_t shm = (size_t)2 * nmax * nmax * sizeof(cd);
+  const size_t shm = (size_t)(2 * nmax * nmax + nmax) * sizeof(cd);
   if (!capturing(c)) {
     cudaError_t e = raise_smem_limit(overlap_kernel<R>);
     if (e != cudaSuccess) return e;
