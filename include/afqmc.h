@@ -238,6 +238,55 @@ void afqmc_batch_destroy(afqmc_batch* batch);
 afqmc_status afqmc_energy_backward(afqmc_ctx* ctx, const afqmc_walkers* w, double e0, double tau, double dJ,
                                    double* grad_h1, double* grad_L);
 
+/* Adjoint of a fixed-field walk: gradient of the mixed estimator after n steps,
+ * J = E_n = sum_w W_n Ebar_L(Psi_n) / sum_w W_n (Sec. II.A), with respect to h1
+ * and every L_g, through every step of the walk (Split-2 propagator, Sec. III.B,
+ * with the Taylor exponential of Eq. taylor).  The paper has no gradients; the
+ * readings taken are: the auxiliary fields are fixed inputs; every threshold
+ * decision of the forward walk (force-bias removal |f_g| >= 1, reweighting cap,
+ * cos(dtheta) <= 0, energy window) is held fixed, so a removed component or a
+ * capped quantity carries no derivative, and d max(0, cos dtheta) =
+ * -sin(dtheta) d(dtheta) where cos > 0; the re-orthonormalisation is a fixed
+ * right multiplication Psi <- Psi R^{-1} (exact here: E_L, the force bias,
+ * the overlap ratio and the Taylor action are invariant under Psi -> Psi M);
+ * the trial is held fixed; the dependence of e^{-tau h''/2} on h'' is taken
+ * through the eigendecomposition (Daleckii-Krein divided differences).  The
+ * mean-field shift L_bar_g = <Psi_T|L_g|Psi_T>, h'' and E_c' are functions of
+ * h1 and L and are differentiated as such.
+ * The walk is recomputed from checkpoints taken every ckpt_every steps.
+ *   initial   walkers at step 0 (read only; logovl must equal
+ *             log <Psi_T|Psi_0>, as afqmc_walkers_init leaves it)
+ *   fields    device [n_steps][Nw][G] double, the fields of each step
+ *   p         n_steps >= 1; order = Taylor order 1..32; reortho_every r:
+ *             re-orthonormalise after step k when (k+1) % r == 0 (0: never);
+ *             ckpt_every >= 1; tau > 0; e0; dJ scales every output gradient
+ *   J_out     device [4] double or NULL: {sum W Ebar_L, sum W, J, live
+ *             walkers} after the walk (as e_mix of afqmc_step)
+ *   grad_h1   device [N][N] double, grad_L device [G][N][N] double (written):
+ *             dJ times the derivative along symmetric perturbations, returned
+ *             symmetrised (for a symmetric direction dH the change of J is
+ *             sum_pq dH_pq grad_pq)
+ *   grad_psi0 device [Nw][na+nb][N] complex double or NULL: G with
+ *             dJ = Re sum G * dPsi_0 element by element (no conjugation), for a
+ *             change of the initial walkers with logovl following Psi_0
+ * Memory: the call allocates and frees its own device workspace (about
+ * (ckpt_every + n_steps/ckpt_every + 2 order + 12) Nw (na+nb) N complex
+ * doubles plus Nw N^2 and G N^2 complex doubles).  FP64 contexts only
+ * (AFQMC_ENOTSUP otherwise or when max(na, nb) > 64).  Synchronises the
+ * stream.  Errors: EINVAL, EDOM, ENOTSUP, ENOMEM, ECUDA. */
+typedef struct {
+  int n_steps;
+  int order;
+  int reortho_every;
+  int ckpt_every;
+  double tau;
+  double e0;
+  double dJ;
+} afqmc_walk_adjoint_params;
+afqmc_status afqmc_walk_backward(afqmc_ctx* ctx, const afqmc_walkers* initial, const double* fields,
+                                 const afqmc_walk_adjoint_params* p, double* J_out, double* grad_h1,
+                                 double* grad_L, void* grad_psi0);
+
 /* Size of the device scratch array used by afqmc_local_energy_static. */
 #define AFQMC_STATIC_SCRATCH_BYTES ((unsigned long long)32 << 20) /* 32 MiB */
 

@@ -54,6 +54,7 @@ __all__ = [
     "split2_propagate", "local_energy", "energy_window", "mixed_energy",
     "mgs_qr", "reorthonormalise", "weight_update", "step", "init_walkers",
     "free_projection_step", "comb", "population_control", "StepInfo",
+    "walk_objective",
 ]
 
 
@@ -166,7 +167,7 @@ def propagation_h1(ham: Hamiltonian, L_bar=None):
         L_bar = mean_field_shift(ham)
     LL = torch.einsum("gpr,grq->pq", ham.L, ham.L)
     hpp = ham.h1 - 0.5 * LL + torch.einsum("g,gpq->pq", L_bar, ham.L)
-    ec = ham.e_const - 0.5 * float((L_bar * L_bar).sum())
+    ec = ham.e_const - 0.5 * (L_bar * L_bar).sum()      # a 0-dim tensor (stays on the autograd graph)
     return hpp, ec
 
 
@@ -470,3 +471,59 @@ def population_control(psi, logovl, W, u):
         total = total + x
     n = W.shape[0]
     return psi[idx].clone(), logovl[idx].clone(), torch.full((n,), total / n, dtype=RT), idx
+
+
+# --------------------------------------------------------------------------
+# Objective of the adjoint (the paper has no gradients; reading R10)
+# --------------------------------------------------------------------------
+def _reortho_fixed_R(ham: Hamiltonian, psi, alive):
+    """Psi_sigma <- Psi_sigma R^{-1} with R of the MGS QR held constant
+    (reading R10), for live walkers; dead walkers are returned unchanged."""
+    out = []
+    for w in range(psi.shape[0]):
+        if not bool(alive[w]):
+            out.append(psi[w])
+            continue
+        blocks = []
+        for sl in ham.spins():
+            if sl.stop == sl.start:
+                continue
+            X = psi[w][:, sl]
+            with torch.no_grad():
+                _, Rm = mgs_qr(X.detach().clone())
+            blocks.append(X @ torch.linalg.inv(Rm))
+        out.append(torch.cat(blocks, dim=1))
+    return torch.stack(out)
+
+
+def walk_objective(ham: Hamiltonian, psi0, W0, fields, tau, e0, k=6, reortho_every=0):
+    """J = E_n, the mixed estimator of the capped local energy after n
+    fixed-field Split-2 steps with the Taylor exponential (Sec. II.A, Sec.
+    III.B, Eq. taylor), as a function that torch autograd differentiates with
+    respect to ham.h1, ham.L and psi0.
+
+    Reading R10: the fields are fixed inputs; every threshold decision is
+    whatever the forward walk takes (torch.where / clamp give zero derivative
+    in a removed or capped branch); L_bar, h'', E_c' and B are recomputed from
+    ham.h1 and ham.L; the initial log-overlap follows psi0; after step k with
+    (k+1) % reortho_every == 0 the orbitals of live walkers are multiplied by
+    R^{-1} of their MGS QR, R held constant.  Returns (J, W_n, E_L(Psi_n)).
+    """
+    L_bar = mean_field_shift(ham)
+    hpp, ec = propagation_h1(ham, L_bar)
+    B = half_step_propagator(hpp, tau)
+    psi = psi0
+    logovl = log_overlap(ham, psi)
+    W = torch.as_tensor(W0, dtype=RT)
+    for kk, x in enumerate(fields):
+        alive = W > 0
+        psi, logovl, W, _ = step(ham, psi, logovl, W, x, tau, e0, method="taylor", k=k,
+                                 reortho=False, B=B, L_bar=L_bar, ec=ec)
+        if reortho_every and (kk + 1) % reortho_every == 0:
+            psi = _reortho_fixed_R(ham, psi, alive)
+            logovl = torch.where(alive, log_overlap(ham, psi), logovl)
+    El = local_energy(ham, psi)
+    live = W > 0
+    Ebar = torch.where(live, energy_window(El, e0, tau, ham.na + ham.nb), torch.zeros_like(W))
+    Wl = torch.where(live, W, torch.zeros_like(W))
+    return (Wl * Ebar).sum() / Wl.sum(), W, El

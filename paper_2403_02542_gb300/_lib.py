@@ -36,6 +36,12 @@ class StepParams(ctypes.Structure):
 _P = ctypes.c_void_p
 _D = ctypes.c_double
 _I = ctypes.c_int
+class WalkAdjointParams(ctypes.Structure):
+    _fields_ = [("n_steps", ctypes.c_int), ("order", ctypes.c_int),
+                ("reortho_every", ctypes.c_int), ("ckpt_every", ctypes.c_int),
+                ("tau", ctypes.c_double), ("e0", ctypes.c_double), ("dJ", ctypes.c_double)]
+
+
 SIGNATURES = {
     "afqmc_create": (_I, [ctypes.POINTER(_P), _I, _I, _I, _I, _P, _P, _P, _D, _I, _P]),
     "afqmc_set_tau": (_I, [_P, _D]),
@@ -54,6 +60,8 @@ SIGNATURES = {
     "afqmc_local_energy_static": (_I, [_P, ctypes.POINTER(Walkers), _D, _D, _P, _P]),
     "afqmc_autotune": (_I, [_P, _I, _P]),
     "afqmc_energy_backward": (_I, [_P, ctypes.POINTER(Walkers), _D, _D, _D, _P, _P]),
+    "afqmc_walk_backward": (_I, [_P, ctypes.POINTER(Walkers), _P, ctypes.POINTER(WalkAdjointParams),
+                                 _P, _P, _P, _P]),
     "afqmc_tune_set": (_I, [_P, _P]),
     "afqmc_tune_get": (_I, [_P, _P]),
     "afqmc_batch_create": (_I, [ctypes.POINTER(_P), _P, _I]),

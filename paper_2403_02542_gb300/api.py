@@ -153,6 +153,33 @@ class Context:
                                               gh.data_ptr(), gL.data_ptr()), "afqmc_energy_backward")
         return gh, gL
 
+    def walk_backward(self, w: WalkerSet, fields: torch.Tensor, tau: float, e0: float, order: int = 6,
+                      reortho_every: int = 0, ckpt_every: int = 10, dJ: float = 1.0, grad_psi0: bool = False):
+        """Gradient of the mixed estimator after a fixed-field walk (afqmc_walk_backward).
+
+        `w` holds the walkers at step 0 (left unchanged); `fields` is a device
+        tensor [n_steps, Nw, G] of the walk's auxiliary fields.  Returns
+        (e_mix [4], dJ/dh1 [N,N], dJ/dL [G,N,N]) and, with grad_psi0=True, the
+        derivative G [Nw, na+nb, N] with dJ = Re sum G * dPsi_0 as well.
+        """
+        f = fields.to(device=self.device, dtype=torch.float64).contiguous()
+        if f.dim() != 3 or f.shape[1] != w.n or f.shape[2] != self.G:
+            raise ValueError("fields must be [n_steps, n_walkers, G]")
+        p = L.WalkAdjointParams(int(f.shape[0]), int(order), int(reortho_every), int(ckpt_every),
+                                float(tau), float(e0), float(dJ))
+        J = torch.empty(4, dtype=torch.float64, device=self.device)
+        gh = torch.empty(self.N, self.N, dtype=torch.float64, device=self.device)
+        gL = torch.empty(self.G, self.N, self.N, dtype=torch.float64, device=self.device)
+        gp = torch.empty(w.n, self.nc, self.N, dtype=torch.complex128, device=self.device) if grad_psi0 else None
+        self._bind_stream()
+        cw = w.c_struct()
+        L.check(L.lib().afqmc_walk_backward(self._h, ctypes.byref(cw), f.data_ptr(), ctypes.byref(p), J.data_ptr(),
+                                            gh.data_ptr(), gL.data_ptr(), gp.data_ptr() if gp is not None else None),
+                "afqmc_walk_backward")
+        if grad_psi0:
+            return J, gh, gL, gp
+        return J, gh, gL
+
     # ------------------------------------------------------------------ tuning
     def tune_key(self, n_walkers: int) -> str:
         return f"N{self.N}_na{self.na}_nb{self.nb}_G{self.G}_{self.precision}_w{n_walkers}"

@@ -235,7 +235,8 @@ static void ctx_free(afqmc_ctx* c) {
   prof_release(c->prof);
   tc_exchange_free(c);
   ws_free(c->ws);
-  void* ptrs[] = {c->d_L, c->d_Lh, c->d_trial, c->d_hhalf, c->d_Lbar, c->d_B, c->f_L, c->f_Lh, c->f_B, c->f_trial};
+  void* ptrs[] = {c->d_L,  c->d_Lh, c->d_trial, c->d_hhalf, c->d_Lbar, c->d_thT,
+                  c->d_B,  c->f_L,  c->f_Lh,    c->f_B,     c->f_trial};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free(c->h_evals);
@@ -292,8 +293,9 @@ static afqmc_status ctx_setup(afqmc_ctx* c, const double* h1, const double* L, c
         thT[(size_t)(off + j) * N + p] = v;
       }
   }
-  double *d_thT = nullptr, *d_LL = nullptr;
-  CK(cudaMalloc(&d_thT, thT.size() * sizeof(double)));
+  double* d_LL = nullptr;
+  CK(cudaMalloc(&c->d_thT, thT.size() * sizeof(double)));
+  double* d_thT = c->d_thT;
   CK(cudaMalloc(&d_LL, NN * sizeof(double)));
   CK(cudaMemcpyAsync(d_thT, thT.data(), thT.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   CK(launch_setup(c, s));
@@ -308,7 +310,6 @@ static afqmc_status ctx_setup(afqmc_ctx* c, const double* h1, const double* L, c
   CK(cudaMemcpyAsync(LL.data(), d_LL, NN * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaMemcpyAsync(Lbar.data(), c->d_Lbar, G * sizeof(double), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  cudaFree(d_thT);
   cudaFree(d_LL);
 
   // h'' and E_c' (mean-field shift as an operator constant)
@@ -567,6 +568,322 @@ static void batch_free(afqmc_batch* b) {
   delete b;
 }
 
+// ---------------------------------------------------------------- walk adjoint
+namespace {
+// Bump allocator over one device allocation (a dry run with base == nullptr
+// only counts the bytes).
+struct Arena {
+  char* base = nullptr;
+  size_t used = 0;
+  template <typename T>
+  T* take(size_t n) {
+    const size_t a = (used + 255) & ~(size_t)255;
+    used = a + n * sizeof(T);
+    return base ? reinterpret_cast<T*>(base + a) : nullptr;
+  }
+};
+
+struct AdjBufs {
+  double2 *ck_psi, *seg_psi, *run_psi, *P0, *Tb, *Ub, *psi2, *psi3, *pb, *p3, *p2, *p1, *thbar, *Abar, *cbar, *tbar,
+      *oinv3, *oinvk, *aR, *gLc, *Lhb, *Bbar, *part, *ys;
+  double *ck_W, *ck_lo, *seg_lo, *run_W, *run_lo, *Wfin, *mu_part, *ld3, *ldk, *omega, *ecoef, *mubar, *V, *lam, *Bs,
+      *T1, *M1, *hbar, *X, *D, *eloc, *emix;
+  uint32_t *ck_st, *run_st, *st_scr;
+  uint8_t* keep;
+  int skc, skb;  // split-K factors of the two long-K contractions
+};
+
+int pick_splitk(long long M, long long Nn, long long K, int cap) {
+  const long long tiles = ((M + 63) / 64) * ((Nn + 63) / 64);
+  int sk = 1;
+  while (sk < cap && tiles * sk < 4 * 152 && K / (2 * sk) >= 256) sk *= 2;
+  return sk;
+}
+
+GemmArgs gargs(int M, int Nn, int K, int batch, const void* A, long long sa_m, long long sa_k, long long sa_b,
+               const void* B, long long sb_n, long long sb_k, long long sb_b, void* C, long long sc_m, long long sc_n,
+               long long sc_b, double are = 1.0, double aim = 0.0) {
+  GemmArgs g{};
+  g.M = M; g.Nn = Nn; g.K = K; g.batch = batch;
+  g.A = A; g.sa_m = sa_m; g.sa_k = sa_k; g.sa_b = sa_b;
+  g.B = B; g.sb_n = sb_n; g.sb_k = sb_k; g.sb_b = sb_b;
+  g.C = C; g.sc_m = sc_m; g.sc_n = sc_n; g.sc_b = sc_b;
+  g.alpha_re = are; g.alpha_im = aim;
+  return g;
+}
+}  // namespace
+
+static void adj_carve(Arena& a, AdjBufs& b, const afqmc_ctx* c, int Nw, int K, int C, int nck) {
+  const size_t nw = (size_t)Nw, per = (size_t)c->nc * c->N, NN = (size_t)c->N * c->N, G = (size_t)c->G;
+  const size_t nmax = (size_t)(c->na > c->nb ? c->na : c->nb);
+  b.ck_psi = a.take<double2>((size_t)nck * nw * per);
+  b.ck_W = a.take<double>((size_t)nck * nw);
+  b.ck_lo = a.take<double>((size_t)nck * nw * 2);
+  b.ck_st = a.take<uint32_t>((size_t)nck * nw);
+  b.seg_psi = a.take<double2>((size_t)(C + 1) * nw * per);
+  b.seg_lo = a.take<double>((size_t)(C + 1) * nw * 2);
+  b.run_psi = a.take<double2>(nw * per);
+  b.run_W = a.take<double>(nw);
+  b.run_lo = a.take<double>(nw * 2);
+  b.run_st = a.take<uint32_t>(nw);
+  b.st_scr = a.take<uint32_t>(nw);
+  b.Wfin = a.take<double>(nw);
+  b.P0 = a.take<double2>(nw * per);
+  b.Tb = a.take<double2>(nw * (K + 1) * per);
+  b.Ub = a.take<double2>(nw * K * per);
+  b.psi2 = a.take<double2>(nw * per);
+  b.psi3 = a.take<double2>(nw * per);
+  b.pb = a.take<double2>(nw * per);
+  b.p3 = a.take<double2>(nw * per);
+  b.p2 = a.take<double2>(nw * per);
+  b.p1 = a.take<double2>(nw * per);
+  b.thbar = a.take<double2>(nw * per);
+  b.Abar = a.take<double2>(nw * NN);
+  b.cbar = a.take<double2>(nw * G);
+  b.tbar = a.take<double2>(nw * G);
+  b.keep = a.take<uint8_t>(nw * G);
+  b.mu_part = a.take<double>(nw * G);
+  b.oinv3 = a.take<double2>(nw * 2 * nmax * nmax);
+  b.oinvk = a.take<double2>(nw * 2 * nmax * nmax);
+  b.ld3 = a.take<double>(nw * 4);
+  b.ldk = a.take<double>(nw * 4);
+  b.aR = a.take<double2>(nw);
+  b.omega = a.take<double>(nw);
+  b.ecoef = a.take<double>(nw);
+  b.gLc = a.take<double2>(G * NN);
+  b.Lhb = a.take<double2>(G * per);
+  b.Bbar = a.take<double2>(NN);
+  b.mubar = a.take<double>(G);
+  const size_t pc = (size_t)b.skc * G * nw, pbb = (size_t)b.skb * NN;
+  b.part = a.take<double2>(pc > pbb ? pc : pbb);
+  b.ys = a.take<double2>(per + G * per);
+  b.V = a.take<double>(NN);
+  b.lam = a.take<double>((size_t)c->N);
+  b.Bs = a.take<double>(NN);
+  b.T1 = a.take<double>(NN);
+  b.M1 = a.take<double>(NN);
+  b.hbar = a.take<double>(NN);
+  b.X = a.take<double>(G * NN);
+  b.D = a.take<double>(NN);
+  b.eloc = a.take<double>(nw * 2);
+  b.emix = a.take<double>(4);
+}
+
+// One reverse step k of the walk: recompute Theta_k, f, c, A, the Taylor terms
+// and Psi3 from the stored Psi_k, then pull the adjoint Psi_bar_{k+1} (in b.pb)
+// back to Psi_bar_k (in b.pb) and accumulate the parameter adjoints.
+static afqmc_status adj_step(afqmc_ctx* c, const AdjBufs& b, int Nw, const double* x, const double2* psik,
+                             const double* lok, const double2* psinext, int qr, int K, double tau) {
+  cudaStream_t s = c->stream;
+  Workspace& ws = c->ws;
+  const int N = c->N, nc = c->nc, G = c->G;
+  const size_t per = (size_t)nc * N, NN = (size_t)N * N, cs = sizeof(double2);
+  const long long perl = (long long)per, NNl = (long long)NN;
+  const double st = std::sqrt(tau);
+  uint64_t nl = 0;
+  auto gm = [&](const GemmArgs& g, bool ac, int epi) -> cudaError_t {
+    nl += (g.splitk > 1 && g.part && g.batch == 1 && epi != EPI_STORE_ADD) ? 2 : 1;
+    return gemm<double>(g, ac, epi, s);
+  };
+  double2* theta = static_cast<double2*>(ws.theta);
+  // forward quantities of step k (same kernels as the step, so the kept
+  // force-bias components are the forward's)
+  CKW(adj_sanitize(psik, b.P0, b.Wfin, c->d_trial, per, Nw, s), "adjoint: sanitise");
+  CKW(launch_overlap<double>(c, Nw, b.P0, ws.theta, ws.logdet, b.st_scr, s), "adjoint: overlap");
+  CKW(gm(site_args<double>(c, SITE_FORCEBIAS, Nw, st, ws.theta, ws.t), false, EPI_STORE), "adjoint: force bias");
+  CKW(launch_bias_finalize<double>(c, Nw, x, st, s, b.keep), "adjoint: bias finalise");
+  CKW(gm(site_args<double>(c, SITE_FIELD, Nw, st, ws.c, ws.A), false, EPI_STORE), "adjoint: field");
+  nl += 3;
+  const long long tstride = (long long)(K + 1) * perl, ustride = (long long)K * perl;
+  CKW(gm(gargs(N, nc, N, Nw, c->d_B, N, 1, 0, b.P0, N, 1, perl, b.Tb, 1, N, tstride), false, EPI_STORE),
+      "adjoint: half step");
+  GemmArgs ga = site_args<double>(c, SITE_EXPM, Nw, st, nullptr, nullptr);
+  ga.sb_b = tstride;
+  ga.sc_b = tstride;
+  for (int j = 1; j <= K; ++j) {
+    ga.B = b.Tb + (size_t)(j - 1) * per;
+    ga.C = b.Tb + (size_t)j * per;
+    ga.alpha_re = 1.0 / j;
+    ga.alpha_im = 0.0;
+    CKW(gm(ga, true, EPI_STORE), "adjoint: Taylor term");
+  }
+  CKW(adj_sum_terms(b.Tb, b.psi2, K + 1, per, Nw, s), "adjoint: Taylor sum");
+  CKW(gm(site_args<double>(c, SITE_HALFSTEP, Nw, st, b.psi2, b.psi3), false, EPI_STORE), "adjoint: half step");
+  // overlap ratio and weight: Psi3_bar
+  CKW(adj_lu(c, Nw, b.psi3, b.oinv3, b.ld3, s), "adjoint: new overlap");
+  CKW(adj_ratio_coef(Nw, b.Wfin, b.omega, b.ld3, lok, ws.scal, b.aR, st, s), "adjoint: ratio coefficient");
+  CKW(adj_ratio(c, Nw, b.pb, psinext, b.oinv3, b.aR, b.Wfin, b.p3, qr, s), "adjoint: ratio");
+  nl += 4;
+  // second half step: Psi2_bar = B Psi3_bar, Bbar += Psi3_bar Psi2^T
+  CKW(gm(site_args<double>(c, SITE_HALFSTEP, Nw, st, b.p3, b.p2), false, EPI_STORE), "adjoint: half step");
+  GemmArgs gb = gargs(N, N, Nw * nc, 1, b.p3, 1, N, 0, b.psi2, 1, N, 0, b.Bbar, N, 1, 0);
+  gb.splitk = b.skb;
+  gb.part = b.part;
+  CKW(gm(gb, true, EPI_ACC), "adjoint: B adjoint");
+  // Taylor action: U_j = T_bar_j / j in Ub slot j-1, T_bar_{j-1} = Psi2_bar + A U_j
+  CKW(adj_scale_copy(b.p2, per, b.Ub + (size_t)(K - 1) * per, (size_t)K * per, 1.0 / K, per, Nw, s),
+      "adjoint: Taylor seed");
+  ++nl;
+  GemmArgs gu = site_args<double>(c, SITE_EXPM, Nw, st, nullptr, nullptr);
+  gu.sb_b = ustride;
+  gu.sc_b = ustride;
+  for (int j = K; j >= 2; --j) {
+    CKW(adj_scale_copy(b.p2, per, b.Ub + (size_t)(j - 2) * per, (size_t)K * per, 1.0 / (j - 1), per, Nw, s),
+        "adjoint: Taylor copy");
+    gu.B = b.Ub + (size_t)(j - 1) * per;
+    gu.C = b.Ub + (size_t)(j - 2) * per;
+    gu.alpha_re = 1.0 / (j - 1);
+    gu.alpha_im = 0.0;
+    CKW(gm(gu, true, EPI_ACC), "adjoint: Taylor adjoint");
+    ++nl;
+  }
+  CKW(cudaMemcpyAsync(b.p1, b.p2, (size_t)Nw * per * cs, cudaMemcpyDeviceToDevice, s), "adjoint: copy");
+  GemmArgs g1 = site_args<double>(c, SITE_EXPM, Nw, st, b.Ub, b.p1);
+  g1.sb_b = ustride;
+  CKW(gm(g1, true, EPI_ACC), "adjoint: Taylor adjoint");
+  // A_bar[w] = sum_j U_j T_{j-1}^T
+  CKW(gm(gargs(N, N, K * nc, Nw, b.Ub, 1, N, ustride, b.Tb, 1, N, tstride, b.Abar, N, 1, NNl), true, EPI_STORE),
+      "adjoint: A adjoint");
+  // A = i sqrt(tau) sum_g c_g L_g: c_bar = i sqrt(tau) <L_g, A_bar>, L_bar_g += i sqrt(tau) sum_w c_wg A_bar_w
+  GemmArgs gc = gargs(G, Nw, (int)NN, 1, c->d_L, NNl, 1, 0, b.Abar, NNl, 1, 0, b.cbar, 1, G, 0, 0.0, st);
+  gc.splitk = b.skc;
+  gc.part = b.part;
+  CKW(gm(gc, false, EPI_STORE), "adjoint: c adjoint");
+  CKW(gm(gargs(G, (int)NN, Nw, 1, ws.c, 1, G, 0, b.Abar, 1, NNl, 0, b.gLc, NNl, 1, 0, 0.0, st), true, EPI_ACC),
+      "adjoint: L adjoint (field)");
+  // force bias and scalar factor
+  CKW(adj_force(c, Nw, b.cbar, static_cast<const double2*>(ws.c), b.keep, b.aR, b.omega, b.tbar, b.mu_part, b.mubar,
+                st, tau, s),
+      "adjoint: force bias");
+  nl += 2;
+  // t_g = sum tr(Lh_g Theta): Theta_bar = sum_g t_bar_g Lh_g^T, Lh_bar_g += sum_w t_bar_wg Theta_w
+  CKW(gm(gargs((int)per, Nw, G, 1, c->d_Lh, 1, perl, 0, b.tbar, G, 1, 0, b.thbar, 1, perl, 0), false, EPI_STORE),
+      "adjoint: Theta adjoint");
+  CKW(gm(gargs(G, (int)per, Nw, 1, b.tbar, 1, G, 0, ws.theta, 1, perl, 0, b.Lhb, perl, 1, 0), true, EPI_ACC),
+      "adjoint: Lh adjoint");
+  // first half step and Theta = Psi O^{-1}: Psi_bar_k
+  CKW(gm(site_args<double>(c, SITE_HALFSTEP, Nw, st, b.p1, b.pb), false, EPI_STORE), "adjoint: half step");
+  GemmArgs gb2 = gargs(N, N, Nw * nc, 1, b.p1, 1, N, 0, b.P0, 1, N, 0, b.Bbar, N, 1, 0);
+  gb2.splitk = b.skb;
+  gb2.part = b.part;
+  CKW(gm(gb2, true, EPI_ACC), "adjoint: B adjoint");
+  CKW(adj_lu(c, Nw, b.P0, b.oinvk, b.ldk, s), "adjoint: overlap inverse");
+  CKW(adj_theta(c, Nw, b.thbar, theta, b.oinvk, b.aR, b.Wfin, b.pb, s), "adjoint: Theta pull-back");
+  nl += 2;
+  c->launches += nl;
+  return AFQMC_OK;
+}
+
+static afqmc_status walk_backward_run(afqmc_ctx* c, const afqmc_walkers* w0, const double* fields,
+                                      const afqmc_walk_adjoint_params* p, double* J_out, double* grad_h1,
+                                      double* grad_L, void* grad_psi0, const AdjBufs& b) {
+  cudaStream_t s = c->stream;
+  const int Nw = w0->n_walkers, N = c->N, nc = c->nc, G = c->G, K = p->order, C = p->ckpt_every, n = p->n_steps;
+  const size_t per = (size_t)nc * N, NN = (size_t)N * N, cs = sizeof(double2), nw = (size_t)Nw;
+  const size_t fstride = nw * G;
+  const int nck = (n + C - 1) / C;
+  const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
+  afqmc_walkers run{};
+  run.n_walkers = Nw;
+  run.psi = b.run_psi;
+  run.weight = b.run_W;
+  run.logovl = b.run_lo;
+  run.status = b.run_st;
+  auto copy_state = [&](void* dp, double* dW, double* dl, uint32_t* ds, const void* sp, const double* sW,
+                        const double* sl, const uint32_t* ss) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(dp, sp, nw * per * cs, dd, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dW, sW, nw * sizeof(double), dd, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dl, sl, nw * 2 * sizeof(double), dd, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ds, ss, nw * sizeof(uint32_t), dd, s);
+    return e;
+  };
+  afqmc_step_params sp{};
+  sp.tau = p->tau;
+  sp.e0 = p->e0;
+  sp.propagator = AFQMC_SPLIT2;
+  sp.expm = AFQMC_EXPM_TAYLOR;
+  sp.order = K;
+  sp.measure = 0;
+  auto qr_at = [&](int k) { return (p->reortho_every > 0 && (k + 1) % p->reortho_every == 0) ? 1 : 0; };
+
+  // forward walk with checkpoints, then J
+  CKW(copy_state(run.psi, run.weight, run.logovl, run.status, w0->psi, w0->weight, w0->logovl, w0->status),
+      "adjoint: copy walkers");
+  for (int k = 0; k < n; ++k) {
+    if (k % C == 0) {
+      const size_t sl = (size_t)(k / C);
+      CKW(copy_state(b.ck_psi + sl * nw * per, b.ck_W + sl * nw, b.ck_lo + sl * nw * 2, b.ck_st + sl * nw, run.psi,
+                     run.weight, run.logovl, run.status),
+          "adjoint: checkpoint");
+    }
+    sp.reortho = qr_at(k);
+    afqmc_status rc = run_step<double>(c, &run, fields + (size_t)k * fstride, &sp, nullptr, nullptr);
+    if (rc != AFQMC_OK) return rc;
+  }
+  afqmc_status rc = run_energy<double>(c, &run, p->e0, p->tau, b.eloc, b.emix);
+  if (rc != AFQMC_OK) return rc;
+  CKW(cudaMemcpyAsync(b.Wfin, run.weight, nw * sizeof(double), dd, s), "adjoint: copy");
+  if (J_out) CKW(cudaMemcpyAsync(J_out, b.emix, 4 * sizeof(double), dd, s), "adjoint: copy");
+
+  // seeds: E_L part of the parameter gradients and Psi_bar_n
+  const int ne = c->na + c->nb;
+  const double dE = 0.5 * std::sqrt(ne / p->tau) + std::sqrt(ne * p->tau);
+  const double st = std::sqrt(p->tau);
+  CKW(adj_seed_coef(Nw, b.Wfin, c->ws.ecap, b.eloc, b.emix, b.omega, b.ecoef, p->e0, dE, p->dJ, s), "adjoint: seed");
+  CKW(launch_energy_backward(c, Nw, b.Wfin, b.eloc, p->e0, p->tau, p->dJ, grad_h1, grad_L, b.ys, s),
+      "adjoint: energy");
+  CKW(gemm<double>(site_args<double>(c, SITE_FORCEBIAS, Nw, st, c->ws.theta, c->ws.t), false, EPI_STORE, s),
+      "adjoint: force bias");
+  CKW(adj_eloc_seed(c, Nw, static_cast<const double2*>(c->ws.theta), static_cast<const double2*>(c->ws.t), b.ecoef,
+                    b.thbar, s),
+      "adjoint: energy seed");
+  CKW(adj_sanitize(b.run_psi, b.P0, b.Wfin, c->d_trial, per, Nw, s), "adjoint: sanitise");
+  CKW(adj_lu(c, Nw, b.P0, b.oinvk, b.ldk, s), "adjoint: overlap inverse");
+  CKW(cudaMemsetAsync(b.pb, 0, nw * per * cs, s), "adjoint: memset");
+  CKW(adj_theta(c, Nw, b.thbar, static_cast<const double2*>(c->ws.theta), b.oinvk, nullptr, b.Wfin, b.pb, s),
+      "adjoint: Theta pull-back");
+  c->launches += 1 + 5 + 2 + 1 + 1 + 1 + 1;
+  CKW(cudaMemsetAsync(b.gLc, 0, (size_t)G * NN * cs, s), "adjoint: memset");
+  CKW(cudaMemsetAsync(b.Lhb, 0, (size_t)G * per * cs, s), "adjoint: memset");
+  CKW(cudaMemsetAsync(b.Bbar, 0, NN * cs, s), "adjoint: memset");
+  CKW(cudaMemsetAsync(b.mubar, 0, (size_t)G * sizeof(double), s), "adjoint: memset");
+
+  // segments in reverse: recompute the states of the segment, then step back
+  for (int sg = nck - 1; sg >= 0; --sg) {
+    const int k0 = sg * C, k1 = (k0 + C < n) ? k0 + C : n;
+    const size_t sl = (size_t)sg;
+    CKW(copy_state(run.psi, run.weight, run.logovl, run.status, b.ck_psi + sl * nw * per, b.ck_W + sl * nw,
+                   b.ck_lo + sl * nw * 2, b.ck_st + sl * nw),
+        "adjoint: restore");
+    for (int k = k0; k < k1; ++k) {
+      const size_t i = (size_t)(k - k0);
+      CKW(cudaMemcpyAsync(b.seg_psi + i * nw * per, run.psi, nw * per * cs, dd, s), "adjoint: store");
+      CKW(cudaMemcpyAsync(b.seg_lo + i * nw * 2, run.logovl, nw * 2 * sizeof(double), dd, s), "adjoint: store");
+      sp.reortho = qr_at(k);
+      rc = run_step<double>(c, &run, fields + (size_t)k * fstride, &sp, nullptr, nullptr);
+      if (rc != AFQMC_OK) return rc;
+    }
+    CKW(cudaMemcpyAsync(b.seg_psi + (size_t)(k1 - k0) * nw * per, run.psi, nw * per * cs, dd, s), "adjoint: store");
+    for (int k = k1 - 1; k >= k0; --k) {
+      const size_t i = (size_t)(k - k0);
+      rc = adj_step(c, b, Nw, fields + (size_t)k * fstride, b.seg_psi + i * nw * per, b.seg_lo + i * nw * 2,
+                    b.seg_psi + (i + 1) * nw * per, qr_at(k), K, p->tau);
+      if (rc != AFQMC_OK) return rc;
+    }
+  }
+  if (grad_psi0) CKW(cudaMemcpyAsync(grad_psi0, b.pb, nw * per * cs, dd, s), "adjoint: copy");
+
+  // e^{-tau h''/2} through the eigendecomposition, then the final gradients
+  CKW(cudaMemcpyAsync(b.V, c->h_evecs, NN * sizeof(double), cudaMemcpyHostToDevice, s), "adjoint: upload");
+  CKW(cudaMemcpyAsync(b.lam, c->h_evals, (size_t)N * sizeof(double), cudaMemcpyHostToDevice, s), "adjoint: upload");
+  int nfin = 0;
+  CKW(adj_finish(c, b.Bbar, b.V, b.lam, p->tau, b.Bs, b.T1, b.M1, b.hbar, b.X, b.D, b.gLc, b.Lhb, b.mubar, grad_h1,
+                 grad_L, &nfin, s),
+      "adjoint: final");
+  c->launches += nfin;
+  return AFQMC_OK;
+}
+
 // ---------------------------------------------------------------- ABI
 extern "C" {
 
@@ -759,6 +1076,62 @@ afqmc_status afqmc_energy_backward(afqmc_ctx* c, const afqmc_walkers* w, double 
   cudaFree(ys);
   if (e != cudaSuccess) return cuda_fail(e, "energy backward");
   c->launches += 5;
+  return AFQMC_OK;
+}
+
+afqmc_status afqmc_walk_backward(afqmc_ctx* c, const afqmc_walkers* w0, const double* fields,
+                                 const afqmc_walk_adjoint_params* p, double* J_out, double* grad_h1, double* grad_L,
+                                 void* grad_psi0) {
+  afqmc_status st = check_walkers(c, w0);
+  if (st != AFQMC_OK) return st;
+  if (!p || !grad_h1 || !grad_L || ((uintptr_t)grad_h1) % 8 || ((uintptr_t)grad_L) % 8) return AFQMC_EINVAL;
+  if ((J_out && ((uintptr_t)J_out) % 8) || (grad_psi0 && ((uintptr_t)grad_psi0) % 16)) return AFQMC_EINVAL;
+  if (!std::isfinite(p->tau) || !std::isfinite(p->e0) || !std::isfinite(p->dJ)) return AFQMC_EDOM;
+  if (!(p->tau > 0.0) || p->n_steps < 1 || p->ckpt_every < 1 || p->reortho_every < 0) return AFQMC_EINVAL;
+  if (p->order < 1 || p->order > 32) return AFQMC_ENOTSUP;
+  if (c->prec != AFQMC_FP64) return AFQMC_ENOTSUP;
+  const int nmax = c->na > c->nb ? c->na : c->nb;
+  if (nmax > 64 || w0->n_walkers > 65535) return AFQMC_ENOTSUP;
+  if ((size_t)(nmax * nmax + nmax * c->N) * 16 > (size_t)max_dyn_smem() - 1024) return AFQMC_ENOTSUP;
+  const int Nw = w0->n_walkers;
+  if (Nw > 0 && !fields) return AFQMC_EINVAL;
+  const size_t NN = (size_t)c->N * c->N;
+  if (Nw == 0) {
+    CK(cudaMemsetAsync(grad_h1, 0, NN * sizeof(double), c->stream));
+    CK(cudaMemsetAsync(grad_L, 0, (size_t)c->G * NN * sizeof(double), c->stream));
+    if (J_out) CK(cudaMemsetAsync(J_out, 0, 4 * sizeof(double), c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return AFQMC_OK;
+  }
+  if (p->tau != c->tau) {
+    st = afqmc_set_tau(c, p->tau);
+    if (st != AFQMC_OK) return st;
+  }
+  st = ws_ensure(c, Nw, c->ws.kmax);
+  if (st != AFQMC_OK) return st;
+  const int C = p->ckpt_every < p->n_steps ? p->ckpt_every : p->n_steps;
+  const int nck = (p->n_steps + C - 1) / C;
+  afqmc_walk_adjoint_params q = *p;
+  q.ckpt_every = C;
+  AdjBufs b{};
+  b.skc = pick_splitk(c->G, Nw, (long long)NN, 32);
+  b.skb = pick_splitk(c->N, c->N, (long long)Nw * c->nc, 64);
+  Arena a;
+  adj_carve(a, b, c, Nw, p->order, C, nck);
+  CK(cudaStreamSynchronize(c->stream));
+  char* base = nullptr;
+  cudaError_t e = cudaMalloc(&base, a.used);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, "adjoint workspace");
+  }
+  a = Arena{base, 0};
+  adj_carve(a, b, c, Nw, p->order, C, nck);
+  st = walk_backward_run(c, w0, fields, &q, J_out, grad_h1, grad_L, grad_psi0, b);
+  e = cudaStreamSynchronize(c->stream);
+  cudaFree(base);
+  if (st != AFQMC_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint");
   return AFQMC_OK;
 }
 

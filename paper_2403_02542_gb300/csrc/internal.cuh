@@ -47,7 +47,7 @@ __device__ __forceinline__ void st(float2* p, cd v) { *p = make_float2((float)v.
 // ---------------------------------------------------------------- GEMM
 // C[b][m][n] = alpha * sum_k A[b][m][k] * B[b][n][k]  (strides in elements),
 // A real or complex, B complex; the epilogue mode decides what is stored.
-enum GemmEpi { EPI_STORE = 0, EPI_STORE_ADD = 1 };
+enum GemmEpi { EPI_STORE = 0, EPI_STORE_ADD = 1, EPI_ACC = 2 };  // EPI_ACC: C += result
 struct GemmArgs {
   int M, Nn, K, batch;
   const void* A;
@@ -58,11 +58,12 @@ struct GemmArgs {
   long long sc_m, sc_n, sc_b;
   void* D;  // EPI_STORE_ADD: D += result (same strides as C)
   double alpha_re, alpha_im;
-  // split-K (batch == 1, EPI_STORE): `splitk` K-ranges write partial tiles to
+  // split-K (batch == 1, EPI_STORE or EPI_ACC): `splitk` K-ranges write partial tiles to
   // `part` [splitk][M][Nn] (complex, R), summed in fixed order afterwards
   int splitk;
   void* part;
   int variant;  // output tile: 0 = 64x64, 1 = 128x32, 2 = 32x128, 3 = 64x32, 4 = per-walker A*V
+  int accum;    // set by gemm() for EPI_ACC: the epilogue adds to C instead of storing
 };
 constexpr int GEMM_VARIANTS = 5;
 // GEMM call sites of the step, each with its own tuned tile variant
@@ -147,6 +148,7 @@ struct afqmc_ctx {
   double* d_trial = nullptr;  // [nc][N]
   double* d_hhalf = nullptr;  // [nc][N]     sum_p trial[j][p] h1[p][q]
   double* d_Lbar = nullptr;   // [G]
+  double* d_thT = nullptr;    // [nc][N]     Theta_T = trial_s (trial_s^T trial_s)^{-1} per spin
   double* d_B = nullptr;      // [N][N]
   // FP32 copies for mixed contexts
   float* f_L = nullptr;
@@ -196,7 +198,7 @@ cudaError_t launch_overlap(const afqmc_ctx* c, int Nw, const void* psi, void* th
                            double* logdet, uint32_t* status, cudaStream_t s);
 template <typename R>
 cudaError_t launch_bias_finalize(const afqmc_ctx* c, int Nw, const double* x, double sqrt_tau,
-                                 cudaStream_t s);
+                                 cudaStream_t s, uint8_t* keep = nullptr);  // keep[w][g]: 1 = f_g kept
 template <typename R>
 cudaError_t launch_normA(const afqmc_ctx* c, int Nw, cudaStream_t s);
 template <typename R>
@@ -230,6 +232,33 @@ cudaError_t launch_comb(afqmc_ctx* c, const afqmc_walkers* w, double u, int* ind
 cudaError_t launch_energy_backward(afqmc_ctx* c, int Nw, const double* weight, const double* e_loc, double e0,
                                    double tau, double dJ, double* grad_h1, double* grad_L, double2* yscratch,
                                    cudaStream_t s);
+
+// adjoint of the fixed-field walk (k_walk_adjoint.cu)
+cudaError_t adj_sanitize(const double2* src, double2* dst, const double* wfin, const double* trial, size_t per,
+                         int Nw, cudaStream_t s);
+cudaError_t adj_sum_terms(const double2* T, double2* out, int K1, size_t per, int Nw, cudaStream_t s);
+cudaError_t adj_scale_copy(const double2* src, size_t sstride, double2* dst, size_t dstride, double sc, size_t per,
+                           int Nw, cudaStream_t s);
+size_t adj_lu_smem(int nmax);
+size_t adj_small_smem(int nmax);
+cudaError_t adj_lu(const afqmc_ctx* c, int Nw, const double2* psi, double2* oinv, double* logdet, cudaStream_t s);
+cudaError_t adj_ratio_coef(int Nw, const double* wfin, const double* omega, const double* ld3, const double* logovl,
+                           const double* scal, double2* aR, double sqrt_tau, cudaStream_t s);
+cudaError_t adj_ratio(const afqmc_ctx* c, int Nw, const double2* pnext, const double2* psinext, const double2* oinv3,
+                      const double2* aR, const double* wfin, double2* p3, int qr, cudaStream_t s);
+cudaError_t adj_force(const afqmc_ctx* c, int Nw, const double2* cbar, const double2* cc, const uint8_t* keep,
+                      const double2* aR, const double* omega, double2* tbar, double* mu_part, double* mubar,
+                      double sqrt_tau, double tau, cudaStream_t s);
+cudaError_t adj_theta(const afqmc_ctx* c, int Nw, const double2* thbar, const double2* theta, const double2* oinv,
+                      const double2* aR, const double* wfin, double2* pbar, cudaStream_t s);
+cudaError_t adj_seed_coef(int Nw, const double* wfin, const double* ecap, const double* e_loc, const double* emix,
+                          double* omega, double* ecoef, double e0, double dE, double dJ, cudaStream_t s);
+cudaError_t adj_eloc_seed(const afqmc_ctx* c, int Nw, const double2* theta, const double2* t, const double* ecoef,
+                          double2* thbar, cudaStream_t s);
+cudaError_t adj_finish(const afqmc_ctx* c, const double2* Bbar, const double* V, const double* lam, double tau,
+                       double* Bs, double* T1, double* M1, double* hbar, double* X, double* D, const double2* gLc,
+                       const double2* Lhb, double* mubar, double* grad_h1, double* grad_L, int* n_launch,
+                       cudaStream_t s);
 
 // tensor-core exchange (k_exchange_tc.cu)
 bool tc_exchange_plan(afqmc_ctx* c);

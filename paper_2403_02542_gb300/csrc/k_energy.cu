@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(256) bias_finalize_kernel(const typename C2<R>
                                                             const double* __restrict__ x,
                                                             const double* __restrict__ Lbar,
                                                             typename C2<R>::t* __restrict__ cout, double* scal,
-                                                            int G, double sqrt_tau) {
+                                                            uint8_t* __restrict__ keep, int G, double sqrt_tau) {
   __shared__ double sh[8 * 5];
   const int w = blockIdx.x;
   double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // logI re, im, cl re, im, nfcap
@@ -61,10 +61,12 @@ __global__ void __launch_bounds__(256) bias_finalize_kernel(const typename C2<R>
     const double lb = Lbar[g];
     // f = -i s (t - Lbar)
     cd f = mk(sqrt_tau * tg.im, -sqrt_tau * (tg.re - lb));
-    if (!(sqrt(abs2(f)) < 1.0)) {
+    const bool kept = sqrt(abs2(f)) < 1.0;
+    if (!kept) {
       f = mk(0.0, 0.0);
       v[4] += 1.0;
     }
+    if (keep) keep[(size_t)w * G + g] = kept ? 1 : 0;
     const double xg = x[(size_t)w * G + g];
     const cd c = mk(xg - f.re, -f.im);
     st(cout + (size_t)w * G + g, c);
@@ -374,9 +376,11 @@ inline int grid_for(size_t n) {
 
 // ---------------------------------------------------------------- wrappers
 template <typename R>
-cudaError_t launch_bias_finalize(const afqmc_ctx* c, int Nw, const double* x, double sqrt_tau, cudaStream_t s) {
+cudaError_t launch_bias_finalize(const afqmc_ctx* c, int Nw, const double* x, double sqrt_tau, cudaStream_t s,
+                                 uint8_t* keep) {
   bias_finalize_kernel<R><<<Nw, 256, 0, s>>>(static_cast<const typename C2<R>::t*>(c->ws.t), x, c->d_Lbar,
-                                             static_cast<typename C2<R>::t*>(c->ws.c), c->ws.scal, c->G, sqrt_tau);
+                                             static_cast<typename C2<R>::t*>(c->ws.c), c->ws.scal, keep, c->G,
+                                             sqrt_tau);
   return cudaGetLastError();
 }
 
@@ -505,7 +509,7 @@ cudaError_t launch_to_float(const double* a, float* b, size_t n, cudaStream_t s)
 }
 
 #define AFQ_INST(R)                                                                                         \
-  template cudaError_t launch_bias_finalize<R>(const afqmc_ctx*, int, const double*, double, cudaStream_t); \
+  template cudaError_t launch_bias_finalize<R>(const afqmc_ctx*, int, const double*, double, cudaStream_t, uint8_t*); \
   template cudaError_t launch_normA<R>(const afqmc_ctx*, int, cudaStream_t);                                \
   template cudaError_t launch_weights<R>(const afqmc_ctx*, const afqmc_walkers*, double, double, cudaStream_t); \
   template cudaError_t launch_commit<R>(const afqmc_ctx*, const afqmc_walkers*, int, cudaStream_t);         \

@@ -140,7 +140,14 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g) {
       v.x = alr * accr[i][j] - ali * acci[i][j];
       v.y = alr * acci[i][j] + ali * accr[i][j];
       const long long off = (long long)m * g.sc_m + (long long)n * g.sc_n;
-      C[off] = v;
+      if (g.accum) {
+        cplx o = C[off];
+        o.x += v.x;
+        o.y += v.y;
+        C[off] = o;
+      } else {
+        C[off] = v;
+      }
       if (D) {
         cplx d = D[off];
         d.x += v.x;
@@ -224,7 +231,14 @@ __global__ void __launch_bounds__(256) walker_gemm_kernel(GemmArgs g) {
       v.x = alr * accr[i][t] - ali * acci[i][t];
       v.y = alr * acci[i][t] + ali * accr[i][t];
       const size_t off = (size_t)m + (size_t)j * g.sc_n;
-      C[off] = v;
+      if (g.accum) {
+        cplx o = C[off];
+        o.x += v.x;
+        o.y += v.y;
+        C[off] = o;
+      } else {
+        C[off] = v;
+      }
       if (D) {
         cplx d = D[off];
         d.x += v.x;
@@ -248,7 +262,7 @@ bool walker_gemm_ok(const GemmArgs& g, bool a_complex) {
   return a_complex && g.batch >= 1 && g.sa_k == 1 && g.sb_k == 1 && g.sc_m == 1 && g.Nn <= 96 && g.batch <= 65535;
 }
 
-// Sum the split-K partials in fixed order, scale by alpha, store to C.
+// Sum the split-K partials in fixed order, scale by alpha, store to (or add to) C.
 template <typename R>
 __global__ void splitk_reduce_kernel(GemmArgs g) {
   typedef typename C2<R>::t cplx;
@@ -266,7 +280,13 @@ __global__ void splitk_reduce_kernel(GemmArgs g) {
     cplx o;
     o.x = (R)g.alpha_re * sr - (R)g.alpha_im * si;
     o.y = (R)g.alpha_re * si + (R)g.alpha_im * sr;
-    C[(long long)m * g.sc_m + (long long)n * g.sc_n] = o;
+    cplx* dst = C + (long long)m * g.sc_m + (long long)n * g.sc_n;
+    if (g.accum) {
+      const cplx prev = *dst;
+      o.x += prev.x;
+      o.y += prev.y;
+    }
+    *dst = o;
   }
 }
 
@@ -296,7 +316,8 @@ cudaError_t gemm(const GemmArgs& a, bool a_complex, int epi, cudaStream_t s) {
   if (g.variant < 0 || g.variant >= GEMM_VARIANTS) g.variant = 0;
   if (g.variant == 4 && (a.splitk > 1 || !walker_gemm_ok(g, a_complex))) g.variant = 0;
   if (epi != EPI_STORE_ADD) g.D = nullptr;
-  if (g.splitk > 1 && g.part && g.batch == 1 && epi == EPI_STORE) {
+  g.accum = epi == EPI_ACC ? 1 : 0;
+  if (g.splitk > 1 && g.part && g.batch == 1 && epi != EPI_STORE_ADD) {
     cudaError_t e = a_complex ? gemm_variant<R, true>(g, g.splitk, s) : gemm_variant<R, false>(g, g.splitk, s);
     if (e != cudaSuccess) return e;
     const size_t MN = (size_t)a.M * a.Nn;

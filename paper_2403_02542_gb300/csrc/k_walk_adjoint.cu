@@ -1,0 +1,706 @@
+// Reverse-mode kernels of the fixed-field walk (adjoint of the Split-2 step
+// with the Taylor exponential, Sec. III.B and Eq. taylor; the paper has no
+// gradients).
+//
+// The objective J = E_n is real; every non-holomorphic piece of the forward
+// walk is a real part, an imaginary part or a threshold:
+//   log W_{k+1} = log W_k + Re(log R_k + log I_k) + tau e0 + log cos Im log R_k
+//   J = sum_w W_n Ebar_L / sum W,  Ebar_L = clamp(Re E_L)
+// With the thresholds held fixed, dJ = Re dF for the holomorphic function
+//   F = sum_{w,k} a_R,wk log R_wk + a_I,w log I_wk + sum_w e_w E_L,w
+// with a_R = omega (1 + i tan dtheta), a_I = omega, omega_w = W_w (Ebar_w - J)
+// / sum W and e_w = W_w / sum W inside the window.  The adjoint of every
+// complex intermediate z is therefore the plain holomorphic derivative
+// dF/dz (a linear map z' = M z pulls back with M^T, no conjugation), and the
+// gradient with respect to a real parameter is the real part of its adjoint.
+//
+// Per step (walker w, spin s; Theta = Psi O^{-1}, O = trial_s^T Psi_s):
+//   d log det O / d Psi       = trial O^{-T}
+//   adjoint of Theta -> Psi    : Psi_bar += [Theta_bar - trial (Theta^T Theta_bar)] O^{-T}
+//   t_g = sum_s tr(Lh_gs Theta_s), f_g = -i sqrt(tau)(t_g - L_bar_g) (kept
+//   components), c_g = x_g - f_g, A = i sqrt(tau) sum_g c_g L_g,
+//   log s = -tau E_c' - i sqrt(tau) sum_g c_g L_bar_g, log I = sum_g x_g f_g - f_g^2/2.
+// All arithmetic is FP64.
+#include <math_constants.h>
+
+#include "internal.cuh"
+
+namespace afq {
+
+namespace {
+
+constexpr int AT = 256;
+
+inline int grid_for(size_t n) {
+  size_t b = (n + AT - 1) / AT;
+  return (int)(b > 152 * 32 ? 152 * 32 : (b == 0 ? 1 : b));
+}
+
+// (-i s) z
+__device__ __forceinline__ cd mul_mis(double s, cd z) { return mk(s * z.im, -s * z.re); }
+__device__ __forceinline__ cd ldc(const double2& v) { return mk(v.x, v.y); }
+
+// dst = src for walkers alive at the end of the walk, the trial otherwise
+// (dead walkers carry no adjoint; their stand-in state only keeps every
+// intermediate finite).
+__global__ void adj_sanitize_kernel(const double2* __restrict__ src, double2* __restrict__ dst,
+                                    const double* __restrict__ wfin, const double* __restrict__ trial, size_t per,
+                                    size_t total) {
+  for (size_t e = blockIdx.x * (size_t)AT + threadIdx.x; e < total; e += (size_t)gridDim.x * AT) {
+    const size_t w = e / per;
+    dst[e] = wfin[w] > 0.0 ? src[e] : make_double2(trial[e - w * per], 0.0);
+  }
+}
+
+// out[w] = sum_{j=0}^{K} T[w][j] in the order j = 0, 1, ..., K
+__global__ void adj_sum_terms_kernel(const double2* __restrict__ T, double2* __restrict__ out, int K1, size_t per,
+                                     size_t total) {
+  for (size_t e = blockIdx.x * (size_t)AT + threadIdx.x; e < total; e += (size_t)gridDim.x * AT) {
+    const size_t w = e / per, r = e - w * per;
+    const double2* t = T + w * K1 * per + r;
+    double sr = t[0].x, si = t[0].y;
+    for (int j = 1; j < K1; ++j) {
+      sr += t[(size_t)j * per].x;
+      si += t[(size_t)j * per].y;
+    }
+    out[e] = make_double2(sr, si);
+  }
+}
+
+// dst[w][r] = s * src[w][r] with per-walker strides
+__global__ void adj_scale_copy_kernel(const double2* __restrict__ src, size_t sstride, double2* __restrict__ dst,
+                                      size_t dstride, double s, size_t per, size_t total) {
+  for (size_t e = blockIdx.x * (size_t)AT + threadIdx.x; e < total; e += (size_t)gridDim.x * AT) {
+    const size_t w = e / per, r = e - w * per;
+    const double2 v = src[w * sstride + r];
+    dst[w * dstride + r] = make_double2(s * v.x, s * v.y);
+  }
+}
+
+// O = trial_s^T psi_s for one (walker, spin); Gauss-Jordan elimination with
+// partial pivoting gives O^{-1} ([i][j], row stride n, in a slot of nmax^2)
+// and log det O = sum_k log pivot_k + i pi (odd number of row swaps).
+// A zero pivot gives log det = NaN and O^{-1} = 0.
+__global__ void __launch_bounds__(AT) adj_lu_kernel(const double2* __restrict__ psi, const double* __restrict__ trial,
+                                                    double2* __restrict__ oinv, double* __restrict__ logdet, int N,
+                                                    int na, int nb, int nmax) {
+  extern __shared__ double2 sm_lu[];
+  const int w = blockIdx.x, spin = blockIdx.y;
+  const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
+  double* ldo = logdet + ((size_t)w * 2 + spin) * 2;
+  if (n == 0) {
+    if (threadIdx.x == 0) ldo[0] = ldo[1] = 0.0;
+    return;
+  }
+  const int n2 = 2 * n;
+  double2* M = sm_lu;       // [n][2n]  (O | I)
+  double2* fac = M + n * n2;  // [n]      column k before elimination
+  __shared__ int s_piv, s_sing, s_swaps;
+  __shared__ double s_lr, s_li;
+  __shared__ double2 s_pinv;
+  const double2* P = psi + (size_t)w * nc * N;
+  for (int e = threadIdx.x; e < n * n; e += AT) {
+    const int i = e / n, j = e - (e / n) * n;
+    const double* a = trial + (size_t)(off + i) * N;
+    const double2* b = P + (size_t)(off + j) * N;
+    double sr = 0.0, si = 0.0;
+    for (int q = 0; q < N; ++q) {
+      sr = fma(a[q], b[q].x, sr);
+      si = fma(a[q], b[q].y, si);
+    }
+    M[i * n2 + j] = make_double2(sr, si);
+    M[i * n2 + n + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+  }
+  if (threadIdx.x == 0) {
+    s_lr = s_li = 0.0;
+    s_sing = s_swaps = 0;
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (threadIdx.x == 0) {
+      int piv = k;
+      double best = -1.0;
+      for (int i = k; i < n; ++i) {
+        const double2 v = M[i * n2 + k];
+        const double a = v.x * v.x + v.y * v.y;
+        if (a > best) {
+          best = a;
+          piv = i;
+        }
+      }
+      s_piv = piv;
+      if (!(best > 0.0) || !isfinite(best)) {
+        s_sing = 1;
+      } else {
+        if (piv != k) s_swaps ^= 1;
+        const double2 u = M[piv * n2 + k];
+        s_lr += 0.5 * log(best);
+        s_li += atan2(u.y, u.x);
+      }
+    }
+    __syncthreads();
+    if (s_sing) break;
+    const int piv = s_piv;
+    if (piv != k)
+      for (int q = threadIdx.x; q < n2; q += AT) {
+        const double2 t = M[k * n2 + q];
+        M[k * n2 + q] = M[piv * n2 + q];
+        M[piv * n2 + q] = t;
+      }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const cd r = cdiv(mk(1.0, 0.0), ldc(M[k * n2 + k]));
+      s_pinv = make_double2(r.re, r.im);
+    }
+    for (int i = threadIdx.x; i < n; i += AT) fac[i] = M[i * n2 + k];
+    __syncthreads();
+    const cd pinv = ldc(s_pinv);
+    for (int q = threadIdx.x; q < n2; q += AT) {
+      const cd v = ldc(M[k * n2 + q]) * pinv;
+      M[k * n2 + q] = make_double2(v.re, v.im);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n2; e += AT) {
+      const int i = e / n2, q = e - (e / n2) * n2;
+      if (i == k) continue;
+      const cd v = ldc(M[i * n2 + q]) - ldc(fac[i]) * ldc(M[k * n2 + q]);
+      M[i * n2 + q] = make_double2(v.re, v.im);
+    }
+    __syncthreads();
+  }
+  double2* out = oinv + ((size_t)w * 2 + spin) * nmax * nmax;
+  const bool sing = s_sing != 0;
+  for (int e = threadIdx.x; e < n * n; e += AT) {
+    const int i = e / n, j = e - (e / n) * n;
+    out[i * n + j] = sing ? make_double2(0.0, 0.0) : M[i * n2 + n + j];
+  }
+  if (threadIdx.x == 0) {
+    ldo[0] = sing ? CUDART_NAN : s_lr;
+    ldo[1] = sing ? CUDART_NAN : s_li + (s_swaps ? CUDART_PI : 0.0);
+  }
+}
+
+// a_R = omega (1 + i tan dtheta) with dtheta = Im log R (Eq. theta): the
+// imaginary part of log det O' - logovl_k + log s; zero for dead walkers.
+__global__ void adj_ratio_coef_kernel(const double* __restrict__ wfin, const double* __restrict__ omega,
+                                      const double* __restrict__ ld3, const double* __restrict__ logovl,
+                                      const double* __restrict__ scal, double2* __restrict__ aR, double sqrt_tau,
+                                      int Nw) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= Nw) return;
+  if (!(wfin[w] > 0.0)) {
+    aR[w] = make_double2(0.0, 0.0);
+    return;
+  }
+  const double dth = ld3[w * 4 + 1] + ld3[w * 4 + 3] - logovl[2 * w + 1] - sqrt_tau * scal[(size_t)w * SC_COUNT + SC_CL_RE];
+  const double om = omega[w];
+  aR[w] = make_double2(om, om * tan(dth));
+}
+
+// Psi3_bar for one (walker, spin):
+//   no re-orthonormalisation: Psi3_bar = Psi'_bar + a_R trial O3^{-T}
+//   re-orthonormalised Psi' = Psi3 R^{-1} = Psi3 O3^{-1} O':
+//                             Psi3_bar = (Psi'_bar O'^T + a_R trial) O3^{-T}
+// with O' = trial^T Psi'.  Dead walkers get zero.
+__global__ void __launch_bounds__(AT) adj_ratio_kernel(const double2* __restrict__ pnext,
+                                                       const double2* __restrict__ psinext,
+                                                       const double* __restrict__ trial,
+                                                       const double2* __restrict__ oinv3,
+                                                       const double2* __restrict__ aR, const double* __restrict__ wfin,
+                                                       double2* __restrict__ p3, int N, int na, int nb, int nmax,
+                                                       int qr) {
+  extern __shared__ double2 sm_ra[];
+  const int w = blockIdx.x, spin = blockIdx.y;
+  const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
+  if (n == 0) return;
+  double2* out = p3 + ((size_t)w * nc + off) * N;
+  if (!(wfin[w] > 0.0)) {
+    for (int e = threadIdx.x; e < n * N; e += AT) out[e] = make_double2(0.0, 0.0);
+    return;
+  }
+  double2* Oi = sm_ra;        // [n][n]  O3^{-1}
+  double2* On = Oi + n * n;   // [n][n]  O'
+  double2* Mx = On + n * n;   // [n][n]  O3^{-1} O'
+  const double2* src = oinv3 + ((size_t)w * 2 + spin) * nmax * nmax;
+  for (int e = threadIdx.x; e < n * n; e += AT) Oi[e] = src[e];
+  const double2* Pn = pnext + ((size_t)w * nc + off) * N;
+  if (qr) {
+    const double2* Sn = psinext + ((size_t)w * nc + off) * N;
+    for (int e = threadIdx.x; e < n * n; e += AT) {
+      const int i = e / n, l = e - (e / n) * n;
+      const double* a = trial + (size_t)(off + i) * N;
+      const double2* b = Sn + (size_t)l * N;
+      double sr = 0.0, si = 0.0;
+      for (int q = 0; q < N; ++q) {
+        sr = fma(a[q], b[q].x, sr);
+        si = fma(a[q], b[q].y, si);
+      }
+      On[e] = make_double2(sr, si);
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += AT) {
+      const int j = e / n, l = e - (e / n) * n;
+      cd s = mk(0.0, 0.0);
+      for (int i = 0; i < n; ++i) s = s + ldc(Oi[j * n + i]) * ldc(On[i * n + l]);
+      Mx[e] = make_double2(s.re, s.im);
+    }
+  }
+  __syncthreads();
+  const cd a = ldc(aR[w]);
+  for (int e = threadIdx.x; e < n * N; e += AT) {
+    const int j = e / N, p = e - (e / N) * N;
+    cd v = mk(0.0, 0.0);
+    if (qr) {
+      for (int l = 0; l < n; ++l) v = v + ldc(Pn[(size_t)l * N + p]) * ldc(Mx[j * n + l]);
+    } else {
+      v = ldc(Pn[(size_t)j * N + p]);
+    }
+    cd u = mk(0.0, 0.0);
+    for (int i = 0; i < n; ++i) u = u + trial[(size_t)(off + i) * N + p] * ldc(Oi[j * n + i]);
+    v = v + a * u;
+    out[e] = make_double2(v.re, v.im);
+  }
+}
+
+// Adjoint of the force bias and of the scalar factor for every (walker, g):
+//   c_bar  += a_R (-i sqrt(tau) L_bar_g)              (log s)
+//   f_bar   = -c_bar + omega c_g                       (c = x - f; log I)
+//   t_bar   = kept ? -i sqrt(tau) f_bar : 0            (Eq. force_shift)
+//   Lbar_bar contribution: Re[-t_bar + a_R (-i sqrt(tau) c_g + tau L_bar_g)]
+__global__ void adj_force_kernel(const double2* __restrict__ cbar, const double2* __restrict__ c,
+                                 const uint8_t* __restrict__ keep, const double2* __restrict__ aR,
+                                 const double* __restrict__ omega, const double* __restrict__ Lbar,
+                                 double2* __restrict__ tbar, double* __restrict__ mu_part, int G, double sqrt_tau,
+                                 double tau, size_t total) {
+  for (size_t e = blockIdx.x * (size_t)AT + threadIdx.x; e < total; e += (size_t)gridDim.x * AT) {
+    const size_t w = e / G;
+    const int g = (int)(e - w * G);
+    const cd a = ldc(aR[w]);
+    const double om = omega[w], mu = Lbar[g];
+    const cd cg = ldc(c[e]);
+    const cd ctot = ldc(cbar[e]) + a * mul_mis(sqrt_tau, mk(mu, 0.0));
+    const cd fb = mk(-ctot.re + om * cg.re, -ctot.im + om * cg.im);
+    const cd tb = keep[e] ? mul_mis(sqrt_tau, fb) : mk(0.0, 0.0);
+    tbar[e] = make_double2(tb.re, tb.im);
+    const cd m = a * (mul_mis(sqrt_tau, cg) + mk(tau * mu, 0.0));
+    mu_part[e] = -tb.re + m.re;
+  }
+}
+
+// mubar[g] += sum_w part[w][g] (walkers in order)
+__global__ void adj_mu_reduce_kernel(const double* __restrict__ part, double* __restrict__ mubar, int Nw, int G) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= G) return;
+  double s = 0.0;
+  for (int w = 0; w < Nw; ++w) s += part[(size_t)w * G + g];
+  mubar[g] += s;
+}
+
+// Psi_bar += [Theta_bar - trial (Theta^T Theta_bar + a I)] O^{-T} for one
+// (walker, spin): the pull-back through Theta = Psi O^{-1} minus a times the
+// derivative trial O^{-T} of log det O (a = a_R: the old overlap enters log R
+// with a minus sign; a = 0 when aR is NULL).  Dead walkers are skipped.
+__global__ void __launch_bounds__(AT) adj_theta_kernel(const double2* __restrict__ thbar,
+                                                       const double2* __restrict__ theta,
+                                                       const double* __restrict__ trial,
+                                                       const double2* __restrict__ oinv,
+                                                       const double2* __restrict__ aR, const double* __restrict__ wfin,
+                                                       double2* __restrict__ pbar, int N, int na, int nb, int nmax) {
+  extern __shared__ double2 sm_th[];
+  const int w = blockIdx.x, spin = blockIdx.y;
+  const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
+  if (n == 0 || !(wfin[w] > 0.0)) return;
+  double2* Oi = sm_th;       // [n][n] O^{-1}
+  double2* S = Oi + n * n;   // [n][n] S[l][i] = (Theta^T Theta_bar)_li + a delta_li
+  double2* Q = S + n * n;    // [n][n] Q[j][l] = sum_i O^{-1}[j][i] S[l][i]
+  const double2* src = oinv + ((size_t)w * 2 + spin) * nmax * nmax;
+  for (int e = threadIdx.x; e < n * n; e += AT) Oi[e] = src[e];
+  const double2* Tb = thbar + ((size_t)w * nc + off) * N;
+  const double2* Th = theta + ((size_t)w * nc + off) * N;
+  const cd a = aR ? ldc(aR[w]) : mk(0.0, 0.0);
+  for (int e = threadIdx.x; e < n * n; e += AT) {
+    const int l = e / n, i = e - (e / n) * n;
+    const double2* x = Th + (size_t)l * N;
+    const double2* y = Tb + (size_t)i * N;
+    double sr = 0.0, si = 0.0;
+    for (int p = 0; p < N; ++p) {
+      sr = fma(x[p].x, y[p].x, sr);
+      sr = fma(-x[p].y, y[p].y, sr);
+      si = fma(x[p].x, y[p].y, si);
+      si = fma(x[p].y, y[p].x, si);
+    }
+    if (l == i) {
+      sr += a.re;
+      si += a.im;
+    }
+    S[e] = make_double2(sr, si);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n * n; e += AT) {
+    const int j = e / n, l = e - (e / n) * n;
+    cd s = mk(0.0, 0.0);
+    for (int i = 0; i < n; ++i) s = s + ldc(Oi[j * n + i]) * ldc(S[l * n + i]);
+    Q[e] = make_double2(s.re, s.im);
+  }
+  __syncthreads();
+  double2* out = pbar + ((size_t)w * nc + off) * N;
+  for (int e = threadIdx.x; e < n * N; e += AT) {
+    const int j = e / N, p = e - (e / N) * N;
+    cd v = ldc(out[e]);
+    for (int i = 0; i < n; ++i) v = v + ldc(Tb[(size_t)i * N + p]) * ldc(Oi[j * n + i]);
+    for (int l = 0; l < n; ++l) v = v - trial[(size_t)(off + l) * N + p] * ldc(Q[j * n + l]);
+    out[e] = make_double2(v.re, v.im);
+  }
+}
+
+// omega_w = dJ W_w (Ebar_w - J) / sum W and e_w = dJ W_w / sum W strictly
+// inside the energy window (Eq. enwin); both zero for dead walkers.
+__global__ void adj_seed_coef_kernel(const double* __restrict__ wfin, const double* __restrict__ ecap,
+                                     const double* __restrict__ e_loc, const double* __restrict__ emix,
+                                     double* __restrict__ omega, double* __restrict__ ecoef, int Nw, double e0,
+                                     double dE, double dJ) {
+  const double tot = emix[1], J = emix[2];
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < Nw; w += gridDim.x * blockDim.x) {
+    const double W = wfin[w];
+    const bool live = W > 0.0 && tot > 0.0;
+    const double e = e_loc[2 * w];
+    const bool inside = e > e0 - dE && e < e0 + dE;
+    omega[w] = live ? dJ * W * (ecap[w] - J) / tot : 0.0;
+    ecoef[w] = (live && inside) ? dJ * W / tot : 0.0;
+  }
+}
+
+// Theta_bar of the local energy for one (walker, spin, row chunk):
+//   dE_L/dTheta_s[p][j] = h_half[j][p] + sum_g [ t_g Lh_g[j][p] - sum_i Lh_g[i][p] T_gs[j][i] ]
+// with T_gs[j][i] = sum_q Lh_g[j][q] Theta_s[i][q] and t_g the trace over
+// both spins; scaled by e_w.
+constexpr int SEED_R = 16;  // outputs per thread
+__global__ void __launch_bounds__(AT) adj_eloc_seed_kernel(const double2* __restrict__ theta,
+                                                           const double2* __restrict__ t,
+                                                           const double* __restrict__ Lh,
+                                                           const double* __restrict__ hhalf,
+                                                           const double* __restrict__ ecoef,
+                                                           double2* __restrict__ thbar, int N, int na, int nb, int G,
+                                                           int prows) {
+  extern __shared__ double2 sm_es[];
+  const int w = blockIdx.x, spin = blockIdx.y;
+  const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
+  const int p0 = blockIdx.z * prows;
+  const int pr = min(prows, N - p0);
+  if (n == 0 || pr <= 0) return;
+  double2* out = thbar + ((size_t)w * nc + off) * N;
+  const double ew = ecoef[w];
+  if (ew == 0.0) {
+    for (int e = threadIdx.x; e < n * pr; e += AT) {
+      const int j = e / pr, p = p0 + e - (e / pr) * pr;
+      out[(size_t)j * N + p] = make_double2(0.0, 0.0);
+    }
+    return;
+  }
+  double2* T = sm_es;  // [n][n]
+  const double2* Th = theta + ((size_t)w * nc + off) * N;
+  cd acc[SEED_R];
+  int jj[SEED_R], pp[SEED_R];
+#pragma unroll
+  for (int r = 0; r < SEED_R; ++r) {
+    const int e = threadIdx.x + r * AT;
+    jj[r] = -1;
+    pp[r] = 0;
+    acc[r] = mk(0.0, 0.0);
+    if (e < n * pr) {
+      jj[r] = e / pr;
+      pp[r] = p0 + e - (e / pr) * pr;
+      acc[r] = mk(hhalf[(size_t)(off + jj[r]) * N + pp[r]], 0.0);
+    }
+  }
+  for (int g = 0; g < G; ++g) {
+    const double* Lg = Lh + ((size_t)g * nc + off) * N;
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += AT) {
+      const int j = e / n, i = e - (e / n) * n;
+      const double* a = Lg + (size_t)j * N;
+      const double2* b = Th + (size_t)i * N;
+      double sr = 0.0, si = 0.0;
+      for (int q = 0; q < N; ++q) {
+        sr = fma(a[q], b[q].x, sr);
+        si = fma(a[q], b[q].y, si);
+      }
+      T[e] = make_double2(sr, si);
+    }
+    __syncthreads();
+    const cd tg = ldc(t[(size_t)w * G + g]);
+#pragma unroll
+    for (int r = 0; r < SEED_R; ++r) {
+      if (jj[r] < 0) continue;
+      const int j = jj[r], p = pp[r];
+      cd v = acc[r] + Lg[(size_t)j * N + p] * tg;
+      for (int i = 0; i < n; ++i) v = v - Lg[(size_t)i * N + p] * ldc(T[j * n + i]);
+      acc[r] = v;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < SEED_R; ++r)
+    if (jj[r] >= 0) out[(size_t)jj[r] * N + pp[r]] = make_double2(ew * acc[r].re, ew * acc[r].im);
+}
+
+// ------------------------------------------------------------ final assembly
+// Bs = (Re Bbar + Re Bbar^T) / 2
+__global__ void adj_bsym_kernel(const double2* __restrict__ Bbar, double* __restrict__ Bs, int N) {
+  const size_t NN = (size_t)N * N;
+  for (size_t e = blockIdx.x * (size_t)AT + threadIdx.x; e < NN; e += (size_t)gridDim.x * AT) {
+    const size_t p = e / N, q = e - p * N;
+    Bs[e] = 0.5 * (Bbar[e].x + Bbar[q * N + p].x);
+  }
+}
+
+// C[b] = op(A[b]) op(B[b]) for n x n real matrices (op = transpose when the
+// flag is set), batch b = blockIdx.z with element strides sA, sB, sC.
+__global__ void __launch_bounds__(256) adj_mm_kernel(const double* __restrict__ A, long long sA, int tA,
+                                                     const double* __restrict__ B, long long sB, int tB,
+                                                     double* __restrict__ C, long long sC, int n) {
+  __shared__ double sa[16][17], sb[16][17];
+  const int b = blockIdx.z;
+  const double* Ab = A + (size_t)b * sA;
+  const double* Bb = B + (size_t)b * sB;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int row = blockIdx.y * 16 + ty, col = blockIdx.x * 16 + tx;
+  double acc = 0.0;
+  for (int k0 = 0; k0 < n; k0 += 16) {
+    const int ka = k0 + tx, kb = k0 + ty;
+    double va = 0.0, vb = 0.0;
+    if (row < n && ka < n) va = tA ? Ab[(size_t)ka * n + row] : Ab[(size_t)row * n + ka];
+    if (col < n && kb < n) vb = tB ? Bb[(size_t)col * n + kb] : Bb[(size_t)kb * n + col];
+    sa[ty][tx] = va;
+    sb[ty][tx] = vb;
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc = fma(sa[ty][k], sb[k][tx], acc);
+    __syncthreads();
+  }
+  if (row < n && col < n) C[(size_t)b * sC + (size_t)row * n + col] = acc;
+}
+
+// M[i][j] *= (f_i - f_j) / (lam_i - lam_j) with f = exp(-tau lam / 2)
+// (f'(lam_i) when equal), written as -(tau/2) f_j expm1(x)/x, x = -tau (lam_i - lam_j)/2
+__global__ void adj_dk_kernel(double* __restrict__ M, const double* __restrict__ lam, double tau, int N) {
+  const size_t NN = (size_t)N * N;
+  for (size_t e = blockIdx.x * (size_t)AT + threadIdx.x; e < NN; e += (size_t)gridDim.x * AT) {
+    const int i = (int)(e / N), j = (int)(e - (size_t)i * N);
+    const double x = -0.5 * tau * (lam[i] - lam[j]);
+    const double phi = x == 0.0 ? 1.0 : expm1(x) / x;
+    M[e] *= -0.5 * tau * exp(-0.5 * tau * lam[j]) * phi;
+  }
+}
+
+// mubar[g] += sum_pq hbar[p][q] L_g[p][q]  (one block per g, fixed tree)
+__global__ void __launch_bounds__(256) adj_mu_h_kernel(const double* __restrict__ L, const double* __restrict__ hbar,
+                                                       double* __restrict__ mubar, size_t NN) {
+  __shared__ double sh[8];
+  const int g = blockIdx.x;
+  const double* Lg = L + (size_t)g * NN;
+  double s = 0.0;
+  for (size_t e = threadIdx.x; e < NN; e += 256) s = fma(hbar[e], Lg[e], s);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += sh[i];
+    mubar[g] += t;
+  }
+}
+
+// D[p][q] = sum_j trial[j][p] thT[j][q] = dL_bar_g / dL_g[p][q]
+__global__ void adj_density_kernel(const double* __restrict__ trial, const double* __restrict__ thT,
+                                   double* __restrict__ D, int N, int nc) {
+  const size_t NN = (size_t)N * N;
+  for (size_t e = blockIdx.x * (size_t)AT + threadIdx.x; e < NN; e += (size_t)gridDim.x * AT) {
+    const int p = (int)(e / N), q = (int)(e - (size_t)p * N);
+    double s = 0.0;
+    for (int j = 0; j < nc; ++j) s = fma(trial[(size_t)j * N + p], thT[(size_t)j * N + q], s);
+    D[e] = s;
+  }
+}
+
+// grad_L[g] = sym( E_L part (in grad_L) + Re gLc[g] + Re sum_j trial[j][p] Lhb[g][j][q]
+//                  - (X_g + X_g^T)/2 + L_bar_g hbar + mubar_g D ),  X_g = L_g hbar.
+// One thread per unordered pair (p <= q) writes both entries.
+__global__ void adj_final_L_kernel(double* __restrict__ gL, const double2* __restrict__ gLc,
+                                   const double2* __restrict__ Lhb, const double* __restrict__ X,
+                                   const double* __restrict__ hbar, const double* __restrict__ D,
+                                   const double* __restrict__ trial, const double* __restrict__ Lbar,
+                                   const double* __restrict__ mubar, int N, int nc, int G) {
+  const size_t NN = (size_t)N * N, total = (size_t)G * NN;
+  for (size_t e = blockIdx.x * (size_t)AT + threadIdx.x; e < total; e += (size_t)gridDim.x * AT) {
+    const size_t g = e / NN, r = e - g * NN;
+    const int p = (int)(r / N), q = (int)(r - (size_t)p * N);
+    if (p > q) continue;
+    const size_t pq = g * NN + (size_t)p * N + q, qp = g * NN + (size_t)q * N + p;
+    const double2* Lg = Lhb + g * nc * N;
+    double ep = 0.0, eq = 0.0;  // sum_j trial[j][p] Lhb[j][q] and the transposed entry
+    for (int j = 0; j < nc; ++j) {
+      ep = fma(trial[(size_t)j * N + p], Lg[(size_t)j * N + q].x, ep);
+      eq = fma(trial[(size_t)j * N + q], Lg[(size_t)j * N + p].x, eq);
+    }
+    const double x = -0.5 * (X[pq] + X[qp]);
+    const double mu = Lbar[g], mb = mubar[g];
+    const double vpq = gL[pq] + gLc[pq].x + ep + x + mu * hbar[(size_t)p * N + q] + mb * D[(size_t)p * N + q];
+    const double vqp = gL[qp] + gLc[qp].x + eq + x + mu * hbar[(size_t)q * N + p] + mb * D[(size_t)q * N + p];
+    const double v = 0.5 * (vpq + vqp);
+    gL[pq] = v;
+    gL[qp] = v;
+  }
+}
+
+// grad_h1 = sym(E_L part + hbar)
+__global__ void adj_final_h_kernel(double* __restrict__ gh, const double* __restrict__ hbar, int N) {
+  const size_t NN = (size_t)N * N;
+  for (size_t e = blockIdx.x * (size_t)AT + threadIdx.x; e < NN; e += (size_t)gridDim.x * AT) {
+    const int p = (int)(e / N), q = (int)(e - (size_t)p * N);
+    if (p > q) continue;
+    const size_t qp = (size_t)q * N + p;
+    const double v = 0.5 * (gh[e] + gh[qp] + hbar[e] + hbar[qp]);
+    gh[e] = v;
+    gh[qp] = v;
+  }
+}
+
+template <typename F>
+cudaError_t smem_ok(F* f, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(reinterpret_cast<const void*>(f), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)bytes);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------ launch wrappers
+cudaError_t adj_sanitize(const double2* src, double2* dst, const double* wfin, const double* trial, size_t per,
+                         int Nw, cudaStream_t s) {
+  const size_t total = per * Nw;
+  adj_sanitize_kernel<<<grid_for(total), AT, 0, s>>>(src, dst, wfin, trial, per, total);
+  return cudaGetLastError();
+}
+
+cudaError_t adj_sum_terms(const double2* T, double2* out, int K1, size_t per, int Nw, cudaStream_t s) {
+  const size_t total = per * Nw;
+  adj_sum_terms_kernel<<<grid_for(total), AT, 0, s>>>(T, out, K1, per, total);
+  return cudaGetLastError();
+}
+
+cudaError_t adj_scale_copy(const double2* src, size_t sstride, double2* dst, size_t dstride, double sc, size_t per,
+                           int Nw, cudaStream_t s) {
+  const size_t total = per * Nw;
+  adj_scale_copy_kernel<<<grid_for(total), AT, 0, s>>>(src, sstride, dst, dstride, sc, per, total);
+  return cudaGetLastError();
+}
+
+size_t adj_lu_smem(int nmax) { return (size_t)(2 * nmax * nmax + nmax) * sizeof(double2); }
+size_t adj_small_smem(int nmax) { return (size_t)3 * nmax * nmax * sizeof(double2); }
+
+cudaError_t adj_lu(const afqmc_ctx* c, int Nw, const double2* psi, double2* oinv, double* logdet, cudaStream_t s) {
+  const int nmax = c->na > c->nb ? c->na : c->nb;
+  const size_t shm = adj_lu_smem(nmax);
+  cudaError_t e = smem_ok(adj_lu_kernel, shm);
+  if (e != cudaSuccess) return e;
+  adj_lu_kernel<<<dim3(Nw, 2), AT, shm, s>>>(psi, c->d_trial, oinv, logdet, c->N, c->na, c->nb, nmax);
+  return cudaGetLastError();
+}
+
+cudaError_t adj_ratio_coef(int Nw, const double* wfin, const double* omega, const double* ld3, const double* logovl,
+                           const double* scal, double2* aR, double sqrt_tau, cudaStream_t s) {
+  adj_ratio_coef_kernel<<<(Nw + 127) / 128, 128, 0, s>>>(wfin, omega, ld3, logovl, scal, aR, sqrt_tau, Nw);
+  return cudaGetLastError();
+}
+
+cudaError_t adj_ratio(const afqmc_ctx* c, int Nw, const double2* pnext, const double2* psinext, const double2* oinv3,
+                      const double2* aR, const double* wfin, double2* p3, int qr, cudaStream_t s) {
+  const int nmax = c->na > c->nb ? c->na : c->nb;
+  const size_t shm = adj_small_smem(nmax);
+  cudaError_t e = smem_ok(adj_ratio_kernel, shm);
+  if (e != cudaSuccess) return e;
+  adj_ratio_kernel<<<dim3(Nw, 2), AT, shm, s>>>(pnext, psinext, c->d_trial, oinv3, aR, wfin, p3, c->N, c->na, c->nb,
+                                                nmax, qr);
+  return cudaGetLastError();
+}
+
+cudaError_t adj_force(const afqmc_ctx* c, int Nw, const double2* cbar, const double2* cc, const uint8_t* keep,
+                      const double2* aR, const double* omega, double2* tbar, double* mu_part, double* mubar,
+                      double sqrt_tau, double tau, cudaStream_t s) {
+  const size_t total = (size_t)Nw * c->G;
+  adj_force_kernel<<<grid_for(total), AT, 0, s>>>(cbar, cc, keep, aR, omega, c->d_Lbar, tbar, mu_part, c->G,
+                                                  sqrt_tau, tau, total);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  adj_mu_reduce_kernel<<<(c->G + 127) / 128, 128, 0, s>>>(mu_part, mubar, Nw, c->G);
+  return cudaGetLastError();
+}
+
+cudaError_t adj_theta(const afqmc_ctx* c, int Nw, const double2* thbar, const double2* theta, const double2* oinv,
+                      const double2* aR, const double* wfin, double2* pbar, cudaStream_t s) {
+  const int nmax = c->na > c->nb ? c->na : c->nb;
+  const size_t shm = adj_small_smem(nmax);
+  cudaError_t e = smem_ok(adj_theta_kernel, shm);
+  if (e != cudaSuccess) return e;
+  adj_theta_kernel<<<dim3(Nw, 2), AT, shm, s>>>(thbar, theta, c->d_trial, oinv, aR, wfin, pbar, c->N, c->na, c->nb,
+                                                nmax);
+  return cudaGetLastError();
+}
+
+cudaError_t adj_seed_coef(int Nw, const double* wfin, const double* ecap, const double* e_loc, const double* emix,
+                          double* omega, double* ecoef, double e0, double dE, double dJ, cudaStream_t s) {
+  adj_seed_coef_kernel<<<(Nw + 255) / 256, 256, 0, s>>>(wfin, ecap, e_loc, emix, omega, ecoef, Nw, e0, dE, dJ);
+  return cudaGetLastError();
+}
+
+cudaError_t adj_eloc_seed(const afqmc_ctx* c, int Nw, const double2* theta, const double2* t, const double* ecoef,
+                          double2* thbar, cudaStream_t s) {
+  const int nmax = c->na > c->nb ? c->na : c->nb;
+  if (nmax == 0) return cudaSuccess;
+  int prows = (SEED_R * AT) / nmax;
+  if (prows > c->N) prows = c->N;
+  const int chunks = (c->N + prows - 1) / prows;
+  const size_t shm = (size_t)nmax * nmax * sizeof(double2);
+  cudaError_t e = smem_ok(adj_eloc_seed_kernel, shm);
+  if (e != cudaSuccess) return e;
+  adj_eloc_seed_kernel<<<dim3(Nw, 2, chunks), AT, shm, s>>>(theta, t, c->d_Lh, c->d_hhalf, ecoef, thbar, c->N, c->na,
+                                                           c->nb, c->G, prows);
+  return cudaGetLastError();
+}
+
+// hbar'' from Bbar: hbar = V (F o (V^T sym(Re Bbar) V)) V^T; then
+// mubar += <hbar, L_g>, X_g = L_g hbar, and the final symmetrised gradients.
+cudaError_t adj_finish(const afqmc_ctx* c, const double2* Bbar, const double* V, const double* lam, double tau,
+                       double* Bs, double* T1, double* M1, double* hbar, double* X, double* D, const double2* gLc,
+                       const double2* Lhb, double* mubar, double* grad_h1, double* grad_L, int* n_launch,
+                       cudaStream_t s) {
+  const int N = c->N, G = c->G, nc = c->nc;
+  const size_t NN = (size_t)N * N;
+  const dim3 mg((N + 15) / 16, (N + 15) / 16, 1);
+  cudaError_t e;
+#define AFQ_L(expr)                      \
+  do {                                   \
+    expr;                                \
+    e = cudaGetLastError();              \
+    if (e != cudaSuccess) return e;      \
+    ++*n_launch;                         \
+  } while (0)
+  AFQ_L((adj_bsym_kernel<<<grid_for(NN), AT, 0, s>>>(Bbar, Bs, N)));
+  AFQ_L((adj_mm_kernel<<<mg, 256, 0, s>>>(V, 0, 1, Bs, 0, 0, T1, 0, N)));      // V^T Bs
+  AFQ_L((adj_mm_kernel<<<mg, 256, 0, s>>>(T1, 0, 0, V, 0, 0, M1, 0, N)));      // (V^T Bs) V
+  AFQ_L((adj_dk_kernel<<<grid_for(NN), AT, 0, s>>>(M1, lam, tau, N)));
+  AFQ_L((adj_mm_kernel<<<mg, 256, 0, s>>>(V, 0, 0, M1, 0, 0, T1, 0, N)));      // V M
+  AFQ_L((adj_mm_kernel<<<mg, 256, 0, s>>>(T1, 0, 0, V, 0, 1, hbar, 0, N)));    // (V M) V^T
+  AFQ_L((adj_mu_h_kernel<<<G, 256, 0, s>>>(c->d_L, hbar, mubar, NN)));
+  AFQ_L((adj_mm_kernel<<<dim3(mg.x, mg.y, G), 256, 0, s>>>(c->d_L, (long long)NN, 0, hbar, 0, 0, X,
+                                                          (long long)NN, N)));  // X_g = L_g hbar
+  AFQ_L((adj_density_kernel<<<grid_for(NN), AT, 0, s>>>(c->d_trial, c->d_thT, D, N, nc)));
+  AFQ_L((adj_final_L_kernel<<<grid_for((size_t)G * NN), AT, 0, s>>>(grad_L, gLc, Lhb, X, hbar, D, c->d_trial,
+                                                                    c->d_Lbar, mubar, N, nc, G)));
+  AFQ_L((adj_final_h_kernel<<<grid_for(NN), AT, 0, s>>>(grad_h1, hbar, N)));
+#undef AFQ_L
+  return cudaSuccess;
+}
+
+}  // namespace afq

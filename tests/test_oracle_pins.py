@@ -516,3 +516,84 @@ def test_oracle_energy_gradient_matches_central_differences():
         fd_L = (J(ham.h1, ham.L + eps * dL) - J(ham.h1, ham.L - eps * dL)) / (2 * eps)
     assert abs(float(fd_h) - float((h1.grad * dH).sum())) < 1e-8
     assert abs(float(fd_L) - float((L.grad * dL).sum())) < 1e-8
+
+
+# ---------------------------------------------------------------- walk adjoint
+class _Sys:
+    """A synthetic closed-shell system with the trial cut to na alpha and nb
+    beta orbitals (na != nb exercises unequal spin blocks)."""
+
+    def __init__(self, N, na, nb, G, seed):
+        base = make_system(N, na, na, G, rho=0.8, seed=seed)
+        self.h1, self.L, self.e_const = base.h1, base.L, base.e_const
+        self.trial = np.concatenate([base.trial[:, :na], base.trial[:, na:na + nb]], axis=1)
+        self.na, self.nb = na, nb
+
+
+def _walk_setup(N=7, na=2, nb=1, G=9, nw=3, steps=5, seed=11, tau=0.05):
+    s = _Sys(N, na, nb, G, seed)
+    ham0 = R.make_hamiltonian(s.h1, s.L, s.trial, na, nb, s.e_const)
+    e0 = float(R.local_energy(ham0, ham0.trial.to(CT)).real)
+    fields = [make_fields(seed, k, nw, G) for k in range(steps)]
+    return s, e0, fields, tau
+
+
+def _walk_J(s, h1, L, psi0, fields, tau, e0, r=2):
+    ham = R.Hamiltonian(torch.as_tensor(h1, dtype=RT), torch.as_tensor(L, dtype=RT),
+                        torch.as_tensor(s.trial, dtype=RT), s.na, s.nb, s.e_const)
+    return R.walk_objective(ham, psi0, torch.ones(psi0.shape[0], dtype=RT), fields, tau, e0,
+                            k=6, reortho_every=r)[0]
+
+
+def test_walk_objective_gradient_matches_central_differences():
+    """Reading R10: torch autograd through the oracle walk (Taylor-6, QR every 2
+    steps) against central differences of J along random symmetric dH, dL."""
+    s, e0, fields, tau = _walk_setup()
+    nw = fields[0].shape[0]
+    psi0 = torch.as_tensor(s.trial, dtype=RT).to(CT).unsqueeze(0).repeat(nw, 1, 1)
+    h1 = torch.tensor(s.h1, dtype=RT, requires_grad=True)
+    L = torch.tensor(s.L, dtype=RT, requires_grad=True)
+    J = _walk_J(s, h1, L, psi0, fields, tau, e0)
+    gh, gL = torch.autograd.grad(J, [h1, L])
+    rng = np.random.default_rng(4)
+    dH = rng.standard_normal(s.h1.shape); dH = 0.5 * (dH + dH.T)
+    dL = rng.standard_normal(s.L.shape); dL = 0.5 * (dL + dL.transpose(0, 2, 1))
+    eps = 1e-5
+    with torch.no_grad():
+        fd_h = (float(_walk_J(s, s.h1 + eps * dH, s.L, psi0, fields, tau, e0))
+                - float(_walk_J(s, s.h1 - eps * dH, s.L, psi0, fields, tau, e0))) / (2 * eps)
+        fd_L = (float(_walk_J(s, s.h1, s.L + eps * dL, psi0, fields, tau, e0))
+                - float(_walk_J(s, s.h1, s.L - eps * dL, psi0, fields, tau, e0))) / (2 * eps)
+    assert abs(fd_h - float((gh * torch.as_tensor(dH)).sum())) <= 1e-6 * max(1.0, abs(fd_h))
+    assert abs(fd_L - float((gL * torch.as_tensor(dL)).sum())) <= 1e-6 * max(1.0, abs(fd_L))
+
+
+def test_walk_objective_gauge_invariance_and_psi_gradient():
+    """J is unchanged by Psi_0 -> Psi_0 M (the Taylor action, Theta, the overlap
+    ratio and E_L are invariant), so its gradient G with respect to Psi_0
+    satisfies Psi_0,s^T G_s = 0 per spin; G = conj(torch's .grad) reproduces
+    a central difference along a random complex direction."""
+    s, e0, fields, tau = _walk_setup(steps=4, seed=12)
+    nw = fields[0].shape[0]
+    g = torch.Generator().manual_seed(3)
+    psi0 = (torch.as_tensor(s.trial, dtype=RT).to(CT).unsqueeze(0).repeat(nw, 1, 1)
+            + 0.1 * _rand_c(g, nw, s.trial.shape[0], s.trial.shape[1]))
+    psi0.requires_grad_(True)
+    J = _walk_J(s, s.h1, s.L, psi0, fields, tau, e0)
+    (tg,) = torch.autograd.grad(J, [psi0])
+    G = tg.conj()
+    with torch.no_grad():
+        M = torch.eye(3, dtype=CT) + 0.3 * _rand_c(g, 3, 3)
+        M[:2, 2] = 0
+        M[2, :2] = 0                      # block diagonal: alpha (2) and beta (1) columns
+        J2 = float(_walk_J(s, s.h1, s.L, psi0.detach() @ M, fields, tau, e0))
+        assert abs(J2 - float(J)) <= 1e-11 * abs(float(J))
+        for sl in (slice(0, 2), slice(2, 3)):
+            P = psi0.detach()[:, :, sl]
+            Z = P.transpose(1, 2) @ G[:, :, sl]
+            assert float(Z.abs().max()) <= 1e-10 * float(G.abs().max()) * 10
+        dP = _rand_c(g, *psi0.shape)
+        eps = 1e-6
+        fd = (float(_walk_J(s, s.h1, s.L, psi0.detach() + eps * dP, fields, tau, e0))
+              - float(_walk_J(s, s.h1, s.L, psi0.detach() - eps * dP, fields, tau, e0))) / (2 * eps)
+        assert abs(fd - float((G * dP).sum().real)) <= 1e-6 * max(1.0, abs(fd))
