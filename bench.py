@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the FP64-path rate measured beside the mixed one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the timed gradient of the differentiation workload")
     ap.add_argument("--cpu-sample-walkers", type=int, default=4)
     ap.add_argument("--walkers", type=int, default=NW,
                     help="walkers per GPU (the workload has 1024; fewer only for small profiling cases)")
@@ -188,6 +190,56 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ our arm
+def adjoint_rate(dev):
+    """Gradient of the mixed estimator through a 100-step fixed-field walk
+    (differentiation workload: N=96, 15+15 electrons, 480 vectors, 512
+    walkers, Taylor-6, QR every 10 steps, checkpoints every 10), FP64, timed
+    with CUDA events; the plain FP64 forward walk of the same workload beside it."""
+    import torch
+    from paper_2403_02542_gb300.api import Context
+    from paper_2403_02542_gb300.inputs import CONFIGS, config_system
+    cfg = CONFIGS["grad"]
+    s = config_system("grad")
+    nw, steps, tau, order, r = cfg["walkers"], cfg["steps"], cfg["tau"], cfg["order"], cfg["reortho"]
+    ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision="fp64", device=dev)
+    w = ctx.new_walkers(nw)
+    ctx.init_walkers(w)
+    el = torch.empty(nw, 2, dtype=torch.float64, device=dev)
+    em = torch.empty(4, dtype=torch.float64, device=dev)
+    ctx.local_energy(w, 0.0, tau, el, em)
+    e0 = float(el[0, 0])
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(99)
+    fields = torch.randn(steps, nw, s.G, dtype=torch.float64, device=dev, generator=gen)
+    stream = torch.cuda.current_stream(dev)
+    ctx.walk_backward(w, fields[:2], tau, e0, order=order, reortho_every=r, ckpt_every=10)   # warm-up
+    torch.cuda.synchronize()
+    l0 = ctx.launch_count
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    J, _, _ = ctx.walk_backward(w, fields, tau, e0, order=order, reortho_every=r, ckpt_every=10)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    t_adj = a0.elapsed_time(a1)
+    launches = ctx.launch_count - l0
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    for k in range(steps):
+        ctx.step(w, fields[k], tau, e0, expm="taylor", order=order, reortho=(k + 1) % r == 0,
+                 measure=(k == steps - 1), e_loc=el, e_mix=em)
+    f1.record(stream)
+    torch.cuda.synchronize()
+    t_fwd = f0.elapsed_time(f1)
+    ctx.close()
+    return {
+        "workload": "gradient of E_n after a 100-step fixed-field walk: N=96, Na=Nb=15, N_gamma=480, "
+                    "512 walkers, tau=0.05, Split-2 + Taylor-6, QR every 10 steps, checkpoints every 10, FP64",
+        "value": nw * steps / (t_adj / 1000.0), "unit": "walker-steps/s (gradient, forward + adjoint)",
+        "ms": t_adj, "forward_ms": t_fwd, "adjoint_over_forward": t_adj / t_fwd,
+        "J": float(J[2]), "live": float(J[3]), "gpu_launches": launches,
+    }
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -370,6 +422,9 @@ def run_ours(args):
                      "(BF16x3 split); achieved counts algorithmic flops once")
         kname = "exchange_tc_kernel (tcgen05 BF16x3)"
     achieved = (ex_flop / (ex_ms / ex_n / 1000.0)) / 1e12 if ex_n else None
+    adjoint = None
+    if world == 1 and not args.no_adjoint:
+        adjoint = adjoint_rate(dev)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu, _ = oracle_rate(system, args.cpu_sample_walkers, 2, "")
@@ -395,6 +450,7 @@ def run_ours(args):
         "graph_value": graph_value,
         "fp64_value": fp64_value,
         "mixed_over_fp64": (value / fp64_value) if fp64_value else None,
+        "adjoint": adjoint,
         "clocks": clk,
         "e_mix_last": emix_final,
     }
