@@ -7,7 +7,8 @@
 // built exactly for any tau (Sec. III.B).
 //
 // Step schedule (all on the context's stream):
-//   overlap/Theta -> force-bias GEMM -> bias finalisation -> field GEMM
+//   overlap/Theta -> force-bias GEMM -> bias finalisation -> field GEMM (tensor
+//   cores for complex64 walkers)
 //   -> B Psi -> Taylor or Arnoldi/Krylov -> B Psi -> new overlap -> weights
 //   -> commit -> [MGS -> overlap] -> [overlap -> local energy -> E_k]
 #include <cmath>
@@ -15,6 +16,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "internal.cuh"
@@ -177,6 +179,7 @@ static afqmc_status ws_ensure(afqmc_ctx* c, int Nw, int kmax) {
   ws.n_walkers = nw;
   ws.kmax = km;
   if (c->tc.ok) CK(tc_exchange_ws(c));
+  if (c->tg.ok) CK(tc_field_ws(c));
   return AFQMC_OK;
 }
 
@@ -198,6 +201,7 @@ cudaError_t prepare_kernels(afqmc_ctx* c) {
   cudaError_t e = c->prec == AFQMC_FP64 ? prepare_overlap<double>(c) : prepare_overlap<float>(c);
   if (e == cudaSuccess) e = c->prec == AFQMC_FP64 ? prepare_energy<double>(c) : prepare_energy<float>(c);
   if (e == cudaSuccess) e = tc_exchange_prepare(c);
+  if (e == cudaSuccess) e = tc_field_prepare(c);
   return e;
 }
 }  // namespace afq
@@ -234,6 +238,7 @@ static void ctx_free(afqmc_ctx* c) {
   if (!c) return;
   prof_release(c->prof);
   tc_exchange_free(c);
+  tc_field_free(c);
   ws_free(c->ws);
   void* ptrs[] = {c->d_L,  c->d_Lh, c->d_trial, c->d_hhalf, c->d_Lbar, c->d_thT,
                   c->d_B,  c->f_L,  c->f_Lh,    c->f_B,     c->f_trial};
@@ -337,6 +342,11 @@ static afqmc_status ctx_setup(afqmc_ctx* c, const double* h1, const double* L, c
     c->launches += 1;
     CK(cudaStreamSynchronize(s));
   }
+  if (c->prec == AFQMC_MIXED) {
+    CK(tc_field_setup(c, s));
+    c->launches += c->tg.ok ? 1 : 0;
+    CK(cudaStreamSynchronize(s));
+  }
   return AFQMC_OK;
 }
 
@@ -432,8 +442,13 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
   // force bias (Eq. force_shift) and c_g = x_g - f_g
   PK(AFQMC_K_FORCEBIAS, gemm<R>(site_args<R>(c, SITE_FORCEBIAS, Nw, st, ws.theta, ws.t), false, EPI_STORE, s));
   PK(AFQMC_K_OTHER, launch_bias_finalize<R>(c, Nw, x, st, s));
-  // A_w = i sqrt(tau) sum_g c_wg L_g (Eq. heffTOT)
-  PK(AFQMC_K_FIELD, gemm<R>(site_args<R>(c, SITE_FIELD, Nw, st, ws.c, ws.A), false, EPI_STORE, s));
+  // A_w = i sqrt(tau) sum_g c_wg L_g (Eq. heffTOT); complex64 walkers: on the tensor cores
+  if (std::is_same<R, float>::value && c->tg.ok) {
+    PK(AFQMC_K_FIELD, tc_field_launch(c, Nw, st, s));
+    c->launches += 1;
+  } else {
+    PK(AFQMC_K_FIELD, gemm<R>(site_args<R>(c, SITE_FIELD, Nw, st, ws.c, ws.A), false, EPI_STORE, s));
+  }
   // psi_b = B psi
   PK(AFQMC_K_HALFSTEP, gemm<R>(site_args<R>(c, SITE_HALFSTEP, Nw, st, w->psi, ws.psi_b), false, EPI_STORE, s));
   c->launches += 5;
@@ -1139,11 +1154,15 @@ afqmc_status afqmc_sync(afqmc_ctx* c) {
   if (!c) return AFQMC_EINVAL;
   CK(cudaStreamSynchronize(c->stream));
   CK(cudaGetLastError());
-  if (c->tc.err) {  // a bounded wait of the tensor-core kernel gave up
+  // a bounded wait of a tensor-core kernel gave up
+  const struct { void* flag; const char* what; } tc_flags[] = {{c->tc.err, "tensor-core exchange"},
+                                                                {c->tg.err, "tensor-core field assembly"}};
+  for (const auto& f : tc_flags) {
+    if (!f.flag) continue;
     int flag = 0;
-    CK(cudaMemcpy(&flag, c->tc.err, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(&flag, f.flag, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) {
-      snprintf(g_cuda_err, sizeof g_cuda_err, "tensor-core exchange: pipeline wait timed out (code %d)", flag);
+      snprintf(g_cuda_err, sizeof g_cuda_err, "%s: pipeline wait timed out (code %d)", f.what, flag);
       return AFQMC_ECUDA;
     }
   }

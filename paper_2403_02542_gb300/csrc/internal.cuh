@@ -138,6 +138,24 @@ struct TcPlan {
 };
 }  // namespace afq
 
+namespace afq {
+// Plan and operands of the tensor-core field assembly (mixed contexts).
+struct TgPlan {
+  bool ok = false;
+  int Kp = 0, m_cap = 0;
+  size_t Np = 0;
+  void* l_hi = nullptr;  // [Np][Kp] bf16: L^T split hi/lo
+  void* l_lo = nullptr;
+  void* x_hi = nullptr;  // [m_cap][Kp] bf16: (-sqrt(tau) Im c, sqrt(tau) Re c) rows split hi/lo
+  void* x_lo = nullptr;
+  void* err = nullptr;   // device int: nonzero after a bounded wait timed out
+  alignas(64) unsigned char map_l_hi[128];
+  alignas(64) unsigned char map_l_lo[128];
+  alignas(64) unsigned char map_x_hi[128];
+  alignas(64) unsigned char map_x_lo[128];
+};
+}  // namespace afq
+
 struct afqmc_ctx {
   int N, na, nb, nc, G, prec;
   double e_const = 0.0, ec_prime = 0.0, tau = -1.0;
@@ -161,6 +179,7 @@ struct afqmc_ctx {
   afq::Workspace ws;
   afq::Prof prof;
   afq::TcPlan tc;
+  afq::TgPlan tg;
   int tune[afq::N_SITES] = {0, 0, 0, 4};  // GEMM tile variant per call site
   bool capturing = false;                  // inside a graph capture (afqmc_batch_step)
   uint64_t launches = 0;
@@ -268,6 +287,13 @@ size_t tc_exchange_plane_bytes(const TcPlan& P, int cap);
 cudaError_t tc_exchange_bind(TcPlan& P, void* b_hi, void* b_lo, int cap);
 void tc_exchange_free(afqmc_ctx* c);
 cudaError_t tc_exchange_launch(afqmc_ctx* c, int Nw, const void* theta, double* epart, cudaStream_t s);
+
+// tensor-core field assembly (k_gemm_tc.cu)
+cudaError_t tc_field_setup(afqmc_ctx* c, cudaStream_t s);
+cudaError_t tc_field_ws(afqmc_ctx* c);
+cudaError_t tc_field_prepare(const afqmc_ctx* c);
+void tc_field_free(afqmc_ctx* c);
+cudaError_t tc_field_launch(afqmc_ctx* c, int Nw, double sqrt_tau, cudaStream_t s);
 
 }  // namespace afq
 
