@@ -453,33 +453,38 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
   PK(AFQMC_K_HALFSTEP, gemm<R>(site_args<R>(c, SITE_HALFSTEP, Nw, st, w->psi, ws.psi_b), false, EPI_STORE, s));
   c->launches += 5;
 
-  // per-walker products with A_w
+  // per-walker products with A_w (tensor cores for complex64 walkers)
   GemmArgs ga = site_args<R>(c, SITE_EXPM, Nw, st, nullptr, nullptr);
+  const bool tc_av = std::is_same<R, float>::value && c->tg.av_ok;
+  auto av = [&](const void* in, void* out, void* add, double alpha) -> cudaError_t {
+    if (tc_av) return tc_av_launch(c, Nw, in, per, out, add, per, alpha, s);
+    ga.B = in; ga.C = out; ga.D = add;
+    ga.alpha_re = alpha; ga.alpha_im = 0.0;
+    return gemm<R>(ga, true, add ? EPI_STORE_ADD : EPI_STORE, s);
+  };
   if (p->expm == AFQMC_EXPM_TAYLOR) {
     CKW(cudaMemcpyAsync(ws.acc, ws.psi_b, (size_t)Nw * per * cs, cudaMemcpyDeviceToDevice, s), "acc copy");
     const void* cur = ws.psi_b;
     for (int n = 1; n <= p->order; ++n) {
       void* nxt = (n & 1) ? ws.term0 : ws.term1;
-      ga.B = cur; ga.C = nxt; ga.D = ws.acc;
-      ga.alpha_re = 1.0 / n; ga.alpha_im = 0.0;
-      PK(AFQMC_K_EXPM, gemm<R>(ga, true, EPI_STORE_ADD, s));
+      PK(AFQMC_K_EXPM, av(cur, nxt, ws.acc, 1.0 / n));
       cur = nxt;
     }
-    c->launches += p->order;
+    c->launches += p->order * (tc_av ? 2 : 1);
   } else {
     const int k = p->order;
     const size_t bstride = (size_t)ws.n_walkers * per;
-    PK(AFQMC_K_OTHER, launch_normA<R>(c, Nw, s));
+    if (tc_av)
+      PK(AFQMC_K_OTHER, tc_av_normA(c, Nw, s));
+    else
+      PK(AFQMC_K_OTHER, launch_normA<R>(c, Nw, s));
     PK(AFQMC_K_OTHER, launch_krylov_init<R>(c, Nw, s));
     for (int it = 0; it < k; ++it) {
-      ga.B = static_cast<char*>(ws.basis) + it * bstride * cs;
-      ga.C = ws.term0; ga.D = nullptr;
-      ga.alpha_re = 1.0; ga.alpha_im = 0.0;
-      PK(AFQMC_K_EXPM, gemm<R>(ga, true, EPI_STORE, s));
+      PK(AFQMC_K_EXPM, av(static_cast<char*>(ws.basis) + it * bstride * cs, ws.term0, nullptr, 1.0));
       PK(AFQMC_K_OTHER, launch_krylov_orth<R>(c, Nw, it, k, s));
     }
     PK(AFQMC_K_OTHER, launch_krylov_finish<R>(c, Nw, k, s));
-    c->launches += 2 + 2 * k + 2;
+    c->launches += 2 + 2 * k + 2 + (tc_av ? k : 0);
   }
   // psi_new = B acc
   PK(AFQMC_K_HALFSTEP, gemm<R>(site_args<R>(c, SITE_HALFSTEP, Nw, st, ws.acc, ws.psi_new), false, EPI_STORE, s));

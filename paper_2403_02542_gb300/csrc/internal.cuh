@@ -153,6 +153,18 @@ struct TgPlan {
   alignas(64) unsigned char map_l_lo[128];
   alignas(64) unsigned char map_x_hi[128];
   alignas(64) unsigned char map_x_lo[128];
+  // products A_w V on the tensor cores: the field kernel then writes A_w as
+  // bf16 hi/lo planes A'[w][p][KA] = [Re A_w[p][:] | Im A_w[p][:]]
+  bool av_ok = false;
+  int KA = 0, NBp = 0, S_av = 0, av_cap = 0;
+  void* a_hi = nullptr;  // [cap * N][KA]
+  void* a_lo = nullptr;
+  void* v_hi = nullptr;  // [cap * NBp][KA]: rows j [Re v_j | -Im v_j], rows nc + j [Im v_j | Re v_j]
+  void* v_lo = nullptr;
+  alignas(64) unsigned char map_a_hi[128];
+  alignas(64) unsigned char map_a_lo[128];
+  alignas(64) unsigned char map_v_hi[128];
+  alignas(64) unsigned char map_v_lo[128];
 };
 }  // namespace afq
 
@@ -294,6 +306,12 @@ cudaError_t tc_field_ws(afqmc_ctx* c);
 cudaError_t tc_field_prepare(const afqmc_ctx* c);
 void tc_field_free(afqmc_ctx* c);
 cudaError_t tc_field_launch(afqmc_ctx* c, int Nw, double sqrt_tau, cudaStream_t s);
+// C[w][j][p] = alpha sum_q A_w[p][q] V[w][j][q] (D[w] += C[w] when D is given),
+// complex64, walker batch strides in complex elements; A_w from the planes.
+cudaError_t tc_av_launch(afqmc_ctx* c, int Nw, const void* V, long long v_stride, void* C, void* D,
+                         long long c_stride, double alpha, cudaStream_t s);
+// ||A_w||_F from the planes into ws.scal[w][SC_NORMA]
+cudaError_t tc_av_normA(afqmc_ctx* c, int Nw, cudaStream_t s);
 
 }  // namespace afq
 

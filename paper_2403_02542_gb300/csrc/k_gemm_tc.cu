@@ -18,6 +18,14 @@
 // lane pair (2w, 2w+1) exchanges halves so that each thread stores four
 // complex values of A_w contiguously).  Every mbarrier wait is bounded; on a
 // timeout the kernel raises an error flag, stops issuing work and frees TMEM.
+//
+// When the products A_w V of the exponential also run on the tensor cores,
+// the field epilogue writes A_w instead as bfloat16 hi/lo planes
+// A'[w][p][k] = [Re A_w[p][q] | Im A_w[p][q]] (k = q, N + q), and
+//   (A V)_re = A' [Re V; -Im V],  (A V)_im = A' [Im V; Re V]
+// is one real contraction per walker with K = 2N and 2 nc output columns
+// (av_tc_kernel: rows p in tiles of 128, the whole V' of the walker as the
+// right operand, same three-MMA split, pipeline and bounded waits).
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -40,10 +48,15 @@ constexpr uint32_t TG_STAGE_BYTES = 2 * TG_A_BYTES + 2 * TG_B_BYTES;
 struct TgArgs {
   int mt, nt, KC, n_items;
   int M, Nn;           // valid rows (2 Nw) and columns (N^2)
-  float* out;          // A as interleaved complex [Nw][Nn]
+  float* out;          // mode 0: A as interleaved complex [Nw][Nn]
+  __nv_bfloat16* a_hi;  // mode 1: A' planes [Nw * N][KA]
+  __nv_bfloat16* a_lo;
+  int N, KA;
   int* err;
 };
 
+// MODE 0 writes A as complex64 [w][p][q]; MODE 1 the split planes A'.
+template <int MODE>
 __global__ void __launch_bounds__(TG_THREADS, 1)
     field_tc_kernel(const __grid_constant__ CUtensorMap tmX_hi, const __grid_constant__ CUtensorMap tmX_lo,
                     const __grid_constant__ CUtensorMap tmL_hi, const __grid_constant__ CUtensorMap tmL_lo,
@@ -174,22 +187,51 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
         uint32_t v[8];
         tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * TG_BN + c0), v);
         tmem_wait_ld();
-        // even lane (row 2w = Re A) keeps columns c0..c0+3, odd lane (Im A) c0+4..c0+7
-        float mine[4], other[4];
+        if constexpr (MODE == 1) {
+          // row 2w + part -> plane column part * N + q of row p of walker w
+          const int e0 = e_base + c0;
+          if (!row_ok || e0 >= p.Nn) continue;
+          const int part = m & 1;
+          if ((p.N & 7) == 0 && e0 + 8 <= p.Nn) {
+            const int pr = e0 / p.N, q = e0 - pr * p.N;
+            const size_t o = ((size_t)w * p.N + pr) * p.KA + (size_t)part * p.N + q;
+            __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const float send = __uint_as_float(odd ? v[t] : v[4 + t]);
-          const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
-          mine[t] = __uint_as_float(odd ? v[4 + t] : v[t]);
-          other[t] = recv;
-        }
-        if (row_ok) {
-          const int e0 = e_base + c0 + (odd ? 4 : 0);
+            for (int t = 0; t < 8; ++t) {
+              const float x = __uint_as_float(v[t]);
+              h[t] = __float2bfloat16(x);
+              l[t] = __float2bfloat16(x - __bfloat162float(h[t]));
+            }
+            *reinterpret_cast<uint4*>(p.a_hi + o) = *reinterpret_cast<const uint4*>(h);
+            *reinterpret_cast<uint4*>(p.a_lo + o) = *reinterpret_cast<const uint4*>(l);
+          } else {
+            for (int t = 0; t < 8 && e0 + t < p.Nn; ++t) {
+              const int e = e0 + t, pr = e / p.N, q = e - pr * p.N;
+              const size_t o = ((size_t)w * p.N + pr) * p.KA + (size_t)part * p.N + q;
+              const float x = __uint_as_float(v[t]);
+              const __nv_bfloat16 h = __float2bfloat16(x);
+              p.a_hi[o] = h;
+              p.a_lo[o] = __float2bfloat16(x - __bfloat162float(h));
+            }
+          }
+        } else {
+          // even lane (row 2w = Re A) keeps columns c0..c0+3, odd lane (Im A) c0+4..c0+7
+          float mine[4], other[4];
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
-            if (e0 + t < p.Nn) {
-              const float re = odd ? other[t] : mine[t], im = odd ? mine[t] : other[t];
-              *reinterpret_cast<float2*>(orow + (size_t)(e0 + t) * 2) = make_float2(re, im);
+            const float send = __uint_as_float(odd ? v[t] : v[4 + t]);
+            const float recv = __shfl_xor_sync(0xffffffffu, send, 1);
+            mine[t] = __uint_as_float(odd ? v[4 + t] : v[t]);
+            other[t] = recv;
+          }
+          if (row_ok) {
+            const int e0 = e_base + c0 + (odd ? 4 : 0);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+              if (e0 + t < p.Nn) {
+                const float re = odd ? other[t] : mine[t], im = odd ? mine[t] : other[t];
+                *reinterpret_cast<float2*>(orow + (size_t)(e0 + t) * 2) = make_float2(re, im);
+              }
             }
           }
         }
@@ -207,6 +249,230 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
     __syncwarp();
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TG_TMEM_COLS) : "memory");
+  }
+}
+
+// Products A_w V for every walker: items (walker, 128-row tile of p), K = KA
+// in slabs of 64, the right operand V'_w (NBp rows) streamed with each slab.
+struct AvArgs {
+  int N, nc, NBp, KC, MT, n_items, S;
+  uint32_t stage_bytes, b_bytes;
+  float2* out;        // C[w][j][p] (walker stride c_stride)
+  float2* add;        // D += C when non-null (same layout)
+  long long c_stride;
+  float alpha;
+  int* err;
+};
+
+__global__ void __launch_bounds__(TG_THREADS, 1)
+    av_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
+                 const __grid_constant__ CUtensorMap tmV_hi, const __grid_constant__ CUtensorMap tmV_lo,
+                 const AvArgs p) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base =
+      reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + (size_t)p.S * p.stage_bytes);
+  uint64_t* full = bars;             // [S]
+  uint64_t* empty = bars + p.S;      // [S]
+  uint64_t* tfull = bars + 2 * p.S;  // [2]
+  uint64_t* tempty = tfull + 2;      // [2]
+  uint64_t* drain = tempty + 2;      // [1]
+  volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(drain + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* epi_ok = abort_flag + 1;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.S; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull + b, 1);
+      mbar_init(tempty + b, 128);
+    }
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(sa((const void*)tmem_slot)),
+                 "r"(TG_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t ph = 0;
+      uint32_t last_ph[8];
+      bool issued[8] = {false, false, false, false, false, false, false, false};
+      for (int item = blockIdx.x; item < p.n_items && !*abort_flag; item += gridDim.x) {
+        const int w = item / p.MT, mt = item - (item / p.MT) * p.MT;
+        const int arow = w * p.N + mt * TG_BM, vrow = w * p.NBp;
+        for (int kc = 0; kc < p.KC; ++kc) {
+          if (!mbar_wait(empty + stage, ph ^ 1)) { atomicOr(p.err, 1); *abort_flag = 1; break; }
+          mbar_expect_tx(full + stage, p.stage_bytes);
+          unsigned char* dst = base + (size_t)stage * p.stage_bytes;
+          tma_load_2d(dst, &tmA_hi, kc * 64, arow, full + stage);
+          tma_load_2d(dst + TG_A_BYTES, &tmA_lo, kc * 64, arow, full + stage);
+          tma_load_2d(dst + 2 * TG_A_BYTES, &tmV_hi, kc * 64, vrow, full + stage);
+          tma_load_2d(dst + 2 * TG_A_BYTES + p.b_bytes, &tmV_lo, kc * 64, vrow, full + stage);
+          issued[stage] = true;
+          last_ph[stage] = ph;
+          if (++stage == p.S) { stage = 0; ph ^= 1; }
+        }
+      }
+      for (int s = 0; s < p.S; ++s)
+        if (issued[s]) mbar_wait(full + s, last_ph[s]);
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      int stage = 0, buf = 0;
+      uint32_t ph = 0, tph[2] = {0, 0};
+      const uint32_t idesc = idesc_bf16(TG_BM, p.NBp);
+      for (int item = blockIdx.x; item < p.n_items && !*abort_flag; item += gridDim.x) {
+        if (!mbar_wait(tempty + buf, tph[buf] ^ 1)) { atomicOr(p.err, 2); *abort_flag = 1; break; }
+        tc_fence_after();
+        const uint32_t d = tmem + (uint32_t)(buf * p.NBp);
+        for (int kc = 0; kc < p.KC; ++kc) {
+          if (!mbar_wait(full + stage, ph)) { atomicOr(p.err, 4); *abort_flag = 1; break; }
+          tc_fence_after();
+          const uint32_t a_hi = sa(base + (size_t)stage * p.stage_bytes);
+          const uint32_t a_lo = a_hi + TG_A_BYTES;
+          const uint32_t b_hi = a_hi + 2 * TG_A_BYTES;
+          const uint32_t b_lo = b_hi + p.b_bytes;
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const uint32_t off = k * 32;
+            umma(d, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, (kc > 0 || k > 0) ? 1u : 0u);
+            umma(d, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
+            umma(d, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
+          }
+          umma_commit(empty + stage);
+          if (++stage == p.S) { stage = 0; ph ^= 1; }
+        }
+        umma_commit(tfull + buf);
+        tph[buf] ^= 1;
+        buf ^= 1;
+      }
+      umma_commit(drain);
+      if (!mbar_wait(drain, 0)) atomicOr(p.err, 8);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int quad = warp & 3;
+    const int r = quad * 32 + lane;
+    int buf = 0;
+    uint32_t tph[2] = {0, 0};
+    for (int item = blockIdx.x; item < p.n_items; item += gridDim.x) {
+      const int w = item / p.MT, mt = item - (item / p.MT) * p.MT;
+      if (r == 0) {
+        const bool ok = mbar_wait(tfull + buf, tph[buf]);
+        if (!ok) { atomicOr(p.err, 16); *abort_flag = 1; }
+        *epi_ok = ok ? 1 : 0;
+      }
+      named_bar(1, 128);
+      const int ok = *epi_ok;
+      named_bar(1, 128);
+      if (!ok) break;
+      tc_fence_after();
+      const int pr = mt * TG_BM + r;
+      const bool row_ok = pr < p.N;
+      float2* o = p.out + (size_t)w * p.c_stride + pr;
+      float2* dd = p.add ? p.add + (size_t)w * p.c_stride + pr : nullptr;
+      const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * p.NBp);
+      for (int j0 = 0; j0 < p.nc; j0 += 8) {
+        uint32_t vr[8], vi[8];
+        tmem_ld8(tbase + (uint32_t)j0, vr);                 // columns j: Re (A V)
+        tmem_ld8(tbase + (uint32_t)(p.nc + j0), vi);        // columns nc + j: Im (A V)
+        tmem_wait_ld();
+        if (!row_ok) continue;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int j = j0 + t;
+          if (j < p.nc) {
+            const float2 v = make_float2(p.alpha * __uint_as_float(vr[t]), p.alpha * __uint_as_float(vi[t]));
+            o[(size_t)j * p.N] = v;
+            if (dd) {
+              float2 x = dd[(size_t)j * p.N];
+              x.x += v.x;
+              x.y += v.y;
+              dd[(size_t)j * p.N] = x;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(tempty + buf);
+      tph[buf] ^= 1;
+      buf ^= 1;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TG_TMEM_COLS) : "memory");
+  }
+}
+
+// V'_w from V (complex64 [w][j][q], walker stride vs): rows j < nc hold
+// [Re v_j | -Im v_j], rows nc + j hold [Im v_j | Re v_j]; rows >= 2 nc and
+// columns >= 2N are zero.  Split into hi/lo.
+__global__ void build_v_kernel(const float2* __restrict__ V, long long vs, __nv_bfloat16* __restrict__ hi,
+                               __nv_bfloat16* __restrict__ lo, int Nw, int N, int nc, int NBp, int KA) {
+  const size_t total = (size_t)Nw * NBp * KA;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e % KA);
+    const size_t rw = e / KA;
+    const int row = (int)(rw % NBp);
+    const size_t w = rw / NBp;
+    float x = 0.f;
+    if (row < 2 * nc && k < 2 * N) {
+      const int j = row < nc ? row : row - nc;
+      const int q = k < N ? k : k - N;
+      const float2 v = V[w * vs + (size_t)j * N + q];
+      if (row < nc) x = k < N ? v.x : -v.y;
+      else x = k < N ? v.y : v.x;
+    }
+    const __nv_bfloat16 h = __float2bfloat16(x);
+    hi[e] = h;
+    lo[e] = __float2bfloat16(x - __bfloat162float(h));
+  }
+}
+
+// ||A_w||_F^2 = sum over the planes of (hi + lo)^2 (one block per walker, fixed tree)
+__global__ void __launch_bounds__(256) normA_planes_kernel(const __nv_bfloat16* __restrict__ hi,
+                                                           const __nv_bfloat16* __restrict__ lo,
+                                                           double* __restrict__ scal, int N, int KA) {
+  __shared__ double sh[8];
+  const int w = blockIdx.x;
+  const size_t per = (size_t)N * KA;
+  const __nv_bfloat16* h = hi + (size_t)w * per;
+  const __nv_bfloat16* l = lo + (size_t)w * per;
+  float part = 0.f;
+  for (size_t e = threadIdx.x; e < per; e += 256) {
+    const float x = __bfloat162float(h[e]) + __bfloat162float(l[e]);
+    part = fmaf(x, x, part);
+  }
+  double v = part;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < 8; ++i) t += sh[i];
+    scal[(size_t)w * SC_COUNT + SC_NORMA] = sqrt(t);
   }
 }
 
@@ -250,10 +516,19 @@ inline int grid_for(size_t n) {
 }
 
 size_t tg_smem_bytes() { return 1024 + (size_t)TG_S * TG_STAGE_BYTES + (2 * TG_S + 5) * 8 + 16; }
+size_t av_stage_bytes(int NBp) { return 2 * (size_t)TG_A_BYTES + 2 * (size_t)NBp * 128; }
+size_t av_smem_bytes(int NBp, int S) { return 1024 + (size_t)S * av_stage_bytes(NBp) + (2 * S + 5) * 8 + 16; }
+
+int sm_count() {
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
 
 }  // namespace
 
-// Plan and right operand of the tensor-core field assembly (mixed contexts).
+// Plan and right operand of the tensor-core field assembly (mixed contexts);
+// the products A V go to the tensor cores as well when 2 nc <= 240.
 cudaError_t tc_field_setup(afqmc_ctx* c, cudaStream_t s) {
   TgPlan& P = c->tg;
   P = TgPlan();
@@ -279,18 +554,32 @@ cudaError_t tc_field_setup(afqmc_ctx* c, cudaStream_t s) {
       !make_map(reinterpret_cast<CUtensorMap*>(P.map_l_lo), P.l_lo, P.Np, P.Kp, TG_BN))
     return cudaErrorInvalidValue;
   P.ok = true;
+  const int nbp = ((2 * c->nc + 15) / 16) * 16;
+  if (nbp <= 240) {
+    int S = 4;
+    while (S > 2 && av_smem_bytes(nbp, S) > (size_t)max_dyn_smem()) --S;
+    if (av_smem_bytes(nbp, S) <= (size_t)max_dyn_smem()) {
+      P.av_ok = true;
+      P.NBp = nbp;
+      P.S_av = S;
+      P.KA = ((2 * c->N + 63) / 64) * 64;
+    }
+  }
   return cudaSuccess;
 }
 
-// Left-operand planes for the workspace's walker capacity.
+// Operand planes sized for the workspace's walker capacity.
 cudaError_t tc_field_ws(afqmc_ctx* c) {
   TgPlan& P = c->tg;
   if (!P.ok) return cudaSuccess;
-  if (P.x_hi) cudaFree(P.x_hi);
-  if (P.x_lo) cudaFree(P.x_lo);
-  P.x_hi = P.x_lo = nullptr;
+  void* old[] = {P.x_hi, P.x_lo, P.a_hi, P.a_lo, P.v_hi, P.v_lo};
+  for (void* q : old)
+    if (q) cudaFree(q);
+  P.x_hi = P.x_lo = P.a_hi = P.a_lo = P.v_hi = P.v_lo = nullptr;
   P.m_cap = 0;
-  const int mp = ((2 * c->ws.n_walkers + TG_BM - 1) / TG_BM) * TG_BM;
+  P.av_cap = 0;
+  const int cap = c->ws.n_walkers;
+  const int mp = ((2 * cap + TG_BM - 1) / TG_BM) * TG_BM;
   cudaError_t e = cudaMalloc(&P.x_hi, (size_t)mp * P.Kp * 2);
   if (e != cudaSuccess) return e;
   e = cudaMalloc(&P.x_lo, (size_t)mp * P.Kp * 2);
@@ -299,27 +588,53 @@ cudaError_t tc_field_ws(afqmc_ctx* c) {
       !make_map(reinterpret_cast<CUtensorMap*>(P.map_x_lo), P.x_lo, (size_t)mp, P.Kp, TG_BM))
     return cudaErrorInvalidValue;
   P.m_cap = mp;
+  if (P.av_ok) {
+    const size_t arows = (size_t)cap * c->N, vrows = (size_t)cap * P.NBp;
+    e = cudaMalloc(&P.a_hi, arows * P.KA * 2);
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&P.a_lo, arows * P.KA * 2);
+    if (e != cudaSuccess) return e;
+    // the K padding columns 2N..KA stay zero (the field epilogue writes k < 2N only)
+    e = cudaMemset(P.a_hi, 0, arows * P.KA * 2);
+    if (e != cudaSuccess) return e;
+    e = cudaMemset(P.a_lo, 0, arows * P.KA * 2);
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&P.v_hi, vrows * P.KA * 2);
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&P.v_lo, vrows * P.KA * 2);
+    if (e != cudaSuccess) return e;
+    if (!make_map(reinterpret_cast<CUtensorMap*>(P.map_a_hi), P.a_hi, arows, P.KA, TG_BM) ||
+        !make_map(reinterpret_cast<CUtensorMap*>(P.map_a_lo), P.a_lo, arows, P.KA, TG_BM) ||
+        !make_map(reinterpret_cast<CUtensorMap*>(P.map_v_hi), P.v_hi, vrows, P.KA, P.NBp) ||
+        !make_map(reinterpret_cast<CUtensorMap*>(P.map_v_lo), P.v_lo, vrows, P.KA, P.NBp))
+      return cudaErrorInvalidValue;
+    P.av_cap = cap;
+  }
   return cudaSuccess;
 }
 
 cudaError_t tc_field_prepare(const afqmc_ctx* c) {
   if (!c->tg.ok) return cudaSuccess;
-  return raise_smem_limit(field_tc_kernel);
+  cudaError_t e = raise_smem_limit(field_tc_kernel<0>);
+  if (e == cudaSuccess) e = raise_smem_limit(field_tc_kernel<1>);
+  if (e == cudaSuccess && c->tg.av_ok) e = raise_smem_limit(av_tc_kernel);
+  return e;
 }
 
 void tc_field_free(afqmc_ctx* c) {
   TgPlan& P = c->tg;
-  void* ptrs[] = {P.l_hi, P.l_lo, P.x_hi, P.x_lo, P.err};
+  void* ptrs[] = {P.l_hi, P.l_lo, P.x_hi, P.x_lo, P.a_hi, P.a_lo, P.v_hi, P.v_lo, P.err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   P = TgPlan();
 }
 
-// A_w = i sqrt(tau) sum_g c_wg L_g for Nw walkers from ws.c into ws.A (complex64).
+// A_w = i sqrt(tau) sum_g c_wg L_g for Nw walkers from ws.c: into ws.A
+// (complex64), or into the A' planes when the products A V use them.
 cudaError_t tc_field_launch(afqmc_ctx* c, int Nw, double sqrt_tau, cudaStream_t s) {
   TgPlan& P = c->tg;
   const int mp = ((2 * Nw + TG_BM - 1) / TG_BM) * TG_BM;
-  if (mp > P.m_cap) return cudaErrorInvalidValue;
+  if (mp > P.m_cap || (P.av_ok && Nw > P.av_cap)) return cudaErrorInvalidValue;
   build_x_kernel<<<grid_for((size_t)mp * P.Kp), 256, 0, s>>>(static_cast<const float2*>(c->ws.c),
                                                             static_cast<__nv_bfloat16*>(P.x_hi),
                                                             static_cast<__nv_bfloat16*>(P.x_lo), Nw, c->G, mp, P.Kp,
@@ -334,20 +649,73 @@ cudaError_t tc_field_launch(afqmc_ctx* c, int Nw, double sqrt_tau, cudaStream_t 
   a.M = 2 * Nw;
   a.Nn = c->N * c->N;
   a.out = static_cast<float*>(c->ws.A);
+  a.a_hi = static_cast<__nv_bfloat16*>(P.a_hi);
+  a.a_lo = static_cast<__nv_bfloat16*>(P.a_lo);
+  a.N = c->N;
+  a.KA = P.KA;
   a.err = static_cast<int*>(P.err);
   if (!capturing(c)) {
-    e = raise_smem_limit(field_tc_kernel);
+    e = P.av_ok ? raise_smem_limit(field_tc_kernel<1>) : raise_smem_limit(field_tc_kernel<0>);
     if (e != cudaSuccess) return e;
   }
-  int sms = 152, dev = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int sms = sm_count();
   const int grid = a.n_items < sms ? a.n_items : sms;
   CUtensorMap mxh, mxl, mlh, mll;
   memcpy(&mxh, P.map_x_hi, sizeof(CUtensorMap));
   memcpy(&mxl, P.map_x_lo, sizeof(CUtensorMap));
   memcpy(&mlh, P.map_l_hi, sizeof(CUtensorMap));
   memcpy(&mll, P.map_l_lo, sizeof(CUtensorMap));
-  field_tc_kernel<<<grid, TG_THREADS, tg_smem_bytes(), s>>>(mxh, mxl, mlh, mll, a);
+  if (P.av_ok)
+    field_tc_kernel<1><<<grid, TG_THREADS, tg_smem_bytes(), s>>>(mxh, mxl, mlh, mll, a);
+  else
+    field_tc_kernel<0><<<grid, TG_THREADS, tg_smem_bytes(), s>>>(mxh, mxl, mlh, mll, a);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_av_launch(afqmc_ctx* c, int Nw, const void* V, long long v_stride, void* C, void* D,
+                         long long c_stride, double alpha, cudaStream_t s) {
+  TgPlan& P = c->tg;
+  if (!P.av_ok || Nw > P.av_cap) return cudaErrorInvalidValue;
+  const size_t elems = (size_t)Nw * P.NBp * P.KA;
+  build_v_kernel<<<grid_for(elems), 256, 0, s>>>(static_cast<const float2*>(V), v_stride,
+                                                 static_cast<__nv_bfloat16*>(P.v_hi),
+                                                 static_cast<__nv_bfloat16*>(P.v_lo), Nw, c->N, c->nc, P.NBp, P.KA);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  AvArgs a;
+  a.N = c->N;
+  a.nc = c->nc;
+  a.NBp = P.NBp;
+  a.KC = P.KA / 64;
+  a.MT = (c->N + TG_BM - 1) / TG_BM;
+  a.n_items = Nw * a.MT;
+  a.S = P.S_av;
+  a.b_bytes = (uint32_t)P.NBp * 128;
+  a.stage_bytes = (uint32_t)av_stage_bytes(P.NBp);
+  a.out = static_cast<float2*>(C);
+  a.add = static_cast<float2*>(D);
+  a.c_stride = c_stride;
+  a.alpha = (float)alpha;
+  a.err = static_cast<int*>(P.err);
+  if (!capturing(c)) {
+    e = raise_smem_limit(av_tc_kernel);
+    if (e != cudaSuccess) return e;
+  }
+  const int sms = sm_count();
+  const int grid = a.n_items < sms ? a.n_items : sms;
+  CUtensorMap mah, mal, mvh, mvl;
+  memcpy(&mah, P.map_a_hi, sizeof(CUtensorMap));
+  memcpy(&mal, P.map_a_lo, sizeof(CUtensorMap));
+  memcpy(&mvh, P.map_v_hi, sizeof(CUtensorMap));
+  memcpy(&mvl, P.map_v_lo, sizeof(CUtensorMap));
+  av_tc_kernel<<<grid, TG_THREADS, av_smem_bytes(P.NBp, P.S_av), s>>>(mah, mal, mvh, mvl, a);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_av_normA(afqmc_ctx* c, int Nw, cudaStream_t s) {
+  const TgPlan& P = c->tg;
+  normA_planes_kernel<<<Nw, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(P.a_hi),
+                                         static_cast<const __nv_bfloat16*>(P.a_lo), c->ws.scal, c->N, P.KA);
   return cudaGetLastError();
 }
 
