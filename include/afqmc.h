@@ -106,7 +106,18 @@ typedef struct {
  *   reortho     nonzero: re-orthonormalise every determinant (modified
  *               Gram-Schmidt) after the weight update and recompute logovl
  *   measure     nonzero: evaluate E_L at the new walkers (see
- *               afqmc_local_energy for the outputs) */
+ *               afqmc_local_energy for the outputs)
+ *   reuse_bias  nonzero: the mixed expectations <L_g> of the force bias (Eq.
+ *               force_shift) are taken from the traces sum_s tr(Lh_gs Theta_s)
+ *               of the last local-energy evaluation on this context when that
+ *               evaluation was of the same walker buffers (psi pointer and
+ *               count) and nothing changed the walkers since (a step,
+ *               afqmc_walkers_init and afqmc_population_control invalidate
+ *               it); Theta is invariant under re-orthonormalisation, so the
+ *               quantity is the one the force bias would recompute.  The
+ *               check runs on the device, so captured graphs honour it too.
+ *               The caller must not modify the walkers between the two calls
+ *               by other means.  0: always recompute. */
 typedef struct {
   double tau;
   double e0;
@@ -115,6 +126,7 @@ typedef struct {
   int order;
   int reortho;
   int measure;
+  int reuse_bias;
 } afqmc_step_params;
 
 /* Create a context for one Hamiltonian (Sec. II.A, Eq. mbham in Cholesky form)

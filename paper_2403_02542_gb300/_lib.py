@@ -30,7 +30,7 @@ class StepParams(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("e0", ctypes.c_double),
                 ("propagator", ctypes.c_int), ("expm", ctypes.c_int),
                 ("order", ctypes.c_int), ("reortho", ctypes.c_int),
-                ("measure", ctypes.c_int)]
+                ("measure", ctypes.c_int), ("reuse_bias", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

@@ -110,13 +110,15 @@ class Context:
     def step(self, w: WalkerSet, fields: torch.Tensor, tau: float, e0: float,
              expm: str = "krylov", order: int = 10, reortho: bool = False,
              measure: bool = False, e_loc: torch.Tensor | None = None,
-             e_mix: torch.Tensor | None = None):
-        """One walker step (afqmc_step).  fields: device [Nw, G] float64."""
+             e_mix: torch.Tensor | None = None, reuse_bias: bool = False):
+        """One walker step (afqmc_step).  fields: device [Nw, G] float64.
+        reuse_bias: take the force bias from the previous measurement of the
+        same, unchanged walkers (see afqmc_step_params in the header)."""
         assert fields.dtype == torch.float64 and fields.is_cuda and fields.is_contiguous()
         self._bind_stream()
         p = L.StepParams(float(tau), float(e0), L.AFQMC_SPLIT2,
                          {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV}[expm],
-                         int(order), int(bool(reortho)), int(bool(measure)))
+                         int(order), int(bool(reortho)), int(bool(measure)), int(bool(reuse_bias)))
         cw = w.c_struct()
         L.check(L.lib().afqmc_step(self._h, ctypes.byref(cw), fields.data_ptr(), ctypes.byref(p),
                                    _ptr(e_loc), _ptr(e_mix)), "afqmc_step")
@@ -252,7 +254,7 @@ class Batch:
         self._h = h
 
     def step(self, walker_sets, fields, tau, e0, expm="krylov", order=10, reortho=False, measure=False,
-             e_loc=None, e_mix=None, stream: torch.cuda.Stream | None = None):
+             e_loc=None, e_mix=None, stream: torch.cuda.Stream | None = None, reuse_bias=False):
         n = len(self.contexts)
         taus = tau if isinstance(tau, (list, tuple)) else [tau] * n
         e0s = e0 if isinstance(e0, (list, tuple)) else [e0] * n
@@ -260,7 +262,8 @@ class Batch:
         fp = (ctypes.c_void_p * n)(*[f.data_ptr() for f in fields])
         ex = {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV}[expm]
         ps = (L.StepParams * n)(*[L.StepParams(float(taus[i]), float(e0s[i]), L.AFQMC_SPLIT2, ex, int(order),
-                                               int(bool(reortho)), int(bool(measure))) for i in range(n)])
+                                               int(bool(reortho)), int(bool(measure)), int(bool(reuse_bias)))
+                                  for i in range(n)])
         el = (ctypes.c_void_p * n)(*[None if e_loc is None or e_loc[i] is None else e_loc[i].data_ptr()
                                      for i in range(n)])
         em = (ctypes.c_void_p * n)(*[None if e_mix is None or e_mix[i] is None else e_mix[i].data_ptr()

@@ -240,8 +240,9 @@ static void ctx_free(afqmc_ctx* c) {
   tc_exchange_free(c);
   tc_field_free(c);
   ws_free(c->ws);
-  void* ptrs[] = {c->d_L,  c->d_Lh, c->d_trial, c->d_hhalf, c->d_Lbar, c->d_thT,
-                  c->d_B,  c->f_L,  c->f_Lh,    c->f_B,     c->f_trial};
+  void* ptrs[] = {c->d_L, c->d_Lh,  c->d_trial, c->d_hhalf,    c->d_Lbar,     c->d_thT,
+                  c->d_B, c->f_L,   c->f_Lh,    c->f_B,        c->f_trial,    c->d_bias_key,
+                  c->d_bias_skip};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free(c->h_evals);
@@ -259,6 +260,10 @@ static afqmc_status ctx_setup(afqmc_ctx* c, const double* h1, const double* L, c
   CK(cudaMalloc(&c->d_hhalf, (size_t)nc * N * sizeof(double)));
   CK(cudaMalloc(&c->d_Lbar, (size_t)G * sizeof(double)));
   CK(cudaMalloc(&c->d_B, NN * sizeof(double)));
+  CK(cudaMalloc(&c->d_bias_key, 2 * sizeof(unsigned long long)));
+  CK(cudaMalloc(&c->d_bias_skip, sizeof(int)));
+  CK(cudaMemsetAsync(c->d_bias_key, 0, 2 * sizeof(unsigned long long), s));
+  CK(cudaMemsetAsync(c->d_bias_skip, 0, sizeof(int), s));
   if (c->prec == AFQMC_MIXED) {
     CK(cudaMalloc(&c->f_L, (size_t)G * NN * sizeof(float)));
     CK(cudaMalloc(&c->f_Lh, (size_t)G * nc * N * sizeof(float)));
@@ -374,7 +379,9 @@ static afqmc_status run_energy(afqmc_ctx* c, const afqmc_walkers* w, double e0, 
     PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, w->psi, c->ws.theta, c->ws.logdet, w->status, s));
   int nl = 0;
   CK(launch_energy<R>(c, Nw, w->weight, e0, tau, e_loc ? e_loc : c->ws.eloc, e_mix ? e_mix : c->ws.emix, s, &nl));
-  c->launches += 2 + nl;
+  // ws.epart now holds sum_s tr(Lh_gs Theta_s) of these walkers (a later step may reuse it)
+  CK(launch_bias_mark(c, w->psi, Nw, s));
+  c->launches += 3 + nl;
   return AFQMC_OK;
 }
 
@@ -437,11 +444,17 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
   Workspace& ws = c->ws;
   const size_t cs = sizeof(typename C2<R>::t);
 
-  // Theta at the current walkers
-  PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, w->psi, ws.theta, ws.logdet, w->status, s));
+  // <L_g> from the last measurement of these walkers when allowed and valid
+  // (then the overlap and force-bias kernels return at once), else Theta and
+  // the force-bias contraction
+  PK(AFQMC_K_OTHER, launch_bias_gate(c, w->psi, Nw, p->reuse_bias ? 1 : 0, s));
+  const int* skip = c->d_bias_skip;
+  PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, w->psi, ws.theta, ws.logdet, w->status, s, skip));
   // force bias (Eq. force_shift) and c_g = x_g - f_g
-  PK(AFQMC_K_FORCEBIAS, gemm<R>(site_args<R>(c, SITE_FORCEBIAS, Nw, st, ws.theta, ws.t), false, EPI_STORE, s));
-  PK(AFQMC_K_OTHER, launch_bias_finalize<R>(c, Nw, x, st, s));
+  GemmArgs gfb = site_args<R>(c, SITE_FORCEBIAS, Nw, st, ws.theta, ws.t);
+  gfb.skip = skip;
+  PK(AFQMC_K_FORCEBIAS, gemm<R>(gfb, false, EPI_STORE, s));
+  PK(AFQMC_K_OTHER, launch_bias_finalize<R>(c, Nw, x, st, s, nullptr, skip));
   // A_w = i sqrt(tau) sum_g c_wg L_g (Eq. heffTOT); complex64 walkers: on the tensor cores
   if (std::is_same<R, float>::value && c->tg.ok) {
     PK(AFQMC_K_FIELD, tc_field_launch(c, Nw, st, s));
@@ -451,7 +464,7 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
   }
   // psi_b = B psi
   PK(AFQMC_K_HALFSTEP, gemm<R>(site_args<R>(c, SITE_HALFSTEP, Nw, st, w->psi, ws.psi_b), false, EPI_STORE, s));
-  c->launches += 5;
+  c->launches += 6;
 
   // per-walker products with A_w (tensor cores for complex64 walkers)
   GemmArgs ga = site_args<R>(c, SITE_EXPM, Nw, st, nullptr, nullptr);
@@ -480,11 +493,13 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
       PK(AFQMC_K_OTHER, launch_normA<R>(c, Nw, s));
     PK(AFQMC_K_OTHER, launch_krylov_init<R>(c, Nw, s));
     for (int it = 0; it < k; ++it) {
-      PK(AFQMC_K_EXPM, av(static_cast<char*>(ws.basis) + it * bstride * cs, ws.term0, nullptr, 1.0));
+      // tensor-core products read b_it from the planes the Arnoldi kernels wrote
+      PK(AFQMC_K_EXPM, av(tc_av ? nullptr : static_cast<char*>(ws.basis) + it * bstride * cs, ws.term0, nullptr,
+                          1.0));
       PK(AFQMC_K_OTHER, launch_krylov_orth<R>(c, Nw, it, k, s));
     }
     PK(AFQMC_K_OTHER, launch_krylov_finish<R>(c, Nw, k, s));
-    c->launches += 2 + 2 * k + 2 + (tc_av ? k : 0);
+    c->launches += 2 + 2 * k + 2;
   }
   // psi_new = B acc
   PK(AFQMC_K_HALFSTEP, gemm<R>(site_args<R>(c, SITE_HALFSTEP, Nw, st, ws.acc, ws.psi_new), false, EPI_STORE, s));
@@ -994,6 +1009,7 @@ afqmc_status afqmc_walkers_init(afqmc_ctx* c, const afqmc_walkers* w) {
   if (w->n_walkers == 0) return AFQMC_OK;
   st = ws_ensure(c, w->n_walkers, c->ws.kmax);
   if (st != AFQMC_OK) return st;
+  CK(cudaMemsetAsync(c->d_bias_key, 0, 2 * sizeof(unsigned long long), c->stream));  // walkers replaced
   if (c->prec == AFQMC_FP64) {
     CK(launch_init_walkers<double>(c, w, c->stream));
     CK(launch_overlap<double>(c, w->n_walkers, w->psi, nullptr, c->ws.logdet, w->status, c->stream));
@@ -1057,6 +1073,7 @@ afqmc_status afqmc_population_control(afqmc_ctx* c, const afqmc_walkers* w, doub
   if (w->n_walkers == 0) return AFQMC_OK;
   st = ws_ensure(c, w->n_walkers, c->ws.kmax);
   if (st != AFQMC_OK) return st;
+  CK(cudaMemsetAsync(c->d_bias_key, 0, 2 * sizeof(unsigned long long), c->stream));  // walkers replaced
   prof_mark(c, AFQMC_K_OTHER, true, c->stream);
   if (c->prec == AFQMC_FP64)
     CK(launch_comb<double>(c, w, u, index_out, c->stream));

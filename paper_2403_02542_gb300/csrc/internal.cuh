@@ -64,6 +64,7 @@ struct GemmArgs {
   void* part;
   int variant;  // output tile: 0 = 64x64, 1 = 128x32, 2 = 32x128, 3 = 64x32, 4 = per-walker A*V
   int accum;    // set by gemm() for EPI_ACC: the epilogue adds to C instead of storing
+  const int* skip;  // device flag or NULL: every block returns at once when *skip != 0
 };
 constexpr int GEMM_VARIANTS = 5;
 // GEMM call sites of the step, each with its own tuned tile variant
@@ -179,6 +180,11 @@ struct afqmc_ctx {
   double* d_hhalf = nullptr;  // [nc][N]     sum_p trial[j][p] h1[p][q]
   double* d_Lbar = nullptr;   // [G]
   double* d_thT = nullptr;    // [nc][N]     Theta_T = trial_s (trial_s^T trial_s)^{-1} per spin
+  // force bias from the last measurement: d_bias_key = {psi pointer, Nw} of the
+  // walkers whose traces ws.epart holds (0 = none); d_bias_skip = 1 while the
+  // current step takes <L_g> from those traces
+  unsigned long long* d_bias_key = nullptr;
+  int* d_bias_skip = nullptr;
   double* d_B = nullptr;      // [N][N]
   // FP32 copies for mixed contexts
   float* f_L = nullptr;
@@ -226,10 +232,15 @@ void prof_mark(afqmc_ctx* c, int cls, bool begin, cudaStream_t s);
 // kernels (launch wrappers); every wrapper returns the launch error
 template <typename R>
 cudaError_t launch_overlap(const afqmc_ctx* c, int Nw, const void* psi, void* theta,
-                           double* logdet, uint32_t* status, cudaStream_t s);
+                           double* logdet, uint32_t* status, cudaStream_t s, const int* skip = nullptr);
 template <typename R>
 cudaError_t launch_bias_finalize(const afqmc_ctx* c, int Nw, const double* x, double sqrt_tau,
-                                 cudaStream_t s, uint8_t* keep = nullptr);  // keep[w][g]: 1 = f_g kept
+                                 cudaStream_t s, uint8_t* keep = nullptr,  // keep[w][g]: 1 = f_g kept
+                                 const int* from_traces = nullptr);      // device flag: <L_g> from ws.epart
+// d_bias_skip = (opt_in && d_bias_key == {psi, Nw}); the key is cleared
+cudaError_t launch_bias_gate(const afqmc_ctx* c, const void* psi, int Nw, int opt_in, cudaStream_t s);
+// d_bias_key = {psi, Nw}: ws.epart now holds the traces of these walkers
+cudaError_t launch_bias_mark(const afqmc_ctx* c, const void* psi, int Nw, cudaStream_t s);
 template <typename R>
 cudaError_t launch_normA(const afqmc_ctx* c, int Nw, cudaStream_t s);
 template <typename R>
@@ -308,6 +319,7 @@ void tc_field_free(afqmc_ctx* c);
 cudaError_t tc_field_launch(afqmc_ctx* c, int Nw, double sqrt_tau, cudaStream_t s);
 // C[w][j][p] = alpha sum_q A_w[p][q] V[w][j][q] (D[w] += C[w] when D is given),
 // complex64, walker batch strides in complex elements; A_w from the planes.
+// V == NULL: the V planes were already written (by the Arnoldi kernels).
 cudaError_t tc_av_launch(afqmc_ctx* c, int Nw, const void* V, long long v_stride, void* C, void* D,
                          long long c_stride, double alpha, cudaStream_t s);
 // ||A_w||_F from the planes into ws.scal[w][SC_NORMA]

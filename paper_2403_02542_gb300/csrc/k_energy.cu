@@ -52,12 +52,23 @@ __global__ void __launch_bounds__(256) bias_finalize_kernel(const typename C2<R>
                                                             const double* __restrict__ x,
                                                             const double* __restrict__ Lbar,
                                                             typename C2<R>::t* __restrict__ cout, double* scal,
-                                                            uint8_t* __restrict__ keep, int G, double sqrt_tau) {
+                                                            uint8_t* __restrict__ keep, int G, double sqrt_tau,
+                                                            const double* __restrict__ epart,
+                                                            const int* __restrict__ from_traces) {
   __shared__ double sh[8 * 5];
   const int w = blockIdx.x;
+  // <L_g> = sum_s tr(Lh_gs Theta_s): the traces of the last measurement of these
+  // walkers (ws.epart [w][g][spin][tr re, tr im, ...]) or the force-bias GEMM
+  const bool tr = from_traces && *from_traces;
   double v[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // logI re, im, cl re, im, nfcap
   for (int g = threadIdx.x; g < G; g += 256) {
-    const cd tg = ld(t + (size_t)w * G + g);
+    cd tg;
+    if (tr) {
+      const double* q = epart + ((size_t)w * G + g) * 8;
+      tg = mk(q[0] + q[4], q[1] + q[5]);
+    } else {
+      tg = ld(t + (size_t)w * G + g);
+    }
     const double lb = Lbar[g];
     // f = -i s (t - Lbar)
     cd f = mk(sqrt_tau * tg.im, -sqrt_tau * (tg.re - lb));
@@ -377,10 +388,37 @@ inline int grid_for(size_t n) {
 // ---------------------------------------------------------------- wrappers
 template <typename R>
 cudaError_t launch_bias_finalize(const afqmc_ctx* c, int Nw, const double* x, double sqrt_tau, cudaStream_t s,
-                                 uint8_t* keep) {
+                                 uint8_t* keep, const int* from_traces) {
   bias_finalize_kernel<R><<<Nw, 256, 0, s>>>(static_cast<const typename C2<R>::t*>(c->ws.t), x, c->d_Lbar,
                                              static_cast<typename C2<R>::t*>(c->ws.c), c->ws.scal, keep, c->G,
-                                             sqrt_tau);
+                                             sqrt_tau, c->ws.epart, from_traces);
+  return cudaGetLastError();
+}
+
+// Force-bias source of the step: skip = opt_in and the traces in ws.epart are
+// those of these walkers; the key is cleared because the step changes them.
+__global__ void bias_gate_kernel(unsigned long long* key, int* skip, unsigned long long psi, int Nw, int opt_in) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    *skip = (opt_in && key[0] == psi && key[1] == (unsigned long long)Nw && psi != 0ull) ? 1 : 0;
+    key[0] = 0ull;
+    key[1] = 0ull;
+  }
+}
+
+__global__ void bias_mark_kernel(unsigned long long* key, unsigned long long psi, int Nw) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    key[0] = psi;
+    key[1] = (unsigned long long)Nw;
+  }
+}
+
+cudaError_t launch_bias_gate(const afqmc_ctx* c, const void* psi, int Nw, int opt_in, cudaStream_t s) {
+  bias_gate_kernel<<<1, 32, 0, s>>>(c->d_bias_key, c->d_bias_skip, (unsigned long long)(uintptr_t)psi, Nw, opt_in);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bias_mark(const afqmc_ctx* c, const void* psi, int Nw, cudaStream_t s) {
+  bias_mark_kernel<<<1, 32, 0, s>>>(c->d_bias_key, (unsigned long long)(uintptr_t)psi, Nw);
   return cudaGetLastError();
 }
 
@@ -509,7 +547,8 @@ cudaError_t launch_to_float(const double* a, float* b, size_t n, cudaStream_t s)
 }
 
 #define AFQ_INST(R)                                                                                         \
-  template cudaError_t launch_bias_finalize<R>(const afqmc_ctx*, int, const double*, double, cudaStream_t, uint8_t*); \
+  template cudaError_t launch_bias_finalize<R>(const afqmc_ctx*, int, const double*, double, cudaStream_t, uint8_t*, \
+                                               const int*);                                                      \
   template cudaError_t launch_normA<R>(const afqmc_ctx*, int, cudaStream_t);                                \
   template cudaError_t launch_weights<R>(const afqmc_ctx*, const afqmc_walkers*, double, double, cudaStream_t); \
   template cudaError_t launch_commit<R>(const afqmc_ctx*, const afqmc_walkers*, int, cudaStream_t);         \

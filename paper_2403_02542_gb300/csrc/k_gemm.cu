@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(NT) gemm_kernel(GemmArgs g) {
   __shared__ R sAi[ACPLX ? BK : 1][ACPLX ? BM : 1];
   __shared__ R sBr[BK][BN];
   __shared__ R sBi[BK][BN];
+  if (g.skip && *g.skip) return;
 
   const bool split = g.splitk > 1;
   const int b = split ? 0 : blockIdx.z;
@@ -169,6 +170,7 @@ __global__ void __launch_bounds__(256) walker_gemm_kernel(GemmArgs g) {
   constexpr int WM_BK = sizeof(R) == 8 ? 16 : 32;  // static shared memory stays below 48 KB
   __shared__ cplx sA[WM_BK][WM_BM];        // A[p][k] slab, p contiguous
   __shared__ cplx sX[WM_BK][8 * JT];       // X[j][k] slab, j contiguous
+  if (g.skip && *g.skip) return;
   const int w = blockIdx.y, m0 = blockIdx.x * WM_BM;
   const int N = g.M, nc = g.Nn, K = g.K;
   const int tid = threadIdx.x;
@@ -266,6 +268,7 @@ bool walker_gemm_ok(const GemmArgs& g, bool a_complex) {
 template <typename R>
 __global__ void splitk_reduce_kernel(GemmArgs g) {
   typedef typename C2<R>::t cplx;
+  if (g.skip && *g.skip) return;
   const size_t MN = (size_t)g.M * g.Nn;
   const cplx* Pp = static_cast<const cplx*>(g.part);
   cplx* C = static_cast<cplx*>(g.C);

@@ -603,6 +603,11 @@ cudaError_t tc_field_ws(afqmc_ctx* c) {
     if (e != cudaSuccess) return e;
     e = cudaMalloc(&P.v_lo, vrows * P.KA * 2);
     if (e != cudaSuccess) return e;
+    // rows 2 nc..NBp and columns 2N..KA stay zero when the Arnoldi kernels fill the planes
+    e = cudaMemset(P.v_hi, 0, vrows * P.KA * 2);
+    if (e != cudaSuccess) return e;
+    e = cudaMemset(P.v_lo, 0, vrows * P.KA * 2);
+    if (e != cudaSuccess) return e;
     if (!make_map(reinterpret_cast<CUtensorMap*>(P.map_a_hi), P.a_hi, arows, P.KA, TG_BM) ||
         !make_map(reinterpret_cast<CUtensorMap*>(P.map_a_lo), P.a_lo, arows, P.KA, TG_BM) ||
         !make_map(reinterpret_cast<CUtensorMap*>(P.map_v_hi), P.v_hi, vrows, P.KA, P.NBp) ||
@@ -676,12 +681,15 @@ cudaError_t tc_av_launch(afqmc_ctx* c, int Nw, const void* V, long long v_stride
                          long long c_stride, double alpha, cudaStream_t s) {
   TgPlan& P = c->tg;
   if (!P.av_ok || Nw > P.av_cap) return cudaErrorInvalidValue;
-  const size_t elems = (size_t)Nw * P.NBp * P.KA;
-  build_v_kernel<<<grid_for(elems), 256, 0, s>>>(static_cast<const float2*>(V), v_stride,
-                                                 static_cast<__nv_bfloat16*>(P.v_hi),
-                                                 static_cast<__nv_bfloat16*>(P.v_lo), Nw, c->N, c->nc, P.NBp, P.KA);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (V) {  // otherwise the planes already hold V (written by the Arnoldi kernels)
+    const size_t elems = (size_t)Nw * P.NBp * P.KA;
+    build_v_kernel<<<grid_for(elems), 256, 0, s>>>(static_cast<const float2*>(V), v_stride,
+                                                   static_cast<__nv_bfloat16*>(P.v_hi),
+                                                   static_cast<__nv_bfloat16*>(P.v_lo), Nw, c->N, c->nc, P.NBp, P.KA);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   AvArgs a;
   a.N = c->N;
   a.nc = c->nc;

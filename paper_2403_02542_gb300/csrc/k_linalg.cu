@@ -6,6 +6,7 @@
 //  * Arnoldi (one MGS pass) for the Krylov action of e^A (Eqs. krylovsub,
 //    projham, krylov) and the small exponential e^{A_k} e_1 (Sec. IV.C).
 // All arithmetic is FP64 whatever the storage type R of the walkers.
+#include <cuda_bf16.h>
 #include <math_constants.h>
 
 #include <type_traits>
@@ -46,8 +47,10 @@ __global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* _
                                                       const float* __restrict__ trial_f, int N, int na,
                                                       int nb, typename C2<R>::t* __restrict__ theta,
                                                       double* __restrict__ logdet,
-                                                      uint32_t* __restrict__ status) {
+                                                      uint32_t* __restrict__ status,
+                                                      const int* __restrict__ skip) {
   extern __shared__ double smem_ov[];
+  if (skip && *skip) return;
   const int w = blockIdx.x, spin = blockIdx.y;
   const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -306,10 +309,33 @@ __global__ void mgs_kernel(typename C2<R>::t* __restrict__ psi, int N, int na, i
 // ---------------------------------------------------------------- Krylov
 // One warp per orbital column (walker w, column j); columns are numbered
 // col = w * nc + j and all column vectors are contiguous [N].
+// Basis vector element p of column col = (w, j) into the split right operand
+// of the tensor-core products A V: row j = [Re v | -Im v], row nc + j =
+// [Im v | Re v] of walker w (bf16 hi/lo planes, row length KA).
+struct VPlanes {
+  __nv_bfloat16* hi = nullptr;
+  __nv_bfloat16* lo = nullptr;
+  int NBp = 0, KA = 0;
+};
+__device__ __forceinline__ void put_vplanes(const VPlanes& P, int col, int nc, int N, int p, float vr, float vi) {
+  const int w = col / nc, j = col - (col / nc) * nc;
+  const size_t ra = ((size_t)w * P.NBp + j) * P.KA, rb = ((size_t)w * P.NBp + nc + j) * P.KA;
+  const __nv_bfloat16 hr = __float2bfloat16(vr), hi = __float2bfloat16(vi);
+  const __nv_bfloat16 lr = __float2bfloat16(vr - __bfloat162float(hr)), li = __float2bfloat16(vi - __bfloat162float(hi));
+  P.hi[ra + p] = hr;
+  P.lo[ra + p] = lr;
+  P.hi[ra + N + p] = __hneg(hi);
+  P.lo[ra + N + p] = __hneg(li);
+  P.hi[rb + p] = hi;
+  P.lo[rb + p] = li;
+  P.hi[rb + N + p] = hr;
+  P.lo[rb + N + p] = lr;
+}
+
 template <typename R>
 __global__ void krylov_init_kernel(const typename C2<R>::t* __restrict__ x, typename C2<R>::t* __restrict__ v0,
                                    double* __restrict__ beta, double* __restrict__ hess, int kmax, int N,
-                                   int ncols) {
+                                   int ncols, int nc, VPlanes vp) {
   const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (col >= ncols) return;
   // the Hessenberg block starts at zero: entries below the subdiagonal are never written
@@ -323,7 +349,14 @@ __global__ void krylov_init_kernel(const typename C2<R>::t* __restrict__ x, type
   }
   const double b = sqrt((double)warp_sum(sp));
   const double inv = b > 0.0 ? 1.0 / b : 0.0;
-  for (int p = lane; p < N; p += 32) st(v0 + (size_t)col * N + p, inv * ld(X + p));
+  for (int p = lane; p < N; p += 32) {
+    const cd v = inv * ld(X + p);
+    st(v0 + (size_t)col * N + p, v);
+    if (vp.hi) {
+      const typename C2<R>::t r = v0[(size_t)col * N + p];  // the stored (rounded) value
+      put_vplanes(vp, col, nc, N, p, (float)r.x, (float)r.y);
+    }
+  }
   if (lane == 0) beta[col] = b;
 }
 
@@ -333,7 +366,7 @@ __global__ void krylov_init_kernel(const typename C2<R>::t* __restrict__ x, type
 template <typename R, int EPL>
 __global__ void krylov_orth_kernel(const typename C2<R>::t* __restrict__ wv, typename C2<R>::t* __restrict__ basis,
                                    double* __restrict__ hess, const double* __restrict__ scal, int N,
-                                   int nc, int ncols, int it, int k, int kmax, size_t bstride) {
+                                   int nc, int ncols, int it, int k, int kmax, size_t bstride, VPlanes vp) {
   typedef typename C2<R>::t cplx;
   const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (col >= ncols) return;
@@ -392,6 +425,7 @@ __global__ void krylov_orth_kernel(const typename C2<R>::t* __restrict__ wv, typ
         o.x = inv * wr[e];
         o.y = inv * wi[e];
         Vn[p] = o;
+        if (vp.hi) put_vplanes(vp, col, nc, N, p, (float)o.x, (float)o.y);
       }
     }
     if (lane == 0) { H[((it + 1) * kmax + it) * 2] = hn; H[((it + 1) * kmax + it) * 2 + 1] = 0.0; }
@@ -449,6 +483,89 @@ __global__ void krylov_expm_kernel(double* __restrict__ hess, const double* __re
   }
 }
 
+// Same exponential with H staged in shared memory as [i][j][lane] (the 32
+// columns of a warp read one entry of their own H without bank conflicts) and
+// the vectors in registers (k <= KM).  The sub-step norm bound is 4 for
+// complex64 walkers (terms to 1e-10 of the sum; the partial sums cancel at
+// most e^4 of FP64 precision) and 2 for FP64 walkers (terms to 1e-18).
+template <typename R, int KM>
+__global__ void __launch_bounds__(32) krylov_expm_smem_kernel(double* __restrict__ hess,
+                                                             const double* __restrict__ beta, int ncols, int k,
+                                                             int kmax) {
+  extern __shared__ double2 hs[];  // [k][k][32]
+  const int lane = threadIdx.x;
+  const int col0 = blockIdx.x * 32;
+  const int nb = ncols - col0 < 32 ? ncols - col0 : 32;
+  const int kk = k * k;
+  for (int e = lane; e < 32 * kk; e += 32) {
+    const int c = e / kk, r = e - (e / kk) * kk, i = r / k, j = r - (r / k) * k;
+    double2 v = make_double2(0.0, 0.0);
+    if (c < nb) v = *reinterpret_cast<const double2*>(hess + ((size_t)(col0 + c) * kmax * kmax + i * kmax + j) * 2);
+    hs[r * 32 + c] = v;
+  }
+  __syncwarp();
+  const int col = col0 + lane;
+  if (col >= ncols) return;
+  const bool f32 = std::is_same<R, float>::value;
+  double n1 = 0.0;
+  for (int j = 0; j < k; ++j) {
+    double cs = 0.0;
+    for (int i = 0; i < k; ++i) {
+      const double2 h = hs[(i * k + j) * 32 + lane];
+      cs += sqrt(h.x * h.x + h.y * h.y);
+    }
+    n1 = fmax(n1, cs);
+  }
+  const double X = f32 ? 4.0 : 2.0;
+  int m = 1;
+  if (n1 < 1e30) m = (int)ceil(n1 / X);
+  if (m < 1) m = 1;
+  if (m > 4096) m = 4096;
+  const double sc = 1.0 / m;
+  const double tol = f32 ? 1e-20 : 1e-36;  // on squared norms
+  cd v[KM], t[KM], u[KM];
+#pragma unroll
+  for (int i = 0; i < KM; ++i) v[i] = mk(i == 0 ? 1.0 : 0.0, 0.0);
+  for (int s = 0; s < m; ++s) {
+#pragma unroll
+    for (int i = 0; i < KM; ++i) t[i] = v[i];
+    for (int d = 1; d <= 60; ++d) {
+      const double f = sc / d;
+#pragma unroll
+      for (int i = 0; i < KM; ++i) {  // upper Hessenberg: H[i][j] = 0 for j < i - 1
+        cd a = mk(0.0, 0.0);
+#pragma unroll
+        for (int j = (i > 0 ? i - 1 : 0); j < KM; ++j) {
+          if (i < k && j < k) {
+            const double2 h = hs[(i * k + j) * 32 + lane];
+            a = a + mk(h.x, h.y) * t[j];
+          }
+        }
+        u[i] = f * a;
+      }
+      double tn = 0.0, an = 0.0;
+#pragma unroll
+      for (int i = 0; i < KM; ++i) {
+        if (i < k) {
+          t[i] = u[i];
+          v[i] = v[i] + u[i];
+          tn += abs2(u[i]);
+          an += abs2(v[i]);
+        }
+      }
+      if (tn <= tol * an) break;
+    }
+  }
+  double* H = hess + (size_t)col * kmax * kmax * 2;
+  const double b = beta[col];
+#pragma unroll
+  for (int i = 0; i < KM; ++i)
+    if (i < k) {
+      H[(i * kmax + 0) * 2] = b * v[i].re;
+      H[(i * kmax + 0) * 2 + 1] = b * v[i].im;
+    }
+}
+
 template <typename R>
 __global__ void krylov_combine_kernel(const double* __restrict__ hess, const typename C2<R>::t* __restrict__ basis,
                                       typename C2<R>::t* __restrict__ out, int N, int ncols, int k, int kmax,
@@ -499,7 +616,7 @@ __global__ void init_walkers_kernel(typename C2<R>::t* __restrict__ psi, const d
 
 template <typename R>
 cudaError_t launch_overlap(const afqmc_ctx* c, int Nw, const void* psi, void* theta, double* logdet,
-                           uint32_t* status, cudaStream_t s) {
+                           uint32_t* status, cudaStream_t s, const int* skip) {
   const int nmax = c->na > c->nb ? c->na : c->nb;
   const size_t shm = (size_t)(2 * nmax * nmax + nmax) * sizeof(cd);
   if (!capturing(c)) {
@@ -509,7 +626,7 @@ cudaError_t launch_overlap(const afqmc_ctx* c, int Nw, const void* psi, void* th
   overlap_kernel<R><<<dim3(Nw, 2), 256, shm, s>>>(static_cast<const typename C2<R>::t*>(psi), c->d_trial,
                                                   c->f_trial, c->N,
                                                   c->na, c->nb, static_cast<typename C2<R>::t*>(theta), logdet,
-                                                  status);
+                                                  status, skip);
   return cudaGetLastError();
 }
 
@@ -527,12 +644,26 @@ cudaError_t launch_mgs(const afqmc_ctx* c, int Nw, void* psi, const uint8_t* mas
   return cudaGetLastError();
 }
 
+// complex64 walkers with the tensor-core products A V: the Arnoldi kernels
+// also write each new basis vector into the split right operand
+template <typename R>
+VPlanes vplanes(const afqmc_ctx* c) {
+  VPlanes v;
+  if (std::is_same<R, float>::value && c->tg.av_ok) {
+    v.hi = static_cast<__nv_bfloat16*>(c->tg.v_hi);
+    v.lo = static_cast<__nv_bfloat16*>(c->tg.v_lo);
+    v.NBp = c->tg.NBp;
+    v.KA = c->tg.KA;
+  }
+  return v;
+}
+
 template <typename R>
 cudaError_t launch_krylov_init(const afqmc_ctx* c, int Nw, cudaStream_t s) {
   const int ncols = Nw * c->nc;
   krylov_init_kernel<R><<<(ncols + 7) / 8, 256, 0, s>>>(
       static_cast<const typename C2<R>::t*>(c->ws.psi_b), static_cast<typename C2<R>::t*>(c->ws.basis),
-      c->ws.beta, c->ws.hess, c->ws.kmax, c->N, ncols);
+      c->ws.beta, c->ws.hess, c->ws.kmax, c->N, ncols, c->nc, vplanes<R>(c));
   return cudaGetLastError();
 }
 
@@ -543,15 +674,16 @@ cudaError_t launch_krylov_orth(const afqmc_ctx* c, int Nw, int it, int k, cudaSt
   const typename C2<R>::t* W = static_cast<const typename C2<R>::t*>(c->ws.term0);
   typename C2<R>::t* Bs = static_cast<typename C2<R>::t*>(c->ws.basis);
   const dim3 grid((ncols + 7) / 8);
+  const VPlanes vp = vplanes<R>(c);
   if (c->N <= 128)
     krylov_orth_kernel<R, 4><<<grid, 256, 0, s>>>(W, Bs, c->ws.hess, c->ws.scal, c->N, c->nc, ncols, it, k,
-                                                  c->ws.kmax, bstride);
+                                                  c->ws.kmax, bstride, vp);
   else if (c->N <= 256)
     krylov_orth_kernel<R, 8><<<grid, 256, 0, s>>>(W, Bs, c->ws.hess, c->ws.scal, c->N, c->nc, ncols, it, k,
-                                                  c->ws.kmax, bstride);
+                                                  c->ws.kmax, bstride, vp);
   else
     krylov_orth_kernel<R, 16><<<grid, 256, 0, s>>>(W, Bs, c->ws.hess, c->ws.scal, c->N, c->nc, ncols, it, k,
-                                                   c->ws.kmax, bstride);
+                                                   c->ws.kmax, bstride, vp);
   return cudaGetLastError();
 }
 
@@ -559,7 +691,22 @@ template <typename R>
 cudaError_t launch_krylov_finish(const afqmc_ctx* c, int Nw, int k, cudaStream_t s) {
   const int ncols = Nw * c->nc;
   const size_t bstride = (size_t)c->ws.n_walkers * c->nc * c->N;
-  krylov_expm_kernel<R><<<(ncols + 127) / 128, 128, 0, s>>>(c->ws.hess, c->ws.beta, ncols, k, c->ws.kmax);
+  const size_t shm = (size_t)k * k * 32 * sizeof(double2);
+  const dim3 g32((ncols + 31) / 32);
+  if (!capturing(c) && k <= 16) {
+    cudaError_t e0 = k <= 8    ? raise_smem_limit(krylov_expm_smem_kernel<R, 8>)
+                     : k <= 12 ? raise_smem_limit(krylov_expm_smem_kernel<R, 12>)
+                               : raise_smem_limit(krylov_expm_smem_kernel<R, 16>);
+    if (e0 != cudaSuccess) return e0;
+  }
+  if (k <= 8)
+    krylov_expm_smem_kernel<R, 8><<<g32, 32, shm, s>>>(c->ws.hess, c->ws.beta, ncols, k, c->ws.kmax);
+  else if (k <= 12)
+    krylov_expm_smem_kernel<R, 12><<<g32, 32, shm, s>>>(c->ws.hess, c->ws.beta, ncols, k, c->ws.kmax);
+  else if (k <= 16)
+    krylov_expm_smem_kernel<R, 16><<<g32, 32, shm, s>>>(c->ws.hess, c->ws.beta, ncols, k, c->ws.kmax);
+  else
+    krylov_expm_kernel<R><<<(ncols + 127) / 128, 128, 0, s>>>(c->ws.hess, c->ws.beta, ncols, k, c->ws.kmax);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   krylov_combine_kernel<R><<<(ncols + 7) / 8, 256, 0, s>>>(
@@ -580,14 +727,18 @@ cudaError_t launch_init_walkers(const afqmc_ctx* c, const afqmc_walkers* w, cuda
 
 template <typename R>
 cudaError_t prepare_overlap(const afqmc_ctx*) {
-  return raise_smem_limit(overlap_kernel<R>);
+  cudaError_t e = raise_smem_limit(overlap_kernel<R>);
+  if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_smem_kernel<R, 8>);
+  if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_smem_kernel<R, 12>);
+  if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_smem_kernel<R, 16>);
+  return e;
 }
 template cudaError_t prepare_overlap<double>(const afqmc_ctx*);
 template cudaError_t prepare_overlap<float>(const afqmc_ctx*);
 
 #define AFQ_INST(R)                                                                                       \
   template cudaError_t launch_overlap<R>(const afqmc_ctx*, int, const void*, void*, double*, uint32_t*,   \
-                                         cudaStream_t);                                                    \
+                                         cudaStream_t, const int*);                                        \
   template cudaError_t launch_mgs<R>(const afqmc_ctx*, int, void*, const uint8_t*, cudaStream_t);          \
   template cudaError_t launch_krylov_init<R>(const afqmc_ctx*, int, cudaStream_t);                         \
   template cudaError_t launch_krylov_orth<R>(const afqmc_ctx*, int, int, int, cudaStream_t);               \

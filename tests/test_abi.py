@@ -80,7 +80,7 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.afqmc_sync(None) == L.AFQMC_EINVAL
     assert lib.afqmc_launch_count(None) == 0
     lib.afqmc_destroy(None)
-    p = L.StepParams(0.1, 0.0, 0, 0, 4, 0, 0)
+    p = L.StepParams(0.1, 0.0, 0, 0, 4, 0, 0, 0)
     w = L.Walkers(1, None, None, None, None)
     assert lib.afqmc_step(None, ctypes.byref(w), None, ctypes.byref(p), None, None) == L.AFQMC_EINVAL
 

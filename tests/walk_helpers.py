@@ -56,7 +56,7 @@ def oracle_walk(sys_, nw, steps, tau, e0, expm, order, reortho_every, seed, dead
 
 
 def gpu_walk(ctx, nw, steps, tau, e0, expm, order, reortho_every, seed, dead=(), record=None,
-             state=None, field_fn=None):
+             state=None, field_fn=None, reuse_bias=False):
     """record: set of step indices to copy back (default: all)."""
     w = ctx.new_walkers(nw)
     if state is None:
@@ -76,7 +76,7 @@ def gpu_walk(ctx, nw, steps, tau, e0, expm, order, reortho_every, seed, dead=(),
         x = torch.as_tensor(np.ascontiguousarray(x), device=ctx.device)
         reo = reortho_every > 0 and (k + 1) % reortho_every == 0
         ctx.step(w, x, tau, e0, expm=expm, order=order, reortho=reo, measure=True,
-                 e_loc=e_loc, e_mix=e_mix)
+                 e_loc=e_loc, e_mix=e_mix, reuse_bias=reuse_bias)
         if record is None or k in record:
             torch.cuda.synchronize()
             out.append(dict(k=k, psi=w.psi.cpu().to(torch.complex128).transpose(1, 2).contiguous(),
