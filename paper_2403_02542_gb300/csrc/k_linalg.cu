@@ -332,46 +332,57 @@ __device__ __forceinline__ void put_vplanes(const VPlanes& P, int col, int nc, i
   P.lo[rb + N + p] = lr;
 }
 
+// Hessenberg storage: entry (column col, row i, column j) of H_k at
+// hess[(i * kmax + j) * hs + col] in the walkers' complex storage type (hs =
+// column capacity), so that per-column threads of the small exponential read
+// one entry of many columns contiguously.  Complex64 walkers: the inner
+// products come from FP32 data and are stored in FP32; the small exponential
+// runs in FP64 and its result y is stored back in FP32.
+
 template <typename R>
 __global__ void krylov_init_kernel(const typename C2<R>::t* __restrict__ x, typename C2<R>::t* __restrict__ v0,
-                                   double* __restrict__ beta, double* __restrict__ hess, int kmax, int N,
-                                   int ncols, int nc, VPlanes vp) {
+                                   double* __restrict__ beta, typename C2<R>::t* __restrict__ hess, size_t hs,
+                                   int kmax, int N, int ncols, int nc, VPlanes vp) {
+  typedef typename C2<R>::t cplx;
   const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (col >= ncols) return;
   // the Hessenberg block starts at zero: entries below the subdiagonal are never written
-  double* H = hess + (size_t)col * kmax * kmax * 2;
-  for (int e = lane; e < kmax * kmax * 2; e += 32) H[e] = 0.0;
-  const typename C2<R>::t* X = x + (size_t)col * N;
+  for (int e = lane; e < kmax * kmax; e += 32) {
+    cplx z;
+    z.x = R(0);
+    z.y = R(0);
+    hess[(size_t)e * hs + col] = z;
+  }
+  const cplx* X = x + (size_t)col * N;
   R sp = R(0);
   for (int p = lane; p < N; p += 32) {
-    const typename C2<R>::t v = X[p];
+    const cplx v = X[p];
     sp += v.x * v.x + v.y * v.y;
   }
-  const double b = sqrt((double)warp_sum(sp));
-  const double inv = b > 0.0 ? 1.0 / b : 0.0;
+  const R b = sqrt(warp_sum(sp));
+  const R inv = b > R(0) ? R(1) / b : R(0);
   for (int p = lane; p < N; p += 32) {
-    const cd v = inv * ld(X + p);
-    st(v0 + (size_t)col * N + p, v);
-    if (vp.hi) {
-      const typename C2<R>::t r = v0[(size_t)col * N + p];  // the stored (rounded) value
-      put_vplanes(vp, col, nc, N, p, (float)r.x, (float)r.y);
-    }
+    cplx v = X[p];
+    v.x *= inv;
+    v.y *= inv;
+    v0[(size_t)col * N + p] = v;
+    if (vp.hi) put_vplanes(vp, col, nc, N, p, (float)v.x, (float)v.y);
   }
-  if (lane == 0) beta[col] = b;
+  if (lane == 0) beta[col] = (double)b;
 }
 
 // Step `it` of Arnoldi: w = A b_it is in `wv`; MGS against b_0..b_it, then the
 // next basis vector (or zero after an invariant subspace was found).  One warp
 // per column; w lives in registers (EPL elements per lane, N <= 32 * EPL).
+// All arithmetic in the walkers' precision.
 template <typename R, int EPL>
 __global__ void krylov_orth_kernel(const typename C2<R>::t* __restrict__ wv, typename C2<R>::t* __restrict__ basis,
-                                   double* __restrict__ hess, const double* __restrict__ scal, int N,
-                                   int nc, int ncols, int it, int k, int kmax, size_t bstride, VPlanes vp) {
+                                   typename C2<R>::t* __restrict__ hess, size_t hs, const double* __restrict__ scal,
+                                   int N, int nc, int ncols, int it, int k, int kmax, size_t bstride, VPlanes vp) {
   typedef typename C2<R>::t cplx;
   const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (col >= ncols) return;
   const cplx* W = wv + (size_t)col * N;
-  double* H = hess + (size_t)col * kmax * kmax * 2;  // H[i][j] at (i*kmax + j)*2
   R wr[EPL], wi[EPL];
 #pragma unroll
   for (int e = 0; e < EPL; ++e) {
@@ -387,7 +398,7 @@ __global__ void krylov_orth_kernel(const typename C2<R>::t* __restrict__ wv, typ
   for (int i = 0; i <= it; ++i) {
     const cplx* V = basis + i * bstride + (size_t)col * N;
     cplx vv[EPL];
-    R pr = R(0), pi = R(0);  // lane partial of b_i^H w (FP32 lanes for complex64 walkers)
+    R pr = R(0), pi = R(0);  // lane partial of b_i^H w
 #pragma unroll
     for (int e = 0; e < EPL; ++e) {
       const int p = lane + 32 * e;
@@ -397,25 +408,28 @@ __global__ void krylov_orth_kernel(const typename C2<R>::t* __restrict__ wv, typ
       pr += vv[e].x * wr[e] + vv[e].y * wi[e];
       pi += vv[e].x * wi[e] - vv[e].y * wr[e];
     }
-    const double dr = (double)warp_sum(pr), di = (double)warp_sum(pi);
-    const R hr = (R)dr, hi = (R)di;
+    const R hr = warp_sum(pr), hi = warp_sum(pi);
 #pragma unroll
     for (int e = 0; e < EPL; ++e) {
       wr[e] -= hr * vv[e].x - hi * vv[e].y;
       wi[e] -= hr * vv[e].y + hi * vv[e].x;
     }
-    if (lane == 0) { H[(i * kmax + it) * 2] = dr; H[(i * kmax + it) * 2 + 1] = di; }
+    if (lane == 0) {
+      cplx h;
+      h.x = hr;
+      h.y = hi;
+      hess[(size_t)(i * kmax + it) * hs + col] = h;
+    }
   }
   if (it + 1 < k) {
     R ps = R(0);
 #pragma unroll
     for (int e = 0; e < EPL; ++e) ps += wr[e] * wr[e] + wi[e] * wi[e];
-    const double s = (double)warp_sum(ps);
-    double hn = sqrt(s);
-    const double normA = scal[(size_t)(col / nc) * SC_COUNT + SC_NORMA];
-    const bool brk = !(hn > 1e-12 * normA);
-    const R inv = brk ? R(0) : (R)(1.0 / hn);
-    if (brk) hn = 0.0;
+    R hn = sqrt(warp_sum(ps));
+    const R thr = (R)(1e-12 * scal[(size_t)(col / nc) * SC_COUNT + SC_NORMA]);
+    const bool brk = !(hn > thr);
+    const R inv = brk ? R(0) : R(1) / hn;
+    if (brk) hn = R(0);
     cplx* Vn = basis + (it + 1) * bstride + (size_t)col * N;
 #pragma unroll
     for (int e = 0; e < EPL; ++e) {
@@ -428,94 +442,54 @@ __global__ void krylov_orth_kernel(const typename C2<R>::t* __restrict__ wv, typ
         if (vp.hi) put_vplanes(vp, col, nc, N, p, (float)o.x, (float)o.y);
       }
     }
-    if (lane == 0) { H[((it + 1) * kmax + it) * 2] = hn; H[((it + 1) * kmax + it) * 2 + 1] = 0.0; }
-  }
-}
-
-// y = beta e^{H_k} e_1 by sub-stepping: (e^{H/m})^m e_1, each factor a Taylor
-// series on the vector summed until its terms fall below 1e-18 of the sum
-// (m chosen so that ||H/m||_1 <= 1).  Then psi_out = B_k y.
-// One thread per column for the small exponential; then a warp per column.
-template <typename R>
-__global__ void krylov_expm_kernel(double* __restrict__ hess, const double* __restrict__ beta, int ncols,
-                                   int k, int kmax) {
-  const int col = blockIdx.x * blockDim.x + threadIdx.x;
-  if (col >= ncols) return;
-  double* H = hess + (size_t)col * kmax * kmax * 2;
-  cd v[32], t[32], u[32];
-  double n1 = 0.0;
-  for (int j = 0; j < k; ++j) {
-    double cs = 0.0;
-    for (int i = 0; i < k; ++i) cs += sqrt(abs2(mk(H[(i * kmax + j) * 2], H[(i * kmax + j) * 2 + 1])));
-    n1 = fmax(n1, cs);
-  }
-  int m = (int)ceil(n1);
-  if (m < 1) m = 1;
-  if (m > 4096) m = 4096;
-  const double sc = 1.0 / m;
-  for (int i = 0; i < k; ++i) v[i] = mk(i == 0 ? 1.0 : 0.0, 0.0);
-  for (int s = 0; s < m; ++s) {
-    for (int i = 0; i < k; ++i) { t[i] = v[i]; }
-    for (int d = 1; d <= 40; ++d) {
-      double tn = 0.0, an = 0.0;
-      for (int i = 0; i < k; ++i) {  // upper Hessenberg: H[i][j] = 0 for j < i - 1
-        cd a = mk(0.0, 0.0);
-        for (int j = (i > 0 ? i - 1 : 0); j < k; ++j)
-          a = a + mk(H[(i * kmax + j) * 2], H[(i * kmax + j) * 2 + 1]) * t[j];
-        u[i] = (sc / d) * a;
-      }
-      for (int i = 0; i < k; ++i) {
-        t[i] = u[i];
-        v[i] = v[i] + u[i];
-        tn += abs2(u[i]);
-        an += abs2(v[i]);
-      }
-      // complex64 walkers carry ~1e-7 relative error: terms below 1e-10 of the sum
-      // are dropped there; FP64 walkers sum to 1e-18
-      if (tn <= (std::is_same<R, float>::value ? 1e-20 : 1e-36) * an) break;
+    if (lane == 0) {
+      cplx h;
+      h.x = hn;
+      h.y = R(0);
+      hess[(size_t)((it + 1) * kmax + it) * hs + col] = h;
     }
   }
-  // store y in column 0 of H (no longer needed)
-  const double b = beta[col];
-  for (int i = 0; i < k; ++i) {
-    H[(i * kmax + 0) * 2] = b * v[i].re;
-    H[(i * kmax + 0) * 2 + 1] = b * v[i].im;
-  }
 }
 
-// Same exponential with H staged in shared memory as [i][j][lane] (the 32
-// columns of a warp read one entry of their own H without bank conflicts) and
-// the vectors in registers (k <= KM).  The sub-step norm bound is 4 for
-// complex64 walkers (terms to 1e-10 of the sum; the partial sums cancel at
-// most e^4 of FP64 precision) and 2 for FP64 walkers (terms to 1e-18).
-template <typename R, int KM>
-__global__ void __launch_bounds__(32) krylov_expm_smem_kernel(double* __restrict__ hess,
-                                                             const double* __restrict__ beta, int ncols, int k,
-                                                             int kmax) {
-  extern __shared__ double2 hs[];  // [k][k][32]
-  const int lane = threadIdx.x;
-  const int col0 = blockIdx.x * 32;
-  const int nb = ncols - col0 < 32 ? ncols - col0 : 32;
-  const int kk = k * k;
-  for (int e = lane; e < 32 * kk; e += 32) {
-    const int c = e / kk, r = e - (e / kk) * kk, i = r / k, j = r - (r / k) * k;
-    double2 v = make_double2(0.0, 0.0);
-    if (c < nb) v = *reinterpret_cast<const double2*>(hess + ((size_t)(col0 + c) * kmax * kmax + i * kmax + j) * 2);
-    hs[r * 32 + c] = v;
-  }
-  __syncwarp();
-  const int col = col0 + lane;
-  if (col >= ncols) return;
-  const bool f32 = std::is_same<R, float>::value;
+// y = beta e^{H_k} e_1 in FP64 by sub-stepping: (e^{H/m})^m e_1, each factor
+// a Taylor series on the vector summed until its terms fall below a relative
+// 1e-10 (complex64 walkers) or 1e-18 (FP64 walkers) of the sum; m chosen so
+// that ||H/m||_1 <= 4 (complex64; the partial sums cancel at most e^4 of FP64
+// precision) or <= 2 (FP64).  One thread per column: the nonzero (upper
+// Hessenberg) entries of its H are staged once in shared memory as FP64, the
+// vectors live in registers (k <= KM).  y overwrites column 0 of H.  SM =
+// false (large k): H is read from global memory at every use instead.
+template <typename R, int KM, bool SM>
+__global__ void __launch_bounds__(64) krylov_expm_kernel(typename C2<R>::t* __restrict__ hess, size_t hs,
+                                                         const double* __restrict__ beta, int ncols, int k,
+                                                         int kmax) {
+  extern __shared__ double2 hsm[];  // [npk][64]: packed rows i, columns j >= max(i - 1, 0)
+  const int t = threadIdx.x;
+  const int col = blockIdx.x * 64 + t;
+  const bool active = col < ncols;
+  // packed offset of row i: row 0 has k entries, row i >= 1 has k - i + 1
   double n1 = 0.0;
-  for (int j = 0; j < k; ++j) {
-    double cs = 0.0;
+  if (active) {
+    double cs[KM];
+#pragma unroll
+    for (int j = 0; j < KM; ++j) cs[j] = 0.0;
+    int o = 0;
     for (int i = 0; i < k; ++i) {
-      const double2 h = hs[(i * k + j) * 32 + lane];
-      cs += sqrt(h.x * h.x + h.y * h.y);
+      const int j0 = i > 0 ? i - 1 : 0;
+      for (int j = j0; j < k; ++j, ++o) {
+        const typename C2<R>::t h = hess[(size_t)(i * kmax + j) * hs + col];
+        const double2 hd = make_double2((double)h.x, (double)h.y);
+        if (SM) hsm[o * 64 + t] = hd;
+#pragma unroll
+        for (int jj = 0; jj < KM; ++jj)
+          if (jj == j) cs[jj] += sqrt(hd.x * hd.x + hd.y * hd.y);
+      }
     }
-    n1 = fmax(n1, cs);
+#pragma unroll
+    for (int j = 0; j < KM; ++j) n1 = fmax(n1, cs[j]);
   }
+  if (!active) return;  // no block-wide synchronisation below: each thread reads only its own entries
+  const bool f32 = std::is_same<R, float>::value;
   const double X = f32 ? 4.0 : 2.0;
   int m = 1;
   if (n1 < 1e30) m = (int)ceil(n1 / X);
@@ -523,23 +497,33 @@ __global__ void __launch_bounds__(32) krylov_expm_smem_kernel(double* __restrict
   if (m > 4096) m = 4096;
   const double sc = 1.0 / m;
   const double tol = f32 ? 1e-20 : 1e-36;  // on squared norms
-  cd v[KM], t[KM], u[KM];
+  cd v[KM], tv[KM], u[KM];
 #pragma unroll
   for (int i = 0; i < KM; ++i) v[i] = mk(i == 0 ? 1.0 : 0.0, 0.0);
   for (int s = 0; s < m; ++s) {
 #pragma unroll
-    for (int i = 0; i < KM; ++i) t[i] = v[i];
+    for (int i = 0; i < KM; ++i) tv[i] = v[i];
     for (int d = 1; d <= 60; ++d) {
       const double f = sc / d;
+      int o = 0;
 #pragma unroll
-      for (int i = 0; i < KM; ++i) {  // upper Hessenberg: H[i][j] = 0 for j < i - 1
+      for (int i = 0; i < KM; ++i) {
         cd a = mk(0.0, 0.0);
+        if (i < k) {
 #pragma unroll
-        for (int j = (i > 0 ? i - 1 : 0); j < KM; ++j) {
-          if (i < k && j < k) {
-            const double2 h = hs[(i * k + j) * 32 + lane];
-            a = a + mk(h.x, h.y) * t[j];
+          for (int j = (i > 0 ? i - 1 : 0); j < KM; ++j) {
+            if (j < k) {
+              double2 h;
+              if (SM) {
+                h = hsm[(o + j - (i > 0 ? i - 1 : 0)) * 64 + t];
+              } else {
+                const typename C2<R>::t hh = hess[(size_t)(i * kmax + j) * hs + col];
+                h = make_double2((double)hh.x, (double)hh.y);
+              }
+              a = a + mk(h.x, h.y) * tv[j];
+            }
           }
+          o += k - (i > 0 ? i - 1 : 0);
         }
         u[i] = f * a;
       }
@@ -547,7 +531,7 @@ __global__ void __launch_bounds__(32) krylov_expm_smem_kernel(double* __restrict
 #pragma unroll
       for (int i = 0; i < KM; ++i) {
         if (i < k) {
-          t[i] = u[i];
+          tv[i] = u[i];
           v[i] = v[i] + u[i];
           tn += abs2(u[i]);
           an += abs2(v[i]);
@@ -556,43 +540,37 @@ __global__ void __launch_bounds__(32) krylov_expm_smem_kernel(double* __restrict
       if (tn <= tol * an) break;
     }
   }
-  double* H = hess + (size_t)col * kmax * kmax * 2;
   const double b = beta[col];
 #pragma unroll
   for (int i = 0; i < KM; ++i)
     if (i < k) {
-      H[(i * kmax + 0) * 2] = b * v[i].re;
-      H[(i * kmax + 0) * 2 + 1] = b * v[i].im;
+      typename C2<R>::t y;
+      y.x = (R)(b * v[i].re);
+      y.y = (R)(b * v[i].im);
+      hess[(size_t)(i * kmax) * hs + col] = y;
     }
 }
 
+// psi_out = B_k y: out = sum_i y_i b_i in the walkers' precision (y from column 0 of H)
 template <typename R>
-__global__ void krylov_combine_kernel(const double* __restrict__ hess, const typename C2<R>::t* __restrict__ basis,
-                                      typename C2<R>::t* __restrict__ out, int N, int ncols, int k, int kmax,
-                                      size_t bstride) {
+__global__ void krylov_combine_kernel(const typename C2<R>::t* __restrict__ hess, size_t hs,
+                                      const typename C2<R>::t* __restrict__ basis, typename C2<R>::t* __restrict__ out,
+                                      int N, int ncols, int k, int kmax, size_t bstride) {
+  typedef typename C2<R>::t cplx;
   const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (col >= ncols) return;
-  const double* H = hess + (size_t)col * kmax * kmax * 2;
-  if constexpr (std::is_same<R, float>::value) {  // complex64: y rounded, FP32 sum
-    for (int p = lane; p < N; p += 32) {
-      float sr = 0.f, si = 0.f;
-      for (int i = 0; i < k; ++i) {
-        const float yr = (float)H[(i * kmax) * 2], yi = (float)H[(i * kmax) * 2 + 1];
-        const float2 v = basis[i * bstride + (size_t)col * N + p];
-        sr += yr * v.x - yi * v.y;
-        si += yr * v.y + yi * v.x;
-      }
-      out[(size_t)col * N + p] = make_float2(sr, si);
+  for (int p = lane; p < N; p += 32) {
+    R sr = R(0), si = R(0);
+    for (int i = 0; i < k; ++i) {
+      const cplx y = hess[(size_t)(i * kmax) * hs + col];
+      const cplx v = basis[i * bstride + (size_t)col * N + p];
+      sr += y.x * v.x - y.y * v.y;
+      si += y.x * v.y + y.y * v.x;
     }
-  } else {
-    for (int p = lane; p < N; p += 32) {
-      cd s = mk(0.0, 0.0);
-      for (int i = 0; i < k; ++i) {
-        const cd y = mk(H[(i * kmax) * 2], H[(i * kmax) * 2 + 1]);
-        s = s + y * ld(basis + i * bstride + (size_t)col * N + p);
-      }
-      st(out + (size_t)col * N + p, s);
-    }
+    cplx o;
+    o.x = sr;
+    o.y = si;
+    out[(size_t)col * N + p] = o;
   }
 }
 
@@ -661,9 +639,11 @@ VPlanes vplanes(const afqmc_ctx* c) {
 template <typename R>
 cudaError_t launch_krylov_init(const afqmc_ctx* c, int Nw, cudaStream_t s) {
   const int ncols = Nw * c->nc;
+  const size_t hs = (size_t)c->ws.n_walkers * c->nc;
   krylov_init_kernel<R><<<(ncols + 7) / 8, 256, 0, s>>>(
       static_cast<const typename C2<R>::t*>(c->ws.psi_b), static_cast<typename C2<R>::t*>(c->ws.basis),
-      c->ws.beta, c->ws.hess, c->ws.kmax, c->N, ncols, c->nc, vplanes<R>(c));
+      c->ws.beta, reinterpret_cast<typename C2<R>::t*>(c->ws.hess), hs, c->ws.kmax, c->N, ncols, c->nc,
+      vplanes<R>(c));
   return cudaGetLastError();
 }
 
@@ -671,19 +651,42 @@ template <typename R>
 cudaError_t launch_krylov_orth(const afqmc_ctx* c, int Nw, int it, int k, cudaStream_t s) {
   const int ncols = Nw * c->nc;
   const size_t bstride = (size_t)c->ws.n_walkers * c->nc * c->N;
+  const size_t hs = (size_t)c->ws.n_walkers * c->nc;
   const typename C2<R>::t* W = static_cast<const typename C2<R>::t*>(c->ws.term0);
   typename C2<R>::t* Bs = static_cast<typename C2<R>::t*>(c->ws.basis);
+  typename C2<R>::t* H = reinterpret_cast<typename C2<R>::t*>(c->ws.hess);
   const dim3 grid((ncols + 7) / 8);
   const VPlanes vp = vplanes<R>(c);
   if (c->N <= 128)
-    krylov_orth_kernel<R, 4><<<grid, 256, 0, s>>>(W, Bs, c->ws.hess, c->ws.scal, c->N, c->nc, ncols, it, k,
-                                                  c->ws.kmax, bstride, vp);
+    krylov_orth_kernel<R, 4><<<grid, 256, 0, s>>>(W, Bs, H, hs, c->ws.scal, c->N, c->nc, ncols, it, k, c->ws.kmax,
+                                                  bstride, vp);
   else if (c->N <= 256)
-    krylov_orth_kernel<R, 8><<<grid, 256, 0, s>>>(W, Bs, c->ws.hess, c->ws.scal, c->N, c->nc, ncols, it, k,
-                                                  c->ws.kmax, bstride, vp);
+    krylov_orth_kernel<R, 8><<<grid, 256, 0, s>>>(W, Bs, H, hs, c->ws.scal, c->N, c->nc, ncols, it, k, c->ws.kmax,
+                                                  bstride, vp);
   else
-    krylov_orth_kernel<R, 16><<<grid, 256, 0, s>>>(W, Bs, c->ws.hess, c->ws.scal, c->N, c->nc, ncols, it, k,
+    krylov_orth_kernel<R, 16><<<grid, 256, 0, s>>>(W, Bs, H, hs, c->ws.scal, c->N, c->nc, ncols, it, k,
                                                    c->ws.kmax, bstride, vp);
+  return cudaGetLastError();
+}
+
+// packed upper-Hessenberg entries of a k x k matrix
+inline int hess_packed(int k) { return k + k * (k + 1) / 2 - 1; }
+
+template <typename R, int KM>
+cudaError_t expm_launch(const afqmc_ctx* c, int ncols, int k, cudaStream_t s) {
+  typename C2<R>::t* H = reinterpret_cast<typename C2<R>::t*>(c->ws.hess);
+  const size_t hs = (size_t)c->ws.n_walkers * c->nc;
+  const size_t shm = (size_t)hess_packed(k) * 64 * sizeof(double2);
+  const dim3 grid((ncols + 63) / 64);
+  if (shm <= (size_t)max_dyn_smem()) {
+    if (!capturing(c)) {
+      cudaError_t e = raise_smem_limit(krylov_expm_kernel<R, KM, true>);
+      if (e != cudaSuccess) return e;
+    }
+    krylov_expm_kernel<R, KM, true><<<grid, 64, shm, s>>>(H, hs, c->ws.beta, ncols, k, c->ws.kmax);
+  } else {
+    krylov_expm_kernel<R, KM, false><<<grid, 64, 0, s>>>(H, hs, c->ws.beta, ncols, k, c->ws.kmax);
+  }
   return cudaGetLastError();
 }
 
@@ -691,27 +694,16 @@ template <typename R>
 cudaError_t launch_krylov_finish(const afqmc_ctx* c, int Nw, int k, cudaStream_t s) {
   const int ncols = Nw * c->nc;
   const size_t bstride = (size_t)c->ws.n_walkers * c->nc * c->N;
-  const size_t shm = (size_t)k * k * 32 * sizeof(double2);
-  const dim3 g32((ncols + 31) / 32);
-  if (!capturing(c) && k <= 16) {
-    cudaError_t e0 = k <= 8    ? raise_smem_limit(krylov_expm_smem_kernel<R, 8>)
-                     : k <= 12 ? raise_smem_limit(krylov_expm_smem_kernel<R, 12>)
-                               : raise_smem_limit(krylov_expm_smem_kernel<R, 16>);
-    if (e0 != cudaSuccess) return e0;
-  }
-  if (k <= 8)
-    krylov_expm_smem_kernel<R, 8><<<g32, 32, shm, s>>>(c->ws.hess, c->ws.beta, ncols, k, c->ws.kmax);
-  else if (k <= 12)
-    krylov_expm_smem_kernel<R, 12><<<g32, 32, shm, s>>>(c->ws.hess, c->ws.beta, ncols, k, c->ws.kmax);
-  else if (k <= 16)
-    krylov_expm_smem_kernel<R, 16><<<g32, 32, shm, s>>>(c->ws.hess, c->ws.beta, ncols, k, c->ws.kmax);
-  else
-    krylov_expm_kernel<R><<<(ncols + 127) / 128, 128, 0, s>>>(c->ws.hess, c->ws.beta, ncols, k, c->ws.kmax);
-  cudaError_t e = cudaGetLastError();
+  const size_t hs = (size_t)c->ws.n_walkers * c->nc;
+  cudaError_t e = k <= 8 ? expm_launch<R, 8>(c, ncols, k, s)
+                  : k <= 12 ? expm_launch<R, 12>(c, ncols, k, s)
+                  : k <= 16 ? expm_launch<R, 16>(c, ncols, k, s)
+                            : expm_launch<R, 32>(c, ncols, k, s);
   if (e != cudaSuccess) return e;
   krylov_combine_kernel<R><<<(ncols + 7) / 8, 256, 0, s>>>(
-      c->ws.hess, static_cast<const typename C2<R>::t*>(c->ws.basis), static_cast<typename C2<R>::t*>(c->ws.acc),
-      c->N, ncols, k, c->ws.kmax, bstride);
+      reinterpret_cast<const typename C2<R>::t*>(c->ws.hess), hs,
+      static_cast<const typename C2<R>::t*>(c->ws.basis), static_cast<typename C2<R>::t*>(c->ws.acc), c->N, ncols, k,
+      c->ws.kmax, bstride);
   return cudaGetLastError();
 }
 
@@ -728,9 +720,10 @@ cudaError_t launch_init_walkers(const afqmc_ctx* c, const afqmc_walkers* w, cuda
 template <typename R>
 cudaError_t prepare_overlap(const afqmc_ctx*) {
   cudaError_t e = raise_smem_limit(overlap_kernel<R>);
-  if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_smem_kernel<R, 8>);
-  if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_smem_kernel<R, 12>);
-  if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_smem_kernel<R, 16>);
+  if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_kernel<R, 8, true>);
+  if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_kernel<R, 12, true>);
+  if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_kernel<R, 16, true>);
+  if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_kernel<R, 32, true>);
   return e;
 }
 template cudaError_t prepare_overlap<double>(const afqmc_ctx*);
