@@ -48,6 +48,9 @@ struct TcArgs {
   int* err;
 };
 
+// NM > 0: n <= NM and each epilogue thread keeps its own accumulator row in
+// registers; NM == 0: the row is read back from shared memory.
+template <int NM>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     exchange_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                        const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
@@ -215,46 +218,66 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         for (int wl = ewg; wl < p.Wc; wl += TC_EPI_WG) {
           const int w = wg * p.Wc + wl;
           if (w >= p.Nw) break;
-          // this walker's 2n accumulator columns: Re T[i][0..n), Im T[i][0..n)
+          // this walker's 2n accumulator columns: (Re T[i][j], Im T[i][j]) for j = 0..n-1
           const uint32_t col0 = (uint32_t)(buf * p.NB + wl * two_n);
-          for (int c0 = 0; c0 < two_n; c0 += 8) {
-            uint32_t v[8];
-            tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + col0 + (uint32_t)c0, v);
+          const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + col0;
+          float rr[NM > 0 ? 2 * NM : 1];
+          if constexpr (NM > 0) {
+#pragma unroll
+            for (int c0 = 0; c0 < 2 * NM; c0 += 8)
+              if (c0 < two_n) tmem_ld8(tl + (uint32_t)c0, reinterpret_cast<uint32_t*>(rr + c0));
             tmem_wait_ld();
 #pragma unroll
-            for (int e = 0; e < 8; ++e)
-              if (c0 + e < two_n) st[r * SP + c0 + e] = __uint_as_float(v[e]);
+            for (int c = 0; c < 2 * NM; ++c)
+              if (c < two_n) st[r * SP + c] = rr[c];
+          } else {
+            for (int c0 = 0; c0 < two_n; c0 += 8) {
+              uint32_t v[8];
+              tmem_ld8(tl + (uint32_t)c0, v);
+              tmem_wait_ld();
+#pragma unroll
+              for (int e = 0; e < 8; ++e)
+                if (c0 + e < two_n) st[r * SP + c0 + e] = __uint_as_float(v[e]);
+            }
           }
           named_bar(bar_id, 128);
           float tr = 0.f, ti = 0.f, er = 0.f, ei = 0.f;
           if (valid) {
-            tr = st[r * SP + i];
-            ti = st[r * SP + n + i];
-            const int rb = gl * n;  // first row of this g block
-            for (int j = 0; j < n; ++j) {
-              const float ar = st[r * SP + j], ai = st[r * SP + n + j];              // T_ij
-              const float br = st[(rb + j) * SP + i], bi = st[(rb + j) * SP + n + i];  // T_ji
-              er = fmaf(ar, br, er);
-              er = fmaf(-ai, bi, er);
-              ei = fmaf(ar, bi, ei);
-              ei = fmaf(ai, br, ei);
+            tr = st[r * SP + 2 * i];
+            ti = st[r * SP + 2 * i + 1];
+            const float* tcol = st + (size_t)(gl * n) * SP + 2 * i;  // T[j][i] at tcol[j * SP]
+            if constexpr (NM > 0) {
+#pragma unroll
+              for (int j = 0; j < NM; ++j) {
+                if (j < n) {
+                  const float ar = rr[2 * j], ai = rr[2 * j + 1];          // T_ij
+                  const float br = tcol[j * SP], bi = tcol[j * SP + 1];   // T_ji
+                  er = fmaf(ar, br, er);
+                  er = fmaf(-ai, bi, er);
+                  ei = fmaf(ar, bi, ei);
+                  ei = fmaf(ai, br, ei);
+                }
+              }
+            } else {
+              for (int j = 0; j < n; ++j) {
+                const float ar = st[r * SP + 2 * j], ai = st[r * SP + 2 * j + 1];
+                const float br = tcol[j * SP], bi = tcol[j * SP + 1];
+                er = fmaf(ar, br, er);
+                er = fmaf(-ai, bi, er);
+                ei = fmaf(ar, bi, ei);
+                ei = fmaf(ai, br, ei);
+              }
             }
           }
-          pb[r * 4 + 0] = tr;
-          pb[r * 4 + 1] = ti;
-          pb[r * 4 + 2] = er;
-          pb[r * 4 + 3] = ei;
+          reinterpret_cast<float4*>(pb)[r] = make_float4(tr, ti, er, ei);
           named_bar(bar_id, 128);
-          if (r < p.gpt) {  // one thread per g block sums its n rows in fixed order
-            const int gg = (int)t * p.gpt + r;
+          for (int x = r; x < 4 * p.gpt; x += 128) {  // (g block, quantity): sum of its n rows in fixed order
+            const int gb = x >> 2, qn = x & 3;
+            const int gg = (int)t * p.gpt + gb;
             if (gg < p.G) {
-              float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
-              for (int ii = 0; ii < n; ++ii) {
-                const float* q = pb + (r * n + ii) * 4;
-                s0 += q[0]; s1 += q[1]; s2 += q[2]; s3 += q[3];
-              }
-              double* o = p.epart + (((size_t)w * p.G + gg) * 2 + spin) * 4;
-              o[0] = s0; o[1] = s1; o[2] = s2; o[3] = s3;
+              float sum = 0.f;
+              for (int ii = 0; ii < n; ++ii) sum += pb[(gb * n + ii) * 4 + qn];
+              p.epart[(((size_t)w * p.G + gg) * 2 + spin) * 4 + qn] = sum;
             }
           }
           named_bar(bar_id, 128);
@@ -293,15 +316,15 @@ __global__ void build_lh_tiles_kernel(const double* __restrict__ Lh, __nv_bfloat
   }
 }
 
-// B operand: [2 spins][Nw][re,im][n][Kp] from Theta[Nw][nc][N] (complex64).
+// B operand: [2 spins][Nw][n][re,im][Kp] from Theta[Nw][nc][N] (complex64).
 __global__ void build_theta_planes_kernel(const float2* __restrict__ theta, __nv_bfloat16* __restrict__ hi,
                                           __nv_bfloat16* __restrict__ lo, int N, int n, int Nw, int cap, int Kp) {
   const size_t per_w = (size_t)2 * n * Kp;  // one walker, one spin: [re,im][n][Kp]
   const size_t total = (size_t)2 * Nw * per_w;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int q = e % Kp;
-    const int j = (e / Kp) % n;
-    const int c = (e / ((size_t)Kp * n)) % 2;
+    const int c = (e / Kp) % 2;
+    const int j = (e / ((size_t)Kp * 2)) % n;
     const size_t w = (e / per_w) % Nw;
     const int spin = (int)(e / (per_w * Nw));
     float x = 0.f;
@@ -310,7 +333,7 @@ __global__ void build_theta_planes_kernel(const float2* __restrict__ theta, __nv
       x = c ? v.y : v.x;
     }
     const __nv_bfloat16 h = __float2bfloat16(x);
-    const size_t o = ((size_t)spin * cap + w) * per_w + e % per_w;
+    const size_t o = ((size_t)spin * cap + w) * per_w + e % per_w;  // rows (j, re/im) of walker w
     hi[o] = h;
     lo[o] = __float2bfloat16(x - __bfloat162float(h));
   }
@@ -425,7 +448,11 @@ cudaError_t tc_exchange_ws(afqmc_ctx* c) {
 cudaError_t tc_exchange_prepare(const afqmc_ctx* c) {
   const TcPlan& P = c->tc;
   if (!P.ok) return cudaSuccess;
-  return raise_smem_limit(exchange_tc_kernel);
+  cudaError_t e = raise_smem_limit(exchange_tc_kernel<0>);
+  if (e == cudaSuccess) e = raise_smem_limit(exchange_tc_kernel<16>);
+  if (e == cudaSuccess) e = raise_smem_limit(exchange_tc_kernel<24>);
+  if (e == cudaSuccess) e = raise_smem_limit(exchange_tc_kernel<32>);
+  return e;
 }
 
 void tc_exchange_free(afqmc_ctx* c) {
@@ -468,7 +495,7 @@ cudaError_t tc_exchange_launch(afqmc_ctx* c, int Nw, const void* theta, double* 
   a.err = static_cast<int*>(P.err);
   const size_t shm = tc_smem_bytes(P.KC, P.NB, P.S, P.n);
   if (!capturing(c)) {
-    e = raise_smem_limit(exchange_tc_kernel);
+    e = tc_exchange_prepare(c);
     if (e != cudaSuccess) return e;
   }
   int sms = 152;
@@ -480,7 +507,14 @@ cudaError_t tc_exchange_launch(afqmc_ctx* c, int Nw, const void* theta, double* 
   memcpy(&mal, P.map_a_lo, sizeof(CUtensorMap));
   memcpy(&mbh, P.map_b_hi, sizeof(CUtensorMap));
   memcpy(&mbl, P.map_b_lo, sizeof(CUtensorMap));
-  exchange_tc_kernel<<<grid, TC_THREADS, shm, s>>>(mah, mal, mbh, mbl, a);
+  if (P.n <= 16)
+    exchange_tc_kernel<16><<<grid, TC_THREADS, shm, s>>>(mah, mal, mbh, mbl, a);
+  else if (P.n <= 24)
+    exchange_tc_kernel<24><<<grid, TC_THREADS, shm, s>>>(mah, mal, mbh, mbl, a);
+  else if (P.n <= 32)
+    exchange_tc_kernel<32><<<grid, TC_THREADS, shm, s>>>(mah, mal, mbh, mbl, a);
+  else
+    exchange_tc_kernel<0><<<grid, TC_THREADS, shm, s>>>(mah, mal, mbh, mbl, a);
   return cudaGetLastError();
 }
 

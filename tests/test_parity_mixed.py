@@ -71,3 +71,34 @@ def test_mixed_step_taylor_ragged():
           f"max rel dW = {dW:.2e}, max rel dPsi = {dpsi:.2e}")
     assert dE <= E_TOL
     assert dW <= 1e-4 and dpsi <= 1e-4
+
+
+@pytest.mark.parametrize("n", [1, 2, 3])
+def test_mixed_local_energy_small_blocks(n):
+    """Tensor-core exchange with many g blocks per 128-row tile (128 / n of
+    them): E_L of fresh walkers and after a local energy of other walkers
+    (nothing may be left from an earlier evaluation), against the oracle."""
+    from paper_2403_02542_gb300.api import Context
+    s = make_system(32, n, n, 200, rho=0.98, seed=40 + n)
+    ham = R.make_hamiltonian(s.h1, s.L, s.trial, n, n)
+    e0 = float(R.local_energy(ham, ham.trial.to(torch.complex128)).real)
+    g = torch.Generator().manual_seed(n)
+    nw = 6
+    psi = (torch.as_tensor(s.trial).to(torch.complex128).unsqueeze(0).repeat(nw, 1, 1)
+           + 0.2 * torch.complex(torch.randn(nw, 32, 2 * n, generator=g, dtype=torch.float64),
+                                 torch.randn(nw, 32, 2 * n, generator=g, dtype=torch.float64)))
+    ref = R.local_energy(ham, psi)
+    ctx = Context(s.h1, s.L, s.trial, n, n, precision="mixed")
+    other = ctx.new_walkers(nw)
+    ctx.init_walkers(other)
+    w = ctx.new_walkers(nw)
+    w.psi.copy_(psi.transpose(1, 2).to(torch.complex64))
+    w.weight.fill_(1.0)
+    w.logovl.zero_()
+    w.status.zero_()
+    for first in (other, w):
+        ctx.local_energy(first, e0, 0.05)  # a different population first, then ours
+    e_loc, _ = ctx.local_energy(w, e0, 0.05)
+    got = torch.complex(e_loc[:, 0], e_loc[:, 1]).cpu()
+    assert float((got - ref).abs().max()) <= E_TOL, float((got - ref).abs().max())
+    ctx.close()
