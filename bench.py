@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the FP64-path rate measured beside the mixed one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the precision workload (N=300, mixed vs FP64)")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the timed gradient of the differentiation workload")
     ap.add_argument("--cpu-sample-walkers", type=int, default=4)
@@ -239,6 +241,54 @@ def adjoint_rate(dev):
         "ms": t_adj, "forward_ms": t_fwd, "adjoint_over_forward": t_adj / t_fwd,
         "J": float(J[2]), "live": float(J[3]), "gpu_launches": launches,
     }
+
+
+def precision_rate(dev):
+    """Precision workload (N=300, 50+50 electrons, 1500 vectors, Krylov 10,
+    tau=0.05, E_L every step): the mixed path on 2048 walkers and the FP64 path
+    on 512 of them (per-walker throughput; walkers are independent), CUDA-event
+    timed, one warm-up step each."""
+    import torch
+    from paper_2403_02542_gb300.api import Context
+    from paper_2403_02542_gb300.inputs import CONFIGS, config_system
+    cfg = CONFIGS["precision"]
+    s = config_system("precision")
+    out = {"workload": "precision form: N=300, Na=Nb=50, N_gamma=1500 (decay rho=1e-5^(1/1500)), tau=0.05, "
+                       "Split-2 + Krylov dim 10, E_loc every step, force bias reused from the previous E_L"}
+    stream = torch.cuda.current_stream(dev)
+    for prec, nw, steps in (("mixed", cfg["walkers"], 2), ("fp64", 512, 1)):
+        ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision=prec, device=dev)
+        w = ctx.new_walkers(nw)
+        ctx.init_walkers(w)
+        el = torch.empty(nw, 2, dtype=torch.float64, device=dev)
+        em = torch.empty(4, dtype=torch.float64, device=dev)
+        ctx.local_energy(w, 0.0, cfg["tau"], el, em)
+        e0 = float(el[0, 0])
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(7)
+        x = torch.randn(steps + 1, nw, s.G, dtype=torch.float64, device=dev, generator=gen)
+        ctx.step(w, x[0], cfg["tau"], e0, expm="krylov", order=cfg["order"], measure=True, e_loc=el, e_mix=em,
+                 reuse_bias=True)
+        torch.cuda.synchronize()
+        ctx.profile(True)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for k in range(steps):
+            ctx.step(w, x[1 + k], cfg["tau"], e0, expm="krylov", order=cfg["order"], measure=True, e_loc=el,
+                     e_mix=em, reuse_bias=True)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        ctx.profile(False)
+        prof = ctx.profile_read()
+        ms = a0.elapsed_time(a1) / steps
+        out[prec] = {"walkers": nw, "steps": steps, "ms_per_step": ms, "value": nw / (ms / 1000.0),
+                     "unit": "walker-steps/s", "e_mix": float(em[2]),
+                     "kernel_ms_per_step": {k: v[0] / steps for k, v in prof.items()}}
+        ctx.close()
+        del w, x
+        torch.cuda.empty_cache()
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
 
 
 def run_ours(args):
@@ -428,6 +478,9 @@ def run_ours(args):
     adjoint = None
     if world == 1 and not args.no_adjoint:
         adjoint = adjoint_rate(dev)
+    precision = None
+    if world == 1 and not args.no_precision:
+        precision = precision_rate(dev)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu, _ = oracle_rate(system, args.cpu_sample_walkers, 2, "")
@@ -454,6 +507,7 @@ def run_ours(args):
         "fp64_value": fp64_value,
         "mixed_over_fp64": (value / fp64_value) if fp64_value else None,
         "adjoint": adjoint,
+        "precision_workload": precision,
         "clocks": clk,
         "e_mix_last": emix_final,
     }

@@ -37,8 +37,6 @@ namespace afq {
 
 namespace {
 
-constexpr int TC_EPI_WG = 2;                       // epilogue warpgroups
-constexpr int TC_THREADS = 64 + 128 * TC_EPI_WG;   // 10 warps
 constexpr int TC_TMEM_COLS = 512;
 
 struct TcArgs {
@@ -49,9 +47,12 @@ struct TcArgs {
 };
 
 // NM > 0: n <= NM and each epilogue thread keeps its own accumulator row in
-// registers; NM == 0: the row is read back from shared memory.
-template <int NM>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+// registers; NM == 0: the row is read back from shared memory.  EWG epilogue
+// warpgroups.  SB = false: the item's B tile (all K) stays in shared memory
+// for all its A tiles; SB = true (large N): each stage of the ring carries
+// the B slab with the A slab (B re-read from L2 for every A tile).
+template <int NM, int EWG, bool SB>
+__global__ void __launch_bounds__(64 + 128 * EWG, 1)
     exchange_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                        const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
                        const TcArgs p) {
@@ -61,8 +62,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   unsigned char* sB = base;                                   // [hi,lo][KC][NB][64] bf16
   unsigned char* sA = sB + p.sB_bytes;                        // [S][hi,lo][128][64] bf16
   float* stg = reinterpret_cast<float*>(sA + (size_t)p.S * p.sA_stage_bytes);  // [WG][128][2n+1]
-  float* pbuf = stg + (size_t)TC_EPI_WG * p.staging_floats;  // [WG][128][4]
-  uint64_t* bars = reinterpret_cast<uint64_t*>(pbuf + TC_EPI_WG * 128 * 4);
+  float* pbuf = stg + (size_t)EWG * p.staging_floats;  // [WG][128][4]
+  uint64_t* bars = reinterpret_cast<uint64_t*>(pbuf + EWG * 128 * 4);
   uint64_t* full = bars;                 // [S]
   uint64_t* empty = bars + p.S;          // [S]
   uint64_t* bfull = bars + 2 * p.S;      // [1]
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   uint64_t* drain = tempty + 2;          // [1] completion of every MMA this CTA issued
   volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  volatile int* epi_ok = abort_flag + 1;  // [TC_EPI_WG] wait result broadcast inside a warpgroup
+  volatile int* epi_ok = abort_flag + 1;  // [EWG] wait result broadcast inside a warpgroup
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = p.n, two_n = 2 * n;
@@ -86,7 +87,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     mbar_init(bempty, 1);
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull + b, 1);
-      mbar_init(tempty + b, 128 * TC_EPI_WG);  // every epilogue thread arrives
+      mbar_init(tempty + b, 128 * EWG);  // every epilogue thread arrives
     }
     mbar_init(drain, 1);
     *abort_flag = 0;
@@ -114,25 +115,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       bool b_issued = false;
       const uint32_t a_bytes = 2u * 128u * 128u;  // hi + lo, 128 rows x 64 bf16
       const uint32_t b_bytes = 2u * (uint32_t)p.KC * (uint32_t)p.NB * 128u;
+      const uint32_t b_slab = 2u * (uint32_t)p.NB * 128u;  // one K slab of B, hi + lo
       for (int item = blockIdx.x; item < p.n_items && !*abort_flag; item += gridDim.x) {
         const int spin = item / p.WG, wg = item % p.WG;
-        if (!mbar_wait(bempty, bph ^ 1)) { atomicOr(p.err, 1); *abort_flag = 1; break; }
-        bph ^= 1;
-        mbar_expect_tx(bfull, b_bytes);
-        b_issued = true;
         const int brow = (spin * p.cap + wg * p.Wc) * two_n;
-        for (int kc = 0; kc < p.KC; ++kc) {
-          tma_load_2d(sB + (size_t)(0 * p.KC + kc) * p.NB * 128, &tmB_hi, kc * 64, brow, bfull);
-          tma_load_2d(sB + (size_t)(1 * p.KC + kc) * p.NB * 128, &tmB_lo, kc * 64, brow, bfull);
+        if constexpr (!SB) {
+          if (!mbar_wait(bempty, bph ^ 1)) { atomicOr(p.err, 1); *abort_flag = 1; break; }
+          bph ^= 1;
+          mbar_expect_tx(bfull, b_bytes);
+          b_issued = true;
+          for (int kc = 0; kc < p.KC; ++kc) {
+            tma_load_2d(sB + (size_t)(0 * p.KC + kc) * p.NB * 128, &tmB_hi, kc * 64, brow, bfull);
+            tma_load_2d(sB + (size_t)(1 * p.KC + kc) * p.NB * 128, &tmB_lo, kc * 64, brow, bfull);
+          }
         }
         for (uint32_t t = 0; t < tiles_per_item && !*abort_flag; ++t) {
           const int arow = (spin * p.T + (int)t) * 128;
           for (int kc = 0; kc < p.KC; ++kc) {
             if (!mbar_wait(empty + stage, ph ^ 1)) { atomicOr(p.err, 2); *abort_flag = 1; break; }
-            mbar_expect_tx(full + stage, a_bytes);
+            mbar_expect_tx(full + stage, SB ? a_bytes + b_slab : a_bytes);
             unsigned char* dst = sA + (size_t)stage * p.sA_stage_bytes;
             tma_load_2d(dst, &tmA_hi, kc * 64, arow, full + stage);
             tma_load_2d(dst + 128 * 128, &tmA_lo, kc * 64, arow, full + stage);
+            if constexpr (SB) {
+              tma_load_2d(dst + 2 * 128 * 128, &tmB_hi, kc * 64, brow, full + stage);
+              tma_load_2d(dst + 2 * 128 * 128 + (size_t)p.NB * 128, &tmB_lo, kc * 64, brow, full + stage);
+            }
             issued[stage] = true;
             last_ph[stage] = ph;
             if (++stage == p.S) { stage = 0; ph ^= 1; }
@@ -151,9 +159,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint32_t ph = 0, bph = 0, tph[2] = {0, 0};
       const uint32_t idesc = idesc_bf16(128, p.NB);
       for (int item = blockIdx.x; item < p.n_items && !*abort_flag; item += gridDim.x) {
-        if (!mbar_wait(bfull, bph)) { atomicOr(p.err, 4); *abort_flag = 1; break; }
-        bph ^= 1;
-        tc_fence_after();
+        if constexpr (!SB) {
+          if (!mbar_wait(bfull, bph)) { atomicOr(p.err, 4); *abort_flag = 1; break; }
+          bph ^= 1;
+          tc_fence_after();
+        }
         for (uint32_t t = 0; t < tiles_per_item && !*abort_flag; ++t) {
           if (!mbar_wait(tempty + buf, tph[buf] ^ 1)) { atomicOr(p.err, 8); *abort_flag = 1; break; }
           tc_fence_after();
@@ -163,8 +173,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             tc_fence_after();
             const uint32_t a_hi = sa(sA + (size_t)stage * p.sA_stage_bytes);
             const uint32_t a_lo = a_hi + 128 * 128;
-            const uint32_t b_hi = sa(sB + (size_t)(0 * p.KC + kc) * p.NB * 128);
-            const uint32_t b_lo = sa(sB + (size_t)(1 * p.KC + kc) * p.NB * 128);
+            const uint32_t b_hi = SB ? a_hi + 2 * 128 * 128 : sa(sB + (size_t)(0 * p.KC + kc) * p.NB * 128);
+            const uint32_t b_lo = SB ? b_hi + (uint32_t)p.NB * 128 : sa(sB + (size_t)(1 * p.KC + kc) * p.NB * 128);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {  // 4 x K=16 inside the 128-byte swizzle row
               const uint32_t off = k * 32;
@@ -179,7 +189,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tph[buf] ^= 1;
           buf ^= 1;
         }
-        umma_commit(bempty);  // B may be overwritten once every MMA of the item is done
+        if constexpr (!SB) umma_commit(bempty);  // B may be overwritten once every MMA of the item is done
       }
       // every MMA issued by this thread has completed before TMEM is released (bounded)
       umma_commit(drain);
@@ -215,7 +225,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         tc_fence_after();
         const int g = (int)t * p.gpt + gl;
         const bool valid = row_ok && g < p.G;
-        for (int wl = ewg; wl < p.Wc; wl += TC_EPI_WG) {
+        for (int wl = ewg; wl < p.Wc; wl += EWG) {
           const int w = wg * p.Wc + wl;
           if (w >= p.Nw) break;
           // this walker's 2n accumulator columns: (Re T[i][j], Im T[i][j]) for j = 0..n-1
@@ -344,10 +354,33 @@ inline int grid_for(size_t n) {
   return (int)(b > 152 * 64 ? 152 * 64 : (b == 0 ? 1 : b));
 }
 
-size_t tc_smem_bytes(int KC, int NB, int S, int n) {
-  const size_t stg = (size_t)TC_EPI_WG * 128 * (2 * n + 1) * 4;
-  return 1024 + (size_t)2 * KC * NB * 128 + (size_t)S * 2 * 128 * 128 + stg + (size_t)TC_EPI_WG * 128 * 4 * 4 +
-         (size_t)(2 * S + 7) * 8 + 16 + 4 * TC_EPI_WG;
+size_t tc_smem_bytes(int KC, int NB, int S, int n, int ewg, bool sb) {
+  const size_t stg = (size_t)ewg * 128 * (2 * n + 1) * 4;
+  const size_t resident_b = sb ? 0 : (size_t)2 * KC * NB * 128;
+  const size_t stage = (size_t)2 * 128 * 128 + (sb ? (size_t)2 * NB * 128 : 0);
+  return 1024 + resident_b + (size_t)S * stage + stg + (size_t)ewg * 128 * 4 * 4 + (size_t)(2 * S + 7) * 8 + 16 +
+         4 * ewg;
+}
+
+template <int NM, int EWG, bool SB>
+void* exchange_fn() {
+  return reinterpret_cast<void*>(exchange_tc_kernel<NM, EWG, SB>);
+}
+
+// kernel instance for (n, epilogue warpgroups, streamed B)
+void* exchange_instance(int n, int ewg, bool sb) {
+  const int nm = n <= 16 ? 16 : n <= 24 ? 24 : n <= 32 ? 32 : 0;
+#define AFQ_X(NM)                                                                   \
+  if (nm == NM) {                                                                   \
+    if (ewg == 2) return sb ? exchange_fn<NM, 2, true>() : exchange_fn<NM, 2, false>(); \
+    return sb ? exchange_fn<NM, 1, true>() : exchange_fn<NM, 1, false>();           \
+  }
+  AFQ_X(16)
+  AFQ_X(24)
+  AFQ_X(32)
+  AFQ_X(0)
+#undef AFQ_X
+  return nullptr;
 }
 
 }  // namespace
@@ -361,20 +394,30 @@ bool tc_exchange_plan(afqmc_ctx* c) {
   const int n = c->na;
   const int Kp = ((c->N + 63) / 64) * 64;
   const int KC = Kp / 64;
-  if (KC > 2 || n > 64) return false;
+  if (n > 64) return false;
   const int gpt = 128 / n;
-  int best_wc = 0, best_nb = 0, best_s = 0;
-  for (int S = 3; S >= 2 && !best_wc; --S)
-    for (int wc = 256 / (2 * n); wc >= 1; --wc) {
-      const int nb = ((wc * 2 * n + 15) / 16) * 16;
-      if (nb > 240) continue;  // two accumulators plus the 8-column read granularity stay inside 512 columns
-      if (tc_smem_bytes(KC, nb, S, n) <= 232448 - 1024) {
-        best_wc = wc;
-        best_nb = nb;
-        best_s = S;
-        break;
+  const size_t budget = 232448 - 1024;
+  // preference: B resident with two epilogue warpgroups, then B streamed with
+  // two, then with one (large N or n)
+  const struct { int ewg; bool sb; } modes[] = {{2, false}, {2, true}, {1, true}};
+  int best_wc = 0, best_nb = 0, best_s = 0, best_ewg = 0;
+  bool best_sb = false;
+  for (const auto& md : modes) {
+    for (int S = 3; S >= 2 && !best_wc; --S)
+      for (int wc = 256 / (2 * n); wc >= 1; --wc) {
+        const int nb = ((wc * 2 * n + 15) / 16) * 16;
+        if (nb > 240) continue;  // two accumulators plus the 8-column read granularity stay inside 512 columns
+        if (tc_smem_bytes(KC, nb, S, n, md.ewg, md.sb) <= budget) {
+          best_wc = wc;
+          best_nb = nb;
+          best_s = S;
+          best_ewg = md.ewg;
+          best_sb = md.sb;
+          break;
+        }
       }
-    }
+    if (best_wc) break;
+  }
   if (!best_wc) return false;
   P.ok = true;
   P.n = n;
@@ -385,6 +428,8 @@ bool tc_exchange_plan(afqmc_ctx* c) {
   P.Wc = best_wc;
   P.NB = best_nb;
   P.S = best_s;
+  P.ewg = best_ewg;
+  P.sb = best_sb;
   return true;
 }
 
@@ -448,11 +493,11 @@ cudaError_t tc_exchange_ws(afqmc_ctx* c) {
 cudaError_t tc_exchange_prepare(const afqmc_ctx* c) {
   const TcPlan& P = c->tc;
   if (!P.ok) return cudaSuccess;
-  cudaError_t e = raise_smem_limit(exchange_tc_kernel<0>);
-  if (e == cudaSuccess) e = raise_smem_limit(exchange_tc_kernel<16>);
-  if (e == cudaSuccess) e = raise_smem_limit(exchange_tc_kernel<24>);
-  if (e == cudaSuccess) e = raise_smem_limit(exchange_tc_kernel<32>);
-  return e;
+  void* f = exchange_instance(P.n, P.ewg, P.sb);
+  cudaFuncAttributes a;
+  cudaError_t e = cudaFuncGetAttributes(&a, f);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem() - (int)a.sharedSizeBytes);
 }
 
 void tc_exchange_free(afqmc_ctx* c) {
@@ -488,12 +533,12 @@ cudaError_t tc_exchange_launch(afqmc_ctx* c, int Nw, const void* theta, double* 
   a.G = c->G;
   a.S = P.S;
   a.n_items = 2 * a.WG;
-  a.sB_bytes = (uint32_t)(2 * P.KC * P.NB * 128);
-  a.sA_stage_bytes = 2 * 128 * 128;
+  a.sB_bytes = P.sb ? 0u : (uint32_t)(2 * P.KC * P.NB * 128);
+  a.sA_stage_bytes = 2 * 128 * 128 + (P.sb ? 2 * P.NB * 128 : 0);
   a.staging_floats = (uint32_t)(128 * (2 * P.n + 1));
   a.epart = epart;
   a.err = static_cast<int*>(P.err);
-  const size_t shm = tc_smem_bytes(P.KC, P.NB, P.S, P.n);
+  const size_t shm = tc_smem_bytes(P.KC, P.NB, P.S, P.n, P.ewg, P.sb);
   if (!capturing(c)) {
     e = tc_exchange_prepare(c);
     if (e != cudaSuccess) return e;
@@ -507,14 +552,10 @@ cudaError_t tc_exchange_launch(afqmc_ctx* c, int Nw, const void* theta, double* 
   memcpy(&mal, P.map_a_lo, sizeof(CUtensorMap));
   memcpy(&mbh, P.map_b_hi, sizeof(CUtensorMap));
   memcpy(&mbl, P.map_b_lo, sizeof(CUtensorMap));
-  if (P.n <= 16)
-    exchange_tc_kernel<16><<<grid, TC_THREADS, shm, s>>>(mah, mal, mbh, mbl, a);
-  else if (P.n <= 24)
-    exchange_tc_kernel<24><<<grid, TC_THREADS, shm, s>>>(mah, mal, mbh, mbl, a);
-  else if (P.n <= 32)
-    exchange_tc_kernel<32><<<grid, TC_THREADS, shm, s>>>(mah, mal, mbh, mbl, a);
-  else
-    exchange_tc_kernel<0><<<grid, TC_THREADS, shm, s>>>(mah, mal, mbh, mbl, a);
+  void* f = exchange_instance(P.n, P.ewg, P.sb);
+  void* args[] = {&mah, &mal, &mbh, &mbl, &a};
+  e = cudaLaunchKernel(f, dim3(grid), dim3(64 + 128 * P.ewg), args, shm, s);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

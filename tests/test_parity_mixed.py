@@ -102,3 +102,65 @@ def test_mixed_local_energy_small_blocks(n):
     got = torch.complex(e_loc[:, 0], e_loc[:, 1]).cpu()
     assert float((got - ref).abs().max()) <= E_TOL, float((got - ref).abs().max())
     ctx.close()
+
+
+def _sampled_mixed_walk(cfg_name, nw, steps, reortho_every, sample, seed):
+    """The mixed path at full size in the benchmark's launch configuration
+    (force bias reused from the previous E_L); the oracle follows a sample of
+    the walkers one by one with the same fields."""
+    from paper_2403_02542_gb300.api import Context
+    from walk_helpers import gpu_walk
+    s = config_system(cfg_name)
+    ham = R.make_hamiltonian(s.h1, s.L, s.trial, s.na, s.nb)
+    e0 = float(R.local_energy(ham, ham.trial.to(torch.complex128)).real)
+    ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, precision="mixed")
+    got, _ = gpu_walk(ctx, nw, steps, 0.05, e0, "krylov", 10, reortho_every, seed=seed, reuse_bias=True,
+                      record=set(range(steps)))
+    ref, ties = oracle_walk(s, len(sample), steps, 0.05, e0, "krylov", 10, reortho_every, seed=None,
+                            field_fn=lambda step: make_fields(seed, step, nw, s.G)[sample])
+    assert ties == 0
+    worst = 0.0
+    for step in range(steps):
+        dE = (got[step]["El"][sample] - ref[step]["El"]).abs()
+        dW = ((got[step]["W"][sample] - ref[step]["W"]).abs() / ref[step]["W"]).max()
+        worst = max(worst, float(dE.max()))
+        assert float(dE.max()) <= E_TOL, (cfg_name, step, float(dE.max()))
+        assert float(dW) <= 1e-4, (cfg_name, step, float(dW))
+    print(f"{cfg_name}: max |dE_L| over sampled walkers = {worst:.2e} Ha")
+    ctx.close()
+
+
+def test_mixed_large_workload_full_launch_sampled():
+    """N=128, 20+20 electrons, 640 vectors, 1024 walkers, Krylov 10, QR every 2."""
+    _sampled_mixed_walk("large", 1024, 3, 2, [0, 511, 1023], seed=4096)
+
+
+def test_mixed_precision_workload_full_launch_sampled():
+    """N=300, 50+50 electrons, 1500 vectors, 2048 walkers, Krylov 10, two steps."""
+    _sampled_mixed_walk("precision", 2048, 2, 0, [0, 2047], seed=5120)
+
+
+@pytest.mark.parametrize("N,n,G", [(192, 48, 200), (300, 50, 120)])
+def test_mixed_local_energy_streamed_operand(N, n, G):
+    """Tensor-core exchange for N > 128, where the Theta tile streams through
+    the pipeline with every K slab (two and one epilogue warpgroups)."""
+    from paper_2403_02542_gb300.api import Context
+    s = make_system(N, n, n, G, rho=0.97, seed=N + n)
+    ham = R.make_hamiltonian(s.h1, s.L, s.trial, n, n)
+    e0 = float(R.local_energy(ham, ham.trial.to(torch.complex128)).real)
+    g = torch.Generator().manual_seed(N)
+    nw = 5
+    psi = (torch.as_tensor(s.trial).to(torch.complex128).unsqueeze(0).repeat(nw, 1, 1)
+           + 0.1 * torch.complex(torch.randn(nw, N, 2 * n, generator=g, dtype=torch.float64),
+                                 torch.randn(nw, N, 2 * n, generator=g, dtype=torch.float64)))
+    ref = R.local_energy(ham, psi)
+    ctx = Context(s.h1, s.L, s.trial, n, n, precision="mixed")
+    w = ctx.new_walkers(nw)
+    w.psi.copy_(psi.transpose(1, 2).to(torch.complex64))
+    w.weight.fill_(1.0)
+    w.logovl.zero_()
+    w.status.zero_()
+    e_loc, _ = ctx.local_energy(w, e0, 0.05)
+    got = torch.complex(e_loc[:, 0], e_loc[:, 1]).cpu()
+    assert float((got - ref).abs().max()) <= E_TOL, float((got - ref).abs().max())
+    ctx.close()
