@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-fp64-compare", action="store_true",
                     help="skip the FP64-path rate measured beside the mixed one")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched workload (16 uneven systems in one graph)")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the precision workload (N=300, mixed vs FP64)")
     ap.add_argument("--no-adjoint", action="store_true",
@@ -291,6 +293,75 @@ def precision_rate(dev):
     return out
 
 
+def batched_rate(dev, steps=3, warmup=2):
+    """Batched workload: 16 systems with N uniform in 64..400, N/6 electrons
+    per spin, 5N vectors, 256-2048 walkers each; all systems advanced by one
+    captured CUDA graph per step (afqmc_batch_step), tile shapes autotuned,
+    mixed precision, Krylov 10, tau=0.05, E_L every step, force bias reused.
+    value = sum of walker-steps over all systems per second."""
+    import torch
+    from paper_2403_02542_gb300.api import Batch, Context
+    from paper_2403_02542_gb300.inputs import batched_systems
+    t0 = time.perf_counter()
+    systems = batched_systems()
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ctxs, ws, els, ems, e0s, xs = [], [], [], [], [], []
+    for s, nw in systems:
+        c = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision="mixed", device=dev)
+        w = c.new_walkers(nw)
+        c.init_walkers(w)
+        el = torch.empty(nw, 2, dtype=torch.float64, device=dev)
+        em = torch.empty(4, dtype=torch.float64, device=dev)
+        c.local_energy(w, 0.0, TAU, el, em)
+        e0s.append(float(el[0, 0]))
+        c.autotune(nw)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(11 + len(ctxs))
+        xs.append(torch.randn(warmup + steps, nw, s.G, dtype=torch.float64, device=dev, generator=gen))
+        ctxs.append(c)
+        ws.append(w)
+        els.append(el)
+        ems.append(em)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    batch = Batch(ctxs)
+    stream = torch.cuda.current_stream(dev)
+
+    def one(k):
+        batch.step(ws, [x[k] for x in xs], TAU, e0s, expm="krylov", order=KDIM, reortho=False, measure=True,
+                   e_loc=els, e_mix=ems, reuse_bias=True)
+
+    for k in range(warmup):
+        one(k)
+    torch.cuda.synchronize()
+    l0 = sum(c.launch_count for c in ctxs)
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for k in range(steps):
+        one(warmup + k)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    ms = a0.elapsed_time(a1) / steps
+    launches = sum(c.launch_count for c in ctxs) - l0
+    total_w = sum(nw for _, nw in systems)
+    out = {
+        "workload": "batched form: 16 synthetic systems, N uniform in 64..400, Na=Nb=N/6, N_gamma=5N, "
+                    "256-2048 walkers each, one CUDA graph per step over all systems, autotuned tiles, "
+                    "tau=0.05, Split-2 + Krylov dim 10, mixed, E_loc every step",
+        "systems": [[s.N, nw] for s, nw in systems], "walkers": total_w, "steps": steps,
+        "ms_per_step": ms, "value": total_w / (ms / 1000.0), "unit": "walker-steps/s (sum over systems)",
+        "gpu_launches_per_step": launches / steps, "generate_s": t_gen, "setup_s": t_setup,
+        "e_mix": [float(em[2]) for em in ems],
+    }
+    batch.close()
+    for c in ctxs:
+        c.close()
+    del ws, xs
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -481,6 +552,9 @@ def run_ours(args):
     precision = None
     if world == 1 and not args.no_precision:
         precision = precision_rate(dev)
+    batched = None
+    if world == 1 and not args.no_batched:
+        batched = batched_rate(dev)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu, _ = oracle_rate(system, args.cpu_sample_walkers, 2, "")
@@ -508,6 +582,7 @@ def run_ours(args):
         "mixed_over_fp64": (value / fp64_value) if fp64_value else None,
         "adjoint": adjoint,
         "precision_workload": precision,
+        "batched_workload": batched,
         "clocks": clk,
         "e_mix_last": emix_final,
     }

@@ -178,6 +178,8 @@ static afqmc_status ws_ensure(afqmc_ctx* c, int Nw, int kmax) {
   CK(cudaMalloc(&ws.alive, (size_t)nw));
   ws.n_walkers = nw;
   ws.kmax = km;
+  // the traces a later step could reuse for its force bias were in the freed buffers
+  if (c->d_bias_key) CK(cudaMemsetAsync(c->d_bias_key, 0, 2 * sizeof(unsigned long long), c->stream));
   if (c->tc.ok) CK(tc_exchange_ws(c));
   if (c->tg.ok) CK(tc_field_ws(c));
   return AFQMC_OK;

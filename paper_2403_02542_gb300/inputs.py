@@ -20,6 +20,13 @@ N = 855, 40 electrons, 5685 vectors for the largest run):
   Fock matrix F = h + sum_g [2 tr(L_g P) L_g - L_g P L_g], P = C C^T,
   iterated with Fock-matrix damping to a fixed point.
 
+The batched workload (16 uneven systems up to N = 400 with N_g = 5N) uses a
+recipe whose cost does not grow as N^4 per SCF iteration or as a QR of
+N^2 x N_g: L_g = sqrt(lambda_g) S_g / ||S_g||_F with S_g random symmetric
+(not orthogonalised; the two-electron integrals stay PSD with rank <= N_g),
+and the trial is the lowest n eigenvectors of the Fock matrix of the
+core-guess density (one Fock step instead of a converged SCF).
+
 The random generator is numpy's PCG64 throughout.
 """
 from __future__ import annotations
@@ -33,6 +40,7 @@ __all__ = [
     "make_system",
     "make_fields",
     "config_system",
+    "batched_systems",
     "CONFIGS",
 ]
 
@@ -170,3 +178,63 @@ def config_system(name: str, system: int = 0, **overrides) -> System:
     c.update(overrides)
     seed = 20240304 + 100 * _CONFIG_INDEX.get(name, 9) + system
     return make_system(c["N"], c["na"], c["na"], c["G"], rho=c["rho"], seed=seed)
+
+
+def _plain_cholesky(rng: np.random.Generator, N: int, G: int, rho: float, chunk: int = 64) -> np.ndarray:
+    """L_g = sqrt(rho^g) S_g / ||S_g||_F, S_g random symmetric, in chunks of g."""
+    L = np.empty((G, N, N))
+    for g0 in range(0, G, chunk):
+        g1 = min(G, g0 + chunk)
+        X = rng.standard_normal((g1 - g0, N, N), dtype=np.float32)
+        X = X + X.transpose(0, 2, 1)
+        scale = np.sqrt(rho ** np.arange(g0, g1)) / np.sqrt(np.einsum("gpq,gpq->g", X, X, dtype=np.float64))
+        np.multiply(X, scale[:, None, None], out=L[g0:g1])
+    return L
+
+
+def _one_step_fock_orbitals(h1: np.ndarray, L: np.ndarray, n: int, chunk: int = 64) -> np.ndarray:
+    """Lowest n eigenvectors of F = h + sum_g [2 tr(L_g P) L_g - L_g P L_g] for
+    the core-guess density P = C C^T (C: lowest n eigenvectors of h)."""
+    _, C = np.linalg.eigh(h1)
+    C = C[:, :n]
+    N = h1.shape[0]
+    F = h1.copy()
+    for g0 in range(0, L.shape[0], chunk):
+        Lc = L[g0:g0 + chunk]
+        m = Lc.shape[0]
+        LC = (Lc.reshape(m * N, N) @ C).reshape(m, N, n)          # L_g C
+        coul = (LC * C[None]).sum(axis=(1, 2))                    # tr(L_g P)
+        F += 2.0 * np.tensordot(coul, Lc, axes=1)
+        M = LC.transpose(1, 0, 2).reshape(N, m * n)
+        F -= M @ M.T                                              # sum_g L_g P L_g
+    F = 0.5 * (F + F.T)
+    _, V = np.linalg.eigh(F)
+    return V[:, :n]
+
+
+def batched_systems(seed: int = 20240304 + 400, n_systems: int = 16, n_min: int = 64, n_max: int = 400,
+                    walkers: tuple = (256, 2048)) -> list:
+    """The batched workload: n_systems systems with N uniform in [n_min, n_max],
+    n = N // 6 electrons per spin, N_g = 5N vectors decaying to 1e-5, and a
+    walker count uniform in `walkers` for each.  Returns [(System, n_walkers)]."""
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Ns = rng.integers(n_min, n_max + 1, size=n_systems).tolist()
+    nws = rng.integers(walkers[0], walkers[1] + 1, size=n_systems).tolist()
+
+    def build(i):  # every system has its own generator: the result does not depend on the threads
+        r = np.random.Generator(np.random.PCG64([seed, i]))
+        N = Ns[i]
+        n, G = N // 6, 5 * N
+        rho = 1e-5 ** (1.0 / G)
+        h1 = _random_h1(r, N)
+        L = _plain_cholesky(r, N, G, rho)
+        C = _one_step_fock_orbitals(h1, L, n)
+        meta = dict(N=N, na=n, nb=n, G=G, rho=rho, seed=[seed, i], recipe="batched")
+        return (System(h1=h1, L=L, trial=np.ascontiguousarray(np.concatenate([C, C], axis=1)), na=n, nb=n,
+                       e_const=0.0, meta=meta), int(nws[i]))
+
+    with ThreadPoolExecutor(max_workers=min(n_systems, os.cpu_count() or 1)) as ex:
+        return list(ex.map(build, range(n_systems)))

@@ -152,3 +152,54 @@ def test_autotune_keeps_results_bit_identical(tmp_path):
         for i in range(len(SYSTEMS)):
             for a, b in zip(got[k][i]["raw"], ref[k][i]["raw"]):
                 assert torch.equal(a, b)
+
+
+def test_batched_workload_full_launch_sampled():
+    """The batched workload at full size (16 systems, N uniform in 64..400,
+    N/6 electrons per spin, 5N vectors, 256-2048 walkers each), mixed
+    precision, all systems in one captured graph per step, tiles autotuned,
+    force bias reused; two steps.  The oracle follows walker 0 of two of the
+    systems with the same fields (|dE_L| <= 1e-4 Ha, weights 1e-4 relative)."""
+    from paper_2403_02542_gb300.api import Batch, Context
+    from paper_2403_02542_gb300.inputs import batched_systems
+    from walk_helpers import oracle_walk
+    systems = batched_systems()
+    order = sorted(range(len(systems)), key=lambda i: systems[i][0].N)
+    sample = [order[0], order[len(order) // 2]]
+    ctxs, ws, els, ems, e0s = [], [], [], [], []
+    for s, nw in systems:
+        c = Context(s.h1, s.L, s.trial, s.na, s.nb, precision="mixed")
+        w = c.new_walkers(nw)
+        c.init_walkers(w)
+        el = torch.empty(nw, 2, dtype=torch.float64, device=c.device)
+        em = torch.empty(4, dtype=torch.float64, device=c.device)
+        c.local_energy(w, 0.0, TAU, el, em)
+        e0s.append(float(el[0, 0]))
+        c.autotune(nw)
+        ctxs.append(c)
+        ws.append(w)
+        els.append(el)
+        ems.append(em)
+    batch = Batch(ctxs)
+    got = {i: [] for i in sample}
+    x = [torch.empty(nw, s.G, dtype=torch.float64, device=ctxs[0].device) for s, nw in systems]
+    for k in range(2):
+        for i, (s, nw) in enumerate(systems):
+            x[i].copy_(torch.as_tensor(make_fields(700 + i, k, nw, s.G)))
+        batch.step(ws, x, TAU, e0s, expm="krylov", order=10, reortho=False, measure=True, e_loc=els, e_mix=ems,
+                   reuse_bias=True)
+        torch.cuda.synchronize()
+        for i in sample:
+            got[i].append((complex(float(els[i][0, 0]), float(els[i][0, 1])), float(ws[i].weight[0])))
+    batch.close()
+    for i in sample:
+        s, nw = systems[i]
+        ref, ties = oracle_walk(s, 1, 2, TAU, e0s[i], "krylov", 10, 0, seed=None,
+                                field_fn=lambda step, i=i, s=s, nw=nw: make_fields(700 + i, step, nw, s.G)[:1])
+        assert ties == 0
+        for k in range(2):
+            dE = abs(got[i][k][0] - complex(ref[k]["El"][0]))
+            dW = abs(got[i][k][1] - float(ref[k]["W"][0])) / float(ref[k]["W"][0])
+            assert dE <= 1e-4 and dW <= 1e-4, (s.N, k, dE, dW)
+    for c in ctxs:
+        c.close()

@@ -132,3 +132,27 @@ def test_reuse_bias_graph_replay_is_bit_identical():
     for a, b in zip(res[0], res[1]):
         for x, y in zip(a, b):
             assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_reuse_bias_after_workspace_growth(precision):
+    """afqmc_local_energy, then a first Krylov step (its basis needs a larger
+    workspace, which frees the stored traces): the step must recompute the
+    force bias, i.e. equal the step without the option bit for bit."""
+    s = make_system(66, 11, 11, 330, rho=1e-5 ** (1 / 330), seed=36)
+    e0, tau, nw = _e0(s), 0.05, 9
+    out = []
+    for reuse in (True, False):
+        ctx = _ctx(s, precision)
+        w = ctx.new_walkers(nw)
+        ctx.init_walkers(w)
+        el = torch.empty(nw, 2, dtype=torch.float64, device=ctx.device)
+        em = torch.empty(4, dtype=torch.float64, device=ctx.device)
+        ctx.local_energy(w, e0, tau, el, em)
+        x = torch.as_tensor(make_fields(12, 0, nw, s.G), device=ctx.device)
+        ctx.step(w, x, tau, e0, expm="krylov", order=10, measure=True, e_loc=el, e_mix=em, reuse_bias=reuse)
+        torch.cuda.synchronize()
+        out.append((w.psi.cpu().clone(), w.weight.cpu().clone(), el.cpu().clone()))
+        ctx.close()
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
