@@ -546,6 +546,13 @@ def run_ours(args):
                      "(BF16x3 split); achieved counts algorithmic flops once")
         kname = "exchange_tc_kernel (tcgen05 BF16x3)"
     achieved = (ex_flop / (ex_ms / ex_n / 1000.0)) / 1e12 if ex_n else None
+    # DRAM bytes of one exchange launch (read + write), ncu capture of this kernel
+    # version at the benchmark size (profiles/launches_mixed_large.md)
+    traffic, traffic_note = None, None
+    if args.precision == "mixed" and NW == 1024:
+        traffic = 63.87e6
+        traffic_note = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of "
+                        "exchange_tc_kernel<24, 2, 0> at 1024 walkers: 56.08 + 7.79 MB; operands 55.9 MB")
     adjoint = None
     if world == 1 and not args.no_adjoint:
         adjoint = adjoint_rate(dev)
@@ -568,7 +575,8 @@ def run_ours(args):
         "config": config_dict(args.precision, world),
         "roofline": {"kernel": kname + ": Coulomb+exchange contraction of E_L",
                      "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-                     "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                     "traffic_source": traffic_note,
                      "flop_per_launch": ex_flop, "avg_launch_ms": ex_ms / ex_n if ex_n else None,
                      "peak_source": peak_note,
                      "share_of_step": ex_ms / total_prof if total_prof else None},
