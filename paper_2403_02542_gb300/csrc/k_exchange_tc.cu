@@ -290,7 +290,9 @@ __global__ void __launch_bounds__(64 + 128 * EWG, 1)
               p.epart[(((size_t)w * p.G + gg) * 2 + spin) * 4 + qn] = sum;
             }
           }
-          named_bar(bar_id, 128);
+          // no barrier here: the next walker's staging writes come after the barrier
+          // above (every thread is past its staging reads) and its row partials after
+          // the next walker's first barrier (every thread is past this tail)
         }
         tc_fence_before();
         mbar_arrive(tempty + buf);
