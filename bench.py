@@ -394,6 +394,7 @@ def run_ours(args):
     e_mix = torch.empty(4, dtype=torch.float64, device=dev)
     ctx.local_energy(w, 0.0, TAU, e_loc, e_mix)
     e0 = float(e_loc[0, 0])
+    tune = ctx.autotune(NW)  # GEMM tile shape per call site (set-up, not timed)
 
     K, Wm = args.steps, args.warmup
     gen = torch.Generator(device=dev)
@@ -501,6 +502,7 @@ def run_ours(args):
         c64 = Context(system.h1, system.L, system.trial, na, nb, system.e_const, precision="fp64", device=dev)
         w64 = c64.new_walkers(NW)
         c64.init_walkers(w64)
+        c64.autotune(NW)
         el64 = torch.empty(NW, 2, dtype=torch.float64, device=dev)
         em64 = torch.empty(4, dtype=torch.float64, device=dev)
         k64 = min(K, 3)
@@ -585,6 +587,7 @@ def run_ours(args):
         "e2e": {"value": e2e, "unit": "walker-steps/s",
                 "h2d_bytes_per_step": NW * G * 8, "d2h_bytes_per_step": 4 * 8},
         "gpu_launches": launches,
+        "gemm_tiles": tune,
         "graph_value": graph_value,
         "fp64_value": fp64_value,
         "mixed_over_fp64": (value / fp64_value) if fp64_value else None,
