@@ -552,9 +552,9 @@ def run_ours(args):
     # version at the benchmark size (profiles/launches_mixed_large.md)
     traffic, traffic_note = None, None
     if args.precision == "mixed" and NW == 1024:
-        traffic = 63.87e6
+        traffic = 64.16e6
         traffic_note = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of "
-                        "exchange_tc_kernel<24, 2, 0> at 1024 walkers: 56.08 + 7.79 MB; operands 55.9 MB")
+                        "exchange_tc_kernel<24, 2, 0> at 1024 walkers: 56.10 + 8.05 MB; operands 55.9 MB")
     adjoint = None
     if world == 1 and not args.no_adjoint:
         adjoint = adjoint_rate(dev)
