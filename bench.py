@@ -198,50 +198,67 @@ def run_reference(args):
 def adjoint_rate(dev):
     """Gradient of the mixed estimator through a 100-step fixed-field walk
     (differentiation workload: N=96, 15+15 electrons, 480 vectors, 512
-    walkers, Taylor-6, QR every 10 steps, checkpoints every 10), FP64, timed
-    with CUDA events; the plain FP64 forward walk of the same workload beside it."""
+    walkers, Taylor-6, QR every 10 steps, checkpoints every 10) in FP64 and in
+    the mixed precision (complex64 walkers), timed with CUDA events; the plain
+    forward walk of the same workload beside each, and the mixed J and
+    gradients against the FP64 ones."""
     import torch
     from paper_2403_02542_gb300.api import Context
     from paper_2403_02542_gb300.inputs import CONFIGS, config_system
     cfg = CONFIGS["grad"]
     s = config_system("grad")
     nw, steps, tau, order, r = cfg["walkers"], cfg["steps"], cfg["tau"], cfg["order"], cfg["reortho"]
-    ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision="fp64", device=dev)
-    w = ctx.new_walkers(nw)
-    ctx.init_walkers(w)
-    el = torch.empty(nw, 2, dtype=torch.float64, device=dev)
-    em = torch.empty(4, dtype=torch.float64, device=dev)
-    ctx.local_energy(w, 0.0, tau, el, em)
-    e0 = float(el[0, 0])
     gen = torch.Generator(device=dev)
     gen.manual_seed(99)
     fields = torch.randn(steps, nw, s.G, dtype=torch.float64, device=dev, generator=gen)
     stream = torch.cuda.current_stream(dev)
-    ctx.walk_backward(w, fields[:2], tau, e0, order=order, reortho_every=r, ckpt_every=10)   # warm-up
-    torch.cuda.synchronize()
-    l0 = ctx.launch_count
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a0.record(stream)
-    J, _, _ = ctx.walk_backward(w, fields, tau, e0, order=order, reortho_every=r, ckpt_every=10)
-    a1.record(stream)
-    torch.cuda.synchronize()
-    t_adj = a0.elapsed_time(a1)
-    launches = ctx.launch_count - l0
-    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    f0.record(stream)
-    for k in range(steps):
-        ctx.step(w, fields[k], tau, e0, expm="taylor", order=order, reortho=(k + 1) % r == 0,
-                 measure=(k == steps - 1), e_loc=el, e_mix=em)
-    f1.record(stream)
-    torch.cuda.synchronize()
-    t_fwd = f0.elapsed_time(f1)
-    ctx.close()
+    e0 = None
+
+    def one(precision):
+        nonlocal e0
+        ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision=precision, device=dev)
+        w = ctx.new_walkers(nw)
+        ctx.init_walkers(w)
+        el = torch.empty(nw, 2, dtype=torch.float64, device=dev)
+        em = torch.empty(4, dtype=torch.float64, device=dev)
+        if e0 is None:
+            ctx.local_energy(w, 0.0, tau, el, em)
+            e0 = float(el[0, 0])
+        ctx.walk_backward(w, fields[:2], tau, e0, order=order, reortho_every=r, ckpt_every=10)   # warm-up
+        torch.cuda.synchronize()
+        l0 = ctx.launch_count
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        J, gh, gL = ctx.walk_backward(w, fields, tau, e0, order=order, reortho_every=r, ckpt_every=10)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        t_adj = a0.elapsed_time(a1)
+        launches = ctx.launch_count - l0
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        for k in range(steps):
+            ctx.step(w, fields[k], tau, e0, expm="taylor", order=order, reortho=(k + 1) % r == 0,
+                     measure=(k == steps - 1), e_loc=el, e_mix=em)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        t_fwd = f0.elapsed_time(f1)
+        ctx.close()
+        res = {"value": nw * steps / (t_adj / 1000.0), "unit": "walker-steps/s (gradient, forward + adjoint)",
+               "ms": t_adj, "forward_ms": t_fwd, "adjoint_over_forward": t_adj / t_fwd,
+               "J": float(J[2]), "live": float(J[3]), "gpu_launches": launches}
+        return res, gh, gL
+
+    r64, gh64, gL64 = one("fp64")
+    r32, gh32, gL32 = one("mixed")
     return {
         "workload": "gradient of E_n after a 100-step fixed-field walk: N=96, Na=Nb=15, N_gamma=480, "
-                    "512 walkers, tau=0.05, Split-2 + Taylor-6, QR every 10 steps, checkpoints every 10, FP64",
-        "value": nw * steps / (t_adj / 1000.0), "unit": "walker-steps/s (gradient, forward + adjoint)",
-        "ms": t_adj, "forward_ms": t_fwd, "adjoint_over_forward": t_adj / t_fwd,
-        "J": float(J[2]), "live": float(J[3]), "gpu_launches": launches,
+                    "512 walkers, tau=0.05, Split-2 + Taylor-6, QR every 10 steps, checkpoints every 10",
+        "fp64": r64, "mixed": r32, "mixed_speedup": r64["ms"] / r32["ms"],
+        "mixed_vs_fp64": {
+            "dJ": abs(r32["J"] - r64["J"]),
+            "grad_h1_rel": float((gh32 - gh64).abs().max() / gh64.abs().max()),
+            "grad_L_rel": float((gL32 - gL64).abs().max() / gL64.abs().max()),
+        },
     }
 
 

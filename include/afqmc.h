@@ -244,8 +244,10 @@ void afqmc_batch_destroy(afqmc_batch* batch);
  * Derivatives are with respect to every entry of h1 and L_g (a symmetric
  * direction dH gives sum_pq dH_pq grad_pq).  The trial is held fixed.
  *   grad_h1  device [N][N] double, grad_L device [G][N][N] double (written)
- * FP64 contexts only (AFQMC_ENOTSUP otherwise, and when na*na + na*N
- * complex doubles exceed one block's shared memory).  Synchronises the stream.
+ * Both precisions: in a mixed context Theta and the per-walker terms are
+ * complex64 (FP32 contractions over N) and the sums over walkers FP64.
+ * AFQMC_ENOTSUP when na*na + na*N complex doubles exceed one block's shared
+ * memory.  Synchronises the stream.
  * Errors: EINVAL, EDOM, ENOTSUP, ENOMEM, ECUDA. */
 afqmc_status afqmc_energy_backward(afqmc_ctx* ctx, const afqmc_walkers* w, double e0, double tau, double dJ,
                                    double* grad_h1, double* grad_L);
@@ -278,14 +280,24 @@ afqmc_status afqmc_energy_backward(afqmc_ctx* ctx, const afqmc_walkers* w, doubl
  *             dJ times the derivative along symmetric perturbations, returned
  *             symmetrised (for a symmetric direction dH the change of J is
  *             sum_pq dH_pq grad_pq)
- *   grad_psi0 device [Nw][na+nb][N] complex double or NULL: G with
- *             dJ = Re sum G * dPsi_0 element by element (no conjugation), for a
- *             change of the initial walkers with logovl following Psi_0
+ *   grad_psi0 device [Nw][na+nb][N] of the walkers' complex type, or NULL:
+ *             G with dJ = Re sum G * dPsi_0 element by element (no
+ *             conjugation), for a change of the initial walkers with logovl
+ *             following Psi_0
+ * Precision: an FP64 context runs everything in FP64.  A mixed context walks
+ * its complex64 walkers with its own step (tensor-core field and Taylor
+ * products) and runs the reverse pass on complex64 states and adjoints with
+ * FP32 contractions; the overlap inverses, log-determinants, weights and the
+ * per-walker coefficients are FP64, and the gradient sums over walkers and
+ * steps are kept in FP64 (each step's complex64 contribution is added once).
+ * The recomputed steps use the SIMT FP32 contractions, so they follow the
+ * forward walk to FP32 rounding.
  * Memory: the call allocates and frees its own device workspace (about
  * (ckpt_every + n_steps/ckpt_every + 2 order + 12) Nw (na+nb) N complex
- * doubles plus Nw N^2 and G N^2 complex doubles).  FP64 contexts only
- * (AFQMC_ENOTSUP otherwise or when max(na, nb) > 64).  Synchronises the
- * stream.  Errors: EINVAL, EDOM, ENOTSUP, ENOMEM, ECUDA. */
+ * numbers of the walkers' type plus Nw N^2 of them, G N^2 complex doubles
+ * and, in mixed contexts, G N^2 + G (na+nb) N complex floats).
+ * AFQMC_ENOTSUP when max(na, nb) > 64.  Synchronises the stream.
+ * Errors: EINVAL, EDOM, ENOTSUP, ENOMEM, ECUDA. */
 typedef struct {
   int n_steps;
   int order;

@@ -162,7 +162,10 @@ class Context:
         `w` holds the walkers at step 0 (left unchanged); `fields` is a device
         tensor [n_steps, Nw, G] of the walk's auxiliary fields.  Returns
         (e_mix [4], dJ/dh1 [N,N], dJ/dL [G,N,N]) and, with grad_psi0=True, the
-        derivative G [Nw, na+nb, N] with dJ = Re sum G * dPsi_0 as well.
+        derivative G [Nw, na+nb, N] (the walkers' complex type) with
+        dJ = Re sum G * dPsi_0 as well.  In a mixed context the walk and its
+        reverse run on complex64 walkers (FP32 contractions, FP64 overlaps,
+        determinants and gradient sums).
         """
         f = fields.to(device=self.device, dtype=torch.float64).contiguous()
         if f.dim() != 3 or f.shape[1] != w.n or f.shape[2] != self.G:
@@ -172,7 +175,7 @@ class Context:
         J = torch.empty(4, dtype=torch.float64, device=self.device)
         gh = torch.empty(self.N, self.N, dtype=torch.float64, device=self.device)
         gL = torch.empty(self.G, self.N, self.N, dtype=torch.float64, device=self.device)
-        gp = torch.empty(w.n, self.nc, self.N, dtype=torch.complex128, device=self.device) if grad_psi0 else None
+        gp = torch.empty(w.n, self.nc, self.N, dtype=self.ctype, device=self.device) if grad_psi0 else None
         self._bind_stream()
         cw = w.c_struct()
         L.check(L.lib().afqmc_walk_backward(self._h, ctypes.byref(cw), f.data_ptr(), ctypes.byref(p), J.data_ptr(),

@@ -17,6 +17,7 @@
 #include <cstring>
 #include <new>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "internal.cuh"
@@ -620,9 +621,15 @@ struct Arena {
   }
 };
 
+template <typename R>
 struct AdjBufs {
-  double2 *ck_psi, *seg_psi, *run_psi, *P0, *Tb, *Ub, *psi2, *psi3, *pb, *p3, *p2, *p1, *thbar, *Abar, *cbar, *tbar,
-      *oinv3, *oinvk, *aR, *gLc, *Lhb, *Bbar, *part, *ys;
+  typedef typename C2<R>::t P;
+  // walker states, their adjoints and the walker-shaped intermediates
+  P *ck_psi, *seg_psi, *run_psi, *P0, *Tb, *Ub, *psi2, *psi3, *pb, *p3, *p2, *p1, *thbar, *Abar, *cbar, *tbar, *part;
+  // complex64 walkers: one step's contributions to Bbar, gLc and Lhb before
+  // they are added to the FP64 sums (NULL for complex128 walkers)
+  P *sB, *sL, *sLh;
+  double2 *oinv3, *oinvk, *aR, *gLc, *Lhb, *Bbar, *ys;
   double *ck_W, *ck_lo, *seg_lo, *run_W, *run_lo, *Wfin, *mu_part, *ld3, *ldk, *omega, *ecoef, *mubar, *V, *lam, *Bs,
       *T1, *M1, *hbar, *X, *D, *eloc, *emix;
   uint32_t *ck_st, *run_st, *st_scr;
@@ -650,34 +657,36 @@ GemmArgs gargs(int M, int Nn, int K, int batch, const void* A, long long sa_m, l
 }
 }  // namespace
 
-static void adj_carve(Arena& a, AdjBufs& b, const afqmc_ctx* c, int Nw, int K, int C, int nck) {
+template <typename R>
+static void adj_carve(Arena& a, AdjBufs<R>& b, const afqmc_ctx* c, int Nw, int K, int C, int nck) {
   const size_t nw = (size_t)Nw, per = (size_t)c->nc * c->N, NN = (size_t)c->N * c->N, G = (size_t)c->G;
+  typedef typename C2<R>::t P;
   const size_t nmax = (size_t)(c->na > c->nb ? c->na : c->nb);
-  b.ck_psi = a.take<double2>((size_t)nck * nw * per);
+  b.ck_psi = a.take<P>((size_t)nck * nw * per);
   b.ck_W = a.take<double>((size_t)nck * nw);
   b.ck_lo = a.take<double>((size_t)nck * nw * 2);
   b.ck_st = a.take<uint32_t>((size_t)nck * nw);
-  b.seg_psi = a.take<double2>((size_t)(C + 1) * nw * per);
+  b.seg_psi = a.take<P>((size_t)(C + 1) * nw * per);
   b.seg_lo = a.take<double>((size_t)(C + 1) * nw * 2);
-  b.run_psi = a.take<double2>(nw * per);
+  b.run_psi = a.take<P>(nw * per);
   b.run_W = a.take<double>(nw);
   b.run_lo = a.take<double>(nw * 2);
   b.run_st = a.take<uint32_t>(nw);
   b.st_scr = a.take<uint32_t>(nw);
   b.Wfin = a.take<double>(nw);
-  b.P0 = a.take<double2>(nw * per);
-  b.Tb = a.take<double2>(nw * (K + 1) * per);
-  b.Ub = a.take<double2>(nw * K * per);
-  b.psi2 = a.take<double2>(nw * per);
-  b.psi3 = a.take<double2>(nw * per);
-  b.pb = a.take<double2>(nw * per);
-  b.p3 = a.take<double2>(nw * per);
-  b.p2 = a.take<double2>(nw * per);
-  b.p1 = a.take<double2>(nw * per);
-  b.thbar = a.take<double2>(nw * per);
-  b.Abar = a.take<double2>(nw * NN);
-  b.cbar = a.take<double2>(nw * G);
-  b.tbar = a.take<double2>(nw * G);
+  b.P0 = a.take<P>(nw * per);
+  b.Tb = a.take<P>(nw * (K + 1) * per);
+  b.Ub = a.take<P>(nw * K * per);
+  b.psi2 = a.take<P>(nw * per);
+  b.psi3 = a.take<P>(nw * per);
+  b.pb = a.take<P>(nw * per);
+  b.p3 = a.take<P>(nw * per);
+  b.p2 = a.take<P>(nw * per);
+  b.p1 = a.take<P>(nw * per);
+  b.thbar = a.take<P>(nw * per);
+  b.Abar = a.take<P>(nw * NN);
+  b.cbar = a.take<P>(nw * G);
+  b.tbar = a.take<P>(nw * G);
   b.keep = a.take<uint8_t>(nw * G);
   b.mu_part = a.take<double>(nw * G);
   b.oinv3 = a.take<double2>(nw * 2 * nmax * nmax);
@@ -692,8 +701,12 @@ static void adj_carve(Arena& a, AdjBufs& b, const afqmc_ctx* c, int Nw, int K, i
   b.Bbar = a.take<double2>(NN);
   b.mubar = a.take<double>(G);
   const size_t pc = (size_t)b.skc * G * nw, pbb = (size_t)b.skb * NN;
-  b.part = a.take<double2>(pc > pbb ? pc : pbb);
+  b.part = a.take<P>(pc > pbb ? pc : pbb);
   b.ys = a.take<double2>(per + G * per);
+  const bool split = std::is_same<R, float>::value;
+  b.sB = split ? a.take<P>(NN) : nullptr;
+  b.sL = split ? a.take<P>(G * NN) : nullptr;
+  b.sLh = split ? a.take<P>(G * per) : nullptr;
   b.V = a.take<double>(NN);
   b.lam = a.take<double>((size_t)c->N);
   b.Bs = a.take<double>(NN);
@@ -708,33 +721,46 @@ static void adj_carve(Arena& a, AdjBufs& b, const afqmc_ctx* c, int Nw, int K, i
 
 // One reverse step k of the walk: recompute Theta_k, f, c, A, the Taylor terms
 // and Psi3 from the stored Psi_k, then pull the adjoint Psi_bar_{k+1} (in b.pb)
-// back to Psi_bar_k (in b.pb) and accumulate the parameter adjoints.
-static afqmc_status adj_step(afqmc_ctx* c, const AdjBufs& b, int Nw, const double* x, const double2* psik,
-                             const double* lok, const double2* psinext, int qr, int K, double tau) {
+// back to Psi_bar_k (in b.pb) and accumulate the parameter adjoints.  With
+// complex64 walkers the contractions run in FP32 and the parameter adjoints
+// of the step are added to their FP64 sums once per step.
+template <typename R>
+static afqmc_status adj_step(afqmc_ctx* c, const AdjBufs<R>& b, int Nw, const double* x,
+                             const typename C2<R>::t* psik, const double* lok, const typename C2<R>::t* psinext, int qr,
+                             int K, double tau) {
+  typedef typename C2<R>::t P;
+  constexpr bool split = std::is_same<R, float>::value;
   cudaStream_t s = c->stream;
   Workspace& ws = c->ws;
   const int N = c->N, nc = c->nc, G = c->G;
-  const size_t per = (size_t)nc * N, NN = (size_t)N * N, cs = sizeof(double2);
+  const size_t per = (size_t)nc * N, NN = (size_t)N * N, cs = sizeof(P);
   const long long perl = (long long)per, NNl = (long long)NN;
   const double st = std::sqrt(tau);
   uint64_t nl = 0;
   auto gm = [&](const GemmArgs& g, bool ac, int epi) -> cudaError_t {
     nl += (g.splitk > 1 && g.part && g.batch == 1 && epi != EPI_STORE_ADD) ? 2 : 1;
-    return gemm<double>(g, ac, epi, s);
+    return gemm<R>(g, ac, epi, s);
   };
-  double2* theta = static_cast<double2*>(ws.theta);
+  // parameter adjoint: straight into the FP64 sum, or into the step's
+  // complex64 buffer (stored by the first contribution, added by the rest)
+  auto pacc = [&](double2* sum, P* step_buf, bool first) -> std::pair<void*, int> {
+    if (!split) return {sum, EPI_ACC};
+    return {step_buf, first ? EPI_STORE : EPI_ACC};
+  };
+  P* theta = static_cast<P*>(ws.theta);
   // forward quantities of step k (same kernels as the step, so the kept
   // force-bias components are the forward's)
-  CKW(adj_sanitize(psik, b.P0, b.Wfin, c->d_trial, per, Nw, s), "adjoint: sanitise");
-  CKW(launch_overlap<double>(c, Nw, b.P0, ws.theta, ws.logdet, b.st_scr, s), "adjoint: overlap");
-  CKW(gm(site_args<double>(c, SITE_FORCEBIAS, Nw, st, ws.theta, ws.t), false, EPI_STORE), "adjoint: force bias");
-  CKW(launch_bias_finalize<double>(c, Nw, x, st, s, b.keep), "adjoint: bias finalise");
-  CKW(gm(site_args<double>(c, SITE_FIELD, Nw, st, ws.c, ws.A), false, EPI_STORE), "adjoint: field");
+  CKW(adj_sanitize<R>(psik, b.P0, b.Wfin, c->d_trial, per, Nw, s), "adjoint: sanitise");
+  CKW(launch_overlap<R>(c, Nw, b.P0, ws.theta, ws.logdet, b.st_scr, s), "adjoint: overlap");
+  CKW(gm(site_args<R>(c, SITE_FORCEBIAS, Nw, st, ws.theta, ws.t), false, EPI_STORE), "adjoint: force bias");
+  CKW(launch_bias_finalize<R>(c, Nw, x, st, s, b.keep), "adjoint: bias finalise");
+  CKW(gm(site_args<R>(c, SITE_FIELD, Nw, st, ws.c, ws.A), false, EPI_STORE), "adjoint: field");
   nl += 3;
   const long long tstride = (long long)(K + 1) * perl, ustride = (long long)K * perl;
-  CKW(gm(gargs(N, nc, N, Nw, c->d_B, N, 1, 0, b.P0, N, 1, perl, b.Tb, 1, N, tstride), false, EPI_STORE),
+  CKW(gm(gargs(N, nc, N, Nw, pick<R>(c->d_B, c->f_B), N, 1, 0, b.P0, N, 1, perl, b.Tb, 1, N, tstride), false,
+         EPI_STORE),
       "adjoint: half step");
-  GemmArgs ga = site_args<double>(c, SITE_EXPM, Nw, st, nullptr, nullptr);
+  GemmArgs ga = site_args<R>(c, SITE_EXPM, Nw, st, nullptr, nullptr);
   ga.sb_b = tstride;
   ga.sc_b = tstride;
   for (int j = 1; j <= K; ++j) {
@@ -744,28 +770,29 @@ static afqmc_status adj_step(afqmc_ctx* c, const AdjBufs& b, int Nw, const doubl
     ga.alpha_im = 0.0;
     CKW(gm(ga, true, EPI_STORE), "adjoint: Taylor term");
   }
-  CKW(adj_sum_terms(b.Tb, b.psi2, K + 1, per, Nw, s), "adjoint: Taylor sum");
-  CKW(gm(site_args<double>(c, SITE_HALFSTEP, Nw, st, b.psi2, b.psi3), false, EPI_STORE), "adjoint: half step");
+  CKW(adj_sum_terms<R>(b.Tb, b.psi2, K + 1, per, Nw, s), "adjoint: Taylor sum");
+  CKW(gm(site_args<R>(c, SITE_HALFSTEP, Nw, st, b.psi2, b.psi3), false, EPI_STORE), "adjoint: half step");
   // overlap ratio and weight: Psi3_bar
-  CKW(adj_lu(c, Nw, b.psi3, b.oinv3, b.ld3, s), "adjoint: new overlap");
+  CKW(adj_lu<R>(c, Nw, b.psi3, b.oinv3, b.ld3, s), "adjoint: new overlap");
   CKW(adj_ratio_coef(Nw, b.Wfin, b.omega, b.ld3, lok, ws.scal, b.aR, st, s), "adjoint: ratio coefficient");
-  CKW(adj_ratio(c, Nw, b.pb, psinext, b.oinv3, b.aR, b.Wfin, b.p3, qr, s), "adjoint: ratio");
+  CKW(adj_ratio<R>(c, Nw, b.pb, psinext, b.oinv3, b.aR, b.Wfin, b.p3, qr, s), "adjoint: ratio");
   nl += 4;
   // second half step: Psi2_bar = B Psi3_bar, Bbar += Psi3_bar Psi2^T
-  CKW(gm(site_args<double>(c, SITE_HALFSTEP, Nw, st, b.p3, b.p2), false, EPI_STORE), "adjoint: half step");
-  GemmArgs gb = gargs(N, N, Nw * nc, 1, b.p3, 1, N, 0, b.psi2, 1, N, 0, b.Bbar, N, 1, 0);
+  CKW(gm(site_args<R>(c, SITE_HALFSTEP, Nw, st, b.p3, b.p2), false, EPI_STORE), "adjoint: half step");
+  auto bb = pacc(b.Bbar, b.sB, true);
+  GemmArgs gb = gargs(N, N, Nw * nc, 1, b.p3, 1, N, 0, b.psi2, 1, N, 0, bb.first, N, 1, 0);
   gb.splitk = b.skb;
   gb.part = b.part;
-  CKW(gm(gb, true, EPI_ACC), "adjoint: B adjoint");
+  CKW(gm(gb, true, bb.second), "adjoint: B adjoint");
   // Taylor action: U_j = T_bar_j / j in Ub slot j-1, T_bar_{j-1} = Psi2_bar + A U_j
-  CKW(adj_scale_copy(b.p2, per, b.Ub + (size_t)(K - 1) * per, (size_t)K * per, 1.0 / K, per, Nw, s),
+  CKW(adj_scale_copy<R>(b.p2, per, b.Ub + (size_t)(K - 1) * per, (size_t)K * per, 1.0 / K, per, Nw, s),
       "adjoint: Taylor seed");
   ++nl;
-  GemmArgs gu = site_args<double>(c, SITE_EXPM, Nw, st, nullptr, nullptr);
+  GemmArgs gu = site_args<R>(c, SITE_EXPM, Nw, st, nullptr, nullptr);
   gu.sb_b = ustride;
   gu.sc_b = ustride;
   for (int j = K; j >= 2; --j) {
-    CKW(adj_scale_copy(b.p2, per, b.Ub + (size_t)(j - 2) * per, (size_t)K * per, 1.0 / (j - 1), per, Nw, s),
+    CKW(adj_scale_copy<R>(b.p2, per, b.Ub + (size_t)(j - 2) * per, (size_t)K * per, 1.0 / (j - 1), per, Nw, s),
         "adjoint: Taylor copy");
     gu.B = b.Ub + (size_t)(j - 1) * per;
     gu.C = b.Ub + (size_t)(j - 2) * per;
@@ -775,48 +802,61 @@ static afqmc_status adj_step(afqmc_ctx* c, const AdjBufs& b, int Nw, const doubl
     ++nl;
   }
   CKW(cudaMemcpyAsync(b.p1, b.p2, (size_t)Nw * per * cs, cudaMemcpyDeviceToDevice, s), "adjoint: copy");
-  GemmArgs g1 = site_args<double>(c, SITE_EXPM, Nw, st, b.Ub, b.p1);
+  GemmArgs g1 = site_args<R>(c, SITE_EXPM, Nw, st, b.Ub, b.p1);
   g1.sb_b = ustride;
   CKW(gm(g1, true, EPI_ACC), "adjoint: Taylor adjoint");
   // A_bar[w] = sum_j U_j T_{j-1}^T
   CKW(gm(gargs(N, N, K * nc, Nw, b.Ub, 1, N, ustride, b.Tb, 1, N, tstride, b.Abar, N, 1, NNl), true, EPI_STORE),
       "adjoint: A adjoint");
   // A = i sqrt(tau) sum_g c_g L_g: c_bar = i sqrt(tau) <L_g, A_bar>, L_bar_g += i sqrt(tau) sum_w c_wg A_bar_w
-  GemmArgs gc = gargs(G, Nw, (int)NN, 1, c->d_L, NNl, 1, 0, b.Abar, NNl, 1, 0, b.cbar, 1, G, 0, 0.0, st);
+  GemmArgs gc = gargs(G, Nw, (int)NN, 1, pick<R>(c->d_L, c->f_L), NNl, 1, 0, b.Abar, NNl, 1, 0, b.cbar, 1, G, 0, 0.0,
+                      st);
   gc.splitk = b.skc;
   gc.part = b.part;
   CKW(gm(gc, false, EPI_STORE), "adjoint: c adjoint");
-  CKW(gm(gargs(G, (int)NN, Nw, 1, ws.c, 1, G, 0, b.Abar, 1, NNl, 0, b.gLc, NNl, 1, 0, 0.0, st), true, EPI_ACC),
+  auto bl = pacc(b.gLc, b.sL, true);
+  CKW(gm(gargs(G, (int)NN, Nw, 1, ws.c, 1, G, 0, b.Abar, 1, NNl, 0, bl.first, NNl, 1, 0, 0.0, st), true, bl.second),
       "adjoint: L adjoint (field)");
   // force bias and scalar factor
-  CKW(adj_force(c, Nw, b.cbar, static_cast<const double2*>(ws.c), b.keep, b.aR, b.omega, b.tbar, b.mu_part, b.mubar,
-                st, tau, s),
+  CKW(adj_force<R>(c, Nw, b.cbar, static_cast<const P*>(ws.c), b.keep, b.aR, b.omega, b.tbar, b.mu_part, b.mubar,
+                   st, tau, s),
       "adjoint: force bias");
   nl += 2;
   // t_g = sum tr(Lh_g Theta): Theta_bar = sum_g t_bar_g Lh_g^T, Lh_bar_g += sum_w t_bar_wg Theta_w
-  CKW(gm(gargs((int)per, Nw, G, 1, c->d_Lh, 1, perl, 0, b.tbar, G, 1, 0, b.thbar, 1, perl, 0), false, EPI_STORE),
+  CKW(gm(gargs((int)per, Nw, G, 1, pick<R>(c->d_Lh, c->f_Lh), 1, perl, 0, b.tbar, G, 1, 0, b.thbar, 1, perl, 0), false,
+         EPI_STORE),
       "adjoint: Theta adjoint");
-  CKW(gm(gargs(G, (int)per, Nw, 1, b.tbar, 1, G, 0, ws.theta, 1, perl, 0, b.Lhb, perl, 1, 0), true, EPI_ACC),
+  auto bh = pacc(b.Lhb, b.sLh, true);
+  CKW(gm(gargs(G, (int)per, Nw, 1, b.tbar, 1, G, 0, ws.theta, 1, perl, 0, bh.first, perl, 1, 0), true, bh.second),
       "adjoint: Lh adjoint");
   // first half step and Theta = Psi O^{-1}: Psi_bar_k
-  CKW(gm(site_args<double>(c, SITE_HALFSTEP, Nw, st, b.p1, b.pb), false, EPI_STORE), "adjoint: half step");
-  GemmArgs gb2 = gargs(N, N, Nw * nc, 1, b.p1, 1, N, 0, b.P0, 1, N, 0, b.Bbar, N, 1, 0);
+  CKW(gm(site_args<R>(c, SITE_HALFSTEP, Nw, st, b.p1, b.pb), false, EPI_STORE), "adjoint: half step");
+  auto bb2 = pacc(b.Bbar, b.sB, false);
+  GemmArgs gb2 = gargs(N, N, Nw * nc, 1, b.p1, 1, N, 0, b.P0, 1, N, 0, bb2.first, N, 1, 0);
   gb2.splitk = b.skb;
   gb2.part = b.part;
-  CKW(gm(gb2, true, EPI_ACC), "adjoint: B adjoint");
-  CKW(adj_lu(c, Nw, b.P0, b.oinvk, b.ldk, s), "adjoint: overlap inverse");
-  CKW(adj_theta(c, Nw, b.thbar, theta, b.oinvk, b.aR, b.Wfin, b.pb, s), "adjoint: Theta pull-back");
+  CKW(gm(gb2, true, bb2.second), "adjoint: B adjoint");
+  CKW(adj_lu<R>(c, Nw, b.P0, b.oinvk, b.ldk, s), "adjoint: overlap inverse");
+  CKW(adj_theta<R>(c, Nw, b.thbar, theta, b.oinvk, b.aR, b.Wfin, b.pb, s), "adjoint: Theta pull-back");
   nl += 2;
+  if (split) {
+    CKW(adj_fold(reinterpret_cast<const float2*>(b.sB), b.Bbar, NN, s), "adjoint: B sum");
+    CKW(adj_fold(reinterpret_cast<const float2*>(b.sL), b.gLc, (size_t)G * NN, s), "adjoint: L sum");
+    CKW(adj_fold(reinterpret_cast<const float2*>(b.sLh), b.Lhb, (size_t)G * per, s), "adjoint: Lh sum");
+    nl += 3;
+  }
   c->launches += nl;
   return AFQMC_OK;
 }
 
+template <typename R>
 static afqmc_status walk_backward_run(afqmc_ctx* c, const afqmc_walkers* w0, const double* fields,
                                       const afqmc_walk_adjoint_params* p, double* J_out, double* grad_h1,
-                                      double* grad_L, void* grad_psi0, const AdjBufs& b) {
+                                      double* grad_L, void* grad_psi0, const AdjBufs<R>& b) {
+  typedef typename C2<R>::t P;
   cudaStream_t s = c->stream;
   const int Nw = w0->n_walkers, N = c->N, nc = c->nc, G = c->G, K = p->order, C = p->ckpt_every, n = p->n_steps;
-  const size_t per = (size_t)nc * N, NN = (size_t)N * N, cs = sizeof(double2), nw = (size_t)Nw;
+  const size_t per = (size_t)nc * N, NN = (size_t)N * N, cs = sizeof(P), nw = (size_t)Nw;
   const size_t fstride = nw * G;
   const int nck = (n + C - 1) / C;
   const cudaMemcpyKind dd = cudaMemcpyDeviceToDevice;
@@ -854,10 +894,10 @@ static afqmc_status walk_backward_run(afqmc_ctx* c, const afqmc_walkers* w0, con
           "adjoint: checkpoint");
     }
     sp.reortho = qr_at(k);
-    afqmc_status rc = run_step<double>(c, &run, fields + (size_t)k * fstride, &sp, nullptr, nullptr);
+    afqmc_status rc = run_step<R>(c, &run, fields + (size_t)k * fstride, &sp, nullptr, nullptr);
     if (rc != AFQMC_OK) return rc;
   }
-  afqmc_status rc = run_energy<double>(c, &run, p->e0, p->tau, b.eloc, b.emix);
+  afqmc_status rc = run_energy<R>(c, &run, p->e0, p->tau, b.eloc, b.emix);
   if (rc != AFQMC_OK) return rc;
   CKW(cudaMemcpyAsync(b.Wfin, run.weight, nw * sizeof(double), dd, s), "adjoint: copy");
   if (J_out) CKW(cudaMemcpyAsync(J_out, b.emix, 4 * sizeof(double), dd, s), "adjoint: copy");
@@ -867,19 +907,19 @@ static afqmc_status walk_backward_run(afqmc_ctx* c, const afqmc_walkers* w0, con
   const double dE = 0.5 * std::sqrt(ne / p->tau) + std::sqrt(ne * p->tau);
   const double st = std::sqrt(p->tau);
   CKW(adj_seed_coef(Nw, b.Wfin, c->ws.ecap, b.eloc, b.emix, b.omega, b.ecoef, p->e0, dE, p->dJ, s), "adjoint: seed");
-  CKW(launch_energy_backward(c, Nw, b.Wfin, b.eloc, p->e0, p->tau, p->dJ, grad_h1, grad_L, b.ys, s),
+  CKW(launch_energy_backward<R>(c, Nw, b.Wfin, b.eloc, p->e0, p->tau, p->dJ, grad_h1, grad_L, b.ys, s),
       "adjoint: energy");
-  CKW(gemm<double>(site_args<double>(c, SITE_FORCEBIAS, Nw, st, c->ws.theta, c->ws.t), false, EPI_STORE, s),
-      "adjoint: force bias");
-  CKW(adj_eloc_seed(c, Nw, static_cast<const double2*>(c->ws.theta), static_cast<const double2*>(c->ws.t), b.ecoef,
-                    b.thbar, s),
+  GemmArgs gfb = site_args<R>(c, SITE_FORCEBIAS, Nw, st, c->ws.theta, c->ws.t);
+  CKW(gemm<R>(gfb, false, EPI_STORE, s), "adjoint: force bias");
+  CKW(adj_eloc_seed<R>(c, Nw, static_cast<const P*>(c->ws.theta), static_cast<const P*>(c->ws.t), b.ecoef, b.thbar,
+                       s),
       "adjoint: energy seed");
-  CKW(adj_sanitize(b.run_psi, b.P0, b.Wfin, c->d_trial, per, Nw, s), "adjoint: sanitise");
-  CKW(adj_lu(c, Nw, b.P0, b.oinvk, b.ldk, s), "adjoint: overlap inverse");
+  CKW(adj_sanitize<R>(b.run_psi, b.P0, b.Wfin, c->d_trial, per, Nw, s), "adjoint: sanitise");
+  CKW(adj_lu<R>(c, Nw, b.P0, b.oinvk, b.ldk, s), "adjoint: overlap inverse");
   CKW(cudaMemsetAsync(b.pb, 0, nw * per * cs, s), "adjoint: memset");
-  CKW(adj_theta(c, Nw, b.thbar, static_cast<const double2*>(c->ws.theta), b.oinvk, nullptr, b.Wfin, b.pb, s),
+  CKW(adj_theta<R>(c, Nw, b.thbar, static_cast<const P*>(c->ws.theta), b.oinvk, nullptr, b.Wfin, b.pb, s),
       "adjoint: Theta pull-back");
-  c->launches += 1 + 5 + 2 + 1 + 1 + 1 + 1;
+  c->launches += 1 + 5 + (gfb.splitk > 1 ? 2 : 1) + 1 + 1 + 1 + 1;
   CKW(cudaMemsetAsync(b.gLc, 0, (size_t)G * NN * cs, s), "adjoint: memset");
   CKW(cudaMemsetAsync(b.Lhb, 0, (size_t)G * per * cs, s), "adjoint: memset");
   CKW(cudaMemsetAsync(b.Bbar, 0, NN * cs, s), "adjoint: memset");
@@ -897,13 +937,13 @@ static afqmc_status walk_backward_run(afqmc_ctx* c, const afqmc_walkers* w0, con
       CKW(cudaMemcpyAsync(b.seg_psi + i * nw * per, run.psi, nw * per * cs, dd, s), "adjoint: store");
       CKW(cudaMemcpyAsync(b.seg_lo + i * nw * 2, run.logovl, nw * 2 * sizeof(double), dd, s), "adjoint: store");
       sp.reortho = qr_at(k);
-      rc = run_step<double>(c, &run, fields + (size_t)k * fstride, &sp, nullptr, nullptr);
+      rc = run_step<R>(c, &run, fields + (size_t)k * fstride, &sp, nullptr, nullptr);
       if (rc != AFQMC_OK) return rc;
     }
     CKW(cudaMemcpyAsync(b.seg_psi + (size_t)(k1 - k0) * nw * per, run.psi, nw * per * cs, dd, s), "adjoint: store");
     for (int k = k1 - 1; k >= k0; --k) {
       const size_t i = (size_t)(k - k0);
-      rc = adj_step(c, b, Nw, fields + (size_t)k * fstride, b.seg_psi + i * nw * per, b.seg_lo + i * nw * 2,
+      rc = adj_step<R>(c, b, Nw, fields + (size_t)k * fstride, b.seg_psi + i * nw * per, b.seg_lo + i * nw * 2,
                     b.seg_psi + (i + 1) * nw * per, qr_at(k), K, p->tau);
       if (rc != AFQMC_OK) return rc;
     }
@@ -918,6 +958,36 @@ static afqmc_status walk_backward_run(afqmc_ctx* c, const afqmc_walkers* w0, con
                  grad_L, &nfin, s),
       "adjoint: final");
   c->launches += nfin;
+  return AFQMC_OK;
+}
+
+// Allocate the adjoint's workspace (one block, carved twice: once to size it),
+// run the walk backward and free the block.
+template <typename R>
+static afqmc_status walk_backward_alloc(afqmc_ctx* c, const afqmc_walkers* w0, const double* fields,
+                                        const afqmc_walk_adjoint_params* q, int nck, double* J_out, double* grad_h1,
+                                        double* grad_L, void* grad_psi0) {
+  const int Nw = w0->n_walkers;
+  const size_t NN = (size_t)c->N * c->N;
+  AdjBufs<R> b{};
+  b.skc = pick_splitk(c->G, Nw, (long long)NN, 32);
+  b.skb = pick_splitk(c->N, c->N, (long long)Nw * c->nc, 64);
+  Arena a;
+  adj_carve<R>(a, b, c, Nw, q->order, q->ckpt_every, nck);
+  CK(cudaStreamSynchronize(c->stream));
+  char* base = nullptr;
+  cudaError_t e = cudaMalloc(&base, a.used);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cuda_fail(e, "adjoint workspace");
+  }
+  a = Arena{base, 0};
+  adj_carve<R>(a, b, c, Nw, q->order, q->ckpt_every, nck);
+  afqmc_status st = walk_backward_run<R>(c, w0, fields, q, J_out, grad_h1, grad_L, grad_psi0, b);
+  e = cudaStreamSynchronize(c->stream);
+  cudaFree(base);
+  if (st != AFQMC_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "adjoint");
   return AFQMC_OK;
 }
 
@@ -1093,7 +1163,6 @@ afqmc_status afqmc_energy_backward(afqmc_ctx* c, const afqmc_walkers* w, double 
   if (!grad_h1 || !grad_L || ((uintptr_t)grad_h1) % 8 || ((uintptr_t)grad_L) % 8) return AFQMC_EINVAL;
   if (!std::isfinite(tau) || !std::isfinite(e0) || !std::isfinite(dJ)) return AFQMC_EDOM;
   if (!(tau > 0.0)) return AFQMC_EINVAL;
-  if (c->prec != AFQMC_FP64) return AFQMC_ENOTSUP;
   const int nmax = c->na > c->nb ? c->na : c->nb;
   if ((size_t)(nmax * nmax + nmax * c->N) * 16 > (size_t)max_dyn_smem() - 1024) return AFQMC_ENOTSUP;
   const size_t NN = (size_t)c->N * c->N;
@@ -1105,12 +1174,16 @@ afqmc_status afqmc_energy_backward(afqmc_ctx* c, const afqmc_walkers* w, double 
   st = ws_ensure(c, w->n_walkers, c->ws.kmax);
   if (st != AFQMC_OK) return st;
   // Theta and E_L at the walkers (window mask), then the adjoint contractions
-  st = run_energy<double>(c, w, e0, tau, c->ws.eloc, c->ws.emix);
+  const bool fp64 = c->prec == AFQMC_FP64;
+  st = fp64 ? run_energy<double>(c, w, e0, tau, c->ws.eloc, c->ws.emix)
+            : run_energy<float>(c, w, e0, tau, c->ws.eloc, c->ws.emix);
   if (st != AFQMC_OK) return st;
   double2* ys = nullptr;
   CK(cudaMalloc(&ys, ((size_t)c->nc * c->N + (size_t)c->G * c->nc * c->N) * sizeof(double2)));
-  cudaError_t e = launch_energy_backward(c, w->n_walkers, w->weight, c->ws.eloc, e0, tau, dJ, grad_h1, grad_L, ys,
-                                         c->stream);
+  cudaError_t e = fp64 ? launch_energy_backward<double>(c, w->n_walkers, w->weight, c->ws.eloc, e0, tau, dJ, grad_h1,
+                                                        grad_L, ys, c->stream)
+                       : launch_energy_backward<float>(c, w->n_walkers, w->weight, c->ws.eloc, e0, tau, dJ, grad_h1,
+                                                       grad_L, ys, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   cudaFree(ys);
   if (e != cudaSuccess) return cuda_fail(e, "energy backward");
@@ -1128,7 +1201,6 @@ afqmc_status afqmc_walk_backward(afqmc_ctx* c, const afqmc_walkers* w0, const do
   if (!std::isfinite(p->tau) || !std::isfinite(p->e0) || !std::isfinite(p->dJ)) return AFQMC_EDOM;
   if (!(p->tau > 0.0) || p->n_steps < 1 || p->ckpt_every < 1 || p->reortho_every < 0) return AFQMC_EINVAL;
   if (p->order < 1 || p->order > 32) return AFQMC_ENOTSUP;
-  if (c->prec != AFQMC_FP64) return AFQMC_ENOTSUP;
   const int nmax = c->na > c->nb ? c->na : c->nb;
   if (nmax > 64 || w0->n_walkers > 65535) return AFQMC_ENOTSUP;
   if ((size_t)(nmax * nmax + nmax * c->N) * 16 > (size_t)max_dyn_smem() - 1024) return AFQMC_ENOTSUP;
@@ -1152,26 +1224,8 @@ afqmc_status afqmc_walk_backward(afqmc_ctx* c, const afqmc_walkers* w0, const do
   const int nck = (p->n_steps + C - 1) / C;
   afqmc_walk_adjoint_params q = *p;
   q.ckpt_every = C;
-  AdjBufs b{};
-  b.skc = pick_splitk(c->G, Nw, (long long)NN, 32);
-  b.skb = pick_splitk(c->N, c->N, (long long)Nw * c->nc, 64);
-  Arena a;
-  adj_carve(a, b, c, Nw, p->order, C, nck);
-  CK(cudaStreamSynchronize(c->stream));
-  char* base = nullptr;
-  cudaError_t e = cudaMalloc(&base, a.used);
-  if (e != cudaSuccess) {
-    cudaGetLastError();
-    return cuda_fail(e, "adjoint workspace");
-  }
-  a = Arena{base, 0};
-  adj_carve(a, b, c, Nw, p->order, C, nck);
-  st = walk_backward_run(c, w0, fields, &q, J_out, grad_h1, grad_L, grad_psi0, b);
-  e = cudaStreamSynchronize(c->stream);
-  cudaFree(base);
-  if (st != AFQMC_OK) return st;
-  if (e != cudaSuccess) return cuda_fail(e, "adjoint");
-  return AFQMC_OK;
+  return c->prec == AFQMC_FP64 ? walk_backward_alloc<double>(c, w0, fields, &q, nck, J_out, grad_h1, grad_L, grad_psi0)
+                               : walk_backward_alloc<float>(c, w0, fields, &q, nck, J_out, grad_h1, grad_L, grad_psi0);
 }
 
 afqmc_status afqmc_sync(afqmc_ctx* c) {

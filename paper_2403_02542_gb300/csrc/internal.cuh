@@ -272,33 +272,49 @@ cudaError_t launch_copy_alive(const afqmc_ctx* c, const afqmc_walkers* w, cudaSt
 template <typename R>
 cudaError_t launch_comb(afqmc_ctx* c, const afqmc_walkers* w, double u, int* index_out, cudaStream_t s);
 
-// adjoint of the mixed estimator (k_adjoint.cu)
+// adjoint of the mixed estimator (k_adjoint.cu); R = the walkers' real type
+template <typename R>
 cudaError_t launch_energy_backward(afqmc_ctx* c, int Nw, const double* weight, const double* e_loc, double e0,
                                    double tau, double dJ, double* grad_h1, double* grad_L, double2* yscratch,
                                    cudaStream_t s);
 
-// adjoint of the fixed-field walk (k_walk_adjoint.cu)
-cudaError_t adj_sanitize(const double2* src, double2* dst, const double* wfin, const double* trial, size_t per,
-                         int Nw, cudaStream_t s);
-cudaError_t adj_sum_terms(const double2* T, double2* out, int K1, size_t per, int Nw, cudaStream_t s);
-cudaError_t adj_scale_copy(const double2* src, size_t sstride, double2* dst, size_t dstride, double sc, size_t per,
-                           int Nw, cudaStream_t s);
+// adjoint of the fixed-field walk (k_walk_adjoint.cu); walker states and
+// their adjoints in C2<R>, overlap inverses, coefficients and sums in FP64
+template <typename R>
+cudaError_t adj_sanitize(const typename C2<R>::t* src, typename C2<R>::t* dst, const double* wfin,
+                         const double* trial, size_t per, int Nw, cudaStream_t s);
+template <typename R>
+cudaError_t adj_sum_terms(const typename C2<R>::t* T, typename C2<R>::t* out, int K1, size_t per, int Nw,
+                          cudaStream_t s);
+template <typename R>
+cudaError_t adj_scale_copy(const typename C2<R>::t* src, size_t sstride, typename C2<R>::t* dst, size_t dstride,
+                           double sc, size_t per, int Nw, cudaStream_t s);
+// dst[i] += src[i], i < n (FP64 accumulation of complex64 contributions)
+cudaError_t adj_fold(const float2* src, double2* dst, size_t n, cudaStream_t s);
 size_t adj_lu_smem(int nmax);
 size_t adj_small_smem(int nmax);
-cudaError_t adj_lu(const afqmc_ctx* c, int Nw, const double2* psi, double2* oinv, double* logdet, cudaStream_t s);
+template <typename R>
+cudaError_t adj_lu(const afqmc_ctx* c, int Nw, const typename C2<R>::t* psi, double2* oinv, double* logdet,
+                   cudaStream_t s);
 cudaError_t adj_ratio_coef(int Nw, const double* wfin, const double* omega, const double* ld3, const double* logovl,
                            const double* scal, double2* aR, double sqrt_tau, cudaStream_t s);
-cudaError_t adj_ratio(const afqmc_ctx* c, int Nw, const double2* pnext, const double2* psinext, const double2* oinv3,
-                      const double2* aR, const double* wfin, double2* p3, int qr, cudaStream_t s);
-cudaError_t adj_force(const afqmc_ctx* c, int Nw, const double2* cbar, const double2* cc, const uint8_t* keep,
-                      const double2* aR, const double* omega, double2* tbar, double* mu_part, double* mubar,
-                      double sqrt_tau, double tau, cudaStream_t s);
-cudaError_t adj_theta(const afqmc_ctx* c, int Nw, const double2* thbar, const double2* theta, const double2* oinv,
-                      const double2* aR, const double* wfin, double2* pbar, cudaStream_t s);
+template <typename R>
+cudaError_t adj_ratio(const afqmc_ctx* c, int Nw, const typename C2<R>::t* pnext, const typename C2<R>::t* psinext,
+                      const double2* oinv3, const double2* aR, const double* wfin, typename C2<R>::t* p3, int qr,
+                      cudaStream_t s);
+template <typename R>
+cudaError_t adj_force(const afqmc_ctx* c, int Nw, const typename C2<R>::t* cbar, const typename C2<R>::t* cc,
+                      const uint8_t* keep, const double2* aR, const double* omega, typename C2<R>::t* tbar,
+                      double* mu_part, double* mubar, double sqrt_tau, double tau, cudaStream_t s);
+template <typename R>
+cudaError_t adj_theta(const afqmc_ctx* c, int Nw, const typename C2<R>::t* thbar, const typename C2<R>::t* theta,
+                      const double2* oinv, const double2* aR, const double* wfin, typename C2<R>::t* pbar,
+                      cudaStream_t s);
 cudaError_t adj_seed_coef(int Nw, const double* wfin, const double* ecap, const double* e_loc, const double* emix,
                           double* omega, double* ecoef, double e0, double dE, double dJ, cudaStream_t s);
-cudaError_t adj_eloc_seed(const afqmc_ctx* c, int Nw, const double2* theta, const double2* t, const double* ecoef,
-                          double2* thbar, cudaStream_t s);
+template <typename R>
+cudaError_t adj_eloc_seed(const afqmc_ctx* c, int Nw, const typename C2<R>::t* theta, const typename C2<R>::t* t,
+                          const double* ecoef, typename C2<R>::t* thbar, cudaStream_t s);
 cudaError_t adj_finish(const afqmc_ctx* c, const double2* Bbar, const double* V, const double* lam, double tau,
                        double* Bs, double* T1, double* M1, double* hbar, double* X, double* D, const double2* gLc,
                        const double2* Lhb, double* mubar, double* grad_h1, double* grad_L, int* n_launch,

@@ -20,7 +20,11 @@
 //   t_g = sum_s tr(Lh_gs Theta_s), f_g = -i sqrt(tau)(t_g - L_bar_g) (kept
 //   components), c_g = x_g - f_g, A = i sqrt(tau) sum_g c_g L_g,
 //   log s = -tau E_c' - i sqrt(tau) sum_g c_g L_bar_g, log I = sum_g x_g f_g - f_g^2/2.
-// All arithmetic is FP64.
+// Precision: the walker states and their adjoints have the walkers' complex
+// type (complex128 in FP64 contexts, complex64 in mixed ones, where the long
+// contractions over N run in FP32); the per-walker overlap matrices, their
+// inverses and log-determinants, the scalar coefficients and every parameter
+// adjoint summed over walkers or steps are FP64.
 #include <math_constants.h>
 
 #include "internal.cuh"
@@ -36,6 +40,34 @@ inline int grid_for(size_t n) {
   return (int)(b > 152 * 32 ? 152 * 32 : (b == 0 ? 1 : b));
 }
 
+// complex number of the walkers' real type R
+template <typename R>
+struct cx {
+  R re, im;
+};
+template <typename R>
+__device__ __forceinline__ cx<R> operator+(cx<R> a, cx<R> b) { return cx<R>{a.re + b.re, a.im + b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator-(cx<R> a, cx<R> b) { return cx<R>{a.re - b.re, a.im - b.im}; }
+template <typename R>
+__device__ __forceinline__ cx<R> operator*(cx<R> a, cx<R> b) {
+  return cx<R>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> operator*(R s, cx<R> a) { return cx<R>{s * a.re, s * a.im}; }
+__device__ __forceinline__ cx<double> ldx(const double2& v) { return cx<double>{v.x, v.y}; }
+__device__ __forceinline__ cx<float> ldx(const float2& v) { return cx<float>{v.x, v.y}; }
+__device__ __forceinline__ double2 stx(cx<double> v) { return make_double2(v.re, v.im); }
+__device__ __forceinline__ float2 stx(cx<float> v) { return make_float2(v.re, v.im); }
+template <typename R>
+__device__ __forceinline__ cx<R> narrow(const double2& v) { return cx<R>{(R)v.x, (R)v.y}; }
+template <typename R>
+__device__ __forceinline__ cx<R> narrow(cd v) { return cx<R>{(R)v.re, (R)v.im}; }
+__device__ __forceinline__ cd widen(cx<double> v) { return mk(v.re, v.im); }
+__device__ __forceinline__ cd widen(cx<float> v) { return mk((double)v.re, (double)v.im); }
+__device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
+
 // (-i s) z
 __device__ __forceinline__ cd mul_mis(double s, cd z) { return mk(s * z.im, -s * z.re); }
 __device__ __forceinline__ cd ldc(const double2& v) { return mk(v.x, v.y); }
@@ -43,47 +75,64 @@ __device__ __forceinline__ cd ldc(const double2& v) { return mk(v.x, v.y); }
 // dst = src for walkers alive at the end of the walk, the trial otherwise
 // (dead walkers carry no adjoint; their stand-in state only keeps every
 // intermediate finite).
-__global__ void adj_sanitize_kernel(const double2* __restrict__ src, double2* __restrict__ dst,
+template <typename R>
+__global__ void adj_sanitize_kernel(const typename C2<R>::t* __restrict__ src, typename C2<R>::t* __restrict__ dst,
                                     const double* __restrict__ wfin, const double* __restrict__ trial, size_t per,
                                     size_t total) {
   for (size_t e = blockIdx.x * (size_t)AT + threadIdx.x; e < total; e += (size_t)gridDim.x * AT) {
     const size_t w = e / per;
-    dst[e] = wfin[w] > 0.0 ? src[e] : make_double2(trial[e - w * per], 0.0);
+    dst[e] = wfin[w] > 0.0 ? src[e] : stx(cx<R>{(R)trial[e - w * per], R(0)});
   }
 }
 
 // out[w] = sum_{j=0}^{K} T[w][j] in the order j = 0, 1, ..., K
-__global__ void adj_sum_terms_kernel(const double2* __restrict__ T, double2* __restrict__ out, int K1, size_t per,
-                                     size_t total) {
+template <typename R>
+__global__ void adj_sum_terms_kernel(const typename C2<R>::t* __restrict__ T, typename C2<R>::t* __restrict__ out,
+                                     int K1, size_t per, size_t total) {
   for (size_t e = blockIdx.x * (size_t)AT + threadIdx.x; e < total; e += (size_t)gridDim.x * AT) {
     const size_t w = e / per, r = e - w * per;
-    const double2* t = T + w * K1 * per + r;
-    double sr = t[0].x, si = t[0].y;
+    const typename C2<R>::t* t = T + w * K1 * per + r;
+    R sr = t[0].x, si = t[0].y;
     for (int j = 1; j < K1; ++j) {
       sr += t[(size_t)j * per].x;
       si += t[(size_t)j * per].y;
     }
-    out[e] = make_double2(sr, si);
+    out[e] = stx(cx<R>{sr, si});
   }
 }
 
 // dst[w][r] = s * src[w][r] with per-walker strides
-__global__ void adj_scale_copy_kernel(const double2* __restrict__ src, size_t sstride, double2* __restrict__ dst,
-                                      size_t dstride, double s, size_t per, size_t total) {
+template <typename R>
+__global__ void adj_scale_copy_kernel(const typename C2<R>::t* __restrict__ src, size_t sstride,
+                                      typename C2<R>::t* __restrict__ dst, size_t dstride, double s, size_t per,
+                                      size_t total) {
+  const R sc = (R)s;
   for (size_t e = blockIdx.x * (size_t)AT + threadIdx.x; e < total; e += (size_t)gridDim.x * AT) {
     const size_t w = e / per, r = e - w * per;
-    const double2 v = src[w * sstride + r];
-    dst[w * dstride + r] = make_double2(s * v.x, s * v.y);
+    dst[w * dstride + r] = stx(sc * ldx(src[w * sstride + r]));
   }
 }
 
-// O = trial_s^T psi_s for one (walker, spin); Gauss-Jordan elimination with
-// partial pivoting gives O^{-1} ([i][j], row stride n, in a slot of nmax^2)
-// and log det O = sum_k log pivot_k + i pi (odd number of row swaps).
+// dst += src (FP64 accumulator of a complex64 contribution)
+__global__ void adj_fold_kernel(const float2* __restrict__ src, double2* __restrict__ dst, size_t total) {
+  for (size_t e = blockIdx.x * (size_t)AT + threadIdx.x; e < total; e += (size_t)gridDim.x * AT) {
+    const float2 v = src[e];
+    double2 d = dst[e];
+    d.x += (double)v.x;
+    d.y += (double)v.y;
+    dst[e] = d;
+  }
+}
+
+// O = trial_s^T psi_s for one (walker, spin) (dot products over N in the
+// walkers' precision); FP64 Gauss-Jordan elimination with partial pivoting
+// gives O^{-1} ([i][j], row stride n, in a slot of nmax^2) and
+// log det O = sum_k log pivot_k + i pi (odd number of row swaps).
 // A zero pivot gives log det = NaN and O^{-1} = 0.
-__global__ void __launch_bounds__(AT) adj_lu_kernel(const double2* __restrict__ psi, const double* __restrict__ trial,
-                                                    double2* __restrict__ oinv, double* __restrict__ logdet, int N,
-                                                    int na, int nb, int nmax) {
+template <typename R>
+__global__ void __launch_bounds__(AT) adj_lu_kernel(const typename C2<R>::t* __restrict__ psi,
+                                                    const R* __restrict__ trial, double2* __restrict__ oinv,
+                                                    double* __restrict__ logdet, int N, int na, int nb, int nmax) {
   extern __shared__ double2 sm_lu[];
   const int w = blockIdx.x, spin = blockIdx.y;
   const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
@@ -98,17 +147,17 @@ __global__ void __launch_bounds__(AT) adj_lu_kernel(const double2* __restrict__ 
   __shared__ int s_piv, s_sing, s_swaps;
   __shared__ double s_lr, s_li;
   __shared__ double2 s_pinv;
-  const double2* P = psi + (size_t)w * nc * N;
+  const typename C2<R>::t* P = psi + (size_t)w * nc * N;
   for (int e = threadIdx.x; e < n * n; e += AT) {
     const int i = e / n, j = e - (e / n) * n;
-    const double* a = trial + (size_t)(off + i) * N;
-    const double2* b = P + (size_t)(off + j) * N;
-    double sr = 0.0, si = 0.0;
+    const R* a = trial + (size_t)(off + i) * N;
+    const typename C2<R>::t* b = P + (size_t)(off + j) * N;
+    R sr = R(0), si = R(0);
     for (int q = 0; q < N; ++q) {
-      sr = fma(a[q], b[q].x, sr);
-      si = fma(a[q], b[q].y, si);
+      sr = fmx(a[q], b[q].x, sr);
+      si = fmx(a[q], b[q].y, si);
     }
-    M[i * n2 + j] = make_double2(sr, si);
+    M[i * n2 + j] = make_double2((double)sr, (double)si);
     M[i * n2 + n + j] = make_double2(i == j ? 1.0 : 0.0, 0.0);
   }
   if (threadIdx.x == 0) {
@@ -202,63 +251,66 @@ __global__ void adj_ratio_coef_kernel(const double* __restrict__ wfin, const dou
 //   re-orthonormalised Psi' = Psi3 R^{-1} = Psi3 O3^{-1} O':
 //                             Psi3_bar = (Psi'_bar O'^T + a_R trial) O3^{-T}
 // with O' = trial^T Psi'.  Dead walkers get zero.
-__global__ void __launch_bounds__(AT) adj_ratio_kernel(const double2* __restrict__ pnext,
-                                                       const double2* __restrict__ psinext,
-                                                       const double* __restrict__ trial,
+template <typename R>
+__global__ void __launch_bounds__(AT) adj_ratio_kernel(const typename C2<R>::t* __restrict__ pnext,
+                                                       const typename C2<R>::t* __restrict__ psinext,
+                                                       const R* __restrict__ trial,
                                                        const double2* __restrict__ oinv3,
                                                        const double2* __restrict__ aR, const double* __restrict__ wfin,
-                                                       double2* __restrict__ p3, int N, int na, int nb, int nmax,
-                                                       int qr) {
-  extern __shared__ double2 sm_ra[];
+                                                       typename C2<R>::t* __restrict__ p3, int N, int na, int nb,
+                                                       int nmax, int qr) {
+  typedef typename C2<R>::t P;
+  extern __shared__ double2 sm_ra_raw[];
+  P* sm_ra = reinterpret_cast<P*>(sm_ra_raw);
   const int w = blockIdx.x, spin = blockIdx.y;
   const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
   if (n == 0) return;
-  double2* out = p3 + ((size_t)w * nc + off) * N;
+  P* out = p3 + ((size_t)w * nc + off) * N;
   if (!(wfin[w] > 0.0)) {
-    for (int e = threadIdx.x; e < n * N; e += AT) out[e] = make_double2(0.0, 0.0);
+    for (int e = threadIdx.x; e < n * N; e += AT) out[e] = stx(cx<R>{R(0), R(0)});
     return;
   }
-  double2* Oi = sm_ra;        // [n][n]  O3^{-1}
-  double2* On = Oi + n * n;   // [n][n]  O'
-  double2* Mx = On + n * n;   // [n][n]  O3^{-1} O'
+  P* Oi = sm_ra;        // [n][n]  O3^{-1}
+  P* On = Oi + n * n;   // [n][n]  O'
+  P* Mx = On + n * n;   // [n][n]  O3^{-1} O'
   const double2* src = oinv3 + ((size_t)w * 2 + spin) * nmax * nmax;
-  for (int e = threadIdx.x; e < n * n; e += AT) Oi[e] = src[e];
-  const double2* Pn = pnext + ((size_t)w * nc + off) * N;
+  for (int e = threadIdx.x; e < n * n; e += AT) Oi[e] = stx(narrow<R>(src[e]));
+  const P* Pn = pnext + ((size_t)w * nc + off) * N;
   if (qr) {
-    const double2* Sn = psinext + ((size_t)w * nc + off) * N;
+    const P* Sn = psinext + ((size_t)w * nc + off) * N;
     for (int e = threadIdx.x; e < n * n; e += AT) {
       const int i = e / n, l = e - (e / n) * n;
-      const double* a = trial + (size_t)(off + i) * N;
-      const double2* b = Sn + (size_t)l * N;
-      double sr = 0.0, si = 0.0;
+      const R* a = trial + (size_t)(off + i) * N;
+      const P* b = Sn + (size_t)l * N;
+      R sr = R(0), si = R(0);
       for (int q = 0; q < N; ++q) {
-        sr = fma(a[q], b[q].x, sr);
-        si = fma(a[q], b[q].y, si);
+        sr = fmx(a[q], b[q].x, sr);
+        si = fmx(a[q], b[q].y, si);
       }
-      On[e] = make_double2(sr, si);
+      On[e] = stx(cx<R>{sr, si});
     }
     __syncthreads();
     for (int e = threadIdx.x; e < n * n; e += AT) {
       const int j = e / n, l = e - (e / n) * n;
-      cd s = mk(0.0, 0.0);
-      for (int i = 0; i < n; ++i) s = s + ldc(Oi[j * n + i]) * ldc(On[i * n + l]);
-      Mx[e] = make_double2(s.re, s.im);
+      cx<R> s{R(0), R(0)};
+      for (int i = 0; i < n; ++i) s = s + ldx(Oi[j * n + i]) * ldx(On[i * n + l]);
+      Mx[e] = stx(s);
     }
   }
   __syncthreads();
-  const cd a = ldc(aR[w]);
+  const cx<R> a = narrow<R>(aR[w]);
   for (int e = threadIdx.x; e < n * N; e += AT) {
     const int j = e / N, p = e - (e / N) * N;
-    cd v = mk(0.0, 0.0);
+    cx<R> v{R(0), R(0)};
     if (qr) {
-      for (int l = 0; l < n; ++l) v = v + ldc(Pn[(size_t)l * N + p]) * ldc(Mx[j * n + l]);
+      for (int l = 0; l < n; ++l) v = v + ldx(Pn[(size_t)l * N + p]) * ldx(Mx[j * n + l]);
     } else {
-      v = ldc(Pn[(size_t)j * N + p]);
+      v = ldx(Pn[(size_t)j * N + p]);
     }
-    cd u = mk(0.0, 0.0);
-    for (int i = 0; i < n; ++i) u = u + trial[(size_t)(off + i) * N + p] * ldc(Oi[j * n + i]);
+    cx<R> u{R(0), R(0)};
+    for (int i = 0; i < n; ++i) u = u + trial[(size_t)(off + i) * N + p] * ldx(Oi[j * n + i]);
     v = v + a * u;
-    out[e] = make_double2(v.re, v.im);
+    out[e] = stx(v);
   }
 }
 
@@ -267,21 +319,22 @@ __global__ void __launch_bounds__(AT) adj_ratio_kernel(const double2* __restrict
 //   f_bar   = -c_bar + omega c_g                       (c = x - f; log I)
 //   t_bar   = kept ? -i sqrt(tau) f_bar : 0            (Eq. force_shift)
 //   Lbar_bar contribution: Re[-t_bar + a_R (-i sqrt(tau) c_g + tau L_bar_g)]
-__global__ void adj_force_kernel(const double2* __restrict__ cbar, const double2* __restrict__ c,
+template <typename R>
+__global__ void adj_force_kernel(const typename C2<R>::t* __restrict__ cbar, const typename C2<R>::t* __restrict__ c,
                                  const uint8_t* __restrict__ keep, const double2* __restrict__ aR,
                                  const double* __restrict__ omega, const double* __restrict__ Lbar,
-                                 double2* __restrict__ tbar, double* __restrict__ mu_part, int G, double sqrt_tau,
-                                 double tau, size_t total) {
+                                 typename C2<R>::t* __restrict__ tbar, double* __restrict__ mu_part, int G,
+                                 double sqrt_tau, double tau, size_t total) {
   for (size_t e = blockIdx.x * (size_t)AT + threadIdx.x; e < total; e += (size_t)gridDim.x * AT) {
     const size_t w = e / G;
     const int g = (int)(e - w * G);
     const cd a = ldc(aR[w]);
     const double om = omega[w], mu = Lbar[g];
-    const cd cg = ldc(c[e]);
-    const cd ctot = ldc(cbar[e]) + a * mul_mis(sqrt_tau, mk(mu, 0.0));
+    const cd cg = widen(ldx(c[e]));
+    const cd ctot = widen(ldx(cbar[e])) + a * mul_mis(sqrt_tau, mk(mu, 0.0));
     const cd fb = mk(-ctot.re + om * cg.re, -ctot.im + om * cg.im);
     const cd tb = keep[e] ? mul_mis(sqrt_tau, fb) : mk(0.0, 0.0);
-    tbar[e] = make_double2(tb.re, tb.im);
+    tbar[e] = stx(narrow<R>(tb));
     const cd m = a * (mul_mis(sqrt_tau, cg) + mk(tau * mu, 0.0));
     mu_part[e] = -tb.re + m.re;
   }
@@ -300,56 +353,60 @@ __global__ void adj_mu_reduce_kernel(const double* __restrict__ part, double* __
 // (walker, spin): the pull-back through Theta = Psi O^{-1} minus a times the
 // derivative trial O^{-T} of log det O (a = a_R: the old overlap enters log R
 // with a minus sign; a = 0 when aR is NULL).  Dead walkers are skipped.
-__global__ void __launch_bounds__(AT) adj_theta_kernel(const double2* __restrict__ thbar,
-                                                       const double2* __restrict__ theta,
-                                                       const double* __restrict__ trial,
+template <typename R>
+__global__ void __launch_bounds__(AT) adj_theta_kernel(const typename C2<R>::t* __restrict__ thbar,
+                                                       const typename C2<R>::t* __restrict__ theta,
+                                                       const R* __restrict__ trial,
                                                        const double2* __restrict__ oinv,
                                                        const double2* __restrict__ aR, const double* __restrict__ wfin,
-                                                       double2* __restrict__ pbar, int N, int na, int nb, int nmax) {
-  extern __shared__ double2 sm_th[];
+                                                       typename C2<R>::t* __restrict__ pbar, int N, int na, int nb,
+                                                       int nmax) {
+  typedef typename C2<R>::t P;
+  extern __shared__ double2 sm_th_raw[];
+  P* sm_th = reinterpret_cast<P*>(sm_th_raw);
   const int w = blockIdx.x, spin = blockIdx.y;
   const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
   if (n == 0 || !(wfin[w] > 0.0)) return;
-  double2* Oi = sm_th;       // [n][n] O^{-1}
-  double2* S = Oi + n * n;   // [n][n] S[l][i] = (Theta^T Theta_bar)_li + a delta_li
-  double2* Q = S + n * n;    // [n][n] Q[j][l] = sum_i O^{-1}[j][i] S[l][i]
+  P* Oi = sm_th;       // [n][n] O^{-1}
+  P* S = Oi + n * n;   // [n][n] S[l][i] = (Theta^T Theta_bar)_li + a delta_li
+  P* Q = S + n * n;    // [n][n] Q[j][l] = sum_i O^{-1}[j][i] S[l][i]
   const double2* src = oinv + ((size_t)w * 2 + spin) * nmax * nmax;
-  for (int e = threadIdx.x; e < n * n; e += AT) Oi[e] = src[e];
-  const double2* Tb = thbar + ((size_t)w * nc + off) * N;
-  const double2* Th = theta + ((size_t)w * nc + off) * N;
-  const cd a = aR ? ldc(aR[w]) : mk(0.0, 0.0);
+  for (int e = threadIdx.x; e < n * n; e += AT) Oi[e] = stx(narrow<R>(src[e]));
+  const P* Tb = thbar + ((size_t)w * nc + off) * N;
+  const P* Th = theta + ((size_t)w * nc + off) * N;
+  const cx<R> a = aR ? narrow<R>(aR[w]) : cx<R>{R(0), R(0)};
   for (int e = threadIdx.x; e < n * n; e += AT) {
     const int l = e / n, i = e - (e / n) * n;
-    const double2* x = Th + (size_t)l * N;
-    const double2* y = Tb + (size_t)i * N;
-    double sr = 0.0, si = 0.0;
+    const P* x = Th + (size_t)l * N;
+    const P* y = Tb + (size_t)i * N;
+    R sr = R(0), si = R(0);
     for (int p = 0; p < N; ++p) {
-      sr = fma(x[p].x, y[p].x, sr);
-      sr = fma(-x[p].y, y[p].y, sr);
-      si = fma(x[p].x, y[p].y, si);
-      si = fma(x[p].y, y[p].x, si);
+      sr = fmx(x[p].x, y[p].x, sr);
+      sr = fmx(-x[p].y, y[p].y, sr);
+      si = fmx(x[p].x, y[p].y, si);
+      si = fmx(x[p].y, y[p].x, si);
     }
     if (l == i) {
       sr += a.re;
       si += a.im;
     }
-    S[e] = make_double2(sr, si);
+    S[e] = stx(cx<R>{sr, si});
   }
   __syncthreads();
   for (int e = threadIdx.x; e < n * n; e += AT) {
     const int j = e / n, l = e - (e / n) * n;
-    cd s = mk(0.0, 0.0);
-    for (int i = 0; i < n; ++i) s = s + ldc(Oi[j * n + i]) * ldc(S[l * n + i]);
-    Q[e] = make_double2(s.re, s.im);
+    cx<R> s{R(0), R(0)};
+    for (int i = 0; i < n; ++i) s = s + ldx(Oi[j * n + i]) * ldx(S[l * n + i]);
+    Q[e] = stx(s);
   }
   __syncthreads();
-  double2* out = pbar + ((size_t)w * nc + off) * N;
+  P* out = pbar + ((size_t)w * nc + off) * N;
   for (int e = threadIdx.x; e < n * N; e += AT) {
     const int j = e / N, p = e - (e / N) * N;
-    cd v = ldc(out[e]);
-    for (int i = 0; i < n; ++i) v = v + ldc(Tb[(size_t)i * N + p]) * ldc(Oi[j * n + i]);
-    for (int l = 0; l < n; ++l) v = v - trial[(size_t)(off + l) * N + p] * ldc(Q[j * n + l]);
-    out[e] = make_double2(v.re, v.im);
+    cx<R> v = ldx(out[e]);
+    for (int i = 0; i < n; ++i) v = v + ldx(Tb[(size_t)i * N + p]) * ldx(Oi[j * n + i]);
+    for (int l = 0; l < n; ++l) v = v - trial[(size_t)(off + l) * N + p] * ldx(Q[j * n + l]);
+    out[e] = stx(v);
   }
 }
 
@@ -373,32 +430,35 @@ __global__ void adj_seed_coef_kernel(const double* __restrict__ wfin, const doub
 // Theta_bar of the local energy for one (walker, spin, row chunk):
 //   dE_L/dTheta_s[p][j] = h_half[j][p] + sum_g [ t_g Lh_g[j][p] - sum_i Lh_g[i][p] T_gs[j][i] ]
 // with T_gs[j][i] = sum_q Lh_g[j][q] Theta_s[i][q] and t_g the trace over
-// both spins; scaled by e_w.
+// both spins; scaled by e_w.  The term of each g is formed in the walkers'
+// precision and summed over g in FP64.
 constexpr int SEED_R = 16;  // outputs per thread
-__global__ void __launch_bounds__(AT) adj_eloc_seed_kernel(const double2* __restrict__ theta,
-                                                           const double2* __restrict__ t,
-                                                           const double* __restrict__ Lh,
+template <typename R>
+__global__ void __launch_bounds__(AT) adj_eloc_seed_kernel(const typename C2<R>::t* __restrict__ theta,
+                                                           const typename C2<R>::t* __restrict__ t,
+                                                           const R* __restrict__ Lh,
                                                            const double* __restrict__ hhalf,
                                                            const double* __restrict__ ecoef,
-                                                           double2* __restrict__ thbar, int N, int na, int nb, int G,
-                                                           int prows) {
-  extern __shared__ double2 sm_es[];
+                                                           typename C2<R>::t* __restrict__ thbar, int N, int na,
+                                                           int nb, int G, int prows) {
+  typedef typename C2<R>::t P;
+  extern __shared__ double2 sm_es_raw[];
+  P* T = reinterpret_cast<P*>(sm_es_raw);  // [n][n]
   const int w = blockIdx.x, spin = blockIdx.y;
   const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
   const int p0 = blockIdx.z * prows;
   const int pr = min(prows, N - p0);
   if (n == 0 || pr <= 0) return;
-  double2* out = thbar + ((size_t)w * nc + off) * N;
+  P* out = thbar + ((size_t)w * nc + off) * N;
   const double ew = ecoef[w];
   if (ew == 0.0) {
     for (int e = threadIdx.x; e < n * pr; e += AT) {
       const int j = e / pr, p = p0 + e - (e / pr) * pr;
-      out[(size_t)j * N + p] = make_double2(0.0, 0.0);
+      out[(size_t)j * N + p] = stx(cx<R>{R(0), R(0)});
     }
     return;
   }
-  double2* T = sm_es;  // [n][n]
-  const double2* Th = theta + ((size_t)w * nc + off) * N;
+  const P* Th = theta + ((size_t)w * nc + off) * N;
   cd acc[SEED_R];
   int jj[SEED_R], pp[SEED_R];
 #pragma unroll
@@ -414,33 +474,33 @@ __global__ void __launch_bounds__(AT) adj_eloc_seed_kernel(const double2* __rest
     }
   }
   for (int g = 0; g < G; ++g) {
-    const double* Lg = Lh + ((size_t)g * nc + off) * N;
+    const R* Lg = Lh + ((size_t)g * nc + off) * N;
     __syncthreads();
     for (int e = threadIdx.x; e < n * n; e += AT) {
       const int j = e / n, i = e - (e / n) * n;
-      const double* a = Lg + (size_t)j * N;
-      const double2* b = Th + (size_t)i * N;
-      double sr = 0.0, si = 0.0;
+      const R* a = Lg + (size_t)j * N;
+      const P* b = Th + (size_t)i * N;
+      R sr = R(0), si = R(0);
       for (int q = 0; q < N; ++q) {
-        sr = fma(a[q], b[q].x, sr);
-        si = fma(a[q], b[q].y, si);
+        sr = fmx(a[q], b[q].x, sr);
+        si = fmx(a[q], b[q].y, si);
       }
-      T[e] = make_double2(sr, si);
+      T[e] = stx(cx<R>{sr, si});
     }
     __syncthreads();
-    const cd tg = ldc(t[(size_t)w * G + g]);
+    const cx<R> tg = ldx(t[(size_t)w * G + g]);
 #pragma unroll
     for (int r = 0; r < SEED_R; ++r) {
       if (jj[r] < 0) continue;
       const int j = jj[r], p = pp[r];
-      cd v = acc[r] + Lg[(size_t)j * N + p] * tg;
-      for (int i = 0; i < n; ++i) v = v - Lg[(size_t)i * N + p] * ldc(T[j * n + i]);
-      acc[r] = v;
+      cx<R> v = Lg[(size_t)j * N + p] * tg;
+      for (int i = 0; i < n; ++i) v = v - Lg[(size_t)i * N + p] * ldx(T[j * n + i]);
+      acc[r] = acc[r] + widen(v);
     }
   }
 #pragma unroll
   for (int r = 0; r < SEED_R; ++r)
-    if (jj[r] >= 0) out[(size_t)jj[r] * N + pp[r]] = make_double2(ew * acc[r].re, ew * acc[r].im);
+    if (jj[r] >= 0) out[(size_t)jj[r] * N + pp[r]] = stx(narrow<R>(mk(ew * acc[r].re, ew * acc[r].im)));
 }
 
 // ------------------------------------------------------------ final assembly
@@ -576,35 +636,60 @@ cudaError_t smem_ok(F* f, size_t bytes) {
 }  // namespace
 
 // ------------------------------------------------------------ launch wrappers
-cudaError_t adj_sanitize(const double2* src, double2* dst, const double* wfin, const double* trial, size_t per,
-                         int Nw, cudaStream_t s) {
+// the trial and Lh in the walkers' precision (mixed contexts hold FP32 copies)
+template <typename R>
+const R* trial_of(const afqmc_ctx* c);
+template <>
+const double* trial_of<double>(const afqmc_ctx* c) { return c->d_trial; }
+template <>
+const float* trial_of<float>(const afqmc_ctx* c) { return c->f_trial; }
+template <typename R>
+const R* lh_of(const afqmc_ctx* c);
+template <>
+const double* lh_of<double>(const afqmc_ctx* c) { return c->d_Lh; }
+template <>
+const float* lh_of<float>(const afqmc_ctx* c) { return c->f_Lh; }
+
+template <typename R>
+cudaError_t adj_sanitize(const typename C2<R>::t* src, typename C2<R>::t* dst, const double* wfin,
+                         const double* trial, size_t per, int Nw, cudaStream_t s) {
   const size_t total = per * Nw;
-  adj_sanitize_kernel<<<grid_for(total), AT, 0, s>>>(src, dst, wfin, trial, per, total);
+  adj_sanitize_kernel<R><<<grid_for(total), AT, 0, s>>>(src, dst, wfin, trial, per, total);
   return cudaGetLastError();
 }
 
-cudaError_t adj_sum_terms(const double2* T, double2* out, int K1, size_t per, int Nw, cudaStream_t s) {
+template <typename R>
+cudaError_t adj_sum_terms(const typename C2<R>::t* T, typename C2<R>::t* out, int K1, size_t per, int Nw,
+                          cudaStream_t s) {
   const size_t total = per * Nw;
-  adj_sum_terms_kernel<<<grid_for(total), AT, 0, s>>>(T, out, K1, per, total);
+  adj_sum_terms_kernel<R><<<grid_for(total), AT, 0, s>>>(T, out, K1, per, total);
   return cudaGetLastError();
 }
 
-cudaError_t adj_scale_copy(const double2* src, size_t sstride, double2* dst, size_t dstride, double sc, size_t per,
-                           int Nw, cudaStream_t s) {
+template <typename R>
+cudaError_t adj_scale_copy(const typename C2<R>::t* src, size_t sstride, typename C2<R>::t* dst, size_t dstride,
+                           double sc, size_t per, int Nw, cudaStream_t s) {
   const size_t total = per * Nw;
-  adj_scale_copy_kernel<<<grid_for(total), AT, 0, s>>>(src, sstride, dst, dstride, sc, per, total);
+  adj_scale_copy_kernel<R><<<grid_for(total), AT, 0, s>>>(src, sstride, dst, dstride, sc, per, total);
+  return cudaGetLastError();
+}
+
+cudaError_t adj_fold(const float2* src, double2* dst, size_t n, cudaStream_t s) {
+  adj_fold_kernel<<<grid_for(n), AT, 0, s>>>(src, dst, n);
   return cudaGetLastError();
 }
 
 size_t adj_lu_smem(int nmax) { return (size_t)(2 * nmax * nmax + nmax) * sizeof(double2); }
 size_t adj_small_smem(int nmax) { return (size_t)3 * nmax * nmax * sizeof(double2); }
 
-cudaError_t adj_lu(const afqmc_ctx* c, int Nw, const double2* psi, double2* oinv, double* logdet, cudaStream_t s) {
+template <typename R>
+cudaError_t adj_lu(const afqmc_ctx* c, int Nw, const typename C2<R>::t* psi, double2* oinv, double* logdet,
+                   cudaStream_t s) {
   const int nmax = c->na > c->nb ? c->na : c->nb;
   const size_t shm = adj_lu_smem(nmax);
-  cudaError_t e = smem_ok(adj_lu_kernel, shm);
+  cudaError_t e = smem_ok(adj_lu_kernel<R>, shm);
   if (e != cudaSuccess) return e;
-  adj_lu_kernel<<<dim3(Nw, 2), AT, shm, s>>>(psi, c->d_trial, oinv, logdet, c->N, c->na, c->nb, nmax);
+  adj_lu_kernel<R><<<dim3(Nw, 2), AT, shm, s>>>(psi, trial_of<R>(c), oinv, logdet, c->N, c->na, c->nb, nmax);
   return cudaGetLastError();
 }
 
@@ -614,37 +699,42 @@ cudaError_t adj_ratio_coef(int Nw, const double* wfin, const double* omega, cons
   return cudaGetLastError();
 }
 
-cudaError_t adj_ratio(const afqmc_ctx* c, int Nw, const double2* pnext, const double2* psinext, const double2* oinv3,
-                      const double2* aR, const double* wfin, double2* p3, int qr, cudaStream_t s) {
+template <typename R>
+cudaError_t adj_ratio(const afqmc_ctx* c, int Nw, const typename C2<R>::t* pnext, const typename C2<R>::t* psinext,
+                      const double2* oinv3, const double2* aR, const double* wfin, typename C2<R>::t* p3, int qr,
+                      cudaStream_t s) {
   const int nmax = c->na > c->nb ? c->na : c->nb;
   const size_t shm = adj_small_smem(nmax);
-  cudaError_t e = smem_ok(adj_ratio_kernel, shm);
+  cudaError_t e = smem_ok(adj_ratio_kernel<R>, shm);
   if (e != cudaSuccess) return e;
-  adj_ratio_kernel<<<dim3(Nw, 2), AT, shm, s>>>(pnext, psinext, c->d_trial, oinv3, aR, wfin, p3, c->N, c->na, c->nb,
-                                                nmax, qr);
+  adj_ratio_kernel<R><<<dim3(Nw, 2), AT, shm, s>>>(pnext, psinext, trial_of<R>(c), oinv3, aR, wfin, p3, c->N, c->na,
+                                                   c->nb, nmax, qr);
   return cudaGetLastError();
 }
 
-cudaError_t adj_force(const afqmc_ctx* c, int Nw, const double2* cbar, const double2* cc, const uint8_t* keep,
-                      const double2* aR, const double* omega, double2* tbar, double* mu_part, double* mubar,
-                      double sqrt_tau, double tau, cudaStream_t s) {
+template <typename R>
+cudaError_t adj_force(const afqmc_ctx* c, int Nw, const typename C2<R>::t* cbar, const typename C2<R>::t* cc,
+                      const uint8_t* keep, const double2* aR, const double* omega, typename C2<R>::t* tbar,
+                      double* mu_part, double* mubar, double sqrt_tau, double tau, cudaStream_t s) {
   const size_t total = (size_t)Nw * c->G;
-  adj_force_kernel<<<grid_for(total), AT, 0, s>>>(cbar, cc, keep, aR, omega, c->d_Lbar, tbar, mu_part, c->G,
-                                                  sqrt_tau, tau, total);
+  adj_force_kernel<R><<<grid_for(total), AT, 0, s>>>(cbar, cc, keep, aR, omega, c->d_Lbar, tbar, mu_part, c->G,
+                                                     sqrt_tau, tau, total);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   adj_mu_reduce_kernel<<<(c->G + 127) / 128, 128, 0, s>>>(mu_part, mubar, Nw, c->G);
   return cudaGetLastError();
 }
 
-cudaError_t adj_theta(const afqmc_ctx* c, int Nw, const double2* thbar, const double2* theta, const double2* oinv,
-                      const double2* aR, const double* wfin, double2* pbar, cudaStream_t s) {
+template <typename R>
+cudaError_t adj_theta(const afqmc_ctx* c, int Nw, const typename C2<R>::t* thbar, const typename C2<R>::t* theta,
+                      const double2* oinv, const double2* aR, const double* wfin, typename C2<R>::t* pbar,
+                      cudaStream_t s) {
   const int nmax = c->na > c->nb ? c->na : c->nb;
   const size_t shm = adj_small_smem(nmax);
-  cudaError_t e = smem_ok(adj_theta_kernel, shm);
+  cudaError_t e = smem_ok(adj_theta_kernel<R>, shm);
   if (e != cudaSuccess) return e;
-  adj_theta_kernel<<<dim3(Nw, 2), AT, shm, s>>>(thbar, theta, c->d_trial, oinv, aR, wfin, pbar, c->N, c->na, c->nb,
-                                                nmax);
+  adj_theta_kernel<R><<<dim3(Nw, 2), AT, shm, s>>>(thbar, theta, trial_of<R>(c), oinv, aR, wfin, pbar, c->N, c->na,
+                                                   c->nb, nmax);
   return cudaGetLastError();
 }
 
@@ -654,20 +744,41 @@ cudaError_t adj_seed_coef(int Nw, const double* wfin, const double* ecap, const 
   return cudaGetLastError();
 }
 
-cudaError_t adj_eloc_seed(const afqmc_ctx* c, int Nw, const double2* theta, const double2* t, const double* ecoef,
-                          double2* thbar, cudaStream_t s) {
+template <typename R>
+cudaError_t adj_eloc_seed(const afqmc_ctx* c, int Nw, const typename C2<R>::t* theta, const typename C2<R>::t* t,
+                          const double* ecoef, typename C2<R>::t* thbar, cudaStream_t s) {
   const int nmax = c->na > c->nb ? c->na : c->nb;
   if (nmax == 0) return cudaSuccess;
   int prows = (SEED_R * AT) / nmax;
   if (prows > c->N) prows = c->N;
   const int chunks = (c->N + prows - 1) / prows;
-  const size_t shm = (size_t)nmax * nmax * sizeof(double2);
-  cudaError_t e = smem_ok(adj_eloc_seed_kernel, shm);
+  const size_t shm = (size_t)nmax * nmax * sizeof(typename C2<R>::t);
+  cudaError_t e = smem_ok(adj_eloc_seed_kernel<R>, shm);
   if (e != cudaSuccess) return e;
-  adj_eloc_seed_kernel<<<dim3(Nw, 2, chunks), AT, shm, s>>>(theta, t, c->d_Lh, c->d_hhalf, ecoef, thbar, c->N, c->na,
-                                                           c->nb, c->G, prows);
+  adj_eloc_seed_kernel<R><<<dim3(Nw, 2, chunks), AT, shm, s>>>(theta, t, lh_of<R>(c), c->d_hhalf, ecoef, thbar,
+                                                              c->N, c->na, c->nb, c->G, prows);
   return cudaGetLastError();
 }
+
+#define AFQ_ADJ_INST(R)                                                                                            \
+  template cudaError_t adj_sanitize<R>(const C2<R>::t*, C2<R>::t*, const double*, const double*, size_t, int,     \
+                                       cudaStream_t);                                                              \
+  template cudaError_t adj_sum_terms<R>(const C2<R>::t*, C2<R>::t*, int, size_t, int, cudaStream_t);               \
+  template cudaError_t adj_scale_copy<R>(const C2<R>::t*, size_t, C2<R>::t*, size_t, double, size_t, int,          \
+                                         cudaStream_t);                                                            \
+  template cudaError_t adj_lu<R>(const afqmc_ctx*, int, const C2<R>::t*, double2*, double*, cudaStream_t);         \
+  template cudaError_t adj_ratio<R>(const afqmc_ctx*, int, const C2<R>::t*, const C2<R>::t*, const double2*,       \
+                                    const double2*, const double*, C2<R>::t*, int, cudaStream_t);                  \
+  template cudaError_t adj_force<R>(const afqmc_ctx*, int, const C2<R>::t*, const C2<R>::t*, const uint8_t*,       \
+                                    const double2*, const double*, C2<R>::t*, double*, double*, double, double,    \
+                                    cudaStream_t);                                                                 \
+  template cudaError_t adj_theta<R>(const afqmc_ctx*, int, const C2<R>::t*, const C2<R>::t*, const double2*,       \
+                                    const double2*, const double*, C2<R>::t*, cudaStream_t);                       \
+  template cudaError_t adj_eloc_seed<R>(const afqmc_ctx*, int, const C2<R>::t*, const C2<R>::t*, const double*,    \
+                                        C2<R>::t*, cudaStream_t);
+AFQ_ADJ_INST(double)
+AFQ_ADJ_INST(float)
+#undef AFQ_ADJ_INST
 
 // hbar'' from Bbar: hbar = V (F o (V^T sym(Re Bbar) V)) V^T; then
 // mubar += <hbar, L_g>, X_g = L_g hbar, and the final symmetrised gradients.

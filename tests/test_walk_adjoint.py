@@ -43,10 +43,10 @@ def _e0(s):
     return float(R.local_energy(ham, ham.trial.to(CT)).real)
 
 
-def _gpu(s, nw, fields, tau, e0, order, r, ckpt, dead=(), psi_grad=False, h1=None, L=None):
+def _gpu(s, nw, fields, tau, e0, order, r, ckpt, dead=(), psi_grad=False, h1=None, L=None, precision="fp64"):
     from paper_2403_02542_gb300.api import Context
     ctx = Context(s.h1 if h1 is None else h1, s.L if L is None else L, s.trial, s.na, s.nb, s.e_const,
-                  precision="fp64")
+                  precision=precision)
     w = ctx.new_walkers(nw)
     ctx.init_walkers(w)
     for d in dead:
@@ -215,7 +215,80 @@ def test_walk_adjoint_argument_checks():
     wm = mixed.new_walkers(2)
     mixed.init_walkers(wm)
     with pytest.raises(Lb.AfqmcError):
-        mixed.walk_backward(wm, f, 0.05, -1.0)
+        mixed.walk_backward(wm, f, 0.05, -1.0, order=33)
+    J, gh, gL, gp = mixed.walk_backward(wm, f, 0.05, -1.0, grad_psi0=True)
+    assert gp.dtype == torch.complex64 and gh.dtype == RT and gL.shape == (s.G, 8, 8)
+    assert bool(torch.isfinite(gh).all()) and bool(torch.isfinite(gL).all())
+    mixed.close()
     e = ctx.new_walkers(0)
     J, gh, gL = ctx.walk_backward(e, torch.zeros(2, 0, s.G, dtype=RT, device=ctx.device), 0.05, -1.0)
     assert torch.all(gh == 0) and torch.all(gL == 0)
+
+
+# ---------------------------------------------------------------- mixed precision
+# Complex64 walkers: the walk and its reverse run with FP32 contractions (the
+# step's own tensor-core field and Taylor products forward, SIMT FP32 in the
+# recomputed steps and the reverse), FP64 overlaps, determinants, weights and
+# gradient sums.  Tolerances: J is an energy and takes the mixed energy bar
+# (1e-4 Ha); a gradient entry carries the FP32 relative rounding of the
+# contractions it passes through (about 6e-8 times a growth factor of a few
+# hundred over the Taylor terms, steps and walker sums), so 1e-4 of the
+# largest entry bounds it with room, and 3e-6 of the largest entry is far
+# below any sign or index mistake, which would change entries at O(1).
+
+MIXED_J_TOL = 1e-4        # Ha
+MIXED_GRAD_RTOL = 1e-4    # of the largest entry
+
+
+@pytest.mark.parametrize("N,na,nb,G,nw,steps,r,ckpt,dead", [
+    (10, 2, 2, 12, 5, 6, 2, 3, (1,)),
+    (14, 3, 2, 20, 6, 7, 3, 2, ()),
+    (24, 3, 3, 40, 4, 5, 0, 10, (3,)),
+    (12, 2, 0, 16, 3, 4, 1, 1, ()),
+])
+def test_walk_adjoint_mixed_matches_oracle_autograd(N, na, nb, G, nw, steps, r, ckpt, dead):
+    s = _Sys(N, na, nb, G, seed=N + steps)
+    tau, order = 0.05, 6
+    e0 = _e0(s)
+    fields = [make_fields(N, k, nw, G) for k in range(steps)]
+    J_ref, gh_ref, gL_ref, gp_ref, W_ref = _oracle(s, nw, fields, tau, e0, order, r, dead)
+    assert int((W_ref > 0).sum()) == nw - len(dead)
+    J, gh, gL, gp = _gpu(s, nw, fields, tau, e0, order, r, ckpt, dead, psi_grad=True, precision="mixed")
+    assert gp.dtype == torch.complex64
+    assert abs(float(J[2]) - J_ref) <= MIXED_J_TOL
+    _close(gh, gh_ref, MIXED_GRAD_RTOL)
+    _close(gL, gL_ref, MIXED_GRAD_RTOL)
+    _close(gp.to(CT), gp_ref.transpose(1, 2), MIXED_GRAD_RTOL)
+    assert torch.equal(gh, gh.T) and torch.equal(gL, gL.transpose(1, 2))
+
+
+def test_walk_adjoint_mixed_is_independent_of_checkpoint_spacing():
+    """The recomputed segments replay the same deterministic complex64 steps,
+    so the checkpoint spacing changes no bit of the mixed result either."""
+    s = _Sys(12, 2, 2, 18, seed=5)
+    tau, nw, steps = 0.05, 5, 8
+    e0 = _e0(s)
+    fields = [make_fields(7, k, nw, s.G) for k in range(steps)]
+    ref = _gpu(s, nw, fields, tau, e0, 6, 3, steps, psi_grad=True, precision="mixed")
+    for ckpt in (1, 3):
+        got = _gpu(s, nw, fields, tau, e0, 6, 3, ckpt, psi_grad=True, precision="mixed")
+        for a, b in zip(got, ref):
+            assert torch.equal(a, b), ckpt
+
+
+def test_walk_adjoint_mixed_full_size_against_fp64():
+    """The differentiation workload at full size (N=96, 15+15 electrons, 480
+    vectors, 512 walkers, 100 steps, Taylor-6, QR every 10 steps): the mixed
+    J and gradients against the FP64 ones (pinned to autograd through the
+    oracle and to central differences above), entry by entry."""
+    cfg = CONFIGS["grad"]
+    s = config_system("grad")
+    tau, nw, steps = cfg["tau"], cfg["walkers"], cfg["steps"]
+    e0 = _e0(s)
+    fields = [make_fields(2024, k, nw, s.G) for k in range(steps)]
+    J64, gh64, gL64 = _gpu(s, nw, fields, tau, e0, cfg["order"], cfg["reortho"], 10)
+    J32, gh32, gL32 = _gpu(s, nw, fields, tau, e0, cfg["order"], cfg["reortho"], 10, precision="mixed")
+    assert float(J32[3]) == float(J64[3])
+    assert abs(float(J32[2]) - float(J64[2])) <= MIXED_J_TOL
+    _close(gh32, gh64, MIXED_GRAD_RTOL)
+    _close(gL32, gL64, MIXED_GRAD_RTOL)
