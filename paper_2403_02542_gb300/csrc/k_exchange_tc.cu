@@ -42,6 +42,7 @@ constexpr int TC_TMEM_COLS = 512;
 struct TcArgs {
   int n, gpt, T, KC, NB, Wc, WG, Nw, cap, G, S, n_items;
   uint32_t sB_bytes, sA_stage_bytes, staging_floats;
+  int sp;  // staging row stride in floats (a multiple of 4 with sp / 4 odd)
   double* epart;
   int* err;
 };
@@ -61,7 +62,7 @@ __global__ void __launch_bounds__(64 + 128 * EWG, 1)
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   unsigned char* sB = base;                                   // [hi,lo][KC][NB][64] bf16
   unsigned char* sA = sB + p.sB_bytes;                        // [S][hi,lo][128][64] bf16
-  float* stg = reinterpret_cast<float*>(sA + (size_t)p.S * p.sA_stage_bytes);  // [WG][128][2n+1]
+  float* stg = reinterpret_cast<float*>(sA + (size_t)p.S * p.sA_stage_bytes);  // [WG][128][sp]
   float* pbuf = stg + (size_t)EWG * p.staging_floats;  // [WG][128][4]
   uint64_t* bars = reinterpret_cast<uint64_t*>(pbuf + EWG * 128 * 4);
   uint64_t* full = bars;                 // [S]
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(64 + 128 * EWG, 1)
     const int r = quad * 32 + lane;                  // accumulator row = (g_local, i)
     const int gl = r / n, i = r % n;
     const bool row_ok = gl < p.gpt;
-    const int SP = two_n + 1;
+    const int SP = p.sp;
     float* st = stg + (size_t)ewg * p.staging_floats;
     float* pb = pbuf + ewg * 128 * 4;
     const int bar_id = 1 + ewg;
@@ -232,63 +233,79 @@ __global__ void __launch_bounds__(64 + 128 * EWG, 1)
           const uint32_t col0 = (uint32_t)(buf * p.NB + wl * two_n);
           const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + col0;
           float rr[NM > 0 ? 2 * NM : 1];
+          // staging row r: 16-byte stores (a row holds 2n values and up to 3
+          // padding floats; rows 16-byte aligned, sp / 4 odd: no bank conflicts)
+          float4* srow = reinterpret_cast<float4*>(st + r * SP);
           if constexpr (NM > 0) {
 #pragma unroll
             for (int c0 = 0; c0 < 2 * NM; c0 += 8)
               if (c0 < two_n) tmem_ld8(tl + (uint32_t)c0, reinterpret_cast<uint32_t*>(rr + c0));
             tmem_wait_ld();
 #pragma unroll
-            for (int c = 0; c < 2 * NM; ++c)
-              if (c < two_n) st[r * SP + c] = rr[c];
+            for (int c0 = 0; c0 < 2 * NM; c0 += 4)
+              if (c0 < two_n) srow[c0 >> 2] = make_float4(rr[c0], rr[c0 + 1], rr[c0 + 2], rr[c0 + 3]);
           } else {
             for (int c0 = 0; c0 < two_n; c0 += 8) {
               uint32_t v[8];
               tmem_ld8(tl + (uint32_t)c0, v);
               tmem_wait_ld();
-#pragma unroll
-              for (int e = 0; e < 8; ++e)
-                if (c0 + e < two_n) st[r * SP + c0 + e] = __uint_as_float(v[e]);
+              srow[c0 >> 2] = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]),
+                                          __uint_as_float(v[3]));
+              if (c0 + 4 < two_n)
+                srow[(c0 >> 2) + 1] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]),
+                                                  __uint_as_float(v[6]), __uint_as_float(v[7]));
             }
           }
           named_bar(bar_id, 128);
           float tr = 0.f, ti = 0.f, er = 0.f, ei = 0.f;
           if (valid) {
-            tr = st[r * SP + 2 * i];
-            ti = st[r * SP + 2 * i + 1];
-            const float* tcol = st + (size_t)(gl * n) * SP + 2 * i;  // T[j][i] at tcol[j * SP]
+            const float2 tt = *reinterpret_cast<const float2*>(st + r * SP + 2 * i);
+            tr = tt.x;
+            ti = tt.y;
+            // T[j][i] at tcol[j * SP / 2] (8-byte reads)
+            const float2* tcol = reinterpret_cast<const float2*>(st + (size_t)(gl * n) * SP + 2 * i);
+            const int hs = SP >> 1;
             if constexpr (NM > 0) {
 #pragma unroll
               for (int j = 0; j < NM; ++j) {
                 if (j < n) {
-                  const float ar = rr[2 * j], ai = rr[2 * j + 1];          // T_ij
-                  const float br = tcol[j * SP], bi = tcol[j * SP + 1];   // T_ji
-                  er = fmaf(ar, br, er);
-                  er = fmaf(-ai, bi, er);
-                  ei = fmaf(ar, bi, ei);
-                  ei = fmaf(ai, br, ei);
+                  const float ar = rr[2 * j], ai = rr[2 * j + 1];  // T_ij
+                  const float2 b = tcol[j * hs];                   // T_ji
+                  er = fmaf(ar, b.x, er);
+                  er = fmaf(-ai, b.y, er);
+                  ei = fmaf(ar, b.y, ei);
+                  ei = fmaf(ai, b.x, ei);
                 }
               }
             } else {
+              const float2* arow = reinterpret_cast<const float2*>(st + r * SP);
               for (int j = 0; j < n; ++j) {
-                const float ar = st[r * SP + 2 * j], ai = st[r * SP + 2 * j + 1];
-                const float br = tcol[j * SP], bi = tcol[j * SP + 1];
-                er = fmaf(ar, br, er);
-                er = fmaf(-ai, bi, er);
-                ei = fmaf(ar, bi, ei);
-                ei = fmaf(ai, br, ei);
+                const float2 a = arow[j];
+                const float2 b = tcol[j * hs];
+                er = fmaf(a.x, b.x, er);
+                er = fmaf(-a.y, b.y, er);
+                ei = fmaf(a.x, b.y, ei);
+                ei = fmaf(a.y, b.x, ei);
               }
             }
           }
           reinterpret_cast<float4*>(pb)[r] = make_float4(tr, ti, er, ei);
           named_bar(bar_id, 128);
-          for (int x = r; x < 4 * p.gpt; x += 128) {  // (g block, quantity): sum of its n rows in fixed order
-            const int gb = x >> 2, qn = x & 3;
+          // (g block, quantity) sums over the block's n rows: four lanes per
+          // pair each add every fourth row, then two shuffles combine them in a
+          // fixed order.  Whole warps run the loop (its bound is warp-uniform).
+          const int nthr = 16 * p.gpt;
+          for (int x0 = quad * 32; x0 < nthr; x0 += 128) {
+            const int x = x0 + lane;
+            const int pair = x >> 2, part = x & 3;
+            const int gb = pair >> 2, qn = pair & 3;
+            float sum = 0.f;
+            if (x < nthr)
+              for (int ii = part; ii < n; ii += 4) sum += pb[(gb * n + ii) * 4 + qn];
+            sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+            sum += __shfl_xor_sync(0xffffffffu, sum, 2);
             const int gg = (int)t * p.gpt + gb;
-            if (gg < p.G) {
-              float sum = 0.f;
-              for (int ii = 0; ii < n; ++ii) sum += pb[(gb * n + ii) * 4 + qn];
-              p.epart[(((size_t)w * p.G + gg) * 2 + spin) * 4 + qn] = sum;
-            }
+            if (x < nthr && part == 0 && gg < p.G) p.epart[(((size_t)w * p.G + gg) * 2 + spin) * 4 + qn] = sum;
           }
           // no barrier here: the next walker's staging writes come after the barrier
           // above (every thread is past its staging reads) and its row partials after
@@ -356,8 +373,17 @@ inline int grid_for(size_t n) {
   return (int)(b > 152 * 64 ? 152 * 64 : (b == 0 ? 1 : b));
 }
 
+// Staging row stride in floats: at least 2n + 1, a multiple of 4 (16-byte
+// rows) with an odd number of 16-byte chunks, so that the eight rows of one
+// 16-byte store wavefront fall on distinct bank groups.
+int tc_stage_stride(int n) {
+  int m = (2 * n + 1 + 3) / 4;
+  if ((m & 1) == 0) ++m;
+  return 4 * m;
+}
+
 size_t tc_smem_bytes(int KC, int NB, int S, int n, int ewg, bool sb) {
-  const size_t stg = (size_t)ewg * 128 * (2 * n + 1) * 4;
+  const size_t stg = (size_t)ewg * 128 * tc_stage_stride(n) * 4;
   const size_t resident_b = sb ? 0 : (size_t)2 * KC * NB * 128;
   const size_t stage = (size_t)2 * 128 * 128 + (sb ? (size_t)2 * NB * 128 : 0);
   return 1024 + resident_b + (size_t)S * stage + stg + (size_t)ewg * 128 * 4 * 4 + (size_t)(2 * S + 7) * 8 + 16 +
@@ -537,7 +563,8 @@ cudaError_t tc_exchange_launch(afqmc_ctx* c, int Nw, const void* theta, double* 
   a.n_items = 2 * a.WG;
   a.sB_bytes = P.sb ? 0u : (uint32_t)(2 * P.KC * P.NB * 128);
   a.sA_stage_bytes = 2 * 128 * 128 + (P.sb ? 2 * P.NB * 128 : 0);
-  a.staging_floats = (uint32_t)(128 * (2 * P.n + 1));
+  a.sp = tc_stage_stride(P.n);
+  a.staging_floats = (uint32_t)(128 * a.sp);
   a.epart = epart;
   a.err = static_cast<int*>(P.err);
   const size_t shm = tc_smem_bytes(P.KC, P.NB, P.S, P.n, P.ewg, P.sb);
