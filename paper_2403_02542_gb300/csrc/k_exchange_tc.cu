@@ -21,6 +21,12 @@
 //   warps 2..9  two epilogue warpgroups; each reads its walkers' columns of the
 //               TMEM accumulator, transposes the n x n blocks through shared
 //               memory and writes (tr T, sum T_ij T_ji) per (w, g, s).
+// Row layout of the A tiles: for n <= 32 every 32-row warp slot holds whole
+// g blocks (gpw = 32 / n of them, the rest zero rows), so each epilogue warp
+// owns its blocks: the transposition goes through the warp's own staging rows
+// and the sums over a block's rows are segmented warp shuffles, with no
+// barrier between warps.  For n > 32 the blocks are packed across the tile
+// (128 / n per tile) and the four warps of a warpgroup share a staging area.
 // The accumulator is double-buffered in TMEM so the epilogue of one A tile
 // overlaps the MMAs of the next.  Every mbarrier wait is bounded; on a
 // timeout the kernel raises an error flag, stops issuing work and frees its
@@ -40,19 +46,20 @@ namespace {
 constexpr int TC_TMEM_COLS = 512;
 
 struct TcArgs {
-  int n, gpt, T, KC, NB, Wc, WG, Nw, cap, G, S, n_items;
+  int n, gpt, gpw, T, KC, NB, Wc, WG, Nw, cap, G, S, n_items;
   uint32_t sB_bytes, sA_stage_bytes, staging_floats;
   int sp;  // staging row stride in floats (a multiple of 4 with sp / 4 odd)
   double* epart;
   int* err;
 };
 
-// NM > 0: n <= NM and each epilogue thread keeps its own accumulator row in
-// registers; NM == 0: the row is read back from shared memory.  EWG epilogue
+// NM > 0: n <= NM <= 32 and each epilogue thread keeps its own accumulator
+// row in registers; NM == 0: the row is read back from shared memory.  WL:
+// warp-slot row layout (needs NM > 0), else packed rows.  EWG epilogue
 // warpgroups.  SB = false: the item's B tile (all K) stays in shared memory
 // for all its A tiles; SB = true (large N): each stage of the ring carries
 // the B slab with the A slab (B re-read from L2 for every A tile).
-template <int NM, int EWG, bool SB>
+template <int NM, int EWG, bool SB, bool WL>
 __global__ void __launch_bounds__(64 + 128 * EWG, 1)
     exchange_tc_kernel(const __grid_constant__ CUtensorMap tmA_hi, const __grid_constant__ CUtensorMap tmA_lo,
                        const __grid_constant__ CUtensorMap tmB_hi, const __grid_constant__ CUtensorMap tmB_lo,
@@ -200,121 +207,222 @@ __global__ void __launch_bounds__(64 + 128 * EWG, 1)
     // ------------------------------------------------------------ epilogue
     const int ewg = (warp - 2) >> 2;                 // epilogue warpgroup 0 / 1
     const int quad = warp & 3;                       // TMEM lane quadrant this warp may read
-    const int r = quad * 32 + lane;                  // accumulator row = (g_local, i)
-    const int gl = r / n, i = r % n;
-    const bool row_ok = gl < p.gpt;
+    const int r = quad * 32 + lane;                  // accumulator row
     const int SP = p.sp;
+    const int hs = SP >> 1;                          // staging row stride in float2
     float* st = stg + (size_t)ewg * p.staging_floats;
-    float* pb = pbuf + ewg * 128 * 4;
-    const int bar_id = 1 + ewg;
     int buf = 0;
     uint32_t tph[2] = {0, 0};
     bool go = true;
-    for (int item = blockIdx.x; item < p.n_items && go; item += gridDim.x) {
-      const int spin = item / p.WG, wg = item % p.WG;
-      for (uint32_t t = 0; t < tiles_per_item; ++t) {
-        // one thread waits for the accumulator; the warpgroup follows its verdict
-        if (r == 0) {
-          const bool ok = mbar_wait(tfull + buf, tph[buf]);
-          if (!ok) { atomicOr(p.err, 32); *abort_flag = 1; }
-          epi_ok[ewg] = ok ? 1 : 0;
+    // sum_j T_ij T_ji for the thread's row i: T_ij from `own` (registers when
+    // NM > 0, else the staged row), T_ji = tcol[j * hs]; eight independent
+    // FMA chains (real/imaginary cross terms, even/odd j)
+    auto exch = [&](const float* own, const float2* arow, const float2* tcol, float& er, float& ei) {
+      float rr0 = 0.f, rr1 = 0.f, ii0 = 0.f, ii1 = 0.f, ri0 = 0.f, ri1 = 0.f, ir0 = 0.f, ir1 = 0.f;
+      if constexpr (NM > 0) {
+#pragma unroll
+        for (int j = 0; j < NM; j += 2) {
+          if (j < n) {
+            const float2 b0 = tcol[j * hs];
+            rr0 = fmaf(own[2 * j], b0.x, rr0);
+            ii0 = fmaf(own[2 * j + 1], b0.y, ii0);
+            ri0 = fmaf(own[2 * j], b0.y, ri0);
+            ir0 = fmaf(own[2 * j + 1], b0.x, ir0);
+          }
+          if (j + 1 < n) {
+            const float2 b1 = tcol[(j + 1) * hs];
+            rr1 = fmaf(own[2 * j + 2], b1.x, rr1);
+            ii1 = fmaf(own[2 * j + 3], b1.y, ii1);
+            ri1 = fmaf(own[2 * j + 2], b1.y, ri1);
+            ir1 = fmaf(own[2 * j + 3], b1.x, ir1);
+          }
         }
-        named_bar(bar_id, 128);
-        const int ok = epi_ok[ewg];
-        named_bar(bar_id, 128);  // every thread has read the verdict before it can be rewritten
-        if (!ok) { go = false; break; }
-        tc_fence_after();
-        const int g = (int)t * p.gpt + gl;
-        const bool valid = row_ok && g < p.G;
-        for (int wl = ewg; wl < p.Wc; wl += EWG) {
-          const int w = wg * p.Wc + wl;
-          if (w >= p.Nw) break;
-          // this walker's 2n accumulator columns: (Re T[i][j], Im T[i][j]) for j = 0..n-1
-          const uint32_t col0 = (uint32_t)(buf * p.NB + wl * two_n);
-          const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + col0;
-          float rr[NM > 0 ? 2 * NM : 1];
-          // staging row r: 16-byte stores (a row holds 2n values and up to 3
-          // padding floats; rows 16-byte aligned, sp / 4 odd: no bank conflicts)
-          float4* srow = reinterpret_cast<float4*>(st + r * SP);
-          if constexpr (NM > 0) {
+      } else {
+        int j = 0;
+        for (; j + 1 < n; j += 2) {
+          const float2 a0 = arow[j], a1 = arow[j + 1];
+          const float2 b0 = tcol[j * hs], b1 = tcol[(j + 1) * hs];
+          rr0 = fmaf(a0.x, b0.x, rr0);
+          ii0 = fmaf(a0.y, b0.y, ii0);
+          ri0 = fmaf(a0.x, b0.y, ri0);
+          ir0 = fmaf(a0.y, b0.x, ir0);
+          rr1 = fmaf(a1.x, b1.x, rr1);
+          ii1 = fmaf(a1.y, b1.y, ii1);
+          ri1 = fmaf(a1.x, b1.y, ri1);
+          ir1 = fmaf(a1.y, b1.x, ir1);
+        }
+        if (j < n) {
+          const float2 a0 = arow[j];
+          const float2 b0 = tcol[j * hs];
+          rr0 = fmaf(a0.x, b0.x, rr0);
+          ii0 = fmaf(a0.y, b0.y, ii0);
+          ri0 = fmaf(a0.x, b0.y, ri0);
+          ir0 = fmaf(a0.y, b0.x, ir0);
+        }
+      }
+      er = (rr0 + rr1) - (ii0 + ii1);
+      ei = (ri0 + ri1) + (ir0 + ir1);
+    };
+    if constexpr (WL) {
+      // warp slot: rows quad*32 + b*n + i hold block b (g = t*gpt + quad*gpw + b), row i
+      const int b = lane / n, i = lane - (lane / n) * n;
+      const bool lane_ok = b < p.gpw;
+      const int seg_end = (b + 1) * n;                // one past the block's last lane
+      float* wst = st + (size_t)quad * 32 * SP;       // this warp's staging rows
+      float4* srow = reinterpret_cast<float4*>(wst + lane * SP);
+      const float2* tcol = reinterpret_cast<const float2*>(wst + (size_t)(b * n) * SP + 2 * i);  // T[j][i]
+      for (int item = blockIdx.x; item < p.n_items && go; item += gridDim.x) {
+        const int spin = item / p.WG, wg = item % p.WG;
+        for (uint32_t t = 0; t < tiles_per_item; ++t) {
+          // lane 0 waits for the accumulator; the warp follows its verdict
+          int ok = 1;
+          if (lane == 0) {
+            ok = mbar_wait(tfull + buf, tph[buf]) ? 1 : 0;
+            if (!ok) { atomicOr(p.err, 32); *abort_flag = 1; }
+          }
+          ok = __shfl_sync(0xffffffffu, ok, 0);
+          if (!ok) { go = false; break; }
+          tc_fence_after();
+          const int g = (int)t * p.gpt + quad * p.gpw + b;
+          const bool valid = lane_ok && g < p.G;
+          for (int wl = ewg; wl < p.Wc; wl += EWG) {
+            const int w = wg * p.Wc + wl;
+            if (w >= p.Nw) break;
+            // this walker's 2n accumulator columns: (Re T[i][j], Im T[i][j]) for j = 0..n-1
+            const uint32_t col0 = (uint32_t)(buf * p.NB + wl * two_n);
+            const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + col0;
+            float rr[2 * (NM > 0 ? NM : 1)];
 #pragma unroll
             for (int c0 = 0; c0 < 2 * NM; c0 += 8)
               if (c0 < two_n) tmem_ld8(tl + (uint32_t)c0, reinterpret_cast<uint32_t*>(rr + c0));
             tmem_wait_ld();
+            __syncwarp();  // every lane is past its reads of the previous walker's rows
 #pragma unroll
             for (int c0 = 0; c0 < 2 * NM; c0 += 4)
               if (c0 < two_n) srow[c0 >> 2] = make_float4(rr[c0], rr[c0 + 1], rr[c0 + 2], rr[c0 + 3]);
-          } else {
-            for (int c0 = 0; c0 < two_n; c0 += 8) {
-              uint32_t v[8];
-              tmem_ld8(tl + (uint32_t)c0, v);
-              tmem_wait_ld();
-              srow[c0 >> 2] = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]),
-                                          __uint_as_float(v[3]));
-              if (c0 + 4 < two_n)
-                srow[(c0 >> 2) + 1] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]),
-                                                  __uint_as_float(v[6]), __uint_as_float(v[7]));
+            __syncwarp();
+            float tr = 0.f, ti = 0.f, er = 0.f, ei = 0.f;
+            if (valid) {
+              exch(rr, nullptr, tcol, er, ei);
+              const float2 tt = *reinterpret_cast<const float2*>(wst + lane * SP + 2 * i);
+              tr = tt.x;
+              ti = tt.y;
+            }
+            // sums over the block's n lanes, collected at its first lane in a fixed tree
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+              const float a0 = __shfl_down_sync(0xffffffffu, tr, off);
+              const float a1 = __shfl_down_sync(0xffffffffu, ti, off);
+              const float a2 = __shfl_down_sync(0xffffffffu, er, off);
+              const float a3 = __shfl_down_sync(0xffffffffu, ei, off);
+              if (lane + off < seg_end) {
+                tr += a0;
+                ti += a1;
+                er += a2;
+                ei += a3;
+              }
+            }
+            if (valid && i == 0) {
+              double* o = p.epart + (((size_t)w * p.G + g) * 2 + spin) * 4;
+              o[0] = tr;
+              o[1] = ti;
+              o[2] = er;
+              o[3] = ei;
             }
           }
+          tc_fence_before();
+          mbar_arrive(tempty + buf);
+          tph[buf] ^= 1;
+          buf ^= 1;
+        }
+      }
+    } else {
+      const int gl = r / n, i = r % n;
+      const bool row_ok = gl < p.gpt;
+      float* pb = pbuf + ewg * 128 * 4;
+      const int bar_id = 1 + ewg;
+      // staging row r: 16-byte stores (a row holds 2n values and up to 3
+      // padding floats; rows 16-byte aligned, sp / 4 odd: no bank conflicts)
+      float4* srow = reinterpret_cast<float4*>(st + r * SP);
+      const float2* arow = reinterpret_cast<const float2*>(st + r * SP);
+      const float2* tcol = reinterpret_cast<const float2*>(st + (size_t)(gl * n) * SP + 2 * i);  // T[j][i]
+      for (int item = blockIdx.x; item < p.n_items && go; item += gridDim.x) {
+        const int spin = item / p.WG, wg = item % p.WG;
+        for (uint32_t t = 0; t < tiles_per_item; ++t) {
+          // one thread waits for the accumulator; the warpgroup follows its verdict
+          if (r == 0) {
+            const bool ok = mbar_wait(tfull + buf, tph[buf]);
+            if (!ok) { atomicOr(p.err, 32); *abort_flag = 1; }
+            epi_ok[ewg] = ok ? 1 : 0;
+          }
           named_bar(bar_id, 128);
-          float tr = 0.f, ti = 0.f, er = 0.f, ei = 0.f;
-          if (valid) {
-            const float2 tt = *reinterpret_cast<const float2*>(st + r * SP + 2 * i);
-            tr = tt.x;
-            ti = tt.y;
-            // T[j][i] at tcol[j * SP / 2] (8-byte reads)
-            const float2* tcol = reinterpret_cast<const float2*>(st + (size_t)(gl * n) * SP + 2 * i);
-            const int hs = SP >> 1;
+          const int ok = epi_ok[ewg];
+          named_bar(bar_id, 128);  // every thread has read the verdict before it can be rewritten
+          if (!ok) { go = false; break; }
+          tc_fence_after();
+          const int g = (int)t * p.gpt + gl;
+          const bool valid = row_ok && g < p.G;
+          for (int wl = ewg; wl < p.Wc; wl += EWG) {
+            const int w = wg * p.Wc + wl;
+            if (w >= p.Nw) break;
+            const uint32_t col0 = (uint32_t)(buf * p.NB + wl * two_n);
+            const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + col0;
+            float rr[2 * (NM > 0 ? NM : 1)];
             if constexpr (NM > 0) {
 #pragma unroll
-              for (int j = 0; j < NM; ++j) {
-                if (j < n) {
-                  const float ar = rr[2 * j], ai = rr[2 * j + 1];  // T_ij
-                  const float2 b = tcol[j * hs];                   // T_ji
-                  er = fmaf(ar, b.x, er);
-                  er = fmaf(-ai, b.y, er);
-                  ei = fmaf(ar, b.y, ei);
-                  ei = fmaf(ai, b.x, ei);
-                }
-              }
+              for (int c0 = 0; c0 < 2 * NM; c0 += 8)
+                if (c0 < two_n) tmem_ld8(tl + (uint32_t)c0, reinterpret_cast<uint32_t*>(rr + c0));
+              tmem_wait_ld();
+#pragma unroll
+              for (int c0 = 0; c0 < 2 * NM; c0 += 4)
+                if (c0 < two_n) srow[c0 >> 2] = make_float4(rr[c0], rr[c0 + 1], rr[c0 + 2], rr[c0 + 3]);
             } else {
-              const float2* arow = reinterpret_cast<const float2*>(st + r * SP);
-              for (int j = 0; j < n; ++j) {
-                const float2 a = arow[j];
-                const float2 b = tcol[j * hs];
-                er = fmaf(a.x, b.x, er);
-                er = fmaf(-a.y, b.y, er);
-                ei = fmaf(a.x, b.y, ei);
-                ei = fmaf(a.y, b.x, ei);
+              for (int c0 = 0; c0 < two_n; c0 += 8) {
+                uint32_t v[8];
+                tmem_ld8(tl + (uint32_t)c0, v);
+                tmem_wait_ld();
+                srow[c0 >> 2] = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]),
+                                            __uint_as_float(v[3]));
+                if (c0 + 4 < two_n)
+                  srow[(c0 >> 2) + 1] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]),
+                                                    __uint_as_float(v[6]), __uint_as_float(v[7]));
               }
             }
+            named_bar(bar_id, 128);
+            float tr = 0.f, ti = 0.f, er = 0.f, ei = 0.f;
+            if (valid) {
+              exch(rr, arow, tcol, er, ei);
+              const float2 tt = arow[i];
+              tr = tt.x;
+              ti = tt.y;
+            }
+            reinterpret_cast<float4*>(pb)[r] = make_float4(tr, ti, er, ei);
+            named_bar(bar_id, 128);
+            // (g block, quantity) sums over the block's n rows: four lanes per
+            // pair each add every fourth row, then two shuffles combine them in a
+            // fixed order.  Whole warps run the loop (its bound is warp-uniform).
+            const int nthr = 16 * p.gpt;
+            for (int x0 = quad * 32; x0 < nthr; x0 += 128) {
+              const int x = x0 + lane;
+              const int pair = x >> 2, part = x & 3;
+              const int gb = pair >> 2, qn = pair & 3;
+              float sum = 0.f;
+              if (x < nthr)
+                for (int ii = part; ii < n; ii += 4) sum += pb[(gb * n + ii) * 4 + qn];
+              sum += __shfl_xor_sync(0xffffffffu, sum, 1);
+              sum += __shfl_xor_sync(0xffffffffu, sum, 2);
+              const int gg = (int)t * p.gpt + gb;
+              if (x < nthr && part == 0 && gg < p.G) p.epart[(((size_t)w * p.G + gg) * 2 + spin) * 4 + qn] = sum;
+            }
+            // no barrier here: the next walker's staging writes come after the barrier
+            // above (every thread is past its staging reads) and its row partials after
+            // the next walker's first barrier (every thread is past this tail)
           }
-          reinterpret_cast<float4*>(pb)[r] = make_float4(tr, ti, er, ei);
-          named_bar(bar_id, 128);
-          // (g block, quantity) sums over the block's n rows: four lanes per
-          // pair each add every fourth row, then two shuffles combine them in a
-          // fixed order.  Whole warps run the loop (its bound is warp-uniform).
-          const int nthr = 16 * p.gpt;
-          for (int x0 = quad * 32; x0 < nthr; x0 += 128) {
-            const int x = x0 + lane;
-            const int pair = x >> 2, part = x & 3;
-            const int gb = pair >> 2, qn = pair & 3;
-            float sum = 0.f;
-            if (x < nthr)
-              for (int ii = part; ii < n; ii += 4) sum += pb[(gb * n + ii) * 4 + qn];
-            sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-            sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-            const int gg = (int)t * p.gpt + gb;
-            if (x < nthr && part == 0 && gg < p.G) p.epart[(((size_t)w * p.G + gg) * 2 + spin) * 4 + qn] = sum;
-          }
-          // no barrier here: the next walker's staging writes come after the barrier
-          // above (every thread is past its staging reads) and its row partials after
-          // the next walker's first barrier (every thread is past this tail)
+          tc_fence_before();
+          mbar_arrive(tempty + buf);
+          tph[buf] ^= 1;
+          buf ^= 1;
         }
-        tc_fence_before();
-        mbar_arrive(tempty + buf);
-        tph[buf] ^= 1;
-        buf ^= 1;
       }
     }
   }
@@ -328,19 +436,33 @@ __global__ void __launch_bounds__(64 + 128 * EWG, 1)
   }
 }
 
-// A operand: [2 spins][T][128 rows][Kp] from Lh[G][nc][N] (rows gg*n + i).
+// A operand: [2 spins][T][128 rows][Kp] from Lh[G][nc][N].  Rows of tile t:
+// gpw > 0: row slot*32 + b*n + i = row i of g = t*gpt + slot*gpw + b (b < gpw,
+// other rows zero); gpw == 0: row gg*n + i = row i of g = t*gpt + gg.
 __global__ void build_lh_tiles_kernel(const double* __restrict__ Lh, __nv_bfloat16* __restrict__ hi,
-                                      __nv_bfloat16* __restrict__ lo, int N, int n, int nc, int G, int gpt, int T,
-                                      int Kp) {
+                                      __nv_bfloat16* __restrict__ lo, int N, int n, int nc, int G, int gpt, int gpw,
+                                      int T, int Kp) {
   const size_t total = (size_t)2 * T * 128 * Kp;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int q = e % Kp;
     const int r = (e / Kp) % 128;
     const int t = (e / ((size_t)Kp * 128)) % T;
     const int spin = (int)(e / ((size_t)Kp * 128 * T));
-    const int gg = r / n, i = r % n, g = t * gpt + gg;
+    int gg, i;
+    bool in_block;
+    if (gpw > 0) {
+      const int slot = r >> 5, b = (r & 31) / n;
+      i = (r & 31) - b * n;
+      gg = slot * gpw + b;
+      in_block = b < gpw;
+    } else {
+      gg = r / n;
+      i = r % n;
+      in_block = gg < gpt;
+    }
+    const int g = t * gpt + gg;
     double x = 0.0;
-    if (gg < gpt && g < G && q < N) x = Lh[((size_t)g * nc + spin * n + i) * N + q];
+    if (in_block && g < G && q < N) x = Lh[((size_t)g * nc + spin * n + i) * N + q];
     split_bf16(x, hi[e], lo[e]);
   }
 }
@@ -390,24 +512,34 @@ size_t tc_smem_bytes(int KC, int NB, int S, int n, int ewg, bool sb) {
          4 * ewg;
 }
 
-template <int NM, int EWG, bool SB>
+template <int NM, int EWG, bool SB, bool WL>
 void* exchange_fn() {
-  return reinterpret_cast<void*>(exchange_tc_kernel<NM, EWG, SB>);
+  return reinterpret_cast<void*>(exchange_tc_kernel<NM, EWG, SB, WL>);
 }
 
-// kernel instance for (n, epilogue warpgroups, streamed B)
-void* exchange_instance(int n, int ewg, bool sb) {
+// kernel instance for (n, epilogue warpgroups, streamed B, warp-slot rows)
+void* exchange_instance(int n, int ewg, bool sb, bool wl) {
   const int nm = n <= 16 ? 16 : n <= 24 ? 24 : n <= 32 ? 32 : 0;
-#define AFQ_X(NM)                                                                   \
-  if (nm == NM) {                                                                   \
-    if (ewg == 2) return sb ? exchange_fn<NM, 2, true>() : exchange_fn<NM, 2, false>(); \
-    return sb ? exchange_fn<NM, 1, true>() : exchange_fn<NM, 1, false>();           \
+#define AFQ_X2(NM, WL)                                                                            \
+  if (ewg == 2) return sb ? exchange_fn<NM, 2, true, WL>() : exchange_fn<NM, 2, false, WL>(); \
+  return sb ? exchange_fn<NM, 1, true, WL>() : exchange_fn<NM, 1, false, WL>();
+#define AFQ_X(NM)            \
+  if (nm == NM) {            \
+    if (wl) {                \
+      AFQ_X2(NM, true)       \
+    } else {                 \
+      AFQ_X2(NM, false)      \
+    }                        \
   }
   AFQ_X(16)
   AFQ_X(24)
   AFQ_X(32)
-  AFQ_X(0)
 #undef AFQ_X
+  if (nm == 0) {
+    if (wl) return nullptr;
+    AFQ_X2(0, false)
+  }
+#undef AFQ_X2
   return nullptr;
 }
 
@@ -423,7 +555,10 @@ bool tc_exchange_plan(afqmc_ctx* c) {
   const int Kp = ((c->N + 63) / 64) * 64;
   const int KC = Kp / 64;
   if (n > 64) return false;
-  const int gpt = 128 / n;
+  // whole g blocks per 32-row warp slot (n <= 32) where that puts as many g
+  // in a tile as packing them across the tile does; else packed
+  const int gpw = (n <= 32 && 4 * (32 / n) >= 128 / n) ? 32 / n : 0;
+  const int gpt = gpw > 0 ? 4 * gpw : 128 / n;
   const size_t budget = 232448 - 1024;
   // preference: B resident with two epilogue warpgroups, then B streamed with
   // two, then with one (large N or n)
@@ -450,6 +585,7 @@ bool tc_exchange_plan(afqmc_ctx* c) {
   P.ok = true;
   P.n = n;
   P.gpt = gpt;
+  P.gpw = gpw;
   P.T = (c->G + gpt - 1) / gpt;
   P.Kp = Kp;
   P.KC = KC;
@@ -475,7 +611,7 @@ cudaError_t tc_exchange_setup(afqmc_ctx* c, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   build_lh_tiles_kernel<<<grid_for(elems), 256, 0, s>>>(c->d_Lh, static_cast<__nv_bfloat16*>(P.a_hi),
                                                         static_cast<__nv_bfloat16*>(P.a_lo), c->N, P.n, c->nc, c->G,
-                                                        P.gpt, P.T, P.Kp);
+                                                        P.gpt, P.gpw, P.T, P.Kp);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (!make_map(reinterpret_cast<CUtensorMap*>(P.map_a_hi), P.a_hi, (size_t)2 * P.T * 128, P.Kp, 128) ||
@@ -521,7 +657,7 @@ cudaError_t tc_exchange_ws(afqmc_ctx* c) {
 cudaError_t tc_exchange_prepare(const afqmc_ctx* c) {
   const TcPlan& P = c->tc;
   if (!P.ok) return cudaSuccess;
-  void* f = exchange_instance(P.n, P.ewg, P.sb);
+  void* f = exchange_instance(P.n, P.ewg, P.sb, P.gpw > 0);
   cudaFuncAttributes a;
   cudaError_t e = cudaFuncGetAttributes(&a, f);
   if (e != cudaSuccess) return e;
@@ -551,6 +687,7 @@ cudaError_t tc_exchange_launch(afqmc_ctx* c, int Nw, const void* theta, double* 
   TcArgs a;
   a.n = P.n;
   a.gpt = P.gpt;
+  a.gpw = P.gpw;
   a.T = P.T;
   a.KC = P.KC;
   a.NB = P.NB;
@@ -581,7 +718,7 @@ cudaError_t tc_exchange_launch(afqmc_ctx* c, int Nw, const void* theta, double* 
   memcpy(&mal, P.map_a_lo, sizeof(CUtensorMap));
   memcpy(&mbh, P.map_b_hi, sizeof(CUtensorMap));
   memcpy(&mbl, P.map_b_lo, sizeof(CUtensorMap));
-  void* f = exchange_instance(P.n, P.ewg, P.sb);
+  void* f = exchange_instance(P.n, P.ewg, P.sb, P.gpw > 0);
   void* args[] = {&mah, &mal, &mbh, &mbl, &a};
   e = cudaLaunchKernel(f, dim3(grid), dim3(64 + 128 * P.ewg), args, shm, s);
   if (e != cudaSuccess) return e;
