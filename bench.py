@@ -567,8 +567,13 @@ def run_ours(args):
     achieved = (ex_flop / (ex_ms / ex_n / 1000.0)) / 1e12 if ex_n else None
     # DRAM bytes of one exchange launch (read + write), ncu capture of this kernel
     # version at the benchmark size (profiles/launches_mixed_large.md)
-    # (null until an ncu capture of the current exchange kernel at this size)
+    # DRAM bytes of one exchange launch (read + write), ncu capture of this kernel
+    # version at the benchmark size (profiles/launches_mixed_large.md)
     traffic, traffic_note = None, None
+    if args.precision == "mixed" and NW == 1024:
+        traffic = 63.51e6
+        traffic_note = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of "
+                        "exchange_tc_kernel<24, 2, 0, 0> at 1024 walkers: 56.08 + 7.43 MB; operands 55.9 MB")
     adjoint = None
     if world == 1 and not args.no_adjoint:
         adjoint = adjoint_rate(dev)

@@ -205,6 +205,7 @@ cudaError_t prepare_kernels(afqmc_ctx* c) {
   if (e == cudaSuccess) e = c->prec == AFQMC_FP64 ? prepare_energy<double>(c) : prepare_energy<float>(c);
   if (e == cudaSuccess) e = tc_exchange_prepare(c);
   if (e == cudaSuccess) e = tc_field_prepare(c);
+  if (e == cudaSuccess) e = halfstep_prepare_kernel(c);
   return e;
 }
 }  // namespace afq
@@ -446,6 +447,12 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
   const double st = std::sqrt(p->tau);
   Workspace& ws = c->ws;
   const size_t cs = sizeof(typename C2<R>::t);
+  // out = B in: complex64 walkers with N <= 128 keep B in shared memory
+  // (dedicated kernel), else the tiled GEMM
+  auto half = [&](const void* in, void* out) -> cudaError_t {
+    if (std::is_same<R, float>::value && halfstep_ok(c)) return halfstep_launch(c, Nw, in, out, s);
+    return gemm<R>(site_args<R>(c, SITE_HALFSTEP, Nw, st, in, out), false, EPI_STORE, s);
+  };
 
   // <L_g> from the last measurement of these walkers when allowed and valid
   // (then the overlap and force-bias kernels return at once), else Theta and
@@ -466,7 +473,7 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
     PK(AFQMC_K_FIELD, gemm<R>(site_args<R>(c, SITE_FIELD, Nw, st, ws.c, ws.A), false, EPI_STORE, s));
   }
   // psi_b = B psi
-  PK(AFQMC_K_HALFSTEP, gemm<R>(site_args<R>(c, SITE_HALFSTEP, Nw, st, w->psi, ws.psi_b), false, EPI_STORE, s));
+  PK(AFQMC_K_HALFSTEP, half(w->psi, ws.psi_b));
   c->launches += 6;
 
   // per-walker products with A_w (tensor cores for complex64 walkers)
@@ -505,7 +512,7 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
     c->launches += 2 + 2 * k + 2;
   }
   // psi_new = B acc
-  PK(AFQMC_K_HALFSTEP, gemm<R>(site_args<R>(c, SITE_HALFSTEP, Nw, st, ws.acc, ws.psi_new), false, EPI_STORE, s));
+  PK(AFQMC_K_HALFSTEP, half(ws.acc, ws.psi_new));
   // new overlap (and Theta for the local energy when no re-orthonormalisation
   // follows), weights, commit
   void* th_new = (p->measure && !p->reortho) ? ws.theta : nullptr;

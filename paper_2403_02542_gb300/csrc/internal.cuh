@@ -71,6 +71,13 @@ constexpr int GEMM_VARIANTS = 5;
 enum GemmSite { SITE_FORCEBIAS = 0, SITE_FIELD = 1, SITE_HALFSTEP = 2, SITE_EXPM = 3, N_SITES = 4 };
 template <typename R>
 cudaError_t gemm(const GemmArgs& a, bool a_complex, int epi, cudaStream_t s);
+// Half steps of complex64 walkers (mixed contexts, N <= 128):
+// out[w][j][p] = sum_q B[p][q] in[w][j][q] with the FP32 copy of B resident
+// in shared memory (k_gemm.cu); halfstep_prepare_kernel sets its shared-memory
+// limit (before any graph capture).
+bool halfstep_ok(const afqmc_ctx* c);
+cudaError_t halfstep_prepare_kernel(const afqmc_ctx* c);
+cudaError_t halfstep_launch(const afqmc_ctx* c, int Nw, const void* in, void* out, cudaStream_t s);
 
 // ---------------------------------------------------------------- context
 struct Workspace {

@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(64 + 128 * EWG, 1)
   uint64_t* drain = tempty + 2;          // [1] completion of every MMA this CTA issued
   volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(drain + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  volatile int* epi_ok = abort_flag + 1;  // [EWG] wait result broadcast inside a warpgroup
+  volatile int* epi_ok = abort_flag + 1;  // [EWG][2] wait result broadcast inside a warpgroup
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = p.n, two_n = 2 * n;
@@ -341,6 +341,7 @@ __global__ void __launch_bounds__(64 + 128 * EWG, 1)
       const bool row_ok = gl < p.gpt;
       float* pb = pbuf + ewg * 128 * 4;
       const int bar_id = 1 + ewg;
+      uint32_t tcount = 0;  // tiles handled so far (selects the verdict slot)
       // staging row r: 16-byte stores (a row holds 2n values and up to 3
       // padding floats; rows 16-byte aligned, sp / 4 odd: no bank conflicts)
       float4* srow = reinterpret_cast<float4*>(st + r * SP);
@@ -349,15 +350,18 @@ __global__ void __launch_bounds__(64 + 128 * EWG, 1)
       for (int item = blockIdx.x; item < p.n_items && go; item += gridDim.x) {
         const int spin = item / p.WG, wg = item % p.WG;
         for (uint32_t t = 0; t < tiles_per_item; ++t) {
-          // one thread waits for the accumulator; the warpgroup follows its verdict
+          // one thread waits for the accumulator; the warpgroup follows its
+          // verdict (two slots alternating with every tile the warpgroup
+          // handles: a slot is rewritten two tiles later, after every thread
+          // has passed the barrier of the tile in between)
           if (r == 0) {
             const bool ok = mbar_wait(tfull + buf, tph[buf]);
             if (!ok) { atomicOr(p.err, 32); *abort_flag = 1; }
-            epi_ok[ewg] = ok ? 1 : 0;
+            epi_ok[2 * ewg + (tcount & 1)] = ok ? 1 : 0;
           }
           named_bar(bar_id, 128);
-          const int ok = epi_ok[ewg];
-          named_bar(bar_id, 128);  // every thread has read the verdict before it can be rewritten
+          const int ok = epi_ok[2 * ewg + (tcount & 1)];
+          ++tcount;
           if (!ok) { go = false; break; }
           tc_fence_after();
           const int g = (int)t * p.gpt + gl;
@@ -509,7 +513,7 @@ size_t tc_smem_bytes(int KC, int NB, int S, int n, int ewg, bool sb) {
   const size_t resident_b = sb ? 0 : (size_t)2 * KC * NB * 128;
   const size_t stage = (size_t)2 * 128 * 128 + (sb ? (size_t)2 * NB * 128 : 0);
   return 1024 + resident_b + (size_t)S * stage + stg + (size_t)ewg * 128 * 4 * 4 + (size_t)(2 * S + 7) * 8 + 16 +
-         4 * ewg;
+         8 * ewg;
 }
 
 template <int NM, int EWG, bool SB, bool WL>

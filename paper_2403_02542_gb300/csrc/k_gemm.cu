@@ -295,6 +295,107 @@ __global__ void splitk_reduce_kernel(GemmArgs g) {
 
 }  // namespace
 
+// Half step out[c][p] = sum_q B[p][q] in[c][q] of complex64 columns (the
+// (walker, orbital) columns of Psi, N values each), N <= 128: B^T stays in
+// shared memory for the whole (persistent) block, columns stream through in
+// tiles of HS_COLS with all of K at once, and each thread accumulates an
+// 8-row x 2-column complex tile (summation over q in order, as the tiled
+// GEMM does).  Warp w covers rows 32 (w & 3) .. + 31 and columns
+// 16 (w >> 2) .. + 15; its lanes form 4 row groups x 8 column pairs, so one
+// q step reads 128 contiguous bytes of B^T and 8 distinct columns of the tile
+// (four shared-memory wavefronts for 32 FMAs per lane).
+constexpr int HS_COLS = 32, HS_T = 256, HS_NMAX = 128;
+constexpr int HS_BS = HS_NMAX + 4;  // B^T row stride (16-byte rows; transposed writes 4-way at most)
+size_t halfstep_smem() { return (size_t)HS_NMAX * HS_BS * 4 + (size_t)HS_COLS * (HS_NMAX + 1) * 8; }
+
+__global__ void __launch_bounds__(HS_T, 2) halfstep_kernel(const float* __restrict__ B, const float2* __restrict__ in,
+                                                           float2* __restrict__ out, int N, int ncols) {
+  extern __shared__ __align__(16) float hs_smem[];
+  float* Bt = hs_smem;                                                      // [128][HS_BS] Bt[q][p], zero beyond N
+  float2* X = reinterpret_cast<float2*>(hs_smem + HS_NMAX * HS_BS);        // [HS_COLS][N + 1]
+  const int XS = N + 1;
+  for (int e = threadIdx.x; e < HS_NMAX * HS_BS; e += HS_T) Bt[e] = 0.f;
+  __syncthreads();
+  // B read along its rows (coalesced), eight loads in flight per thread
+  const int NN = N * N;
+  for (int e0 = 0; e0 < NN; e0 += 8 * HS_T) {
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int e = e0 + k * HS_T + threadIdx.x;
+      v[k] = e < NN ? B[e] : 0.f;
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int e = e0 + k * HS_T + threadIdx.x;
+      if (e < NN) Bt[(e % N) * HS_BS + e / N] = v[k];
+    }
+  }
+  const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int p0 = (wid & 3) * 32 + (lane & 3) * 8;   // this thread's 8 rows
+  const int cl = (wid >> 2) * 16 + (lane >> 2) * 2;  // and its 2 columns in the tile
+  const int ntiles = (ncols + HS_COLS - 1) / HS_COLS;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int cbase = tile * HS_COLS;
+    // the tile's columns: warp wid loads columns wid + 8a, lanes run along q,
+    // all sixteen loads of a thread in flight before the first store
+    float2 v[HS_COLS / 8][HS_NMAX / 32];
+#pragma unroll
+    for (int a = 0; a < HS_COLS / 8; ++a) {
+      const int c = cbase + wid + 8 * a;
+#pragma unroll
+      for (int b = 0; b < HS_NMAX / 32; ++b) {
+        const int q = lane + 32 * b;
+        v[a][b] = (c < ncols && q < N) ? in[(size_t)c * N + q] : make_float2(0.f, 0.f);
+      }
+    }
+    __syncthreads();  // B^T written; the previous tile's reads of X are done
+#pragma unroll
+    for (int a = 0; a < HS_COLS / 8; ++a)
+#pragma unroll
+      for (int b = 0; b < HS_NMAX / 32; ++b) {
+        const int q = lane + 32 * b;
+        if (q < N) X[(wid + 8 * a) * XS + q] = v[a][b];
+      }
+    __syncthreads();
+    float ar[8][2], ai[8][2];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      ar[r][0] = ar[r][1] = 0.f;
+      ai[r][0] = ai[r][1] = 0.f;
+    }
+    const float2* x0p = X + cl * XS;
+    const float2* x1p = x0p + XS;
+    for (int q = 0; q < N; ++q) {
+      const float4 b0 = *reinterpret_cast<const float4*>(Bt + q * HS_BS + p0);
+      const float4 b1 = *reinterpret_cast<const float4*>(Bt + q * HS_BS + p0 + 4);
+      const float bb[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+      const float2 x0 = x0p[q], x1 = x1p[q];
+#pragma unroll
+      for (int r = 0; r < 8; ++r) {
+        ar[r][0] = fmaf(bb[r], x0.x, ar[r][0]);
+        ai[r][0] = fmaf(bb[r], x0.y, ai[r][0]);
+        ar[r][1] = fmaf(bb[r], x1.x, ar[r][1]);
+        ai[r][1] = fmaf(bb[r], x1.y, ai[r][1]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int c = cbase + cl + i;
+      if (c >= ncols) continue;
+      float2* o = out + (size_t)c * N;
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (p0 + r < N) o[p0 + r] = make_float2(ar[r][i], ai[r][i]);
+    }
+  }
+}
+
+cudaError_t halfstep_prepare() {
+  return cudaFuncSetAttribute(reinterpret_cast<const void*>(halfstep_kernel),
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)halfstep_smem());
+}
+
 template <typename R, bool AC, int BM, int BN>
 cudaError_t gemm_launch(const GemmArgs& g, int zdim, cudaStream_t s) {
   dim3 grid((g.M + BM - 1) / BM, (g.Nn + BN - 1) / BN, zdim);
@@ -342,5 +443,25 @@ cudaError_t gemm(const GemmArgs& a, bool a_complex, int epi, cudaStream_t s) {
 
 template cudaError_t gemm<double>(const GemmArgs&, bool, int, cudaStream_t);
 template cudaError_t gemm<float>(const GemmArgs&, bool, int, cudaStream_t);
+
+bool halfstep_ok(const afqmc_ctx* c) { return c->prec == AFQMC_MIXED && c->N <= HS_NMAX && c->f_B != nullptr; }
+
+cudaError_t halfstep_prepare_kernel(const afqmc_ctx* c) { return halfstep_ok(c) ? halfstep_prepare() : cudaSuccess; }
+
+cudaError_t halfstep_launch(const afqmc_ctx* c, int Nw, const void* in, void* out, cudaStream_t s) {
+  const int ncols = Nw * c->nc;
+  if (ncols <= 0) return cudaSuccess;
+  const int ntiles = (ncols + HS_COLS - 1) / HS_COLS;
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = ntiles < 2 * sms ? ntiles : 2 * sms;
+  if (!capturing(c)) {  // dynamic shared memory above the default limit
+    cudaError_t e = halfstep_prepare();
+    if (e != cudaSuccess) return e;
+  }
+  halfstep_kernel<<<grid, HS_T, halfstep_smem(), s>>>(c->f_B, static_cast<const float2*>(in), static_cast<float2*>(out),
+                                                     c->N, ncols);
+  return cudaGetLastError();
+}
 
 }  // namespace afq
