@@ -31,6 +31,13 @@ Readings of the paper used here (the paper is silent or ambiguous on them):
       invariant subspace is declared when the new subdiagonal entry is
       <= 1e-12 ||A||_F (the basis vectors are unit vectors).
   R6  The small exponential e^{A_k} is torch.linalg.matrix_exp.
+  R20 Block Krylov (Sec. IV, Eqs. bkrylovsub-bkrylov) works on each spin
+      block separately (the two determinants span separate spaces); the QR
+      of Psi and of every new block is modified Gram-Schmidt (mgs_qr), the
+      new block is orthogonalised against the previous ones by one block
+      modified Gram-Schmidt pass, the number of blocks is at most N // n, and
+      the space is declared invariant at the first new block whose QR has a
+      diagonal entry <= 1e-12 ||A||_F.
   R7  E_0 is a caller-supplied scalar.
   R8  Population control: comb with caller-supplied uniform u.
   R9  Threshold tests use the strict inequalities printed in Sec. V.
@@ -50,7 +57,7 @@ __all__ = [
     "Hamiltonian", "make_hamiltonian", "overlap", "greens_function",
     "log_overlap", "theta", "mean_field_shift", "mixed_L_expectation",
     "force_bias", "propagation_h1", "half_step_propagator", "field_matrix",
-    "taylor_action", "krylov_action", "exact_action", "expm_action",
+    "taylor_action", "krylov_action", "block_krylov_action", "exact_action", "expm_action",
     "split2_propagate", "local_energy", "energy_window", "mixed_energy",
     "mgs_qr", "reorthonormalise", "weight_update", "step", "init_walkers",
     "free_projection_step", "comb", "population_control", "StepInfo",
@@ -237,26 +244,71 @@ def krylov_action(A, psi, k):
     return torch.stack(cols, dim=1)
 
 
+def _block_arnoldi(A, X, k, normA):
+    """Block-Krylov approximation of e^A X for one spin block X [N, n]
+    (Eqs. bkrylovsub-bkrylov): X = B_1 R, the orthonormal basis
+    B_k = [B_1 .. B_k] of span{X, A X, .., A^{k-1} X}, the block upper
+    Hessenberg A_k = B_k^dagger A B_k, and bkrylov_k = B_k e^{A_k} E_n R."""
+    N, n = X.shape
+    if n == 0:
+        return X.clone(), 0
+    B1, Rx = mgs_qr(X)                                       # X = B_1 R
+    kk = max(1, min(k, N // n))
+    blocks = [B1]
+    H = torch.zeros(kk * n, kk * n, dtype=CT)
+    k_eff = kk
+    for j in range(kk):
+        W = A @ blocks[j]
+        for i in range(j + 1):                               # block modified Gram-Schmidt
+            Hij = blocks[i].conj().T @ W                     # B_i^dagger W
+            H[i * n:(i + 1) * n, j * n:(j + 1) * n] = Hij
+            W = W - blocks[i] @ Hij
+        if j + 1 < kk:
+            Bn, Rn = mgs_qr(W)                               # W = B_{j+1} H_{j+1,j}
+            if float(Rn.diagonal().abs().min()) <= 1e-12 * float(normA):   # invariant (R20)
+                k_eff = j + 1
+                break
+            H[(j + 1) * n:(j + 2) * n, j * n:(j + 1) * n] = Rn
+            blocks.append(Bn)
+    m = k_eff * n
+    F = torch.linalg.matrix_exp(H[:m, :m])[:, :n] @ Rx      # e^{A_k} E_n R
+    return torch.cat(blocks[:k_eff], dim=1) @ F, k_eff
+
+
+def block_krylov_action(A, psi, k, spins=None):
+    """bkrylov_k{A, Psi} for every spin block of psi [N, nc] (or [Nw, N, nc])."""
+    if psi.dim() == 3:
+        return torch.stack([block_krylov_action(A[w], psi[w], k, spins) for w in range(psi.shape[0])])
+    normA = torch.linalg.matrix_norm(A)
+    out = psi.clone()
+    for sl in (spins if spins is not None else (slice(0, psi.shape[1]),)):
+        if sl.stop > sl.start:
+            out[:, sl] = _block_arnoldi(A, psi[:, sl], k, normA)[0]
+    return out
+
+
 def exact_action(A, psi):
     """e^A Psi by (non-Hermitian) diagonalisation, A = V diag(l) V^{-1} (Sec. IV)."""
     lam, V = torch.linalg.eig(A.to(CT))
     return V @ (torch.exp(lam)[..., :, None] * torch.linalg.solve(V, psi.to(CT)))
 
 
-def expm_action(A, psi, method, k):
+def expm_action(A, psi, method, k, spins=None):
     if method == "taylor":
         return taylor_action(A, psi, k)
     if method == "krylov":
         return krylov_action(A, psi, k)
+    if method == "bkrylov":
+        return block_krylov_action(A, psi, k, spins)
     if method == "exact":
         return exact_action(A, psi)
     raise ValueError(method)
 
 
-def split2_propagate(B, A, psi, method, k):
+def split2_propagate(B, A, psi, method, k, spins=None):
     """U_S2 Psi = e^{-tau H1/2} e^{A} e^{-tau H1/2} Psi (Sec. III.B)."""
     Bc = B.to(CT)
-    return Bc @ expm_action(A, Bc @ psi, method, k)
+    return Bc @ expm_action(A, Bc @ psi, method, k, spins)
 
 
 # --------------------------------------------------------------------------
@@ -396,7 +448,7 @@ def step(ham: Hamiltonian, psi, logovl, W, x, tau, e0, method="krylov", k=10,
     f, f_raw = force_bias(ham, psi, tau, L_bar)                     # Eq. force_shift
     c = x.to(CT) - f
     A = field_matrix(ham, c, tau)                                   # Eq. heffTOT
-    psi_new = split2_propagate(B, A, psi, method, k)                # Eq. psiupdate
+    psi_new = split2_propagate(B, A, psi, method, k, ham.spins())   # Eq. psiupdate
     logovl_new = log_overlap(ham, psi_new)
     log_s = -tau * ec - 1j * math.sqrt(tau) * (c @ L_bar.to(CT))
     log_ratio = logovl_new - logovl + log_s
@@ -428,7 +480,7 @@ def free_projection_step(ham: Hamiltonian, psi, logovl, weight, x, tau, e0,
     f, _ = force_bias(ham, psi, tau, L_bar)
     c = x.to(CT) - f
     A = field_matrix(ham, c, tau)
-    psi_new = split2_propagate(B, A, psi, method, k)
+    psi_new = split2_propagate(B, A, psi, method, k, ham.spins())
     logovl_new = log_overlap(ham, psi_new)
     log_s = -tau * ec - 1j * math.sqrt(tau) * (c @ L_bar.to(CT))
     log_ratio = logovl_new - logovl + log_s

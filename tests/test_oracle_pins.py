@@ -119,6 +119,64 @@ def test_krylov_hessenberg_projection():
     assert torch.allclose(out, ref, rtol=1e-9, atol=1e-11)
 
 
+def test_block_krylov_full_space_is_exact():
+    """k n = N (Eq. bkrylov): the block Krylov space is the whole space, so the
+    action is e^A X to roundoff, for each spin block separately."""
+    g = torch.Generator().manual_seed(41)
+    for N, na, nb in ((6, 2, 3), (8, 4, 2), (9, 3, 3)):
+        A = 0.4 * _rand_c(g, N, N)
+        X = _rand_c(g, N, na + nb)
+        ref = torch.linalg.matrix_exp(A) @ X
+        spins = (slice(0, na), slice(na, na + nb))
+        out = torch.empty_like(X)
+        for sl in spins:
+            n = sl.stop - sl.start
+            out[:, sl] = R.block_krylov_action(A, X[:, sl], N // n)
+        assert torch.allclose(out, ref, rtol=1e-11, atol=1e-12)
+        # the spin-split call gives the same, and more blocks than N // n are clamped
+        assert torch.allclose(R.block_krylov_action(A, X, N, spins), ref, rtol=1e-11, atol=1e-12)
+
+
+def test_block_krylov_one_column_is_krylov():
+    """n = 1: the block algorithm is the column Arnoldi of Eq. krylov."""
+    g = torch.Generator().manual_seed(42)
+    N = 10
+    A = 0.3 * _rand_c(g, N, N)
+    x = _rand_c(g, N, 1)
+    for k in (1, 3, 6):
+        assert torch.allclose(R.block_krylov_action(A, x, k), R.krylov_action(A, x, k), rtol=1e-12, atol=1e-13)
+
+
+def test_block_krylov_is_a_projection_on_the_block_krylov_space():
+    """bkrylov_k = Q e^{Q^dagger A Q} Q^dagger X for any orthonormal basis Q of
+    span{X, A X, .., A^{k-1} X}; Q here from a library QR of those blocks."""
+    g = torch.Generator().manual_seed(43)
+    N, n, k = 14, 3, 3
+    A = 0.5 * _rand_c(g, N, N)
+    X = _rand_c(g, N, n)
+    K = torch.cat([torch.linalg.matrix_power(A, j) @ X for j in range(k)], 1)
+    Q, _ = torch.linalg.qr(K)
+    ref = Q @ (torch.linalg.matrix_exp(Q.conj().T @ A @ Q) @ (Q.conj().T @ X))
+    assert torch.allclose(R.block_krylov_action(A, X, k), ref, rtol=1e-9, atol=1e-11)
+
+
+def test_block_krylov_equivariance_and_convergence():
+    """The block Krylov space depends on span(X) only, so bkrylov(X M) =
+    bkrylov(X) M for invertible M; the error against e^A X falls with k."""
+    g = torch.Generator().manual_seed(44)
+    N, n = 16, 4
+    A = 0.3 * _rand_c(g, N, N)
+    X = _rand_c(g, N, n)
+    M = _rand_c(g, n, n) + 2.0 * torch.eye(n, dtype=CT)
+    for k in (1, 2, 3):
+        assert torch.allclose(R.block_krylov_action(A, X @ M, k), R.block_krylov_action(A, X, k) @ M,
+                              rtol=1e-10, atol=1e-11)
+    ref = torch.linalg.matrix_exp(A) @ X
+    errs = [float((R.block_krylov_action(A, X, k) - ref).norm()) for k in range(1, 5)]
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-12 * float(ref.norm())   # k = 4 = N / n: exact
+
+
 # ---------------------------------------------------------------- propagator
 def test_half_step_squares_to_one_body_exponential():
     s, ham = _small_ham()
@@ -398,6 +456,9 @@ def test_first_step_from_trial_closed_form():
     Lbar = R.mean_field_shift(ham)
     B = R.half_step_propagator(hpp, tau).to(CT)
     psi1, lo1, W1, info = R.step(ham, psi, lo, W, x, tau, -5.0, method="krylov", k=ham.N)
+    # block Krylov with N // n blocks spans each spin's whole space: the same step
+    psib, lob, Wb, _ = R.step(ham, psi, lo, W, x, tau, -5.0, method="bkrylov", k=ham.N)
+    assert torch.allclose(psib, psi1, rtol=1e-11, atol=1e-12) and torch.allclose(Wb, W1, rtol=1e-12)
     for w in range(2):
         A = 1j * math.sqrt(tau) * torch.einsum("g,gpq->pq", x[w].to(CT), ham.L.to(CT))
         ref = B @ torch.linalg.matrix_exp(A) @ B @ ham.trial.to(CT)
