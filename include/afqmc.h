@@ -65,7 +65,7 @@ typedef enum {
 enum { AFQMC_SPLIT2 = 0 };
 
 /* Action of the one-body exponential (Sec. IV). */
-enum { AFQMC_EXPM_TAYLOR = 0, AFQMC_EXPM_KRYLOV = 1 };
+enum { AFQMC_EXPM_TAYLOR = 0, AFQMC_EXPM_KRYLOV = 1, AFQMC_EXPM_BLOCK_KRYLOV = 2 };
 
 /* Arithmetic of a context.
  * AFQMC_FP64:  complex128 walkers, every step in FP64.
@@ -101,8 +101,17 @@ typedef struct {
  *   tau         time step (> 0)
  *   e0          best estimate of the ground-state energy E_0 (Eq. imag_prop)
  *   propagator  AFQMC_SPLIT2
- *   expm        AFQMC_EXPM_TAYLOR (order = Taylor order k >= 0) or
- *               AFQMC_EXPM_KRYLOV (order = Krylov dimension 1 <= k <= 32)
+ *   expm        AFQMC_EXPM_TAYLOR (order = Taylor order k >= 0),
+ *               AFQMC_EXPM_KRYLOV (order = Krylov dimension 1 <= k <= 32, one
+ *               Krylov space per orbital column, Eq. krylov) or
+ *               AFQMC_EXPM_BLOCK_KRYLOV (order = number of blocks 1 <= k <= 16,
+ *               Eq. bkrylov: per walker and spin, QR of the n orbitals, block
+ *               Arnoldi with modified Gram-Schmidt, e^{A_k} E_n R of the
+ *               (k n) x (k n) block Hessenberg; at most N / n blocks; the
+ *               space is taken as invariant at the first new block whose QR
+ *               has a diagonal entry <= 1e-12 ||A||_F).  ENOTSUP when the
+ *               (k n)^2 + 3 (k n) n complex entries of the small exponential
+ *               do not fit one block's shared memory
  *   reortho     nonzero: re-orthonormalise every determinant (modified
  *               Gram-Schmidt) after the weight update and recompute logovl
  *   measure     nonzero: evaluate E_L at the new walkers (see

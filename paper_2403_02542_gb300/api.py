@@ -117,7 +117,7 @@ class Context:
         assert fields.dtype == torch.float64 and fields.is_cuda and fields.is_contiguous()
         self._bind_stream()
         p = L.StepParams(float(tau), float(e0), L.AFQMC_SPLIT2,
-                         {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV}[expm],
+                         {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV, "bkrylov": L.AFQMC_EXPM_BLOCK_KRYLOV}[expm],
                          int(order), int(bool(reortho)), int(bool(measure)), int(bool(reuse_bias)))
         cw = w.c_struct()
         L.check(L.lib().afqmc_step(self._h, ctypes.byref(cw), fields.data_ptr(), ctypes.byref(p),
@@ -263,7 +263,7 @@ class Batch:
         e0s = e0 if isinstance(e0, (list, tuple)) else [e0] * n
         ws = (L.Walkers * n)(*[w.c_struct() for w in walker_sets])
         fp = (ctypes.c_void_p * n)(*[f.data_ptr() for f in fields])
-        ex = {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV}[expm]
+        ex = {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV, "bkrylov": L.AFQMC_EXPM_BLOCK_KRYLOV}[expm]
         ps = (L.StepParams * n)(*[L.StepParams(float(taus[i]), float(e0s[i]), L.AFQMC_SPLIT2, ex, int(order),
                                                int(bool(reortho)), int(bool(measure)), int(bool(reuse_bias)))
                                   for i in range(n)])

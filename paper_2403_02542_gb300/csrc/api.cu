@@ -140,7 +140,8 @@ static bool small_inverse(int n, std::vector<double> m, std::vector<double>& inv
 // ---------------------------------------------------------------- workspace
 static void ws_free(Workspace& ws) {
   void* ptrs[] = {ws.theta, ws.t, ws.c, ws.A, ws.psi_b, ws.term0, ws.term1, ws.acc, ws.psi_new, ws.splitk, ws.basis,
-                  ws.hess, ws.beta, ws.scal, ws.logdet, ws.epart, ws.eloc, ws.ecap, ws.emix, ws.alive};
+                  ws.hess, ws.beta, ws.scal, ws.logdet, ws.epart, ws.eloc, ws.ecap, ws.emix, ws.alive,
+                  ws.bk, ws.bk_keff};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   ws = Workspace();
@@ -206,6 +207,7 @@ cudaError_t prepare_kernels(afqmc_ctx* c) {
   if (e == cudaSuccess) e = tc_exchange_prepare(c);
   if (e == cudaSuccess) e = tc_field_prepare(c);
   if (e == cudaSuccess) e = halfstep_prepare_kernel(c);
+  if (e == cudaSuccess) e = c->prec == AFQMC_FP64 ? prepare_bk<double>(c) : prepare_bk<float>(c);
   return e;
 }
 }  // namespace afq
@@ -438,6 +440,22 @@ static GemmArgs site_args(const afqmc_ctx* c, int site, int Nw, double sqrt_tau,
   return g;
 }
 
+// Blocks of the block-Krylov layout for order k: room for min(k, N / n)
+// blocks of either spin (at most N rows of A_k).
+static int bk_blocks(const afqmc_ctx* c, int k) {
+  const int nmax = c->na > c->nb ? c->na : c->nb;
+  const int cap = (c->N + nmax - 1) / nmax;
+  return k < cap ? k : cap;
+}
+// Whether the block-Krylov kernels' shared memory fits for order k.
+static bool bk_fits(const afqmc_ctx* c, int k) {
+  const int nmax = c->na > c->nb ? c->na : c->nb;
+  if (nmax < 1) return false;
+  const size_t cs = c->prec == AFQMC_FP64 ? 16 : 8;
+  const size_t lim = (size_t)max_dyn_smem();
+  return bk_expm_smem(bk_blocks(c, k), nmax, cs) <= lim && ((size_t)nmax * c->N + (size_t)nmax * nmax) * cs <= lim;
+}
+
 template <typename R>
 static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double* x, const afqmc_step_params* p,
                              double* e_loc, double* e_mix) {
@@ -494,6 +512,24 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
       cur = nxt;
     }
     c->launches += p->order * (tc_av ? 2 : 1);
+  } else if (p->expm == AFQMC_EXPM_BLOCK_KRYLOV) {
+    // block Krylov (Eq. bkrylov): QR, then per block the products A B_j and
+    // one block Arnoldi step, then e^{A_k} E_n R and B_k F into acc
+    const int k = p->order;
+    const size_t bstride = (size_t)ws.n_walkers * per;
+    const int nmin = (c->na > 0 && c->nb > 0) ? (c->na < c->nb ? c->na : c->nb) : (c->na > 0 ? c->na : c->nb);
+    const int jmax = k < N / nmin ? k : N / nmin;  // blocks of the spin with the most
+    if (tc_av)
+      PK(AFQMC_K_OTHER, tc_av_normA(c, Nw, s));
+    else
+      PK(AFQMC_K_OTHER, launch_normA<R>(c, Nw, s));
+    PK(AFQMC_K_OTHER, launch_bk_start<R>(c, Nw, k, s));
+    for (int j = 0; j < jmax; ++j) {
+      PK(AFQMC_K_EXPM, av(static_cast<char*>(ws.basis) + j * bstride * cs, ws.term0, nullptr, 1.0));
+      PK(AFQMC_K_OTHER, launch_bk_orth<R>(c, Nw, j, s));
+    }
+    PK(AFQMC_K_OTHER, launch_bk_finish<R>(c, Nw, s));
+    c->launches += 2 + jmax * (tc_av ? 3 : 2) + 2;
   } else {
     const int k = p->order;
     const size_t bstride = (size_t)ws.n_walkers * per;
@@ -1113,6 +1149,8 @@ afqmc_status afqmc_step(afqmc_ctx* c, const afqmc_walkers* w, const double* fiel
     if (p->order < 0 || p->order > 64) return AFQMC_ENOTSUP;
   } else if (p->expm == AFQMC_EXPM_KRYLOV) {
     if (p->order < 1 || p->order > 32) return AFQMC_ENOTSUP;
+  } else if (p->expm == AFQMC_EXPM_BLOCK_KRYLOV) {
+    if (p->order < 1 || p->order > 16 || !bk_fits(c, p->order)) return AFQMC_ENOTSUP;
   } else {
     return AFQMC_ENOTSUP;
   }
@@ -1121,11 +1159,13 @@ afqmc_status afqmc_step(afqmc_ctx* c, const afqmc_walkers* w, const double* fiel
     st = afqmc_set_tau(c, p->tau);
     if (st != AFQMC_OK) return st;
   }
-  const int k = p->expm == AFQMC_EXPM_KRYLOV ? (p->order < c->N ? p->order : c->N) : 0;
+  const bool kry = p->expm == AFQMC_EXPM_KRYLOV || p->expm == AFQMC_EXPM_BLOCK_KRYLOV;
+  const int k = kry ? (p->order < c->N ? p->order : c->N) : 0;
   st = ws_ensure(c, w->n_walkers, k);
   if (st != AFQMC_OK) return st;
+  if (p->expm == AFQMC_EXPM_BLOCK_KRYLOV) CK(bk_ensure(c, w->n_walkers, bk_blocks(c, p->order)));
   afqmc_step_params q = *p;
-  q.order = p->expm == AFQMC_EXPM_KRYLOV ? k : p->order;
+  q.order = kry ? k : p->order;
   if (c->prec == AFQMC_FP64) return run_step<double>(c, w, fields, &q, e_loc, e_mix);
   return run_step<float>(c, w, fields, &q, e_loc, e_mix);
 }
@@ -1377,6 +1417,8 @@ static afqmc_status step_checks(afqmc_ctx* c, const afqmc_walkers* w, const doub
     if (p->order < 0 || p->order > 64) return AFQMC_ENOTSUP;
   } else if (p->expm == AFQMC_EXPM_KRYLOV) {
     if (p->order < 1 || p->order > 32) return AFQMC_ENOTSUP;
+  } else if (p->expm == AFQMC_EXPM_BLOCK_KRYLOV) {
+    if (p->order < 1 || p->order > 16 || !bk_fits(c, p->order)) return AFQMC_ENOTSUP;
   } else {
     return AFQMC_ENOTSUP;
   }
@@ -1398,7 +1440,8 @@ afqmc_status afqmc_batch_step(afqmc_batch* b, const afqmc_walkers* ws, const dou
     afqmc_ctx* c = b->ctxs[i];
     afqmc_status st = step_checks(c, &ws[i], fields[i], &p[i]);
     if (st != AFQMC_OK) return st;
-    if (p[i].expm == AFQMC_EXPM_KRYLOV) q[i].order = p[i].order < c->N ? p[i].order : c->N;
+    if (p[i].expm == AFQMC_EXPM_KRYLOV || p[i].expm == AFQMC_EXPM_BLOCK_KRYLOV)
+      q[i].order = p[i].order < c->N ? p[i].order : c->N;
     double* el = e_loc ? e_loc[i] : nullptr;
     double* em = e_mix ? e_mix[i] : nullptr;
     put(&ws[i], sizeof(afqmc_walkers));
@@ -1420,9 +1463,11 @@ afqmc_status afqmc_batch_step(afqmc_batch* b, const afqmc_walkers* ws, const dou
         afqmc_status st = afqmc_set_tau(c, p[i].tau);
         if (st != AFQMC_OK) return st;
       }
-      const int k = q[i].expm == AFQMC_EXPM_KRYLOV ? q[i].order : 0;
-      afqmc_status st = ws_ensure(c, ws[i].n_walkers, k);
+      const bool kry = q[i].expm == AFQMC_EXPM_KRYLOV || q[i].expm == AFQMC_EXPM_BLOCK_KRYLOV;
+      afqmc_status st = ws_ensure(c, ws[i].n_walkers, kry ? q[i].order : 0);
       if (st != AFQMC_OK) return st;
+      if (q[i].expm == AFQMC_EXPM_BLOCK_KRYLOV)
+        CKW(bk_ensure(c, ws[i].n_walkers, bk_blocks(c, q[i].order)), "block-Krylov workspace");
       CKW(prepare_kernels(c), "prepare_kernels");
       CKW(cudaStreamSynchronize(c->stream), "prepare sync");
     }

@@ -103,6 +103,10 @@ struct Workspace {
   double* ecap = nullptr;    // [Nw]     capped Re E_L
   double* emix = nullptr;    // [4]
   uint8_t* alive = nullptr;  // [Nw]     W > 0 at the start of the step
+  // block Krylov: per (walker, spin) A_k, R and F (k_block_krylov.cu), k_eff
+  void* bk = nullptr;
+  int* bk_keff = nullptr;    // [Nw][2]
+  int bk_cap = 0, bk_k = 0;  // walker capacity and number of blocks of the layout
 };
 
 // per-walker scalar slots in Workspace::scal
@@ -275,6 +279,21 @@ cudaError_t launch_setup(afqmc_ctx* c, cudaStream_t s);
 cudaError_t launch_logovl_from_logdet(const afqmc_ctx* c, const afqmc_walkers* w,
                                       const uint8_t* mask, cudaStream_t s);
 cudaError_t launch_copy_alive(const afqmc_ctx* c, const afqmc_walkers* w, cudaStream_t s);
+
+// block-Krylov action of the exponential (k_block_krylov.cu): bk_ensure sizes
+// the per (walker, spin) area for k blocks; start = QR of psi_b into basis
+// slot 0; orth(j) = block Arnoldi step on W = A B_j in ws.term0; finish =
+// e^{A_k} E_n R and B_k F into ws.acc.
+size_t bk_expm_smem(int k, int nmax, size_t csize);
+cudaError_t bk_ensure(afqmc_ctx* c, int Nw, int k);
+template <typename R>
+cudaError_t launch_bk_start(const afqmc_ctx* c, int Nw, int k, cudaStream_t s);
+template <typename R>
+cudaError_t launch_bk_orth(const afqmc_ctx* c, int Nw, int j, cudaStream_t s);
+template <typename R>
+cudaError_t launch_bk_finish(const afqmc_ctx* c, int Nw, cudaStream_t s);
+template <typename R>
+cudaError_t prepare_bk(const afqmc_ctx* c);
 
 // comb population control (k_population.cu)
 template <typename R>
