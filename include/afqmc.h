@@ -111,7 +111,8 @@ typedef struct {
  *               space is taken as invariant at the first new block whose QR
  *               has a diagonal entry <= 1e-12 ||A||_F).  ENOTSUP when the
  *               (k n)^2 + 3 (k n) n complex entries of the small exponential
- *               do not fit one block's shared memory
+ *               or the k n (n + N) of the combination do not fit one block's
+ *               shared memory
  *   reortho     nonzero: re-orthonormalise every determinant (modified
  *               Gram-Schmidt) after the weight update and recompute logovl
  *   measure     nonzero: evaluate E_L at the new walkers (see

@@ -453,7 +453,8 @@ static bool bk_fits(const afqmc_ctx* c, int k) {
   if (nmax < 1) return false;
   const size_t cs = c->prec == AFQMC_FP64 ? 16 : 8;
   const size_t lim = (size_t)max_dyn_smem();
-  return bk_expm_smem(bk_blocks(c, k), nmax, cs) <= lim && ((size_t)nmax * c->N + (size_t)nmax * nmax) * cs <= lim;
+  return bk_expm_smem(bk_blocks(c, k), nmax, cs) <= lim && bk_orth_smem(c->N, nmax, cs) <= lim &&
+         bk_combine_smem(c->N, bk_blocks(c, k), nmax, cs) <= lim;
 }
 
 template <typename R>

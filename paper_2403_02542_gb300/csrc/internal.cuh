@@ -285,6 +285,8 @@ cudaError_t launch_copy_alive(const afqmc_ctx* c, const afqmc_walkers* w, cudaSt
 // slot 0; orth(j) = block Arnoldi step on W = A B_j in ws.term0; finish =
 // e^{A_k} E_n R and B_k F into ws.acc.
 size_t bk_expm_smem(int k, int nmax, size_t csize);
+size_t bk_orth_smem(int N, int nmax, size_t csize);
+size_t bk_combine_smem(int N, int k, int nmax, size_t csize);
 cudaError_t bk_ensure(afqmc_ctx* c, int Nw, int k);
 template <typename R>
 cudaError_t launch_bk_start(const afqmc_ctx* c, int Nw, int k, cudaStream_t s);

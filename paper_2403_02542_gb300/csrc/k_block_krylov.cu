@@ -9,8 +9,8 @@
 // previous ones by one block modified Gram-Schmidt pass; at most N / n blocks;
 // the space is invariant at the first new block whose QR has a diagonal
 // entry <= 1e-12 ||A||_F.  e^{A_k} E_n is the Taylor series of e^{A_k / s}
-// applied s times (s = ceil ||A_k||_1), each series summed until its terms
-// fall below the working precision.
+// applied s times (s = ceil ||A_k||_1 / 2), each series summed until its
+// terms fall below the working precision.
 //
 // One block of 128 threads per (walker, spin); the basis blocks live in the
 // Krylov basis slots of the workspace ([slot][w][na+nb][N], the spin's
@@ -87,17 +87,17 @@ struct BkLayout {
 };
 
 // Modified Gram-Schmidt QR of the n columns X[b][p] (shared memory, column b
-// at X + b * N) in place, right-looking: once q_j is final every later column
+// at X + b * XS) in place, right-looking: once q_j is final every later column
 // is projected on it, so each column receives the projections q_0, q_1, ...
 // in order.  R[j][l] is written to Rg (row stride ld).  Returns false when a
 // diagonal entry is <= tol (the columns are then left finite).
 template <typename R>
-__device__ bool mgs_smem(cz<R>* X, int N, int n, typename C2<R>::t* Rg, int ld, double tol, double* sh) {
+__device__ bool mgs_smem(cz<R>* X, int N, int XS, int n, typename C2<R>::t* Rg, int ld, double tol, double* sh) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
   __shared__ R s_inv;
   bool ok = true;
   for (int j = 0; j < n; ++j) {
-    cz<R>* xj = X + (size_t)j * N;
+    cz<R>* xj = X + (size_t)j * XS;
     double part = 0.0;
     for (int p = tid; p < N; p += blockDim.x) part += (double)xj[p].re * xj[p].re + (double)xj[p].im * xj[p].im;
     const double r = sqrt(block_reduce(part, false, sh));
@@ -113,7 +113,7 @@ __device__ bool mgs_smem(cz<R>* X, int N, int n, typename C2<R>::t* Rg, int ld, 
     for (int l = tid; l < j; l += blockDim.x) Rg[(size_t)j * ld + l] = st(cz<R>{R(0), R(0)});
     __syncthreads();
     for (int l = j + 1 + wid; l < n; l += nw) {  // one warp per later column
-      cz<R>* xl = X + (size_t)l * N;
+      cz<R>* xl = X + (size_t)l * XS;
       R dr = R(0), di = R(0);
       for (int p = lane; p < N; p += 32) {
         const cz<R> d = cjmul(xj[p], xl[p]);
@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(BKT) bk_start_kernel(const typename C2<R>::t* 
   const P* src = X + ((size_t)w * nc + off) * N;
   for (int e = threadIdx.x; e < n * N; e += blockDim.x) Xs[e] = ld<R>(src[e]);
   __syncthreads();
-  mgs_smem<R>(Xs, N, n, area + L.M * L.M, (int)L.nm, 0.0, sh);
+  mgs_smem<R>(Xs, N, N, n, area + L.M * L.M, (int)L.nm, 0.0, sh);
   P* dst = basis + ((size_t)w * nc + off) * N;
   for (int e = threadIdx.x; e < n * N; e += blockDim.x) dst[e] = st(Xs[e]);
   if (threadIdx.x == 0) {
@@ -176,47 +176,55 @@ __global__ void __launch_bounds__(BKT) bk_orth_kernel(const typename C2<R>::t* _
   const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
   const int nmax = na > nb ? na : nb;
   if (n == 0 || keff[w * 2 + spin] <= j) return;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nw = blockDim.x >> 5;
+  const int tid = threadIdx.x;
   const BkLayout L(k, nmax);
   P* H = bk + ((size_t)w * 2 + spin) * L.stride;
-  cz<R>* Ws = reinterpret_cast<cz<R>*>(bk_smem);  // [n][N]
-  cz<R>* Hs = Ws + (size_t)n * N;                  // [n][n]
+  // W and B_i staged with row stride N + 1 (the entry loop reads them across
+  // rows: the odd stride spreads the rows over the banks)
+  const int NS = N + 1;
+  cz<R>* Ws = reinterpret_cast<cz<R>*>(bk_smem);  // [n][NS]
+  cz<R>* Bs = Ws + (size_t)n * NS;                 // [n][NS]
+  cz<R>* Hs = Bs + (size_t)n * NS;                 // [n][n]
   const size_t col0 = (size_t)w * nc + off;
-  for (int e = tid; e < n * N; e += blockDim.x) Ws[e] = ld<R>(W[col0 * N + e]);
-  __syncthreads();
+  for (int e = tid; e < n * N; e += blockDim.x) {
+    const int b = e / N, p = e - (e / N) * N;
+    Ws[b * NS + p] = ld<R>(W[col0 * N + e]);
+  }
   for (int i = 0; i <= j; ++i) {
     const P* Bi = basis + (size_t)i * bstride + col0 * N;
-    for (int e = wid; e < n * n; e += nw) {  // H_ij[a][b] = B_i[:, a]^dagger W[:, b]
+    for (int e = tid; e < n * N; e += blockDim.x) {
+      const int a = e / N, p = e - (e / N) * N;
+      Bs[a * NS + p] = ld<R>(Bi[e]);
+    }
+    __syncthreads();
+    for (int e = tid; e < n * n; e += blockDim.x) {  // H_ij[a][b] = B_i[:, a]^dagger W[:, b]
       const int a = e / n, b = e - (e / n) * n;
-      R dr = R(0), di = R(0);
-      for (int p = lane; p < N; p += 32) {
-        const cz<R> d = cjmul(ld<R>(Bi[(size_t)a * N + p]), Ws[(size_t)b * N + p]);
-        dr += d.re;
-        di += d.im;
-      }
-      dr = wsum(dr);
-      di = wsum(di);
-      if (lane == 0) {
-        Hs[e] = cz<R>{dr, di};
-        H[((size_t)i * n + a) * L.M + (size_t)j * n + b] = st(cz<R>{dr, di});
-      }
+      const cz<R>* x = Bs + (size_t)a * NS;
+      const cz<R>* y = Ws + (size_t)b * NS;
+      cz<R> acc{R(0), R(0)};
+      for (int p = 0; p < N; ++p) acc = acc + cjmul(x[p], y[p]);
+      Hs[e] = acc;
+      H[((size_t)i * n + a) * L.M + (size_t)j * n + b] = st(acc);
     }
     __syncthreads();
     for (int e = tid; e < n * N; e += blockDim.x) {  // W -= B_i H_ij
       const int b = e / N, p = e - (e / N) * N;
       cz<R> acc{R(0), R(0)};
-      for (int a = 0; a < n; ++a) acc = acc + ld<R>(Bi[(size_t)a * N + p]) * Hs[a * n + b];
-      Ws[e] = Ws[e] - acc;
+      for (int a = 0; a < n; ++a) acc = acc + Bs[a * NS + p] * Hs[a * n + b];
+      Ws[b * NS + p] = Ws[b * NS + p] - acc;
     }
     __syncthreads();
   }
   if (j + 1 >= keff[w * 2 + spin]) return;
   // B_{j+1} H_{j+1,j} = QR(W); R into the subdiagonal block of A_k
   const double tol = 1e-12 * scal[(size_t)w * SC_COUNT + SC_NORMA];
-  const bool ok = mgs_smem<R>(Ws, N, n, H + ((size_t)(j + 1) * n) * L.M + (size_t)j * n, (int)L.M, tol, sh);
+  const bool ok = mgs_smem<R>(Ws, N, NS, n, H + ((size_t)(j + 1) * n) * L.M + (size_t)j * n, (int)L.M, tol, sh);
   P* dst = basis + (size_t)(j + 1) * bstride + col0 * N;
   if (ok) {
-    for (int e = tid; e < n * N; e += blockDim.x) dst[e] = st(Ws[e]);
+    for (int e = tid; e < n * N; e += blockDim.x) {
+      const int b = e / N, p = e - (e / N) * N;
+      dst[e] = st(Ws[b * NS + p]);
+    }
   } else {
     // invariant subspace: stop here; the slot stays finite for the next product
     for (int e = tid; e < n * N; e += blockDim.x) dst[e] = st(cz<R>{R(0), R(0)});
@@ -243,28 +251,34 @@ __global__ void __launch_bounds__(BKT) bk_expm_kernel(typename C2<R>::t* __restr
   const BkLayout L(k, nmax);
   P* area = bk + ((size_t)w * 2 + spin) * L.stride;
   const int m = keff[w * 2 + spin] * n;
-  cz<R>* Hs = reinterpret_cast<cz<R>*>(bk_smem);  // [m][m] row-major
+  // A_k column-major in shared memory (Hs[c * m + r] = A_k[r][c]): the lanes
+  // of a warp take consecutive rows r of one product column, so they read
+  // consecutive words
+  cz<R>* Hs = reinterpret_cast<cz<R>*>(bk_smem);
   cz<R>* X = Hs + (size_t)m * m;                   // [n][m]: column b of the running result
   cz<R>* T = X + (size_t)m * n;                    // current series term
   cz<R>* U = T + (size_t)m * n;                    // next term
   for (int e = tid; e < m * m; e += blockDim.x) {
     const int r = e / m, c = e - (e / m) * m;
-    Hs[e] = ld<R>(area[(size_t)r * L.M + c]);
+    Hs[(size_t)c * m + r] = ld<R>(area[(size_t)r * L.M + c]);
   }
   for (int e = tid; e < m * n; e += blockDim.x) {
     const int b = e / m, r = e - (e / m) * m;
     X[e] = cz<R>{r == b ? R(1) : R(0), R(0)};
   }
-  __syncthreads();
-  double cs = 0.0;  // ||A_k||_1: largest column sum of |entries|
+  double cs = 0.0;  // ||A_k||_1: largest column sum of |entries| (rows read along c)
   for (int c = tid; c < m; c += blockDim.x) {
     double t = 0.0;
-    for (int r = 0; r < m; ++r) t += sqrt((double)Hs[r * m + c].re * Hs[r * m + c].re + (double)Hs[r * m + c].im * Hs[r * m + c].im);
+    for (int r = 0; r < m; ++r) {
+      const cz<R> h = ld<R>(area[(size_t)r * L.M + c]);
+      t += sqrt((double)h.re * h.re + (double)h.im * h.im);
+    }
     cs = fmax(cs, t);
   }
-  const double norm1 = block_reduce(cs, true, sh);
-  // (bounded: a non-finite or huge norm takes at most 4096 sub-steps)
-  const int nsteps = norm1 > 1.0 ? (norm1 < 4096.0 ? (int)ceil(norm1) : 4096) : 1;
+  const double norm1 = block_reduce(cs, true, sh);  // (its barriers also publish Hs and X)
+  // sub-steps of norm <= 2 (bounded: a non-finite or huge norm takes at most
+  // 4096 sub-steps)
+  const int nsteps = norm1 > 2.0 ? (norm1 < 8192.0 ? (int)ceil(0.5 * norm1) : 4096) : 1;
   const double eps = std::is_same<R, double>::value ? 1.1e-16 : 6.0e-8;
   const int max_terms = std::is_same<R, double>::value ? 40 : 24;
   for (int step = 0; step < nsteps; ++step) {
@@ -275,10 +289,9 @@ __global__ void __launch_bounds__(BKT) bk_expm_kernel(typename C2<R>::t* __restr
       double tmax = 0.0, xmax = 0.0;
       for (int e = tid; e < m * n; e += blockDim.x) {  // U = A_k T / (s t); X += U
         const int b = e / m, r = e - (e / m) * m;
-        const cz<R>* hr = Hs + (size_t)r * m;
         const cz<R>* tb = T + (size_t)b * m;
         cz<R> acc{R(0), R(0)};
-        for (int c = 0; c < m; ++c) acc = acc + hr[c] * tb[c];
+        for (int c = 0; c < m; ++c) acc = acc + Hs[(size_t)c * m + r] * tb[c];
         acc = cz<R>{acc.re * scale, acc.im * scale};
         U[e] = acc;
         const cz<R> x = X[e] + acc;
@@ -329,13 +342,16 @@ __global__ void __launch_bounds__(BKT) bk_combine_kernel(const typename C2<R>::t
   }
   __syncthreads();
   const size_t col0 = (size_t)w * nc + off;
+  cz<R>* Bs = Fs + (size_t)m * n;  // [m][N]: the k_eff basis blocks stacked, row i n + a = B_i[:, a]
+  for (int i = 0; i < ke; ++i) {
+    const P* Bi = basis + (size_t)i * bstride + col0 * N;
+    for (int e = threadIdx.x; e < n * N; e += blockDim.x) Bs[(size_t)i * n * N + e] = ld<R>(Bi[e]);
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < n * N; e += blockDim.x) {
     const int b = e / N, p = e - (e / N) * N;
     cz<R> acc{R(0), R(0)};
-    for (int i = 0; i < ke; ++i) {
-      const P* Bi = basis + (size_t)i * bstride + col0 * N + p;
-      for (int a = 0; a < n; ++a) acc = acc + ld<R>(Bi[(size_t)a * N]) * Fs[(i * n + a) * n + b];
-    }
+    for (int r = 0; r < m; ++r) acc = acc + Bs[(size_t)r * N + p] * Fs[r * n + b];
     out[col0 * N + e] = st(acc);
   }
 }
@@ -348,10 +364,16 @@ cudaError_t bk_smem_limit(const afqmc_ctx* c, F* f, size_t bytes) {
 
 }  // namespace
 
-// shared-memory bytes of the small-exponential kernel (the largest of the four)
+// shared-memory bytes of the small-exponential and the Arnoldi kernels
 size_t bk_expm_smem(int k, int nmax, size_t csize) {
   const size_t m = (size_t)k * nmax;
   return (m * m + 3 * m * nmax) * csize;
+}
+size_t bk_combine_smem(int N, int k, int nmax, size_t csize) {
+  return (size_t)k * nmax * ((size_t)nmax + N) * csize;
+}
+size_t bk_orth_smem(int N, int nmax, size_t csize) {
+  return (2 * (size_t)nmax * (N + 1) + (size_t)nmax * nmax) * csize;
 }
 
 cudaError_t bk_ensure(afqmc_ctx* c, int Nw, int k) {
@@ -395,7 +417,7 @@ template <typename R>
 cudaError_t launch_bk_orth(const afqmc_ctx* c, int Nw, int j, cudaStream_t s) {
   typedef typename C2<R>::t P;
   const int nmax = c->na > c->nb ? c->na : c->nb;
-  const size_t shm = ((size_t)nmax * c->N + (size_t)nmax * nmax) * sizeof(P);
+  const size_t shm = bk_orth_smem(c->N, nmax, sizeof(P));
   cudaError_t e = bk_smem_limit(c, bk_orth_kernel<R>, shm);
   if (e != cudaSuccess) return e;
   const size_t bstride = (size_t)c->ws.n_walkers * c->nc * c->N;
@@ -416,7 +438,7 @@ cudaError_t launch_bk_finish(const afqmc_ctx* c, int Nw, cudaStream_t s) {
                                                   c->ws.bk_k);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t shc = (size_t)c->ws.bk_k * nmax * nmax * sizeof(P);
+  const size_t shc = bk_combine_smem(c->N, c->ws.bk_k, nmax, sizeof(P));
   e = bk_smem_limit(c, bk_combine_kernel<R>, shc);
   if (e != cudaSuccess) return e;
   const size_t bstride = (size_t)c->ws.n_walkers * c->nc * c->N;
