@@ -9,7 +9,7 @@
 // previous ones by one block modified Gram-Schmidt pass; at most N / n blocks;
 // the space is invariant at the first new block whose QR has a diagonal
 // entry <= 1e-12 ||A||_F.  e^{A_k} E_n is the Taylor series of e^{A_k / s}
-// applied s times (s = ceil ||A_k||_1 / 2), each series summed until its
+// applied s times (s = ceil ||A_k||_1 / 4), each series summed until its
 // terms fall below the working precision.
 //
 // One block of 128 threads per (walker, spin); the basis blocks live in the
@@ -276,9 +276,10 @@ __global__ void __launch_bounds__(BKT) bk_expm_kernel(typename C2<R>::t* __restr
     cs = fmax(cs, t);
   }
   const double norm1 = block_reduce(cs, true, sh);  // (its barriers also publish Hs and X)
-  // sub-steps of norm <= 2 (bounded: a non-finite or huge norm takes at most
-  // 4096 sub-steps)
-  const int nsteps = norm1 > 2.0 ? (norm1 < 8192.0 ? (int)ceil(0.5 * norm1) : 4096) : 1;
+  // sub-steps of norm <= 4: the terms peak near 4^4/4! ~ 11 before they fall,
+  // a digit of headroom (bounded: a non-finite or huge norm takes at most 4096
+  // sub-steps)
+  const int nsteps = norm1 > 4.0 ? (norm1 < 16384.0 ? (int)ceil(0.25 * norm1) : 4096) : 1;
   const double eps = std::is_same<R, double>::value ? 1.1e-16 : 6.0e-8;
   const int max_terms = std::is_same<R, double>::value ? 40 : 24;
   for (int step = 0; step < nsteps; ++step) {
