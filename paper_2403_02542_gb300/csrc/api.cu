@@ -387,7 +387,7 @@ static afqmc_status run_energy(afqmc_ctx* c, const afqmc_walkers* w, double e0, 
   CK(launch_energy<R>(c, Nw, w->weight, e0, tau, e_loc ? e_loc : c->ws.eloc, e_mix ? e_mix : c->ws.emix, s, &nl));
   // ws.epart now holds sum_s tr(Lh_gs Theta_s) of these walkers (a later step may reuse it)
   CK(launch_bias_mark(c, w->psi, Nw, s));
-  c->launches += 3 + nl;
+  c->launches += (theta_ready ? 0 : 1) + nl + 1;
   return AFQMC_OK;
 }
 

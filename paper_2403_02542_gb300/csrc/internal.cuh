@@ -356,7 +356,9 @@ cudaError_t tc_exchange_ws(afqmc_ctx* c);
 size_t tc_exchange_plane_bytes(const TcPlan& P, int cap);
 cudaError_t tc_exchange_bind(TcPlan& P, void* b_hi, void* b_lo, int cap);
 void tc_exchange_free(afqmc_ctx* c);
-cudaError_t tc_exchange_launch(afqmc_ctx* c, int Nw, const void* theta, double* epart, cudaStream_t s);
+// split Theta planes of Nw walkers, then the contraction (writes epart)
+cudaError_t tc_exchange_planes(afqmc_ctx* c, int Nw, const void* theta, cudaStream_t s);
+cudaError_t tc_exchange_contract(afqmc_ctx* c, int Nw, double* epart, cudaStream_t s);
 
 // tensor-core field assembly (k_gemm_tc.cu)
 cudaError_t tc_field_setup(afqmc_ctx* c, cudaStream_t s);

