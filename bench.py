@@ -613,8 +613,6 @@ def run_ours(args):
     achieved = (ex_flop / (ex_ms / ex_n / 1000.0)) / 1e12 if ex_n else None
     # DRAM bytes of one exchange launch (read + write), ncu capture of this kernel
     # version at the benchmark size (profiles/launches_mixed_large.md)
-    # DRAM bytes of one exchange launch (read + write), ncu capture of this kernel
-    # version at the benchmark size (profiles/launches_mixed_large.md)
     traffic, traffic_note = None, None
     if args.precision == "mixed" and NW == 1024:
         traffic = 63.51e6
