@@ -77,6 +77,30 @@ def dist_env():
     return rank, world, local
 
 
+# ------------------------------------------------------------------ ranks
+def slowest_rank(seconds: float, world: int, device) -> float:
+    """The largest of one per-rank duration over all ranks (the job lasts as long
+    as its slowest rank); the duration itself when the job has one rank."""
+    if world == 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
+def job_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (walkers are sharded, so each rank holds the same number)."""
+    return world * units_per_rank / seconds
+
+
+def shard_seed(base: int, rank: int) -> int:
+    """Seed of a rank's synthetic fields: each rank draws its own walkers' fields."""
+    return base + rank
+
+
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
@@ -461,7 +485,7 @@ def run_ours(args):
 
     K, Wm = args.steps, args.warmup
     gen = torch.Generator(device=dev)
-    gen.manual_seed(1234 + rank)
+    gen.manual_seed(shard_seed(1234, rank))
     fields = torch.randn(Wm + K, NW, G, dtype=torch.float64, device=dev, generator=gen)
     step_idx = 0
 
@@ -496,16 +520,12 @@ def run_ours(args):
     ctx.profile(False)
     prof = ctx.profile_read()
     clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t[0])
-    value = world * NW * K / (ms / 1000.0)
+    ms = slowest_rank(ev0.elapsed_time(ev1), world, dev)
+    value = job_rate(NW * K, world, ms / 1000.0)
     emix_final = float(e_mix[2])
 
     # -------- end to end through the API with host buffers
-    rng = np.random.default_rng(4321 + rank)
+    rng = np.random.default_rng(shard_seed(4321, rank))
     host_fields = torch.from_numpy(rng.standard_normal((K, NW, G))).pin_memory()
     x_dev = torch.empty(NW, G, dtype=torch.float64, device=dev)
     emix_host = torch.empty(4, dtype=torch.float64).pin_memory()
@@ -520,12 +540,10 @@ def run_ours(args):
         stream.synchronize()
         _ = float(emix_host[2])
     torch.cuda.synchronize()
-    te = time.perf_counter() - t0
-    tt = torch.tensor([te], dtype=torch.float64, device=dev)
+    te = slowest_rank(time.perf_counter() - t0, world, dev)
     if world > 1:
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         dist.barrier()
-    e2e = world * NW * K / float(tt[0])
+    e2e = job_rate(NW * K, world, te)
 
     # -------- the same step replayed as a CUDA graph (one-system batch)
     from paper_2403_02542_gb300.api import Batch
@@ -553,10 +571,8 @@ def run_ours(args):
         graph_step(i)
     g1.record(stream)
     torch.cuda.synchronize()
-    tg = torch.tensor([g0.elapsed_time(g1)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(tg, op=dist.ReduceOp.MAX)
-    graph_value = world * NW * K / (float(tg[0]) / 1000.0)
+    tg = slowest_rank(g0.elapsed_time(g1), world, dev)
+    graph_value = job_rate(NW * K, world, tg / 1000.0)
     batch.close()
 
     # -------- the FP64 path on the same workload, for the mixed-vs-FP64 comparison
@@ -581,10 +597,8 @@ def run_ours(args):
                      measure=True, e_loc=el64, e_mix=em64, reuse_bias=True)
         h1e.record(stream)
         torch.cuda.synchronize()
-        th = torch.tensor([h0.elapsed_time(h1e)], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(th, op=dist.ReduceOp.MAX)
-        fp64_value = world * NW * k64 / (float(th[0]) / 1000.0)
+        th = slowest_rank(h0.elapsed_time(h1e), world, dev)
+        fp64_value = job_rate(NW * k64, world, th / 1000.0)
         c64.close()
 
     if rank != 0:
