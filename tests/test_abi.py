@@ -110,3 +110,25 @@ def test_product_path_fails_loudly_without_library(monkeypatch):
     monkeypatch.setattr(L, "LIB_PATH", "/nonexistent/libafqmc.so")
     with pytest.raises(RuntimeError, match="missing"):
         L.lib()
+
+
+def test_binding_constants_match_the_header():
+    """Every enumerator and #define value of the header equals the binding's."""
+    text = open(os.path.join(ROOT, "include", "afqmc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    values = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+        for name, val in re.findall(r"(AFQMC_\w+)\s*=\s*(\d+)", body):
+            values[name] = int(val)
+    for name, val in re.findall(r"#define\s+(AFQMC_W_\w+)\s+(0x[0-9a-fA-F]+)u", text):
+        values[name] = int(val, 16)
+    assert values["AFQMC_EXPM_BLOCK_KRYLOV"] == 2 and values["AFQMC_MIXED"] == 1
+    for name, val in values.items():
+        if name.startswith("AFQMC_K_") and name != "AFQMC_K_COUNT":
+            assert L.KERNEL_CLASSES[val] == name[len("AFQMC_K_"):].lower().replace("forcebias", "force_bias") \
+                .replace("halfstep", "half_step"), name
+        elif hasattr(L, name):
+            assert getattr(L, name) == val, name
+    assert values["AFQMC_K_COUNT"] == len(L.KERNEL_CLASSES)
+    m = re.search(r"AFQMC_STATIC_SCRATCH_BYTES\s*\(\(unsigned long long\)(\d+)\s*<<\s*(\d+)\)", text)
+    assert m and L.STATIC_SCRATCH_BYTES == int(m.group(1)) << int(m.group(2))
