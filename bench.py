@@ -64,6 +64,8 @@ def parse():
                     help="skip the timed gradient of the differentiation workload")
     ap.add_argument("--no-block-krylov", action="store_true",
                     help="skip the large workload with the block-Krylov exponential")
+    ap.add_argument("--no-tau-scan", action="store_true",
+                    help="skip the energy runs and time-step extrapolation of the small workload")
     ap.add_argument("--cpu-sample-walkers", type=int, default=4)
     ap.add_argument("--walkers", type=int, default=NW,
                     help="walkers per GPU (the workload has 1024; fewer only for small profiling cases)")
@@ -380,6 +382,53 @@ def block_krylov_rate(dev, steps=5):
     return out
 
 
+def tau_scan(dev, imag_time=10.0, taus=(0.01, 0.02, 0.05, 0.1), nw=1024):
+    """Energy runs and the time-step extrapolation (Sec. VI) on the small
+    workload (N=8, 2+2 electrons, 32 vectors lambda_g = 0.5^g, Split-2 +
+    Taylor-6, QR every 5 steps, FP64): for each tau, imag_time / tau steps of
+    1024 walkers with E_L every step, comb population control every 10 steps
+    and E_0 updates, the first 30 % as equilibration; the blocking analysis of
+    each run and the fit E(tau) = E_0 + beta tau^2."""
+    import numpy as np
+    import torch
+    from paper_2403_02542_gb300 import energy as S
+    from paper_2403_02542_gb300.api import Context
+    from paper_2403_02542_gb300.inputs import config_system
+    s = config_system("small")
+    runs = []
+    t0 = time.perf_counter()
+    total_steps = 0
+    for i, tau in enumerate(taus):
+        n_steps = int(round(imag_time / tau))
+        n_eq = int(0.3 * n_steps)
+        ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision="fp64", device=dev)
+        w = ctx.new_walkers(nw)
+        ctx.init_walkers(w)
+        el = torch.empty(nw, 2, dtype=torch.float64, device=dev)
+        em = torch.empty(4, dtype=torch.float64, device=dev)
+        ctx.local_energy(w, 0.0, tau, el, em)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(100 + i)
+        x = torch.empty(nw, s.G, dtype=torch.float64, device=dev)
+
+        def fields(k):
+            return x.normal_(generator=gen)
+
+        out = S.energy_run(ctx, w, tau, float(em[2]), n_steps, fields=fields, n_eq=n_eq, expm="taylor", order=6,
+                           reortho_every=5, pop_every=10, seed=200 + i, update_e0=True)
+        st = out["stats"]
+        runs.append({"tau": tau, "steps": n_steps, "E": st["E_bar"], "sigma": st["sigma"], "kappa": st["kappa"]})
+        total_steps += n_steps
+        ctx.close()
+    wall = time.perf_counter() - t0
+    e0, beta, s0, sb, chi2 = S.extrapolate([r["tau"] for r in runs], [r["E"] for r in runs],
+                                           [r["sigma"] for r in runs], 2)
+    return {"workload": "small workload (N=8, Na=Nb=2, N_gamma=32, lambda_g=0.5^g), FP64, 1024 walkers, "
+                        "Split-2 + Taylor-6, QR every 5, comb every 10 steps, E_0 updated, imaginary time 10 per tau",
+            "runs": runs, "fit": {"E0": e0, "beta": beta, "sigma_E0": s0, "sigma_beta": sb, "chi2_dof": chi2},
+            "wall_s": wall, "walker_steps_per_s": nw * total_steps / wall}
+
+
 def batched_rate(dev, steps=3, warmup=2):
     """Batched workload: 16 systems with N uniform in 64..400, N/6 electrons
     per spin, 5N vectors, 256-2048 walkers each; all systems advanced by one
@@ -644,6 +693,9 @@ def run_ours(args):
     block_krylov = None
     if world == 1 and not args.no_block_krylov:
         block_krylov = block_krylov_rate(dev)
+    tau_ext = None
+    if world == 1 and not args.no_tau_scan:
+        tau_ext = tau_scan(dev)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu, _ = oracle_rate(system, args.cpu_sample_walkers, 2, "")
@@ -675,6 +727,7 @@ def run_ours(args):
         "precision_workload": precision,
         "batched_workload": batched,
         "block_krylov_workload": block_krylov,
+        "tau_extrapolation": tau_ext,
         "clocks": clk,
         "e_mix_last": emix_final,
     }

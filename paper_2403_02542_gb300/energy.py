@@ -1,0 +1,124 @@
+"""Energy runs and their statistics: the time average of the mixed estimator
+with its variance and correlation length (Sec. II.A), and the time-step
+extrapolation E(tau) = E_0 + beta tau^2 (Split-2, quadratic) or E_0 + alpha tau
+(linear) (Sec. VI).
+
+Readings where the paper leaves the procedure open:
+  * the correlation length kappa of the variance sigma_Ebar^2 = sigma_E^2 kappa / N
+    is taken from a blocking analysis: the post-equilibration series E_k is
+    averaged (weights W_k) in blocks of 2^b steps, the variance of the mean is
+    estimated from the block means at every level, and the first level whose
+    estimate is within its own statistical uncertainty of the next level's (a
+    plateau) is kept; kappa = N sigma_Ebar^2 / sigma_E^2;
+  * E_0 (the best estimate of the ground-state energy, Eq. imag_prop) may be
+    updated during a run: at every population-control event it becomes the
+    latest mixed estimate E_k during equilibration and the running time
+    average after it;
+  * population control is the comb of afqmc_population_control with uniform
+    numbers drawn from one seeded generator per run.
+The statistics are host arithmetic on the per-step estimates; the steps run in
+the library.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def time_average(W, E, n_eq: int = 0):
+    """(E_bar, sigma_E^2) of the samples k > n_eq: E_bar = sum W_k E_k / sum W_k,
+    sigma_E^2 = <E^2> - E_bar^2 with the same weights (Sec. II.A)."""
+    W = np.asarray(W, dtype=np.float64)[n_eq:]
+    E = np.asarray(E, dtype=np.float64)[n_eq:]
+    if W.size == 0 or not W.sum() > 0:
+        raise ValueError("no samples after equilibration")
+    wsum = W.sum()
+    ebar = float((W * E).sum() / wsum)
+    e2 = float((W * E * E).sum() / wsum)
+    return ebar, max(e2 - ebar * ebar, 0.0)
+
+
+def blocking(W, E, n_eq: int = 0, min_blocks: int = 8):
+    """Blocking analysis of the post-equilibration series.  Returns a dict with
+    E_bar, sigma_E2, the chosen block size, sigma (the standard error of E_bar),
+    kappa = N sigma^2 / sigma_E^2 and the per-level estimates [(size, sigma, dsigma)]."""
+    W = np.asarray(W, dtype=np.float64)[n_eq:]
+    E = np.asarray(E, dtype=np.float64)[n_eq:]
+    n = E.size
+    ebar, var = time_average(W, E)
+    levels = []
+    size = 1
+    while n // size >= min_blocks:
+        nb = n // size
+        Wb = W[: nb * size].reshape(nb, size)
+        Eb = E[: nb * size].reshape(nb, size)
+        means = (Wb * Eb).sum(1) / Wb.sum(1)
+        s2 = float(((means - means.mean()) ** 2).sum() / (nb - 1) / nb)  # variance of the mean
+        s = math.sqrt(max(s2, 0.0))
+        levels.append((size, s, s / math.sqrt(2.0 * (nb - 1))))
+        size *= 2
+    if not levels:
+        raise ValueError("too few samples for a blocking analysis")
+    chosen = levels[-1]
+    for a, b in zip(levels, levels[1:]):
+        if b[1] - a[1] <= a[2]:  # the next level agrees within this level's uncertainty
+            chosen = a
+            break
+    sigma = chosen[1]
+    kappa = n * sigma * sigma / var if var > 0 else 1.0
+    return dict(E_bar=ebar, sigma_E2=var, block=chosen[0], sigma=sigma, kappa=kappa, levels=levels, n=n)
+
+
+def extrapolate(taus, energies, sigmas=None, power: int = 2):
+    """Weighted least-squares fit E(tau) = E_0 + c tau^power (power 2: Split-2 and
+    the Taylor propagator; power 1: Split-1 and Crank-Nicolson).  Returns
+    (E_0, c, sigma_E0, sigma_c, chi2 per degree of freedom or None)."""
+    t = np.asarray(taus, dtype=np.float64)
+    y = np.asarray(energies, dtype=np.float64)
+    if t.size < 2:
+        raise ValueError("need at least two time steps")
+    s = np.ones_like(y) if sigmas is None else np.asarray(sigmas, dtype=np.float64)
+    X = np.stack([np.ones_like(t), t ** power], axis=1)
+    wgt = 1.0 / (s * s)
+    F = X.T @ (X * wgt[:, None])
+    cov = np.linalg.inv(F)
+    beta = cov @ (X.T @ (wgt * y))
+    resid = y - X @ beta
+    dof = t.size - 2
+    chi2 = float((wgt * resid * resid).sum() / dof) if dof > 0 else None
+    return float(beta[0]), float(beta[1]), math.sqrt(cov[0, 0]), math.sqrt(cov[1, 1]), chi2
+
+
+def energy_run(ctx, walkers, tau: float, e0: float, n_steps: int, *, fields, n_eq: int = 0,
+               expm: str = "krylov", order: int = 10, reortho_every: int = 5, pop_every: int = 0,
+               seed: int = 0, update_e0: bool = False, reuse_bias: bool = False):
+    """Propagate `walkers` for n_steps steps of the library with the local energy
+    measured every step.  fields(k) returns the device fields [Nw, G] of step k.
+    With pop_every > 0 the population is combed after every pop_every steps
+    (uniform numbers from numpy's PCG64 seeded with `seed`).  Returns a dict
+    with the per-step total weight W, mixed estimate E and E_0 used, and the
+    blocking analysis of the steps after n_eq."""
+    import torch
+    nw = walkers.n
+    dev = ctx.device
+    e_loc = torch.empty(nw, 2, dtype=torch.float64, device=dev)
+    e_mix = torch.empty(4, dtype=torch.float64, device=dev)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Ws, Es, E0s = [], [], []
+    for k in range(n_steps):
+        reo = reortho_every > 0 and (k + 1) % reortho_every == 0
+        ctx.step(walkers, fields(k), tau, e0, expm=expm, order=order, reortho=reo, measure=True,
+                 e_loc=e_loc, e_mix=e_mix, reuse_bias=reuse_bias)
+        m = e_mix.cpu()
+        E0s.append(e0)
+        Ws.append(float(m[1]))
+        Es.append(float(m[2]))
+        if pop_every > 0 and (k + 1) % pop_every == 0:
+            ctx.population_control(walkers, float(rng.random()))
+            if update_e0:
+                e0 = Es[-1] if k < n_eq else time_average(Ws, Es, n_eq)[0]
+    out = dict(W=Ws, E=Es, e0=E0s)
+    if n_steps - n_eq >= 16:
+        out["stats"] = blocking(Ws, Es, n_eq)
+    return out

@@ -1,0 +1,73 @@
+"""Statistics of the energy run (no GPU): the weighted time average and
+variance of Sec. II.A, the correlation length of Eq. variance from a blocking
+analysis, checked on series whose correlation is known in closed form, and the
+time-step extrapolation fits, checked on exact and on noisy synthetic data."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2403_02542_gb300 import energy as S
+
+
+def test_time_average_small_example_and_weight_scale():
+    W, E = [5.0, 1.0, 2.0, 1.0], [9.0, 1.0, 2.0, 4.0]
+    ebar, var = S.time_average(W, E, n_eq=1)          # the first sample is equilibration
+    assert ebar == pytest.approx(9.0 / 4.0) and var == pytest.approx(25.0 / 4.0 - (9.0 / 4.0) ** 2)
+    e2, v2 = S.time_average([3 * x for x in W], E, n_eq=1)   # a common weight factor cancels
+    assert e2 == pytest.approx(ebar) and v2 == pytest.approx(var)
+    with pytest.raises(ValueError):
+        S.time_average([0.0, 0.0], [1.0, 2.0])
+
+
+def test_blocking_uncorrelated_series():
+    rng = np.random.default_rng(1)
+    n = 1 << 14
+    E = rng.standard_normal(n)
+    r = S.blocking(np.ones(n), E)
+    assert 0.75 < r["kappa"] < 1.35
+    assert r["sigma"] == pytest.approx(1.0 / math.sqrt(n), rel=0.25)
+
+
+@pytest.mark.parametrize("rho", [0.5, 0.8, 0.9])
+def test_blocking_ar1_correlation_length(rho):
+    """AR(1) E_k = rho E_{k-1} + noise: kappa = (1 + rho) / (1 - rho)."""
+    rng = np.random.default_rng(7)
+    n = 1 << 17
+    x = np.empty(n)
+    x[0] = 0.0
+    eps = rng.standard_normal(n)
+    for k in range(1, n):
+        x[k] = rho * x[k - 1] + eps[k]
+    r = S.blocking(np.ones(n), 10.0 + x, n_eq=0)
+    kappa = (1 + rho) / (1 - rho)
+    assert r["kappa"] == pytest.approx(kappa, rel=0.3), (r["kappa"], kappa)
+    assert r["E_bar"] == pytest.approx(10.0, abs=6 * r["sigma"])
+
+
+@pytest.mark.parametrize("power", [1, 2])
+def test_extrapolation_exact_data(power):
+    taus = [0.01, 0.02, 0.05, 0.1]
+    e0, c = -75.25, 3.5
+    y = [e0 + c * t ** power for t in taus]
+    f0, fc, s0, sc, chi2 = S.extrapolate(taus, y, None, power)
+    assert f0 == pytest.approx(e0, abs=1e-12) and fc == pytest.approx(c, rel=1e-10)
+    assert chi2 == pytest.approx(0.0, abs=1e-20)
+
+
+def test_extrapolation_errors_match_the_scatter():
+    """Noisy replicas: the spread of the fitted E_0 matches its reported error
+    and chi^2 per degree of freedom averages to one."""
+    rng = np.random.default_rng(3)
+    taus = np.array([0.01, 0.02, 0.05, 0.1, 0.2])
+    sig = np.array([2e-3, 1.5e-3, 1e-3, 1e-3, 1e-3])
+    e0, c = -1.0, 0.8
+    fits, chis = [], []
+    for _ in range(4000):
+        y = e0 + c * taus ** 2 + sig * rng.standard_normal(taus.size)
+        f0, fc, s0, sc, chi2 = S.extrapolate(taus, y, sig, 2)
+        fits.append(f0)
+        chis.append(chi2)
+    assert np.std(fits) == pytest.approx(s0, rel=0.06)
+    assert np.mean(fits) == pytest.approx(e0, abs=4 * s0 / math.sqrt(len(fits)))
+    assert np.mean(chis) == pytest.approx(1.0, rel=0.06)
