@@ -58,7 +58,8 @@ __all__ = [
     "log_overlap", "theta", "mean_field_shift", "mixed_L_expectation",
     "force_bias", "propagation_h1", "half_step_propagator", "field_matrix",
     "taylor_action", "krylov_action", "block_krylov_action", "exact_action", "expm_action",
-    "split2_propagate", "local_energy", "energy_window", "mixed_energy",
+    "split2_propagate", "split1_propagate", "taylor_propagate", "crank_nicolson_propagate", "propagate",
+    "local_energy", "energy_window", "mixed_energy",
     "mgs_qr", "reorthonormalise", "weight_update", "step", "init_walkers",
     "free_projection_step", "comb", "population_control", "StepInfo",
     "walk_objective",
@@ -311,6 +312,42 @@ def split2_propagate(B, A, psi, method, k, spins=None):
     return Bc @ expm_action(A, Bc @ psi, method, k, spins)
 
 
+def split1_propagate(B, A, psi, method, k, spins=None):
+    """U_S1 Psi = e^{-tau H1} e^{A} Psi (Sec. III, Split-1): the interaction
+    exponential first, then the whole one-body step B B = e^{-tau h''}."""
+    Bc = B.to(CT)
+    return Bc @ (Bc @ expm_action(A, psi, method, k, spins))
+
+
+def taylor_propagate(hpp, A, psi, tau, k):
+    """U_T Psi = taylor_k{-tau Heff, Psi} with -tau Heff = A - tau h'' (Sec. III,
+    Taylor propagator: the refactorised exponent expanded directly)."""
+    return taylor_action(A - tau * hpp.to(CT), psi, k)
+
+
+def crank_nicolson_propagate(hpp, A, psi, tau):
+    """U_CN Psi = (1 + tau Heff/2)^{-1} (1 - tau Heff/2) Psi (Sec. III,
+    Crank-Nicolson) with -tau Heff = A - tau h''."""
+    X = A - tau * hpp.to(CT)
+    eye = torch.eye(X.shape[-1], dtype=CT)
+    return torch.linalg.solve(eye - 0.5 * X, psi + 0.5 * (X @ psi))
+
+
+def propagate(propagator, B, hpp, A, psi, tau, method, k, spins=None):
+    """The walker update of Eq. psiupdate for one of the propagators of Sec. III:
+    "split2" (default), "split1", "taylor" (the Taylor propagator; k is its
+    order and `method` is ignored) or "cn" (Crank-Nicolson)."""
+    if propagator == "split2":
+        return split2_propagate(B, A, psi, method, k, spins)
+    if propagator == "split1":
+        return split1_propagate(B, A, psi, method, k, spins)
+    if propagator == "taylor":
+        return taylor_propagate(hpp, A, psi, tau, k)
+    if propagator == "cn":
+        return crank_nicolson_propagate(hpp, A, psi, tau)
+    raise ValueError(propagator)
+
+
 # --------------------------------------------------------------------------
 # Local energy and the mixed estimator (Eq. eloc; Sec. V.A capping)
 # --------------------------------------------------------------------------
@@ -432,8 +469,9 @@ def init_walkers(ham: Hamiltonian, n_walkers):
 
 
 def step(ham: Hamiltonian, psi, logovl, W, x, tau, e0, method="krylov", k=10,
-         reortho=False, B=None, L_bar=None, ec=None):
-    """One phaseless walker step with the Split-2 propagator.
+         reortho=False, B=None, L_bar=None, ec=None, propagator="split2"):
+    """One phaseless walker step (by default with the Split-2 propagator;
+    `propagator` selects another walker update of Sec. III, see `propagate`).
 
     psi [Nw, N, na+nb] complex, logovl [Nw] complex, W [Nw] real, x [Nw, G]
     real standard-normal fields.  Walkers with W = 0 are kept as they are.
@@ -441,14 +479,15 @@ def step(ham: Hamiltonian, psi, logovl, W, x, tau, e0, method="krylov", k=10,
     """
     if L_bar is None:
         L_bar = mean_field_shift(ham)
-    if B is None or ec is None:
+    hpp = None
+    if B is None or ec is None or propagator in ("taylor", "cn"):
         hpp, ec = propagation_h1(ham, L_bar)
-        B = half_step_propagator(hpp, tau)
+        B = half_step_propagator(hpp, tau) if B is None else B
     x = torch.as_tensor(x, dtype=RT)
     f, f_raw = force_bias(ham, psi, tau, L_bar)                     # Eq. force_shift
     c = x.to(CT) - f
     A = field_matrix(ham, c, tau)                                   # Eq. heffTOT
-    psi_new = split2_propagate(B, A, psi, method, k, ham.spins())   # Eq. psiupdate
+    psi_new = propagate(propagator, B, hpp, A, psi, tau, method, k, ham.spins())   # Eq. psiupdate
     logovl_new = log_overlap(ham, psi_new)
     log_s = -tau * ec - 1j * math.sqrt(tau) * (c @ L_bar.to(CT))
     log_ratio = logovl_new - logovl + log_s

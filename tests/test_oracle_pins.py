@@ -177,6 +177,79 @@ def test_block_krylov_equivariance_and_convergence():
     assert errs[-1] < 1e-12 * float(ref.norm())   # k = 4 = N / n: exact
 
 
+# ---------------------------------------------------------------- other propagators (Sec. III)
+def _sym(g, N, scale):
+    X = torch.randn(N, N, dtype=RT, generator=g)
+    return scale * 0.5 * (X + X.T)
+
+
+def test_split1_error_is_half_the_commutator():
+    """Split-1 (Sec. III): e^{-tau H1} e^{-tau M} = e^{-tau (H1 + M)} + tau^2/2 [H1, M]
+    + O(tau^3), the paper's leading term E_S1 = [H1, H2]/2 for a deterministic
+    interaction."""
+    g = torch.Generator().manual_seed(51)
+    N = 6
+    H1, M = _sym(g, N, 1.0), _sym(g, N, 1.0)
+    I = torch.eye(N, dtype=CT)
+    comm = 0.5 * (H1 @ M - M @ H1).to(CT)
+    for tau in (1e-2, 1e-3):
+        B = R.half_step_propagator(H1, tau)
+        U1 = R.split1_propagate(B, (-tau * M).to(CT), I, "exact", 0)
+        U = torch.linalg.matrix_exp((-tau * (H1 + M)).to(CT))
+        err = float(((U1 - U) / tau ** 2 - comm).norm() / comm.norm())
+        assert err < 20 * tau, (tau, err)
+
+
+def test_taylor_propagator_expands_the_whole_exponent():
+    """The Taylor propagator expands e^{-tau (h'' + M)} directly: order 1 is
+    1 - tau (h'' + M), a high order is the exponential."""
+    g = torch.Generator().manual_seed(52)
+    N, tau = 6, 0.1
+    H1, M = _sym(g, N, 1.0), _sym(g, N, 1.0)
+    psi = torch.randn(N, 3, dtype=RT, generator=g).to(CT)
+    A = (-tau * M).to(CT)
+    one = R.taylor_propagate(H1, A, psi, tau, 1)
+    assert torch.allclose(one, psi - tau * ((H1 + M).to(CT) @ psi), rtol=1e-14, atol=1e-14)
+    ref = torch.linalg.matrix_exp((-tau * (H1 + M)).to(CT)) @ psi
+    assert torch.allclose(R.taylor_propagate(H1, A, psi, tau, 25), ref, rtol=1e-13, atol=1e-14)
+
+
+def test_crank_nicolson_pade_error():
+    """Crank-Nicolson (Sec. III) is the (1,1) Pade approximant of e^{-tau H}:
+    U_CN - e^{-tau H} = -(tau H)^3 / 12 + O(tau^4) for a deterministic H = h'' + M."""
+    g = torch.Generator().manual_seed(53)
+    N = 5
+    H1, M = _sym(g, N, 1.0), _sym(g, N, 1.0)
+    H = (H1 + M).to(CT)
+    I = torch.eye(N, dtype=CT)
+    lead = -(H @ H @ H) / 12.0
+    for tau in (1e-2, 1e-3):
+        Ucn = R.crank_nicolson_propagate(H1, (-tau * M).to(CT), I, tau)
+        U = torch.linalg.matrix_exp(-tau * H)
+        err = float(((Ucn - U) / tau ** 3 - lead).norm() / lead.norm())
+        assert err < 20 * tau, (tau, err)
+
+
+def test_propagators_agree_without_interaction():
+    """At Psi_T with zero fields the force bias and the field vanish (A = 0):
+    Split-1 and Split-2 both give e^{-tau h''} Psi_T, the Taylor propagator of
+    high order too, and Crank-Nicolson to O(tau^3)."""
+    s, ham = _small_ham()
+    tau = 0.05
+    psi, lo, W = R.init_walkers(ham, 2)
+    x = torch.zeros(2, ham.G, dtype=RT)
+    out = {p: R.step(ham, psi, lo, W, x, tau, -5.0, method="exact", k=30, propagator=p)
+           for p in ("split2", "split1", "taylor", "cn")}
+    hpp, _ = R.propagation_h1(ham)
+    ref = torch.linalg.matrix_exp((-tau * hpp).to(CT)) @ ham.trial.to(CT)
+    for p in ("split2", "split1", "taylor"):
+        assert torch.allclose(out[p][0][0], ref, rtol=1e-12, atol=1e-13), p
+    d = float((out["cn"][0][0] - ref).norm() / ref.norm())
+    assert d < tau ** 3 * float(torch.linalg.matrix_norm(hpp, 2)) ** 3, d
+    with pytest.raises(ValueError):
+        R.step(ham, psi, lo, W, x, tau, -5.0, propagator="split3")
+
+
 # ---------------------------------------------------------------- propagator
 def test_half_step_squares_to_one_body_exponential():
     s, ham = _small_ham()
