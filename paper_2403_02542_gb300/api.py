@@ -110,13 +110,14 @@ class Context:
     def step(self, w: WalkerSet, fields: torch.Tensor, tau: float, e0: float,
              expm: str = "krylov", order: int = 10, reortho: bool = False,
              measure: bool = False, e_loc: torch.Tensor | None = None,
-             e_mix: torch.Tensor | None = None, reuse_bias: bool = False):
+             e_mix: torch.Tensor | None = None, reuse_bias: bool = False, propagator: str = "split2"):
         """One walker step (afqmc_step).  fields: device [Nw, G] float64.
         reuse_bias: take the force bias from the previous measurement of the
-        same, unchanged walkers (see afqmc_step_params in the header)."""
+        same, unchanged walkers (see afqmc_step_params in the header).
+        propagator: "split2" (default) or "split1"."""
         assert fields.dtype == torch.float64 and fields.is_cuda and fields.is_contiguous()
         self._bind_stream()
-        p = L.StepParams(float(tau), float(e0), L.AFQMC_SPLIT2,
+        p = L.StepParams(float(tau), float(e0), {"split2": L.AFQMC_SPLIT2, "split1": L.AFQMC_SPLIT1}[propagator],
                          {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV, "bkrylov": L.AFQMC_EXPM_BLOCK_KRYLOV}[expm],
                          int(order), int(bool(reortho)), int(bool(measure)), int(bool(reuse_bias)))
         cw = w.c_struct()
@@ -257,14 +258,16 @@ class Batch:
         self._h = h
 
     def step(self, walker_sets, fields, tau, e0, expm="krylov", order=10, reortho=False, measure=False,
-             e_loc=None, e_mix=None, stream: torch.cuda.Stream | None = None, reuse_bias=False):
+             e_loc=None, e_mix=None, stream: torch.cuda.Stream | None = None, reuse_bias=False,
+             propagator="split2"):
         n = len(self.contexts)
         taus = tau if isinstance(tau, (list, tuple)) else [tau] * n
         e0s = e0 if isinstance(e0, (list, tuple)) else [e0] * n
         ws = (L.Walkers * n)(*[w.c_struct() for w in walker_sets])
         fp = (ctypes.c_void_p * n)(*[f.data_ptr() for f in fields])
         ex = {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV, "bkrylov": L.AFQMC_EXPM_BLOCK_KRYLOV}[expm]
-        ps = (L.StepParams * n)(*[L.StepParams(float(taus[i]), float(e0s[i]), L.AFQMC_SPLIT2, ex, int(order),
+        pr = {"split2": L.AFQMC_SPLIT2, "split1": L.AFQMC_SPLIT1}[propagator]
+        ps = (L.StepParams * n)(*[L.StepParams(float(taus[i]), float(e0s[i]), pr, ex, int(order),
                                                int(bool(reortho)), int(bool(measure)), int(bool(reuse_bias)))
                                   for i in range(n)])
         el = (ctypes.c_void_p * n)(*[None if e_loc is None or e_loc[i] is None else e_loc[i].data_ptr()

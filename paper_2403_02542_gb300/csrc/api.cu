@@ -491,9 +491,14 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
   } else {
     PK(AFQMC_K_FIELD, gemm<R>(site_args<R>(c, SITE_FIELD, Nw, st, ws.c, ws.A), false, EPI_STORE, s));
   }
-  // psi_b = B psi
-  PK(AFQMC_K_HALFSTEP, half(w->psi, ws.psi_b));
-  c->launches += 6;
+  // psi_b = B psi (Split-2); Split-1 starts the exponential from psi itself
+  const bool split1 = p->propagator == AFQMC_SPLIT1;
+  if (split1) {
+    CKW(cudaMemcpyAsync(ws.psi_b, w->psi, (size_t)Nw * per * cs, cudaMemcpyDeviceToDevice, s), "psi copy");
+  } else {
+    PK(AFQMC_K_HALFSTEP, half(w->psi, ws.psi_b));
+  }
+  c->launches += split1 ? 5 : 6;
 
   // per-walker products with A_w (tensor cores for complex64 walkers)
   GemmArgs ga = site_args<R>(c, SITE_EXPM, Nw, st, nullptr, nullptr);
@@ -548,8 +553,14 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
     PK(AFQMC_K_OTHER, launch_krylov_finish<R>(c, Nw, k, s));
     c->launches += 2 + 2 * k + 2;
   }
-  // psi_new = B acc
-  PK(AFQMC_K_HALFSTEP, half(ws.acc, ws.psi_new));
+  // psi_new = B acc (Split-2); B B acc = e^{-tau h''} acc (Split-1)
+  if (split1) {
+    PK(AFQMC_K_HALFSTEP, half(ws.acc, ws.term1));
+    PK(AFQMC_K_HALFSTEP, half(ws.term1, ws.psi_new));
+    c->launches += 1;
+  } else {
+    PK(AFQMC_K_HALFSTEP, half(ws.acc, ws.psi_new));
+  }
   // new overlap (and Theta for the local energy when no re-orthonormalisation
   // follows), weights, commit
   void* th_new = (p->measure && !p->reortho) ? ws.theta : nullptr;
@@ -1145,7 +1156,7 @@ afqmc_status afqmc_step(afqmc_ctx* c, const afqmc_walkers* w, const double* fiel
   if (!p || (!fields && w->n_walkers > 0)) return AFQMC_EINVAL;
   if (!std::isfinite(p->tau) || !std::isfinite(p->e0)) return AFQMC_EDOM;
   if (!(p->tau > 0.0)) return AFQMC_EINVAL;
-  if (p->propagator != AFQMC_SPLIT2) return AFQMC_ENOTSUP;
+  if (p->propagator != AFQMC_SPLIT2 && p->propagator != AFQMC_SPLIT1) return AFQMC_ENOTSUP;
   if (p->expm == AFQMC_EXPM_TAYLOR) {
     if (p->order < 0 || p->order > 64) return AFQMC_ENOTSUP;
   } else if (p->expm == AFQMC_EXPM_KRYLOV) {
@@ -1413,7 +1424,7 @@ static afqmc_status step_checks(afqmc_ctx* c, const afqmc_walkers* w, const doub
   if (!p || (!fields && w->n_walkers > 0)) return AFQMC_EINVAL;
   if (!std::isfinite(p->tau) || !std::isfinite(p->e0)) return AFQMC_EDOM;
   if (!(p->tau > 0.0)) return AFQMC_EINVAL;
-  if (p->propagator != AFQMC_SPLIT2) return AFQMC_ENOTSUP;
+  if (p->propagator != AFQMC_SPLIT2 && p->propagator != AFQMC_SPLIT1) return AFQMC_ENOTSUP;
   if (p->expm == AFQMC_EXPM_TAYLOR) {
     if (p->order < 0 || p->order > 64) return AFQMC_ENOTSUP;
   } else if (p->expm == AFQMC_EXPM_KRYLOV) {

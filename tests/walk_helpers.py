@@ -31,7 +31,8 @@ def near_ties(info, tau, e0, eps=1e-9):
 
 
 def oracle_walk(sys_, nw, steps, tau, e0, expm, order, reortho_every, seed, dead=(),
-                trial=None, na=None, nb=None, psi0=None, lo0=None, W0=None, field_fn=None):
+                trial=None, na=None, nb=None, psi0=None, lo0=None, W0=None, field_fn=None,
+                propagator="split2"):
     ham, Lbar, ec, B = oracle_setup(sys_, tau, trial, na, nb)
     if psi0 is None:
         psi, lo, W = R.init_walkers(ham, nw)
@@ -45,7 +46,7 @@ def oracle_walk(sys_, nw, steps, tau, e0, expm, order, reortho_every, seed, dead
         x = make_fields(seed, k, nw, ham.G) if field_fn is None else field_fn(k)
         reo = reortho_every > 0 and (k + 1) % reortho_every == 0
         psi, lo, W, info = R.step(ham, psi, lo, W, x, tau, e0, method=expm, k=order, reortho=reo,
-                                  B=B, L_bar=Lbar, ec=ec)
+                                  B=B, L_bar=Lbar, ec=ec, propagator=propagator)
         ties += near_ties(info, tau, e0)
         El = R.local_energy(ham, psi)
         Ecap = R.energy_window(El, e0, tau, ham.na + ham.nb)
@@ -56,7 +57,7 @@ def oracle_walk(sys_, nw, steps, tau, e0, expm, order, reortho_every, seed, dead
 
 
 def gpu_walk(ctx, nw, steps, tau, e0, expm, order, reortho_every, seed, dead=(), record=None,
-             state=None, field_fn=None, reuse_bias=False):
+             state=None, field_fn=None, reuse_bias=False, propagator="split2"):
     """record: set of step indices to copy back (default: all)."""
     w = ctx.new_walkers(nw)
     if state is None:
@@ -76,7 +77,7 @@ def gpu_walk(ctx, nw, steps, tau, e0, expm, order, reortho_every, seed, dead=(),
         x = torch.as_tensor(np.ascontiguousarray(x), device=ctx.device)
         reo = reortho_every > 0 and (k + 1) % reortho_every == 0
         ctx.step(w, x, tau, e0, expm=expm, order=order, reortho=reo, measure=True,
-                 e_loc=e_loc, e_mix=e_mix, reuse_bias=reuse_bias)
+                 e_loc=e_loc, e_mix=e_mix, reuse_bias=reuse_bias, propagator=propagator)
         if record is None or k in record:
             torch.cuda.synchronize()
             out.append(dict(k=k, psi=w.psi.cpu().to(torch.complex128).transpose(1, 2).contiguous(),
