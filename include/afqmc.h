@@ -61,9 +61,9 @@ typedef enum {
   AFQMC_ESTATE = 6    /* call out of order (e.g. a step before afqmc_set_tau)   */
 } afqmc_status;
 
-/* Propagators (Sec. III): Split-2, the paper's recommended one, and Split-1.  The
- * Taylor and Crank-Nicolson propagators are not built (AFQMC_ENOTSUP). */
-enum { AFQMC_SPLIT2 = 0, AFQMC_SPLIT1 = 1 };
+/* Propagators (Sec. III): Split-2, the paper's recommended one, Split-1 and the
+ * Taylor propagator.  Crank-Nicolson is not built. */
+enum { AFQMC_SPLIT2 = 0, AFQMC_SPLIT1 = 1, AFQMC_TAYLORPROP = 2 };
 
 /* Action of the one-body exponential (Sec. IV). */
 enum { AFQMC_EXPM_TAYLOR = 0, AFQMC_EXPM_KRYLOV = 1, AFQMC_EXPM_BLOCK_KRYLOV = 2 };
@@ -102,8 +102,11 @@ typedef struct {
  *   tau         time step (> 0)
  *   e0          best estimate of the ground-state energy E_0 (Eq. imag_prop)
  *   propagator  AFQMC_SPLIT2 (Sec. III.B: e^{-tau H1/2} e^{A} e^{-tau H1/2}) or
- *               AFQMC_SPLIT1 (Sec. III: e^{-tau H1} e^{A}, the exponential first,
- *               then the one-body step applied as two half steps)
+ *               AFQMC_SPLIT1 (Sec. III.A: e^{-tau H1} e^{A}, the exponential first,
+ *               then the one-body step applied as two half steps) or
+ *               AFQMC_TAYLORPROP (Sec. III.C: the Taylor series of order `order` of
+ *               e^{A - tau h''} applied to the walkers, no splitting; expm must be
+ *               AFQMC_EXPM_TAYLOR, else AFQMC_ENOTSUP); other values: AFQMC_ENOTSUP
  *   expm        AFQMC_EXPM_TAYLOR (order = Taylor order k >= 0),
  *               AFQMC_EXPM_KRYLOV (order = Krylov dimension 1 <= k <= 32, one
  *               Krylov space per orbital column, Eq. krylov) or

@@ -12,6 +12,9 @@ import torch
 
 from . import _lib as L
 
+# walker updates of Sec. III built in the library
+PROPAGATORS = {"split2": L.AFQMC_SPLIT2, "split1": L.AFQMC_SPLIT1, "taylor": L.AFQMC_TAYLORPROP}
+
 
 def _ptr(t: torch.Tensor | None) -> int | None:
     return None if t is None else t.data_ptr()
@@ -114,10 +117,11 @@ class Context:
         """One walker step (afqmc_step).  fields: device [Nw, G] float64.
         reuse_bias: take the force bias from the previous measurement of the
         same, unchanged walkers (see afqmc_step_params in the header).
-        propagator: "split2" (default) or "split1"."""
+        propagator: "split2" (default), "split1" or "taylor" (the Taylor
+        propagator; expm must then be "taylor")."""
         assert fields.dtype == torch.float64 and fields.is_cuda and fields.is_contiguous()
         self._bind_stream()
-        p = L.StepParams(float(tau), float(e0), {"split2": L.AFQMC_SPLIT2, "split1": L.AFQMC_SPLIT1}[propagator],
+        p = L.StepParams(float(tau), float(e0), PROPAGATORS[propagator],
                          {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV, "bkrylov": L.AFQMC_EXPM_BLOCK_KRYLOV}[expm],
                          int(order), int(bool(reortho)), int(bool(measure)), int(bool(reuse_bias)))
         cw = w.c_struct()
@@ -266,7 +270,7 @@ class Batch:
         ws = (L.Walkers * n)(*[w.c_struct() for w in walker_sets])
         fp = (ctypes.c_void_p * n)(*[f.data_ptr() for f in fields])
         ex = {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV, "bkrylov": L.AFQMC_EXPM_BLOCK_KRYLOV}[expm]
-        pr = {"split2": L.AFQMC_SPLIT2, "split1": L.AFQMC_SPLIT1}[propagator]
+        pr = PROPAGATORS[propagator]
         ps = (L.StepParams * n)(*[L.StepParams(float(taus[i]), float(e0s[i]), pr, ex, int(order),
                                                int(bool(reortho)), int(bool(measure)), int(bool(reuse_bias)))
                                   for i in range(n)])

@@ -248,7 +248,7 @@ static void ctx_free(afqmc_ctx* c) {
   ws_free(c->ws);
   void* ptrs[] = {c->d_L, c->d_Lh,  c->d_trial, c->d_hhalf,    c->d_Lbar,     c->d_thT,
                   c->d_B, c->f_L,   c->f_Lh,    c->f_B,        c->f_trial,    c->d_bias_key,
-                  c->d_bias_skip};
+                  c->d_bias_skip, c->d_hpp};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   free(c->h_evals);
@@ -266,6 +266,7 @@ static afqmc_status ctx_setup(afqmc_ctx* c, const double* h1, const double* L, c
   CK(cudaMalloc(&c->d_hhalf, (size_t)nc * N * sizeof(double)));
   CK(cudaMalloc(&c->d_Lbar, (size_t)G * sizeof(double)));
   CK(cudaMalloc(&c->d_B, NN * sizeof(double)));
+  CK(cudaMalloc(&c->d_hpp, NN * sizeof(double)));
   CK(cudaMalloc(&c->d_bias_key, 2 * sizeof(unsigned long long)));
   CK(cudaMalloc(&c->d_bias_skip, sizeof(int)));
   CK(cudaMemsetAsync(c->d_bias_key, 0, 2 * sizeof(unsigned long long), s));
@@ -344,6 +345,8 @@ static afqmc_status ctx_setup(afqmc_ctx* c, const double* h1, const double* L, c
       hpp[(size_t)p * N + q] = hpp[(size_t)q * N + p] = v;
     }
   c->ec_prime = c->e_const - 0.5 * lb2;
+  CK(cudaMemcpyAsync(c->d_hpp, hpp.data(), NN * sizeof(double), cudaMemcpyHostToDevice, s));
+  CK(cudaStreamSynchronize(s));  // hpp is a host temporary
   c->h_evals = (double*)malloc(N * sizeof(double));
   c->h_evecs = (double*)malloc(NN * sizeof(double));
   if (!c->h_evals || !c->h_evecs) return AFQMC_ENOMEM;
@@ -484,25 +487,31 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
   gfb.skip = skip;
   PK(AFQMC_K_FORCEBIAS, gemm<R>(gfb, false, EPI_STORE, s));
   PK(AFQMC_K_OTHER, launch_bias_finalize<R>(c, Nw, x, st, s, nullptr, skip));
-  // A_w = i sqrt(tau) sum_g c_wg L_g (Eq. heffTOT); complex64 walkers: on the tensor cores
-  if (std::is_same<R, float>::value && c->tg.ok) {
+  // A_w = i sqrt(tau) sum_g c_wg L_g (Eq. heffTOT); complex64 walkers: on the
+  // tensor cores, except for the Taylor propagator, which needs A_w - tau h''
+  // in memory (the field GEMM, then the shift)
+  const bool split1 = p->propagator == AFQMC_SPLIT1, tprop = p->propagator == AFQMC_TAYLORPROP;
+  if (std::is_same<R, float>::value && c->tg.ok && !tprop) {
     PK(AFQMC_K_FIELD, tc_field_launch(c, Nw, st, s));
     c->launches += 1;
   } else {
     PK(AFQMC_K_FIELD, gemm<R>(site_args<R>(c, SITE_FIELD, Nw, st, ws.c, ws.A), false, EPI_STORE, s));
   }
-  // psi_b = B psi (Split-2); Split-1 starts the exponential from psi itself
-  const bool split1 = p->propagator == AFQMC_SPLIT1;
-  if (split1) {
+  if (tprop) {
+    PK(AFQMC_K_FIELD, launch_shift_field<R>(c, Nw, p->tau, s));
+    c->launches += 1;
+  }
+  // psi_b = B psi (Split-2); Split-1 and the Taylor propagator start from psi itself
+  if (split1 || tprop) {
     CKW(cudaMemcpyAsync(ws.psi_b, w->psi, (size_t)Nw * per * cs, cudaMemcpyDeviceToDevice, s), "psi copy");
   } else {
     PK(AFQMC_K_HALFSTEP, half(w->psi, ws.psi_b));
   }
-  c->launches += split1 ? 5 : 6;
+  c->launches += (split1 || tprop) ? 5 : 6;
 
   // per-walker products with A_w (tensor cores for complex64 walkers)
   GemmArgs ga = site_args<R>(c, SITE_EXPM, Nw, st, nullptr, nullptr);
-  const bool tc_av = std::is_same<R, float>::value && c->tg.av_ok;
+  const bool tc_av = std::is_same<R, float>::value && c->tg.av_ok && !tprop;
   auto av = [&](const void* in, void* out, void* add, double alpha) -> cudaError_t {
     if (tc_av) return tc_av_launch(c, Nw, in, per, out, add, per, alpha, s);
     ga.B = in; ga.C = out; ga.D = add;
@@ -553,8 +562,12 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
     PK(AFQMC_K_OTHER, launch_krylov_finish<R>(c, Nw, k, s));
     c->launches += 2 + 2 * k + 2;
   }
-  // psi_new = B acc (Split-2); B B acc = e^{-tau h''} acc (Split-1)
-  if (split1) {
+  // psi_new = B acc (Split-2); B B acc = e^{-tau h''} acc (Split-1); acc itself
+  // (the Taylor propagator)
+  if (tprop) {
+    CKW(cudaMemcpyAsync(ws.psi_new, ws.acc, (size_t)Nw * per * cs, cudaMemcpyDeviceToDevice, s), "acc copy");
+    c->launches -= 1;
+  } else if (split1) {
     PK(AFQMC_K_HALFSTEP, half(ws.acc, ws.term1));
     PK(AFQMC_K_HALFSTEP, half(ws.term1, ws.psi_new));
     c->launches += 1;
@@ -1156,7 +1169,9 @@ afqmc_status afqmc_step(afqmc_ctx* c, const afqmc_walkers* w, const double* fiel
   if (!p || (!fields && w->n_walkers > 0)) return AFQMC_EINVAL;
   if (!std::isfinite(p->tau) || !std::isfinite(p->e0)) return AFQMC_EDOM;
   if (!(p->tau > 0.0)) return AFQMC_EINVAL;
-  if (p->propagator != AFQMC_SPLIT2 && p->propagator != AFQMC_SPLIT1) return AFQMC_ENOTSUP;
+  if (p->propagator != AFQMC_SPLIT2 && p->propagator != AFQMC_SPLIT1 && p->propagator != AFQMC_TAYLORPROP)
+    return AFQMC_ENOTSUP;
+  if (p->propagator == AFQMC_TAYLORPROP && p->expm != AFQMC_EXPM_TAYLOR) return AFQMC_ENOTSUP;
   if (p->expm == AFQMC_EXPM_TAYLOR) {
     if (p->order < 0 || p->order > 64) return AFQMC_ENOTSUP;
   } else if (p->expm == AFQMC_EXPM_KRYLOV) {
@@ -1424,7 +1439,9 @@ static afqmc_status step_checks(afqmc_ctx* c, const afqmc_walkers* w, const doub
   if (!p || (!fields && w->n_walkers > 0)) return AFQMC_EINVAL;
   if (!std::isfinite(p->tau) || !std::isfinite(p->e0)) return AFQMC_EDOM;
   if (!(p->tau > 0.0)) return AFQMC_EINVAL;
-  if (p->propagator != AFQMC_SPLIT2 && p->propagator != AFQMC_SPLIT1) return AFQMC_ENOTSUP;
+  if (p->propagator != AFQMC_SPLIT2 && p->propagator != AFQMC_SPLIT1 && p->propagator != AFQMC_TAYLORPROP)
+    return AFQMC_ENOTSUP;
+  if (p->propagator == AFQMC_TAYLORPROP && p->expm != AFQMC_EXPM_TAYLOR) return AFQMC_ENOTSUP;
   if (p->expm == AFQMC_EXPM_TAYLOR) {
     if (p->order < 0 || p->order > 64) return AFQMC_ENOTSUP;
   } else if (p->expm == AFQMC_EXPM_KRYLOV) {

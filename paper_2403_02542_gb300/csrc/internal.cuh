@@ -200,6 +200,7 @@ struct afqmc_ctx {
   unsigned long long* d_bias_key = nullptr;
   int* d_bias_skip = nullptr;
   double* d_B = nullptr;      // [N][N]
+  double* d_hpp = nullptr;    // [N][N]     h'' (the Taylor propagator's one-body part)
   // FP32 copies for mixed contexts
   float* f_L = nullptr;
   float* f_Lh = nullptr;
@@ -257,6 +258,9 @@ cudaError_t launch_bias_gate(const afqmc_ctx* c, const void* psi, int Nw, int op
 cudaError_t launch_bias_mark(const afqmc_ctx* c, const void* psi, int Nw, cudaStream_t s);
 template <typename R>
 cudaError_t launch_normA(const afqmc_ctx* c, int Nw, cudaStream_t s);
+// ws.A[w] -= tau h'' (real part) for Nw walkers: the Taylor propagator's exponent
+template <typename R>
+cudaError_t launch_shift_field(const afqmc_ctx* c, int Nw, double tau, cudaStream_t s);
 template <typename R>
 cudaError_t launch_krylov_init(const afqmc_ctx* c, int Nw, cudaStream_t s);
 template <typename R>

@@ -378,6 +378,16 @@ __global__ void to_float_kernel(const double* __restrict__ a, float* __restrict_
     b[e] = (float)a[e];
 }
 
+// A_w <- A_w - tau h'' for every walker: the exponent -tau H_eff = A - tau h''
+// of the Taylor propagator (Sec. III); h'' is real and shared by the walkers,
+// so only the real parts change
+template <typename R>
+__global__ void shift_field_kernel(typename C2<R>::t* __restrict__ A, const double* __restrict__ hpp, double tau,
+                                   size_t NN, size_t total) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
+    A[e].x = (R)((double)A[e].x - tau * hpp[e % NN]);
+}
+
 inline int grid_for(size_t n) {
   size_t b = (n + 255) / 256;
   return (int)(b > 152 * 64 ? 152 * 64 : (b == 0 ? 1 : b));
@@ -551,7 +561,17 @@ cudaError_t launch_to_float(const double* a, float* b, size_t n, cudaStream_t s)
   return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t launch_shift_field(const afqmc_ctx* c, int Nw, double tau, cudaStream_t s) {
+  const size_t NN = (size_t)c->N * c->N, total = (size_t)Nw * NN;
+  if (total == 0) return cudaSuccess;
+  shift_field_kernel<R><<<grid_for(total), 256, 0, s>>>(static_cast<typename C2<R>::t*>(c->ws.A), c->d_hpp, tau,
+                                                        NN, total);
+  return cudaGetLastError();
+}
+
 #define AFQ_INST(R)                                                                                         \
+  template cudaError_t launch_shift_field<R>(const afqmc_ctx*, int, double, cudaStream_t);                  \
   template cudaError_t launch_bias_finalize<R>(const afqmc_ctx*, int, const double*, double, cudaStream_t, uint8_t*, \
                                                const int*);                                                      \
   template cudaError_t launch_normA<R>(const afqmc_ctx*, int, cudaStream_t);                                \
