@@ -38,6 +38,10 @@ Readings of the paper used here (the paper is silent or ambiguous on them):
       modified Gram-Schmidt pass, the number of blocks is at most N // n, and
       the space is declared invariant at the first new block whose QR has a
       diagonal entry <= 1e-12 ||A||_F.
+  R23 The Chebyshev expansion (Sec. IV.B) is applied to A as printed, with
+      no rescaling of its spectrum into [-1, 1]: A is O(sqrt(tau)) small at
+      the paper's time steps, and the coefficients c_n = 2 I_n(1) fall off
+      like 1 / (2^n n!).
   R7  E_0 is a caller-supplied scalar.
   R8  Population control: comb with caller-supplied uniform u.
   R9  Threshold tests use the strict inequalities printed in Sec. V.
@@ -57,7 +61,7 @@ __all__ = [
     "Hamiltonian", "make_hamiltonian", "overlap", "greens_function",
     "log_overlap", "theta", "mean_field_shift", "mixed_L_expectation",
     "force_bias", "propagation_h1", "half_step_propagator", "field_matrix",
-    "taylor_action", "krylov_action", "block_krylov_action", "exact_action", "expm_action",
+    "taylor_action", "chebyshev_coefficients", "chebyshev_action", "krylov_action", "block_krylov_action", "exact_action", "expm_action",
     "split2_propagate", "split1_propagate", "taylor_propagate", "crank_nicolson_propagate", "propagate",
     "local_energy", "energy_window", "mixed_energy",
     "mgs_qr", "reorthonormalise", "weight_update", "step", "init_walkers",
@@ -207,6 +211,31 @@ def taylor_action(A, psi, k):
     return acc
 
 
+def chebyshev_coefficients(k):
+    """c_0 = J_0(i) and c_n = 2 i^n J_n(-i) for n = 1..k (Sec. IV.B), the
+    Bessel functions of the first kind at complex argument from scipy.special
+    (a library routine).  Returns a complex tensor [k+1]."""
+    from scipy.special import jv
+    c = [complex(jv(0, 1j))] + [2.0 * (1j ** n) * complex(jv(n, -1j)) for n in range(1, k + 1)]
+    return torch.tensor(c, dtype=CT)
+
+
+def chebyshev_action(A, psi, k):
+    """cheb_k{A, Psi} = sum_{n=0}^{k} c_n T_n(A) Psi (Sec. IV.B) with the
+    polynomials of Eq. chebpoly: T_0 = 1, T_1 = A, T_n = 2 A T_{n-1} - T_{n-2},
+    applied to Psi without rescaling A (reading R23)."""
+    c = chebyshev_coefficients(k)
+    acc = c[0] * psi
+    if k == 0:
+        return acc
+    t_prev, t_cur = psi, A @ psi
+    acc = acc + c[1] * t_cur
+    for n in range(2, k + 1):
+        t_prev, t_cur = t_cur, 2.0 * (A @ t_cur) - t_prev
+        acc = acc + c[n] * t_cur
+    return acc
+
+
 def _arnoldi_column(A, psi_col, k, normA):
     """Krylov approximation of e^A psi for one orbital vector (Eqs. krylovsub-krylov)."""
     N = A.shape[-1]
@@ -301,6 +330,8 @@ def expm_action(A, psi, method, k, spins=None):
         return krylov_action(A, psi, k)
     if method == "bkrylov":
         return block_krylov_action(A, psi, k, spins)
+    if method == "chebyshev":
+        return chebyshev_action(A, psi, k)
     if method == "exact":
         return exact_action(A, psi)
     raise ValueError(method)
@@ -313,14 +344,14 @@ def split2_propagate(B, A, psi, method, k, spins=None):
 
 
 def split1_propagate(B, A, psi, method, k, spins=None):
-    """U_S1 Psi = e^{-tau H1} e^{A} Psi (Sec. III, Split-1): the interaction
+    """U_S1 Psi = e^{-tau H1} e^{A} Psi (Sec. III.A, Split-1): the interaction
     exponential first, then the whole one-body step B B = e^{-tau h''}."""
     Bc = B.to(CT)
     return Bc @ (Bc @ expm_action(A, psi, method, k, spins))
 
 
 def taylor_propagate(hpp, A, psi, tau, k):
-    """U_T Psi = taylor_k{-tau Heff, Psi} with -tau Heff = A - tau h'' (Sec. III,
+    """U_T Psi = taylor_k{-tau Heff, Psi} with -tau Heff = A - tau h'' (Sec. III.C,
     Taylor propagator: the refactorised exponent expanded directly)."""
     return taylor_action(A - tau * hpp.to(CT), psi, k)
 

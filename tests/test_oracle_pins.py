@@ -53,6 +53,60 @@ def test_taylor_order_zero_and_one():
     assert torch.allclose(R.taylor_action(A, psi, 1), psi + A @ psi, atol=1e-15)
 
 
+def test_chebyshev_coefficients_are_the_modified_bessel_values():
+    """Sec. IV.B: J_0(i) = I_0(1) and 2 i^n J_n(-i) = 2 I_n(1), real; tabulated
+    I_0(1) = 1.266065878, I_1(1) = 0.565159104, I_2(1) = 0.135747670
+    (Abramowitz and Stegun, Table 9.8), and the power series
+    I_n(1) = sum_m (1/2)^{2m+n} / (m! (m+n)!)."""
+    c = R.chebyshev_coefficients(12)
+    assert float(c.imag.abs().max()) < 1e-15
+    assert abs(float(c[0].real) - 1.266065878) < 1e-9
+    assert abs(float(c[1].real) - 2 * 0.565159104) < 2e-9
+    assert abs(float(c[2].real) - 2 * 0.135747670) < 2e-9
+    for n in range(13):
+        i_n = sum(0.5 ** (2 * m + n) / (math.factorial(m) * math.factorial(m + n)) for m in range(30))
+        assert abs(float(c[n].real) - (i_n if n == 0 else 2 * i_n)) < 1e-15 * max(1.0, i_n)
+
+
+def test_chebyshev_series_of_a_scalar_is_the_exponential():
+    """sum_n c_n T_n(x) = e^x with T_n(cos t) = cos(n t) (Eq. chebpoly) for x in
+    [-1, 1], and at complex x by the action on a 1 x 1 matrix."""
+    for x in (-1.0, -0.3, 0.0, 0.5, 1.0):
+        t = math.acos(x)
+        c = R.chebyshev_coefficients(25).real
+        val = sum(float(c[n]) * math.cos(n * t) for n in range(26))
+        assert abs(val - math.exp(x)) < 1e-14
+        one = R.chebyshev_action(torch.tensor([[x]], dtype=CT), torch.ones(1, 1, dtype=CT), 25)
+        assert abs(complex(one[0, 0]) - math.exp(x)) < 1e-14
+    z = 0.2 + 0.7j
+    one = R.chebyshev_action(torch.tensor([[z]], dtype=CT), torch.ones(1, 1, dtype=CT), 30)
+    assert abs(complex(one[0, 0]) - complex(np.exp(z))) < 1e-14
+
+
+def test_chebyshev_action_converges_to_matrix_exp_within_its_bound():
+    """For Hermitian A with spectrum in [-1, 1], |T_n| <= 1 there, so
+    ||cheb_k - e^A psi|| <= sum_{n>k} |c_n| ||psi||; at high order it is
+    matrix_exp(A) psi for general complex A of small norm; at equal order it
+    beats the Taylor series on [-1, 1] (the smaller error prefactor of Sec. IV.B)."""
+    g = torch.Generator().manual_seed(7)
+    N = 8
+    H = _rand_c(g, N, N)
+    H = 0.5 * (H + H.conj().T)
+    H = H / float(torch.linalg.eigvalsh(H).abs().max())
+    psi = _rand_c(g, N, 3)
+    ref = torch.linalg.matrix_exp(H) @ psi
+    tail = R.chebyshev_coefficients(40).abs()
+    for k in (2, 4, 6, 8):
+        err = float(torch.linalg.vector_norm(R.chebyshev_action(H, psi, k) - ref))
+        bound = float(tail[k + 1:].sum()) * float(torch.linalg.vector_norm(psi))
+        assert err <= bound
+        assert err < float(torch.linalg.vector_norm(R.taylor_action(H, psi, k) - ref))
+    A = 0.3 * _rand_c(g, N, N)
+    got = R.chebyshev_action(A, psi, 30)
+    want = torch.linalg.matrix_exp(A) @ psi
+    assert float((got - want).abs().max()) < 1e-13
+
+
 def test_exact_action_matches_matrix_exp():
     g = torch.Generator().manual_seed(3)
     A = _rand_c(g, 7, 7)
