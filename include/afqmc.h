@@ -66,7 +66,7 @@ typedef enum {
 enum { AFQMC_SPLIT2 = 0, AFQMC_SPLIT1 = 1, AFQMC_TAYLORPROP = 2 };
 
 /* Action of the one-body exponential (Sec. IV). */
-enum { AFQMC_EXPM_TAYLOR = 0, AFQMC_EXPM_KRYLOV = 1, AFQMC_EXPM_BLOCK_KRYLOV = 2 };
+enum { AFQMC_EXPM_TAYLOR = 0, AFQMC_EXPM_KRYLOV = 1, AFQMC_EXPM_BLOCK_KRYLOV = 2, AFQMC_EXPM_CHEBYSHEV = 3 };
 
 /* Arithmetic of a context.
  * AFQMC_FP64:  complex128 walkers, every step in FP64.
@@ -109,7 +109,11 @@ typedef struct {
  *               AFQMC_EXPM_TAYLOR, else AFQMC_ENOTSUP); other values: AFQMC_ENOTSUP
  *   expm        AFQMC_EXPM_TAYLOR (order = Taylor order k >= 0),
  *               AFQMC_EXPM_KRYLOV (order = Krylov dimension 1 <= k <= 32, one
- *               Krylov space per orbital column, Eq. krylov) or
+ *               Krylov space per orbital column, Eq. krylov),
+ *               AFQMC_EXPM_CHEBYSHEV (order = expansion order 0 <= k <= 64,
+ *               Sec. IV.B: sum_n c_n T_n(A) Psi with c_0 = I_0(1),
+ *               c_n = 2 I_n(1) and the recurrence of Eq. chebpoly, A not
+ *               rescaled),
  *               AFQMC_EXPM_BLOCK_KRYLOV (order = number of blocks 1 <= k <= 16,
  *               Eq. bkrylov: per walker and spin, QR of the n orbitals, block
  *               Arnoldi with modified Gram-Schmidt, e^{A_k} E_n R of the

@@ -14,6 +14,9 @@ from . import _lib as L
 
 # walker updates of Sec. III built in the library
 PROPAGATORS = {"split2": L.AFQMC_SPLIT2, "split1": L.AFQMC_SPLIT1, "taylor": L.AFQMC_TAYLORPROP}
+# actions of the one-body exponential of Sec. IV built in the library
+EXPMS = {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV, "bkrylov": L.AFQMC_EXPM_BLOCK_KRYLOV,
+         "chebyshev": L.AFQMC_EXPM_CHEBYSHEV}
 
 
 def _ptr(t: torch.Tensor | None) -> int | None:
@@ -122,7 +125,7 @@ class Context:
         assert fields.dtype == torch.float64 and fields.is_cuda and fields.is_contiguous()
         self._bind_stream()
         p = L.StepParams(float(tau), float(e0), PROPAGATORS[propagator],
-                         {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV, "bkrylov": L.AFQMC_EXPM_BLOCK_KRYLOV}[expm],
+                         EXPMS[expm],
                          int(order), int(bool(reortho)), int(bool(measure)), int(bool(reuse_bias)))
         cw = w.c_struct()
         L.check(L.lib().afqmc_step(self._h, ctypes.byref(cw), fields.data_ptr(), ctypes.byref(p),
@@ -269,7 +272,7 @@ class Batch:
         e0s = e0 if isinstance(e0, (list, tuple)) else [e0] * n
         ws = (L.Walkers * n)(*[w.c_struct() for w in walker_sets])
         fp = (ctypes.c_void_p * n)(*[f.data_ptr() for f in fields])
-        ex = {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV, "bkrylov": L.AFQMC_EXPM_BLOCK_KRYLOV}[expm]
+        ex = EXPMS[expm]
         pr = PROPAGATORS[propagator]
         ps = (L.StepParams * n)(*[L.StepParams(float(taus[i]), float(e0s[i]), pr, ex, int(order),
                                                int(bool(reortho)), int(bool(measure)), int(bool(reuse_bias)))

@@ -443,6 +443,20 @@ static GemmArgs site_args(const afqmc_ctx* c, int site, int Nw, double sqrt_tau,
   return g;
 }
 
+// Chebyshev coefficient c_n of e^x (Sec. IV.B): c_0 = J_0(i) = I_0(1) and
+// c_n = 2 i^n J_n(-i) = 2 I_n(1), with the modified Bessel function from its
+// power series I_n(1) = sum_m (1/2)^{2m+n} / (m! (m+n)!)
+static double cheb_coef(int n) {
+  double term = 1.0;
+  for (int j = 1; j <= n; ++j) term *= 0.5 / j;  // (1/2)^n / n!
+  double sum = 0.0;
+  for (int m = 0; m < 40 && term > 1e-18 * sum; ++m) {
+    sum += term;
+    term *= 0.25 / ((m + 1.0) * (m + 1.0 + n));
+  }
+  return n == 0 ? sum : 2.0 * sum;
+}
+
 // Blocks of the block-Krylov layout for order k: room for min(k, N / n)
 // blocks of either spin (at most N rows of A_k).
 static int bk_blocks(const afqmc_ctx* c, int k) {
@@ -527,6 +541,26 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
       cur = nxt;
     }
     c->launches += p->order * (tc_av ? 2 : 1);
+  } else if (p->expm == AFQMC_EXPM_CHEBYSHEV) {
+    // Chebyshev (Eq. chebpoly): T_0 Psi = psi_b, T_1 Psi = A psi_b, then
+    // T_n Psi = 2 A T_{n-1} Psi - T_{n-2} Psi in place of T_{n-2} Psi (the
+    // product goes to psi_new, free until the last half step), acc = sum c_n T_n Psi
+    const int k = p->order;
+    if (k == 0) {
+      PK(AFQMC_K_OTHER, launch_cheb_step<R>(c, Nw, ws.psi_b, ws.psi_b, ws.acc, cheb_coef(0), 0.0, 1, s));
+      c->launches += 1;
+    } else {
+      PK(AFQMC_K_EXPM, av(ws.psi_b, ws.term0, nullptr, 1.0));
+      PK(AFQMC_K_OTHER, launch_cheb_step<R>(c, Nw, ws.term0, ws.psi_b, ws.acc, cheb_coef(0), cheb_coef(1), 1, s));
+      void* prev = ws.psi_b;
+      void* cur = ws.term0;
+      for (int n = 2; n <= k; ++n) {
+        PK(AFQMC_K_EXPM, av(cur, ws.psi_new, nullptr, 2.0));
+        PK(AFQMC_K_OTHER, launch_cheb_step<R>(c, Nw, ws.psi_new, prev, ws.acc, 0.0, cheb_coef(n), 0, s));
+        std::swap(prev, cur);
+      }
+      c->launches += k * ((tc_av ? 2 : 1) + 1);
+    }
   } else if (p->expm == AFQMC_EXPM_BLOCK_KRYLOV) {
     // block Krylov (Eq. bkrylov): QR, then per block the products A B_j and
     // one block Arnoldi step, then e^{A_k} E_n R and B_k F into acc
@@ -1172,7 +1206,7 @@ afqmc_status afqmc_step(afqmc_ctx* c, const afqmc_walkers* w, const double* fiel
   if (p->propagator != AFQMC_SPLIT2 && p->propagator != AFQMC_SPLIT1 && p->propagator != AFQMC_TAYLORPROP)
     return AFQMC_ENOTSUP;
   if (p->propagator == AFQMC_TAYLORPROP && p->expm != AFQMC_EXPM_TAYLOR) return AFQMC_ENOTSUP;
-  if (p->expm == AFQMC_EXPM_TAYLOR) {
+  if (p->expm == AFQMC_EXPM_TAYLOR || p->expm == AFQMC_EXPM_CHEBYSHEV) {
     if (p->order < 0 || p->order > 64) return AFQMC_ENOTSUP;
   } else if (p->expm == AFQMC_EXPM_KRYLOV) {
     if (p->order < 1 || p->order > 32) return AFQMC_ENOTSUP;
@@ -1442,7 +1476,7 @@ static afqmc_status step_checks(afqmc_ctx* c, const afqmc_walkers* w, const doub
   if (p->propagator != AFQMC_SPLIT2 && p->propagator != AFQMC_SPLIT1 && p->propagator != AFQMC_TAYLORPROP)
     return AFQMC_ENOTSUP;
   if (p->propagator == AFQMC_TAYLORPROP && p->expm != AFQMC_EXPM_TAYLOR) return AFQMC_ENOTSUP;
-  if (p->expm == AFQMC_EXPM_TAYLOR) {
+  if (p->expm == AFQMC_EXPM_TAYLOR || p->expm == AFQMC_EXPM_CHEBYSHEV) {
     if (p->order < 0 || p->order > 64) return AFQMC_ENOTSUP;
   } else if (p->expm == AFQMC_EXPM_KRYLOV) {
     if (p->order < 1 || p->order > 32) return AFQMC_ENOTSUP;

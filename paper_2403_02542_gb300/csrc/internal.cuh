@@ -258,6 +258,11 @@ cudaError_t launch_bias_gate(const afqmc_ctx* c, const void* psi, int Nw, int op
 cudaError_t launch_bias_mark(const afqmc_ctx* c, const void* psi, int Nw, cudaStream_t s);
 template <typename R>
 cudaError_t launch_normA(const afqmc_ctx* c, int Nw, cudaStream_t s);
+// One step of the Chebyshev recurrence on Nw walkers' [nc][N] vectors (see
+// cheb_step_kernel in k_energy.cu)
+template <typename R>
+cudaError_t launch_cheb_step(const afqmc_ctx* c, int Nw, const void* prod, void* t, void* acc, double a, double b,
+                             int first, cudaStream_t s);
 // ws.A[w] -= tau h'' (real part) for Nw walkers: the Taylor propagator's exponent
 template <typename R>
 cudaError_t launch_shift_field(const afqmc_ctx* c, int Nw, double tau, cudaStream_t s);

@@ -388,6 +388,32 @@ __global__ void shift_field_kernel(typename C2<R>::t* __restrict__ A, const doub
     A[e].x = (R)((double)A[e].x - tau * hpp[e % NN]);
 }
 
+// One step of the Chebyshev recurrence (Eq. chebpoly) over `total` complex
+// entries.  first: acc = a t + b prod (t = T_0 Psi, prod = T_1 Psi; prod may be
+// t when b = 0).  Otherwise t <- prod - t (prod = 2 A T_{n-1} Psi and
+// t = T_{n-2} Psi, so t becomes T_n Psi) and acc += b t.
+template <typename R>
+__global__ void cheb_step_kernel(const typename C2<R>::t* prod, typename C2<R>::t* t,
+                                 typename C2<R>::t* __restrict__ acc, double a, double b, int first, size_t total) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const auto pv = prod[e];
+    const auto tv = t[e];
+    auto av = acc[e];
+    if (first) {
+      av.x = (R)(a * (double)tv.x + b * (double)pv.x);
+      av.y = (R)(a * (double)tv.y + b * (double)pv.y);
+    } else {
+      auto nv = tv;
+      nv.x = (R)((double)pv.x - (double)tv.x);
+      nv.y = (R)((double)pv.y - (double)tv.y);
+      t[e] = nv;
+      av.x = (R)((double)av.x + b * (double)nv.x);
+      av.y = (R)((double)av.y + b * (double)nv.y);
+    }
+    acc[e] = av;
+  }
+}
+
 inline int grid_for(size_t n) {
   size_t b = (n + 255) / 256;
   return (int)(b > 152 * 64 ? 152 * 64 : (b == 0 ? 1 : b));
@@ -570,8 +596,21 @@ cudaError_t launch_shift_field(const afqmc_ctx* c, int Nw, double tau, cudaStrea
   return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t launch_cheb_step(const afqmc_ctx* c, int Nw, const void* prod, void* t, void* acc, double a, double b,
+                             int first, cudaStream_t s) {
+  typedef typename C2<R>::t C;
+  const size_t total = (size_t)Nw * c->nc * c->N;
+  if (total == 0) return cudaSuccess;
+  cheb_step_kernel<R><<<grid_for(total), 256, 0, s>>>(static_cast<const C*>(prod), static_cast<C*>(t),
+                                                      static_cast<C*>(acc), a, b, first, total);
+  return cudaGetLastError();
+}
+
 #define AFQ_INST(R)                                                                                         \
   template cudaError_t launch_shift_field<R>(const afqmc_ctx*, int, double, cudaStream_t);                  \
+  template cudaError_t launch_cheb_step<R>(const afqmc_ctx*, int, const void*, void*, void*, double, double, \
+                                           int, cudaStream_t);                                              \
   template cudaError_t launch_bias_finalize<R>(const afqmc_ctx*, int, const double*, double, cudaStream_t, uint8_t*, \
                                                const int*);                                                      \
   template cudaError_t launch_normA<R>(const afqmc_ctx*, int, cudaStream_t);                                \
