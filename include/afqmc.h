@@ -61,9 +61,9 @@ typedef enum {
   AFQMC_ESTATE = 6    /* call out of order (e.g. a step before afqmc_set_tau)   */
 } afqmc_status;
 
-/* Propagators (Sec. III): Split-2, the paper's recommended one, Split-1 and the
- * Taylor propagator.  Crank-Nicolson is not built. */
-enum { AFQMC_SPLIT2 = 0, AFQMC_SPLIT1 = 1, AFQMC_TAYLORPROP = 2 };
+/* Propagators (Sec. III): Split-2, the paper's recommended one, Split-1, the
+ * Taylor propagator and Crank-Nicolson. */
+enum { AFQMC_SPLIT2 = 0, AFQMC_SPLIT1 = 1, AFQMC_TAYLORPROP = 2, AFQMC_CN = 3 };
 
 /* Action of the one-body exponential (Sec. IV). */
 enum { AFQMC_EXPM_TAYLOR = 0, AFQMC_EXPM_KRYLOV = 1, AFQMC_EXPM_BLOCK_KRYLOV = 2, AFQMC_EXPM_CHEBYSHEV = 3 };
@@ -106,7 +106,12 @@ typedef struct {
  *               then the one-body step applied as two half steps) or
  *               AFQMC_TAYLORPROP (Sec. III.C: the Taylor series of order `order` of
  *               e^{A - tau h''} applied to the walkers, no splitting; expm must be
- *               AFQMC_EXPM_TAYLOR, else AFQMC_ENOTSUP); other values: AFQMC_ENOTSUP
+ *               AFQMC_EXPM_TAYLOR, else AFQMC_ENOTSUP) or
+ *               AFQMC_CN (Sec. III.D: (1 - X/2)^{-1} (1 + X/2) Psi with
+ *               X = A - tau h'', by Gaussian elimination with partial pivoting
+ *               per walker; expm and order are checked but not used; a
+ *               singular 1 - X/2 leaves the walker non-finite, so the weight
+ *               update kills it); other values: AFQMC_ENOTSUP
  *   expm        AFQMC_EXPM_TAYLOR (order = Taylor order k >= 0),
  *               AFQMC_EXPM_KRYLOV (order = Krylov dimension 1 <= k <= 32, one
  *               Krylov space per orbital column, Eq. krylov),

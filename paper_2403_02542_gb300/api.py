@@ -13,7 +13,8 @@ import torch
 from . import _lib as L
 
 # walker updates of Sec. III built in the library
-PROPAGATORS = {"split2": L.AFQMC_SPLIT2, "split1": L.AFQMC_SPLIT1, "taylor": L.AFQMC_TAYLORPROP}
+PROPAGATORS = {"split2": L.AFQMC_SPLIT2, "split1": L.AFQMC_SPLIT1, "taylor": L.AFQMC_TAYLORPROP,
+               "cn": L.AFQMC_CN}
 # actions of the one-body exponential of Sec. IV built in the library
 EXPMS = {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV, "bkrylov": L.AFQMC_EXPM_BLOCK_KRYLOV,
          "chebyshev": L.AFQMC_EXPM_CHEBYSHEV}
@@ -120,8 +121,9 @@ class Context:
         """One walker step (afqmc_step).  fields: device [Nw, G] float64.
         reuse_bias: take the force bias from the previous measurement of the
         same, unchanged walkers (see afqmc_step_params in the header).
-        propagator: "split2" (default), "split1" or "taylor" (the Taylor
-        propagator; expm must then be "taylor")."""
+        propagator: "split2" (default), "split1", "taylor" (the Taylor
+        propagator; expm must then be "taylor") or "cn" (Crank-Nicolson;
+        expm and order are not used)."""
         assert fields.dtype == torch.float64 and fields.is_cuda and fields.is_contiguous()
         self._bind_stream()
         p = L.StepParams(float(tau), float(e0), PROPAGATORS[propagator],

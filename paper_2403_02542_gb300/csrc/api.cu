@@ -502,37 +502,46 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
   PK(AFQMC_K_FORCEBIAS, gemm<R>(gfb, false, EPI_STORE, s));
   PK(AFQMC_K_OTHER, launch_bias_finalize<R>(c, Nw, x, st, s, nullptr, skip));
   // A_w = i sqrt(tau) sum_g c_wg L_g (Eq. heffTOT); complex64 walkers: on the
-  // tensor cores, except for the Taylor propagator, which needs A_w - tau h''
-  // in memory (the field GEMM, then the shift)
-  const bool split1 = p->propagator == AFQMC_SPLIT1, tprop = p->propagator == AFQMC_TAYLORPROP;
-  if (std::is_same<R, float>::value && c->tg.ok && !tprop) {
+  // tensor cores, except for the Taylor and Crank-Nicolson propagators, which
+  // need X_w = A_w - tau h'' in memory (the field GEMM, then the shift)
+  const bool split1 = p->propagator == AFQMC_SPLIT1, tprop = p->propagator == AFQMC_TAYLORPROP,
+             cn = p->propagator == AFQMC_CN, xmat = tprop || cn;
+  if (std::is_same<R, float>::value && c->tg.ok && !xmat) {
     PK(AFQMC_K_FIELD, tc_field_launch(c, Nw, st, s));
     c->launches += 1;
   } else {
     PK(AFQMC_K_FIELD, gemm<R>(site_args<R>(c, SITE_FIELD, Nw, st, ws.c, ws.A), false, EPI_STORE, s));
   }
-  if (tprop) {
+  if (xmat) {
     PK(AFQMC_K_FIELD, launch_shift_field<R>(c, Nw, p->tau, s));
     c->launches += 1;
   }
-  // psi_b = B psi (Split-2); Split-1 and the Taylor propagator start from psi itself
-  if (split1 || tprop) {
+  // psi_b = B psi (Split-2); the other propagators start from psi itself
+  if (split1 || xmat) {
     CKW(cudaMemcpyAsync(ws.psi_b, w->psi, (size_t)Nw * per * cs, cudaMemcpyDeviceToDevice, s), "psi copy");
   } else {
     PK(AFQMC_K_HALFSTEP, half(w->psi, ws.psi_b));
   }
-  c->launches += (split1 || tprop) ? 5 : 6;
+  c->launches += (split1 || xmat) ? 5 : 6;
 
   // per-walker products with A_w (tensor cores for complex64 walkers)
   GemmArgs ga = site_args<R>(c, SITE_EXPM, Nw, st, nullptr, nullptr);
-  const bool tc_av = std::is_same<R, float>::value && c->tg.av_ok && !tprop;
+  const bool tc_av = std::is_same<R, float>::value && c->tg.av_ok && !xmat;
   auto av = [&](const void* in, void* out, void* add, double alpha) -> cudaError_t {
     if (tc_av) return tc_av_launch(c, Nw, in, per, out, add, per, alpha, s);
     ga.B = in; ga.C = out; ga.D = add;
     ga.alpha_re = alpha; ga.alpha_im = 0.0;
     return gemm<R>(ga, true, add ? EPI_STORE_ADD : EPI_STORE, s);
   };
-  if (p->expm == AFQMC_EXPM_TAYLOR) {
+  if (cn) {
+    // Crank-Nicolson (Sec. III.D): psi_new = (I - X/2)^{-1} (psi + X psi / 2),
+    // the right-hand side by one product, then one pivoted solve per walker
+    CKW(cudaMemcpyAsync(ws.acc, ws.psi_b, (size_t)Nw * per * cs, cudaMemcpyDeviceToDevice, s), "acc copy");
+    PK(AFQMC_K_EXPM, av(ws.psi_b, ws.term0, ws.acc, 0.5));
+    CKW(cudaMemcpyAsync(ws.psi_new, ws.acc, (size_t)Nw * per * cs, cudaMemcpyDeviceToDevice, s), "rhs copy");
+    PK(AFQMC_K_OTHER, launch_cn_solve<R>(c, Nw, ws.A, ws.psi_new, s));
+    c->launches += 2;
+  } else if (p->expm == AFQMC_EXPM_TAYLOR) {
     CKW(cudaMemcpyAsync(ws.acc, ws.psi_b, (size_t)Nw * per * cs, cudaMemcpyDeviceToDevice, s), "acc copy");
     const void* cur = ws.psi_b;
     for (int n = 1; n <= p->order; ++n) {
@@ -598,7 +607,9 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
   }
   // psi_new = B acc (Split-2); B B acc = e^{-tau h''} acc (Split-1); acc itself
   // (the Taylor propagator)
-  if (tprop) {
+  if (cn) {
+    c->launches -= 1;  // psi_new holds the solution
+  } else if (tprop) {
     CKW(cudaMemcpyAsync(ws.psi_new, ws.acc, (size_t)Nw * per * cs, cudaMemcpyDeviceToDevice, s), "acc copy");
     c->launches -= 1;
   } else if (split1) {
@@ -1203,7 +1214,8 @@ afqmc_status afqmc_step(afqmc_ctx* c, const afqmc_walkers* w, const double* fiel
   if (!p || (!fields && w->n_walkers > 0)) return AFQMC_EINVAL;
   if (!std::isfinite(p->tau) || !std::isfinite(p->e0)) return AFQMC_EDOM;
   if (!(p->tau > 0.0)) return AFQMC_EINVAL;
-  if (p->propagator != AFQMC_SPLIT2 && p->propagator != AFQMC_SPLIT1 && p->propagator != AFQMC_TAYLORPROP)
+  if (p->propagator != AFQMC_SPLIT2 && p->propagator != AFQMC_SPLIT1 && p->propagator != AFQMC_TAYLORPROP &&
+      p->propagator != AFQMC_CN)
     return AFQMC_ENOTSUP;
   if (p->propagator == AFQMC_TAYLORPROP && p->expm != AFQMC_EXPM_TAYLOR) return AFQMC_ENOTSUP;
   if (p->expm == AFQMC_EXPM_TAYLOR || p->expm == AFQMC_EXPM_CHEBYSHEV) {
@@ -1473,7 +1485,8 @@ static afqmc_status step_checks(afqmc_ctx* c, const afqmc_walkers* w, const doub
   if (!p || (!fields && w->n_walkers > 0)) return AFQMC_EINVAL;
   if (!std::isfinite(p->tau) || !std::isfinite(p->e0)) return AFQMC_EDOM;
   if (!(p->tau > 0.0)) return AFQMC_EINVAL;
-  if (p->propagator != AFQMC_SPLIT2 && p->propagator != AFQMC_SPLIT1 && p->propagator != AFQMC_TAYLORPROP)
+  if (p->propagator != AFQMC_SPLIT2 && p->propagator != AFQMC_SPLIT1 && p->propagator != AFQMC_TAYLORPROP &&
+      p->propagator != AFQMC_CN)
     return AFQMC_ENOTSUP;
   if (p->propagator == AFQMC_TAYLORPROP && p->expm != AFQMC_EXPM_TAYLOR) return AFQMC_ENOTSUP;
   if (p->expm == AFQMC_EXPM_TAYLOR || p->expm == AFQMC_EXPM_CHEBYSHEV) {

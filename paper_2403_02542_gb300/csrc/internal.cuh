@@ -258,6 +258,11 @@ cudaError_t launch_bias_gate(const afqmc_ctx* c, const void* psi, int Nw, int op
 cudaError_t launch_bias_mark(const afqmc_ctx* c, const void* psi, int Nw, cudaStream_t s);
 template <typename R>
 cudaError_t launch_normA(const afqmc_ctx* c, int Nw, cudaStream_t s);
+// Y[w] <- (I - X[w]/2)^{-1} Y[w] for Nw walkers (Crank-Nicolson; X [Nw][N][N]
+// is overwritten by the factors, Y [Nw][nc][N] in place; see cn_solve_kernel
+// in k_linalg.cu)
+template <typename R>
+cudaError_t launch_cn_solve(const afqmc_ctx* c, int Nw, void* X, void* Y, cudaStream_t s);
 // One step of the Chebyshev recurrence on Nw walkers' [nc][N] vectors (see
 // cheb_step_kernel in k_energy.cu)
 template <typename R>

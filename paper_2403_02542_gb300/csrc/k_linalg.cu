@@ -710,6 +710,94 @@ __global__ void krylov_combine_kernel(const typename C2<R>::t* __restrict__ hess
   }
 }
 
+// Crank-Nicolson solve (Sec. III.D), one walker per block: M = I - X/2 is
+// formed in place of X (row-major [N][N]), Gaussian elimination with partial
+// pivoting (the first row of largest |M_ik| is the pivot) runs on M and on the
+// nc right-hand sides Y [nc][N] together, then back substitution leaves
+// Y = (I - X/2)^{-1} Y.  FP64 arithmetic; M and Y keep the walkers' precision
+// in memory.  A zero pivot gives non-finite entries, which the weight update
+// turns into a dead walker.
+template <typename R>
+__global__ void __launch_bounds__(256) cn_solve_kernel(typename C2<R>::t* Xall, typename C2<R>::t* Yall, int N, int nc,
+                                                       size_t per) {
+  typedef typename C2<R>::t cplx;
+  __shared__ double s_val[256];
+  __shared__ int s_idx[256];
+  const int tid = threadIdx.x;
+  const size_t NN = (size_t)N * N;
+  cplx* M = Xall + blockIdx.x * NN;
+  cplx* Y = Yall + blockIdx.x * per;
+  for (size_t e = tid; e < NN; e += 256) {
+    const cd x = ld(M + e);
+    st(M + e, mk((e / N == e % N ? 1.0 : 0.0) - 0.5 * x.re, -0.5 * x.im));
+  }
+  __syncthreads();
+  for (int k = 0; k < N; ++k) {
+    double best = -1.0;
+    int bi = k;
+    for (int i = k + tid; i < N; i += 256) {
+      const double a = abs2(ld(M + (size_t)i * N + k));
+      if (a > best) {
+        best = a;
+        bi = i;
+      }
+    }
+    s_val[tid] = best;
+    s_idx[tid] = bi;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+      if (tid < o) {
+        const double v2 = s_val[tid + o];
+        const int i2 = s_idx[tid + o];
+        if (v2 > s_val[tid] || (v2 == s_val[tid] && i2 < s_idx[tid])) {
+          s_val[tid] = v2;
+          s_idx[tid] = i2;
+        }
+      }
+      __syncthreads();
+    }
+    const int piv = s_idx[0];  // rewritten only after the syncs of this k's later phases
+    if (piv != k) {
+      for (int q = k + tid; q < N; q += 256) {
+        const cplx a = M[(size_t)k * N + q];
+        M[(size_t)k * N + q] = M[(size_t)piv * N + q];
+        M[(size_t)piv * N + q] = a;
+      }
+      for (int j = tid; j < nc; j += 256) {
+        const cplx a = Y[(size_t)j * N + k];
+        Y[(size_t)j * N + k] = Y[(size_t)j * N + piv];
+        Y[(size_t)j * N + piv] = a;
+      }
+    }
+    __syncthreads();
+    const cd d = ld(M + (size_t)k * N + k);
+    for (int i = k + 1 + tid; i < N; i += 256) st(M + (size_t)i * N + k, cdiv(ld(M + (size_t)i * N + k), d));
+    __syncthreads();
+    const int r = N - k - 1;
+    const size_t nup = (size_t)r * r, nyu = (size_t)nc * r;
+    for (size_t e = tid; e < nup; e += 256) {
+      const size_t i = k + 1 + e / r, q = k + 1 + e % r;
+      st(M + i * N + q, ld(M + i * N + q) - ld(M + i * N + k) * ld(M + (size_t)k * N + q));
+    }
+    for (size_t e = tid; e < nyu; e += 256) {
+      const size_t j = e / r, i = k + 1 + e % r;
+      st(Y + j * N + i, ld(Y + j * N + i) - ld(M + i * N + k) * ld(Y + j * N + k));
+    }
+    __syncthreads();
+  }
+  for (int k = N - 1; k >= 0; --k) {
+    const cd d = ld(M + (size_t)k * N + k);
+    for (int j = tid; j < nc; j += 256) st(Y + (size_t)j * N + k, cdiv(ld(Y + (size_t)j * N + k), d));
+    __syncthreads();
+    const size_t nb = (size_t)nc * k;
+    for (size_t e = tid; e < nb; e += 256) {
+      const size_t j = e / k, i = e % k;
+      st(Y + j * N + i, ld(Y + j * N + i) - ld(M + i * N + k) * ld(Y + j * N + k));
+    }
+    __syncthreads();
+  }
+}
+
 template <typename R>
 __global__ void init_walkers_kernel(typename C2<R>::t* __restrict__ psi, const double* __restrict__ trial,
                                     double* __restrict__ weight, uint32_t* __restrict__ status, int N, int nc,
@@ -882,7 +970,16 @@ cudaError_t prepare_overlap(const afqmc_ctx*) {
 template cudaError_t prepare_overlap<double>(const afqmc_ctx*);
 template cudaError_t prepare_overlap<float>(const afqmc_ctx*);
 
+template <typename R>
+cudaError_t launch_cn_solve(const afqmc_ctx* c, int Nw, void* X, void* Y, cudaStream_t s) {
+  if (Nw <= 0) return cudaSuccess;
+  typedef typename C2<R>::t C;
+  cn_solve_kernel<R><<<Nw, 256, 0, s>>>(static_cast<C*>(X), static_cast<C*>(Y), c->N, c->nc, (size_t)c->nc * c->N);
+  return cudaGetLastError();
+}
+
 #define AFQ_INST(R)                                                                                       \
+  template cudaError_t launch_cn_solve<R>(const afqmc_ctx*, int, void*, void*, cudaStream_t);               \
   template cudaError_t launch_overlap<R>(const afqmc_ctx*, int, const void*, void*, double*, uint32_t*,   \
                                          cudaStream_t, const int*);                                        \
   template cudaError_t launch_mgs<R>(const afqmc_ctx*, int, void*, const uint8_t*, cudaStream_t);          \

@@ -1,7 +1,8 @@
 """The Split-1 propagator (Sec. III.A: the interaction exponential first, then
-the whole one-body step e^{-tau h''} as two half steps) and the Taylor
-propagator (Sec. III.C: the Taylor series of e^{A - tau h''}, no splitting) of
-the CUDA library against the CPU oracle on the same seeded systems and common
+the whole one-body step e^{-tau h''} as two half steps), the Taylor
+propagator (Sec. III.C: the Taylor series of e^{A - tau h''}, no splitting)
+and the Crank-Nicolson propagator (Sec. III.D: (1 - X/2)^{-1} (1 + X/2) with
+X = A - tau h'') of the CUDA library against the CPU oracle on the same seeded systems and common
 random fields: FP64 element by element (1e-10 relative, as the other FP64
 parity tests), complex64 walkers within the mixed energy bar (1e-4 Ha per
 walker), and the argument checks."""
@@ -113,4 +114,37 @@ def test_taylor_propagator_needs_the_taylor_action():
             ctx.step(w, x, 0.05, -1.0, expm=expm, order=4, propagator="taylor")
     ctx.step(w, x, 0.05, -1.0, expm="taylor", order=4, propagator="taylor")
     ctx.sync()
+    ctx.close()
+
+
+@pytest.mark.parametrize("N,n,G,nw,reo", [(40, 4, 70, 6, 2), (72, 5, 150, 5, 0)])
+def test_crank_nicolson_fp64_matches_oracle(N, n, G, nw, reo):
+    from paper_2403_02542_gb300.api import Context
+    s = make_system(N, n, n, G, rho=0.85 if G < 100 else 1e-5 ** (1 / G), seed=N + 3)
+    tau = 0.05
+    e0 = _e0(s)
+    ref, ties = oracle_walk(s, nw, 3, tau, e0, "taylor", 1, reo, seed=53, propagator="cn")
+    assert ties == 0
+    ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision="fp64")
+    got, _ = gpu_walk(ctx, nw, 3, tau, e0, "taylor", 1, reo, seed=53, propagator="cn")
+    for g, r in zip(got, ref):
+        compare(g, r, RTOL, what=f"Crank-Nicolson N={N} step {g['k']}")
+    ctx.close()
+
+
+def test_crank_nicolson_mixed_large_workload_energy():
+    """Complex64 walkers on the large workload (N=128, 20+20, 640 vectors):
+    E_L after two Crank-Nicolson steps within 1e-4 Ha of the oracle."""
+    from paper_2403_02542_gb300.api import Context
+    s = config_system("large")
+    tau = 0.05
+    e0 = _e0(s)
+    nw = 4
+    ref, ties = oracle_walk(s, nw, 2, tau, e0, "taylor", 1, 0, seed=59, propagator="cn")
+    assert ties == 0
+    ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, precision="mixed")
+    got, _ = gpu_walk(ctx, nw, 2, tau, e0, "taylor", 1, 0, seed=59, propagator="cn")
+    dE = max(float((g["El"] - r["El"]).abs().max()) for g, r in zip(got, ref))
+    print(f"Crank-Nicolson mixed vs oracle: max|dE_L| = {dE:.2e} Ha")
+    assert dE <= E_TOL
     ctx.close()
