@@ -64,6 +64,9 @@ def parse():
                     help="skip the timed gradient of the differentiation workload")
     ap.add_argument("--no-block-krylov", action="store_true",
                     help="skip the large workload with the block-Krylov exponential")
+    ap.add_argument("--no-propagators", action="store_true",
+                    help="skip the large workload with Split-1, the Taylor and Crank-Nicolson propagators "
+                         "and the Chebyshev action")
     ap.add_argument("--no-tau-scan", action="store_true",
                     help="skip the energy runs and time-step extrapolation of the small workload")
     ap.add_argument("--cpu-sample-walkers", type=int, default=4)
@@ -382,6 +385,56 @@ def block_krylov_rate(dev, steps=5):
     return out
 
 
+def propagator_rates(dev, steps=3):
+    """The large-step workload (N=128, 20+20 electrons, 640 vectors, 1024
+    walkers, tau=0.05, E_L every step, MGS every 5 steps, mixed) with the other
+    walker updates of Sec. III and the Chebyshev action of Sec. IV.B in place of
+    Split-2 + Krylov 10: CUDA-event timed after two warm-up steps.  A variant
+    that fails reports its error instead of a rate."""
+    import torch
+    from paper_2403_02542_gb300.api import Context
+    from paper_2403_02542_gb300.inputs import config_system
+    s = config_system("large")
+    variants = [("split1", "krylov", 10), ("taylor", "taylor", 8), ("cn", "taylor", 0),
+                ("split2", "chebyshev", 8), ("split2", "taylor", 8)]
+    out = {"workload": "large-step workload (N=128, Na=Nb=20, N_gamma=640, 1024 walkers, tau=0.05, E_loc every "
+                       "step, MGS every 5 steps), mixed", "unit": "walker-steps/s", "rates": {}}
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(13)
+    x = torch.randn(steps + 2, NW, s.G, dtype=torch.float64, device=dev, generator=gen)
+    stream = torch.cuda.current_stream(dev)
+    for prop, expm, k in variants:
+        name = f"{prop}+{expm}{k}" if prop != "cn" else "cn"
+        ctx = None
+        try:
+            ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision="mixed", device=dev)
+            w = ctx.new_walkers(NW)
+            ctx.init_walkers(w)
+            el = torch.empty(NW, 2, dtype=torch.float64, device=dev)
+            em = torch.empty(4, dtype=torch.float64, device=dev)
+            ctx.local_energy(w, 0.0, TAU, el, em)
+            e0 = float(el[0, 0])
+            for i in range(2):
+                ctx.step(w, x[i], TAU, e0, expm=expm, order=k, measure=True, e_loc=el, e_mix=em, reuse_bias=True,
+                         propagator=prop)
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for i in range(steps):
+                ctx.step(w, x[2 + i], TAU, e0, expm=expm, order=k, reortho=(i + 1) % REORTHO == 0, measure=True,
+                         e_loc=el, e_mix=em, reuse_bias=True, propagator=prop)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            ms = a0.elapsed_time(a1) / steps
+            out["rates"][name] = {"value": NW / (ms / 1000.0), "ms_per_step": ms, "e_mix": float(em[2])}
+        except Exception as exc:  # noqa: BLE001 - one failing variant must not end the bench line
+            out["rates"][name] = {"error": f"{type(exc).__name__}: {exc}"}
+        finally:
+            if ctx is not None:
+                ctx.close()
+    return out
+
+
 def tau_scan(dev, imag_time=10.0, taus=(0.01, 0.02, 0.05, 0.1), nw=1024):
     """Energy runs and the time-step extrapolation (Sec. VI) on the small
     workload (N=8, 2+2 electrons, 32 vectors lambda_g = 0.5^g, Split-2 +
@@ -693,6 +746,9 @@ def run_ours(args):
     block_krylov = None
     if world == 1 and not args.no_block_krylov:
         block_krylov = block_krylov_rate(dev)
+    props = None
+    if world == 1 and not args.no_propagators:
+        props = propagator_rates(dev)
     tau_ext = None
     if world == 1 and not args.no_tau_scan:
         tau_ext = tau_scan(dev)
@@ -727,6 +783,7 @@ def run_ours(args):
         "precision_workload": precision,
         "batched_workload": batched,
         "block_krylov_workload": block_krylov,
+        "propagator_workload": props,
         "tau_extrapolation": tau_ext,
         "clocks": clk,
         "e_mix_last": emix_final,

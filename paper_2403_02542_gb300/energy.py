@@ -92,9 +92,12 @@ def extrapolate(taus, energies, sigmas=None, power: int = 2):
 
 def energy_run(ctx, walkers, tau: float, e0: float, n_steps: int, *, fields, n_eq: int = 0,
                expm: str = "krylov", order: int = 10, reortho_every: int = 5, pop_every: int = 0,
-               seed: int = 0, update_e0: bool = False, reuse_bias: bool = False):
+               seed: int = 0, update_e0: bool = False, reuse_bias: bool = False, propagator: str = "split2"):
     """Propagate `walkers` for n_steps steps of the library with the local energy
     measured every step.  fields(k) returns the device fields [Nw, G] of step k.
+    propagator selects the walker update of Sec. III (see Context.step); fit
+    the energies of Split-1 and Crank-Nicolson runs with power 1 in
+    `extrapolate`.
     With pop_every > 0 the population is combed after every pop_every steps
     (uniform numbers from numpy's PCG64 seeded with `seed`).  Returns a dict
     with the per-step total weight W, mixed estimate E and E_0 used, and the
@@ -109,7 +112,7 @@ def energy_run(ctx, walkers, tau: float, e0: float, n_steps: int, *, fields, n_e
     for k in range(n_steps):
         reo = reortho_every > 0 and (k + 1) % reortho_every == 0
         ctx.step(walkers, fields(k), tau, e0, expm=expm, order=order, reortho=reo, measure=True,
-                 e_loc=e_loc, e_mix=e_mix, reuse_bias=reuse_bias)
+                 e_loc=e_loc, e_mix=e_mix, reuse_bias=reuse_bias, propagator=propagator)
         m = e_mix.cpu()
         E0s.append(e0)
         Ws.append(float(m[1]))
