@@ -240,25 +240,30 @@ def _arnoldi_column(A, psi_col, k, normA):
     """Krylov approximation of e^A psi for one orbital vector (Eqs. krylovsub-krylov)."""
     N = A.shape[-1]
     beta = torch.linalg.vector_norm(psi_col)
-    if float(beta) == 0.0:
+    if float(beta.detach()) == 0.0:
         return torch.zeros_like(psi_col), 0
     kk = min(k, N)
     basis = [psi_col / beta]                                 # b_1 = psi/||psi||
-    H = torch.zeros(kk, kk, dtype=psi_col.dtype)
+    entries = {}                                             # (i, j) -> H_ij of A_k
     k_eff = kk
     for j in range(kk):
         w = A @ basis[j]
         for i in range(j + 1):                               # modified Gram-Schmidt
-            H[i, j] = torch.vdot(basis[i], w)                # b_i^dagger w
-            w = w - H[i, j] * basis[i]
+            entries[i, j] = torch.vdot(basis[i], w)          # b_i^dagger w
+            w = w - entries[i, j] * basis[i]
         if j + 1 < kk:
             h = torch.linalg.vector_norm(w)
-            if float(h) <= 1e-12 * float(normA):             # invariant subspace (R5)
+            if float(h.detach()) <= 1e-12 * float(normA.detach()):   # invariant subspace (R5)
                 k_eff = j + 1
                 break
-            H[j + 1, j] = h
+            entries[j + 1, j] = h.to(psi_col.dtype)
             basis.append(w / h)
-    y = torch.linalg.matrix_exp(H[:k_eff, :k_eff])[:, 0] * beta   # e^{A_k} e_1 ||psi||
+    # A_k assembled once all its entries exist (so that autograd can follow them)
+    H = torch.zeros(k_eff, k_eff, dtype=psi_col.dtype)
+    for (i, j), v in entries.items():
+        if i < k_eff and j < k_eff:
+            H[i, j] = v
+    y = torch.linalg.matrix_exp(H)[:, 0] * beta              # e^{A_k} e_1 ||psi||
     out = torch.zeros_like(psi_col)
     for i in range(k_eff):
         out = out + y[i] * basis[i]                          # B_k y
@@ -618,10 +623,12 @@ def _reortho_fixed_R(ham: Hamiltonian, psi, alive):
     return torch.stack(out)
 
 
-def walk_objective(ham: Hamiltonian, psi0, W0, fields, tau, e0, k=6, reortho_every=0):
+def walk_objective(ham: Hamiltonian, psi0, W0, fields, tau, e0, k=6, reortho_every=0, method="taylor"):
     """J = E_n, the mixed estimator of the capped local energy after n
-    fixed-field Split-2 steps with the Taylor exponential (Sec. II.A, Sec.
-    III.B, Eq. taylor), as a function that torch autograd differentiates with
+    fixed-field Split-2 steps with the Taylor exponential of order k (Sec.
+    II.A, Sec. III.B, Eq. taylor) or another action of Sec. IV (`method`, e.g.
+    "krylov" of dimension k, differentiated through the Arnoldi steps and the
+    small exponential), as a function that torch autograd differentiates with
     respect to ham.h1, ham.L and psi0.
 
     Reading R10: the fields are fixed inputs; every threshold decision is
@@ -639,7 +646,7 @@ def walk_objective(ham: Hamiltonian, psi0, W0, fields, tau, e0, k=6, reortho_eve
     W = torch.as_tensor(W0, dtype=RT)
     for kk, x in enumerate(fields):
         alive = W > 0
-        psi, logovl, W, _ = step(ham, psi, logovl, W, x, tau, e0, method="taylor", k=k,
+        psi, logovl, W, _ = step(ham, psi, logovl, W, x, tau, e0, method=method, k=k,
                                  reortho=False, B=B, L_bar=L_bar, ec=ec)
         if reortho_every and (kk + 1) % reortho_every == 0:
             psi = _reortho_fixed_R(ham, psi, alive)

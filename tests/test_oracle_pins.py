@@ -726,11 +726,11 @@ def _walk_setup(N=7, na=2, nb=1, G=9, nw=3, steps=5, seed=11, tau=0.05):
     return s, e0, fields, tau
 
 
-def _walk_J(s, h1, L, psi0, fields, tau, e0, r=2):
+def _walk_J(s, h1, L, psi0, fields, tau, e0, r=2, method="taylor", k=6):
     ham = R.Hamiltonian(torch.as_tensor(h1, dtype=RT), torch.as_tensor(L, dtype=RT),
                         torch.as_tensor(s.trial, dtype=RT), s.na, s.nb, s.e_const)
     return R.walk_objective(ham, psi0, torch.ones(psi0.shape[0], dtype=RT), fields, tau, e0,
-                            k=6, reortho_every=r)[0]
+                            k=k, reortho_every=r, method=method)[0]
 
 
 def test_walk_objective_gradient_matches_central_differences():
@@ -785,3 +785,42 @@ def test_walk_objective_gauge_invariance_and_psi_gradient():
         fd = (float(_walk_J(s, s.h1, s.L, psi0.detach() + eps * dP, fields, tau, e0))
               - float(_walk_J(s, s.h1, s.L, psi0.detach() - eps * dP, fields, tau, e0))) / (2 * eps)
         assert abs(fd - float((G * dP).sum().real)) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_krylov_walk_gradient_matches_central_differences_and_exact_at_full_dimension():
+    """The Krylov path of the walk objective (Eq. krylov, dimension 4 < N = 7):
+    autograd through the Arnoldi steps and the small exponential against
+    central differences along random symmetric dH, dL; at dimension N the
+    Krylov action is the exact e^A psi, so J and its gradients equal those of
+    the exact action (matrix_exp)."""
+    s, e0, fields, tau = _walk_setup(steps=4, seed=13)
+    nw = fields[0].shape[0]
+    psi0 = torch.as_tensor(s.trial, dtype=RT).to(CT).unsqueeze(0).repeat(nw, 1, 1)
+    rng = np.random.default_rng(6)
+    dH = rng.standard_normal(s.h1.shape); dH = 0.5 * (dH + dH.T)
+    dL = rng.standard_normal(s.L.shape); dL = 0.5 * (dL + dL.transpose(0, 2, 1))
+    h1 = torch.tensor(s.h1, dtype=RT, requires_grad=True)
+    L = torch.tensor(s.L, dtype=RT, requires_grad=True)
+    J = _walk_J(s, h1, L, psi0, fields, tau, e0, method="krylov", k=4)
+    gh, gL = torch.autograd.grad(J, [h1, L])
+    eps = 1e-5
+    with torch.no_grad():
+        def Jk(hh, LL):
+            return float(_walk_J(s, hh, LL, psi0, fields, tau, e0, method="krylov", k=4))
+        fd_h = (Jk(s.h1 + eps * dH, s.L) - Jk(s.h1 - eps * dH, s.L)) / (2 * eps)
+        fd_L = (Jk(s.h1, s.L + eps * dL) - Jk(s.h1, s.L - eps * dL)) / (2 * eps)
+    assert abs(fd_h - float((gh * torch.as_tensor(dH)).sum())) <= 1e-6 * max(1.0, abs(fd_h))
+    assert abs(fd_L - float((gL * torch.as_tensor(dL)).sum())) <= 1e-6 * max(1.0, abs(fd_L))
+    N = s.h1.shape[0]
+    grads = {}
+    for method, k in (("krylov", N), ("exact", 0)):
+        h1 = torch.tensor(s.h1, dtype=RT, requires_grad=True)
+        L = torch.tensor(s.L, dtype=RT, requires_grad=True)
+        Jm = _walk_J(s, h1, L, psi0, fields, tau, e0, method=method, k=k)
+        grads[method] = (float(Jm.detach()),) + tuple(torch.autograd.grad(Jm, [h1, L]))
+    (Jk_, ghk, gLk), (Je, ghe, gLe) = grads["krylov"], grads["exact"]
+    assert abs(Jk_ - Je) <= 1e-11 * abs(Je)
+    assert float((ghk - ghe).abs().max()) <= 1e-8 * float(ghe.abs().max())
+    assert float((gLk - gLe).abs().max()) <= 1e-8 * float(gLe.abs().max())
+    # and the dimension-4 gradient differs from the exact one (the test sees the truncation)
+    assert float((gh - ghe).abs().max()) > 1e-10
