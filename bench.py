@@ -67,6 +67,8 @@ def parse():
     ap.add_argument("--no-propagators", action="store_true",
                     help="skip the large workload with Split-1, the Taylor and Crank-Nicolson propagators "
                          "and the Chebyshev action")
+    ap.add_argument("--no-expm-accuracy", action="store_true",
+                    help="skip the k_min study of the exponential actions (Fig. 1 analogue)")
     ap.add_argument("--no-tau-scan", action="store_true",
                     help="skip the energy runs and time-step extrapolation of the small workload")
     ap.add_argument("--cpu-sample-walkers", type=int, default=4)
@@ -435,6 +437,48 @@ def propagator_rates(dev, steps=3):
     return out
 
 
+def expm_accuracy(dev, nw=2400, n_steps=10, taus=(0.02, 0.1, 0.3), budget_s=90.0):
+    """The accuracy study of Sec. IV.E (Fig. 1) through the library: on one
+    synthetic system (N=64, Na=Nb=10, N_gamma=320, FP64), 2400 walkers, 10 steps
+    per run, the smallest order of the Taylor, Chebyshev, Krylov and
+    block-Krylov actions (orders up to 24; None beyond) whose run energy is
+    within 1e-5 Ha of the order-64 Taylor run, at each time step.  Stops after
+    budget_s seconds (the time steps not reached are left out)."""
+    import time
+    import torch
+    from paper_2403_02542_gb300 import expm_study as S
+    from paper_2403_02542_gb300.api import Context
+    from paper_2403_02542_gb300.inputs import make_system
+    out = {"workload": "N=64, Na=Nb=10, N_gamma=320 (rho = 1e-5^(1/320)), 2400 walkers, 10 steps per run, FP64, "
+                       "eps = 1e-5 Ha against the order-64 Taylor run", "k_min": {}}
+    ctx = None
+    try:
+        s = make_system(64, 10, 10, 320, rho=1e-5 ** (1 / 320), seed=64)
+        ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision="fp64", device=dev)
+        w = ctx.new_walkers(1)
+        ctx.init_walkers(w)
+        el = torch.empty(1, 2, dtype=torch.float64, device=dev)
+        em = torch.empty(4, dtype=torch.float64, device=dev)
+        ctx.local_energy(w, 0.0, 0.1, el, em)
+        e0 = float(el[0, 0])
+        t0 = time.time()
+        for tau in taus:
+            if time.time() - t0 > budget_s:
+                break
+            gen = torch.Generator(device=dev)
+            gen.manual_seed(17)
+            x = torch.randn(n_steps, nw, s.G, dtype=torch.float64, device=dev, generator=gen)
+            res = S.sweep(ctx, nw, n_steps, lambda _t: (lambda k: x[k]), (tau,), e0, k_max=24)[tau]
+            out["k_min"][str(tau)] = res
+        out["seconds"] = time.time() - t0
+    except Exception as exc:  # noqa: BLE001 - the study must not end the bench line
+        out["error"] = f"{type(exc).__name__}: {exc}"
+    finally:
+        if ctx is not None:
+            ctx.close()
+    return out
+
+
 def tau_scan(dev, imag_time=10.0, taus=(0.01, 0.02, 0.05, 0.1), nw=1024):
     """Energy runs and the time-step extrapolation (Sec. VI) on the small
     workload (N=8, 2+2 electrons, 32 vectors lambda_g = 0.5^g, Split-2 +
@@ -749,6 +793,9 @@ def run_ours(args):
     props = None
     if world == 1 and not args.no_propagators:
         props = propagator_rates(dev)
+    accuracy = None
+    if world == 1 and not args.no_expm_accuracy:
+        accuracy = expm_accuracy(dev)
     tau_ext = None
     if world == 1 and not args.no_tau_scan:
         tau_ext = tau_scan(dev)
@@ -784,6 +831,7 @@ def run_ours(args):
         "batched_workload": batched,
         "block_krylov_workload": block_krylov,
         "propagator_workload": props,
+        "expm_accuracy": accuracy,
         "tau_extrapolation": tau_ext,
         "clocks": clk,
         "e_mix_last": emix_final,
