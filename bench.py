@@ -437,7 +437,7 @@ def propagator_rates(dev, steps=3):
     return out
 
 
-def expm_accuracy(dev, nw=2400, n_steps=10, taus=(0.02, 0.1, 0.3), budget_s=90.0):
+def expm_accuracy(dev, nw=2400, n_steps=10, taus=(0.02, 0.1, 0.3), budget_s=60.0):
     """The accuracy study of Sec. IV.E (Fig. 1) through the library: on one
     synthetic system (N=64, Na=Nb=10, N_gamma=320, FP64), 2400 walkers, 10 steps
     per run, the smallest order of the Taylor, Chebyshev, Krylov and
