@@ -1,7 +1,8 @@
 """A CPU stand-in for `Context` whose steps are the oracle's: the same
-new_walkers / init_walkers / step(measure=True) calls, walkers kept as
-oracle tensors.  Tests use it to exercise host-side drivers (the accuracy study)
-without a GPU, and to compute, through the oracle, what the library should give."""
+new_walkers / init_walkers / step(measure=True) / population_control calls,
+walkers kept as oracle tensors.  Tests use it to exercise host-side drivers
+(the accuracy study, the energy run) without a GPU, and to compute, through the
+oracle, what the library should give."""
 from types import SimpleNamespace
 
 import torch
@@ -43,6 +44,11 @@ class OracleContext:
             if e_mix is not None:
                 e_mix[1] = float(wsum)
                 e_mix[2] = float(emix)
+
+    def population_control(self, w, u, index_out=None):
+        w.psi, w.lo, w.W, idx = R.population_control(w.psi, w.lo, w.W, u)
+        if index_out is not None:
+            index_out.copy_(idx)
 
 
 def field_fn(seed, nw, G, device=None):

@@ -2,13 +2,13 @@
 control, E_0 updates) against the same protocol driven through the CPU oracle
 with the same fields and comb numbers: the per-step total weights and mixed
 estimates agree to 1e-10 in FP64, and the run's statistics follow."""
-import numpy as np
 import pytest
 import torch
 
 from oracle import afqmc_ref as R
 from paper_2403_02542_gb300 import energy as S
 from paper_2403_02542_gb300.inputs import make_fields, make_system
+from walk_helpers import oracle_energy_run as _oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -19,29 +19,6 @@ def _built():
     build.build()
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-
-
-def _oracle_run(s, nw, tau, e0, n_steps, n_eq, order, reortho_every, pop_every, seed, fseed):
-    ham = R.make_hamiltonian(s.h1, s.L, s.trial, s.na, s.nb, s.e_const)
-    Lbar = R.mean_field_shift(ham)
-    hpp, ec = R.propagation_h1(ham, Lbar)
-    B = R.half_step_propagator(hpp, tau)
-    psi, lo, W = R.init_walkers(ham, nw)
-    rng = np.random.Generator(np.random.PCG64(seed))
-    Ws, Es = [], []
-    for k in range(n_steps):
-        reo = reortho_every > 0 and (k + 1) % reortho_every == 0
-        x = make_fields(fseed, k, nw, ham.G)
-        psi, lo, W, _ = R.step(ham, psi, lo, W, x, tau, e0, method="krylov", k=order, reortho=reo,
-                               B=B, L_bar=Lbar, ec=ec)
-        El = R.local_energy(ham, psi)
-        emix, wsum = R.mixed_energy(W, R.energy_window(El, e0, tau, ham.na + ham.nb))
-        Ws.append(float(wsum))
-        Es.append(float(emix))
-        if (k + 1) % pop_every == 0:
-            psi, lo, W, _ = R.population_control(psi, lo, W, float(rng.random()))
-            e0 = Es[-1] if k < n_eq else S.time_average(Ws, Es, n_eq)[0]
-    return Ws, Es
 
 
 def test_energy_run_matches_the_oracle_protocol():

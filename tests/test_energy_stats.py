@@ -71,3 +71,30 @@ def test_extrapolation_errors_match_the_scatter():
     assert np.std(fits) == pytest.approx(s0, rel=0.06)
     assert np.mean(fits) == pytest.approx(e0, abs=4 * s0 / math.sqrt(len(fits)))
     assert np.mean(chis) == pytest.approx(1.0, rel=0.06)
+
+
+def test_energy_run_driver_follows_its_protocol_on_the_oracle():
+    """energy_run's host logic (steps with E_L every step, QR every 3 steps, the
+    comb every 4 steps with numbers from PCG64(seed), E_0 updates at each comb)
+    driven through the oracle-backed stand-in context gives exactly the
+    per-step weights and estimates of the same protocol written out on the
+    oracle, and E_0 takes the values the protocol names."""
+    import torch
+    from oracle import afqmc_ref as R
+    from oracle_context import OracleContext
+    from paper_2403_02542_gb300.inputs import make_fields, make_system
+    from walk_helpers import oracle_energy_run
+    s = make_system(10, 2, 2, 16, rho=0.8, seed=12)
+    nw, tau, n_steps, n_eq, order, reo, pop, seed, fseed = 12, 0.05, 12, 4, 6, 3, 4, 5, 77
+    octx = OracleContext(s)
+    e0 = float(R.local_energy(octx.ham, octx.ham.trial.to(torch.complex128)).real)
+    Wr, Er = oracle_energy_run(s, nw, tau, e0, n_steps, n_eq, order, reo, pop, seed, fseed)
+    w = octx.new_walkers(nw)
+    octx.init_walkers(w)
+    out = S.energy_run(octx, w, tau, e0, n_steps, fields=lambda k: torch.as_tensor(make_fields(fseed, k, nw, s.G)),
+                       n_eq=n_eq, order=order, reortho_every=reo, pop_every=pop, seed=seed, update_e0=True)
+    assert out["W"] == pytest.approx(Wr, rel=1e-14)
+    assert out["E"] == pytest.approx(Er, rel=1e-14)
+    assert out["e0"][:4] == [e0] * 4
+    assert out["e0"][4] == pytest.approx(Er[3], rel=1e-14)
+    assert out["e0"][8] == pytest.approx(S.time_average(Wr[:8], Er[:8], n_eq)[0], rel=1e-14)

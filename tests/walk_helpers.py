@@ -108,3 +108,31 @@ def compare(g, r, rtol, alive=None, what=""):
     for k, v in worst.items():
         assert v <= rtol, f"{what} {k}: relative error {v:.3e} > {rtol:.1e}"
     return worst
+
+
+def oracle_energy_run(s, nw, tau, e0, n_steps, n_eq, order, reortho_every, pop_every, seed, fseed):
+    """The protocol of energy.energy_run (update_e0=True) driven through the
+    oracle: steps with E_L every step, the comb every pop_every steps with
+    numbers from one PCG64(seed), E_0 updated at each comb.  Returns the
+    per-step total weights and mixed estimates."""
+    from paper_2403_02542_gb300 import energy as S
+    ham = R.make_hamiltonian(s.h1, s.L, s.trial, s.na, s.nb, s.e_const)
+    Lbar = R.mean_field_shift(ham)
+    hpp, ec = R.propagation_h1(ham, Lbar)
+    B = R.half_step_propagator(hpp, tau)
+    psi, lo, W = R.init_walkers(ham, nw)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    Ws, Es = [], []
+    for k in range(n_steps):
+        reo = reortho_every > 0 and (k + 1) % reortho_every == 0
+        x = make_fields(fseed, k, nw, ham.G)
+        psi, lo, W, _ = R.step(ham, psi, lo, W, x, tau, e0, method="krylov", k=order, reortho=reo,
+                               B=B, L_bar=Lbar, ec=ec)
+        El = R.local_energy(ham, psi)
+        emix, wsum = R.mixed_energy(W, R.energy_window(El, e0, tau, ham.na + ham.nb))
+        Ws.append(float(wsum))
+        Es.append(float(emix))
+        if (k + 1) % pop_every == 0:
+            psi, lo, W, _ = R.population_control(psi, lo, W, float(rng.random()))
+            e0 = Es[-1] if k < n_eq else S.time_average(Ws, Es, n_eq)[0]
+    return Ws, Es
