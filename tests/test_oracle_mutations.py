@@ -1,0 +1,89 @@
+"""The oracle's pins bind: each plausible mistake below (a dropped factor, a
+wrong sign, an order off by one, a missing conjugate, a stale value), planted
+in the oracle on the CPU by replacing one function, makes the named pin of
+tests/test_oracle_pins.py fail.  The oracle itself is untouched outside each
+test (monkeypatch restores it)."""
+import pytest
+import torch
+
+import test_oracle_pins as P
+from oracle import afqmc_ref as R
+
+CT = torch.complex128
+
+
+def _split1_one_half_step(orig):
+    def bad(B, A, psi, method, k, spins=None):       # B once instead of B B after e^A
+        return B.to(CT) @ R.expm_action(A, psi, method, k, spins)
+    return bad
+
+
+# (mistake, oracle function, replacement built from the original, pin that must fail)
+MUTATIONS = [
+    ("Taylor order one short", "taylor_action",
+     lambda o: lambda A, psi, k: o(A, psi, max(k - 1, 0)), "test_taylor_order_zero_and_one"),
+    ("Chebyshev c_n without the factor 2", "chebyshev_coefficients",
+     lambda o: lambda k: torch.cat([o(k)[:1], o(k)[1:] / 2]),
+     "test_chebyshev_coefficients_are_the_modified_bessel_values"),
+    ("Chebyshev order one short", "chebyshev_action",
+     lambda o: lambda A, psi, k: o(A, psi, max(k - 1, 0)),
+     "test_chebyshev_action_converges_to_matrix_exp_within_its_bound"),
+    ("Krylov without ||psi||", "krylov_action",
+     lambda o: lambda A, psi, k: o(A, psi, k) / torch.linalg.vector_norm(psi, dim=-2, keepdim=True),
+     "test_krylov_full_dimension_is_exact"),
+    ("Krylov dimension one short", "krylov_action",
+     lambda o: lambda A, psi, k: o(A, psi, max(k - 1, 1)), "test_krylov_full_dimension_is_exact"),
+    ("block Krylov one block short", "block_krylov_action",
+     lambda o: lambda A, psi, k, spins=None: o(A, psi, max(k - 1, 1), spins),
+     "test_block_krylov_full_space_is_exact"),
+    ("exact action of -A", "exact_action",
+     lambda o: lambda A, psi: o(-A, psi), "test_exact_action_matches_matrix_exp"),
+    ("half step e^{-tau h''}", "half_step_propagator",
+     lambda o: lambda hpp, tau: o(hpp, 2 * tau), "test_half_step_squares_to_one_body_exponential"),
+    ("field matrix sign", "field_matrix",
+     lambda o: lambda ham, c, tau: -o(ham, c, tau), "test_first_step_from_trial_closed_form"),
+    ("Split-1 with one half step", "split1_propagate", _split1_one_half_step,
+     "test_split1_error_is_half_the_commutator"),
+    ("Taylor propagator without tau on h''", "taylor_propagate",
+     lambda o: lambda hpp, A, psi, tau, k: o(hpp / tau, A, psi, tau, k),
+     "test_taylor_propagator_expands_the_whole_exponent"),
+    ("Crank-Nicolson factors swapped", "crank_nicolson_propagate",
+     lambda o: lambda hpp, A, psi, tau: o(-hpp, -A, psi, tau), "test_crank_nicolson_pade_error"),
+    ("h'' without the mean-field shift", "propagation_h1",
+     lambda o: lambda ham, L_bar=None: o(ham, 0 * R.mean_field_shift(ham)),
+     "test_propagation_h1_reproduces_one_electron_hamiltonian"),
+    ("mean-field shift halved", "mean_field_shift",
+     lambda o: lambda ham: 0.5 * o(ham), "test_mean_field_shift_closed_form"),
+    ("force bias sign", "force_bias",
+     lambda o: lambda ham, psi, tau, L_bar=None: (lambda f, fr: (-f, fr))(*o(ham, psi, tau, L_bar)),
+     "test_force_bias_capping_removes_components"),
+    ("Theta of the conjugate walker", "theta",
+     lambda o: lambda t, p: o(t, p.conj()), "test_mixed_expectation_is_derivative_of_log_overlap"),
+    ("log-overlap conjugated", "log_overlap",
+     lambda o: lambda ham, psi: o(ham, psi).conj(), "test_log_overlap_closed_form_small_dets"),
+    ("stale log-overlap after QR", "reorthonormalise",
+     lambda o: lambda ham, psi: (o(ham, psi)[0], R.log_overlap(ham, psi)),
+     "test_log_overlap_after_qr_shifts_by_log_det_R"),
+    ("MGS columns not normalised", "mgs_qr",
+     lambda o: lambda X: (lambda q, r: (2 * q, r / 2))(*o(X)), "test_mgs_qr_against_library_qr"),
+    ("local energy of the conjugate walker", "local_energy",
+     lambda o: lambda ham, psi: o(ham, psi.conj()), "test_local_energy_matches_bruteforce_for_general_walker"),
+    ("energy window four times too wide", "energy_window",
+     lambda o: lambda e, e0, tau, n: o(e, e0, tau, 4 * n), "test_energy_window_values"),
+    ("energy window centred at 0", "energy_window",
+     lambda o: lambda e, e0, tau, n: o(e, 0.0, tau, n), "test_energy_window_values"),
+    ("weight update with -E_0", "weight_update",
+     lambda o: lambda W, lr, li, tau, e0: o(W, lr, li, tau, -e0), "test_weight_real_positive_special_case"),
+    ("mixed estimate without weights", "mixed_energy",
+     lambda o: lambda W, e: o((W > 0).to(W.dtype), e), "test_mixed_energy_ignores_dead_walkers"),
+    ("comb teeth shifted by half a spacing", "comb",
+     lambda o: lambda W, u: o(W, (u + 0.5) % 1.0), "test_comb_example"),
+]
+
+
+@pytest.mark.parametrize("mistake,name,make,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_planted_mistake_fails_its_pin(monkeypatch, mistake, name, make, pin):
+    getattr(P, pin)()                                  # the pin passes on the oracle as it is
+    monkeypatch.setattr(R, name, make(getattr(R, name)))
+    with pytest.raises(AssertionError):
+        getattr(P, pin)()

@@ -482,24 +482,28 @@ def test_local_energy_at_trial_matches_bruteforce_determinant():
 
 def test_local_energy_matches_bruteforce_for_general_walker():
     """E_L(Psi) = <Psi_T|H|Psi>/<Psi_T|Psi> with both determinants expanded in the
-    FCI basis (real walker, so the brute force stays real)."""
+    FCI basis, for a real walker and for a complex one (the trial is real, so
+    the brute force takes no complex conjugate)."""
     s, ham = _small_ham(N=5, n=2, G=8)
     g = np.random.default_rng(14)
-    psi = s.trial + 0.3 * g.standard_normal(s.trial.shape)
     H, dets = fci.hamiltonian_matrix(s.h1, s.L, 2, 2)
 
     def expand(Ca, Cb):
-        v = np.zeros(len(dets))
+        v = np.zeros(len(dets), dtype=np.result_type(Ca, Cb))
         for i, d in enumerate(dets):
             oa = [p for p in range(5) if (d >> p) & 1]
             ob = [p for p in range(5) if (d >> (5 + p)) & 1]
             v[i] = np.linalg.det(Ca[oa, :]) * np.linalg.det(Cb[ob, :])
         return v
     vt = expand(s.trial[:, :2], s.trial[:, 2:])
-    vp = expand(psi[:, :2], psi[:, 2:])
-    ref = (vt @ H @ vp) / (vt @ vp)
-    got = R.local_energy(ham, torch.as_tensor(psi).to(CT))
-    assert abs(complex(got) - ref) < 1e-10
+    real = s.trial + 0.3 * g.standard_normal(s.trial.shape)
+    cplx = real + 0.3j * g.standard_normal(s.trial.shape)
+    for psi in (real, cplx):
+        vp = expand(psi[:, :2], psi[:, 2:])
+        ref = (vt @ H @ vp) / (vt @ vp)
+        got = R.local_energy(ham, torch.as_tensor(psi).to(CT))
+        assert abs(complex(got) - complex(ref)) < 1e-10
+    assert abs(complex(ref).imag) > 1e-3      # the complex case tests the imaginary part
 
 
 def test_local_energy_gauge_invariance():
