@@ -74,6 +74,12 @@ MUTATIONS = [
      lambda o: lambda e, e0, tau, n: o(e, 0.0, tau, n), "test_energy_window_values"),
     ("weight update with -E_0", "weight_update",
      lambda o: lambda W, lr, li, tau, e0: o(W, lr, li, tau, -e0), "test_weight_real_positive_special_case"),
+    ("phase of the overlap ratio conjugated", "weight_update",
+     lambda o: lambda W, lr, li, tau, e0: o(W, lr.conj(), li, tau, e0), "test_weight_caps"),
+    ("importance factor dropped", "weight_update",
+     lambda o: lambda W, lr, li, tau, e0: o(W, lr, 0 * li, tau, e0), "test_weight_real_positive_special_case"),
+    ("importance factor doubled", "weight_update",
+     lambda o: lambda W, lr, li, tau, e0: o(W, lr, 2 * li, tau, e0), "test_weight_real_positive_special_case"),
     ("mixed estimate without weights", "mixed_energy",
      lambda o: lambda W, e: o((W > 0).to(W.dtype), e), "test_mixed_energy_ignores_dead_walkers"),
     ("comb teeth shifted by half a spacing", "comb",
