@@ -11,7 +11,11 @@
  *   field assembly                  (Eq. heffTOT)
  *   Split-2 propagation             (Sec. III.B) with the Taylor (Eq. taylor)
  *                                   or Krylov (Eqs. krylovsub-krylov) action
- *                                   of the one-body exponential
+ *                                   of the one-body exponential; also the
+ *                                   block-Krylov (Eq. bkrylov) and Chebyshev
+ *                                   (Sec. IV.B) actions, and the Split-1,
+ *                                   Taylor and Crank-Nicolson propagators
+ *                                   (Sec. III.A, III.C, III.D)
  *   overlap ratio, hybrid energy    (Eqs. hyben, theta)
  *   phaseless weight with capping   (Eq. phaseless; Sec. V.B)
  *   optional re-orthonormalisation  (modified Gram-Schmidt; Sec. IV.D)
