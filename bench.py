@@ -481,49 +481,69 @@ def expm_accuracy(dev, nw=2400, n_steps=10, taus=(0.02, 0.1, 0.3), budget_s=60.0
 
 def tau_scan(dev, imag_time=10.0, taus=(0.01, 0.02, 0.05, 0.1), nw=1024):
     """Energy runs and the time-step extrapolation (Sec. VI) on the small
-    workload (N=8, 2+2 electrons, 32 vectors lambda_g = 0.5^g, Split-2 +
-    Taylor-6, QR every 5 steps, FP64): for each tau, imag_time / tau steps of
-    1024 walkers with E_L every step, comb population control every 10 steps
-    and E_0 updates, the first 30 % as equilibration; the blocking analysis of
-    each run and the fit E(tau) = E_0 + beta tau^2."""
-    import numpy as np
+    workload (N=8, 2+2 electrons, 32 vectors lambda_g = 0.5^g, Taylor-6, QR
+    every 5 steps, FP64): for each tau, imag_time / tau steps of 1024 walkers
+    with E_L every step, comb population control every 10 steps and E_0
+    updates, the first 30 % as equilibration; the blocking analysis of each
+    run and the fit E(tau) = E_0 + beta tau^2 for Split-2.  The same series with
+    Split-1, whose time-step error is linear, is fitted by E_0 + alpha tau: both
+    fits estimate the same E_0."""
     import torch
     from paper_2403_02542_gb300 import energy as S
     from paper_2403_02542_gb300.api import Context
     from paper_2403_02542_gb300.inputs import config_system
     s = config_system("small")
-    runs = []
+
+    def series(propagator, seed_base):
+        runs = []
+        total_steps = 0
+        for i, tau in enumerate(taus):
+            n_steps = int(round(imag_time / tau))
+            n_eq = int(0.3 * n_steps)
+            ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision="fp64", device=dev)
+            w = ctx.new_walkers(nw)
+            ctx.init_walkers(w)
+            el = torch.empty(nw, 2, dtype=torch.float64, device=dev)
+            em = torch.empty(4, dtype=torch.float64, device=dev)
+            ctx.local_energy(w, 0.0, tau, el, em)
+            gen = torch.Generator(device=dev)
+            gen.manual_seed(seed_base + i)
+            x = torch.empty(nw, s.G, dtype=torch.float64, device=dev)
+
+            def fields(k):
+                return x.normal_(generator=gen)
+
+            out = S.energy_run(ctx, w, tau, float(em[2]), n_steps, fields=fields, n_eq=n_eq, expm="taylor",
+                               order=6, reortho_every=5, pop_every=10, seed=seed_base + 100 + i, update_e0=True,
+                               propagator=propagator)
+            st = out["stats"]
+            runs.append({"tau": tau, "steps": n_steps, "E": st["E_bar"], "sigma": st["sigma"],
+                         "kappa": st["kappa"]})
+            total_steps += n_steps
+            ctx.close()
+        return runs, total_steps
+
+    def fit(runs, power):
+        e0, c, s0, sc, chi2 = S.extrapolate([r["tau"] for r in runs], [r["E"] for r in runs],
+                                            [r["sigma"] for r in runs], power)
+        return {"E0": e0, ("beta" if power == 2 else "alpha"): c, "sigma_E0": s0,
+                ("sigma_beta" if power == 2 else "sigma_alpha"): sc, "chi2_dof": chi2}
+
     t0 = time.perf_counter()
-    total_steps = 0
-    for i, tau in enumerate(taus):
-        n_steps = int(round(imag_time / tau))
-        n_eq = int(0.3 * n_steps)
-        ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision="fp64", device=dev)
-        w = ctx.new_walkers(nw)
-        ctx.init_walkers(w)
-        el = torch.empty(nw, 2, dtype=torch.float64, device=dev)
-        em = torch.empty(4, dtype=torch.float64, device=dev)
-        ctx.local_energy(w, 0.0, tau, el, em)
-        gen = torch.Generator(device=dev)
-        gen.manual_seed(100 + i)
-        x = torch.empty(nw, s.G, dtype=torch.float64, device=dev)
-
-        def fields(k):
-            return x.normal_(generator=gen)
-
-        out = S.energy_run(ctx, w, tau, float(em[2]), n_steps, fields=fields, n_eq=n_eq, expm="taylor", order=6,
-                           reortho_every=5, pop_every=10, seed=200 + i, update_e0=True)
-        st = out["stats"]
-        runs.append({"tau": tau, "steps": n_steps, "E": st["E_bar"], "sigma": st["sigma"], "kappa": st["kappa"]})
-        total_steps += n_steps
-        ctx.close()
+    runs, total_steps = series("split2", 100)
     wall = time.perf_counter() - t0
-    e0, beta, s0, sb, chi2 = S.extrapolate([r["tau"] for r in runs], [r["E"] for r in runs],
-                                           [r["sigma"] for r in runs], 2)
-    return {"workload": "small workload (N=8, Na=Nb=2, N_gamma=32, lambda_g=0.5^g), FP64, 1024 walkers, "
-                        "Split-2 + Taylor-6, QR every 5, comb every 10 steps, E_0 updated, imaginary time 10 per tau",
-            "runs": runs, "fit": {"E0": e0, "beta": beta, "sigma_E0": s0, "sigma_beta": sb, "chi2_dof": chi2},
-            "wall_s": wall, "walker_steps_per_s": nw * total_steps / wall}
+    out = {"workload": "small workload (N=8, Na=Nb=2, N_gamma=32, lambda_g=0.5^g), FP64, 1024 walkers, "
+                       "Split-2 + Taylor-6, QR every 5, comb every 10 steps, E_0 updated, imaginary time 10 per tau",
+           "runs": runs, "fit": fit(runs, 2), "wall_s": wall, "walker_steps_per_s": nw * total_steps / wall}
+    try:
+        runs1, _ = series("split1", 300)
+        f1 = fit(runs1, 1)
+        out["split1"] = {"runs": runs1, "fit": f1,
+                         "E0_difference_sigmas": (f1["E0"] - out["fit"]["E0"])
+                         / max(1e-300, (f1["sigma_E0"] ** 2 + out["fit"]["sigma_E0"] ** 2) ** 0.5)}
+    except Exception as exc:  # noqa: BLE001 - the Split-2 series stands on its own
+        out["split1"] = {"error": f"{type(exc).__name__}: {exc}"}
+    return out
 
 
 def batched_rate(dev, steps=3, warmup=2):
