@@ -42,6 +42,12 @@ MUTATIONS = [
      lambda o: lambda hpp, tau: o(hpp, 2 * tau), "test_half_step_squares_to_one_body_exponential"),
     ("field matrix sign", "field_matrix",
      lambda o: lambda ham, c, tau: -o(ham, c, tau), "test_first_step_from_trial_closed_form"),
+    ("field matrix without the i", "field_matrix",
+     lambda o: lambda ham, c, tau: -1j * o(ham, c, tau),
+     "test_hubbard_stratonovich_average_of_the_field_propagator"),
+    ("field matrix with sqrt(2 tau)", "field_matrix",
+     lambda o: lambda ham, c, tau: o(ham, c, 2 * tau),
+     "test_hubbard_stratonovich_average_of_the_field_propagator"),
     ("Split-1 with one half step", "split1_propagate", _split1_one_half_step,
      "test_split1_error_is_half_the_commutator"),
     ("Taylor propagator without tau on h''", "taylor_propagate",

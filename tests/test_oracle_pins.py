@@ -305,6 +305,43 @@ def test_propagators_agree_without_interaction():
 
 
 # ---------------------------------------------------------------- propagator
+def _gauss_average(ham, tau, nodes):
+    """E_x[e^{A(x)}] over standard-normal fields x_g (one per Cholesky vector)
+    by a tensor Gauss-Hermite rule (weight e^{-x^2/2}), A from field_matrix."""
+    import itertools
+    xs, ws = np.polynomial.hermite_e.hermegauss(nodes)
+    ws = ws / ws.sum()
+    acc = torch.zeros(ham.N, ham.N, dtype=CT)
+    for idx in itertools.product(range(nodes), repeat=ham.G):
+        c = torch.tensor([xs[i] for i in idx], dtype=CT)
+        acc = acc + float(np.prod([ws[i] for i in idx])) * torch.linalg.matrix_exp(R.field_matrix(ham, c, tau))
+    return acc
+
+
+def test_hubbard_stratonovich_average_of_the_field_propagator():
+    """Sec. II.A: the Gaussian average of e^{i sqrt(tau) sum_g x_g L_g} is
+    e^{-tau/2 sum_g L_g^2}: exactly for one Cholesky vector, and up to O(tau^2)
+    for two non-commuting ones (halving tau divides the error by about 4)."""
+    s1 = make_system(4, 1, 1, 1, rho=0.5, seed=21)
+    ham1 = R.make_hamiltonian(s1.h1, s1.L, s1.trial, 1, 1)
+    for tau in (0.05, 0.2):
+        L = ham1.L[0].to(CT)
+        want = torch.linalg.matrix_exp(-0.5 * tau * L @ L)
+        got = _gauss_average(ham1, tau, 60)
+        assert float((got - want).abs().max()) < 1e-12
+    s2 = make_system(4, 1, 1, 2, rho=0.8, seed=22)
+    ham2 = R.make_hamiltonian(s2.h1, s2.L, s2.trial, 1, 1)
+    L2 = ham2.L.to(CT)
+    comm = float((L2[0] @ L2[1] - L2[1] @ L2[0]).abs().max())
+    assert comm > 1e-2                                   # the two vectors do not commute
+    errs = []
+    for tau in (0.1, 0.05, 0.025):
+        want = torch.linalg.matrix_exp(-0.5 * tau * (L2[0] @ L2[0] + L2[1] @ L2[1]))
+        errs.append(float((_gauss_average(ham2, tau, 24) - want).abs().max()))
+    for a, b in zip(errs, errs[1:]):
+        assert 3.2 < a / b < 4.8, errs
+
+
 def test_half_step_squares_to_one_body_exponential():
     s, ham = _small_ham()
     hpp, _ = R.propagation_h1(ham)
