@@ -116,7 +116,7 @@ typedef struct {
  *               per walker; expm and order are checked but not used; a
  *               singular 1 - X/2 leaves the walker non-finite, so the weight
  *               update kills it); other values: AFQMC_ENOTSUP
- *   expm        AFQMC_EXPM_TAYLOR (order = Taylor order k >= 0),
+ *   expm        AFQMC_EXPM_TAYLOR (order = Taylor order 0 <= k <= 64),
  *               AFQMC_EXPM_KRYLOV (order = Krylov dimension 1 <= k <= 32, one
  *               Krylov space per orbital column, Eq. krylov),
  *               AFQMC_EXPM_CHEBYSHEV (order = expansion order 0 <= k <= 64,

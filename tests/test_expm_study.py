@@ -20,6 +20,21 @@ def _setup():
     return s, octx, e0
 
 
+def test_order_limits_match_the_header():
+    """The study tries each action up to the largest order afqmc_step accepts,
+    as the header states it."""
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "include", "afqmc.h")).read()
+    for name, macro in (("taylor", "TAYLOR"), ("krylov", "KRYLOV"), ("chebyshev", "CHEBYSHEV"),
+                        ("bkrylov", "BLOCK_KRYLOV")):
+        m = re.search(r"AFQMC_EXPM_" + macro + r" \(order = [^)]*?(\d+) <= k <= (\d+)", hdr)
+        assert m is not None, name
+        assert S.K_MAX[name] == int(m.group(2)), name
+    assert S.REFERENCE == ("taylor", S.K_MAX["taylor"])
+
+
 def test_reference_run_is_the_exact_exponential():
     """The order-64 Taylor reference equals the run with the exact action
     (the oracle's eigendecomposition/matrix_exp) and with Krylov at dimension N."""
