@@ -485,16 +485,17 @@ def tau_scan(dev, imag_time=10.0, taus=(0.01, 0.02, 0.05, 0.1), nw=1024):
     every 5 steps, FP64): for each tau, imag_time / tau steps of 1024 walkers
     with E_L every step, comb population control every 10 steps and E_0
     updates, the first 30 % as equilibration; the blocking analysis of each
-    run and the fit E(tau) = E_0 + beta tau^2 for Split-2.  The same series with
-    Split-1, whose time-step error is linear, is fitted by E_0 + alpha tau: both
-    fits estimate the same E_0."""
+    run and the fits E(tau) = E_0 + beta tau^2 and E_0 + alpha tau + beta tau^2
+    (Eq. square_fit) for Split-2.  A Split-1 series, whose time-step error is
+    linear, runs at tau < 0.05 (the range the paper fits linearly) and is fitted
+    by E_0 + alpha tau: the fits estimate the same E_0."""
     import torch
     from paper_2403_02542_gb300 import energy as S
     from paper_2403_02542_gb300.api import Context
     from paper_2403_02542_gb300.inputs import config_system
     s = config_system("small")
 
-    def series(propagator, seed_base):
+    def series(propagator, seed_base, taus):
         runs = []
         total_steps = 0
         for i, tau in enumerate(taus):
@@ -530,13 +531,17 @@ def tau_scan(dev, imag_time=10.0, taus=(0.01, 0.02, 0.05, 0.1), nw=1024):
                 ("sigma_beta" if power == 2 else "sigma_alpha"): sc, "chi2_dof": chi2}
 
     t0 = time.perf_counter()
-    runs, total_steps = series("split2", 100)
+    runs, total_steps = series("split2", 100, taus)
     wall = time.perf_counter() - t0
+    general = S.fit_time_step([r["tau"] for r in runs], [r["E"] for r in runs], [r["sigma"] for r in runs], (1, 2))
     out = {"workload": "small workload (N=8, Na=Nb=2, N_gamma=32, lambda_g=0.5^g), FP64, 1024 walkers, "
                        "Split-2 + Taylor-6, QR every 5, comb every 10 steps, E_0 updated, imaginary time 10 per tau",
-           "runs": runs, "fit": fit(runs, 2), "wall_s": wall, "walker_steps_per_s": nw * total_steps / wall}
+           "runs": runs, "fit": fit(runs, 2),
+           "fit_general": {"E0": general["E0"], "alpha": general["c"][0], "beta": general["c"][1],
+                           "sigma_E0": general["sigma_E0"], "chi2_dof": general["chi2_dof"]},
+           "wall_s": wall, "walker_steps_per_s": nw * total_steps / wall}
     try:
-        runs1, _ = series("split1", 300)
+        runs1, _ = series("split1", 300, (0.005, 0.01, 0.02, 0.04))
         f1 = fit(runs1, 1)
         out["split1"] = {"runs": runs1, "fit": f1,
                          "E0_difference_sigmas": (f1["E0"] - out["fit"]["E0"])

@@ -1,7 +1,8 @@
 """Energy runs and their statistics: the time average of the mixed estimator
 with its variance and correlation length (Sec. II.A), and the time-step
-extrapolation E(tau) = E_0 + beta tau^2 (Split-2, quadratic) or E_0 + alpha tau
-(linear) (Sec. VI).
+extrapolation E(tau) = E_0 + alpha tau + beta tau^2 (Eq. square_fit) or its
+pure quadratic (Split-2, Taylor propagator) and linear (Split-1,
+Crank-Nicolson) forms (Sec. VI).
 
 Readings where the paper leaves the procedure open:
   * the correlation length kappa of the variance sigma_Ebar^2 = sigma_E^2 kappa / N
@@ -70,24 +71,37 @@ def blocking(W, E, n_eq: int = 0, min_blocks: int = 8):
     return dict(E_bar=ebar, sigma_E2=var, block=chosen[0], sigma=sigma, kappa=kappa, levels=levels, n=n)
 
 
+def fit_time_step(taus, energies, sigmas=None, powers=(1, 2)):
+    """Weighted least-squares fit E(tau) = E_0 + sum_p c_p tau^p over the given
+    powers (Sec. VI): (1, 2) is the general form E_0 + alpha tau + beta tau^2 of
+    Eq. square_fit, (2,) the pure quadratic of Split-2 and the Taylor propagator,
+    (1,) the linear form of Split-1 and Crank-Nicolson.  Returns a dict with E_0,
+    the coefficients c [per power], their standard errors, and chi^2 per
+    degree of freedom (None without a spare point)."""
+    t = np.asarray(taus, dtype=np.float64)
+    y = np.asarray(energies, dtype=np.float64)
+    powers = tuple(powers)
+    if t.size < 1 + len(powers):
+        raise ValueError("need at least one time step per fitted coefficient")
+    s = np.ones_like(y) if sigmas is None else np.asarray(sigmas, dtype=np.float64)
+    X = np.stack([np.ones_like(t)] + [t ** p for p in powers], axis=1)
+    wgt = 1.0 / (s * s)
+    cov = np.linalg.inv(X.T @ (X * wgt[:, None]))
+    coef = cov @ (X.T @ (wgt * y))
+    resid = y - X @ coef
+    dof = t.size - X.shape[1]
+    chi2 = float((wgt * resid * resid).sum() / dof) if dof > 0 else None
+    err = np.sqrt(np.diag(cov))
+    return {"E0": float(coef[0]), "sigma_E0": float(err[0]), "powers": powers,
+            "c": [float(v) for v in coef[1:]], "sigma_c": [float(v) for v in err[1:]], "chi2_dof": chi2}
+
+
 def extrapolate(taus, energies, sigmas=None, power: int = 2):
     """Weighted least-squares fit E(tau) = E_0 + c tau^power (power 2: Split-2 and
     the Taylor propagator; power 1: Split-1 and Crank-Nicolson).  Returns
     (E_0, c, sigma_E0, sigma_c, chi2 per degree of freedom or None)."""
-    t = np.asarray(taus, dtype=np.float64)
-    y = np.asarray(energies, dtype=np.float64)
-    if t.size < 2:
-        raise ValueError("need at least two time steps")
-    s = np.ones_like(y) if sigmas is None else np.asarray(sigmas, dtype=np.float64)
-    X = np.stack([np.ones_like(t), t ** power], axis=1)
-    wgt = 1.0 / (s * s)
-    F = X.T @ (X * wgt[:, None])
-    cov = np.linalg.inv(F)
-    beta = cov @ (X.T @ (wgt * y))
-    resid = y - X @ beta
-    dof = t.size - 2
-    chi2 = float((wgt * resid * resid).sum() / dof) if dof > 0 else None
-    return float(beta[0]), float(beta[1]), math.sqrt(cov[0, 0]), math.sqrt(cov[1, 1]), chi2
+    f = fit_time_step(taus, energies, sigmas, (power,))
+    return f["E0"], f["c"][0], f["sigma_E0"], f["sigma_c"][0], f["chi2_dof"]
 
 
 def energy_run(ctx, walkers, tau: float, e0: float, n_steps: int, *, fields, n_eq: int = 0,

@@ -73,6 +73,29 @@ def test_extrapolation_errors_match_the_scatter():
     assert np.mean(chis) == pytest.approx(1.0, rel=0.06)
 
 
+def test_general_time_step_fit_recovers_linear_and_quadratic_terms():
+    """Eq. square_fit, E(tau) = E_0 + alpha tau + beta tau^2: exact data give back
+    all three coefficients; noisy replicas scatter as the reported errors; the
+    pure forms are the special cases with one power."""
+    taus = np.array([0.005, 0.01, 0.02, 0.05, 0.1, 0.2])
+    e0, a, b = -40.125, -0.35, 2.5
+    f = S.fit_time_step(taus, e0 + a * taus + b * taus ** 2, None, (1, 2))
+    assert f["E0"] == pytest.approx(e0, abs=1e-11)
+    assert f["c"] == pytest.approx([a, b], rel=1e-9) and f["chi2_dof"] == pytest.approx(0.0, abs=1e-18)
+    one = S.fit_time_step(taus, e0 + b * taus ** 2, None, (2,))
+    assert (one["E0"], one["c"][0]) == pytest.approx((e0, b), rel=1e-12)
+    assert one["E0"] == pytest.approx(S.extrapolate(taus, e0 + b * taus ** 2, None, 2)[0], abs=0)
+    rng = np.random.default_rng(8)
+    sig = np.full(taus.size, 1e-3)
+    fits = [S.fit_time_step(taus, e0 + a * taus + b * taus ** 2 + sig * rng.standard_normal(taus.size), sig)
+            for _ in range(3000)]
+    e0s = np.array([q["E0"] for q in fits])
+    assert np.std(e0s) == pytest.approx(fits[0]["sigma_E0"], rel=0.06)
+    assert np.mean([q["chi2_dof"] for q in fits]) == pytest.approx(1.0, rel=0.06)
+    with pytest.raises(ValueError):
+        S.fit_time_step(taus[:2], [1.0, 2.0], None, (1, 2))
+
+
 def test_energy_run_driver_follows_its_protocol_on_the_oracle():
     """energy_run's host logic (steps with E_L every step, QR every 3 steps, the
     comb every 4 steps with numbers from PCG64(seed), E_0 updates at each comb)
