@@ -528,7 +528,8 @@ def tau_scan(dev, imag_time=10.0, taus=(0.01, 0.02, 0.05, 0.1), nw=1024):
         e0, c, s0, sc, chi2 = S.extrapolate([r["tau"] for r in runs], [r["E"] for r in runs],
                                             [r["sigma"] for r in runs], power)
         return {"E0": e0, ("beta" if power == 2 else "alpha"): c, "sigma_E0": s0,
-                ("sigma_beta" if power == 2 else "sigma_alpha"): sc, "chi2_dof": chi2}
+                ("sigma_beta" if power == 2 else "sigma_alpha"): sc, "chi2_dof": chi2,
+                "sigma_x": S.extrapolation_error([r["sigma"] for r in runs])}
 
     t0 = time.perf_counter()
     runs, total_steps = series("split2", 100, taus)

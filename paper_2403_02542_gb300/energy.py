@@ -96,6 +96,17 @@ def fit_time_step(taus, energies, sigmas=None, powers=(1, 2)):
             "c": [float(v) for v in coef[1:]], "sigma_c": [float(v) for v in err[1:]], "chi2_dof": chi2}
 
 
+def extrapolation_error(sigmas) -> float:
+    """The paper's estimate of the statistical error of an extrapolated energy
+    (Eq. staterr): sigma_x = sqrt(sum_i sigma_i^2) / N_tau over the N_tau time
+    steps of the fit, sigma_i their 1-sigma errors.  (fit_time_step also reports
+    the least-squares standard error of E_0, which weighs the points.)"""
+    s = np.asarray(sigmas, dtype=np.float64)
+    if s.size == 0:
+        raise ValueError("no time steps")
+    return float(math.sqrt((s * s).sum()) / s.size)
+
+
 def extrapolate(taus, energies, sigmas=None, power: int = 2):
     """Weighted least-squares fit E(tau) = E_0 + c tau^power (power 2: Split-2 and
     the Taylor propagator; power 1: Split-1 and Crank-Nicolson).  Returns

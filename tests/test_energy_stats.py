@@ -96,6 +96,15 @@ def test_general_time_step_fit_recovers_linear_and_quadratic_terms():
         S.fit_time_step(taus[:2], [1.0, 2.0], None, (1, 2))
 
 
+def test_extrapolation_error_of_eq_staterr():
+    """sigma_x = sqrt(sum sigma_i^2) / N_tau: equal errors give sigma / sqrt(N_tau);
+    a worked case sqrt(9 + 16) / 2 = 2.5."""
+    assert S.extrapolation_error([0.2] * 4) == pytest.approx(0.2 / 2.0, rel=1e-15)
+    assert S.extrapolation_error([3.0, 4.0]) == pytest.approx(2.5, rel=1e-15)
+    with pytest.raises(ValueError):
+        S.extrapolation_error([])
+
+
 def test_energy_run_driver_follows_its_protocol_on_the_oracle():
     """energy_run's host logic (steps with E_L every step, QR every 3 steps, the
     comb every 4 steps with numbers from PCG64(seed), E_0 updates at each comb)
