@@ -488,20 +488,23 @@ def tau_scan(dev, imag_time=10.0, taus=(0.01, 0.02, 0.05, 0.1), nw=1024):
     run and the fits E(tau) = E_0 + beta tau^2 and E_0 + alpha tau + beta tau^2
     (Eq. square_fit) for Split-2.  A Split-1 series, whose time-step error is
     linear, runs at tau < 0.05 (the range the paper fits linearly) and is fitted
-    by E_0 + alpha tau: the fits estimate the same E_0."""
+    by E_0 + alpha tau: the fits estimate the same E_0.  The same time steps
+    then run on the large workload (N=128, 20+20, 640 vectors) in mixed
+    precision with Split-2 + Krylov 10."""
     import torch
     from paper_2403_02542_gb300 import energy as S
     from paper_2403_02542_gb300.api import Context
     from paper_2403_02542_gb300.inputs import config_system
     s = config_system("small")
 
-    def series(propagator, seed_base, taus):
+    def series(propagator, seed_base, taus, sys_=s, precision="fp64", expm="taylor", order=6):
+        s = sys_
         runs = []
         total_steps = 0
         for i, tau in enumerate(taus):
             n_steps = int(round(imag_time / tau))
             n_eq = int(0.3 * n_steps)
-            ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision="fp64", device=dev)
+            ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision=precision, device=dev)
             w = ctx.new_walkers(nw)
             ctx.init_walkers(w)
             el = torch.empty(nw, 2, dtype=torch.float64, device=dev)
@@ -514,9 +517,9 @@ def tau_scan(dev, imag_time=10.0, taus=(0.01, 0.02, 0.05, 0.1), nw=1024):
             def fields(k):
                 return x.normal_(generator=gen)
 
-            out = S.energy_run(ctx, w, tau, float(em[2]), n_steps, fields=fields, n_eq=n_eq, expm="taylor",
-                               order=6, reortho_every=5, pop_every=10, seed=seed_base + 100 + i, update_e0=True,
-                               propagator=propagator)
+            out = S.energy_run(ctx, w, tau, float(em[2]), n_steps, fields=fields, n_eq=n_eq, expm=expm,
+                               order=order, reortho_every=5, pop_every=10, seed=seed_base + 100 + i,
+                               update_e0=True, propagator=propagator)
             st = out["stats"]
             runs.append({"tau": tau, "steps": n_steps, "E": st["E_bar"], "sigma": st["sigma"],
                          "kappa": st["kappa"]})
@@ -549,6 +552,22 @@ def tau_scan(dev, imag_time=10.0, taus=(0.01, 0.02, 0.05, 0.1), nw=1024):
                          / max(1e-300, (f1["sigma_E0"] ** 2 + out["fit"]["sigma_E0"] ** 2) ** 0.5)}
     except Exception as exc:  # noqa: BLE001 - the Split-2 series stands on its own
         out["split1"] = {"error": f"{type(exc).__name__}: {exc}"}
+    # the large workload over the same time steps, mixed precision, Split-2 + Krylov 10
+    try:
+        t1 = time.perf_counter()
+        runs_l, steps_l = series("split2", 500, taus, config_system("large"), "mixed", "krylov", 10)
+        wall_l = time.perf_counter() - t1
+        gen_l = S.fit_time_step([r["tau"] for r in runs_l], [r["E"] for r in runs_l],
+                                [r["sigma"] for r in runs_l], (1, 2))
+        out["large"] = {"workload": "large workload (N=128, Na=Nb=20, N_gamma=640), mixed, 1024 walkers, "
+                                    "Split-2 + Krylov 10, QR every 5, comb every 10 steps, E_0 updated, "
+                                    "imaginary time 10 per tau",
+                        "runs": runs_l, "fit": fit(runs_l, 2),
+                        "fit_general": {"E0": gen_l["E0"], "alpha": gen_l["c"][0], "beta": gen_l["c"][1],
+                                        "sigma_E0": gen_l["sigma_E0"], "chi2_dof": gen_l["chi2_dof"]},
+                        "wall_s": wall_l, "walker_steps_per_s": nw * steps_l / wall_l}
+    except Exception as exc:  # noqa: BLE001 - the small-workload series stand on their own
+        out["large"] = {"error": f"{type(exc).__name__}: {exc}"}
     return out
 
 
