@@ -480,7 +480,7 @@ def expm_accuracy(dev, nw=2400, n_steps=10, taus=(0.02, 0.1, 0.3), budget_s=60.0
 
 
 def tau_scan(dev, imag_time=10.0, taus=(0.01, 0.02, 0.05, 0.1), nw=1024):
-    """Energy runs and the time-step extrapolation (Sec. VI) on the small
+    """Energy runs and the time-step extrapolation (Sec. V.G) on the small
     workload (N=8, 2+2 electrons, 32 vectors lambda_g = 0.5^g, Taylor-6, QR
     every 5 steps, FP64): for each tau, imag_time / tau steps of 1024 walkers
     with E_L every step, comb population control every 10 steps and E_0

@@ -18,7 +18,9 @@
  *                                   (Sec. III.A, III.C, III.D)
  *   overlap ratio, hybrid energy    (Eqs. hyben, theta)
  *   phaseless weight with capping   (Eq. phaseless; Sec. V.B)
- *   optional re-orthonormalisation  (modified Gram-Schmidt; Sec. IV.D)
+ *   optional re-orthonormalisation  (modified Gram-Schmidt per spin; the
+ *                                   QR of Sec. IV.D, Psi = B_1 R, applied
+ *                                   to the walkers)
  *   optional local energy, capping  (Eq. eloc, Eq. enwin) and the mixed
  *   and mixed estimator              estimator E_k (Sec. II.A).
  *

@@ -46,6 +46,8 @@ Readings of the paper used here (the paper is silent or ambiguous on them):
   R8  Population control: comb with caller-supplied uniform u.
   R9  Threshold tests use the strict inequalities printed in Sec. V.
   R11 The mixed estimator and the energy window use Re E_L.
+  R25 The walkers are re-orthonormalised every r steps (a caller's choice) by
+      modified Gram-Schmidt per spin; the paper does not discuss it.
 """
 from __future__ import annotations
 
@@ -429,8 +431,9 @@ def mixed_energy(W, e_loc_capped):
 
 
 # --------------------------------------------------------------------------
-# Re-orthonormalisation (Sec. IV.D: orbitals must be orthogonalised under
-# imaginary-time propagation)
+# Re-orthonormalisation (reading R25: the paper is silent on the periodic
+# orthonormalisation of the walkers; its only QR of Psi is the block-Krylov
+# start Psi = B_1 R of Sec. IV.D, which is the same factorisation)
 # --------------------------------------------------------------------------
 def mgs_qr(X):
     """Modified Gram-Schmidt QR of the columns of X ([N, n]) -> (Q, R)."""

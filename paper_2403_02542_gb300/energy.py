@@ -2,7 +2,7 @@
 with its variance and correlation length (Sec. II.A), and the time-step
 extrapolation E(tau) = E_0 + alpha tau + beta tau^2 (Eq. square_fit) or its
 pure quadratic (Split-2, Taylor propagator) and linear (Split-1,
-Crank-Nicolson) forms (Sec. VI).
+Crank-Nicolson) forms (Sec. V.G).
 
 Readings where the paper leaves the procedure open:
   * the correlation length kappa of the variance sigma_Ebar^2 = sigma_E^2 kappa / N
@@ -73,7 +73,7 @@ def blocking(W, E, n_eq: int = 0, min_blocks: int = 8):
 
 def fit_time_step(taus, energies, sigmas=None, powers=(1, 2)):
     """Weighted least-squares fit E(tau) = E_0 + sum_p c_p tau^p over the given
-    powers (Sec. VI): (1, 2) is the general form E_0 + alpha tau + beta tau^2 of
+    powers (Sec. V.G): (1, 2) is the general form E_0 + alpha tau + beta tau^2 of
     Eq. square_fit, (2,) the pure quadratic of Split-2 and the Taylor propagator,
     (1,) the linear form of Split-1 and Crank-Nicolson.  Returns a dict with E_0,
     the coefficients c [per power], their standard errors, and chi^2 per
