@@ -319,9 +319,13 @@ def _gauss_average(ham, tau, nodes):
 
 
 def test_hubbard_stratonovich_average_of_the_field_propagator():
-    """Sec. II.A: the Gaussian average of e^{i sqrt(tau) sum_g x_g L_g} is
+    """Eq. hstrafo: the Gaussian average of e^{i sqrt(tau) sum_g x_g L_g} is
     e^{-tau/2 sum_g L_g^2}: exactly for one Cholesky vector, and up to O(tau^2)
-    for two non-commuting ones (halving tau divides the error by about 4)."""
+    for two non-commuting ones (halving tau divides the error by about 4).  The
+    tau^2 term is the one printed in Eq. hserror: with e^{-tau H_2} = average +
+    tau^2 E_HS + O(tau^3) (Sec. III), (average - e^{-tau H_2}) / tau^2 tends to
+    -E_HS, E_HS = 1/48 sum_{g != g'} {L_g L_g', [L_g', L_g]}
+    + 1/24 sum_{g != g'} [L_g, [L_g, L_g'^2]], the residual shrinking like tau."""
     s1 = make_system(4, 1, 1, 1, rho=0.5, seed=21)
     ham1 = R.make_hamiltonian(s1.h1, s1.L, s1.trial, 1, 1)
     for tau in (0.05, 0.2):
@@ -340,6 +344,21 @@ def test_hubbard_stratonovich_average_of_the_field_propagator():
         errs.append(float((_gauss_average(ham2, tau, 24) - want).abs().max()))
     for a, b in zip(errs, errs[1:]):
         assert 3.2 < a / b < 4.8, errs
+
+    def cm(a, b):
+        return a @ b - b @ a
+    E_hs = torch.zeros_like(L2[0])
+    for g in range(2):
+        for h in range(2):
+            if g != h:
+                E_hs = E_hs + (L2[g] @ L2[h] @ cm(L2[h], L2[g]) + cm(L2[h], L2[g]) @ L2[g] @ L2[h]) / 48 \
+                    + cm(L2[g], cm(L2[g], L2[h] @ L2[h])) / 24
+    res = []
+    for tau in (0.01, 0.005):
+        want = torch.linalg.matrix_exp(-0.5 * tau * (L2[0] @ L2[0] + L2[1] @ L2[1]))
+        res.append(float(((_gauss_average(ham2, tau, 30) - want) / tau ** 2 + E_hs).abs().max()))
+    assert res[0] < 0.01 * float(E_hs.abs().max())
+    assert 1.7 < res[0] / res[1] < 2.3, res
 
 
 def test_half_step_squares_to_one_body_exponential():
