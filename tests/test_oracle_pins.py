@@ -361,6 +361,57 @@ def test_hubbard_stratonovich_average_of_the_field_propagator():
     assert 1.7 < res[0] / res[1] < 2.3, res
 
 
+def test_field_averaged_propagators_have_the_printed_tau2_errors():
+    """Sec. III: averaged over the fields (Gauss-Hermite, two non-commuting
+    Cholesky vectors), each propagator differs from U = e^{-tau (H_1 + H_2)},
+    H_2 = 1/2 sum_g L_g^2, by tau^2 E + O(tau^3) with the leading terms the paper
+    prints: Split-2 E_HS; Split-1 1/2 [H_1, H_2] + E_HS; Taylor propagator
+    1/12 sum_g [[L_g, H_1], L_g] + E_HS; Crank-Nicolson 1/4 {H_1, H_2} +
+    1/8 sum_g [[L_g, H_1], L_g] + its HS part.  E_HS enters with the sign of
+    Eq. hstrafo (reading R26), and the Crank-Nicolson HS part is
+    H_2^2 - 3 E_HS (reading R27).  (U_P - U) / tau^2 - E falls like tau."""
+    s2 = make_system(4, 1, 1, 2, rho=0.8, seed=22)
+    ham = R.make_hamiltonian(s2.h1, s2.L, s2.trial, 1, 1)
+    L = ham.L.to(CT)
+    g = torch.Generator().manual_seed(5)
+    K = torch.randn(4, 4, generator=g, dtype=RT)
+    K = 0.5 * (K + K.T)                                 # H_1, a one-body matrix
+    Kc = K.to(CT)
+    H2 = 0.5 * (L[0] @ L[0] + L[1] @ L[1])
+    eye = torch.eye(4, dtype=CT)
+
+    def cm(a, b):
+        return a @ b - b @ a
+    E_hs = sum((L[a] @ L[b] @ cm(L[b], L[a]) + cm(L[b], L[a]) @ L[a] @ L[b]) / 48
+               + cm(L[a], cm(L[a], L[b] @ L[b])) / 24 for a in range(2) for b in range(2) if a != b)
+    LHL = sum(cm(cm(L[a], Kc), L[a]) for a in range(2))
+    import itertools
+    xs, ws = np.polynomial.hermite_e.hermegauss(30)
+    ws = ws / ws.sum()
+
+    def average(prop, tau):
+        acc = torch.zeros(4, 4, dtype=CT)
+        for i, j in itertools.product(range(30), repeat=2):
+            A = R.field_matrix(ham, torch.tensor([xs[i], xs[j]], dtype=CT), tau)
+            acc = acc + float(ws[i] * ws[j]) * prop(A, tau)
+        return acc
+    cases = {
+        "split2": (lambda A, t: R.split2_propagate(R.half_step_propagator(K, t), A, eye, "exact", 0), -E_hs),
+        "split1": (lambda A, t: R.split1_propagate(R.half_step_propagator(K, t), A, eye, "exact", 0),
+                   0.5 * cm(Kc, H2) - E_hs),
+        "taylor": (lambda A, t: R.taylor_propagate(K, A, eye, t, 40), LHL / 12 - E_hs),
+        "cn": (lambda A, t: R.crank_nicolson_propagate(K, A, eye, t),
+               0.25 * (Kc @ H2 + H2 @ Kc) + LHL / 8 + H2 @ H2 - 3 * E_hs),
+    }
+    for name, (prop, E) in cases.items():
+        res = []
+        for tau in (0.01, 0.005):
+            U = torch.linalg.matrix_exp(-tau * (Kc + H2))
+            res.append(float(((average(prop, tau) - U) / tau ** 2 - E).abs().max()))
+        assert res[0] < 0.1 * float(E.abs().max()), (name, res)
+        assert 1.7 < res[0] / res[1] < 2.3, (name, res)
+
+
 def test_half_step_squares_to_one_body_exponential():
     s, ham = _small_ham()
     hpp, _ = R.propagation_h1(ham)
