@@ -31,7 +31,7 @@ Readings of the paper used here (the paper is silent or ambiguous on them):
       invariant subspace is declared when the new subdiagonal entry is
       <= 1e-12 ||A||_F (the basis vectors are unit vectors).
   R6  The small exponential e^{A_k} is torch.linalg.matrix_exp.
-  R20 Block Krylov (Sec. IV, Eqs. bkrylovsub-bkrylov) works on each spin
+  R20 Block Krylov (Sec. IV.D, Eqs. bkrylovsub-bkrylov) works on each spin
       block separately (the two determinants span separate spaces); the QR
       of Psi and of every new block is modified Gram-Schmidt (mgs_qr), the
       new block is orthogonalised against the previous ones by one block
