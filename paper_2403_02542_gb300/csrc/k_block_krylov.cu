@@ -1,4 +1,4 @@
-// Block-Krylov action of the exponential (Sec. IV, Eqs. bkrylovsub-bkrylov)
+// Block-Krylov action of the exponential (Sec. IV.D, Eqs. bkrylovsub-bkrylov)
 // for every walker and spin block: Psi_s = B_1 R (QR), the orthonormal basis
 // B_k = [B_1 .. B_k] of span{Psi_s, A Psi_s, .., A^{k-1} Psi_s} by block
 // Arnoldi, the block upper Hessenberg A_k = B_k^dagger A B_k, and
