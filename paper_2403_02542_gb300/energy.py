@@ -117,7 +117,8 @@ def extrapolate(taus, energies, sigmas=None, power: int = 2):
 
 def energy_run(ctx, walkers, tau: float, e0: float, n_steps: int, *, fields, n_eq: int = 0,
                expm: str = "krylov", order: int = 10, reortho_every: int = 5, pop_every: int = 0,
-               seed: int = 0, update_e0: bool = False, reuse_bias: bool = False, propagator: str = "split2"):
+               seed: int = 0, update_e0: bool = False, reuse_bias: bool = False, propagator: str = "split2",
+               group=None):
     """Propagate `walkers` for n_steps steps of the library with the local energy
     measured every step.  fields(k) returns the device fields [Nw, G] of step k.
     propagator selects the walker update of Sec. III (see Context.step); fit
@@ -126,27 +127,53 @@ def energy_run(ctx, walkers, tau: float, e0: float, n_steps: int, *, fields, n_e
     With pop_every > 0 the population is combed after every pop_every steps
     (uniform numbers from numpy's PCG64 seeded with `seed`).  Returns a dict
     with the per-step total weight W, mixed estimate E and E_0 used, and the
-    blocking analysis of the steps after n_eq."""
+    blocking analysis of the steps after n_eq.
+
+    group: a torch.distributed process group whose ranks each propagate their
+    own walkers (the population sharded by walkers).  Every step then
+    all-reduces [sum W E_k, sum W] once, so W and E are the whole population's
+    (W_local and E_local keep this rank's); each rank combs its own walkers
+    with numbers from PCG64([seed, rank]) (the comb keeps each rank's total
+    weight, so the global estimate needs no further exchange); E_0 is updated
+    from the global estimates and stays the same on every rank.  With an NCCL
+    group the two numbers are reduced on ctx's device."""
     import torch
     nw = walkers.n
     dev = ctx.device
     e_loc = torch.empty(nw, 2, dtype=torch.float64, device=dev)
     e_mix = torch.empty(4, dtype=torch.float64, device=dev)
-    rng = np.random.Generator(np.random.PCG64(seed))
-    Ws, Es, E0s = [], [], []
+    if group is None:
+        rng = np.random.Generator(np.random.PCG64(seed))
+    else:
+        import torch.distributed as dist
+        rng = np.random.Generator(np.random.PCG64([seed, dist.get_rank(group)]))
+        red_dev = dev if dist.get_backend(group) == "nccl" else torch.device("cpu")
+    Ws, Es, E0s, Wl, El = [], [], [], [], []
     for k in range(n_steps):
         reo = reortho_every > 0 and (k + 1) % reortho_every == 0
         ctx.step(walkers, fields(k), tau, e0, expm=expm, order=order, reortho=reo, measure=True,
                  e_loc=e_loc, e_mix=e_mix, reuse_bias=reuse_bias, propagator=propagator)
         m = e_mix.cpu()
         E0s.append(e0)
-        Ws.append(float(m[1]))
-        Es.append(float(m[2]))
+        w_k, e_k = float(m[1]), float(m[2])
+        if group is None:
+            Ws.append(w_k)
+            Es.append(e_k)
+        else:
+            Wl.append(w_k)
+            El.append(e_k)
+            t = torch.tensor([w_k * e_k if w_k > 0 else 0.0, w_k], dtype=torch.float64, device=red_dev)
+            dist.all_reduce(t, group=group)
+            t = t.cpu()
+            Ws.append(float(t[1]))
+            Es.append(float(t[0] / t[1]) if float(t[1]) > 0 else float("nan"))
         if pop_every > 0 and (k + 1) % pop_every == 0:
             ctx.population_control(walkers, float(rng.random()))
             if update_e0:
                 e0 = Es[-1] if k < n_eq else time_average(Ws, Es, n_eq)[0]
     out = dict(W=Ws, E=Es, e0=E0s)
+    if group is not None:
+        out["W_local"], out["E_local"] = Wl, El
     if n_steps - n_eq >= 16:
         out["stats"] = blocking(Ws, Es, n_eq)
     return out
