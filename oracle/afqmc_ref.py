@@ -66,7 +66,7 @@ __all__ = [
     "taylor_action", "chebyshev_coefficients", "chebyshev_action", "krylov_action", "block_krylov_action", "exact_action", "expm_action",
     "split2_propagate", "split1_propagate", "taylor_propagate", "crank_nicolson_propagate", "propagate",
     "local_energy", "energy_window", "mixed_energy",
-    "mgs_qr", "reorthonormalise", "weight_update", "step", "init_walkers",
+    "mgs_qr", "reorthonormalise", "weight_update", "propagate_and_ratio", "step", "init_walkers",
     "free_projection_step", "comb", "population_control", "StepInfo",
     "walk_objective",
 ]
@@ -507,6 +507,33 @@ def init_walkers(ham: Hamiltonian, n_walkers):
     return psi, log_overlap(ham, psi), W
 
 
+def propagate_and_ratio(ham: Hamiltonian, psi, logovl, x, tau, method, k, B, L_bar, ec,
+                        hpp=None, propagator="split2"):
+    """The part of one step that the phaseless and the free-projection walks
+    share: force bias, field matrix, walker update, and the two factors of the
+    weight.
+
+    f_g = -i sqrt(tau)(<L_g> - L_bar_g), capped (Eq. force_shift, Sec. V.C);
+    c_g = x_g - f_g and A = i sqrt(tau) sum_g c_g L_g (Eq. heffTOT);
+    Psi' = U Psi (Eq. psiupdate, Sec. III);
+    log ratio = log<Psi_T|Psi'> - log<Psi_T|Psi> + log s with the scalar
+    s = exp(-tau E_c' - i sqrt(tau) sum_g c_g L_bar_g) of reading R1;
+    log I = sum_g (x_g f_g - f_g^2 / 2), the importance factor that goes with
+    the shifted fields (Eq. wupdate).
+    Returns (psi', logovl', log_ratio, log_I, f, f_uncapped).
+    """
+    x = torch.as_tensor(x, dtype=RT)
+    f, f_raw = force_bias(ham, psi, tau, L_bar)                     # Eq. force_shift
+    c = x.to(CT) - f
+    A = field_matrix(ham, c, tau)                                   # Eq. heffTOT
+    psi_new = propagate(propagator, B, hpp, A, psi, tau, method, k, ham.spins())   # Eq. psiupdate
+    logovl_new = log_overlap(ham, psi_new)
+    log_s = -tau * ec - 1j * math.sqrt(tau) * (c @ L_bar.to(CT))
+    log_ratio = logovl_new - logovl + log_s
+    log_I = (x.to(CT) * f - 0.5 * f * f).sum(-1)                    # importance factor
+    return psi_new, logovl_new, log_ratio, log_I, f, f_raw
+
+
 def step(ham: Hamiltonian, psi, logovl, W, x, tau, e0, method="krylov", k=10,
          reortho=False, B=None, L_bar=None, ec=None, propagator="split2"):
     """One phaseless walker step (by default with the Split-2 propagator;
@@ -522,15 +549,8 @@ def step(ham: Hamiltonian, psi, logovl, W, x, tau, e0, method="krylov", k=10,
     if B is None or ec is None or propagator in ("taylor", "cn"):
         hpp, ec = propagation_h1(ham, L_bar)
         B = half_step_propagator(hpp, tau) if B is None else B
-    x = torch.as_tensor(x, dtype=RT)
-    f, f_raw = force_bias(ham, psi, tau, L_bar)                     # Eq. force_shift
-    c = x.to(CT) - f
-    A = field_matrix(ham, c, tau)                                   # Eq. heffTOT
-    psi_new = propagate(propagator, B, hpp, A, psi, tau, method, k, ham.spins())   # Eq. psiupdate
-    logovl_new = log_overlap(ham, psi_new)
-    log_s = -tau * ec - 1j * math.sqrt(tau) * (c @ L_bar.to(CT))
-    log_ratio = logovl_new - logovl + log_s
-    log_I = (x.to(CT) * f - 0.5 * f * f).sum(-1)                    # importance factor
+    psi_new, logovl_new, log_ratio, log_I, f, f_raw = propagate_and_ratio(
+        ham, psi, logovl, x, tau, method, k, B, L_bar, ec, hpp, propagator)
     W_new, e_h, dth, fac = weight_update(W, log_ratio, log_I, tau, e0)
     if reortho:
         psi_new, logovl_new = reorthonormalise(ham, psi_new)
@@ -547,22 +567,16 @@ def free_projection_step(ham: Hamiltonian, psi, logovl, weight, x, tau, e0,
                          method="taylor", k=6, B=None, L_bar=None, ec=None):
     """Free-projection step (Eqs. psiupdate, wupdate): complex weight, no phaseless cut.
 
-    weight' = weight * ratio * I * e^{tau E0} = weight e^{-tau(E_H - E0)}.
+    weight' = weight * ratio * I * e^{tau E0} = weight e^{-tau(E_H - E0)}, with
+    the ratio and I of `propagate_and_ratio`, the same code as the phaseless step.
     """
     if L_bar is None:
         L_bar = mean_field_shift(ham)
     if B is None or ec is None:
         hpp, ec = propagation_h1(ham, L_bar)
         B = half_step_propagator(hpp, tau)
-    x = torch.as_tensor(x, dtype=RT)
-    f, _ = force_bias(ham, psi, tau, L_bar)
-    c = x.to(CT) - f
-    A = field_matrix(ham, c, tau)
-    psi_new = split2_propagate(B, A, psi, method, k, ham.spins())
-    logovl_new = log_overlap(ham, psi_new)
-    log_s = -tau * ec - 1j * math.sqrt(tau) * (c @ L_bar.to(CT))
-    log_ratio = logovl_new - logovl + log_s
-    log_I = (x.to(CT) * f - 0.5 * f * f).sum(-1)
+    psi_new, logovl_new, log_ratio, log_I, _, _ = propagate_and_ratio(
+        ham, psi, logovl, x, tau, method, k, B, L_bar, ec)
     return psi_new, logovl_new, weight * torch.exp(log_ratio + log_I + tau * e0)
 
 

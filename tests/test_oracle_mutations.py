@@ -3,6 +3,8 @@ wrong sign, an order off by one, a missing conjugate, a stale value), planted
 in the oracle on the CPU by replacing one function, makes the named pin of
 tests/test_oracle_pins.py fail.  The oracle itself is untouched outside each
 test (monkeypatch restores it)."""
+import math
+
 import pytest
 import torch
 
@@ -17,6 +19,36 @@ def _split1_one_half_step(orig):
         return B.to(CT) @ R.expm_action(A, psi, method, k, spins)
     return bad
 
+
+def _ratio_mutant(change):
+    """Replace propagate_and_ratio by one whose outputs pass through `change`
+    (called with the original's arguments and its output tuple)."""
+    def make(orig):
+        def bad(*args, **kw):
+            return change(args, orig(*args, **kw))
+        return bad
+    return make
+
+
+def _with(out, **repl):
+    names = ("psi", "logovl", "log_ratio", "log_I", "f", "f_raw")
+    return tuple(repl.get(n, v) for n, v in zip(names, out))
+
+
+# arguments of propagate_and_ratio: (ham, psi, logovl, x, tau, method, k, B, L_bar, ec, ...)
+_STEP_MUTANTS = [
+    ("step: importance factor with the wrong sign",
+     lambda a, o: _with(o, log_I=-o[3])),
+    ("step: importance factor without the 1/2",
+     lambda a, o: _with(o, log_I=o[3] - 0.5 * (o[4] * o[4]).sum(-1))),
+    ("step: scalar s from x instead of c = x - f",
+     lambda a, o: _with(o, log_ratio=o[2] - 1j * math.sqrt(a[4]) * (o[4] @ a[8].to(CT)))),
+    ("step: scalar s with +i sqrt(tau) c.L_bar",
+     lambda a, o: _with(o, log_ratio=o[2] + 2j * math.sqrt(a[4])
+                        * ((torch.as_tensor(a[3]).to(CT) - o[4]) @ a[8].to(CT)))),
+    ("step: scalar s with +tau E_c'",
+     lambda a, o: _with(o, log_ratio=o[2] + 2 * a[4] * a[9])),
+]
 
 # (mistake, oracle function, replacement built from the original, pin that must fail)
 MUTATIONS = [
@@ -91,6 +123,8 @@ MUTATIONS = [
     ("comb teeth shifted by half a spacing", "comb",
      lambda o: lambda W, u: o(W, (u + 0.5) % 1.0), "test_comb_example"),
 ]
+MUTATIONS += [(m, "propagate_and_ratio", _ratio_mutant(ch),
+               "test_importance_sampled_step_keeps_the_gaussian_average") for m, ch in _STEP_MUTANTS]
 
 
 @pytest.mark.parametrize("mistake,name,make,pin", MUTATIONS, ids=[m[0] for m in MUTATIONS])
