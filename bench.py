@@ -507,9 +507,6 @@ def tau_scan(dev, imag_time=10.0, taus=(0.01, 0.02, 0.05, 0.1), nw=1024):
             ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision=precision, device=dev)
             w = ctx.new_walkers(nw)
             ctx.init_walkers(w)
-            el = torch.empty(nw, 2, dtype=torch.float64, device=dev)
-            em = torch.empty(4, dtype=torch.float64, device=dev)
-            ctx.local_energy(w, 0.0, tau, el, em)
             gen = torch.Generator(device=dev)
             gen.manual_seed(seed_base + i)
             x = torch.empty(nw, s.G, dtype=torch.float64, device=dev)
@@ -517,7 +514,8 @@ def tau_scan(dev, imag_time=10.0, taus=(0.01, 0.02, 0.05, 0.1), nw=1024):
             def fields(k):
                 return x.normal_(generator=gen)
 
-            out = S.energy_run(ctx, w, tau, float(em[2]), n_steps, fields=fields, n_eq=n_eq, expm=expm,
+            # E_0 starts at the uncapped mean E_L of the starting walkers (initial_e0)
+            out = S.energy_run(ctx, w, tau, None, n_steps, fields=fields, n_eq=n_eq, expm=expm,
                                order=order, reortho_every=5, pop_every=10, seed=seed_base + 100 + i,
                                update_e0=True, propagator=propagator)
             st = out["stats"]

@@ -364,8 +364,12 @@ afqmc_status afqmc_walk_backward(afqmc_ctx* ctx, const afqmc_walkers* initial, c
  *   Nw*nc*N*c (c = 16 for FP64, 8 for mixed contexts) + Nw*32 + Nw*128
  *   + Nw*G*64 + Nw*8 bytes, plus 2 * (8*Nw*na*Kp) bytes (Kp = N rounded up to
  *   a multiple of 64) for mixed contexts whose exchange term runs on the
- *   tensor cores (na == nb <= 64, N <= 128); a call needing more than
- *   AFQMC_STATIC_SCRATCH_BYTES returns AFQMC_EINVAL and launches nothing.
+ *   tensor cores (every mixed context with 1 <= na == nb <= 64, whatever N);
+ *   a call needing more than AFQMC_STATIC_SCRATCH_BYTES returns AFQMC_EINVAL
+ *   and launches nothing.
+ * The call must be made with the context's device current (the device that
+ * was current at afqmc_create); from any other device it returns
+ * AFQMC_EINVAL and launches nothing.
  * The first call on a device looks up the array's device address on the
  * current device (cudaGetSymbolAddress); make that first call before any
  * stream capture.  All calls share the one array and it keeps the contents of
@@ -373,7 +377,8 @@ afqmc_status afqmc_walk_backward(afqmc_ctx* ctx, const afqmc_walkers* initial, c
  * first, so nothing needs clearing.  Calls whose work overlaps on the GPU
  * (different streams, contexts or host threads without ordering) race on the
  * array and give wrong results.
- * Errors: EINVAL (null outputs, misaligned buffers, too large), EDOM, ECUDA. */
+ * Errors: EINVAL (null outputs, misaligned buffers, too large, not the
+ * context's device), EDOM, ECUDA. */
 afqmc_status afqmc_local_energy_static(afqmc_ctx* ctx, const afqmc_walkers* w, double e0, double tau,
                                        double* e_loc, double* e_mix);
 
@@ -398,8 +403,14 @@ enum {
  * stops.  afqmc_profile_read synchronises the stream, folds the recorded
  * event pairs into the accumulators and returns, per class, the summed
  * milliseconds ms[AFQMC_K_COUNT] and the number of launches n[AFQMC_K_COUNT].
- * Errors: EINVAL, ENOMEM, ECUDA. */
+ * afqmc_profile_mask does the same for the classes whose bit (1 << class) is
+ * set in mask and records nothing around the other launches (mask 0 stops;
+ * afqmc_profile(ctx, 1) is afqmc_profile_mask(ctx, (1 << AFQMC_K_COUNT) - 1)),
+ * so that one kernel class can be timed inside a run without event pairs
+ * around every other launch.
+ * Errors: EINVAL (also: mask bits beyond AFQMC_K_COUNT), ENOMEM, ECUDA. */
 afqmc_status afqmc_profile(afqmc_ctx* ctx, int enable);
+afqmc_status afqmc_profile_mask(afqmc_ctx* ctx, uint32_t mask);
 afqmc_status afqmc_profile_read(afqmc_ctx* ctx, double* ms, uint64_t* n);
 
 /* Number of kernel launches the context has issued so far. */

@@ -229,9 +229,17 @@ class Context:
         L.check(L.lib().afqmc_tune_get(self._h, table), "afqmc_tune_get")
         return list(table)
 
-    def profile(self, enable: bool):
-        """Start (clearing) or stop per-kernel-class event timing (afqmc_profile)."""
-        L.check(L.lib().afqmc_profile(self._h, int(bool(enable))), "afqmc_profile")
+    def profile(self, enable: bool, classes=None):
+        """Start (clearing) or stop per-kernel-class event timing: every class
+        (afqmc_profile), or only the named ones of L.KERNEL_CLASSES
+        (afqmc_profile_mask)."""
+        if classes is None or not enable:
+            L.check(L.lib().afqmc_profile(self._h, int(bool(enable))), "afqmc_profile")
+            return
+        mask = 0
+        for name in classes:
+            mask |= 1 << L.KERNEL_CLASSES.index(name)
+        L.check(L.lib().afqmc_profile_mask(self._h, mask), "afqmc_profile_mask")
 
     def profile_read(self) -> dict:
         """{class: (total ms, launches)} accumulated since profile(True)."""

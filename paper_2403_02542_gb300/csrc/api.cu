@@ -216,7 +216,7 @@ cudaError_t prepare_kernels(afqmc_ctx* c) {
 namespace afq {
 void prof_mark(afqmc_ctx* c, int cls, bool begin, cudaStream_t s) {
   Prof& p = c->prof;
-  if (!p.on) return;
+  if (!p.on || !((p.mask >> cls) & 1u)) return;
   if (begin) {
     if (p.used >= p.cap) { p.open_cls = -1; return; }
     cudaEventRecord(p.pool[2 * p.used], s);
@@ -1139,6 +1139,10 @@ afqmc_status afqmc_create(afqmc_ctx** out, int N, int n_alpha, int n_beta, int n
   c->N = N; c->na = n_alpha; c->nb = n_beta; c->nc = (int)nc; c->G = n_chol; c->prec = precision;
   c->e_const = e_const;
   c->stream = static_cast<cudaStream_t>(stream);
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    delete c;
+    return AFQMC_ECUDA;
+  }
   afqmc_status st = ctx_setup(c, h1, L, trial);
   if (st != AFQMC_OK) {
     ctx_free(c);
@@ -1370,9 +1374,14 @@ afqmc_status afqmc_sync(afqmc_ctx* c) {
 uint64_t afqmc_launch_count(const afqmc_ctx* c) { return c ? c->launches : 0; }
 
 afqmc_status afqmc_profile(afqmc_ctx* c, int enable) {
+  return afqmc_profile_mask(c, enable ? (1u << AFQMC_K_COUNT) - 1u : 0u);
+}
+
+afqmc_status afqmc_profile_mask(afqmc_ctx* c, uint32_t mask) {
   if (!c) return AFQMC_EINVAL;
+  if (mask >> AFQMC_K_COUNT) return AFQMC_EINVAL;
   Prof& p = c->prof;
-  if (enable) {
+  if (mask) {
     if (!p.pool) {
       const int cap = 32768;
       p.pool = (cudaEvent_t*)calloc((size_t)2 * cap, sizeof(cudaEvent_t));
@@ -1392,6 +1401,7 @@ afqmc_status afqmc_profile(afqmc_ctx* c, int enable) {
     p.used = 0;
     p.open_cls = -1;
     for (int k = 0; k < AFQMC_K_COUNT; ++k) { p.ms[k] = 0.0; p.n[k] = 0; }
+    p.mask = mask;
     p.on = true;
   } else {
     p.on = false;

@@ -125,6 +125,7 @@ namespace afq {
 // Kernel-class event profiler (see afqmc_profile in the header).
 struct Prof {
   bool on = false;
+  uint32_t mask = 0;            // bit k: record launches of class k
   cudaEvent_t* pool = nullptr;  // 2 events per recorded launch
   int* cls = nullptr;           // class of each recorded launch
   int cap = 0, used = 0, open_cls = -1;
@@ -216,6 +217,7 @@ struct afqmc_ctx {
   int tune[afq::N_SITES] = {0, 0, 0, 4};  // GEMM tile variant per call site
   bool capturing = false;                  // inside a graph capture (afqmc_batch_step)
   uint64_t launches = 0;
+  int device = -1;                         // CUDA device current at afqmc_create (holds the context's memory)
 };
 
 namespace afq {

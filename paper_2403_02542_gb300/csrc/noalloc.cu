@@ -58,9 +58,13 @@ extern "C" afqmc_status afqmc_local_energy_static(afqmc_ctx* c, const afqmc_walk
   const size_t need = b_theta + b_logdet + b_scal + b_epart + b_ecap + 2 * b_plane;
   if (need > kScratchBytes) return AFQMC_EINVAL;  // beyond AFQMC_STATIC_SCRATCH_BYTES
 
-  // device address of the array on the current device, resolved once per device
+  // device address of the array on the current device, resolved once per device.
+  // The context's memory and stream belong to the device that was current at
+  // afqmc_create; the array's address is per device, so a call from another
+  // device is refused before anything is launched.
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return AFQMC_ECUDA;
+  if (dev != c->device) return AFQMC_EINVAL;
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_scratch_mu);

@@ -115,7 +115,23 @@ def extrapolate(taus, energies, sigmas=None, power: int = 2):
     return f["E0"], f["c"][0], f["sigma_E0"], f["sigma_c"][0], f["chi2_dof"]
 
 
-def energy_run(ctx, walkers, tau: float, e0: float, n_steps: int, *, fields, n_eq: int = 0,
+def initial_e0(ctx, walkers, tau: float) -> float:
+    """A starting E_0 for a run: the weighted mean of Re E_L over the live
+    walkers, uncapped.  (A local energy evaluated with some other E_0 is
+    clamped to that E_0 +- DeltaE by Eq. enwin, so its mixed estimate is not a
+    usable seed when |E| is large against DeltaE.)"""
+    import torch
+    e_loc = torch.empty(walkers.n, 2, dtype=torch.float64, device=ctx.device)
+    e_mix = torch.empty(4, dtype=torch.float64, device=ctx.device)
+    ctx.local_energy(walkers, 0.0, tau, e_loc, e_mix)
+    W = walkers.weight.double()
+    live = W > 0
+    if not bool(live.any()):
+        raise ValueError("initial_e0: no walker has a positive weight")
+    return float((W[live] * e_loc[live, 0]).sum() / W[live].sum())
+
+
+def energy_run(ctx, walkers, tau: float, e0, n_steps: int, *, fields, n_eq: int = 0,
                expm: str = "krylov", order: int = 10, reortho_every: int = 5, pop_every: int = 0,
                seed: int = 0, update_e0: bool = False, reuse_bias: bool = False, propagator: str = "split2",
                group=None):
@@ -128,6 +144,10 @@ def energy_run(ctx, walkers, tau: float, e0: float, n_steps: int, *, fields, n_e
     (uniform numbers from numpy's PCG64 seeded with `seed`).  Returns a dict
     with the per-step total weight W, mixed estimate E and E_0 used, and the
     blocking analysis of the steps after n_eq.
+
+    e0: the starting E_0, or None to take it from the uncapped local energies
+    of the starting walkers (initial_e0; with a group, the weighted mean over
+    all ranks).
 
     group: a torch.distributed process group whose ranks each propagate their
     own walkers (the population sharded by walkers).  Every step then
@@ -148,6 +168,21 @@ def energy_run(ctx, walkers, tau: float, e0: float, n_steps: int, *, fields, n_e
         import torch.distributed as dist
         rng = np.random.Generator(np.random.PCG64([seed, dist.get_rank(group)]))
         red_dev = dev if dist.get_backend(group) == "nccl" else torch.device("cpu")
+    if e0 is None:
+        if group is None:
+            e0 = initial_e0(ctx, walkers, tau)
+        else:
+            e_loc0 = torch.empty(nw, 2, dtype=torch.float64, device=dev)
+            e_mix0 = torch.empty(4, dtype=torch.float64, device=dev)
+            ctx.local_energy(walkers, 0.0, tau, e_loc0, e_mix0)
+            W0 = walkers.weight.double()
+            live = W0 > 0
+            t = torch.stack([(W0[live] * e_loc0[live, 0]).sum(), W0[live].sum()]).to(red_dev)
+            dist.all_reduce(t, group=group)
+            t = t.cpu()
+            if not float(t[1]) > 0:
+                raise ValueError("energy_run: no walker has a positive weight")
+            e0 = float(t[0] / t[1])
     Ws, Es, E0s, Wl, El = [], [], [], [], []
     for k in range(n_steps):
         reo = reortho_every > 0 and (k + 1) % reortho_every == 0
@@ -170,6 +205,9 @@ def energy_run(ctx, walkers, tau: float, e0: float, n_steps: int, *, fields, n_e
         if pop_every > 0 and (k + 1) % pop_every == 0:
             ctx.population_control(walkers, float(rng.random()))
             if update_e0:
+                if not (Ws[-1] > 0 and math.isfinite(Es[-1])):
+                    raise RuntimeError(f"energy_run: the population has died at step {k} "
+                                       f"(total weight {Ws[-1]}, E_k {Es[-1]}); E_0 cannot be updated")
                 e0 = Es[-1] if k < n_eq else time_average(Ws, Es, n_eq)[0]
     out = dict(W=Ws, E=Es, e0=E0s)
     if group is not None:

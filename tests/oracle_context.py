@@ -22,7 +22,7 @@ class OracleContext:
         self._B = {}
 
     def new_walkers(self, n):
-        return SimpleNamespace(n=n, psi=None, lo=None, W=None)
+        return _Walkers(n)
 
     def init_walkers(self, w):
         w.psi, w.lo, w.W = R.init_walkers(self.ham, w.n)
@@ -45,10 +45,35 @@ class OracleContext:
                 e_mix[1] = float(wsum)
                 e_mix[2] = float(emix)
 
+    def local_energy(self, w, e0, tau, e_loc=None, e_mix=None):
+        El = R.local_energy(self.ham, w.psi)
+        emix, wsum = R.mixed_energy(w.W, R.energy_window(El, e0, tau, self.ham.na + self.ham.nb))
+        if e_loc is None:
+            e_loc = torch.empty(w.n, 2, dtype=torch.float64)
+        if e_mix is None:
+            e_mix = torch.zeros(4, dtype=torch.float64)
+        e_loc[:, 0] = El.real
+        e_loc[:, 1] = El.imag
+        e_mix[1] = float(wsum)
+        e_mix[2] = float(emix)
+        return e_loc, e_mix
+
     def population_control(self, w, u, index_out=None):
         w.psi, w.lo, w.W, idx = R.population_control(w.psi, w.lo, w.W, u)
         if index_out is not None:
             index_out.copy_(idx)
+
+
+class _Walkers(SimpleNamespace):
+    """Oracle walkers (psi, log-overlap, weights); `weight` names W as the
+    library's walker set does."""
+
+    def __init__(self, n):
+        super().__init__(n=n, psi=None, lo=None, W=None)
+
+    @property
+    def weight(self):
+        return self.W
 
 
 def field_fn(seed, nw, G, device=None):

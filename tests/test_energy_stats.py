@@ -130,3 +130,51 @@ def test_energy_run_driver_follows_its_protocol_on_the_oracle():
     assert out["e0"][:4] == [e0] * 4
     assert out["e0"][4] == pytest.approx(Er[3], rel=1e-14)
     assert out["e0"][8] == pytest.approx(S.time_average(Wr[:8], Er[:8], n_eq)[0], rel=1e-14)
+
+
+def test_energy_run_seeds_e0_from_the_uncapped_local_energy():
+    """With e0=None the run starts from the weighted mean of the uncapped E_L
+    of its starting walkers (initial_e0).  On a system whose energy lies far
+    outside the window DeltaE around 0, an E_0 taken from a mixed estimate
+    clamped around 0 would be wrong by many DeltaE; the seeded run instead
+    equals the protocol started at E_L(Psi_T) step for step."""
+    import torch
+    from oracle import afqmc_ref as R
+    from oracle_context import OracleContext
+    from paper_2403_02542_gb300.inputs import make_fields, make_system
+    from walk_helpers import oracle_energy_run
+    s = make_system(8, 2, 2, 32, rho=0.5, seed=20240304)
+    nw, tau, n_steps, n_eq, order, reo, pop, seed, fseed = 10, 0.04, 8, 4, 6, 3, 4, 6, 78
+    octx = OracleContext(s)
+    e_trial = float(R.local_energy(octx.ham, octx.ham.trial.to(torch.complex128)).real)
+    dE = 0.5 * math.sqrt(4 / tau) + math.sqrt(4 * tau)
+    assert abs(e_trial) > dE                 # E_L lies outside the window around 0
+    w = octx.new_walkers(nw)
+    octx.init_walkers(w)
+    assert S.initial_e0(octx, w, tau) == pytest.approx(e_trial, rel=1e-13)
+    Wr, Er = oracle_energy_run(s, nw, tau, e_trial, n_steps, n_eq, order, reo, pop, seed, fseed)
+    out = S.energy_run(octx, w, tau, None, n_steps, fields=lambda k: torch.as_tensor(make_fields(fseed, k, nw, s.G)),
+                       n_eq=n_eq, order=order, reortho_every=reo, pop_every=pop, seed=seed, update_e0=True)
+    assert out["e0"][0] == pytest.approx(e_trial, rel=1e-13)
+    assert out["W"] == pytest.approx(Wr, rel=1e-12)
+    assert out["E"] == pytest.approx(Er, rel=1e-12)
+    assert all(x > 0 for x in out["W"])
+
+
+def test_energy_run_reports_a_dead_population():
+    """A population whose total weight is 0 at a comb cannot update E_0: the
+    run stops with an error naming the step instead of passing a NaN E_0 on
+    to the next step; a run asked to seed E_0 from such a population refuses."""
+    import torch
+    from oracle_context import OracleContext
+    from paper_2403_02542_gb300.inputs import make_fields, make_system
+    s = make_system(8, 2, 2, 32, rho=0.5, seed=20240304)
+    octx = OracleContext(s)
+    w = octx.new_walkers(4)
+    octx.init_walkers(w)
+    w.W = torch.zeros(4, dtype=torch.float64)
+    with pytest.raises(ValueError, match="positive weight"):
+        S.initial_e0(octx, w, 0.05)
+    with pytest.raises(RuntimeError, match="died at step 1"):
+        S.energy_run(octx, w, 0.05, -7.0, 4, fields=lambda k: torch.as_tensor(make_fields(1, k, 4, s.G)),
+                     order=6, pop_every=2, seed=1, update_e0=True)
