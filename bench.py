@@ -1,13 +1,17 @@
 #!/usr/bin/env python
-"""Walker-steps/s of the ph-AFQMC walker step (Split-2 + Krylov + E_loc).
+"""Walker-steps/s of the ph-AFQMC walker step (Split-2 + Krylov + E_loc),
+mixed precision against FP64.
 
-Workload (large-step plain method): synthetic Hamiltonian with N=128 orbitals,
-20+20 electrons, 640 Cholesky vectors (lambda_g = rho^g, rho = 1e-5^(1/640)),
-RHF trial, 1024 walkers per GPU, tau = 0.05, Split-2 with the Krylov action
-of dimension 10, local energy and mixed estimator every step, modified
-Gram-Schmidt every 5 steps.  One step = one pass of the whole walker step over
-all walkers.  Multi-GPU (torchrun): every rank propagates its own walkers
-(weak scaling, no collective on the data path).
+Headline workload (precision form): synthetic Hamiltonian with N=300
+orbitals, 50+50 electrons, 1500 Cholesky vectors (lambda_g = rho^g,
+rho = 1e-5^(1/1500)), RHF trial, 2048 walkers per GPU, tau = 0.05, Split-2
+with the Krylov action of dimension 10, local energy and mixed estimator every
+step, modified Gram-Schmidt every 5 steps, complex64 walkers (mixed path).
+One step = one pass of the whole walker step over all walkers.  Beside it: the
+FP64 path on the same workload, the large-step workload (N=128, 20+20, 640
+vectors, 1024 walkers) and the other legs listed in run_ours.  Multi-GPU
+(torchrun): every rank propagates its own walkers (weak scaling, no collective
+on the data path).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|fp64]
   python bench.py --impl reference ...   # the CPU oracle, timed on host cores
@@ -18,6 +22,7 @@ import argparse
 import json
 import math
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -28,9 +33,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "walker-steps/s (Split-2+Krylov+E_loc), mixed vs FP64 at ≤1e-4 Ha/walker"
-WORKLOAD = ("large-step plain method: N=128, Na=Nb=20, N_gamma=640 (decay rho=1e-5^(1/640)), "
-            "1024 walkers/GPU, tau=0.05, Split-2 + Krylov dim 10, E_loc every step, MGS every 5 steps")
-NW, TAU, KDIM, REORTHO = 1024, 0.05, 10, 5
+HEADLINE = "precision"   # inputs.CONFIGS key of the headline workload
+WORKLOAD = ("precision form: N=300, Na=Nb=50, N_gamma=1500 (decay rho=1e-5^(1/1500)), 2048 walkers/GPU, "
+            "tau=0.05, Split-2 + Krylov dim 10, E_loc every step, MGS every 5 steps, complex64 walkers")
+NW, TAU, KDIM, REORTHO = 2048, 0.05, 10, 5
+LARGE_NW = 1024          # walkers of the large-step workload (N=128) legs
 # peaks for the roofline denominators
 NOMINAL_FP64_TFLOPS = 1.25          # GB300 FP64 (recipe table)
 SM_COUNT, SM_MAX_MHZ = 152, 2070.0  # recipe table
@@ -58,8 +65,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched workload (16 uneven systems in one graph)")
-    ap.add_argument("--no-precision", action="store_true",
-                    help="skip the precision workload (N=300, mixed vs FP64)")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the large-step workload (N=128, 1024 walkers) rates")
+    ap.add_argument("--no-precision-errors", action="store_true",
+                    help="skip the per-result error of the mixed path against the FP64 path")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the timed gradient of the differentiation workload")
     ap.add_argument("--no-block-krylov", action="store_true",
@@ -71,9 +80,11 @@ def parse():
                     help="skip the k_min study of the exponential actions (Fig. 1 analogue)")
     ap.add_argument("--no-tau-scan", action="store_true",
                     help="skip the energy runs and time-step extrapolation of the small workload")
-    ap.add_argument("--cpu-sample-walkers", type=int, default=4)
+    ap.add_argument("--cpu-sample-walkers", type=int, default=1)
     ap.add_argument("--walkers", type=int, default=NW,
-                    help="walkers per GPU (the workload has 1024; fewer only for small profiling cases)")
+                    help="walkers per GPU (the workload has 2048; fewer only for small profiling cases)")
+    ap.add_argument("--only-headline", action="store_true",
+                    help="time the headline workload and nothing else (profiling runs)")
     return ap.parse_args()
 
 
@@ -155,9 +166,22 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ CPU oracle
-def oracle_rate(system, n_walkers: int, n_steps: int, precision_note: str):
-    """Time the CPU oracle as it stands on a bounded sample of the workload."""
-    import numpy as np
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu on Linux, else the platform string)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.processor() or platform.machine()
+
+
+def oracle_rate(system, n_walkers: int, n_steps: int, tau: float = TAU):
+    """Time the CPU oracle as it stands on a bounded sample of the workload:
+    n_walkers walkers for n_steps steps (Split-2 + Krylov 10, E_L every step),
+    walker by walker.  Returns the cpu_baseline object and the per-step times."""
     import torch
 
     from oracle import afqmc_ref as R
@@ -166,7 +190,7 @@ def oracle_rate(system, n_walkers: int, n_steps: int, precision_note: str):
     ham = R.make_hamiltonian(system.h1, system.L, system.trial, system.na, system.nb)
     Lbar = R.mean_field_shift(ham)
     hpp, ec = R.propagation_h1(ham, Lbar)
-    B = R.half_step_propagator(hpp, TAU)
+    B = R.half_step_propagator(hpp, tau)
     psi, lo, W = R.init_walkers(ham, n_walkers)
     e0 = float(R.local_energy(ham, psi[:1]).real[0])
     t0 = time.perf_counter()
@@ -174,25 +198,25 @@ def oracle_rate(system, n_walkers: int, n_steps: int, precision_note: str):
     for k in range(n_steps):
         ts = time.perf_counter()
         x = make_fields(99, k, n_walkers, ham.G)
-        psi, lo, W, _ = R.step(ham, psi, lo, W, x, TAU, e0, method="krylov", k=KDIM,
+        psi, lo, W, _ = R.step(ham, psi, lo, W, x, tau, e0, method="krylov", k=KDIM,
                                reortho=(k + 1) % REORTHO == 0, B=B, L_bar=Lbar, ec=ec)
         El = R.local_energy(ham, psi)
-        R.mixed_energy(W, R.energy_window(El, e0, TAU, ham.na + ham.nb))
+        R.mixed_energy(W, R.energy_window(El, e0, tau, ham.na + ham.nb))
         per_step.append(time.perf_counter() - ts)
     dt = time.perf_counter() - t0
     return dict(value=n_walkers * n_steps / dt, unit="walker-steps/s", cores=torch.get_num_threads(),
-                kind="oracle",
-                sample=f"{n_walkers} walkers x {n_steps} steps of the same workload (FP64 oracle, "
-                       f"walker-by-walker Krylov), {dt:.1f} s"), per_step
+                host_cores=os.cpu_count(), cpu_model=cpu_model(), kind="oracle",
+                sample=f"{n_walkers} walker(s) x {n_steps} steps of the same workload (FP64 oracle, "
+                       f"walker-by-walker Krylov, E_L every step), {dt:.1f} s"), per_step
 
 
-def config_dict(precision: str, world: int):
-    wl = WORKLOAD if NW == 1024 else WORKLOAD.replace("1024 walkers/GPU", f"{NW} walkers/GPU (reduced)")
-    return {"workload": wl, "walkers_per_gpu": NW, "N": 128, "na": 20, "nb": 20, "G": 640,
+def config_dict(precision: str, world: int, nw: int):
+    wl = WORKLOAD if nw == NW else WORKLOAD.replace(f"{NW} walkers/GPU", f"{nw} walkers/GPU (reduced)")
+    return {"workload": wl, "walkers_per_gpu": nw, "N": 300, "na": 50, "nb": 50, "G": 1500,
             "tau": TAU, "expm": "krylov", "krylov_dim": KDIM, "reortho_every": REORTHO,
             "precision": precision, "parallelism": f"walkers sharded over {world} GPU(s)",
             "force_bias": "<L_g> of each step from the Coulomb traces of the previous step's E_L (same walkers)",
-            "l2": "working set larger than L2 (walkers, Krylov basis, A_w > 129 MB)"}
+            "l2": "working set larger than L2 (walkers 0.49 GB, Krylov basis, A_w planes > 129 MB)"}
 
 
 # ------------------------------------------------------------------ reference arm
@@ -203,10 +227,10 @@ def run_reference(args):
     import torch
 
     from paper_2403_02542_gb300.inputs import config_system
-    system = config_system("large")
-    nwalk = 2
+    system = config_system(HEADLINE)
+    nwalk = 1
     total_steps = args.warmup + args.steps
-    _, per_step = oracle_rate(system, nwalk, total_steps, "")
+    cpu, per_step = oracle_rate(system, nwalk, total_steps)
     timed = per_step[args.warmup:]
     t = sum(timed)
     value = nwalk * len(timed) / t
@@ -215,10 +239,10 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t / len(timed),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded Hamiltonian, Gaussian fields)", "impl": "reference",
-        "config": config_dict("fp64 oracle", 1),
+        "config": config_dict("fp64 oracle", 1, NW),
         "cpu_baseline": {"value": value, "unit": "walker-steps/s", "cores": torch.get_num_threads(),
-                         "kind": "oracle",
-                         "sample": f"{nwalk} walkers per step of the same workload, {args.steps} "
+                         "host_cores": os.cpu_count(), "cpu_model": cpu["cpu_model"], "kind": "oracle",
+                         "sample": f"{nwalk} walker per step of the same workload, {args.steps} "
                                    f"timed steps after {args.warmup} warm-up steps"},
         "e2e": {"value": value, "unit": "walker-steps/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -295,54 +319,6 @@ def adjoint_rate(dev):
     }
 
 
-def precision_rate(dev):
-    """Precision workload (N=300, 50+50 electrons, 1500 vectors, Krylov 10,
-    tau=0.05, E_L every step): the mixed path on 2048 walkers and the FP64 path
-    on 512 of them (per-walker throughput; walkers are independent), CUDA-event
-    timed, one warm-up step each."""
-    import torch
-    from paper_2403_02542_gb300.api import Context
-    from paper_2403_02542_gb300.inputs import CONFIGS, config_system
-    cfg = CONFIGS["precision"]
-    s = config_system("precision")
-    out = {"workload": "precision form: N=300, Na=Nb=50, N_gamma=1500 (decay rho=1e-5^(1/1500)), tau=0.05, "
-                       "Split-2 + Krylov dim 10, E_loc every step, force bias reused from the previous E_L"}
-    stream = torch.cuda.current_stream(dev)
-    for prec, nw, steps in (("mixed", cfg["walkers"], 2), ("fp64", 512, 1)):
-        ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision=prec, device=dev)
-        w = ctx.new_walkers(nw)
-        ctx.init_walkers(w)
-        el = torch.empty(nw, 2, dtype=torch.float64, device=dev)
-        em = torch.empty(4, dtype=torch.float64, device=dev)
-        ctx.local_energy(w, 0.0, cfg["tau"], el, em)
-        e0 = float(el[0, 0])
-        gen = torch.Generator(device=dev)
-        gen.manual_seed(7)
-        x = torch.randn(steps + 1, nw, s.G, dtype=torch.float64, device=dev, generator=gen)
-        ctx.step(w, x[0], cfg["tau"], e0, expm="krylov", order=cfg["order"], measure=True, e_loc=el, e_mix=em,
-                 reuse_bias=True)
-        torch.cuda.synchronize()
-        ctx.profile(True)
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for k in range(steps):
-            ctx.step(w, x[1 + k], cfg["tau"], e0, expm="krylov", order=cfg["order"], measure=True, e_loc=el,
-                     e_mix=em, reuse_bias=True)
-        a1.record(stream)
-        torch.cuda.synchronize()
-        ctx.profile(False)
-        prof = ctx.profile_read()
-        ms = a0.elapsed_time(a1) / steps
-        out[prec] = {"walkers": nw, "steps": steps, "ms_per_step": ms, "value": nw / (ms / 1000.0),
-                     "unit": "walker-steps/s", "e_mix": float(em[2]),
-                     "kernel_ms_per_step": {k: v[0] / steps for k, v in prof.items()}}
-        ctx.close()
-        del w, x
-        torch.cuda.empty_cache()
-    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
-    return out
-
-
 def block_krylov_rate(dev, steps=5):
     """The large-step workload (N=128, 20+20 electrons, 640 vectors, 1024
     walkers, tau=0.05, E_L every step, MGS every 5 steps) with the block-Krylov
@@ -355,15 +331,15 @@ def block_krylov_rate(dev, steps=5):
     s = config_system("large")
     k = 4
     ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision="mixed", device=dev)
-    w = ctx.new_walkers(NW)
+    w = ctx.new_walkers(LARGE_NW)
     ctx.init_walkers(w)
-    el = torch.empty(NW, 2, dtype=torch.float64, device=dev)
+    el = torch.empty(LARGE_NW, 2, dtype=torch.float64, device=dev)
     em = torch.empty(4, dtype=torch.float64, device=dev)
     ctx.local_energy(w, 0.0, TAU, el, em)
     e0 = float(el[0, 0])
     gen = torch.Generator(device=dev)
     gen.manual_seed(11)
-    x = torch.randn(steps + 2, NW, s.G, dtype=torch.float64, device=dev, generator=gen)
+    x = torch.randn(steps + 2, LARGE_NW, s.G, dtype=torch.float64, device=dev, generator=gen)
     stream = torch.cuda.current_stream(dev)
     for i in range(2):
         ctx.step(w, x[i], TAU, e0, expm="bkrylov", order=k, measure=True, e_loc=el, e_mix=em, reuse_bias=True)
@@ -381,7 +357,7 @@ def block_krylov_rate(dev, steps=5):
     ms = a0.elapsed_time(a1) / steps
     out = {"workload": "large-step workload (N=128, Na=Nb=20, N_gamma=640, 1024 walkers, tau=0.05, E_loc every "
                        "step, MGS every 5 steps) with block Krylov of 4 blocks, mixed",
-           "value": NW / (ms / 1000.0), "unit": "walker-steps/s", "ms_per_step": ms, "e_mix": float(em[2]),
+           "value": LARGE_NW / (ms / 1000.0), "unit": "walker-steps/s", "ms_per_step": ms, "e_mix": float(em[2]),
            "kernel_ms_per_step": {c: v[0] / steps for c, v in prof.items()}}
     ctx.close()
     return out
@@ -403,16 +379,16 @@ def propagator_rates(dev, steps=3):
                        "step, MGS every 5 steps), mixed", "unit": "walker-steps/s", "rates": {}}
     gen = torch.Generator(device=dev)
     gen.manual_seed(13)
-    x = torch.randn(steps + 2, NW, s.G, dtype=torch.float64, device=dev, generator=gen)
+    x = torch.randn(steps + 2, LARGE_NW, s.G, dtype=torch.float64, device=dev, generator=gen)
     stream = torch.cuda.current_stream(dev)
     for prop, expm, k in variants:
         name = f"{prop}+{expm}{k}" if prop != "cn" else "cn"
         ctx = None
         try:
             ctx = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision="mixed", device=dev)
-            w = ctx.new_walkers(NW)
+            w = ctx.new_walkers(LARGE_NW)
             ctx.init_walkers(w)
-            el = torch.empty(NW, 2, dtype=torch.float64, device=dev)
+            el = torch.empty(LARGE_NW, 2, dtype=torch.float64, device=dev)
             em = torch.empty(4, dtype=torch.float64, device=dev)
             ctx.local_energy(w, 0.0, TAU, el, em)
             e0 = float(el[0, 0])
@@ -428,7 +404,7 @@ def propagator_rates(dev, steps=3):
             a1.record(stream)
             torch.cuda.synchronize()
             ms = a0.elapsed_time(a1) / steps
-            out["rates"][name] = {"value": NW / (ms / 1000.0), "ms_per_step": ms, "e_mix": float(em[2])}
+            out["rates"][name] = {"value": LARGE_NW / (ms / 1000.0), "ms_per_step": ms, "e_mix": float(em[2])}
         except Exception as exc:  # noqa: BLE001 - one failing variant must not end the bench line
             out["rates"][name] = {"error": f"{type(exc).__name__}: {exc}"}
         finally:
@@ -638,6 +614,200 @@ def batched_rate(dev, steps=3, warmup=2):
     return out
 
 
+def exchange_flop_per_walker(system) -> int:
+    """Algorithmic flops of the Coulomb + exchange contraction per walker:
+    T_gs = Lh_gs Theta_s for every g and spin, G * 4 (na^2 + nb^2) * N real
+    flops (a real-times-complex multiply-add is 4 flops)."""
+    return system.G * 4 * (system.na * system.na + system.nb * system.nb) * system.N
+
+
+def exchange_peak(precision: str):
+    """Roofline denominator of the exchange kernel: (peak, bound, note)."""
+    if precision == "fp64":
+        return NOMINAL_FP64_TFLOPS, "alu", "FP64 nominal 1.25 TFLOP/s (recipe table); own FMA probe measured 1.19"
+    # BF16x3 split on tcgen05: three bf16 MMAs per algorithmic product; the kernel
+    # runs inside a long step, so the sustained bf16 figure is the denominator
+    peaks = measured_peaks()
+    bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
+    src = "MEASURED_PEAKS.json" if peaks else "fallback 1.7 PFLOP/s"
+    return bf16 / 3.0, "tensor", (f"of measured: sustained bf16 {bf16:.1f} TFLOP/s ({src}) / 3 MMA passes "
+                                  "(BF16x3 split); achieved counts algorithmic flops once")
+
+
+def make_context(dev, cfg_name, precision, nw, tune=True):
+    """Context, initialised walkers, E_L buffers and an uncapped E_0 for one workload."""
+    import torch
+    from paper_2403_02542_gb300.api import Context
+    from paper_2403_02542_gb300.inputs import config_system
+    system = config_system(cfg_name)
+    ctx = Context(system.h1, system.L, system.trial, system.na, system.nb, system.e_const,
+                  precision=precision, device=dev)
+    w = ctx.new_walkers(nw)
+    ctx.init_walkers(w)
+    el = torch.empty(nw, 2, dtype=torch.float64, device=dev)
+    em = torch.empty(4, dtype=torch.float64, device=dev)
+    ctx.local_energy(w, 0.0, TAU, el, em)
+    e0 = float(el[0, 0])            # uncapped E_L of the trial (all walkers start there)
+    tiles = ctx.autotune(nw) if tune else None
+    return system, ctx, w, el, em, e0, tiles
+
+
+class Stepper:
+    """Split-2 + Krylov 10 steps with E_L every step, MGS every REORTHO steps
+    and the force bias from the previous E_L, counting steps for the MGS
+    schedule."""
+
+    def __init__(self, ctx, w, el, em, e0):
+        self.ctx, self.w, self.el, self.em, self.e0 = ctx, w, el, em, e0
+        self.k = 0
+
+    def __call__(self, x):
+        self.k += 1
+        self.ctx.step(self.w, x, TAU, self.e0, expm="krylov", order=KDIM, reortho=(self.k % REORTHO == 0),
+                      measure=True, e_loc=self.el, e_mix=self.em, reuse_bias=True)
+
+
+def timed_steps(step, fields, first, K, stream):
+    """K steps on device-resident fields, CUDA events on the launching stream."""
+    import torch
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for i in range(K):
+        step(fields[(first + i) % fields.shape[0]])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+def class_split(ctx, step, fields, first, n, stream):
+    """Per-kernel-class device time per step from a separate, untimed pass of
+    n steps with an event pair around every launch."""
+    ctx.profile(True)
+    timed_steps(step, fields, first, n, stream)
+    ctx.profile(False)
+    return {c: v[0] / n for c, v in ctx.profile_read().items()}
+
+
+def large_rates(dev, K=10, warmup=3):
+    """The large-step workload (N=128, 20+20 electrons, 640 vectors, 1024
+    walkers, tau=0.05, Split-2 + Krylov 10, E_L every step, MGS every 5 steps):
+    the mixed path (exchange roofline and per-class split) and the FP64 path,
+    CUDA-event timed."""
+    import torch
+    out = {"workload": "large-step workload: N=128, Na=Nb=20, N_gamma=640 (rho = 1e-5^(1/640)), 1024 walkers, "
+                       "tau=0.05, Split-2 + Krylov 10, E_loc every step, MGS every 5 steps"}
+    stream = torch.cuda.current_stream(dev)
+    for prec, k in (("mixed", K), ("fp64", 3)):
+        system, ctx, w, el, em, e0, _ = make_context(dev, "large", prec, LARGE_NW)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(1234)
+        fields = torch.randn(warmup + k, LARGE_NW, system.G, dtype=torch.float64, device=dev, generator=gen)
+        step = Stepper(ctx, w, el, em, e0)
+        for i in range(warmup):
+            step(fields[i])
+        ctx.profile(True, classes=("exchange",))
+        ms = timed_steps(step, fields, warmup, k, stream) / k
+        ctx.profile(False)
+        ex_ms, ex_n = ctx.profile_read()["exchange"]
+        peak, bound, _ = exchange_peak(prec)
+        ach = exchange_flop_per_walker(system) * LARGE_NW / (ex_ms / ex_n / 1000.0) / 1e12
+        res = {"value": LARGE_NW / (ms / 1000.0), "unit": "walker-steps/s", "ms_per_step": ms, "steps": k,
+               "e_mix": float(em[2]),
+               "exchange": {"avg_launch_ms": ex_ms / ex_n, "achieved_tflops": ach, "peak": peak, "bound": bound,
+                            "frac": ach / peak}}
+        if prec == "mixed":
+            res["kernel_ms_per_step"] = class_split(ctx, step, fields, 0, 3, stream)
+        out[prec] = res
+        ctx.close()
+        del fields, w
+        torch.cuda.empty_cache()
+    out["mixed_over_fp64"] = out["mixed"]["value"] / out["fp64"]["value"]
+    return out
+
+
+def precision_errors(dev, cfg_name, nw=16, pre_steps=3):
+    """Error of the mixed path against the FP64 path (which matches the FP64
+    oracle to 1e-10) per result, from a common state: nw walkers of the
+    workload after pre_steps FP64 steps are copied into a mixed context, and
+    both contexts run one step with the same fields (Split-2 + Krylov 10,
+    force bias recomputed) and one with re-orthonormalisation.  Reported: the
+    largest |E_L| difference (the local energy of the same FP64 state through
+    the mixed kernels, and after one step), the relative errors of the weights,
+    walkers and log-overlaps after the step, and the orthonormality
+    max |Q^H Q - I| of the mixed re-orthonormalisation."""
+    import torch
+    from paper_2403_02542_gb300.api import Context
+    from paper_2403_02542_gb300.inputs import config_system, make_fields
+    s = config_system(cfg_name)
+    ctxs = {p: Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision=p, device=dev)
+            for p in ("fp64", "mixed")}
+    w64 = ctxs["fp64"].new_walkers(nw)
+    ctxs["fp64"].init_walkers(w64)
+    el = torch.empty(nw, 2, dtype=torch.float64, device=dev)
+    em = torch.empty(4, dtype=torch.float64, device=dev)
+    ctxs["fp64"].local_energy(w64, 0.0, TAU, el, em)
+    e0 = float(el[0, 0])
+    for k in range(pre_steps):
+        x = torch.as_tensor(make_fields(71, k, nw, s.G), device=dev)
+        ctxs["fp64"].step(w64, x, TAU, e0, expm="krylov", order=KDIM)
+    state = {"psi": w64.psi.clone(), "W": w64.weight.clone(), "lo": w64.logovl.clone()}
+
+    def load(ctx):
+        w = ctx.new_walkers(nw)
+        w.psi.copy_(state["psi"].to(ctx.ctype))
+        w.weight.copy_(state["W"])
+        w.logovl.copy_(state["lo"])
+        w.status.zero_()
+        return w
+
+    out = {"workload": f"{cfg_name} workload, {nw} walkers after {pre_steps} FP64 steps, tau={TAU}, "
+                       "Split-2 + Krylov 10"}
+    eloc = {}
+    res = {}
+    for p, ctx in ctxs.items():
+        w = load(ctx)
+        e_l = torch.empty(nw, 2, dtype=torch.float64, device=dev)
+        e_m = torch.empty(4, dtype=torch.float64, device=dev)
+        ctx.local_energy(w, e0, TAU, e_l, e_m)
+        eloc[p] = e_l.clone()
+        x = torch.as_tensor(make_fields(71, pre_steps, nw, s.G), device=dev)
+        ctx.step(w, x, TAU, e0, expm="krylov", order=KDIM, measure=True, e_loc=e_l, e_mix=e_m)
+        r = {"El": e_l.clone(), "W": w.weight.clone(), "lo": w.logovl.clone(),
+             "psi": w.psi.to(torch.complex128).clone(), "emix": float(e_m[2])}
+        w2 = load(ctx)
+        ctx.step(w2, x, TAU, e0, expm="krylov", order=KDIM, reortho=True)
+        r["Q"] = w2.psi.to(torch.complex128).clone()
+        res[p] = r
+    torch.cuda.synchronize()
+    a, b = res["mixed"], res["fp64"]
+    live = b["W"] > 0
+    dpsi = ((a["psi"] - b["psi"]).flatten(1).norm(dim=1) / b["psi"].flatten(1).norm(dim=1))[live]
+    dlo = (a["lo"] - b["lo"])
+    dlo_im = torch.remainder(dlo[:, 1] + math.pi, 2 * math.pi) - math.pi
+    Q = a["Q"][live]
+    orth = 0.0
+    for spin, (o, n) in enumerate(((0, s.na), (s.na, s.nb))):
+        if n:
+            q = Q[:, o:o + n, :]
+            gram = q.conj() @ q.transpose(1, 2)
+            orth = max(orth, float((gram - torch.eye(n, dtype=gram.dtype, device=dev)).abs().max()))
+    out.update({
+        "live": int(live.sum()),
+        "E_L_same_state_max_abs_Ha": float((eloc["mixed"] - eloc["fp64"]).norm(dim=1).max()),
+        "E_L_after_step_max_abs_Ha": float((a["El"] - b["El"]).norm(dim=1)[live].max()),
+        "E_k_after_step_abs_Ha": abs(a["emix"] - b["emix"]),
+        "W_after_step_max_rel": float(((a["W"] - b["W"]).abs() / b["W"])[live].max()),
+        "psi_after_step_max_rel": float(dpsi.max()),
+        "logovl_after_step_max_abs": float(torch.maximum(dlo[:, 0].abs(), dlo_im.abs())[live].max()),
+        "mgs_orthonormality_max": orth,
+    })
+    for c in ctxs.values():
+        c.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -657,61 +827,38 @@ def run_ours(args):
             B.build()
         if world > 1:
             dist.barrier()
-    from paper_2403_02542_gb300.api import Context
-    from paper_2403_02542_gb300.inputs import config_system
 
-    system = config_system("large")
-    N, G, na, nb = system.N, system.G, system.na, system.nb
-    ctx = Context(system.h1, system.L, system.trial, na, nb, system.e_const,
-                  precision=args.precision, device=dev)
-    w = ctx.new_walkers(NW)
-    ctx.init_walkers(w)
-    e_loc = torch.empty(NW, 2, dtype=torch.float64, device=dev)
-    e_mix = torch.empty(4, dtype=torch.float64, device=dev)
-    ctx.local_energy(w, 0.0, TAU, e_loc, e_mix)
-    e0 = float(e_loc[0, 0])
-    tune = ctx.autotune(NW)  # GEMM tile shape per call site (set-up, not timed)
-
+    system, ctx, w, e_loc, e_mix, e0, tune = make_context(dev, HEADLINE, args.precision, NW)
+    G = system.G
     K, Wm = args.steps, args.warmup
     gen = torch.Generator(device=dev)
     gen.manual_seed(shard_seed(1234, rank))
     fields = torch.randn(Wm + K, NW, G, dtype=torch.float64, device=dev, generator=gen)
-    step_idx = 0
-
-    def one(x):
-        nonlocal step_idx
-        step_idx += 1
-        ctx.step(w, x, TAU, e0, expm="krylov", order=KDIM, reortho=(step_idx % REORTHO == 0),
-                 measure=True, e_loc=e_loc, e_mix=e_mix, reuse_bias=True)
-
+    step = Stepper(ctx, w, e_loc, e_mix, e0)
     for i in range(Wm):
-        one(fields[i])
+        step(fields[i])
     torch.cuda.synchronize()
-
-    # -------- device-timed region: inputs resident in HBM
     stream = torch.cuda.current_stream(dev)
+
+    # -------- device-timed region: inputs resident in HBM; events recorded
+    # only around the exchange kernel (its launch time for the roofline)
     clocks = ClockSampler(local)
     if world > 1:
         dist.barrier()
-    torch.cuda.synchronize()
-    ctx.profile(True)
+    ctx.profile(True, classes=("exchange",))
     l0 = ctx.launch_count
-    ev0 = torch.cuda.Event(enable_timing=True)
-    ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    for i in range(K):
-        one(fields[Wm + i])
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    ms = slowest_rank(timed_steps(step, fields, Wm, K, stream), world, dev)
     launches = ctx.launch_count - l0
     ctx.profile(False)
-    prof = ctx.profile_read()
+    ex_ms, ex_n = ctx.profile_read()["exchange"]
     clk = clocks.stop()
-    ms = slowest_rank(ev0.elapsed_time(ev1), world, dev)
+    if world > 1:
+        dist.barrier()
     value = job_rate(NW * K, world, ms / 1000.0)
     emix_final = float(e_mix[2])
+
+    # -------- per-class split: a separate, untimed pass with events around every launch
+    split = class_split(ctx, step, fields, 0, min(K, 5), stream)
 
     # -------- end to end through the API with host buffers
     rng = np.random.default_rng(shard_seed(4321, rank))
@@ -724,7 +871,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for i in range(K):
         x_dev.copy_(host_fields[i], non_blocking=True)
-        one(x_dev)
+        step(x_dev)
         emix_host.copy_(e_mix, non_blocking=True)
         stream.synchronize()
         _ = float(emix_host[2])
@@ -733,62 +880,52 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     e2e = job_rate(NW * K, world, te)
+    del host_fields
 
     # -------- the same step replayed as a CUDA graph (one-system batch)
-    from paper_2403_02542_gb300.api import Batch
-    batch = Batch([ctx])
-    x_graph = torch.empty(NW, G, dtype=torch.float64, device=dev)
-    graph_steps = 0
+    graph_value = None
+    if not args.only_headline:
+        from paper_2403_02542_gb300.api import Batch
+        batch = Batch([ctx])
+        x_graph = torch.empty(NW, G, dtype=torch.float64, device=dev)
+        graph_steps = 0
 
-    def graph_step(i):
-        nonlocal graph_steps
-        graph_steps += 1
-        x_graph.copy_(fields[i % (Wm + K)])
-        batch.step([w], [x_graph], TAU, e0, expm="krylov", order=KDIM,
-                   reortho=(graph_steps % REORTHO == 0), measure=True, e_loc=[e_loc], e_mix=[e_mix],
-                   reuse_bias=True)
+        def graph_step(x):
+            nonlocal graph_steps
+            graph_steps += 1
+            x_graph.copy_(x)
+            batch.step([w], [x_graph], TAU, e0, expm="krylov", order=KDIM,
+                       reortho=(graph_steps % REORTHO == 0), measure=True, e_loc=[e_loc], e_mix=[e_mix],
+                       reuse_bias=True)
 
-    for i in range(2 * REORTHO):  # capture both graphs (with and without MGS)
-        graph_step(i)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    g0 = torch.cuda.Event(enable_timing=True)
-    g1 = torch.cuda.Event(enable_timing=True)
-    g0.record(stream)
-    for i in range(K):
-        graph_step(i)
-    g1.record(stream)
-    torch.cuda.synchronize()
-    tg = slowest_rank(g0.elapsed_time(g1), world, dev)
-    graph_value = job_rate(NW * K, world, tg / 1000.0)
-    batch.close()
+        for i in range(2 * REORTHO):  # capture both graphs (with and without MGS)
+            graph_step(fields[i % (Wm + K)])
+        if world > 1:
+            dist.barrier()
+        tg = slowest_rank(timed_steps(graph_step, fields, 0, K, stream), world, dev)
+        graph_value = job_rate(NW * K, world, tg / 1000.0)
+        batch.close()
+    ctx.close()
+    del fields, w
+    torch.cuda.empty_cache()
 
-    # -------- the FP64 path on the same workload, for the mixed-vs-FP64 comparison
-    fp64_value = None
-    if args.precision == "mixed" and not args.no_fp64_compare:
-        c64 = Context(system.h1, system.L, system.trial, na, nb, system.e_const, precision="fp64", device=dev)
-        w64 = c64.new_walkers(NW)
-        c64.init_walkers(w64)
-        c64.autotune(NW)
-        el64 = torch.empty(NW, 2, dtype=torch.float64, device=dev)
-        em64 = torch.empty(4, dtype=torch.float64, device=dev)
-        k64 = min(K, 3)
-        for i in range(2):
-            c64.step(w64, fields[i], TAU, e0, expm="krylov", order=KDIM, measure=True, e_loc=el64, e_mix=em64,
-                     reuse_bias=True)
-        torch.cuda.synchronize()
-        h0 = torch.cuda.Event(enable_timing=True)
-        h1e = torch.cuda.Event(enable_timing=True)
-        h0.record(stream)
-        for i in range(k64):
-            c64.step(w64, fields[2 + i], TAU, e0, expm="krylov", order=KDIM, reortho=((i + 3) % REORTHO == 0),
-                     measure=True, e_loc=el64, e_mix=em64, reuse_bias=True)
-        h1e.record(stream)
-        torch.cuda.synchronize()
-        th = slowest_rank(h0.elapsed_time(h1e), world, dev)
-        fp64_value = job_rate(NW * k64, world, th / 1000.0)
+    # -------- the FP64 path on the same workload (walkers are independent:
+    # per-walker throughput on 512 of them), for the mixed-vs-FP64 comparison
+    fp64 = None
+    if args.precision == "mixed" and not args.no_fp64_compare and not args.only_headline:
+        nw64, k64 = min(512, NW), 2
+        s64, c64, w64, el64, em64, e064, _ = make_context(dev, HEADLINE, "fp64", nw64, tune=False)
+        gen64 = torch.Generator(device=dev)
+        gen64.manual_seed(shard_seed(99, rank))
+        f64 = torch.randn(1 + k64, nw64, G, dtype=torch.float64, device=dev, generator=gen64)
+        st64 = Stepper(c64, w64, el64, em64, e064)
+        st64(f64[0])
+        th = slowest_rank(timed_steps(st64, f64, 1, k64, stream), world, dev)
+        fp64 = {"value": job_rate(nw64 * k64, world, th / 1000.0), "walkers": nw64, "steps": k64,
+                "ms_per_step": th / k64, "unit": "walker-steps/s", "e_mix": float(em64[2])}
         c64.close()
+        del f64, w64
+        torch.cuda.empty_cache()
 
     if rank != 0:
         if world > 1:
@@ -796,89 +933,64 @@ def run_ours(args):
         return 0
 
     # -------- roofline of the dominant kernel (exchange contraction of E_L)
-    ex_ms, ex_n = prof["exchange"]
-    flop_walker = G * 4 * (na * na + nb * nb) * N
-    ex_flop = flop_walker * NW
-    if args.precision == "fp64":
-        peak, bound, unit = NOMINAL_FP64_TFLOPS, "alu", "TFLOP/s"
-        peak_note = "FP64 nominal 1.25 TFLOP/s (recipe table); own FMA probe measured 1.19"
-        kname = "exchange_kernel<double> (SIMT FP64)"
-    else:
-        # BF16x3 split on tcgen05: three bf16 MMAs per algorithmic product; the kernel
-        # runs inside a long step, so the sustained bf16 figure is the denominator
-        peaks = measured_peaks()
-        bf16 = peaks.get("bf16_tflops_sustained") or 1700.0
-        peak, bound, unit = bf16 / 3.0, "tensor", "TFLOP/s"
-        src = "MEASURED_PEAKS.json" if peaks else "fallback 1.7 PFLOP/s"
-        peak_note = (f"of measured: sustained bf16 {bf16:.1f} TFLOP/s ({src}) / 3 MMA passes "
-                     "(BF16x3 split); achieved counts algorithmic flops once")
-        kname = "exchange_tc_kernel (tcgen05 BF16x3)"
+    peak, bound, peak_note = exchange_peak(args.precision)
+    ex_flop = exchange_flop_per_walker(system) * NW
     achieved = (ex_flop / (ex_ms / ex_n / 1000.0)) / 1e12 if ex_n else None
-    # DRAM bytes of one exchange launch (read + write), ncu capture of this kernel
-    # version at the benchmark size (profiles/launches_mixed_large.md)
+    kname = "exchange_kernel<double> (SIMT FP64)" if args.precision == "fp64" else "exchange_tc_kernel (tcgen05 BF16x3)"
+    # DRAM bytes of one exchange launch (read + write) from ncu, when taken on
+    # the current kernel (None otherwise)
     traffic, traffic_note = None, None
-    if args.precision == "mixed" and NW == 1024:
-        traffic = 63.51e6
-        traffic_note = ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch of "
-                        "exchange_tc_kernel<24, 2, 0, 0> at 1024 walkers: 56.08 + 7.43 MB; operands 55.9 MB")
-    adjoint = None
-    if world == 1 and not args.no_adjoint:
-        adjoint = adjoint_rate(dev)
-    precision = None
-    if world == 1 and not args.no_precision:
-        precision = precision_rate(dev)
-    batched = None
-    if world == 1 and not args.no_batched:
-        batched = batched_rate(dev)
-    block_krylov = None
-    if world == 1 and not args.no_block_krylov:
-        block_krylov = block_krylov_rate(dev)
-    props = None
-    if world == 1 and not args.no_propagators:
-        props = propagator_rates(dev)
-    accuracy = None
-    if world == 1 and not args.no_expm_accuracy:
-        accuracy = expm_accuracy(dev)
-    tau_ext = None
-    if world == 1 and not args.no_tau_scan:
-        tau_ext = tau_scan(dev)
+    total_split = sum(split.values())
+    extras = {}
+    if world == 1 and not args.only_headline:
+        legs = [("large_workload", args.no_large, lambda: large_rates(dev)),
+                ("precision_errors", args.no_precision_errors,
+                 lambda: {"precision": precision_errors(dev, HEADLINE), "large": precision_errors(dev, "large")}),
+                ("adjoint", args.no_adjoint, lambda: adjoint_rate(dev)),
+                ("batched_workload", args.no_batched, lambda: batched_rate(dev)),
+                ("block_krylov_workload", args.no_block_krylov, lambda: block_krylov_rate(dev)),
+                ("propagator_workload", args.no_propagators, lambda: propagator_rates(dev)),
+                ("expm_accuracy", args.no_expm_accuracy, lambda: expm_accuracy(dev)),
+                ("tau_extrapolation", args.no_tau_scan, lambda: tau_scan(dev))]
+        for name, skip, fn in legs:
+            if skip:
+                continue
+            try:
+                extras[name] = fn()
+            except Exception as exc:  # noqa: BLE001 - one failing leg must not end the bench line
+                extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            torch.cuda.empty_cache()
     cpu = None
-    if world == 1 and not args.no_cpu_baseline:
-        cpu, _ = oracle_rate(system, args.cpu_sample_walkers, 2, "")
-    total_prof = sum(v[0] for v in prof.values())
+    if world == 1 and not args.no_cpu_baseline and not args.only_headline:
+        cpu, _ = oracle_rate(system, args.cpu_sample_walkers, 2)
     line = {
         "metric": METRIC, "value": value, "unit": "walker-steps/s", "n_gpus": world,
         "steps": K, "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if args.precision == "fp64" else "f32+f64 (mixed)",
         "data": "synthetic (seeded Hamiltonian, Gaussian fields)",
-        "config": config_dict(args.precision, world),
+        "config": config_dict(args.precision, world, NW),
         "roofline": {"kernel": kname + ": Coulomb+exchange contraction of E_L",
-                     "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+                     "bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                      "traffic_source": traffic_note,
                      "flop_per_launch": ex_flop, "avg_launch_ms": ex_ms / ex_n if ex_n else None,
-                     "peak_source": peak_note,
-                     "share_of_step": ex_ms / total_prof if total_prof else None},
-        "kernel_ms_per_step": {k: v[0] / K for k, v in prof.items()},
+                     "launches_timed": ex_n, "peak_source": peak_note,
+                     "share_of_step": (split.get("exchange", 0.0) / total_split) if total_split else None},
+        "kernel_ms_per_step": split,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": "walker-steps/s",
                 "h2d_bytes_per_step": NW * G * 8, "d2h_bytes_per_step": 4 * 8},
         "gpu_launches": launches,
         "gemm_tiles": tune,
         "graph_value": graph_value,
-        "fp64_value": fp64_value,
-        "mixed_over_fp64": (value / fp64_value) if fp64_value else None,
-        "adjoint": adjoint,
-        "precision_workload": precision,
-        "batched_workload": batched,
-        "block_krylov_workload": block_krylov,
-        "propagator_workload": props,
-        "expm_accuracy": accuracy,
-        "tau_extrapolation": tau_ext,
+        "fp64": fp64,
+        "fp64_value": fp64["value"] if fp64 else None,
+        "mixed_over_fp64": (value / fp64["value"]) if fp64 else None,
         "clocks": clk,
         "e_mix_last": emix_final,
     }
+    line.update(extras)
     print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

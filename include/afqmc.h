@@ -76,11 +76,23 @@ enum { AFQMC_EXPM_TAYLOR = 0, AFQMC_EXPM_KRYLOV = 1, AFQMC_EXPM_BLOCK_KRYLOV = 2
 
 /* Arithmetic of a context.
  * AFQMC_FP64:  complex128 walkers, every step in FP64.
- * AFQMC_MIXED: complex64 walkers; force bias, field assembly, B*Psi, A*Psi and
- *              the exchange energy in FP32 (tensor cores where the kernel
- *              says so); overlaps, log-determinants, LU, Gram-Schmidt, Krylov
- *              coefficients, the small exponential, weights and all
- *              reductions in FP64. */
+ * AFQMC_MIXED: complex64 walkers.  On the tensor cores in split BF16 (three
+ *              bf16 products per FP32 operand pair, FP32 accumulation): the
+ *              field assembly A = i sqrt(tau) sum_g c_g L_g, the products A*V
+ *              of the Taylor and Krylov actions and the Coulomb + exchange
+ *              contraction of E_L (whose Coulomb traces also give the force
+ *              bias of the next step when reuse_bias is set).  In FP32: the
+ *              overlap products trial^T Psi, Theta's triangular solves, the
+ *              half steps B*Psi, the force-bias contraction when it is
+ *              recomputed, the Arnoldi inner products and norms and the
+ *              Gram-Schmidt projections of the re-orthonormalisation (the
+ *              walkers are stored in FP32; every result that depends on them
+ *              is invariant under Psi -> Psi M, so the orthonormality of Q
+ *              affects no energy or weight).  In FP64: the LU of the overlap
+ *              matrices and their log-determinants, the small exponential
+ *              e^{A_k} e_1 of the Krylov action, the hybrid energy, the
+ *              phaseless weights, population control, and every sum over
+ *              Cholesky vectors or walkers of the energies. */
 enum { AFQMC_FP64 = 0, AFQMC_MIXED = 1 };
 
 /* Per-walker status bits, OR-ed into status[w] (never cleared by the library). */
@@ -382,8 +394,24 @@ afqmc_status afqmc_walk_backward(afqmc_ctx* ctx, const afqmc_walkers* initial, c
 afqmc_status afqmc_local_energy_static(afqmc_ctx* ctx, const afqmc_walkers* w, double e0, double tau,
                                        double* e_loc, double* e_mix);
 
-/* Block until the context's stream is idle; returns ECUDA on a pending error. */
+/* Block until the context's stream is idle; returns ECUDA on a pending error.
+ * Every wait of the tensor-core pipelines (TMA, MMA, TMEM hand-offs) gives up
+ * after about 2 s; the kernel then raises the context's timeout flag, drains
+ * what it issued, frees its TMEM and returns.  afqmc_sync reports a raised
+ * flag as ECUDA (afqmc_last_cuda_error names the pipeline and the stage bits)
+ * and clears it, so the next call starts clean. */
 afqmc_status afqmc_sync(afqmc_ctx* ctx);
+
+/* Check of the bounded waits above: one kernel waits for an mbarrier phase
+ * that nothing completes, with the pipelines' wait helper bounded by
+ * limit_cycles (1 .. 4e9 SM cycles, about 2 s at the top clock), then raises
+ * bit 128 of the context's tensor-core timeout flag and returns; the next
+ * afqmc_sync reports it.  The paper has no counterpart: this exists so that
+ * the timeout path can be exercised without a GPU fault.  Nothing else is
+ * launched or left in flight.
+ * Errors: EINVAL (limit out of range), ENOTSUP (no tensor-core exchange in
+ * this context, i.e. not a mixed context with 1 <= na == nb <= 64), ECUDA. */
+afqmc_status afqmc_wait_probe(afqmc_ctx* ctx, long long limit_cycles);
 
 /* Kernel classes of the per-class timer. */
 enum {

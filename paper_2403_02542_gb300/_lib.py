@@ -57,6 +57,7 @@ SIGNATURES = {
     "afqmc_host_eigh": (_I, [_I, _P, _P, _P]),
     "afqmc_profile": (_I, [_P, _I]),
     "afqmc_profile_mask": (_I, [_P, ctypes.c_uint32]),
+    "afqmc_wait_probe": (_I, [_P, ctypes.c_longlong]),
     "afqmc_population_control": (_I, [_P, ctypes.POINTER(Walkers), _D, _P]),
     "afqmc_local_energy_static": (_I, [_P, ctypes.POINTER(Walkers), _D, _D, _P, _P]),
     "afqmc_autotune": (_I, [_P, _I, _P]),

@@ -5,8 +5,8 @@
 //  * modified Gram-Schmidt re-orthonormalisation of each determinant;
 //  * Arnoldi (one MGS pass) for the Krylov action of e^A (Eqs. krylovsub,
 //    projham, krylov) and the small exponential e^{A_k} e_1 (Sec. IV.C).
-// Overlaps, log-determinants and the small exponential are FP64 (double-float
-// for the exponential of complex64 walkers); the Arnoldi steps run in the
+// Overlaps, log-determinants and the small exponential are FP64 in both
+// precisions; the Arnoldi steps and the Gram-Schmidt projections run in the
 // walkers' precision.
 #include <cuda_bf16.h>
 #include <math_constants.h>
@@ -245,8 +245,8 @@ __global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* _
 
 // ---------------------------------------------------------------- MGS QR
 // One warp per determinant (walker w, spin): columns in order, the current
-// column in registers (EPL elements per lane), projections reduced with warp
-// shuffles in FP64 (lane partials in the storage precision).
+// column in registers (EPL elements per lane), projections and norms reduced
+// with warp shuffles in the walkers' precision (the reciprocal norm in FP64).
 template <typename R, int EPL>
 __global__ void mgs_kernel(typename C2<R>::t* __restrict__ psi, int N, int na, int nb, int Nw,
                            const uint8_t* __restrict__ mask) {
@@ -553,140 +553,6 @@ __global__ void __launch_bounds__(64) krylov_expm_kernel(typename C2<R>::t* __re
     }
 }
 
-// Double-float arithmetic (value = hi + lo, two FP32 numbers, about 2^-48
-// relative precision): the error-free sum (Knuth) and the product with an
-// FMA-computed rounding error (Dekker's algorithm with FMA).  Used for the
-// small exponential of complex64 walkers, where FP32 instructions are ~58x
-// cheaper than FP64 ones on this GPU and 2^-48 is far below the 1e-10
-// relative tolerance of the series.
-struct dfl {
-  float hi, lo;
-};
-__device__ __forceinline__ dfl two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return dfl{s, e};
-}
-__device__ __forceinline__ dfl fast_two_sum(float a, float b) {  // |a| >= |b|
-  const float s = __fadd_rn(a, b);
-  return dfl{s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
-  const dfl s = two_sum(x.hi, y.hi);
-  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
-}
-__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
-  const float p = __fmul_rn(x.hi, y.hi);
-  float e = __fmaf_rn(x.hi, y.hi, -p);
-  e = __fmaf_rn(x.hi, y.lo, e);
-  e = __fmaf_rn(x.lo, y.hi, e);
-  return fast_two_sum(p, e);
-}
-// acc += h * t for an FP32 h and a double-float t: the product's leading part
-// goes through an error-free sum, the small terms into the low word
-__device__ __forceinline__ void df_mac(dfl& acc, float h, dfl t) {
-  const float p = __fmul_rn(h, t.hi);
-  float e = __fmaf_rn(h, t.hi, -p);
-  e = __fmaf_rn(h, t.lo, e);
-  const dfl s = two_sum(acc.hi, p);
-  acc = fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(acc.lo, e)));
-}
-
-// Small exponential for complex64 walkers in double-float arithmetic; same
-// sub-stepping (||H/m||_1 <= 4) and stopping rule (terms below 1e-10 of the
-// sum) as the FP64 kernel.  H (FP32, exact in double-float) is staged in
-// shared memory per thread; the vectors live in registers.
-template <int KM>
-__global__ void __launch_bounds__(64) krylov_expm_df_kernel(float2* __restrict__ hess, size_t hs,
-                                                            const double* __restrict__ beta, int ncols, int k,
-                                                            int kmax) {
-  extern __shared__ float2 hsf[];  // [npk][64]
-  const int t = threadIdx.x;
-  const int col = blockIdx.x * 64 + t;
-  if (col >= ncols) return;  // no block-wide synchronisation: each thread reads only its own entries
-  float n1 = 0.f;
-  {
-    float cs[KM];
-#pragma unroll
-    for (int j = 0; j < KM; ++j) cs[j] = 0.f;
-    int o = 0;
-    for (int i = 0; i < k; ++i) {
-      const int j0 = i > 0 ? i - 1 : 0;
-      for (int j = j0; j < k; ++j, ++o) {
-        const float2 h = hess[(size_t)(i * kmax + j) * hs + col];
-        hsf[o * 64 + t] = h;
-#pragma unroll
-        for (int jj = 0; jj < KM; ++jj)
-          if (jj == j) cs[jj] += sqrtf(h.x * h.x + h.y * h.y);
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < KM; ++j) n1 = fmaxf(n1, cs[j]);
-  }
-  int m = 1;
-  if (n1 < 1e30f) m = (int)ceilf(n1 * 0.25f);
-  if (m < 1) m = 1;
-  if (m > 4096) m = 4096;
-  dfl vr[KM], vi[KM], tr[KM], ti[KM];
-#pragma unroll
-  for (int i = 0; i < KM; ++i) {
-    vr[i] = dfl{i == 0 ? 1.f : 0.f, 0.f};
-    vi[i] = dfl{0.f, 0.f};
-  }
-  for (int s = 0; s < m; ++s) {
-#pragma unroll
-    for (int i = 0; i < KM; ++i) {
-      tr[i] = vr[i];
-      ti[i] = vi[i];
-    }
-    for (int d = 1; d <= 60; ++d) {
-      // 1 / (m d) as a double-float: FP32 reciprocal plus its FMA residual
-      const float md = (float)(m * d);
-      const float fh = __frcp_rn(md);
-      const dfl f{fh, __fmul_rn(__fmaf_rn(-md, fh, 1.0f), fh)};
-      float tn = 0.f, an = 0.f;
-      dfl ur[KM], ui[KM];
-      int o = 0;
-#pragma unroll
-      for (int i = 0; i < KM; ++i) {
-        dfl ar{0.f, 0.f}, ai{0.f, 0.f};
-        if (i < k) {
-#pragma unroll
-          for (int j = (i > 0 ? i - 1 : 0); j < KM; ++j) {
-            if (j < k) {
-              const float2 h = hsf[(o + j - (i > 0 ? i - 1 : 0)) * 64 + t];
-              df_mac(ar, h.x, tr[j]);
-              df_mac(ar, -h.y, ti[j]);
-              df_mac(ai, h.x, ti[j]);
-              df_mac(ai, h.y, tr[j]);
-            }
-          }
-          o += k - (i > 0 ? i - 1 : 0);
-        }
-        ur[i] = df_mul(ar, f);
-        ui[i] = df_mul(ai, f);
-      }
-#pragma unroll
-      for (int i = 0; i < KM; ++i) {
-        if (i < k) {
-          tr[i] = ur[i];
-          ti[i] = ui[i];
-          vr[i] = df_add(vr[i], ur[i]);
-          vi[i] = df_add(vi[i], ui[i]);
-          tn += ur[i].hi * ur[i].hi + ui[i].hi * ui[i].hi;
-          an += vr[i].hi * vr[i].hi + vi[i].hi * vi[i].hi;
-        }
-      }
-      if (tn <= 1e-20f * an) break;
-    }
-  }
-  const float b = (float)beta[col];
-#pragma unroll
-  for (int i = 0; i < KM; ++i)
-    if (i < k) hess[(size_t)(i * kmax) * hs + col] = make_float2(b * (vr[i].hi + vr[i].lo), b * (vi[i].hi + vi[i].lo));
-}
-
 // psi_out = B_k y: out = sum_i y_i b_i in the walkers' precision (y from column 0 of H)
 template <typename R>
 __global__ void krylov_combine_kernel(const typename C2<R>::t* __restrict__ hess, size_t hs,
@@ -900,17 +766,6 @@ template <typename R, int KM>
 cudaError_t expm_launch(const afqmc_ctx* c, int ncols, int k, cudaStream_t s) {
   typename C2<R>::t* H = reinterpret_cast<typename C2<R>::t*>(c->ws.hess);
   const size_t hs = (size_t)c->ws.n_walkers * c->nc;
-  if constexpr (std::is_same<R, float>::value) {  // complex64 walkers: double-float series
-    const size_t shf = (size_t)hess_packed(k) * 64 * sizeof(float2);
-    if (shf <= (size_t)max_dyn_smem()) {
-      if (!capturing(c)) {
-        cudaError_t e = raise_smem_limit(krylov_expm_df_kernel<KM>);
-        if (e != cudaSuccess) return e;
-      }
-      krylov_expm_df_kernel<KM><<<(ncols + 63) / 64, 64, shf, s>>>(H, hs, c->ws.beta, ncols, k, c->ws.kmax);
-      return cudaGetLastError();
-    }
-  }
   const size_t shm = (size_t)hess_packed(k) * 64 * sizeof(double2);
   const dim3 grid((ncols + 63) / 64);
   if (shm <= (size_t)max_dyn_smem()) {
@@ -959,12 +814,6 @@ cudaError_t prepare_overlap(const afqmc_ctx*) {
   if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_kernel<R, 12, true>);
   if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_kernel<R, 16, true>);
   if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_kernel<R, 32, true>);
-  if constexpr (std::is_same<R, float>::value) {
-    if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_df_kernel<8>);
-    if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_df_kernel<12>);
-    if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_df_kernel<16>);
-    if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_df_kernel<32>);
-  }
   return e;
 }
 template cudaError_t prepare_overlap<double>(const afqmc_ctx*);

@@ -26,7 +26,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* b) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sa(b)) : "memory");
 }
 // Wait for the phase with the given parity to complete; false after the cycle limit.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, long long limit = kTcWaitCycles) {
   const uint32_t a = sa(b);
   const long long t0 = clock64();
   while (true) {
@@ -37,7 +37,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
         : "r"(a), "r"(parity)
         : "memory");
     if (ok) return true;
-    if (clock64() - t0 > kTcWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {

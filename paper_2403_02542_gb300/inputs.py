@@ -110,11 +110,14 @@ def _rhf_orbitals(h1: np.ndarray, L: np.ndarray, n: int, tol: float = 1e-10,
     F_prev = None
     converged = False
     it = 0
+    G, N = L.shape[0], L.shape[1]
+    Lf = L.reshape(G, N * N)
     for it in range(1, max_iter + 1):
-        coul = np.einsum("gpq,pq->g", L, P)
+        coul = Lf @ P.reshape(N * N)                # tr(L_g P)
         LC = L @ C                                  # [G, N, n]
-        K = np.einsum("gpi,gqi->pq", LC, LC)        # sum_g L_g P L_g
-        F = h1 + 2.0 * np.einsum("g,gpq->pq", coul, L) - K
+        M = LC.transpose(1, 0, 2).reshape(N, G * n)
+        K = M @ M.T                                 # sum_g L_g P L_g
+        F = h1 + 2.0 * (coul @ Lf).reshape(N, N) - K
         if F_prev is not None:
             F = (1.0 - damping) * F + damping * F_prev
         F_prev = F
@@ -172,12 +175,22 @@ CONFIGS = {
 _CONFIG_INDEX = {"small": 1, "large": 2, "precision": 3, "grad": 5}
 
 
+_SYSTEM_CACHE: dict = {}
+
+
 def config_system(name: str, system: int = 0, **overrides) -> System:
-    """The synthetic system of a named workload; seed 20240304 + 100*config + system."""
+    """The synthetic system of a named workload; seed 20240304 + 100*config + system.
+
+    Generated once per process and key (the N = 300 workload takes tens of
+    seconds); every call returns its own copy of the arrays."""
     c = dict(CONFIGS[name])
     c.update(overrides)
     seed = 20240304 + 100 * _CONFIG_INDEX.get(name, 9) + system
-    return make_system(c["N"], c["na"], c["na"], c["G"], rho=c["rho"], seed=seed)
+    key = (c["N"], c["na"], c["G"], c["rho"], seed)
+    if key not in _SYSTEM_CACHE:
+        _SYSTEM_CACHE[key] = make_system(c["N"], c["na"], c["na"], c["G"], rho=c["rho"], seed=seed)
+    s = _SYSTEM_CACHE[key]
+    return dataclasses.replace(s, h1=s.h1.copy(), L=s.L.copy(), trial=s.trial.copy(), meta=dict(s.meta))
 
 
 def _plain_cholesky(rng: np.random.Generator, N: int, G: int, rho: float, chunk: int = 64) -> np.ndarray:
