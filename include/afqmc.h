@@ -100,7 +100,8 @@ enum { AFQMC_FP64 = 0, AFQMC_MIXED = 1 };
 #define AFQMC_W_REWEIGHT  0x2u  /* reweighting factor >= 10 set to 0 (Sec. V.B)  */
 #define AFQMC_W_PHASE     0x4u  /* cos(dtheta) <= 0: killed by the phaseless cut */
 #define AFQMC_W_NONFINITE 0x8u  /* non-finite ratio/energy/weight: weight set 0  */
-#define AFQMC_W_SINGULAR  0x10u /* zero pivot in the overlap matrix              */
+#define AFQMC_W_SINGULAR  0x10u /* zero pivot in the overlap matrix; the weight
+                                   update of the step gives such a walker W = 0 */
 
 /* Walker population: caller-owned device buffers.
  *   psi     [Nw][nc][N] complex (see above)

@@ -483,9 +483,13 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
   const double st = std::sqrt(p->tau);
   Workspace& ws = c->ws;
   const size_t cs = sizeof(typename C2<R>::t);
-  // out = B in: complex64 walkers with N <= 128 keep B in shared memory
-  // (dedicated kernel), else the tiled GEMM
+  // out = B in: complex64 walkers on the tensor cores (in + (B - I) in; two
+  // launches: the walker planes, then the contraction), else the tiled GEMM
   auto half = [&](const void* in, void* out) -> cudaError_t {
+    if (std::is_same<R, float>::value && c->tg.hs_ok) {
+      c->launches += 1;
+      return tc_halfstep_launch(c, Nw, in, out, s);
+    }
     if (std::is_same<R, float>::value && halfstep_ok(c)) return halfstep_launch(c, Nw, in, out, s);
     return gemm<R>(site_args<R>(c, SITE_HALFSTEP, Nw, st, in, out), false, EPI_STORE, s);
   };
@@ -1170,6 +1174,10 @@ afqmc_status afqmc_set_tau(afqmc_ctx* c, double tau) {
   if (c->prec == AFQMC_MIXED) {
     CK(launch_to_float(c->d_B, c->f_B, Bh.size(), c->stream));
     c->launches += 1;
+    if (c->tg.hs_ok) {  // D = B - I planes of the tensor-core half step
+      CK(tc_halfstep_set_b(c, c->stream));
+      c->launches += 1;
+    }
     CK(cudaStreamSynchronize(c->stream));
   }
   c->tau = tau;

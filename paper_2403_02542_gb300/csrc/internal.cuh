@@ -181,6 +181,20 @@ struct TgPlan {
   alignas(64) unsigned char map_a_lo[128];
   alignas(64) unsigned char map_v_hi[128];
   alignas(64) unsigned char map_v_lo[128];
+  // half steps B Psi on the tensor cores as Psi + D Psi, D = B - I (B is
+  // close to the identity, so the split-bf16 error scales with ||D||):
+  // rows p of D against rows 2 (w nc + j) + part = Re / Im psi_wj of the
+  // walker planes, K = q
+  bool hs_ok = false;
+  int hs_Mp = 0, hs_Kp = 0, hs_rows = 0;  // D rows (128-padded), K (64-padded), plane rows allocated
+  void* d_hi = nullptr;  // [hs_Mp][hs_Kp] bf16: D = e^{-tau h''/2} - I split hi/lo (set with tau)
+  void* d_lo = nullptr;
+  void* p_hi = nullptr;  // [hs_rows][hs_Kp] bf16: walker planes split hi/lo (every half step)
+  void* p_lo = nullptr;
+  alignas(64) unsigned char map_d_hi[128];
+  alignas(64) unsigned char map_d_lo[128];
+  alignas(64) unsigned char map_p_hi[128];
+  alignas(64) unsigned char map_p_lo[128];
 };
 }  // namespace afq
 
@@ -389,6 +403,10 @@ cudaError_t tc_av_launch(afqmc_ctx* c, int Nw, const void* V, long long v_stride
                          long long c_stride, double alpha, cudaStream_t s);
 // ||A_w||_F from the planes into ws.scal[w][SC_NORMA]
 cudaError_t tc_av_normA(afqmc_ctx* c, int Nw, cudaStream_t s);
+// half step out = B in (complex64 [Nw][nc][N], in != out) on the tensor cores,
+// as in + D in with D = B - I; D's planes from tc_halfstep_set_b (after B changes)
+cudaError_t tc_halfstep_set_b(afqmc_ctx* c, cudaStream_t s);
+cudaError_t tc_halfstep_launch(afqmc_ctx* c, int Nw, const void* in, void* out, cudaStream_t s);
 
 }  // namespace afq
 

@@ -146,6 +146,10 @@ __global__ void weights_kernel(double* __restrict__ weight, double* __restrict__
     Wn = 0.0;
     flags |= AFQMC_W_NONFINITE;
   }
+  // a singular overlap matrix at the start of this step (the bit is set by the
+  // overlap kernel; a walker that had it before was killed then): its Theta
+  // and force bias are meaningless, so the walker is dropped
+  if (status[w] & AFQMC_W_SINGULAR) Wn = 0.0;
   weight[w] = Wn;
   logovl[2 * w] = ldn.re;
   logovl[2 * w + 1] = ldn.im;

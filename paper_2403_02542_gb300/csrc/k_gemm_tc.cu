@@ -19,6 +19,15 @@
 // complex values of A_w contiguously).  Every mbarrier wait is bounded; on a
 // timeout the kernel raises an error flag, stops issuing work and frees TMEM.
 //
+// The same tiled kernel (MODE 2) runs the half steps B Psi of the Split-2
+// propagator (Sec. III.B): rows p of D = B - I (B = e^{-tau h''/2} is within
+// O(tau ||h''||) of the identity), columns 2 (w nc + j) + part of the walker
+// planes (Re / Im of orbital j of walker w, split hi/lo), K = q; the epilogue
+// adds the exact identity part, out[w][j][p] = in[w][j][p] + (D in)[w][j][p],
+// so the split error is relative to ||D Psi||, not to ||Psi||.  Each thread
+// owns row p, so for every column pair the 32 lanes of a warp store 32
+// consecutive complex entries of one orbital.
+//
 // When the products A_w V of the exponential also run on the tensor cores,
 // the field epilogue writes A_w instead as bfloat16 hi/lo planes
 // A'[w][p][k] = [Re A_w[p][q] | Im A_w[p][q]] (k = q, N + q), and
@@ -47,15 +56,18 @@ constexpr uint32_t TG_STAGE_BYTES = 2 * TG_A_BYTES + 2 * TG_B_BYTES;
 
 struct TgArgs {
   int mt, nt, KC, n_items;
-  int M, Nn;           // valid rows (2 Nw) and columns (N^2)
+  int M, Nn;           // valid rows (2 Nw; mode 2: N) and columns (N^2; mode 2: 2 Nw nc)
   float* out;          // mode 0: A as interleaved complex [Nw][Nn]
   __nv_bfloat16* a_hi;  // mode 1: A' planes [Nw * N][KA]
   __nv_bfloat16* a_lo;
   int N, KA;
+  const float2* hs_in;  // mode 2: walkers in [Nw nc][N] complex64
+  float2* hs_out;       // mode 2: walkers out, same layout
   int* err;
 };
 
-// MODE 0 writes A as complex64 [w][p][q]; MODE 1 the split planes A'.
+// MODE 0 writes A as complex64 [w][p][q]; MODE 1 the split planes A'; MODE 2
+// the half step out = in + D in.
 template <int MODE>
 __global__ void __launch_bounds__(TG_THREADS, 1)
     field_tc_kernel(const __grid_constant__ CUtensorMap tmX_hi, const __grid_constant__ CUtensorMap tmX_lo,
@@ -181,13 +193,27 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
       const int m = mt * TG_BM + r;
       const int w = m >> 1;
       const bool row_ok = m < p.M;
-      float* orow = p.out + (size_t)w * p.Nn * 2;
+      float* orow = MODE == 2 ? nullptr : p.out + (size_t)w * p.Nn * 2;
       const int e_base = nt * TG_BN;
       for (int c0 = 0; c0 < TG_BN; c0 += 8) {
         uint32_t v[8];
         tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * TG_BN + c0), v);
         tmem_wait_ld();
-        if constexpr (MODE == 1) {
+        if constexpr (MODE == 2) {
+          // row m = p; columns e0 .. e0 + 7 = (Re, Im) of orbitals wj .. wj + 3
+          if (!row_ok) continue;
+          const int wj0 = (e_base + c0) >> 1;
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            if (2 * (wj0 + t) < p.Nn) {
+              const size_t o = (size_t)(wj0 + t) * p.N + m;
+              float2 x = p.hs_in[o];
+              x.x += __uint_as_float(v[2 * t]);
+              x.y += __uint_as_float(v[2 * t + 1]);
+              p.hs_out[o] = x;
+            }
+          }
+        } else if constexpr (MODE == 1) {
           // row 2w + part -> plane column part * N + q of row p of walker w
           const int e0 = e_base + c0;
           if (!row_ok || e0 >= p.Nn) continue;
@@ -510,6 +536,48 @@ __global__ void build_x_kernel(const float2* __restrict__ c, __nv_bfloat16* __re
   }
 }
 
+// D = B - I from the FP64 half-step matrix, split into hi/lo; rows p < Mp and
+// columns q < Kp, zero outside N x N.
+__global__ void build_d_kernel(const double* __restrict__ B, __nv_bfloat16* __restrict__ hi,
+                               __nv_bfloat16* __restrict__ lo, int N, int Mp, int Kp) {
+  const size_t total = (size_t)Mp * Kp;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const int q = (int)(e % Kp), pr = (int)(e / Kp);
+    double x = 0.0;
+    if (pr < N && q < N) x = B[(size_t)pr * N + q] - (pr == q ? 1.0 : 0.0);
+    split_bf16(x, hi[e], lo[e]);
+  }
+}
+
+// Walker planes of a half step: row 2 wj + part holds Re (part 0) or Im
+// (part 1) of psi_wj[q] for q < N, split hi/lo; each thread converts eight
+// consecutive q of one orbital (16-byte plane stores).  Columns N .. Kp stay
+// zero from the allocation.
+__global__ void build_psi_planes_kernel(const float2* __restrict__ in, __nv_bfloat16* __restrict__ hi,
+                                        __nv_bfloat16* __restrict__ lo, int n_orb, int N, int Kp) {
+  const int q8 = (N + 7) / 8;
+  const size_t total = (size_t)n_orb * q8;
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+    const size_t wj = e / q8;
+    const int q0 = (int)(e - wj * q8) * 8;
+    __align__(16) __nv_bfloat16 rh[8], rl[8], ih[8], il[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      float2 v = make_float2(0.f, 0.f);
+      if (q0 + t < N) v = in[wj * N + q0 + t];
+      rh[t] = __float2bfloat16(v.x);
+      rl[t] = __float2bfloat16(v.x - __bfloat162float(rh[t]));
+      ih[t] = __float2bfloat16(v.y);
+      il[t] = __float2bfloat16(v.y - __bfloat162float(ih[t]));
+    }
+    const size_t o_re = (2 * wj) * (size_t)Kp + q0, o_im = o_re + Kp;
+    *reinterpret_cast<uint4*>(hi + o_re) = *reinterpret_cast<const uint4*>(rh);
+    *reinterpret_cast<uint4*>(lo + o_re) = *reinterpret_cast<const uint4*>(rl);
+    *reinterpret_cast<uint4*>(hi + o_im) = *reinterpret_cast<const uint4*>(ih);
+    *reinterpret_cast<uint4*>(lo + o_im) = *reinterpret_cast<const uint4*>(il);
+  }
+}
+
 inline int grid_for(size_t n) {
   size_t b = (n + 255) / 256;
   return (int)(b > 152 * 64 ? 152 * 64 : (b == 0 ? 1 : b));
@@ -554,6 +622,21 @@ cudaError_t tc_field_setup(afqmc_ctx* c, cudaStream_t s) {
       !make_map(reinterpret_cast<CUtensorMap*>(P.map_l_lo), P.l_lo, P.Np, P.Kp, TG_BN))
     return cudaErrorInvalidValue;
   P.ok = true;
+  // half steps: D planes [hs_Mp][hs_Kp] (filled by tc_halfstep_set_b)
+  P.hs_Mp = ((c->N + TG_BM - 1) / TG_BM) * TG_BM;
+  P.hs_Kp = ((c->N + 63) / 64) * 64;
+  e = cudaMalloc(&P.d_hi, (size_t)P.hs_Mp * P.hs_Kp * 2);
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&P.d_lo, (size_t)P.hs_Mp * P.hs_Kp * 2);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(P.d_hi, 0, (size_t)P.hs_Mp * P.hs_Kp * 2, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(P.d_lo, 0, (size_t)P.hs_Mp * P.hs_Kp * 2, s);
+  if (e != cudaSuccess) return e;
+  if (!make_map(reinterpret_cast<CUtensorMap*>(P.map_d_hi), P.d_hi, P.hs_Mp, P.hs_Kp, TG_BM) ||
+      !make_map(reinterpret_cast<CUtensorMap*>(P.map_d_lo), P.d_lo, P.hs_Mp, P.hs_Kp, TG_BM))
+    return cudaErrorInvalidValue;
+  P.hs_ok = true;
   const int nbp = ((2 * c->nc + 15) / 16) * 16;
   if (nbp <= 240) {
     int S = 4;
@@ -572,13 +655,31 @@ cudaError_t tc_field_setup(afqmc_ctx* c, cudaStream_t s) {
 cudaError_t tc_field_ws(afqmc_ctx* c) {
   TgPlan& P = c->tg;
   if (!P.ok) return cudaSuccess;
-  void* old[] = {P.x_hi, P.x_lo, P.a_hi, P.a_lo, P.v_hi, P.v_lo};
+  void* old[] = {P.x_hi, P.x_lo, P.a_hi, P.a_lo, P.v_hi, P.v_lo, P.p_hi, P.p_lo};
   for (void* q : old)
     if (q) cudaFree(q);
-  P.x_hi = P.x_lo = P.a_hi = P.a_lo = P.v_hi = P.v_lo = nullptr;
+  P.x_hi = P.x_lo = P.a_hi = P.a_lo = P.v_hi = P.v_lo = P.p_hi = P.p_lo = nullptr;
   P.m_cap = 0;
   P.av_cap = 0;
+  P.hs_rows = 0;
   const int cap = c->ws.n_walkers;
+  if (P.hs_ok) {
+    // walker planes: rows 2 (w nc + j) + part, padded to the 256-row column tile;
+    // the K padding N .. hs_Kp and the padding rows stay zero
+    const size_t rows = (((size_t)2 * cap * c->nc + TG_BN - 1) / TG_BN) * TG_BN;
+    cudaError_t e = cudaMalloc(&P.p_hi, rows * P.hs_Kp * 2);
+    if (e != cudaSuccess) return e;
+    e = cudaMalloc(&P.p_lo, rows * P.hs_Kp * 2);
+    if (e != cudaSuccess) return e;
+    e = cudaMemset(P.p_hi, 0, rows * P.hs_Kp * 2);
+    if (e != cudaSuccess) return e;
+    e = cudaMemset(P.p_lo, 0, rows * P.hs_Kp * 2);
+    if (e != cudaSuccess) return e;
+    if (!make_map(reinterpret_cast<CUtensorMap*>(P.map_p_hi), P.p_hi, rows, P.hs_Kp, TG_BN) ||
+        !make_map(reinterpret_cast<CUtensorMap*>(P.map_p_lo), P.p_lo, rows, P.hs_Kp, TG_BN))
+      return cudaErrorInvalidValue;
+    P.hs_rows = (int)rows;
+  }
   const int mp = ((2 * cap + TG_BM - 1) / TG_BM) * TG_BM;
   cudaError_t e = cudaMalloc(&P.x_hi, (size_t)mp * P.Kp * 2);
   if (e != cudaSuccess) return e;
@@ -622,13 +723,15 @@ cudaError_t tc_field_prepare(const afqmc_ctx* c) {
   if (!c->tg.ok) return cudaSuccess;
   cudaError_t e = raise_smem_limit(field_tc_kernel<0>);
   if (e == cudaSuccess) e = raise_smem_limit(field_tc_kernel<1>);
+  if (e == cudaSuccess && c->tg.hs_ok) e = raise_smem_limit(field_tc_kernel<2>);
   if (e == cudaSuccess && c->tg.av_ok) e = raise_smem_limit(av_tc_kernel);
   return e;
 }
 
 void tc_field_free(afqmc_ctx* c) {
   TgPlan& P = c->tg;
-  void* ptrs[] = {P.l_hi, P.l_lo, P.x_hi, P.x_lo, P.a_hi, P.a_lo, P.v_hi, P.v_lo, P.err};
+  void* ptrs[] = {P.l_hi, P.l_lo, P.x_hi, P.x_lo, P.a_hi, P.a_lo, P.v_hi, P.v_lo,
+                  P.d_hi, P.d_lo, P.p_hi, P.p_lo, P.err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   P = TgPlan();
@@ -717,6 +820,50 @@ cudaError_t tc_av_launch(afqmc_ctx* c, int Nw, const void* V, long long v_stride
   memcpy(&mvh, P.map_v_hi, sizeof(CUtensorMap));
   memcpy(&mvl, P.map_v_lo, sizeof(CUtensorMap));
   av_tc_kernel<<<grid, TG_THREADS, av_smem_bytes(P.NBp, P.S_av), s>>>(mah, mal, mvh, mvl, a);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_halfstep_set_b(afqmc_ctx* c, cudaStream_t s) {
+  TgPlan& P = c->tg;
+  if (!P.hs_ok) return cudaSuccess;
+  build_d_kernel<<<grid_for((size_t)P.hs_Mp * P.hs_Kp), 256, 0, s>>>(
+      c->d_B, static_cast<__nv_bfloat16*>(P.d_hi), static_cast<__nv_bfloat16*>(P.d_lo), c->N, P.hs_Mp, P.hs_Kp);
+  return cudaGetLastError();
+}
+
+cudaError_t tc_halfstep_launch(afqmc_ctx* c, int Nw, const void* in, void* out, cudaStream_t s) {
+  TgPlan& P = c->tg;
+  const int n_orb = Nw * c->nc;
+  const int rows = ((2 * n_orb + TG_BN - 1) / TG_BN) * TG_BN;
+  if (!P.hs_ok || rows > P.hs_rows || in == out) return cudaErrorInvalidValue;
+  build_psi_planes_kernel<<<grid_for((size_t)n_orb * ((c->N + 7) / 8)), 256, 0, s>>>(
+      static_cast<const float2*>(in), static_cast<__nv_bfloat16*>(P.p_hi), static_cast<__nv_bfloat16*>(P.p_lo),
+      n_orb, c->N, P.hs_Kp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  TgArgs a{};
+  a.mt = P.hs_Mp / TG_BM;
+  a.nt = rows / TG_BN;
+  a.KC = P.hs_Kp / 64;
+  a.n_items = a.mt * a.nt;
+  a.M = c->N;
+  a.Nn = 2 * n_orb;
+  a.N = c->N;
+  a.hs_in = static_cast<const float2*>(in);
+  a.hs_out = static_cast<float2*>(out);
+  a.err = static_cast<int*>(P.err);
+  if (!capturing(c)) {
+    e = raise_smem_limit(field_tc_kernel<2>);
+    if (e != cudaSuccess) return e;
+  }
+  const int sms = sm_count();
+  const int grid = a.n_items < sms ? a.n_items : sms;
+  CUtensorMap mdh, mdl, mph, mpl;
+  memcpy(&mdh, P.map_d_hi, sizeof(CUtensorMap));
+  memcpy(&mdl, P.map_d_lo, sizeof(CUtensorMap));
+  memcpy(&mph, P.map_p_hi, sizeof(CUtensorMap));
+  memcpy(&mpl, P.map_p_lo, sizeof(CUtensorMap));
+  field_tc_kernel<2><<<grid, TG_THREADS, tg_smem_bytes(), s>>>(mdh, mdl, mph, mpl, a);
   return cudaGetLastError();
 }
 
