@@ -319,6 +319,51 @@ def adjoint_rate(dev):
     }
 
 
+def bond_scan(dev, n_points=11, s_max=0.05):
+    """The 11-point path scan of the differentiation workload (N=96, 15+15
+    electrons, 480 vectors, 512 walkers, 100 fixed-field steps at tau=0.05,
+    Split-2 + Taylor-6, QR every 10, checkpoints every 10, mixed precision):
+    h1(s) = h1 + s dH1, L(s) = L + s dL with dH1, dL random symmetric scaled
+    to 0.01 (of max|L| for dL), s in [-0.05, 0.05]; at every point J(s), the
+    adjoint dJ/ds and a central difference of J (step 0.01), all with the same
+    fields, trial and E_0."""
+    import numpy as np
+    import torch
+    from paper_2403_02542_gb300.inputs import CONFIGS, config_system
+    from paper_2403_02542_gb300.scan import path_scan
+    cfg = CONFIGS["grad"]
+    s = config_system("grad")
+    rng = np.random.default_rng(2403)
+    dH = rng.standard_normal(s.h1.shape)
+    dH = 0.5 * (dH + dH.T)
+    dH *= 0.01 / np.abs(dH).max()
+    dL = rng.standard_normal(s.L.shape)
+    dL = 0.5 * (dL + dL.transpose(0, 2, 1))
+    dL *= 0.01 * np.abs(s.L).max() / np.abs(dL).max()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2403)
+    fields = torch.randn(cfg["steps"], cfg["walkers"], s.G, dtype=torch.float64, device=dev, generator=gen)
+    from paper_2403_02542_gb300.api import Context
+    c = Context(s.h1, s.L, s.trial, s.na, s.nb, s.e_const, precision="mixed", device=dev)
+    w = c.new_walkers(1)
+    c.init_walkers(w)
+    el = torch.empty(1, 2, dtype=torch.float64, device=dev)
+    em = torch.empty(4, dtype=torch.float64, device=dev)
+    c.local_energy(w, 0.0, cfg["tau"], el, em)
+    e0 = float(el[0, 0])
+    c.close()
+    t0 = time.perf_counter()
+    pts = path_scan(s, fields, np.linspace(-s_max, s_max, n_points), dH, dL, cfg["tau"], e0, order=cfg["order"],
+                    reortho_every=cfg["reortho"], ckpt_every=10, precision="mixed", fd_step=1e-2, device=dev)
+    wall = time.perf_counter() - t0
+    scale = max(abs(p["dJds"]) for p in pts)
+    return {"workload": "differentiation workload (N=96, Na=Nb=15, N_gamma=480, 512 walkers, 100 fixed-field steps, "
+                        "tau=0.05, Split-2 + Taylor-6, QR every 10, checkpoints every 10), mixed; "
+                        "h1(s) = h1 + s dH1, L(s) = L + s dL, dH1 and dL random symmetric of max 0.01 (dL: 0.01 max|L|)",
+            "points": pts, "max_abs_dJds_minus_fd": max(abs(p["dJds"] - p["dJds_fd"]) for p in pts),
+            "max_abs_dJds": scale, "wall_s": wall}
+
+
 def block_krylov_rate(dev, steps=5):
     """The large-step workload (N=128, 20+20 electrons, 640 vectors, 1024
     walkers, tau=0.05, E_L every step, MGS every 5 steps) with the block-Krylov
@@ -597,6 +642,33 @@ def batched_rate(dev, steps=3, warmup=2):
     ms = a0.elapsed_time(a1) / steps
     launches = sum(c.launch_count for c in ctxs) - l0
     total_w = sum(nw for _, nw in systems)
+
+    # the same systems and steps without the graph: every system's step by
+    # plain afqmc_step calls, one system after another on one stream, each
+    # timed with its own event pair
+    def seq_one(k):
+        evs = []
+        for i, c in enumerate(ctxs):
+            e_a, e_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e_a.record(stream)
+            c.step(ws[i], xs[i][k], TAU, e0s[i], expm="krylov", order=KDIM, measure=True, e_loc=els[i],
+                   e_mix=ems[i], reuse_bias=True)
+            e_b.record(stream)
+            evs.append((e_a, e_b))
+        return evs
+
+    seq_one(0)
+    torch.cuda.synchronize()
+    per_sys = [0.0] * len(ctxs)
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    all_evs = [seq_one(warmup + k) for k in range(steps)]
+    b1.record(stream)
+    torch.cuda.synchronize()
+    for evs in all_evs:
+        for i, (e_a, e_b) in enumerate(evs):
+            per_sys[i] += e_a.elapsed_time(e_b) / steps
+    seq_ms = b0.elapsed_time(b1) / steps
     out = {
         "workload": "batched form: 16 synthetic systems, N uniform in 64..400, Na=Nb=N/6, N_gamma=5N, "
                     "256-2048 walkers each, one CUDA graph per step over all systems, autotuned tiles, "
@@ -605,6 +677,10 @@ def batched_rate(dev, steps=3, warmup=2):
         "ms_per_step": ms, "value": total_w / (ms / 1000.0), "unit": "walker-steps/s (sum over systems)",
         "gpu_launches_per_step": launches / steps, "generate_s": t_gen, "setup_s": t_setup,
         "e_mix": [float(em[2]) for em in ems],
+        "sequential": {"ms_per_step": seq_ms, "value": total_w / (seq_ms / 1000.0),
+                       "per_system_ms": per_sys,
+                       "note": "the same steps by plain afqmc_step calls, one system after another on one stream"},
+        "graph_over_sequential": seq_ms / ms,
     }
     batch.close()
     for c in ctxs:
@@ -947,6 +1023,7 @@ def run_ours(args):
                 ("precision_errors", args.no_precision_errors,
                  lambda: {"precision": precision_errors(dev, HEADLINE), "large": precision_errors(dev, "large")}),
                 ("adjoint", args.no_adjoint, lambda: adjoint_rate(dev)),
+                ("bond_scan", args.no_adjoint, lambda: bond_scan(dev)),
                 ("batched_workload", args.no_batched, lambda: batched_rate(dev)),
                 ("block_krylov_workload", args.no_block_krylov, lambda: block_krylov_rate(dev)),
                 ("propagator_workload", args.no_propagators, lambda: propagator_rates(dev)),

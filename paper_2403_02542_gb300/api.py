@@ -329,3 +329,67 @@ class MixedEnergy(torch.autograd.Function):
         c, w, e0, tau = ctx.state
         gh, gL = c.energy_backward(w, e0, tau, float(grad_out))
         return gh.to(grad_out.device), gL.to(grad_out.device), None, None, None, None, None, None
+
+
+def walk_energy(ctx: "Context", n_walkers: int, fields: torch.Tensor, tau: float, e0: float, order: int = 6,
+                reortho_every: int = 0) -> torch.Tensor:
+    """J = E_n after n fixed-field steps (Split-2 + Taylor) from walkers at the
+    trial, by plain afqmc_step calls with the local energy measured at the
+    last step.  Returns e_mix [4] = (sum W Ebar_L, sum W, J, live walkers)."""
+    w = ctx.new_walkers(n_walkers)
+    ctx.init_walkers(w)
+    e_loc = torch.empty(n_walkers, 2, dtype=torch.float64, device=ctx.device)
+    e_mix = torch.empty(4, dtype=torch.float64, device=ctx.device)
+    n = int(fields.shape[0])
+    for k in range(n):
+        ctx.step(w, fields[k], tau, e0, expm="taylor", order=order,
+                 reortho=bool(reortho_every) and (k + 1) % reortho_every == 0, measure=(k == n - 1),
+                 e_loc=e_loc, e_mix=e_mix)
+    return e_mix
+
+
+class WalkEnergy(torch.autograd.Function):
+    """J(h1, L) = E_n, the mixed estimator after an n-step fixed-field walk
+    from walkers at the trial, as a differentiable function (the energy
+    derivatives of a bond-length scan).  The forward is the walk itself
+    (afqmc_step, Split-2 + Taylor of the given order, re-orthonormalisation
+    every reortho_every steps); the backward is afqmc_walk_backward on a
+    context built from the same (h1, L), which recomputes the walk from
+    checkpoints every ckpt_every steps and returns dJ/dh1 and dJ/dL scaled by
+    the incoming gradient.  The auxiliary fields, the trial, e0 and tau are
+    fixed inputs (no gradient).
+
+    apply(h1 [N,N] float64, L [G,N,N] float64, fields [n, Nw, G] float64 on
+          the device, trial [N, na+nb], na, nb, e0, tau, order, reortho_every,
+          ckpt_every, precision ("fp64" or "mixed"), e_const) -> J (0-dim)"""
+
+    @staticmethod
+    def forward(ctx, h1, chol, fields, trial, na, nb, e0, tau, order=6, reortho_every=0, ckpt_every=10,
+                precision="fp64", e_const=0.0):
+        dev = fields.device
+        c = Context(h1.detach().cpu().numpy(), chol.detach().cpu().numpy(), trial, na, nb, e_const,
+                    precision=precision, device=dev)
+        try:
+            e_mix = walk_energy(c, int(fields.shape[1]), fields, tau, e0, order, reortho_every)
+            J = e_mix[2].clone()
+            torch.cuda.synchronize(dev)
+        finally:
+            c.close()
+        ctx.args = (h1.detach(), chol.detach(), fields, trial, na, nb, e0, tau, order, reortho_every, ckpt_every,
+                    precision, e_const)
+        return J.to(h1.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        h1, chol, fields, trial, na, nb, e0, tau, order, r, ckpt, precision, e_const = ctx.args
+        dev = fields.device
+        c = Context(h1.cpu().numpy(), chol.cpu().numpy(), trial, na, nb, e_const, precision=precision, device=dev)
+        try:
+            w = c.new_walkers(int(fields.shape[1]))
+            c.init_walkers(w)
+            _, gh, gL = c.walk_backward(w, fields, tau, e0, order=order, reortho_every=r, ckpt_every=ckpt,
+                                        dJ=float(grad_out))
+            torch.cuda.synchronize(dev)
+        finally:
+            c.close()
+        return (gh.to(h1.device), gL.to(chol.device)) + (None,) * 11

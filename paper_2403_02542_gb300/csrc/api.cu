@@ -156,28 +156,28 @@ static afqmc_status ws_ensure(afqmc_ctx* c, int Nw, int kmax) {
   Workspace& ws = c->ws;
   const size_t cs = c->prec == AFQMC_FP64 ? 16 : 8;  // complex storage bytes
   const size_t per = (size_t)c->nc * c->N;
-  CK(cudaMalloc(&ws.theta, nw * per * cs));
-  CK(cudaMalloc(&ws.t, (size_t)nw * c->G * cs));
-  CK(cudaMalloc(&ws.c, (size_t)nw * c->G * cs));
-  CK(cudaMalloc(&ws.A, (size_t)nw * c->N * c->N * cs));
-  CK(cudaMalloc(&ws.psi_b, nw * per * cs));
-  CK(cudaMalloc(&ws.term0, nw * per * cs));
-  CK(cudaMalloc(&ws.term1, nw * per * cs));
-  CK(cudaMalloc(&ws.acc, nw * per * cs));
-  CK(cudaMalloc(&ws.psi_new, nw * per * cs));
-  CK(cudaMalloc(&ws.splitk, (size_t)8 * nw * c->G * cs));
+  CK(dmalloc(&ws.theta, nw * per * cs));
+  CK(dmalloc(&ws.t, (size_t)nw * c->G * cs));
+  CK(dmalloc(&ws.c, (size_t)nw * c->G * cs));
+  CK(dmalloc(&ws.A, (size_t)nw * c->N * c->N * cs));
+  CK(dmalloc(&ws.psi_b, nw * per * cs));
+  CK(dmalloc(&ws.term0, nw * per * cs));
+  CK(dmalloc(&ws.term1, nw * per * cs));
+  CK(dmalloc(&ws.acc, nw * per * cs));
+  CK(dmalloc(&ws.psi_new, nw * per * cs));
+  CK(dmalloc(&ws.splitk, (size_t)8 * nw * c->G * cs));
   if (km > 0) {
-    CK(cudaMalloc(&ws.basis, (size_t)km * nw * per * cs));
-    CK(cudaMalloc(&ws.hess, (size_t)nw * c->nc * km * km * 2 * sizeof(double)));
-    CK(cudaMalloc(&ws.beta, (size_t)nw * c->nc * sizeof(double)));
+    CK(dmalloc(&ws.basis, (size_t)km * nw * per * cs));
+    CK(dmalloc(&ws.hess, (size_t)nw * c->nc * km * km * 2 * sizeof(double)));
+    CK(dmalloc(&ws.beta, (size_t)nw * c->nc * sizeof(double)));
   }
-  CK(cudaMalloc(&ws.scal, (size_t)nw * SC_COUNT * sizeof(double)));
-  CK(cudaMalloc(&ws.logdet, (size_t)nw * 4 * sizeof(double)));
-  CK(cudaMalloc(&ws.epart, (size_t)nw * c->G * 8 * sizeof(double)));
-  CK(cudaMalloc(&ws.eloc, (size_t)nw * 2 * sizeof(double)));
-  CK(cudaMalloc(&ws.ecap, (size_t)nw * sizeof(double)));
-  CK(cudaMalloc(&ws.emix, 4 * sizeof(double)));
-  CK(cudaMalloc(&ws.alive, (size_t)nw));
+  CK(dmalloc(&ws.scal, (size_t)nw * SC_COUNT * sizeof(double)));
+  CK(dmalloc(&ws.logdet, (size_t)nw * 4 * sizeof(double)));
+  CK(dmalloc(&ws.epart, (size_t)nw * c->G * 8 * sizeof(double)));
+  CK(dmalloc(&ws.eloc, (size_t)nw * 2 * sizeof(double)));
+  CK(dmalloc(&ws.ecap, (size_t)nw * sizeof(double)));
+  CK(dmalloc(&ws.emix, 4 * sizeof(double)));
+  CK(dmalloc(&ws.alive, (size_t)nw));
   ws.n_walkers = nw;
   ws.kmax = km;
   // the traces a later step could reuse for its force bias were in the freed buffers
@@ -260,22 +260,22 @@ static afqmc_status ctx_setup(afqmc_ctx* c, const double* h1, const double* L, c
   const int N = c->N, nc = c->nc, G = c->G;
   const size_t NN = (size_t)N * N;
   cudaStream_t s = c->stream;
-  CK(cudaMalloc(&c->d_L, (size_t)G * NN * sizeof(double)));
-  CK(cudaMalloc(&c->d_Lh, (size_t)G * nc * N * sizeof(double)));
-  CK(cudaMalloc(&c->d_trial, (size_t)nc * N * sizeof(double)));
-  CK(cudaMalloc(&c->d_hhalf, (size_t)nc * N * sizeof(double)));
-  CK(cudaMalloc(&c->d_Lbar, (size_t)G * sizeof(double)));
-  CK(cudaMalloc(&c->d_B, NN * sizeof(double)));
-  CK(cudaMalloc(&c->d_hpp, NN * sizeof(double)));
-  CK(cudaMalloc(&c->d_bias_key, 2 * sizeof(unsigned long long)));
-  CK(cudaMalloc(&c->d_bias_skip, sizeof(int)));
+  CK(dmalloc(&c->d_L, (size_t)G * NN * sizeof(double)));
+  CK(dmalloc(&c->d_Lh, (size_t)G * nc * N * sizeof(double)));
+  CK(dmalloc(&c->d_trial, (size_t)nc * N * sizeof(double)));
+  CK(dmalloc(&c->d_hhalf, (size_t)nc * N * sizeof(double)));
+  CK(dmalloc(&c->d_Lbar, (size_t)G * sizeof(double)));
+  CK(dmalloc(&c->d_B, NN * sizeof(double)));
+  CK(dmalloc(&c->d_hpp, NN * sizeof(double)));
+  CK(dmalloc(&c->d_bias_key, 2 * sizeof(unsigned long long)));
+  CK(dmalloc(&c->d_bias_skip, sizeof(int)));
   CK(cudaMemsetAsync(c->d_bias_key, 0, 2 * sizeof(unsigned long long), s));
   CK(cudaMemsetAsync(c->d_bias_skip, 0, sizeof(int), s));
   if (c->prec == AFQMC_MIXED) {
-    CK(cudaMalloc(&c->f_L, (size_t)G * NN * sizeof(float)));
-    CK(cudaMalloc(&c->f_Lh, (size_t)G * nc * N * sizeof(float)));
-    CK(cudaMalloc(&c->f_B, NN * sizeof(float)));
-    CK(cudaMalloc(&c->f_trial, (size_t)nc * N * sizeof(float)));
+    CK(dmalloc(&c->f_L, (size_t)G * NN * sizeof(float)));
+    CK(dmalloc(&c->f_Lh, (size_t)G * nc * N * sizeof(float)));
+    CK(dmalloc(&c->f_B, NN * sizeof(float)));
+    CK(dmalloc(&c->f_trial, (size_t)nc * N * sizeof(float)));
   }
   CK(cudaMemcpyAsync(c->d_L, L, (size_t)G * NN * sizeof(double), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->d_trial, trial, (size_t)nc * N * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -311,9 +311,9 @@ static afqmc_status ctx_setup(afqmc_ctx* c, const double* h1, const double* L, c
       }
   }
   double* d_LL = nullptr;
-  CK(cudaMalloc(&c->d_thT, thT.size() * sizeof(double)));
+  CK(dmalloc(&c->d_thT, thT.size() * sizeof(double)));
   double* d_thT = c->d_thT;
-  CK(cudaMalloc(&d_LL, NN * sizeof(double)));
+  CK(dmalloc(&d_LL, NN * sizeof(double)));
   CK(cudaMemcpyAsync(d_thT, thT.data(), thT.size() * sizeof(double), cudaMemcpyHostToDevice, s));
   CK(launch_setup(c, s));
   if (c->prec == AFQMC_MIXED) {
@@ -623,18 +623,19 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
   } else {
     PK(AFQMC_K_HALFSTEP, half(ws.acc, ws.psi_new));
   }
-  // new overlap (and Theta for the local energy when no re-orthonormalisation
-  // follows), weights, commit
-  void* th_new = (p->measure && !p->reortho) ? ws.theta : nullptr;
+  // new overlap (and Theta for the local energy), weights, commit.  Theta =
+  // Psi (trial^T Psi)^{-1} is unchanged by the re-orthonormalisation Psi ->
+  // Psi R^{-1}, and the log-overlap moves by -sum log R_jj, so no second
+  // overlap is needed after it.
+  void* th_new = p->measure ? ws.theta : nullptr;
   PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, ws.psi_new, th_new, ws.logdet, w->status, s));
   PK(AFQMC_K_OTHER, launch_weights<R>(c, w, p->tau, p->e0, s));
   PK(AFQMC_K_OTHER, launch_commit<R>(c, w, p->reortho, s));
   c->launches += 4;
   if (p->reortho) {
-    PK(AFQMC_K_OTHER, launch_mgs<R>(c, Nw, w->psi, ws.alive, s));
-    PK(AFQMC_K_OVERLAP, launch_overlap<R>(c, Nw, w->psi, p->measure ? ws.theta : nullptr, ws.logdet, w->status, s));
-    PK(AFQMC_K_OTHER, launch_logovl_from_logdet(c, w, ws.alive, s));
-    c->launches += 3;
+    PK(AFQMC_K_OTHER, launch_mgs<R>(c, Nw, w->psi, ws.alive, ws.logdet, s));
+    PK(AFQMC_K_OTHER, launch_logovl_shift(c, w, ws.alive, s));
+    c->launches += 2;
   }
   // Theta of every live walker is the one of its committed determinant (for
   // walkers that were already dead it is that of the discarded proposal; their
@@ -1093,7 +1094,7 @@ static afqmc_status walk_backward_alloc(afqmc_ctx* c, const afqmc_walkers* w0, c
   adj_carve<R>(a, b, c, Nw, q->order, q->ckpt_every, nck);
   CK(cudaStreamSynchronize(c->stream));
   char* base = nullptr;
-  cudaError_t e = cudaMalloc(&base, a.used);
+  cudaError_t e = dmalloc(&base, a.used);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return cuda_fail(e, "adjoint workspace");
@@ -1311,7 +1312,7 @@ afqmc_status afqmc_energy_backward(afqmc_ctx* c, const afqmc_walkers* w, double 
             : run_energy<float>(c, w, e0, tau, c->ws.eloc, c->ws.emix);
   if (st != AFQMC_OK) return st;
   double2* ys = nullptr;
-  CK(cudaMalloc(&ys, ((size_t)c->nc * c->N + (size_t)c->G * c->nc * c->N) * sizeof(double2)));
+  CK(dmalloc(&ys, ((size_t)c->nc * c->N + (size_t)c->G * c->nc * c->N) * sizeof(double2)));
   cudaError_t e = fp64 ? launch_energy_backward<double>(c, w->n_walkers, w->weight, c->ws.eloc, e0, tau, dJ, grad_h1,
                                                         grad_L, ys, c->stream)
                        : launch_energy_backward<float>(c, w->n_walkers, w->weight, c->ws.eloc, e0, tau, dJ, grad_h1,

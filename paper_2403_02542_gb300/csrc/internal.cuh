@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <cstddef>
+#include <cstdlib>
 
 #include "../../include/afqmc.h"
 
@@ -119,6 +120,32 @@ enum {
   SC_COUNT = 16
 };
 
+}  // namespace afq
+
+namespace afq {
+// Device allocation of every library buffer.  With the environment variable
+// AFQMC_POISON_ALLOC=1 each new allocation is filled with 0xFF bytes (NaN in
+// every floating-point type) before use, so that a read of memory no kernel
+// wrote shows up as NaN instead of as whatever the allocation last held.
+inline bool poison_allocations() {
+  static const bool on = [] {
+    const char* v = getenv("AFQMC_POISON_ALLOC");
+    return v && v[0] == '1';
+  }();
+  return on;
+}
+inline cudaError_t dmalloc(void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess && poison_allocations()) {
+    e = cudaMemset(*p, 0xFF, bytes);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  }
+  return e;
+}
+template <typename T>
+inline cudaError_t dmalloc(T** p, size_t bytes) {
+  return dmalloc(reinterpret_cast<void**>(p), bytes);
+}
 }  // namespace afq
 
 namespace afq {
@@ -299,7 +326,7 @@ cudaError_t launch_weights(const afqmc_ctx* c, const afqmc_walkers* w, double ta
 template <typename R>
 cudaError_t launch_commit(const afqmc_ctx* c, const afqmc_walkers* w, int reortho, cudaStream_t s);
 template <typename R>
-cudaError_t launch_mgs(const afqmc_ctx* c, int Nw, void* psi, const uint8_t* mask, cudaStream_t s);
+cudaError_t launch_mgs(const afqmc_ctx* c, int Nw, void* psi, const uint8_t* mask, double* logr, cudaStream_t s);
 template <typename R>
 cudaError_t launch_energy(afqmc_ctx* c, int Nw, const double* weight, double e0, double tau,
                           double* e_loc, double* e_mix, cudaStream_t s, int* n_launch);
@@ -308,6 +335,8 @@ cudaError_t launch_init_walkers(const afqmc_ctx* c, const afqmc_walkers* w, cuda
 cudaError_t launch_setup(afqmc_ctx* c, cudaStream_t s);
 cudaError_t launch_logovl_from_logdet(const afqmc_ctx* c, const afqmc_walkers* w,
                                       const uint8_t* mask, cudaStream_t s);
+// logovl[w] -= sum_s log det R_s from the MGS kernel's output in ws.logdet
+cudaError_t launch_logovl_shift(const afqmc_ctx* c, const afqmc_walkers* w, const uint8_t* mask, cudaStream_t s);
 cudaError_t launch_copy_alive(const afqmc_ctx* c, const afqmc_walkers* w, cudaStream_t s);
 
 // block-Krylov action of the exponential (k_block_krylov.cu): bk_ensure sizes

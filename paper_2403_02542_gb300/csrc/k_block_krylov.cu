@@ -392,9 +392,9 @@ cudaError_t bk_ensure(afqmc_ctx* c, int Nw, int k) {
   ws.bk_cap = ws.bk_k = 0;
   const size_t cs = c->prec == AFQMC_FP64 ? 16 : 8;
   const BkLayout L(kk, nmax);
-  e = cudaMalloc(&ws.bk, (size_t)cap * 2 * L.stride * cs);
+  e = dmalloc(&ws.bk, (size_t)cap * 2 * L.stride * cs);
   if (e != cudaSuccess) return e;
-  e = cudaMalloc(&ws.bk_keff, (size_t)cap * 2 * sizeof(int));
+  e = dmalloc(&ws.bk_keff, (size_t)cap * 2 * sizeof(int));
   if (e != cudaSuccess) return e;
   ws.bk_cap = cap;
   ws.bk_k = kk;

@@ -486,6 +486,20 @@ cudaError_t launch_commit(const afqmc_ctx* c, const afqmc_walkers* w, int, cudaS
   return cudaGetLastError();
 }
 
+// after re-orthonormalisation Psi = Q R: log<Psi_T|Q> = log<Psi_T|Psi> - sum_s sum_j log R_jj
+// (the sums per spin in logdet[w][2 spin], written by the MGS kernel)
+__global__ void logovl_shift_kernel(double* __restrict__ logovl, const double* __restrict__ logr,
+                                    const uint8_t* __restrict__ mask, int Nw) {
+  const int w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w >= Nw || (mask && !mask[w])) return;
+  logovl[2 * w] -= logr[w * 4 + 0] + logr[w * 4 + 2];
+}
+
+cudaError_t launch_logovl_shift(const afqmc_ctx* c, const afqmc_walkers* w, const uint8_t* mask, cudaStream_t s) {
+  logovl_shift_kernel<<<(w->n_walkers + 127) / 128, 128, 0, s>>>(w->logovl, c->ws.logdet, mask, w->n_walkers);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_logovl_from_logdet(const afqmc_ctx* c, const afqmc_walkers* w, const uint8_t* mask,
                                       cudaStream_t s) {
   logovl_kernel<<<(w->n_walkers + 127) / 128, 128, 0, s>>>(w->logovl, c->ws.logdet, mask, w->n_walkers);

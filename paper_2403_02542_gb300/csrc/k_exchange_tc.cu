@@ -616,11 +616,11 @@ bool tc_exchange_plan(afqmc_ctx* c) {
 cudaError_t tc_exchange_setup(afqmc_ctx* c, cudaStream_t s) {
   TcPlan& P = c->tc;
   const size_t elems = (size_t)2 * P.T * 128 * P.Kp;
-  cudaError_t e = cudaMalloc(&P.a_hi, elems * 2);
+  cudaError_t e = dmalloc(&P.a_hi, elems * 2);
   if (e != cudaSuccess) return e;
-  e = cudaMalloc(&P.a_lo, elems * 2);
+  e = dmalloc(&P.a_lo, elems * 2);
   if (e != cudaSuccess) return e;
-  e = cudaMalloc(&P.err, sizeof(int));
+  e = dmalloc(&P.err, sizeof(int));
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(P.err, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
@@ -660,10 +660,10 @@ cudaError_t tc_exchange_ws(afqmc_ctx* c) {
   P.b_cap = 0;
   const int cap = c->ws.n_walkers;
   void *hi = nullptr, *lo = nullptr;
-  cudaError_t e = cudaMalloc(&hi, tc_exchange_plane_bytes(P, cap));
+  cudaError_t e = dmalloc(&hi, tc_exchange_plane_bytes(P, cap));
   if (e != cudaSuccess) return e;
   P.b_hi = hi;
-  e = cudaMalloc(&lo, tc_exchange_plane_bytes(P, cap));
+  e = dmalloc(&lo, tc_exchange_plane_bytes(P, cap));
   if (e != cudaSuccess) return e;
   P.b_lo = lo;
   return tc_exchange_bind(P, hi, lo, cap);

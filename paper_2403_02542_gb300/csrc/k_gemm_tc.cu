@@ -195,25 +195,39 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
       const bool row_ok = m < p.M;
       float* orow = MODE == 2 ? nullptr : p.out + (size_t)w * p.Nn * 2;
       const int e_base = nt * TG_BN;
-      for (int c0 = 0; c0 < TG_BN; c0 += 8) {
+      if constexpr (MODE == 2) {
+        // row m = p; columns (Re, Im) of 128 orbitals, in chunks of 32
+        // orbitals: the 32 input loads of a chunk are issued together (each a
+        // 256-byte warp access over 32 consecutive p), then the chunk's 64
+        // accumulator columns are read and the sums stored
+        for (int c0 = 0; c0 < TG_BN; c0 += 64) {
+          const int wj0 = (e_base + c0) >> 1;
+          float2 x[32];
+#pragma unroll
+          for (int t = 0; t < 32; ++t) {
+            x[t] = make_float2(0.f, 0.f);
+            if (row_ok && 2 * (wj0 + t) < p.Nn) x[t] = p.hs_in[(size_t)(wj0 + t) * p.N + m];
+          }
+          uint32_t v[64];
+          const uint32_t ta = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * TG_BN + c0);
+          tmem_ld32(ta, v);
+          tmem_ld32(ta + 32, v + 32);
+          tmem_wait_ld();
+#pragma unroll
+          for (int t = 0; t < 32; ++t) {
+            if (row_ok && 2 * (wj0 + t) < p.Nn) {
+              x[t].x += __uint_as_float(v[2 * t]);
+              x[t].y += __uint_as_float(v[2 * t + 1]);
+              p.hs_out[(size_t)(wj0 + t) * p.N + m] = x[t];
+            }
+          }
+        }
+      }
+      for (int c0 = 0; MODE != 2 && c0 < TG_BN; c0 += 8) {
         uint32_t v[8];
         tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * TG_BN + c0), v);
         tmem_wait_ld();
-        if constexpr (MODE == 2) {
-          // row m = p; columns e0 .. e0 + 7 = (Re, Im) of orbitals wj .. wj + 3
-          if (!row_ok) continue;
-          const int wj0 = (e_base + c0) >> 1;
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            if (2 * (wj0 + t) < p.Nn) {
-              const size_t o = (size_t)(wj0 + t) * p.N + m;
-              float2 x = p.hs_in[o];
-              x.x += __uint_as_float(v[2 * t]);
-              x.y += __uint_as_float(v[2 * t + 1]);
-              p.hs_out[o] = x;
-            }
-          }
-        } else if constexpr (MODE == 1) {
+        if constexpr (MODE == 1) {
           // row 2w + part -> plane column part * N + q of row p of walker w
           const int e0 = e_base + c0;
           if (!row_ok || e0 >= p.Nn) continue;
@@ -606,11 +620,11 @@ cudaError_t tc_field_setup(afqmc_ctx* c, cudaStream_t s) {
   P.Kp = ((c->G + 63) / 64) * 64;
   P.Np = ((NN + TG_BN - 1) / TG_BN) * TG_BN;
   if (P.Np / TG_BN > (size_t)(1 << 20)) return cudaSuccess;
-  cudaError_t e = cudaMalloc(&P.l_hi, P.Np * P.Kp * 2);
+  cudaError_t e = dmalloc(&P.l_hi, P.Np * P.Kp * 2);
   if (e != cudaSuccess) return e;
-  e = cudaMalloc(&P.l_lo, P.Np * P.Kp * 2);
+  e = dmalloc(&P.l_lo, P.Np * P.Kp * 2);
   if (e != cudaSuccess) return e;
-  e = cudaMalloc(&P.err, sizeof(int));
+  e = dmalloc(&P.err, sizeof(int));
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(P.err, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
@@ -625,9 +639,9 @@ cudaError_t tc_field_setup(afqmc_ctx* c, cudaStream_t s) {
   // half steps: D planes [hs_Mp][hs_Kp] (filled by tc_halfstep_set_b)
   P.hs_Mp = ((c->N + TG_BM - 1) / TG_BM) * TG_BM;
   P.hs_Kp = ((c->N + 63) / 64) * 64;
-  e = cudaMalloc(&P.d_hi, (size_t)P.hs_Mp * P.hs_Kp * 2);
+  e = dmalloc(&P.d_hi, (size_t)P.hs_Mp * P.hs_Kp * 2);
   if (e != cudaSuccess) return e;
-  e = cudaMalloc(&P.d_lo, (size_t)P.hs_Mp * P.hs_Kp * 2);
+  e = dmalloc(&P.d_lo, (size_t)P.hs_Mp * P.hs_Kp * 2);
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(P.d_hi, 0, (size_t)P.hs_Mp * P.hs_Kp * 2, s);
   if (e != cudaSuccess) return e;
@@ -667,9 +681,9 @@ cudaError_t tc_field_ws(afqmc_ctx* c) {
     // walker planes: rows 2 (w nc + j) + part, padded to the 256-row column tile;
     // the K padding N .. hs_Kp and the padding rows stay zero
     const size_t rows = (((size_t)2 * cap * c->nc + TG_BN - 1) / TG_BN) * TG_BN;
-    cudaError_t e = cudaMalloc(&P.p_hi, rows * P.hs_Kp * 2);
+    cudaError_t e = dmalloc(&P.p_hi, rows * P.hs_Kp * 2);
     if (e != cudaSuccess) return e;
-    e = cudaMalloc(&P.p_lo, rows * P.hs_Kp * 2);
+    e = dmalloc(&P.p_lo, rows * P.hs_Kp * 2);
     if (e != cudaSuccess) return e;
     e = cudaMemset(P.p_hi, 0, rows * P.hs_Kp * 2);
     if (e != cudaSuccess) return e;
@@ -681,9 +695,9 @@ cudaError_t tc_field_ws(afqmc_ctx* c) {
     P.hs_rows = (int)rows;
   }
   const int mp = ((2 * cap + TG_BM - 1) / TG_BM) * TG_BM;
-  cudaError_t e = cudaMalloc(&P.x_hi, (size_t)mp * P.Kp * 2);
+  cudaError_t e = dmalloc(&P.x_hi, (size_t)mp * P.Kp * 2);
   if (e != cudaSuccess) return e;
-  e = cudaMalloc(&P.x_lo, (size_t)mp * P.Kp * 2);
+  e = dmalloc(&P.x_lo, (size_t)mp * P.Kp * 2);
   if (e != cudaSuccess) return e;
   if (!make_map(reinterpret_cast<CUtensorMap*>(P.map_x_hi), P.x_hi, (size_t)mp, P.Kp, TG_BM) ||
       !make_map(reinterpret_cast<CUtensorMap*>(P.map_x_lo), P.x_lo, (size_t)mp, P.Kp, TG_BM))
@@ -691,18 +705,18 @@ cudaError_t tc_field_ws(afqmc_ctx* c) {
   P.m_cap = mp;
   if (P.av_ok) {
     const size_t arows = (size_t)cap * c->N, vrows = (size_t)cap * P.NBp;
-    e = cudaMalloc(&P.a_hi, arows * P.KA * 2);
+    e = dmalloc(&P.a_hi, arows * P.KA * 2);
     if (e != cudaSuccess) return e;
-    e = cudaMalloc(&P.a_lo, arows * P.KA * 2);
+    e = dmalloc(&P.a_lo, arows * P.KA * 2);
     if (e != cudaSuccess) return e;
     // the K padding columns 2N..KA stay zero (the field epilogue writes k < 2N only)
     e = cudaMemset(P.a_hi, 0, arows * P.KA * 2);
     if (e != cudaSuccess) return e;
     e = cudaMemset(P.a_lo, 0, arows * P.KA * 2);
     if (e != cudaSuccess) return e;
-    e = cudaMalloc(&P.v_hi, vrows * P.KA * 2);
+    e = dmalloc(&P.v_hi, vrows * P.KA * 2);
     if (e != cudaSuccess) return e;
-    e = cudaMalloc(&P.v_lo, vrows * P.KA * 2);
+    e = dmalloc(&P.v_lo, vrows * P.KA * 2);
     if (e != cudaSuccess) return e;
     // rows 2 nc..NBp and columns 2N..KA stay zero when the Arnoldi kernels fill the planes
     e = cudaMemset(P.v_hi, 0, vrows * P.KA * 2);

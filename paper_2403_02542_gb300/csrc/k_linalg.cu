@@ -247,9 +247,12 @@ __global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* _
 // One warp per determinant (walker w, spin): columns in order, the current
 // column in registers (EPL elements per lane), projections and norms reduced
 // with warp shuffles in the walkers' precision (the reciprocal norm in FP64).
+// Psi = Q R with R_jj = ||q_j|| > 0, so log det(trial^T Q) = log det(trial^T
+// Psi) - sum_j log R_jj: the kernel writes sum_j log R_jj (FP64) of
+// determinant (w, spin) to logr[w * 4 + 2 * spin].
 template <typename R, int EPL>
 __global__ void mgs_kernel(typename C2<R>::t* __restrict__ psi, int N, int na, int nb, int Nw,
-                           const uint8_t* __restrict__ mask) {
+                           const uint8_t* __restrict__ mask, double* __restrict__ logr) {
   typedef typename C2<R>::t cplx;
   const int det = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (det >= 2 * Nw) return;
@@ -257,6 +260,7 @@ __global__ void mgs_kernel(typename C2<R>::t* __restrict__ psi, int N, int na, i
   if (mask && !mask[w]) return;
   const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
   cplx* P = psi + ((size_t)w * nc + off) * N;
+  double lr = 0.0;
   for (int j = 0; j < n; ++j) {
     R qr[EPL], qi[EPL];
 #pragma unroll
@@ -293,7 +297,9 @@ __global__ void mgs_kernel(typename C2<R>::t* __restrict__ psi, int N, int na, i
     R ps = R(0);
 #pragma unroll
     for (int e = 0; e < EPL; ++e) ps += qr[e] * qr[e] + qi[e] * qi[e];
-    const R inv = (R)(1.0 / sqrt((double)warp_sum(ps)));
+    const double nrm2 = (double)warp_sum(ps);
+    lr += 0.5 * log(nrm2);
+    const R inv = (R)(1.0 / sqrt(nrm2));
 #pragma unroll
     for (int e = 0; e < EPL; ++e) {
       const int p = lane + 32 * e;
@@ -306,6 +312,7 @@ __global__ void mgs_kernel(typename C2<R>::t* __restrict__ psi, int N, int na, i
     }
     __syncwarp();
   }
+  if (logr && lane == 0) logr[(size_t)w * 4 + 2 * spin] = lr;
 }
 
 // ---------------------------------------------------------------- Krylov
@@ -699,16 +706,18 @@ cudaError_t launch_overlap(const afqmc_ctx* c, int Nw, const void* psi, void* th
 }
 
 template <typename R>
-cudaError_t launch_mgs(const afqmc_ctx* c, int Nw, void* psi, const uint8_t* mask, cudaStream_t s) {
+cudaError_t launch_mgs(const afqmc_ctx* c, int Nw, void* psi, const uint8_t* mask, double* logr, cudaStream_t s) {
   const int dets = 2 * Nw;
   typename C2<R>::t* P = static_cast<typename C2<R>::t*>(psi);
   const dim3 grid((dets + 7) / 8);
   if (c->N <= 128)
-    mgs_kernel<R, 4><<<grid, 256, 0, s>>>(P, c->N, c->na, c->nb, Nw, mask);
+    mgs_kernel<R, 4><<<grid, 256, 0, s>>>(P, c->N, c->na, c->nb, Nw, mask, logr);
   else if (c->N <= 256)
-    mgs_kernel<R, 8><<<grid, 256, 0, s>>>(P, c->N, c->na, c->nb, Nw, mask);
+    mgs_kernel<R, 8><<<grid, 256, 0, s>>>(P, c->N, c->na, c->nb, Nw, mask, logr);
+  else if (c->N <= 320)
+    mgs_kernel<R, 10><<<grid, 256, 0, s>>>(P, c->N, c->na, c->nb, Nw, mask, logr);
   else
-    mgs_kernel<R, 16><<<grid, 256, 0, s>>>(P, c->N, c->na, c->nb, Nw, mask);
+    mgs_kernel<R, 16><<<grid, 256, 0, s>>>(P, c->N, c->na, c->nb, Nw, mask, logr);
   return cudaGetLastError();
 }
 
@@ -831,7 +840,7 @@ cudaError_t launch_cn_solve(const afqmc_ctx* c, int Nw, void* X, void* Y, cudaSt
   template cudaError_t launch_cn_solve<R>(const afqmc_ctx*, int, void*, void*, cudaStream_t);               \
   template cudaError_t launch_overlap<R>(const afqmc_ctx*, int, const void*, void*, double*, uint32_t*,   \
                                          cudaStream_t, const int*);                                        \
-  template cudaError_t launch_mgs<R>(const afqmc_ctx*, int, void*, const uint8_t*, cudaStream_t);          \
+  template cudaError_t launch_mgs<R>(const afqmc_ctx*, int, void*, const uint8_t*, double*, cudaStream_t);  \
   template cudaError_t launch_krylov_init<R>(const afqmc_ctx*, int, cudaStream_t);                         \
   template cudaError_t launch_krylov_orth<R>(const afqmc_ctx*, int, int, int, cudaStream_t);               \
   template cudaError_t launch_krylov_finish<R>(const afqmc_ctx*, int, int, cudaStream_t);                  \

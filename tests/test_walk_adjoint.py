@@ -330,3 +330,51 @@ def test_walk_adjoint_mixed_full_size_against_fp64():
     assert abs(float(J32[2]) - float(J64[2])) <= MIXED_J_TOL
     _close(gh32, gh64, MIXED_GRAD_RTOL)
     _close(gL32, gL64, MIXED_GRAD_RTOL)
+
+
+def test_walk_energy_autograd_function_matches_the_oracle():
+    """WalkEnergy: forward = the walk through afqmc_step, backward =
+    afqmc_walk_backward.  J and the gradients that torch autograd returns
+    through it equal the oracle's walk objective and its autograd gradients
+    (FP64, entry by entry at the FP64 gradient bar)."""
+    from paper_2403_02542_gb300.api import WalkEnergy
+    s = _Sys(12, 2, 2, 16, seed=31)
+    tau, order, nw, steps, r = 0.05, 6, 6, 6, 2
+    e0 = _e0(s)
+    fields = [make_fields(31, k, nw, s.G) for k in range(steps)]
+    J_ref, gh_ref, gL_ref, _, W_ref = _oracle(s, nw, fields, tau, e0, order, r)
+    assert int((W_ref > 0).sum()) == nw
+    h1 = torch.tensor(s.h1, dtype=RT, requires_grad=True)
+    L = torch.tensor(s.L, dtype=RT, requires_grad=True)
+    f = torch.as_tensor(np.stack(fields), device="cuda")
+    J = WalkEnergy.apply(h1, L, f, s.trial, s.na, s.nb, e0, tau, order, r, 2, "fp64", s.e_const)
+    assert abs(float(J) - J_ref) <= 1e-10 * abs(J_ref)
+    gh, gL = torch.autograd.grad(J, [h1, L])
+    _close_entrywise(gh.cpu(), gh_ref, "WalkEnergy dJ/dh1")
+    _close_entrywise(gL.cpu(), gL_ref, "WalkEnergy dJ/dL")
+    # the incoming gradient scales the result
+    J2 = WalkEnergy.apply(h1, L, f, s.trial, s.na, s.nb, e0, tau, order, r, 2, "fp64", s.e_const)
+    gh2, = torch.autograd.grad(3.0 * J2, [h1])
+    assert torch.allclose(gh2, 3.0 * gh, rtol=1e-14, atol=0.0)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-6), ("mixed", 2e-3)])
+def test_path_scan_derivative_against_central_differences(precision, tol):
+    """A three-point scan h1(s) = h1 + s dH1, L(s) = L + s dL: the adjoint
+    derivative dJ/ds at every point against central differences of J(s)
+    (FP64: 1e-6 relative; mixed: FP32 noise in J over the step 1e-2 bounds
+    the difference, 2e-3 of max(|dJ/ds|, 1))."""
+    from paper_2403_02542_gb300.scan import path_scan
+    s = _Sys(16, 3, 3, 24, seed=41)
+    tau, order, nw, steps, r = 0.05, 6, 8, 6, 3
+    e0 = _e0(s)
+    rng = np.random.default_rng(41)
+    dH = rng.standard_normal(s.h1.shape); dH = 0.01 * (dH + dH.T)
+    dL = rng.standard_normal(s.L.shape); dL = 0.01 * np.abs(s.L).max() * (dL + dL.transpose(0, 2, 1))
+    f = torch.as_tensor(np.stack([make_fields(41, k, nw, s.G) for k in range(steps)]), device="cuda")
+    pts = path_scan(s, f, [-0.05, 0.0, 0.05], dH, dL, tau, e0, order=order, reortho_every=r, ckpt_every=3,
+                    precision=precision, fd_step=1e-2 if precision == "mixed" else 1e-4)
+    for p in pts:
+        assert p["live"] == nw
+        assert abs(p["dJds"] - p["dJds_fd"]) <= tol * max(abs(p["dJds"]), 1.0), p
+    assert len({round(p["J"], 12) for p in pts}) == 3     # the path moves the energy
