@@ -148,6 +148,7 @@ static void ws_free(Workspace& ws) {
 }
 
 static afqmc_status ws_ensure(afqmc_ctx* c, int Nw, int kmax) {
+  AllocScope alloc_scope(AG_WORKSPACE);
   if (Nw <= c->ws.n_walkers && kmax <= c->ws.kmax) return AFQMC_OK;
   const int nw = Nw > c->ws.n_walkers ? Nw : c->ws.n_walkers;
   const int km = kmax > c->ws.kmax ? kmax : c->ws.kmax;
@@ -257,6 +258,7 @@ static void ctx_free(afqmc_ctx* c) {
 }
 
 static afqmc_status ctx_setup(afqmc_ctx* c, const double* h1, const double* L, const double* trial) {
+  AllocScope alloc_scope(AG_CONTEXT);
   const int N = c->N, nc = c->nc, G = c->G;
   const size_t NN = (size_t)N * N;
   cudaStream_t s = c->stream;
@@ -1085,6 +1087,7 @@ template <typename R>
 static afqmc_status walk_backward_alloc(afqmc_ctx* c, const afqmc_walkers* w0, const double* fields,
                                         const afqmc_walk_adjoint_params* q, int nck, double* J_out, double* grad_h1,
                                         double* grad_L, void* grad_psi0) {
+  AllocScope alloc_scope(AG_ADJOINT);
   const int Nw = w0->n_walkers;
   const size_t NN = (size_t)c->N * c->N;
   AdjBufs<R> b{};

@@ -127,12 +127,27 @@ namespace afq {
 // AFQMC_POISON_ALLOC=1 each new allocation is filled with 0xFF bytes (NaN in
 // every floating-point type) before use, so that a read of memory no kernel
 // wrote shows up as NaN instead of as whatever the allocation last held.
+// AFQMC_POISON_ALLOC=<mask> restricts it to groups of allocations: bit 0
+// context constants, bit 1 step workspace, bit 2 walk-adjoint workspace, bit
+// 3 tensor-core operand planes, bit 4 everything else ("1" poisons all).
+enum AllocGroup { AG_CONTEXT = 0, AG_WORKSPACE = 1, AG_ADJOINT = 2, AG_PLANES = 3, AG_OTHER = 4 };
+inline int& alloc_group() {
+  static thread_local int g = AG_OTHER;
+  return g;
+}
+struct AllocScope {  // allocations inside the scope belong to group g
+  int prev;
+  explicit AllocScope(int g) : prev(alloc_group()) { alloc_group() = g; }
+  ~AllocScope() { alloc_group() = prev; }
+};
 inline bool poison_allocations() {
-  static const bool on = [] {
+  static const unsigned mask = [] {
     const char* v = getenv("AFQMC_POISON_ALLOC");
-    return v && v[0] == '1';
+    if (!v || !v[0] || v[0] == '0') return 0u;
+    if (v[0] == '1' && v[1] == 0) return 0xFFu;
+    return (unsigned)strtoul(v, nullptr, 0);
   }();
-  return on;
+  return (mask >> alloc_group()) & 1u;
 }
 inline cudaError_t dmalloc(void** p, size_t bytes) {
   cudaError_t e = cudaMalloc(p, bytes);

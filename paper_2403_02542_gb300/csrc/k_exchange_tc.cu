@@ -653,6 +653,7 @@ cudaError_t tc_exchange_bind(TcPlan& P, void* b_hi, void* b_lo, int cap) {
 
 // (Re)allocate the split Theta planes for the workspace's walker capacity.
 cudaError_t tc_exchange_ws(afqmc_ctx* c) {
+  AllocScope alloc_scope(AG_PLANES);
   TcPlan& P = c->tc;
   if (P.b_hi) cudaFree(P.b_hi);
   if (P.b_lo) cudaFree(P.b_lo);

@@ -667,6 +667,7 @@ cudaError_t tc_field_setup(afqmc_ctx* c, cudaStream_t s) {
 
 // Operand planes sized for the workspace's walker capacity.
 cudaError_t tc_field_ws(afqmc_ctx* c) {
+  AllocScope alloc_scope(AG_PLANES);
   TgPlan& P = c->tg;
   if (!P.ok) return cudaSuccess;
   void* old[] = {P.x_hi, P.x_lo, P.a_hi, P.a_lo, P.v_hi, P.v_lo, P.p_hi, P.p_lo};

@@ -243,6 +243,212 @@ __global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* _
   }
 }
 
+// ---------------------------------------------------------------- overlap, complex64 walkers
+// grid (Nw, 2 spins), block 256.  The same quantities as overlap_kernel with
+// the work laid out for FP32 walkers:
+//   O = trial_s^T Psi_s in FP32, p in tiles of 32 staged through shared
+//     memory (each thread owns up to OV_MAXE entries of O in registers);
+//   the LU of O with partial pivoting and log det O in FP64 (each warp owns
+//     rows i = k + 1 + warp (mod 8), its lanes the columns j);
+//   O^{-1} in FP32 from the rounded factors, one thread per column
+//     (P O = L U, so column j of O^{-1} is U^{-1} L^{-1} P e_j);
+//   Theta = Psi O^{-1}: threads over (p, block of OV_JB columns j), the
+//     rows of O^{-1} read from shared memory (broadcast within a warp), Psi
+//     from L1, Theta stored coalesced over p.
+// Shared: LU [n][n] FP64 complex, Lf and Inv [n][n] FP32 complex; the O
+// staging tiles trial [32][n] and Psi [32][n] occupy the Lf area, which is
+// written only after the LU.
+constexpr int OV_TP = 32, OV_MAXE = 25, OV_JB = 10;  // p tile; (80 * 80) / 256 entries; Theta column block
+size_t overlap_c64_smem(int nmax) {
+  const size_t lf = (size_t)nmax * nmax * 8, stage = (size_t)OV_TP * nmax * 12;
+  return (size_t)nmax * nmax * 16 + (lf > stage ? lf : stage) + (size_t)nmax * nmax * 8;
+}
+
+__global__ void __launch_bounds__(256) overlap_c64_kernel(const float2* __restrict__ psi,
+                                                          const float* __restrict__ trial_f, int N, int na, int nb,
+                                                          float2* __restrict__ theta, double* __restrict__ logdet,
+                                                          uint32_t* __restrict__ status, const int* __restrict__ skip) {
+  extern __shared__ double smem_oc[];
+  if (skip && *skip) return;
+  const int w = blockIdx.x, spin = blockIdx.y;
+  const int n = spin ? nb : na, off = spin ? na : 0, nc = na + nb;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  double* ldw = logdet + (size_t)w * 4 + spin * 2;
+  if (n == 0) {
+    if (tid == 0) { ldw[0] = 0.0; ldw[1] = 0.0; }
+    return;
+  }
+  cd* LU = reinterpret_cast<cd*>(smem_oc);                 // [n][n]
+  float2* Lf = reinterpret_cast<float2*>(LU + n * n);      // [n][n] rounded factors (after the LU)
+  float* Ts = reinterpret_cast<float*>(Lf);                // [OV_TP][n] (before the LU)
+  float2* Ps = reinterpret_cast<float2*>(Ts + OV_TP * n);  // [OV_TP][n] (before the LU)
+  const size_t lf_words = ((size_t)n * n * 8 > (size_t)OV_TP * n * 12 ? (size_t)n * n * 8 : (size_t)OV_TP * n * 12) / 8;
+  float2* Inv = Lf + lf_words;                             // [n][n] O^{-1}
+  __shared__ int perm[128];
+  __shared__ int s_piv, s_swaps, s_sing;
+  __shared__ cd s_rpk;
+  const float2* P = psi + ((size_t)w * nc + off) * N;
+  const float* T = trial_f + (size_t)off * N;
+  const int nn = n * n;
+
+  // O[i][j] = sum_p T[i][p] P[j][p]
+  float ar[OV_MAXE], ai[OV_MAXE];
+#pragma unroll
+  for (int r = 0; r < OV_MAXE; ++r) { ar[r] = 0.f; ai[r] = 0.f; }
+  for (int p0 = 0; p0 < N; p0 += OV_TP) {
+    __syncthreads();
+    for (int e = tid; e < OV_TP * n; e += 256) {  // e = i * OV_TP + pp: consecutive pp are consecutive p
+      const int i = e / OV_TP, pp = e - i * OV_TP, p = p0 + pp;
+      Ts[pp * n + i] = p < N ? T[(size_t)i * N + p] : 0.f;
+      Ps[pp * n + i] = p < N ? P[(size_t)i * N + p] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < OV_MAXE; ++r) {
+      const int e = tid + 256 * r;
+      if (e < nn) {
+        const int i = e / n, j = e - i * n;
+        float sr = ar[r], si = ai[r];
+#pragma unroll 8
+        for (int pp = 0; pp < OV_TP; ++pp) {
+          const float t = Ts[pp * n + i];
+          const float2 x = Ps[pp * n + j];
+          sr = fmaf(t, x.x, sr);
+          si = fmaf(t, x.y, si);
+        }
+        ar[r] = sr;
+        ai[r] = si;
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < OV_MAXE; ++r) {
+    const int e = tid + 256 * r;
+    if (e < nn) LU[e] = mk((double)ar[r], (double)ai[r]);
+  }
+  if (tid < n) perm[tid] = tid;
+  if (tid == 0) { s_swaps = 0; s_sing = 0; }
+  __syncthreads();
+
+  // LU with partial pivoting in FP64: (P O) = L U, row i of PO is row perm[i] of O
+  for (int k = 0; k < n; ++k) {
+    if (wid == 0) {  // pivot: largest |LU[i][k]|, i >= k; ties keep the smaller row
+      int piv = k;
+      double best = -1.0;
+      for (int i = k + lane; i < n; i += 32) {
+        const double v = abs2(LU[i * n + k]);
+        if (v > best) { best = v; piv = i; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, piv, o);
+        if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
+      }
+      if (lane == 0) {
+        s_piv = piv;
+        if (!(best > 0.0)) s_sing = 1;
+        s_rpk = crecip(LU[piv * n + k]);
+        if (piv != k) {
+          s_swaps ^= 1;
+          const int t = perm[k]; perm[k] = perm[piv]; perm[piv] = t;
+        }
+      }
+    }
+    __syncthreads();
+    const int piv = s_piv;
+    if (piv != k)
+      for (int j = tid; j < n; j += 256) {
+        const cd t = LU[k * n + j]; LU[k * n + j] = LU[piv * n + j]; LU[piv * n + j] = t;
+      }
+    __syncthreads();
+    const cd rpk = s_rpk;
+    for (int i = k + 1 + wid; i < n; i += 8) {  // warp: row i; lanes: columns j
+      const cd lik = LU[i * n + k] * rpk;
+      for (int j = k + 1 + lane; j < n; j += 32) LU[i * n + j] = LU[i * n + j] - lik * LU[k * n + j];
+      __syncwarp();
+      if (lane == 0) LU[i * n + k] = lik;
+    }
+    __syncthreads();
+  }
+
+  // log det = sum_i log U_ii + i pi [odd number of swaps], summed across warp 0
+  if (wid == 0) {
+    double lr = 0.0, li = 0.0;
+    for (int k = lane; k < n; k += 32) {
+      const cd u = LU[k * n + k];
+      lr += 0.5 * log(abs2(u));
+      li += atan2(u.im, u.re);
+    }
+    lr = warp_sum(lr);
+    li = warp_sum(li);
+    if (lane == 0) {
+      li += s_swaps ? M_PI : 0.0;
+      if (s_sing) { lr = CUDART_NAN; li = CUDART_NAN; }
+      ldw[0] = lr;
+      ldw[1] = li;
+      if (s_sing && status) atomicOr(status + w, (uint32_t)AFQMC_W_SINGULAR);
+    }
+  }
+  if (!theta) return;
+
+  // O^{-1} = U^{-1} L^{-1} P in FP32 from the rounded factors (the diagonal of U inverted in FP64)
+  for (int e = tid; e < nn; e += 256) Lf[e] = make_float2((float)LU[e].re, (float)LU[e].im);
+  __syncthreads();
+  if (tid < n) {
+    const int j = tid;
+    int r = 0;
+    while (perm[r] != j) ++r;
+    for (int i = 0; i < r; ++i) Inv[i * n + j] = make_float2(0.f, 0.f);
+    Inv[r * n + j] = make_float2(1.f, 0.f);
+    for (int i = r + 1; i < n; ++i) {  // L y = P e_j (unit lower L)
+      float yr = 0.f, yi = 0.f;
+      for (int k = r; k < i; ++k) {
+        const float2 l = Lf[i * n + k], y = Inv[k * n + j];
+        yr -= l.x * y.x - l.y * y.y;
+        yi -= l.x * y.y + l.y * y.x;
+      }
+      Inv[i * n + j] = make_float2(yr, yi);
+    }
+    for (int i = n - 1; i >= 0; --i) {  // U x = y
+      float2 x = Inv[i * n + j];
+      for (int k = i + 1; k < n; ++k) {
+        const float2 u = Lf[i * n + k], v = Inv[k * n + j];
+        x.x -= u.x * v.x - u.y * v.y;
+        x.y -= u.x * v.y + u.y * v.x;
+      }
+      const cd rd = crecip(LU[i * n + i]);
+      const float dr = (float)rd.re, di = (float)rd.im;
+      Inv[i * n + j] = make_float2(x.x * dr - x.y * di, x.x * di + x.y * dr);
+    }
+  }
+  __syncthreads();
+
+  // Theta[j][p] = sum_i Psi[i][p] O^{-1}[i][j]
+  float2* Th = theta + ((size_t)w * nc + off) * N;
+  const int nblk = (n + OV_JB - 1) / OV_JB;
+  for (int it = tid; it < N * nblk; it += 256) {
+    const int jb = it / N, p = it - jb * N, j0 = jb * OV_JB;
+    float sr[OV_JB], si[OV_JB];
+#pragma unroll
+    for (int t = 0; t < OV_JB; ++t) { sr[t] = 0.f; si[t] = 0.f; }
+    for (int i = 0; i < n; ++i) {
+      const float2 x = P[(size_t)i * N + p];
+#pragma unroll
+      for (int t = 0; t < OV_JB; ++t) {
+        if (j0 + t < n) {
+          const float2 v = Inv[i * n + j0 + t];
+          sr[t] = fmaf(x.x, v.x, fmaf(-x.y, v.y, sr[t]));
+          si[t] = fmaf(x.x, v.y, fmaf(x.y, v.x, si[t]));
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < OV_JB; ++t)
+      if (j0 + t < n) Th[(size_t)(j0 + t) * N + p] = make_float2(sr[t], si[t]);
+  }
+}
+
 // ---------------------------------------------------------------- MGS QR
 // One warp per determinant (walker w, spin): columns in order, the current
 // column in registers (EPL elements per lane), projections and norms reduced
@@ -693,6 +899,18 @@ template <typename R>
 cudaError_t launch_overlap(const afqmc_ctx* c, int Nw, const void* psi, void* theta, double* logdet,
                            uint32_t* status, cudaStream_t s, const int* skip) {
   const int nmax = c->na > c->nb ? c->na : c->nb;
+  if constexpr (std::is_same<R, float>::value) {
+    const size_t shc = overlap_c64_smem(nmax);
+    if (shc <= (size_t)max_dyn_smem()) {
+      if (!capturing(c)) {
+        cudaError_t e = raise_smem_limit(overlap_c64_kernel);
+        if (e != cudaSuccess) return e;
+      }
+      overlap_c64_kernel<<<dim3(Nw, 2), 256, shc, s>>>(static_cast<const float2*>(psi), c->f_trial, c->N, c->na,
+                                                       c->nb, static_cast<float2*>(theta), logdet, status, skip);
+      return cudaGetLastError();
+    }
+  }
   const size_t shm = (size_t)(2 * nmax * nmax + nmax) * sizeof(cd);
   if (!capturing(c)) {
     cudaError_t e = raise_smem_limit(overlap_kernel<R>);
@@ -819,6 +1037,7 @@ cudaError_t launch_init_walkers(const afqmc_ctx* c, const afqmc_walkers* w, cuda
 template <typename R>
 cudaError_t prepare_overlap(const afqmc_ctx*) {
   cudaError_t e = raise_smem_limit(overlap_kernel<R>);
+  if (e == cudaSuccess && std::is_same<R, float>::value) e = raise_smem_limit(overlap_c64_kernel);
   if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_kernel<R, 8, true>);
   if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_kernel<R, 12, true>);
   if (e == cudaSuccess) e = raise_smem_limit(krylov_expm_kernel<R, 16, true>);
