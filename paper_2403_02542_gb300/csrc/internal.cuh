@@ -143,7 +143,7 @@ struct AllocScope {  // allocations inside the scope belong to group g
 inline bool poison_allocations() {
   static const unsigned mask = [] {
     const char* v = getenv("AFQMC_POISON_ALLOC");
-    if (!v || !v[0] || v[0] == '0') return 0u;
+    if (!v || !v[0]) return 0u;
     if (v[0] == '1' && v[1] == 0) return 0xFFu;
     return (unsigned)strtoul(v, nullptr, 0);
   }();
