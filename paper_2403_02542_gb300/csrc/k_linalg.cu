@@ -218,7 +218,7 @@ __global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* _
     __syncthreads();
     for (int j = tid; j < n; j += nt) {
       int r = 0;
-      while (perm[r] != j) ++r;
+      while (r < n - 1 && perm[r] != j) ++r;
       for (int i = 0; i < r; ++i) Inv[i * n + j] = mk(0.0, 0.0);
       Inv[r * n + j] = mk(1.0, 0.0);
       for (int i = r + 1; i < n; ++i) {
@@ -248,8 +248,8 @@ __global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* _
 // the work laid out for FP32 walkers:
 //   O = trial_s^T Psi_s in FP32, p in tiles of 32 staged through shared
 //     memory (each thread owns up to OV_MAXE entries of O in registers);
-//   the LU of O with partial pivoting and log det O in FP64 (each warp owns
-//     rows i = k + 1 + warp (mod 8), its lanes the columns j);
+//   the LU of O with partial pivoting and log det O in FP64 (rows stay in
+//     place; each warp owns rows i = warp (mod 8), its lanes the columns j);
 //   O^{-1} in FP32 from the rounded factors, one thread per column
 //     (P O = L U, so column j of O^{-1} is U^{-1} L^{-1} P e_j);
 //   Theta = Psi O^{-1}: threads over (p, block of OV_JB columns j), the
@@ -284,8 +284,8 @@ __global__ void __launch_bounds__(256) overlap_c64_kernel(const float2* __restri
   float2* Ps = reinterpret_cast<float2*>(Ts + OV_TP * n);  // [OV_TP][n] (before the LU)
   const size_t lf_words = ((size_t)n * n * 8 > (size_t)OV_TP * n * 12 ? (size_t)n * n * 8 : (size_t)OV_TP * n * 12) / 8;
   float2* Inv = Lf + lf_words;                             // [n][n] O^{-1}
-  __shared__ int perm[128];
-  __shared__ int s_piv, s_swaps, s_sing;
+  __shared__ int perm[128], rank[128];
+  __shared__ int s_swaps, s_sing;
   __shared__ cd s_rpk;
   const float2* P = psi + ((size_t)w * nc + off) * N;
   const float* T = trial_f + (size_t)off * N;
@@ -326,18 +326,26 @@ __global__ void __launch_bounds__(256) overlap_c64_kernel(const float2* __restri
     const int e = tid + 256 * r;
     if (e < nn) LU[e] = mk((double)ar[r], (double)ai[r]);
   }
-  if (tid < n) perm[tid] = tid;
-  if (tid == 0) { s_swaps = 0; s_sing = 0; }
+  // rank[i]: the step at which row i became the pivot (n: not yet)
+  if (tid < n) rank[tid] = n;
+  if (tid == 0) s_sing = 0;
   __syncthreads();
 
-  // LU with partial pivoting in FP64: (P O) = L U, row i of PO is row perm[i] of O
+  // LU with partial pivoting in FP64, rows left in place (implicit pivoting):
+  // at step k the pivot is the largest |LU[i][k]| among the rows not chosen
+  // yet (ties keep the smaller row); every other remaining row i gets
+  // l_ik = LU[i][k] / LU[piv][k] and LU[i][j] -= l_ik LU[piv][j] for j > k.
+  // perm[k] = piv, so row k of P O is row perm[k] of O.  Each warp owns rows
+  // i = warp (mod 8), its lanes the columns; the complex update is four FMAs.
   for (int k = 0; k < n; ++k) {
-    if (wid == 0) {  // pivot: largest |LU[i][k]|, i >= k; ties keep the smaller row
-      int piv = k;
+    if (wid == 0) {
+      int piv = n;
       double best = -1.0;
-      for (int i = k + lane; i < n; i += 32) {
+      for (int i = lane; i < n; i += 32) {
+        if (rank[i] < n) continue;
         const double v = abs2(LU[i * n + k]);
-        if (v > best) { best = v; piv = i; }
+        const double vv = v >= 0.0 ? v : 0.0;  // NaN counts as a zero pivot (the walker is then singular)
+        if (vv > best) { best = vv; piv = i; }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -346,37 +354,53 @@ __global__ void __launch_bounds__(256) overlap_c64_kernel(const float2* __restri
         if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
       }
       if (lane == 0) {
-        s_piv = piv;
+        perm[k] = piv;
+        rank[piv] = k;
         if (!(best > 0.0)) s_sing = 1;
         s_rpk = crecip(LU[piv * n + k]);
-        if (piv != k) {
-          s_swaps ^= 1;
-          const int t = perm[k]; perm[k] = perm[piv]; perm[piv] = t;
-        }
       }
     }
     __syncthreads();
-    const int piv = s_piv;
-    if (piv != k)
-      for (int j = tid; j < n; j += 256) {
-        const cd t = LU[k * n + j]; LU[k * n + j] = LU[piv * n + j]; LU[piv * n + j] = t;
-      }
-    __syncthreads();
+    const int piv = perm[k];
     const cd rpk = s_rpk;
-    for (int i = k + 1 + wid; i < n; i += 8) {  // warp: row i; lanes: columns j
-      const cd lik = LU[i * n + k] * rpk;
-      for (int j = k + 1 + lane; j < n; j += 32) LU[i * n + j] = LU[i * n + j] - lik * LU[k * n + j];
+    const cd* up = LU + piv * n;
+    for (int i = wid; i < n; i += 8) {
+      if (rank[i] <= k) continue;  // chosen rows (the pivot included) are final
+      cd* row = LU + i * n;
+      const cd lik = row[k] * rpk;
+      for (int j = k + 1 + lane; j < n; j += 32) {
+        const cd u = up[j];
+        cd v = row[j];
+        v.re = fma(-lik.re, u.re, fma(lik.im, u.im, v.re));
+        v.im = fma(-lik.re, u.im, fma(-lik.im, u.re, v.im));
+        row[j] = v;
+      }
       __syncwarp();
-      if (lane == 0) LU[i * n + k] = lik;
+      if (lane == 0) row[k] = lik;
     }
     __syncthreads();
   }
+  // sign of the permutation: parity of n minus its number of cycles
+  if (tid == 0) {
+    int cycles = 0;
+    for (int i = 0; i < n; ++i) {
+      if (rank[i] < 0) continue;
+      ++cycles;
+      for (int j = i; rank[j] >= 0;) {  // follow the cycle through i, marking it
+        const int nx = perm[j];
+        rank[j] = -1;
+        j = nx;
+      }
+    }
+    s_swaps = (n - cycles) & 1;
+  }
+  __syncthreads();
 
-  // log det = sum_i log U_ii + i pi [odd number of swaps], summed across warp 0
+  // log det = sum_k log U_kk + i pi [odd permutation], summed across warp 0
   if (wid == 0) {
     double lr = 0.0, li = 0.0;
     for (int k = lane; k < n; k += 32) {
-      const cd u = LU[k * n + k];
+      const cd u = LU[perm[k] * n + k];
       lr += 0.5 * log(abs2(u));
       li += atan2(u.im, u.re);
     }
@@ -393,12 +417,17 @@ __global__ void __launch_bounds__(256) overlap_c64_kernel(const float2* __restri
   if (!theta) return;
 
   // O^{-1} = U^{-1} L^{-1} P in FP32 from the rounded factors (the diagonal of U inverted in FP64)
-  for (int e = tid; e < nn; e += 256) Lf[e] = make_float2((float)LU[e].re, (float)LU[e].im);
+  // factors in pivot order: row k of L and U is physical row perm[k]
+  for (int e = tid; e < nn; e += 256) {
+    const int kr = e / n, j = e - kr * n;
+    const cd v = LU[perm[kr] * n + j];
+    Lf[e] = make_float2((float)v.re, (float)v.im);
+  }
   __syncthreads();
   if (tid < n) {
     const int j = tid;
     int r = 0;
-    while (perm[r] != j) ++r;
+    while (r < n - 1 && perm[r] != j) ++r;
     for (int i = 0; i < r; ++i) Inv[i * n + j] = make_float2(0.f, 0.f);
     Inv[r * n + j] = make_float2(1.f, 0.f);
     for (int i = r + 1; i < n; ++i) {  // L y = P e_j (unit lower L)
@@ -417,7 +446,7 @@ __global__ void __launch_bounds__(256) overlap_c64_kernel(const float2* __restri
         x.x -= u.x * v.x - u.y * v.y;
         x.y -= u.x * v.y + u.y * v.x;
       }
-      const cd rd = crecip(LU[i * n + i]);
+      const cd rd = crecip(LU[perm[i] * n + i]);
       const float dr = (float)rd.re, di = (float)rd.im;
       Inv[i * n + j] = make_float2(x.x * dr - x.y * di, x.x * di + x.y * dr);
     }
