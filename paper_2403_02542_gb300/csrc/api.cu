@@ -1042,9 +1042,10 @@ static afqmc_status walk_backward_run(afqmc_ctx* c, const afqmc_walkers* w0, con
   CKW(adj_theta<R>(c, Nw, b.thbar, static_cast<const P*>(c->ws.theta), b.oinvk, nullptr, b.Wfin, b.pb, s),
       "adjoint: Theta pull-back");
   c->launches += 1 + 5 + (gfb.splitk > 1 ? 2 : 1) + 1 + 1 + 1 + 1;
-  CKW(cudaMemsetAsync(b.gLc, 0, (size_t)G * NN * cs, s), "adjoint: memset");
-  CKW(cudaMemsetAsync(b.Lhb, 0, (size_t)G * per * cs, s), "adjoint: memset");
-  CKW(cudaMemsetAsync(b.Bbar, 0, NN * cs, s), "adjoint: memset");
+  // the parameter-adjoint sums are FP64 complex (double2) for both walker types
+  CKW(cudaMemsetAsync(b.gLc, 0, (size_t)G * NN * sizeof(double2), s), "adjoint: memset");
+  CKW(cudaMemsetAsync(b.Lhb, 0, (size_t)G * per * sizeof(double2), s), "adjoint: memset");
+  CKW(cudaMemsetAsync(b.Bbar, 0, NN * sizeof(double2), s), "adjoint: memset");
   CKW(cudaMemsetAsync(b.mubar, 0, (size_t)G * sizeof(double), s), "adjoint: memset");
 
   // segments in reverse: recompute the states of the segment, then step back

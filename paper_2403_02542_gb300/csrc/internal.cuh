@@ -182,9 +182,6 @@ struct TcPlan {
   bool ok = false;
   int n = 0, gpt = 0, T = 0, Kp = 0, KC = 0, Wc = 0, NB = 0, S = 0, b_cap = 0;
   int gpw = 0;      // n <= 32: g blocks per 32-row warp slot (0: blocks packed across the tile)
-  bool cp = false;  // n > 32: rows packed continuously over the tiles (blocks may straddle two tiles)
-  void* carry = nullptr;  // cp: per-CTA carry of straddling blocks, [ctas][2][Wc][n * n + 2] float2
-  int carry_ctas = 0;
   int ewg = 2;      // epilogue warpgroups
   bool sb = false;  // B streamed with every K slab (else resident for the whole item)
   void* a_hi = nullptr;  // [2 spins][T][128][Kp] bf16, Lh split hi/lo

@@ -25,17 +25,8 @@
 // g blocks (gpw = 32 / n of them, the rest zero rows), so each epilogue warp
 // owns its blocks: the transposition goes through the warp's own staging rows
 // and the sums over a block's rows are segmented warp shuffles, with no
-// barrier between warps; or the blocks are packed across the tile (128 / n per
-// tile).  For n > 32 the rows run on continuously over the tiles (row R of a
-// spin's A operand is row R % n of g = R / n), so no tile row is padding; a g
-// block may then straddle tiles t and t + 1, which the same CTA processes one
-// after the other.  With P = the block's rows in tile t and Q = those in t + 1,
-// sum_ij T_ij T_ji = sum_{P,P} + sum_{Q,Q} + 2 sum_{i in P, j in Q} T_ij T_ji:
-// the P rows add their P part and leave T_ij (j in Q) and their partial sums
-// in a per-CTA carry (global memory, two slots alternating with the tile), the
-// Q rows add their Q part and twice the cross term from the carry, and the
-// block is written out on tile t + 1.  The four warps of a warpgroup share a
-// staging area.
+// barrier between warps.  For n > 32 the blocks are packed across the tile
+// (128 / n per tile) and the four warps of a warpgroup share a staging area.
 // The accumulator is double-buffered in TMEM so the epilogue of one A tile
 // overlaps the MMAs of the next.  Every mbarrier wait is bounded; on a
 // timeout the kernel raises an error flag, stops issuing work and frees its
@@ -59,7 +50,6 @@ struct TcArgs {
   uint32_t sB_bytes, sA_stage_bytes, staging_floats;
   int sp;  // staging row stride in floats (a multiple of 4 with sp / 4 odd)
   double* epart;
-  float2* carry;  // cp: [gridDim][2][Wc][n * n + 2]
   int* err;
 };
 
@@ -346,137 +336,6 @@ __global__ void __launch_bounds__(64 + 128 * EWG, 1)
           buf ^= 1;
         }
       }
-    } else if constexpr (NM == 0) {
-      // continuous rows (n > 32), see the file comment
-      float* pb = pbuf + ewg * 128 * 4;
-      const int bar_id = 1 + ewg;
-      uint32_t tcount = 0;
-      float4* srow = reinterpret_cast<float4*>(st + r * SP);
-      const float2* arow = reinterpret_cast<const float2*>(st + r * SP);
-      const int nn = n * n, cslot = nn + 2;
-      for (int item = blockIdx.x; item < p.n_items && go; item += gridDim.x) {
-        const int spin = item / p.WG, wg = item % p.WG;
-        for (uint32_t t = 0; t < tiles_per_item; ++t) {
-          if (r == 0) {
-            const bool ok = mbar_wait(tfull + buf, tph[buf]);
-            if (!ok) { atomicOr(p.err, 32); *abort_flag = 1; }
-            epi_ok[2 * ewg + (tcount & 1)] = ok ? 1 : 0;
-          }
-          named_bar(bar_id, 128);
-          const int ok = epi_ok[2 * ewg + (tcount & 1)];
-          ++tcount;
-          if (!ok) { go = false; break; }
-          tc_fence_after();
-          const int Rt = (int)t * 128;
-          const int R = Rt + r, g = R / n, i = R - (R / n) * n;
-          const bool valid = g < p.G;
-          const int s0 = g * n - Rt;              // first row of this row's block, relative to the tile
-          const int np = s0 < 0 ? -s0 : 0;       // rows of the block in the previous tile
-          const int jhi = min(n, 128 - s0);      // one past its last row in this tile
-          const bool cont = s0 + n > 128;        // the block goes on in the next tile
-          const float2* stf = reinterpret_cast<const float2*>(st);  // T[k][i] of tile row k at stf[k * hs + i]
-          const int tbase = s0 * hs + i;                              // T[j][i] of block row j at stf[tbase + j * hs]
-          const int g_lo = Rt / n;
-          const int nbt = min((Rt + 127) / n, p.G - 1) - g_lo + 1;
-          const int par = (int)(t & 1u);
-          for (int wl = ewg; wl < p.Wc; wl += EWG) {
-            const int w = wg * p.Wc + wl;
-            if (w >= p.Nw) break;
-            float2* cw = p.carry + ((size_t)(blockIdx.x * 2 + par) * p.Wc + wl) * cslot;
-            const float2* cr = p.carry + ((size_t)(blockIdx.x * 2 + (par ^ 1)) * p.Wc + wl) * cslot;
-            const uint32_t col0 = (uint32_t)(buf * p.NB + wl * two_n);
-            const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16) + col0;
-            for (int c0 = 0; c0 < two_n; c0 += 8) {
-              uint32_t v[8];
-              tmem_ld8(tl + (uint32_t)c0, v);
-              tmem_wait_ld();
-              srow[c0 >> 2] = make_float4(__uint_as_float(v[0]), __uint_as_float(v[1]), __uint_as_float(v[2]),
-                                          __uint_as_float(v[3]));
-              if (c0 + 4 < two_n)
-                srow[(c0 >> 2) + 1] = make_float4(__uint_as_float(v[4]), __uint_as_float(v[5]),
-                                                  __uint_as_float(v[6]), __uint_as_float(v[7]));
-            }
-            named_bar(bar_id, 128);
-            float tr = 0.f, ti = 0.f, er = 0.f, ei = 0.f;
-            if (valid) {
-              // rows of the block in this tile: sum_j T_ij T_ji over j in [np, jhi)
-              float rr0 = 0.f, ii0 = 0.f, ri0 = 0.f, ir0 = 0.f, rr1 = 0.f, ii1 = 0.f, ri1 = 0.f, ir1 = 0.f;
-              int j = np;
-              for (; j + 1 < jhi; j += 2) {
-                const float2 a0 = arow[j], a1 = arow[j + 1];
-                const float2 b0 = stf[tbase + j * hs], b1 = stf[tbase + (j + 1) * hs];
-                rr0 = fmaf(a0.x, b0.x, rr0);
-                ii0 = fmaf(a0.y, b0.y, ii0);
-                ri0 = fmaf(a0.x, b0.y, ri0);
-                ir0 = fmaf(a0.y, b0.x, ir0);
-                rr1 = fmaf(a1.x, b1.x, rr1);
-                ii1 = fmaf(a1.y, b1.y, ii1);
-                ri1 = fmaf(a1.x, b1.y, ri1);
-                ir1 = fmaf(a1.y, b1.x, ir1);
-              }
-              if (j < jhi) {
-                const float2 a0 = arow[j], b0 = stf[tbase + j * hs];
-                rr0 = fmaf(a0.x, b0.x, rr0);
-                ii0 = fmaf(a0.y, b0.y, ii0);
-                ri0 = fmaf(a0.x, b0.y, ri0);
-                ir0 = fmaf(a0.y, b0.x, ir0);
-              }
-              er = (rr0 + rr1) - (ii0 + ii1);
-              ei = (ri0 + ri1) + (ir0 + ir1);
-              if (np > 0) {
-                // Q row: twice the cross term with the P rows, T_ji from the carry
-                float cr0 = 0.f, ci0 = 0.f, cc0 = 0.f, cd0 = 0.f;
-                for (int jp = 0; jp < np; ++jp) {
-                  const float2 a0 = arow[jp], b0 = cr[jp * n + (i - np)];
-                  cr0 = fmaf(a0.x, b0.x, cr0);
-                  ci0 = fmaf(a0.y, b0.y, ci0);
-                  cc0 = fmaf(a0.x, b0.y, cc0);
-                  cd0 = fmaf(a0.y, b0.x, cd0);
-                }
-                er += 2.f * (cr0 - ci0);
-                ei += 2.f * (cc0 + cd0);
-              }
-              if (cont) {
-                // P row: T_ij for the block's rows j in the next tile, for its Q rows
-                for (int jq = 0; jq < n - jhi; ++jq) cw[i * n + jq] = arow[jhi + jq];
-              }
-              const float2 tt = arow[i];
-              tr = tt.x;
-              ti = tt.y;
-            }
-            reinterpret_cast<float4*>(pb)[r] = make_float4(tr, ti, er, ei);
-            named_bar(bar_id, 128);
-            // (block, quantity) sums over the block's rows in this tile: four
-            // lanes per pair, fixed-order shuffles; a block that goes on leaves
-            // its sums in the carry, one that came from the previous tile adds them
-            const int nthr = 16 * nbt;
-            for (int x0 = quad * 32; x0 < nthr; x0 += 128) {
-              const int x = x0 + lane;
-              const int pair = x >> 2, part = x & 3;
-              const int gb = pair >> 2, qn = pair & 3;
-              const int gg = g_lo + gb;
-              const int a = max(gg * n - Rt, 0), b = min(gg * n + n - Rt, 128);
-              float sum = 0.f;
-              if (x < nthr)
-                for (int ii = a + part; ii < b; ii += 4) sum += pb[ii * 4 + qn];
-              sum += __shfl_xor_sync(0xffffffffu, sum, 1);
-              sum += __shfl_xor_sync(0xffffffffu, sum, 2);
-              if (x < nthr && part == 0) {
-                if (gg * n + n - Rt > 128) {
-                  reinterpret_cast<float*>(cw + nn)[qn] = sum;
-                } else {
-                  if (gg * n - Rt < 0) sum += reinterpret_cast<const float*>(cr + nn)[qn];
-                  p.epart[(((size_t)w * p.G + gg) * 2 + spin) * 4 + qn] = sum;
-                }
-              }
-            }
-          }
-          tc_fence_before();
-          mbar_arrive(tempty + buf);
-          tph[buf] ^= 1;
-          buf ^= 1;
-        }
-      }
     } else {
       const int gl = r / n, i = r % n;
       const bool row_ok = gl < p.gpt;
@@ -582,12 +441,11 @@ __global__ void __launch_bounds__(64 + 128 * EWG, 1)
 }
 
 // A operand: [2 spins][T][128 rows][Kp] from Lh[G][nc][N].  Rows of tile t:
-// cp: row r = row R % n of g = R / n, R = 128 t + r (rows past G n zero);
 // gpw > 0: row slot*32 + b*n + i = row i of g = t*gpt + slot*gpw + b (b < gpw,
 // other rows zero); gpw == 0: row gg*n + i = row i of g = t*gpt + gg.
 __global__ void build_lh_tiles_kernel(const double* __restrict__ Lh, __nv_bfloat16* __restrict__ hi,
                                       __nv_bfloat16* __restrict__ lo, int N, int n, int nc, int G, int gpt, int gpw,
-                                      int T, int Kp, int cp) {
+                                      int T, int Kp) {
   const size_t total = (size_t)2 * T * 128 * Kp;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int q = e % Kp;
@@ -596,13 +454,7 @@ __global__ void build_lh_tiles_kernel(const double* __restrict__ Lh, __nv_bfloat
     const int spin = (int)(e / ((size_t)Kp * 128 * T));
     int gg, i;
     bool in_block;
-    if (cp) {  // continuous rows: R = 128 t + r is row R % n of g = R / n
-      const int R = t * 128 + r;
-      const int g = R / n;
-      i = R - g * n;
-      gg = g - t * gpt;  // gpt == 0 here, so g = t * gpt + gg below
-      in_block = true;
-    } else if (gpw > 0) {
+    if (gpw > 0) {
       const int slot = r >> 5, b = (r & 31) / n;
       i = (r & 31) - b * n;
       gg = slot * gpw + b;
@@ -747,10 +599,9 @@ bool tc_exchange_plan(afqmc_ctx* c) {
   if (!best_wc) return false;
   P.ok = true;
   P.n = n;
-  P.cp = n > 32;
-  P.gpt = P.cp ? 0 : gpt;
+  P.gpt = gpt;
   P.gpw = gpw;
-  P.T = P.cp ? (c->G * n + 127) / 128 : (c->G + gpt - 1) / gpt;
+  P.T = (c->G + gpt - 1) / gpt;
   P.Kp = Kp;
   P.KC = KC;
   P.Wc = best_wc;
@@ -773,16 +624,9 @@ cudaError_t tc_exchange_setup(afqmc_ctx* c, cudaStream_t s) {
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(P.err, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
-  if (P.cp) {  // carry of straddling blocks: one slot pair per CTA of the persistent grid
-    int sms = 152, dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    P.carry_ctas = sms;
-    e = dmalloc(&P.carry, (size_t)sms * 2 * P.Wc * ((size_t)P.n * P.n + 2) * sizeof(float2));
-    if (e != cudaSuccess) return e;
-  }
   build_lh_tiles_kernel<<<grid_for(elems), 256, 0, s>>>(c->d_Lh, static_cast<__nv_bfloat16*>(P.a_hi),
                                                         static_cast<__nv_bfloat16*>(P.a_lo), c->N, P.n, c->nc, c->G,
-                                                        P.gpt, P.gpw, P.T, P.Kp, P.cp ? 1 : 0);
+                                                        P.gpt, P.gpw, P.T, P.Kp);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (!make_map(reinterpret_cast<CUtensorMap*>(P.map_a_hi), P.a_hi, (size_t)2 * P.T * 128, P.Kp, 128) ||
@@ -838,7 +682,7 @@ cudaError_t tc_exchange_prepare(const afqmc_ctx* c) {
 
 void tc_exchange_free(afqmc_ctx* c) {
   TcPlan& P = c->tc;
-  void* ptrs[] = {P.a_hi, P.a_lo, P.b_hi, P.b_lo, P.err, P.carry};
+  void* ptrs[] = {P.a_hi, P.a_lo, P.b_hi, P.b_lo, P.err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   P = TcPlan();
@@ -881,7 +725,6 @@ cudaError_t tc_exchange_contract(afqmc_ctx* c, int Nw, double* epart, cudaStream
   a.sp = tc_stage_stride(P.n);
   a.staging_floats = (uint32_t)(128 * a.sp);
   a.epart = epart;
-  a.carry = static_cast<float2*>(P.carry);
   a.err = static_cast<int*>(P.err);
   const size_t shm = tc_smem_bytes(P.KC, P.NB, P.S, P.n, P.ewg, P.sb);
   if (!capturing(c)) {
@@ -891,8 +734,7 @@ cudaError_t tc_exchange_contract(afqmc_ctx* c, int Nw, double* epart, cudaStream
   int sms = 152;
   int dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int grid = a.n_items < sms ? a.n_items : sms;
-  if (P.cp && grid > P.carry_ctas) grid = P.carry_ctas;
+  const int grid = a.n_items < sms ? a.n_items : sms;
   CUtensorMap mah, mal, mbh, mbl;
   memcpy(&mah, P.map_a_hi, sizeof(CUtensorMap));
   memcpy(&mal, P.map_a_lo, sizeof(CUtensorMap));
