@@ -733,12 +733,10 @@ namespace {
 struct Arena {
   char* base = nullptr;
   size_t used = 0;
-  std::vector<std::pair<size_t, size_t>> parts;  // (offset, bytes) of every take, in order
   template <typename T>
   T* take(size_t n) {
     const size_t a = (used + 255) & ~(size_t)255;
     used = a + n * sizeof(T);
-    parts.emplace_back(a, n * sizeof(T));
     return base ? reinterpret_cast<T*>(base + a) : nullptr;
   }
 };
@@ -1105,16 +1103,8 @@ static afqmc_status walk_backward_alloc(afqmc_ctx* c, const afqmc_walkers* w0, c
     cudaGetLastError();
     return cuda_fail(e, "adjoint workspace");
   }
-  a = Arena{base, 0, {}};
+  a = Arena{base, 0};
   adj_carve<R>(a, b, c, Nw, q->order, q->ckpt_every, nck);
-  if (const char* rg = getenv("AFQMC_POISON_ADJ_RANGE")) {  // debugging: NaN bytes in takes [lo, hi) only
-    const int lo = atoi(rg), hi = strchr(rg, ',') ? atoi(strchr(rg, ',') + 1) : lo + 1;
-    if (cudaMemset(base, 0, a.used) != cudaSuccess) return cuda_fail(cudaGetLastError(), "adjoint workspace");
-    for (int k = lo; k < hi && k < (int)a.parts.size(); ++k)
-      if (cudaMemset(base + a.parts[k].first, 0xFF, a.parts[k].second) != cudaSuccess)
-        return cuda_fail(cudaGetLastError(), "adjoint workspace");
-    if (cudaDeviceSynchronize() != cudaSuccess) return cuda_fail(cudaGetLastError(), "adjoint workspace");
-  }
   afqmc_status st = walk_backward_run<R>(c, w0, fields, q, J_out, grad_h1, grad_L, grad_psi0, b);
   e = cudaStreamSynchronize(c->stream);
   cudaFree(base);
