@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* _
 // grid (Nw, 2 spins), block 256.  The same quantities as overlap_kernel with
 // the work laid out for FP32 walkers:
 //   O = trial_s^T Psi_s in FP32, p in tiles of 32 staged through shared
-//     memory (each thread owns up to OV_MAXE entries of O in registers);
+//     memory (each thread owns 2 x 5 blocks of O in registers);
 //   the LU of O with partial pivoting and log det O in FP64 (rows stay in
 //     place; each warp owns rows i = warp (mod 8), its lanes the columns j);
 //   O^{-1} in FP32 from the rounded factors, one thread per column
@@ -258,10 +258,11 @@ __global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* _
 // Shared: LU [n][n] FP64 complex, Lf and Inv [n][n] FP32 complex; the O
 // staging tiles trial [32][n] and Psi [32][n] occupy the Lf area, which is
 // written only after the LU.
-constexpr int OV_TP = 32, OV_MAXE = 25, OV_JB = 10;  // p tile; (80 * 80) / 256 entries; Theta column block
+// p tile; O register block of OV_TI x OV_TJ entries per thread; Theta column block
+constexpr int OV_TP = 32, OV_TI = 2, OV_TJ = 5, OV_JB = 10;
 size_t overlap_c64_smem(int nmax) {
-  const size_t lf = (size_t)nmax * nmax * 8, stage = (size_t)OV_TP * nmax * 12;
-  return (size_t)nmax * nmax * 16 + (lf > stage ? lf : stage) + (size_t)nmax * nmax * 8;
+  const size_t inv = (size_t)nmax * nmax * 8, stage = (size_t)OV_TP * nmax * 12;
+  return (size_t)nmax * nmax * 16 + (inv > stage ? inv : stage);
 }
 
 __global__ void __launch_bounds__(256) overlap_c64_kernel(const float2* __restrict__ psi,
@@ -278,53 +279,73 @@ __global__ void __launch_bounds__(256) overlap_c64_kernel(const float2* __restri
     if (tid == 0) { ldw[0] = 0.0; ldw[1] = 0.0; }
     return;
   }
+  // shared memory: the FP64 LU [n][n], then one region that holds in turn the
+  // O staging tiles, the rounded factors (before they move into the LU area)
+  // and O^{-1}
   cd* LU = reinterpret_cast<cd*>(smem_oc);                 // [n][n]
-  float2* Lf = reinterpret_cast<float2*>(LU + n * n);      // [n][n] rounded factors (after the LU)
-  float* Ts = reinterpret_cast<float*>(Lf);                // [OV_TP][n] (before the LU)
+  float2* Lf = reinterpret_cast<float2*>(LU);              // [n][n] rounded factors (after the LU)
+  float2* Rg = reinterpret_cast<float2*>(LU + n * n);      // the second region
+  float* Ts = reinterpret_cast<float*>(Rg);                // [OV_TP][n] (before the LU)
   float2* Ps = reinterpret_cast<float2*>(Ts + OV_TP * n);  // [OV_TP][n] (before the LU)
-  const size_t lf_words = ((size_t)n * n * 8 > (size_t)OV_TP * n * 12 ? (size_t)n * n * 8 : (size_t)OV_TP * n * 12) / 8;
-  float2* Inv = Lf + lf_words;                             // [n][n] O^{-1}
-  __shared__ int perm[128], rank[128];
+  float2* Inv = Rg;                                        // [n][n] O^{-1} (after the factors moved)
+  __shared__ int perm[128], rank[128], cand_r[8];
+  __shared__ double cand_v[8];
   __shared__ int s_swaps, s_sing;
   __shared__ cd s_rpk;
   const float2* P = psi + ((size_t)w * nc + off) * N;
   const float* T = trial_f + (size_t)off * N;
   const int nn = n * n;
 
-  // O[i][j] = sum_p T[i][p] P[j][p]
-  float ar[OV_MAXE], ai[OV_MAXE];
+  // O[i][j] = sum_p T[i][p] P[j][p]: each thread accumulates one block of
+  // OV_TI x OV_TJ entries in registers over the staged p tiles (rounds of 256
+  // blocks; a single round for n <= 50)
+  const int nbi = (n + OV_TI - 1) / OV_TI, nbj = (n + OV_TJ - 1) / OV_TJ, nblocks = nbi * nbj;
+  for (int blk0 = 0; blk0 < nblocks; blk0 += 256) {
+    const int blk = blk0 + tid;
+    const bool has = blk < nblocks;
+    const int bi = has ? blk / nbj : 0, bj = has ? blk - bi * nbj : 0;
+    const int i0 = bi * OV_TI, j0 = bj * OV_TJ;
+    float ar[OV_TI][OV_TJ], ai[OV_TI][OV_TJ];
 #pragma unroll
-  for (int r = 0; r < OV_MAXE; ++r) { ar[r] = 0.f; ai[r] = 0.f; }
-  for (int p0 = 0; p0 < N; p0 += OV_TP) {
-    __syncthreads();
-    for (int e = tid; e < OV_TP * n; e += 256) {  // e = i * OV_TP + pp: consecutive pp are consecutive p
-      const int i = e / OV_TP, pp = e - i * OV_TP, p = p0 + pp;
-      Ts[pp * n + i] = p < N ? T[(size_t)i * N + p] : 0.f;
-      Ps[pp * n + i] = p < N ? P[(size_t)i * N + p] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
+    for (int a0 = 0; a0 < OV_TI; ++a0)
 #pragma unroll
-    for (int r = 0; r < OV_MAXE; ++r) {
-      const int e = tid + 256 * r;
-      if (e < nn) {
-        const int i = e / n, j = e - i * n;
-        float sr = ar[r], si = ai[r];
-#pragma unroll 8
+      for (int b0 = 0; b0 < OV_TJ; ++b0) { ar[a0][b0] = 0.f; ai[a0][b0] = 0.f; }
+    for (int p0 = 0; p0 < N; p0 += OV_TP) {
+      __syncthreads();
+      for (int e = tid; e < OV_TP * n; e += 256) {  // e = i * OV_TP + pp: consecutive pp are consecutive p
+        const int i = e / OV_TP, pp = e - i * OV_TP, p = p0 + pp;
+        Ts[pp * n + i] = p < N ? T[(size_t)i * N + p] : 0.f;
+        Ps[pp * n + i] = p < N ? P[(size_t)i * N + p] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      if (has) {
+#pragma unroll 4
         for (int pp = 0; pp < OV_TP; ++pp) {
-          const float t = Ts[pp * n + i];
-          const float2 x = Ps[pp * n + j];
-          sr = fmaf(t, x.x, sr);
-          si = fmaf(t, x.y, si);
+          float t[OV_TI];
+          float2 x[OV_TJ];
+#pragma unroll
+          for (int a0 = 0; a0 < OV_TI; ++a0) t[a0] = i0 + a0 < n ? Ts[pp * n + i0 + a0] : 0.f;
+#pragma unroll
+          for (int b0 = 0; b0 < OV_TJ; ++b0) x[b0] = j0 + b0 < n ? Ps[pp * n + j0 + b0] : make_float2(0.f, 0.f);
+#pragma unroll
+          for (int a0 = 0; a0 < OV_TI; ++a0)
+#pragma unroll
+            for (int b0 = 0; b0 < OV_TJ; ++b0) {
+              ar[a0][b0] = fmaf(t[a0], x[b0].x, ar[a0][b0]);
+              ai[a0][b0] = fmaf(t[a0], x[b0].y, ai[a0][b0]);
+            }
         }
-        ar[r] = sr;
-        ai[r] = si;
       }
     }
-  }
+    if (has) {
 #pragma unroll
-  for (int r = 0; r < OV_MAXE; ++r) {
-    const int e = tid + 256 * r;
-    if (e < nn) LU[e] = mk((double)ar[r], (double)ai[r]);
+      for (int a0 = 0; a0 < OV_TI; ++a0)
+#pragma unroll
+        for (int b0 = 0; b0 < OV_TJ; ++b0) {
+          const int i = i0 + a0, j = j0 + b0;
+          if (i < n && j < n) LU[i * n + j] = mk((double)ar[a0][b0], (double)ai[a0][b0]);
+        }
+    }
   }
   // rank[i]: the step at which row i became the pivot (n: not yet)
   if (tid < n) rank[tid] = n;
@@ -337,33 +358,50 @@ __global__ void __launch_bounds__(256) overlap_c64_kernel(const float2* __restri
   // l_ik = LU[i][k] / LU[piv][k] and LU[i][j] -= l_ik LU[piv][j] for j > k.
   // perm[k] = piv, so row k of P O is row perm[k] of O.  Each warp owns rows
   // i = warp (mod 8), its lanes the columns; the complex update is four FMAs.
-  for (int k = 0; k < n; ++k) {
-    if (wid == 0) {
-      int piv = n;
-      double best = -1.0;
-      for (int i = lane; i < n; i += 32) {
-        if (rank[i] < n) continue;
-        const double v = abs2(LU[i * n + k]);
-        const double vv = v >= 0.0 ? v : 0.0;  // NaN counts as a zero pivot (the walker is then singular)
-        if (vv > best) { best = vv; piv = i; }
+  // The pivot search of step k + 1 rides on the update of step k: every warp
+  // leaves the best candidate among its rows (column k + 1 after the update)
+  // and one thread picks among the eight.
+  auto pick = [&](int kk) {  // thread 0: pivot of step kk from the warps' candidates
+    int piv = n;
+    double best = -1.0;
+    for (int q = 0; q < 8; ++q)
+      if (cand_r[q] < n && (cand_v[q] > best || (cand_v[q] == best && cand_r[q] < piv))) {
+        best = cand_v[q];
+        piv = cand_r[q];
       }
+    perm[kk] = piv;
+    rank[piv] = kk;
+    if (!(best > 0.0)) s_sing = 1;
+    s_rpk = crecip(LU[piv * n + kk]);
+  };
+  auto warp_best = [&](double v, int row) {  // reduce (value, row) over the warp, ties to the smaller row
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int op = __shfl_xor_sync(0xffffffffu, piv, o);
-        if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
-      }
-      if (lane == 0) {
-        perm[k] = piv;
-        rank[piv] = k;
-        if (!(best > 0.0)) s_sing = 1;
-        s_rpk = crecip(LU[piv * n + k]);
-      }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int orow = __shfl_xor_sync(0xffffffffu, row, o);
+      if (ov > v || (ov == v && orow < row)) { v = ov; row = orow; }
     }
-    __syncthreads();
+    if (lane == 0) { cand_v[wid] = v; cand_r[wid] = row; }
+  };
+  {  // candidates of step 0: every row
+    double v = -1.0;
+    int row = n;
+    for (int i = tid; i < n; i += 256) {
+      const double a2 = abs2(LU[i * n]);
+      const double vv = a2 >= 0.0 ? a2 : 0.0;  // NaN counts as a zero pivot (the walker is then singular)
+      if (vv > v || (vv == v && i < row)) { v = vv; row = i; }
+    }
+    warp_best(v, row);
+  }
+  __syncthreads();
+  if (tid == 0) pick(0);
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
     const int piv = perm[k];
     const cd rpk = s_rpk;
     const cd* up = LU + piv * n;
+    double cv = -1.0;  // this lane's best candidate for step k + 1
+    int crow = n;
     for (int i = wid; i < n; i += 8) {
       if (rank[i] <= k) continue;  // chosen rows (the pivot included) are final
       cd* row = LU + i * n;
@@ -374,11 +412,21 @@ __global__ void __launch_bounds__(256) overlap_c64_kernel(const float2* __restri
         v.re = fma(-lik.re, u.re, fma(lik.im, u.im, v.re));
         v.im = fma(-lik.re, u.im, fma(-lik.im, u.re, v.im));
         row[j] = v;
+        if (j == k + 1) {
+          const double a2 = abs2(v);
+          const double vv = a2 >= 0.0 ? a2 : 0.0;
+          if (vv > cv || (vv == cv && i < crow)) { cv = vv; crow = i; }
+        }
       }
       __syncwarp();
       if (lane == 0) row[k] = lik;
     }
+    if (k + 1 < n) warp_best(cv, crow);
     __syncthreads();
+    if (k + 1 < n) {
+      if (tid == 0) pick(k + 1);
+      __syncthreads();
+    }
   }
   // sign of the permutation: parity of n minus its number of cycles
   if (tid == 0) {
@@ -417,12 +465,20 @@ __global__ void __launch_bounds__(256) overlap_c64_kernel(const float2* __restri
   if (!theta) return;
 
   // O^{-1} = U^{-1} L^{-1} P in FP32 from the rounded factors (the diagonal of U inverted in FP64)
-  // factors in pivot order: row k of L and U is physical row perm[k]
+  // factors in pivot order: row k of L and U is physical row perm[k]; the
+  // diagonal of U inverted once in FP64
+  __shared__ float2 s_rdiag[128];
   for (int e = tid; e < nn; e += 256) {
     const int kr = e / n, j = e - kr * n;
     const cd v = LU[perm[kr] * n + j];
-    Lf[e] = make_float2((float)v.re, (float)v.im);
+    Rg[e] = make_float2((float)v.re, (float)v.im);
   }
+  for (int i = tid; i < n; i += 256) {
+    const cd rd = crecip(LU[perm[i] * n + i]);
+    s_rdiag[i] = make_float2((float)rd.re, (float)rd.im);
+  }
+  __syncthreads();
+  for (int e = tid; e < nn; e += 256) Lf[e] = Rg[e];  // the FP64 LU is no longer needed
   __syncthreads();
   if (tid < n) {
     const int j = tid;
@@ -446,8 +502,7 @@ __global__ void __launch_bounds__(256) overlap_c64_kernel(const float2* __restri
         x.x -= u.x * v.x - u.y * v.y;
         x.y -= u.x * v.y + u.y * v.x;
       }
-      const cd rd = crecip(LU[perm[i] * n + i]);
-      const float dr = (float)rd.re, di = (float)rd.im;
+      const float dr = s_rdiag[i].x, di = s_rdiag[i].y;
       Inv[i * n + j] = make_float2(x.x * dr - x.y * di, x.x * di + x.y * dr);
     }
   }
@@ -764,7 +819,8 @@ __global__ void __launch_bounds__(64) krylov_expm_kernel(typename C2<R>::t* __re
                 const typename C2<R>::t hh = hess[(size_t)(i * kmax + j) * hs + col];
                 h = make_double2((double)hh.x, (double)hh.y);
               }
-              a = a + mk(h.x, h.y) * tv[j];
+              a.re = fma(h.x, tv[j].re, fma(-h.y, tv[j].im, a.re));  // a += h tv[j], four FMAs
+              a.im = fma(h.x, tv[j].im, fma(h.y, tv[j].re, a.im));
             }
           }
           o += k - (i > 0 ? i - 1 : 0);
