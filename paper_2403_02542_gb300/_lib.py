@@ -39,7 +39,8 @@ _I = ctypes.c_int
 class WalkAdjointParams(ctypes.Structure):
     _fields_ = [("n_steps", ctypes.c_int), ("order", ctypes.c_int),
                 ("reortho_every", ctypes.c_int), ("ckpt_every", ctypes.c_int),
-                ("tau", ctypes.c_double), ("e0", ctypes.c_double), ("dJ", ctypes.c_double)]
+                ("tau", ctypes.c_double), ("e0", ctypes.c_double), ("dJ", ctypes.c_double),
+                ("expm", ctypes.c_int)]
 
 
 SIGNATURES = {

@@ -166,11 +166,14 @@ class Context:
         return gh, gL
 
     def walk_backward(self, w: WalkerSet, fields: torch.Tensor, tau: float, e0: float, order: int = 6,
-                      reortho_every: int = 0, ckpt_every: int = 10, dJ: float = 1.0, grad_psi0: bool = False):
+                      reortho_every: int = 0, ckpt_every: int = 10, dJ: float = 1.0, grad_psi0: bool = False,
+                      expm: str = "taylor"):
         """Gradient of the mixed estimator after a fixed-field walk (afqmc_walk_backward).
 
         `w` holds the walkers at step 0 (left unchanged); `fields` is a device
-        tensor [n_steps, Nw, G] of the walk's auxiliary fields.  Returns
+        tensor [n_steps, Nw, G] of the walk's auxiliary fields; `expm` is
+        "taylor" (order = Taylor order) or "krylov" (order = Krylov
+        dimension), the action of e^A in every step.  Returns
         (e_mix [4], dJ/dh1 [N,N], dJ/dL [G,N,N]) and, with grad_psi0=True, the
         derivative G [Nw, na+nb, N] (the walkers' complex type) with
         dJ = Re sum G * dPsi_0 as well.  In a mixed context the walk and its
@@ -180,8 +183,10 @@ class Context:
         f = fields.to(device=self.device, dtype=torch.float64).contiguous()
         if f.dim() != 3 or f.shape[1] != w.n or f.shape[2] != self.G:
             raise ValueError("fields must be [n_steps, n_walkers, G]")
+        if expm not in ("taylor", "krylov"):
+            raise ValueError("the walk adjoint takes expm='taylor' or 'krylov'")
         p = L.WalkAdjointParams(int(f.shape[0]), int(order), int(reortho_every), int(ckpt_every),
-                                float(tau), float(e0), float(dJ))
+                                float(tau), float(e0), float(dJ), EXPMS[expm])
         J = torch.empty(4, dtype=torch.float64, device=self.device)
         gh = torch.empty(self.N, self.N, dtype=torch.float64, device=self.device)
         gL = torch.empty(self.G, self.N, self.N, dtype=torch.float64, device=self.device)
@@ -332,17 +337,18 @@ class MixedEnergy(torch.autograd.Function):
 
 
 def walk_energy(ctx: "Context", n_walkers: int, fields: torch.Tensor, tau: float, e0: float, order: int = 6,
-                reortho_every: int = 0) -> torch.Tensor:
-    """J = E_n after n fixed-field steps (Split-2 + Taylor) from walkers at the
-    trial, by plain afqmc_step calls with the local energy measured at the
-    last step.  Returns e_mix [4] = (sum W Ebar_L, sum W, J, live walkers)."""
+                reortho_every: int = 0, expm: str = "taylor") -> torch.Tensor:
+    """J = E_n after n fixed-field steps (Split-2 + Taylor of the given order,
+    or Krylov of that dimension) from walkers at the trial, by plain
+    afqmc_step calls with the local energy measured at the last step.
+    Returns e_mix [4] = (sum W Ebar_L, sum W, J, live walkers)."""
     w = ctx.new_walkers(n_walkers)
     ctx.init_walkers(w)
     e_loc = torch.empty(n_walkers, 2, dtype=torch.float64, device=ctx.device)
     e_mix = torch.empty(4, dtype=torch.float64, device=ctx.device)
     n = int(fields.shape[0])
     for k in range(n):
-        ctx.step(w, fields[k], tau, e0, expm="taylor", order=order,
+        ctx.step(w, fields[k], tau, e0, expm=expm, order=order,
                  reortho=bool(reortho_every) and (k + 1) % reortho_every == 0, measure=(k == n - 1),
                  e_loc=e_loc, e_mix=e_mix)
     return e_mix
@@ -352,8 +358,9 @@ class WalkEnergy(torch.autograd.Function):
     """J(h1, L) = E_n, the mixed estimator after an n-step fixed-field walk
     from walkers at the trial, as a differentiable function (the energy
     derivatives of a bond-length scan).  The forward is the walk itself
-    (afqmc_step, Split-2 + Taylor of the given order, re-orthonormalisation
-    every reortho_every steps); the backward is afqmc_walk_backward on a
+    (afqmc_step, Split-2 + Taylor of the given order or Krylov of that
+    dimension, re-orthonormalisation every reortho_every steps); the
+    backward is afqmc_walk_backward on a
     context built from the same (h1, L), which recomputes the walk from
     checkpoints every ckpt_every steps and returns dJ/dh1 and dJ/dL scaled by
     the incoming gradient.  The auxiliary fields, the trial, e0 and tau are
@@ -361,35 +368,36 @@ class WalkEnergy(torch.autograd.Function):
 
     apply(h1 [N,N] float64, L [G,N,N] float64, fields [n, Nw, G] float64 on
           the device, trial [N, na+nb], na, nb, e0, tau, order, reortho_every,
-          ckpt_every, precision ("fp64" or "mixed"), e_const) -> J (0-dim)"""
+          ckpt_every, precision ("fp64" or "mixed"), e_const, expm ("taylor" or
+          "krylov")) -> J (0-dim)"""
 
     @staticmethod
     def forward(ctx, h1, chol, fields, trial, na, nb, e0, tau, order=6, reortho_every=0, ckpt_every=10,
-                precision="fp64", e_const=0.0):
+                precision="fp64", e_const=0.0, expm="taylor"):
         dev = fields.device
         c = Context(h1.detach().cpu().numpy(), chol.detach().cpu().numpy(), trial, na, nb, e_const,
                     precision=precision, device=dev)
         try:
-            e_mix = walk_energy(c, int(fields.shape[1]), fields, tau, e0, order, reortho_every)
+            e_mix = walk_energy(c, int(fields.shape[1]), fields, tau, e0, order, reortho_every, expm)
             J = e_mix[2].clone()
             torch.cuda.synchronize(dev)
         finally:
             c.close()
         ctx.args = (h1.detach(), chol.detach(), fields, trial, na, nb, e0, tau, order, reortho_every, ckpt_every,
-                    precision, e_const)
+                    precision, e_const, expm)
         return J.to(h1.device)
 
     @staticmethod
     def backward(ctx, grad_out):
-        h1, chol, fields, trial, na, nb, e0, tau, order, r, ckpt, precision, e_const = ctx.args
+        h1, chol, fields, trial, na, nb, e0, tau, order, r, ckpt, precision, e_const, expm = ctx.args
         dev = fields.device
         c = Context(h1.cpu().numpy(), chol.cpu().numpy(), trial, na, nb, e_const, precision=precision, device=dev)
         try:
             w = c.new_walkers(int(fields.shape[1]))
             c.init_walkers(w)
             _, gh, gL = c.walk_backward(w, fields, tau, e0, order=order, reortho_every=r, ckpt_every=ckpt,
-                                        dJ=float(grad_out))
+                                        dJ=float(grad_out), expm=expm)
             torch.cuda.synchronize(dev)
         finally:
             c.close()
-        return (gh.to(h1.device), gL.to(chol.device)) + (None,) * 11
+        return (gh.to(h1.device), gL.to(chol.device)) + (None,) * 12

@@ -331,8 +331,9 @@ template <typename R>
 cudaError_t launch_shift_field(const afqmc_ctx* c, int Nw, double tau, cudaStream_t s);
 template <typename R>
 cudaError_t launch_krylov_init(const afqmc_ctx* c, int Nw, cudaStream_t s);
+// Arnoldi step `it` with the product A b_it in wv (NULL: ws.term0)
 template <typename R>
-cudaError_t launch_krylov_orth(const afqmc_ctx* c, int Nw, int it, int k, cudaStream_t s);
+cudaError_t launch_krylov_orth(const afqmc_ctx* c, int Nw, int it, int k, cudaStream_t s, const void* wv = nullptr);
 template <typename R>
 cudaError_t launch_krylov_finish(const afqmc_ctx* c, int Nw, int k, cudaStream_t s);
 template <typename R>
@@ -415,6 +416,23 @@ cudaError_t adj_theta(const afqmc_ctx* c, int Nw, const typename C2<R>::t* thbar
                       cudaStream_t s);
 cudaError_t adj_seed_coef(int Nw, const double* wfin, const double* ecap, const double* e_loc, const double* emix,
                           double* omega, double* ecoef, double e0, double dE, double dJ, cudaStream_t s);
+// Krylov-action reverse (basis, Hessenberg and beta of the forward in the
+// workspace; Hs a copy of the Hessenberg block taken before the small
+// exponential overwrote its first column; Gb the basis adjoints, planes
+// gstride apart, stored as holomorphic-style adjoints g = conj(Gamma))
+template <typename R>
+cudaError_t kadj_seed(const afqmc_ctx* c, int Nw, int k, const typename C2<R>::t* gout, typename C2<R>::t* Gb,
+                      size_t gstride, double2* gy, cudaStream_t s);
+template <typename R>
+cudaError_t kadj_expm(const afqmc_ctx* c, int Nw, int k, const typename C2<R>::t* Hs, const double2* gy, double2* GH,
+                      double* gbeta, cudaStream_t s);
+template <typename R>
+cudaError_t kadj_orth(const afqmc_ctx* c, int Nw, int j, int k, const typename C2<R>::t* wj,
+                      const typename C2<R>::t* Hs, const double2* GH, typename C2<R>::t* Gb, size_t gstride,
+                      typename C2<R>::t* U, cudaStream_t s);
+template <typename R>
+cudaError_t kadj_input(const afqmc_ctx* c, int Nw, const typename C2<R>::t* Gb0, const double* gbeta,
+                       typename C2<R>::t* gx, cudaStream_t s);
 template <typename R>
 cudaError_t adj_eloc_seed(const afqmc_ctx* c, int Nw, const typename C2<R>::t* theta, const typename C2<R>::t* t,
                           const double* ecoef, typename C2<R>::t* thbar, cudaStream_t s);

@@ -1050,11 +1050,11 @@ cudaError_t launch_krylov_init(const afqmc_ctx* c, int Nw, cudaStream_t s) {
 }
 
 template <typename R>
-cudaError_t launch_krylov_orth(const afqmc_ctx* c, int Nw, int it, int k, cudaStream_t s) {
+cudaError_t launch_krylov_orth(const afqmc_ctx* c, int Nw, int it, int k, cudaStream_t s, const void* wv) {
   const int ncols = Nw * c->nc;
   const size_t bstride = (size_t)c->ws.n_walkers * c->nc * c->N;
   const size_t hs = (size_t)c->ws.n_walkers * c->nc;
-  const typename C2<R>::t* W = static_cast<const typename C2<R>::t*>(c->ws.term0);
+  const typename C2<R>::t* W = static_cast<const typename C2<R>::t*>(wv ? wv : c->ws.term0);
   typename C2<R>::t* Bs = static_cast<typename C2<R>::t*>(c->ws.basis);
   typename C2<R>::t* H = reinterpret_cast<typename C2<R>::t*>(c->ws.hess);
   const dim3 grid((ncols + 7) / 8);
@@ -1146,7 +1146,7 @@ cudaError_t launch_cn_solve(const afqmc_ctx* c, int Nw, void* X, void* Y, cudaSt
                                          cudaStream_t, const int*);                                        \
   template cudaError_t launch_mgs<R>(const afqmc_ctx*, int, void*, const uint8_t*, double*, cudaStream_t);  \
   template cudaError_t launch_krylov_init<R>(const afqmc_ctx*, int, cudaStream_t);                         \
-  template cudaError_t launch_krylov_orth<R>(const afqmc_ctx*, int, int, int, cudaStream_t);               \
+  template cudaError_t launch_krylov_orth<R>(const afqmc_ctx*, int, int, int, cudaStream_t, const void*);  \
   template cudaError_t launch_krylov_finish<R>(const afqmc_ctx*, int, int, cudaStream_t);                  \
   template cudaError_t launch_init_walkers<R>(const afqmc_ctx*, const afqmc_walkers*, cudaStream_t);
 AFQ_INST(double)

@@ -633,6 +633,301 @@ cudaError_t smem_ok(F* f, size_t bytes) {
                               (int)bytes);
 }
 
+// ---------------------------------------------------------------- Krylov action
+// Reverse of the Arnoldi approximation e^A x ~ beta B_k e^{H_k} e_1 of one
+// orbital column (Eqs. krylovsub-krylov; the forward is krylov_init/orth/
+// expm/combine).  The norms and the inner products b_i^H w are not
+// holomorphic, so inside these kernels the adjoint of a complex z is
+// Gamma_z with dJ = Re sum conj(Gamma_z) dz; at their boundary it is
+// converted to the holomorphic-style adjoint g = conj(Gamma) that the rest
+// of the reverse pass uses.  The basis adjoints are stored as g (Gb), so
+// that the product with A (g_b_j += A U_j, A symmetric) is a plain GEMM.
+
+template <typename R>
+__device__ __forceinline__ R wsum(R v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Seed of the output out = sum_i y_i b_i with adjoint g_out (= p2):
+// g_y_i = b_i^T g_out and Gb_i = y_i g_out, i < k.  One warp per column.
+template <typename R>
+__global__ void kadj_seed_kernel(const typename C2<R>::t* __restrict__ gout, const typename C2<R>::t* __restrict__ basis,
+                                 size_t bstride, const typename C2<R>::t* __restrict__ hy, size_t hs, int kmax,
+                                 typename C2<R>::t* __restrict__ Gb, size_t gstride, double2* __restrict__ gy, int N,
+                                 int ncols, int k) {
+  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (col >= ncols) return;
+  const typename C2<R>::t* g = gout + (size_t)col * N;
+  for (int i = 0; i < k; ++i) {
+    const cx<R> y = ldx(hy[(size_t)(i * kmax) * hs + col]);
+    const typename C2<R>::t* b = basis + i * bstride + (size_t)col * N;
+    typename C2<R>::t* o = Gb + i * gstride + (size_t)col * N;
+    R sr = R(0), si = R(0);
+    for (int p = lane; p < N; p += 32) {
+      const cx<R> gv = ldx(g[p]), bv = ldx(b[p]);
+      sr += bv.re * gv.re - bv.im * gv.im;
+      si += bv.re * gv.im + bv.im * gv.re;
+      o[p] = stx(y * gv);
+    }
+    sr = wsum(sr);
+    si = wsum(si);
+    if (lane == 0) gy[(size_t)i * hs + col] = make_double2((double)sr, (double)si);
+  }
+}
+
+// Adjoint of y = beta e^{H} e_1 (FP64, one thread per column).  With
+// Gamma_y = conj(g_y) and u = beta Gamma_y:
+//   Gamma_H = L(H^H, u e_1^T), the Frechet derivative of exp at H^H in the
+//   direction u e_1^T; its column m is the top half of exp(M) [0; e_m] for
+//   M = [[H^H, u e_1^T], [0, H^H]] (block-triangular exponential), taken by
+//   sub-steps of a Taylor series on the 2k-vector (u scaled to unit norm,
+//   the result scaled back: L is linear in its direction);
+//   Gamma_beta = Re sum_i conj(Gamma_y_i) v_i = Re sum_i g_y_i y_i / beta.
+// Only the upper-Hessenberg entries of Gamma_H are written (the others are
+// constant zeros of H).
+template <typename R, int KM>
+__global__ void __launch_bounds__(64) kadj_expm_kernel(const typename C2<R>::t* __restrict__ Hs,
+                                                       const typename C2<R>::t* __restrict__ hy, size_t hs, int kmax,
+                                                       const double* __restrict__ beta,
+                                                       const double2* __restrict__ gy, double2* __restrict__ GH,
+                                                       double* __restrict__ gbeta, int ncols, int k) {
+  const int col = blockIdx.x * 64 + threadIdx.x;
+  if (col >= ncols) return;
+  auto H = [&](int i, int j) -> cd { return ld(Hs + (size_t)(i * kmax + j) * hs + col); };
+  const double b = beta[col];
+  cd u[KM];
+  double gb = 0.0, un = 0.0;
+#pragma unroll
+  for (int i = 0; i < KM; ++i) {
+    u[i] = mk(0.0, 0.0);
+    if (i < k) {
+      const cd g = ldc(gy[(size_t)i * hs + col]);
+      gb += (g * ld(hy + (size_t)(i * kmax) * hs + col)).re;
+      u[i] = b * conj(g);
+      un += abs2(u[i]);
+    }
+  }
+  gbeta[col] = b > 0.0 ? gb / b : 0.0;
+  un = sqrt(un);
+  if (!(un > 0.0) || !(b > 0.0)) {
+    for (int m = 0; m < k; ++m)
+      for (int i = 0; i <= m + 1 && i < k; ++i) GH[(size_t)(i * kmax + m) * hs + col] = make_double2(0.0, 0.0);
+    return;
+  }
+  double u1 = 0.0;
+#pragma unroll
+  for (int i = 0; i < KM; ++i) {
+    u[i] = (1.0 / un) * u[i];
+    u1 += sqrt(abs2(u[i]));
+  }
+  // 1- and infinity-norms of H (H^H has them swapped)
+  double n1 = 0.0, ni = 0.0;
+  for (int j = 0; j < k; ++j) {
+    double cs = 0.0, rs = 0.0;
+    for (int i = 0; i <= j + 1 && i < k; ++i) cs += sqrt(abs2(H(i, j)));
+    for (int i = (j > 0 ? j - 1 : 0); i < k; ++i) rs += sqrt(abs2(H(j, i)));
+    n1 = fmax(n1, cs);
+    ni = fmax(ni, rs);
+  }
+  const double nm = fmax(n1, ni) + u1;
+  int msub = 1;
+  if (nm < 1e30) msub = (int)ceil(nm / 2.0);
+  if (msub < 1) msub = 1;
+  if (msub > 4096) msub = 4096;
+  const double sc = 1.0 / msub;
+  for (int m = 0; m < k; ++m) {
+    cd top[KM], bot[KM], tt[KM], tb[KM], nt[KM], nb[KM];
+#pragma unroll
+    for (int i = 0; i < KM; ++i) {
+      top[i] = mk(0.0, 0.0);
+      bot[i] = mk(i == m ? 1.0 : 0.0, 0.0);
+    }
+    for (int s = 0; s < msub; ++s) {
+#pragma unroll
+      for (int i = 0; i < KM; ++i) {
+        tt[i] = top[i];
+        tb[i] = bot[i];
+      }
+      for (int d = 1; d <= 80; ++d) {
+        const double f = sc / d;
+        // (H^H)_{ij} = conj(H_{ji}), nonzero for j <= i + 1
+#pragma unroll
+        for (int i = 0; i < KM; ++i) {
+          cd at = mk(0.0, 0.0), ab = mk(0.0, 0.0);
+          if (i < k) {
+#pragma unroll
+            for (int j = 0; j < KM; ++j)
+              if (j <= i + 1 && j < k) {
+                const cd a = conj(H(j, i));
+                at = at + a * tt[j];
+                ab = ab + a * tb[j];
+              }
+            at = at + u[i] * tb[0];
+          }
+          nt[i] = f * at;
+          nb[i] = f * ab;
+        }
+        double tn = 0.0, an = 0.0;
+#pragma unroll
+        for (int i = 0; i < KM; ++i) {
+          top[i] = top[i] + nt[i];
+          bot[i] = bot[i] + nb[i];
+          tt[i] = nt[i];
+          tb[i] = nb[i];
+          tn += abs2(nt[i]) + abs2(nb[i]);
+          an += abs2(top[i]) + abs2(bot[i]);
+        }
+        if (tn <= 1e-36 * an) break;
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < KM; ++i)
+      if (i <= m + 1 && i < k) GH[(size_t)(i * kmax + m) * hs + col] = make_double2(un * top[i].re, un * top[i].im);
+  }
+}
+
+// Reverse of Arnoldi step j (one warp per column, w in registers):
+//   forward  w^(0) = A b_j;  h_ij = b_i^H w^(i), w^(i+1) = w^(i) - h_ij b_i
+//            (i = 0..j);  nu = ||w^(j+1)||, b_{j+1} = w^(j+1) / nu (j+1 < k)
+//   reverse  Gamma_nu = Re Gamma_H[j+1][j] - Re(Gamma_b_{j+1}^H b_{j+1}) / nu
+//            Gamma_w  = Gamma_b_{j+1} / nu + Gamma_nu b_{j+1}
+//            for i = j..0:  Gamma_h = Gamma_H[i][j] - b_i^H Gamma_w,
+//              w^(i) = w^(i+1) + h_ij b_i,
+//              Gamma_b_i += -conj(h_ij) Gamma_w + conj(Gamma_h) w^(i),
+//              Gamma_w += Gamma_h b_i
+//   U_j = conj(Gamma_w) is the adjoint of A b_j (the caller adds A U_j to
+//   g_b_j and U_j b_j^T to the adjoint of A).  w^(j+1) is rebuilt from the
+//   stored product A b_j and the stored h_ij in the forward's order.  A
+//   column that broke down (nu = 0, b_{j+1} = 0) has Gamma_w = 0.
+template <typename R, int EPL>
+__global__ void kadj_orth_kernel(const typename C2<R>::t* __restrict__ basis, size_t bstride,
+                                 const typename C2<R>::t* __restrict__ wj, const typename C2<R>::t* __restrict__ Hs,
+                                 size_t hs, int kmax, const double2* __restrict__ GH, typename C2<R>::t* __restrict__ Gb,
+                                 size_t gstride, typename C2<R>::t* __restrict__ U, int N, int ncols, int j, int k) {
+  typedef typename C2<R>::t P;
+  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (col >= ncols) return;
+  const size_t co = (size_t)col * N;
+  cx<R> w[EPL], gw[EPL];
+#pragma unroll
+  for (int e = 0; e < EPL; ++e) {
+    const int p = lane + 32 * e;
+    w[e] = cx<R>{R(0), R(0)};
+    gw[e] = cx<R>{R(0), R(0)};
+    if (p < N) w[e] = ldx(wj[co + p]);
+  }
+  for (int i = 0; i <= j; ++i) {
+    const cx<R> h = ldx(Hs[(size_t)(i * kmax + j) * hs + col]);
+    const P* b = basis + i * bstride + co;
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      const int p = lane + 32 * e;
+      if (p < N) {
+        const cx<R> v = ldx(b[p]);
+        w[e].re -= h.re * v.re - h.im * v.im;
+        w[e].im -= h.re * v.im + h.im * v.re;
+      }
+    }
+  }
+  if (j + 1 < k) {
+    const R nu = Hs[(size_t)((j + 1) * kmax + j) * hs + col].x;
+    if (nu > R(0)) {
+      const P* bn = basis + (j + 1) * bstride + co;
+      const P* gn = Gb + (j + 1) * gstride + co;
+      cx<R> bv[EPL], gv[EPL];
+      R dot = R(0);  // Re(Gamma_b^H b) = Re sum g b
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) {
+        const int p = lane + 32 * e;
+        bv[e] = cx<R>{R(0), R(0)};
+        gv[e] = cx<R>{R(0), R(0)};
+        if (p < N) {
+          bv[e] = ldx(bn[p]);
+          gv[e] = ldx(gn[p]);
+        }
+        dot += gv[e].re * bv[e].re - gv[e].im * bv[e].im;
+      }
+      dot = wsum(dot);
+      const double gnu = GH[(size_t)((j + 1) * kmax + j) * hs + col].x - (double)dot / (double)nu;
+      const R inv = R(1) / nu, gr = (R)gnu;
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) {
+        gw[e].re = gv[e].re * inv + gr * bv[e].re;
+        gw[e].im = -gv[e].im * inv + gr * bv[e].im;
+      }
+    }
+  }
+  for (int i = j; i >= 0; --i) {
+    const cx<R> h = ldx(Hs[(size_t)(i * kmax + j) * hs + col]);
+    const P* b = basis + i * bstride + co;
+    P* gi = Gb + i * gstride + co;
+    cx<R> bv[EPL];
+    R sr = R(0), si = R(0);  // b_i^H Gamma_w
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      const int p = lane + 32 * e;
+      bv[e] = cx<R>{R(0), R(0)};
+      if (p < N) bv[e] = ldx(b[p]);
+      sr += bv[e].re * gw[e].re + bv[e].im * gw[e].im;
+      si += bv[e].re * gw[e].im - bv[e].im * gw[e].re;
+    }
+    sr = wsum(sr);
+    si = wsum(si);
+    const double2 gH = GH[(size_t)(i * kmax + j) * hs + col];
+    const cx<R> gh{(R)(gH.x - (double)sr), (R)(gH.y - (double)si)};
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      const int p = lane + 32 * e;
+      const cx<R> wp = w[e] + h * bv[e];  // w^(i)
+      if (p < N) {
+        // stored conjugated: g_b_i += -h conj(Gamma_w) + Gamma_h conj(w^(i))
+        cx<R> g = ldx(gi[p]);
+        g.re += -(h.re * gw[e].re + h.im * gw[e].im) + (gh.re * wp.re + gh.im * wp.im);
+        g.im += -(h.im * gw[e].re - h.re * gw[e].im) + (gh.im * wp.re - gh.re * wp.im);
+        gi[p] = stx(g);
+      }
+      gw[e] = gw[e] + gh * bv[e];
+      w[e] = wp;
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < EPL; ++e) {
+    const int p = lane + 32 * e;
+    if (p < N) U[co + p] = stx(cx<R>{gw[e].re, -gw[e].im});
+  }
+}
+
+// Adjoint of b_0 = x / beta, beta = ||x||, into g_x = conj(Gamma_x):
+//   Gamma_beta_tot = Gamma_beta - Re(Gamma_b0^H b_0) / beta
+//   Gamma_x = Gamma_b0 / beta + Gamma_beta_tot b_0
+// (g_x = 0 for a zero column, whose forward output is identically zero).
+template <typename R>
+__global__ void kadj_input_kernel(const typename C2<R>::t* __restrict__ basis, const typename C2<R>::t* __restrict__ Gb0,
+                                  const double* __restrict__ beta, const double* __restrict__ gbeta,
+                                  typename C2<R>::t* __restrict__ gx, int N, int ncols) {
+  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (col >= ncols) return;
+  const size_t co = (size_t)col * N;
+  const double b = beta[col];
+  if (!(b > 0.0)) {
+    for (int p = lane; p < N; p += 32) gx[co + p] = stx(cx<R>{R(0), R(0)});
+    return;
+  }
+  R dot = R(0);
+  for (int p = lane; p < N; p += 32) {
+    const cx<R> g = ldx(Gb0[co + p]), v = ldx(basis[co + p]);
+    dot += g.re * v.re - g.im * v.im;
+  }
+  dot = wsum(dot);
+  const R gbt = (R)(gbeta[col] - (double)dot / b), inv = (R)(1.0 / b);
+  for (int p = lane; p < N; p += 32) {
+    const cx<R> g = ldx(Gb0[co + p]), v = ldx(basis[co + p]);
+    gx[co + p] = stx(cx<R>{g.re * inv + gbt * v.re, g.im * inv - gbt * v.im});
+  }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ launch wrappers
@@ -760,7 +1055,75 @@ cudaError_t adj_eloc_seed(const afqmc_ctx* c, int Nw, const typename C2<R>::t* t
   return cudaGetLastError();
 }
 
+// Krylov-action reverse (the forward's basis, Hessenberg and beta in the
+// workspace; hs = column capacity of the Hessenberg arrays)
+template <typename R>
+cudaError_t kadj_seed(const afqmc_ctx* c, int Nw, int k, const typename C2<R>::t* gout, typename C2<R>::t* Gb,
+                      size_t gstride, double2* gy, cudaStream_t s) {
+  const int ncols = Nw * c->nc;
+  const size_t hs = (size_t)c->ws.n_walkers * c->nc, bstride = hs * c->N;
+  kadj_seed_kernel<R><<<(ncols + 7) / 8, 256, 0, s>>>(
+      gout, static_cast<const typename C2<R>::t*>(c->ws.basis), bstride,
+      reinterpret_cast<const typename C2<R>::t*>(c->ws.hess), hs, c->ws.kmax, Gb, gstride, gy, c->N, ncols, k);
+  return cudaGetLastError();
+}
+
+template <typename R, int KM>
+static cudaError_t kadj_expm_k(const afqmc_ctx* c, int ncols, int k, const typename C2<R>::t* Hs, const double2* gy,
+                               double2* GH, double* gbeta, cudaStream_t s) {
+  const size_t hs = (size_t)c->ws.n_walkers * c->nc;
+  kadj_expm_kernel<R, KM><<<(ncols + 63) / 64, 64, 0, s>>>(
+      Hs, reinterpret_cast<const typename C2<R>::t*>(c->ws.hess), hs, c->ws.kmax, c->ws.beta, gy, GH, gbeta, ncols, k);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t kadj_expm(const afqmc_ctx* c, int Nw, int k, const typename C2<R>::t* Hs, const double2* gy, double2* GH,
+                      double* gbeta, cudaStream_t s) {
+  const int ncols = Nw * c->nc;
+  return k <= 8 ? kadj_expm_k<R, 8>(c, ncols, k, Hs, gy, GH, gbeta, s)
+         : k <= 16 ? kadj_expm_k<R, 16>(c, ncols, k, Hs, gy, GH, gbeta, s)
+                   : kadj_expm_k<R, 32>(c, ncols, k, Hs, gy, GH, gbeta, s);
+}
+
+template <typename R>
+cudaError_t kadj_orth(const afqmc_ctx* c, int Nw, int j, int k, const typename C2<R>::t* wj,
+                      const typename C2<R>::t* Hs, const double2* GH, typename C2<R>::t* Gb, size_t gstride,
+                      typename C2<R>::t* U, cudaStream_t s) {
+  const int ncols = Nw * c->nc;
+  const size_t hs = (size_t)c->ws.n_walkers * c->nc, bstride = hs * c->N;
+  const typename C2<R>::t* B = static_cast<const typename C2<R>::t*>(c->ws.basis);
+  const dim3 grid((ncols + 7) / 8);
+  if (c->N <= 128)
+    kadj_orth_kernel<R, 4><<<grid, 256, 0, s>>>(B, bstride, wj, Hs, hs, c->ws.kmax, GH, Gb, gstride, U, c->N, ncols,
+                                                j, k);
+  else if (c->N <= 256)
+    kadj_orth_kernel<R, 8><<<grid, 256, 0, s>>>(B, bstride, wj, Hs, hs, c->ws.kmax, GH, Gb, gstride, U, c->N, ncols,
+                                                j, k);
+  else
+    kadj_orth_kernel<R, 16><<<grid, 256, 0, s>>>(B, bstride, wj, Hs, hs, c->ws.kmax, GH, Gb, gstride, U, c->N,
+                                                 ncols, j, k);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t kadj_input(const afqmc_ctx* c, int Nw, const typename C2<R>::t* Gb0, const double* gbeta,
+                       typename C2<R>::t* gx, cudaStream_t s) {
+  const int ncols = Nw * c->nc;
+  kadj_input_kernel<R><<<(ncols + 7) / 8, 256, 0, s>>>(static_cast<const typename C2<R>::t*>(c->ws.basis), Gb0,
+                                                       c->ws.beta, gbeta, gx, c->N, ncols);
+  return cudaGetLastError();
+}
+
 #define AFQ_ADJ_INST(R)                                                                                            \
+  template cudaError_t kadj_seed<R>(const afqmc_ctx*, int, int, const C2<R>::t*, C2<R>::t*, size_t, double2*,      \
+                                    cudaStream_t);                                                                 \
+  template cudaError_t kadj_expm<R>(const afqmc_ctx*, int, int, const C2<R>::t*, const double2*, double2*, double*, \
+                                    cudaStream_t);                                                                 \
+  template cudaError_t kadj_orth<R>(const afqmc_ctx*, int, int, int, const C2<R>::t*, const C2<R>::t*,              \
+                                    const double2*, C2<R>::t*, size_t, C2<R>::t*, cudaStream_t);                   \
+  template cudaError_t kadj_input<R>(const afqmc_ctx*, int, const C2<R>::t*, const double*, C2<R>::t*,             \
+                                     cudaStream_t);                                                                \
   template cudaError_t adj_sanitize<R>(const C2<R>::t*, C2<R>::t*, const double*, const double*, size_t, int,     \
                                        cudaStream_t);                                                              \
   template cudaError_t adj_sum_terms<R>(const C2<R>::t*, C2<R>::t*, int, size_t, int, cudaStream_t);               \

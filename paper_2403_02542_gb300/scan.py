@@ -7,7 +7,8 @@ so the points are correlated), and its derivative
 dJ/ds = sum dJ/dh1 * dH1 + sum dJ/dL * dL from the walk adjoint
 (afqmc_walk_backward).  Central differences of J along the path are taken
 beside it as a check.  The paper has no gradients; this uses the library's
-adjoint of the fixed-field walk (Split-2 + Taylor, Sec. III.B, Eq. taylor).
+adjoint of the fixed-field walk (Split-2 with the Taylor action, Sec. III.B,
+Eq. taylor, or the Krylov action, Eqs. krylovsub-krylov).
 """
 from __future__ import annotations
 
@@ -19,7 +20,7 @@ from .api import Context, walk_energy
 
 def path_scan(system, fields: torch.Tensor, s_values, dH1: np.ndarray, dL: np.ndarray, tau: float, e0: float,
               order: int = 6, reortho_every: int = 0, ckpt_every: int = 10, precision: str = "mixed",
-              fd_step: float | None = 1e-2, device="cuda"):
+              fd_step: float | None = 1e-2, device="cuda", expm: str = "taylor"):
     """Returns a list of dicts {s, J, dJds, dJds_fd (or None), live} for every s."""
     out = []
     nw = int(fields.shape[1])
@@ -31,7 +32,7 @@ def path_scan(system, fields: torch.Tensor, s_values, dH1: np.ndarray, dL: np.nd
             w = c.new_walkers(nw)
             c.init_walkers(w)
             J, gh, gL = c.walk_backward(w, fields, tau, e0, order=order, reortho_every=reortho_every,
-                                        ckpt_every=ckpt_every)
+                                        ckpt_every=ckpt_every, expm=expm)
             dJds = float((gh.cpu().numpy() * dH1).sum() + (gL.cpu().numpy() * dL).sum())
             Jv, live = float(J[2]), float(J[3])
         finally:
@@ -44,7 +45,7 @@ def path_scan(system, fields: torch.Tensor, s_values, dH1: np.ndarray, dL: np.nd
                 c = Context(system.h1 + sp * dH1, system.L + sp * dL, system.trial, system.na, system.nb,
                             system.e_const, precision=precision, device=device)
                 try:
-                    vals.append(float(walk_energy(c, nw, fields, tau, e0, order, reortho_every)[2]))
+                    vals.append(float(walk_energy(c, nw, fields, tau, e0, order, reortho_every, expm)[2]))
                 finally:
                     c.close()
             fd = (vals[0] - vals[1]) / (2.0 * fd_step)

@@ -43,7 +43,8 @@ def _e0(s):
     return float(R.local_energy(ham, ham.trial.to(CT)).real)
 
 
-def _gpu(s, nw, fields, tau, e0, order, r, ckpt, dead=(), psi_grad=False, h1=None, L=None, precision="fp64"):
+def _gpu(s, nw, fields, tau, e0, order, r, ckpt, dead=(), psi_grad=False, h1=None, L=None, precision="fp64",
+         expm="taylor"):
     from paper_2403_02542_gb300.api import Context
     ctx = Context(s.h1 if h1 is None else h1, s.L if L is None else L, s.trial, s.na, s.nb, s.e_const,
                   precision=precision)
@@ -52,7 +53,8 @@ def _gpu(s, nw, fields, tau, e0, order, r, ckpt, dead=(), psi_grad=False, h1=Non
     for d in dead:
         w.weight[d] = 0.0
     f = torch.as_tensor(np.stack(fields), device=ctx.device)
-    out = ctx.walk_backward(w, f, tau, e0, order=order, reortho_every=r, ckpt_every=ckpt, grad_psi0=psi_grad)
+    out = ctx.walk_backward(w, f, tau, e0, order=order, reortho_every=r, ckpt_every=ckpt, grad_psi0=psi_grad,
+                            expm=expm)
     torch.cuda.synchronize()
     # the initial walkers are left unchanged
     assert torch.all(w.weight.cpu()[list(set(range(nw)) - set(dead))] == 1.0)
@@ -79,7 +81,7 @@ def _plain_J(s, nw, fields, tau, e0, order, r, h1=None, L=None):
     return v
 
 
-def _oracle(s, nw, fields, tau, e0, order, r, dead=()):
+def _oracle(s, nw, fields, tau, e0, order, r, dead=(), method="taylor"):
     h1 = torch.tensor(s.h1, dtype=RT, requires_grad=True)
     L = torch.tensor(s.L, dtype=RT, requires_grad=True)
     ham = R.Hamiltonian(h1, L, torch.as_tensor(s.trial, dtype=RT), s.na, s.nb, s.e_const)
@@ -87,7 +89,7 @@ def _oracle(s, nw, fields, tau, e0, order, r, dead=()):
     W0 = torch.ones(nw, dtype=RT)
     for d in dead:
         W0[d] = 0.0
-    J, W, _ = R.walk_objective(ham, psi0, W0, fields, tau, e0, k=order, reortho_every=r)
+    J, W, _ = R.walk_objective(ham, psi0, W0, fields, tau, e0, k=order, reortho_every=r, method=method)
     gh, gL, gp = torch.autograd.grad(J, [h1, L, psi0])
     return float(J), _sym(gh), _sym(gL), gp.conj(), W
 
@@ -138,6 +140,62 @@ def test_walk_adjoint_matches_oracle_autograd(N, na, nb, G, nw, steps, r, ckpt, 
     _close_entrywise(gL, gL_ref, "dJ/dL")
     _close_entrywise(gp, gp_ref.transpose(1, 2), "dJ/dPsi0")
     assert torch.equal(gh, gh.T) and torch.equal(gL, gL.transpose(1, 2))
+
+
+@pytest.mark.parametrize("N,na,nb,G,nw,steps,r,ckpt,dead,k", [
+    (10, 2, 2, 12, 5, 6, 2, 3, (1,), 6),
+    (14, 3, 2, 20, 6, 5, 3, 2, (), 10),
+    (10, 2, 1, 12, 3, 4, 0, 10, (), 12),     # dimension above N: the whole space, k = N
+    (24, 3, 3, 40, 4, 4, 1, 1, (2,), 4),
+])
+def test_walk_adjoint_krylov_matches_oracle_autograd(N, na, nb, G, nw, steps, r, ckpt, dead, k):
+    """The Krylov action of Eqs. krylovsub-krylov in every step: FP64
+    gradients entry by entry against autograd through the oracle's Arnoldi
+    steps, norms and small exponential (torch.linalg.matrix_exp)."""
+    s = _Sys(N, na, nb, G, seed=3 * N + steps)
+    tau = 0.05
+    e0 = _e0(s)
+    fields = [make_fields(N, 50 + kk, nw, G) for kk in range(steps)]
+    J_ref, gh_ref, gL_ref, gp_ref, W_ref = _oracle(s, nw, fields, tau, e0, k, r, dead, method="krylov")
+    assert int((W_ref > 0).sum()) == nw - len(dead)
+    J, gh, gL, gp = _gpu(s, nw, fields, tau, e0, k, r, ckpt, dead, psi_grad=True, expm="krylov")
+    assert abs(float(J[2]) - J_ref) <= 1e-10 * abs(J_ref)
+    _close_entrywise(gh, gh_ref, "dJ/dh1")
+    _close_entrywise(gL, gL_ref, "dJ/dL")
+    _close_entrywise(gp, gp_ref.transpose(1, 2), "dJ/dPsi0")
+    assert torch.equal(gh, gh.T) and torch.equal(gL, gL.transpose(1, 2))
+
+
+@pytest.mark.parametrize("N,na,nb,G,nw,steps,r,ckpt,dead,k", [
+    (10, 2, 2, 12, 5, 6, 2, 3, (1,), 6),
+    (24, 3, 3, 40, 4, 4, 1, 2, (), 8),
+])
+def test_walk_adjoint_krylov_mixed_matches_oracle_autograd(N, na, nb, G, nw, steps, r, ckpt, dead, k):
+    s = _Sys(N, na, nb, G, seed=3 * N + steps)
+    tau = 0.05
+    e0 = _e0(s)
+    fields = [make_fields(N, 50 + kk, nw, G) for kk in range(steps)]
+    J_ref, gh_ref, gL_ref, gp_ref, W_ref = _oracle(s, nw, fields, tau, e0, k, r, dead, method="krylov")
+    assert int((W_ref > 0).sum()) == nw - len(dead)
+    J, gh, gL, gp = _gpu(s, nw, fields, tau, e0, k, r, ckpt, dead, psi_grad=True, precision="mixed",
+                         expm="krylov")
+    assert gp.dtype == torch.complex64
+    assert abs(float(J[2]) - J_ref) <= MIXED_J_TOL
+    _close(gh, gh_ref, MIXED_GRAD_RTOL)
+    _close(gL, gL_ref, MIXED_GRAD_RTOL)
+    _close(gp.to(CT), gp_ref.transpose(1, 2), MIXED_GRAD_RTOL)
+
+
+def test_walk_adjoint_krylov_is_independent_of_checkpoint_spacing():
+    """Recomputing the Arnoldi steps from checkpoints changes no bit."""
+    s = _Sys(14, 3, 2, 20, seed=1401)
+    tau, nw, steps, k = 0.05, 6, 6, 8
+    e0 = _e0(s)
+    fields = [make_fields(14, 70 + kk, nw, s.G) for kk in range(steps)]
+    a = _gpu(s, nw, fields, tau, e0, k, 2, 1, psi_grad=True, expm="krylov")
+    b = _gpu(s, nw, fields, tau, e0, k, 2, 4, psi_grad=True, expm="krylov")
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
 
 
 def test_walk_adjoint_matches_oracle_autograd_mid_size():
