@@ -31,6 +31,12 @@ Readings of the paper used here (the paper is silent or ambiguous on them):
       invariant subspace is declared when the new subdiagonal entry is
       <= 1e-12 ||A||_F (the basis vectors are unit vectors).
   R6  The small exponential e^{A_k} is torch.linalg.matrix_exp.
+  R30 Lanczos variant of the Krylov action: the paper uses Arnoldi (Sec.
+      IV.C) for a general non-Hermitian A; the field matrix is complex
+      symmetric, so the three-term recurrence with the bilinear form u^T v
+      spans the same Krylov space with a tridiagonal projected matrix
+      (lanczos_action).  No re-orthogonalisation; the breakdown test of R5
+      on |beta_j|.
   R20 Block Krylov (Sec. IV.D, Eqs. bkrylovsub-bkrylov) works on each spin
       block separately (the two determinants span separate spaces); the QR
       of Psi and of every new block is modified Gram-Schmidt (mgs_qr), the
@@ -63,7 +69,7 @@ __all__ = [
     "Hamiltonian", "make_hamiltonian", "overlap", "greens_function",
     "log_overlap", "theta", "mean_field_shift", "mixed_L_expectation",
     "force_bias", "propagation_h1", "half_step_propagator", "field_matrix",
-    "taylor_action", "chebyshev_coefficients", "chebyshev_action", "krylov_action", "block_krylov_action", "exact_action", "expm_action",
+    "taylor_action", "chebyshev_coefficients", "chebyshev_action", "krylov_action", "lanczos_action", "block_krylov_action", "exact_action", "expm_action",
     "split2_propagate", "split1_propagate", "taylor_propagate", "crank_nicolson_propagate", "propagate",
     "local_energy", "energy_window", "mixed_energy",
     "mgs_qr", "reorthonormalise", "weight_update", "propagate_and_ratio", "step", "init_walkers",
@@ -281,6 +287,73 @@ def krylov_action(A, psi, k):
     return torch.stack(cols, dim=1)
 
 
+def _bilinear(u, v):
+    """u^T v, the symmetric bilinear form of complex-symmetric Lanczos (no conjugation)."""
+    return (u * v).sum()
+
+
+def _tridiagonal(alpha, beta):
+    """Symmetric tridiagonal T with diagonal alpha and off-diagonals beta."""
+    k = len(alpha)
+    T = torch.zeros(k, k, dtype=CT)
+    for j in range(k):
+        T[j, j] = alpha[j]
+    for j in range(k - 1):
+        T[j + 1, j] = beta[j]
+        T[j, j + 1] = beta[j]
+    return T
+
+
+def _lanczos_column(A, psi_col, k, normA, f=None):
+    """Complex-symmetric Lanczos approximation of e^A psi for one orbital
+    vector (reading R30).  The field matrix is complex symmetric (A^T = A,
+    Eq. heffTOT with real symmetric L_g), so the three-term recurrence with
+    the bilinear form u^T v builds a basis V_k of the Krylov space of Eq.
+    krylovsub with V_k^T V_k = 1 and the symmetric tridiagonal
+    T_k = V_k^T A V_k; the action is V_k f(T_k) e_1 beta with
+    beta = (psi^T psi)^{1/2} (principal root; the result does not depend on
+    the sign) and f = exp (Eq. krylov with the Hermitian projection replaced
+    by the bilinear one).  The recurrence stops like the Arnoldi one (R5)
+    when |beta_j| <= 1e-12 ||A||_F."""
+    N = A.shape[-1]
+    beta = torch.sqrt(_bilinear(psi_col, psi_col))
+    if float(beta.detach().abs()) == 0.0:
+        return torch.zeros_like(psi_col), 0
+    kk = min(k, N)
+    V = [psi_col / beta]
+    alpha, off = [], []
+    for j in range(kk):
+        w = A @ V[j]
+        if j > 0:
+            w = w - off[j - 1] * V[j - 1]
+        alpha.append(_bilinear(V[j], w))
+        w = w - alpha[j] * V[j]
+        if j + 1 < kk:
+            b = torch.sqrt(_bilinear(w, w))
+            if float(b.detach().abs()) <= 1e-12 * float(normA.detach()):
+                break
+            off.append(b)
+            V.append(w / b)
+    k_eff = len(alpha)
+    T = _tridiagonal(alpha, off[:k_eff - 1])
+    fT = torch.linalg.matrix_exp(T) if f is None else f(T)
+    y = fT[:, 0] * beta
+    out = torch.zeros_like(psi_col)
+    for i in range(k_eff):
+        out = out + y[i] * V[i]
+    return out, k_eff
+
+
+def lanczos_action(A, psi, k, f=None):
+    """lanczos_k{A, psi} = V_k e^{T_k} e_1 (psi^T psi)^{1/2} for every orbital
+    column (reading R30); f replaces exp for the pins."""
+    if psi.dim() == 3:
+        return torch.stack([lanczos_action(A[w], psi[w], k, f) for w in range(psi.shape[0])])
+    normA = torch.linalg.matrix_norm(A)
+    cols = [_lanczos_column(A, psi[:, j], k, normA, f)[0] for j in range(psi.shape[1])]
+    return torch.stack(cols, dim=1)
+
+
 def _block_arnoldi(A, X, k, normA):
     """Block-Krylov approximation of e^A X for one spin block X [N, n]
     (Eqs. bkrylovsub-bkrylov): X = B_1 R, the orthonormal basis
@@ -335,6 +408,8 @@ def expm_action(A, psi, method, k, spins=None):
         return taylor_action(A, psi, k)
     if method == "krylov":
         return krylov_action(A, psi, k)
+    if method == "lanczos":
+        return lanczos_action(A, psi, k)
     if method == "bkrylov":
         return block_krylov_action(A, psi, k, spins)
     if method == "chebyshev":

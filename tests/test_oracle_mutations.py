@@ -35,6 +35,32 @@ def _with(out, **repl):
     return tuple(repl.get(n, v) for n, v in zip(names, out))
 
 
+def _lanczos_two_term(orig):
+    """Lanczos column without the beta_{j-1} v_{j-1} term of the recurrence."""
+    def bad(A, psi_col, k, normA, f=None):
+        beta = torch.sqrt((psi_col * psi_col).sum())
+        kk = min(k, A.shape[-1])
+        V, alpha, off = [psi_col / beta], [], []
+        for j in range(kk):
+            w = A @ V[j]
+            alpha.append((V[j] * w).sum())
+            w = w - alpha[j] * V[j]
+            if j + 1 < kk:
+                off.append(torch.sqrt((w * w).sum()))
+                V.append(w / off[j])
+        T = R._tridiagonal(alpha, off)
+        y = (torch.linalg.matrix_exp(T) if f is None else f(T))[:, 0] * beta
+        return sum(y[i] * V[i] for i in range(len(alpha))), len(alpha)
+    return bad
+
+
+def _tridiagonal_lower_only(orig):
+    def bad(alpha, beta):
+        T = orig(alpha, beta)
+        return torch.tril(T)
+    return bad
+
+
 # arguments of propagate_and_ratio: (ham, psi, logovl, x, tau, method, k, B, L_bar, ec, ...)
 _STEP_MUTANTS = [
     ("step: importance factor with the wrong sign",
@@ -65,6 +91,17 @@ MUTATIONS = [
      "test_krylov_full_dimension_is_exact"),
     ("Krylov dimension one short", "krylov_action",
      lambda o: lambda A, psi, k: o(A, psi, max(k - 1, 1)), "test_krylov_full_dimension_is_exact"),
+    ("Lanczos with the Hermitian inner product", "_bilinear",
+     lambda o: lambda u, v: torch.vdot(u, v), "test_lanczos_full_dimension_is_exact"),
+    ("Lanczos without (psi^T psi)^(1/2)", "lanczos_action",
+     lambda o: lambda A, psi, k, f=None: o(A, psi, k, f) / torch.sqrt((psi * psi).sum(-2, keepdim=True)),
+     "test_lanczos_full_dimension_is_exact"),
+    ("Lanczos dimension one short", "lanczos_action",
+     lambda o: lambda A, psi, k, f=None: o(A, psi, max(k - 1, 1), f), "test_lanczos_full_dimension_is_exact"),
+    ("Lanczos tridiagonal without its upper diagonal", "_tridiagonal", _tridiagonal_lower_only,
+     "test_lanczos_is_exact_for_polynomials_below_the_dimension"),
+    ("Lanczos recurrence without the beta_{j-1} v_{j-1} term", "_lanczos_column", _lanczos_two_term,
+     "test_lanczos_is_the_bilinear_projection_on_the_krylov_space"),
     ("block Krylov one block short", "block_krylov_action",
      lambda o: lambda A, psi, k, spins=None: o(A, psi, max(k - 1, 1), spins),
      "test_block_krylov_full_space_is_exact"),

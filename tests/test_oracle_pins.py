@@ -173,6 +173,89 @@ def test_krylov_hessenberg_projection():
     assert torch.allclose(out, ref, rtol=1e-9, atol=1e-11)
 
 
+def _rand_csym(g, N, scale):
+    X = _rand_c(g, N, N)
+    return scale * 0.5 * (X + X.T)
+
+
+def test_lanczos_full_dimension_is_exact():
+    """Reading R30, k = N: the Lanczos space is the whole space and V_N is
+    complex orthogonal, so V_N e^{T_N} V_N^T psi = e^A psi to roundoff."""
+    g = torch.Generator().manual_seed(40)
+    for N in (3, 5, 8):
+        A = _rand_csym(g, N, 0.5)
+        psi = _rand_c(g, N, 2)
+        ref = torch.linalg.matrix_exp(A) @ psi
+        assert torch.allclose(R.lanczos_action(A, psi, N), ref, rtol=1e-10, atol=1e-11)
+        assert torch.allclose(R.lanczos_action(A, psi, N + 2), ref, rtol=1e-10, atol=1e-11)
+
+
+def test_lanczos_is_exact_for_polynomials_below_the_dimension():
+    """Any polynomial p of degree <= k - 1: V_k p(T_k) e_1 beta = p(A) psi
+    (the Krylov space of Eq. krylovsub holds p(A) psi and the bilinear
+    projection reproduces it), at every k."""
+    g = torch.Generator().manual_seed(41)
+    N = 10
+    A = _rand_csym(g, N, 0.4)
+    psi = _rand_c(g, N, 3)
+    for k in (1, 2, 4, 7):
+        coef = _rand_c(g, k, 1)[:, 0]
+
+        def p(M):
+            out = torch.zeros_like(M)
+            P = torch.eye(M.shape[0], dtype=CT)
+            for c in coef:
+                out = out + c * P
+                P = P @ M
+            return out
+        ref = p(A) @ psi
+        assert torch.allclose(R.lanczos_action(A, psi, k, f=p), ref, rtol=1e-10, atol=1e-11), k
+
+
+def test_lanczos_is_the_bilinear_projection_on_the_krylov_space():
+    """With the power basis K = [psi, A psi, ..., A^{k-1} psi] and its
+    bilinear Gram matrix K^T K, lanczos_k = K exp((K^T K)^{-1} K^T A K) e_1
+    (the same space and projection written without the recurrence; library
+    solve and matrix_exp)."""
+    g = torch.Generator().manual_seed(42)
+    N, k = 9, 4
+    A = _rand_csym(g, N, 0.6)
+    psi = _rand_c(g, N, 1)[:, 0]
+    K = torch.stack([torch.linalg.matrix_power(A, j) @ psi for j in range(k)], 1)
+    M = torch.linalg.solve(K.T @ K, K.T @ A @ K)
+    e1 = torch.zeros(k, dtype=CT)
+    e1[0] = 1.0
+    ref = K @ (torch.linalg.matrix_exp(M) @ e1)
+    out = R.lanczos_action(A, psi[:, None], k)[:, 0]
+    assert torch.allclose(out, ref, rtol=1e-8, atol=1e-10)
+    # and it is not the Hermitian (Arnoldi) projection for a complex A
+    arn = R.krylov_action(A, psi[:, None], k)[:, 0]
+    assert float((arn - out).abs().max()) > 1e-6 * float(out.abs().max())
+
+
+def test_lanczos_equals_arnoldi_for_real_symmetric_matrices():
+    """A real symmetric and psi real: the bilinear and Hermitian forms agree,
+    so Lanczos and Arnoldi build the same basis and projected matrix."""
+    g = torch.Generator().manual_seed(43)
+    N = 11
+    X = torch.randn(N, N, dtype=torch.float64, generator=g)
+    A = (0.2 * (X + X.T)).to(CT)
+    psi = torch.randn(N, 3, dtype=torch.float64, generator=g).to(CT)
+    for k in (2, 5, 8):
+        assert torch.allclose(R.lanczos_action(A, psi, k), R.krylov_action(A, psi, k), rtol=1e-11, atol=1e-12)
+
+
+def test_lanczos_error_decreases_with_k():
+    g = torch.Generator().manual_seed(44)
+    N = 12
+    A = _rand_csym(g, N, 0.3)
+    psi = _rand_c(g, N, 1)
+    ref = torch.linalg.matrix_exp(A) @ psi
+    errs = [float((R.lanczos_action(A, psi, k) - ref).norm()) for k in range(1, 10)]
+    assert all(b < a for a, b in zip(errs, errs[1:]))
+    assert errs[-1] < 1e-6 * float(ref.norm())
+
+
 def test_block_krylov_full_space_is_exact():
     """k n = N (Eq. bkrylov): the block Krylov space is the whole space, so the
     action is e^A X to roundoff, for each spin block separately."""
@@ -697,6 +780,9 @@ def test_first_step_from_trial_closed_form():
     # block Krylov with N // n blocks spans each spin's whole space: the same step
     psib, lob, Wb, _ = R.step(ham, psi, lo, W, x, tau, -5.0, method="bkrylov", k=ham.N)
     assert torch.allclose(psib, psi1, rtol=1e-11, atol=1e-12) and torch.allclose(Wb, W1, rtol=1e-12)
+    # and so does the Lanczos space of dimension N (reading R30)
+    psil, lol, Wl, _ = R.step(ham, psi, lo, W, x, tau, -5.0, method="lanczos", k=ham.N)
+    assert torch.allclose(psil, psi1, rtol=1e-10, atol=1e-11) and torch.allclose(Wl, W1, rtol=1e-11)
     for w in range(2):
         A = 1j * math.sqrt(tau) * torch.einsum("g,gpq->pq", x[w].to(CT), ham.L.to(CT))
         ref = B @ torch.linalg.matrix_exp(A) @ B @ ham.trial.to(CT)
