@@ -419,7 +419,7 @@ def propagator_rates(dev, steps=3):
     from paper_2403_02542_gb300.inputs import config_system
     s = config_system("large")
     variants = [("split1", "krylov", 10), ("taylor", "taylor", 8), ("cn", "taylor", 0),
-                ("split2", "chebyshev", 8), ("split2", "taylor", 8)]
+                ("split2", "chebyshev", 8), ("split2", "taylor", 8), ("split2", "lanczos", 10)]
     out = {"workload": "large-step workload (N=128, Na=Nb=20, N_gamma=640, 1024 walkers, tau=0.05, E_loc every "
                        "step, MGS every 5 steps), mixed", "unit": "walker-steps/s", "rates": {}}
     gen = torch.Generator(device=dev)
@@ -458,11 +458,55 @@ def propagator_rates(dev, steps=3):
     return out
 
 
+def lanczos_rate(dev, K=5, warmup=3):
+    """The headline workload (N=300, 50+50 electrons, 1500 vectors, 2048
+    walkers, tau=0.05, E_L every step, MGS every 5 steps, mixed) with the
+    complex-symmetric Lanczos action of dimension 10 in place of Arnoldi:
+    CUDA-event timed, per-class split from a separate pass, and E_L of the
+    two actions on the same walkers after one step."""
+    import torch
+    system, ctx, w, el, em, e0, _ = make_context(dev, HEADLINE, "mixed", NW, tune=True)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2718)
+    fields = torch.randn(warmup + K, NW, system.G, dtype=torch.float64, device=dev, generator=gen)
+    stream = torch.cuda.current_stream(dev)
+
+    n_steps = 0
+
+    def lstep(x):
+        nonlocal n_steps
+        n_steps += 1
+        ctx.step(w, x, TAU, e0, expm="lanczos", order=KDIM, reortho=(n_steps % REORTHO == 0), measure=True,
+                 e_loc=el, e_mix=em, reuse_bias=True)
+
+    for i in range(warmup):
+        lstep(fields[i])
+    ms = timed_steps(lstep, fields, warmup, K, stream) / K
+    split = class_split(ctx, lstep, fields, 0, 3, stream)
+    # one step from the same walkers with each action
+    psi0, W0, lo0, st0 = w.psi.clone(), w.weight.clone(), w.logovl.clone(), w.status.clone()
+    out_e = {}
+    for expm in ("krylov", "lanczos"):
+        w.psi.copy_(psi0); w.weight.copy_(W0); w.logovl.copy_(lo0); w.status.copy_(st0)
+        ctx.step(w, fields[0], TAU, e0, expm=expm, order=KDIM, measure=True, e_loc=el, e_mix=em)
+        out_e[expm] = el[:, 0].clone()
+    live = W0 > 0
+    dE = float((out_e["krylov"] - out_e["lanczos"]).abs()[live].max())
+    ctx.close()
+    del fields, w
+    torch.cuda.empty_cache()
+    return {"workload": "precision workload (N=300, Na=Nb=50, N_gamma=1500, 2048 walkers, tau=0.05, E_loc every "
+                        "step, MGS every 5 steps), mixed, complex-symmetric Lanczos of dimension 10",
+            "value": NW / (ms / 1000.0), "unit": "walker-steps/s", "ms_per_step": ms, "steps": K,
+            "kernel_ms_per_step": split,
+            "E_L_vs_arnoldi_max_abs_Ha": dE}
+
+
 def expm_accuracy(dev, nw=2400, n_steps=10, taus=(0.02, 0.1, 0.3), budget_s=60.0):
     """The accuracy study of Sec. IV.E (Fig. 1) through the library: on one
     synthetic system (N=64, Na=Nb=10, N_gamma=320, FP64), 2400 walkers, 10 steps
-    per run, the smallest order of the Taylor, Chebyshev, Krylov and
-    block-Krylov actions (orders up to 24; None beyond) whose run energy is
+    per run, the smallest order of the Taylor, Chebyshev, Krylov,
+    block-Krylov and Lanczos actions (orders up to 24; None beyond) whose run energy is
     within 1e-5 Ha of the order-64 Taylor run, at each time step.  Stops after
     budget_s seconds (the time steps not reached are left out)."""
     import time
@@ -1027,6 +1071,7 @@ def run_ours(args):
                 ("batched_workload", args.no_batched, lambda: batched_rate(dev)),
                 ("block_krylov_workload", args.no_block_krylov, lambda: block_krylov_rate(dev)),
                 ("propagator_workload", args.no_propagators, lambda: propagator_rates(dev)),
+                ("lanczos_workload", args.no_propagators, lambda: lanczos_rate(dev)),
                 ("expm_accuracy", args.no_expm_accuracy, lambda: expm_accuracy(dev)),
                 ("tau_extrapolation", args.no_tau_scan, lambda: tau_scan(dev))]
         for name, skip, fn in legs:

@@ -72,7 +72,13 @@ typedef enum {
 enum { AFQMC_SPLIT2 = 0, AFQMC_SPLIT1 = 1, AFQMC_TAYLORPROP = 2, AFQMC_CN = 3 };
 
 /* Action of the one-body exponential (Sec. IV). */
-enum { AFQMC_EXPM_TAYLOR = 0, AFQMC_EXPM_KRYLOV = 1, AFQMC_EXPM_BLOCK_KRYLOV = 2, AFQMC_EXPM_CHEBYSHEV = 3 };
+enum {
+  AFQMC_EXPM_TAYLOR = 0,
+  AFQMC_EXPM_KRYLOV = 1,
+  AFQMC_EXPM_BLOCK_KRYLOV = 2,
+  AFQMC_EXPM_CHEBYSHEV = 3,
+  AFQMC_EXPM_LANCZOS = 4
+};
 
 /* Arithmetic of a context.
  * AFQMC_FP64:  complex128 walkers, every step in FP64.
@@ -134,6 +140,16 @@ typedef struct {
  *   expm        AFQMC_EXPM_TAYLOR (order = Taylor order 0 <= k <= 64),
  *               AFQMC_EXPM_KRYLOV (order = Krylov dimension 1 <= k <= 32, one
  *               Krylov space per orbital column, Eq. krylov),
+ *               AFQMC_EXPM_LANCZOS (order = Krylov dimension 1 <= k <= 32; the
+ *               same Krylov space per column, Eq. krylovsub, built by the
+ *               complex-symmetric Lanczos recurrence, which the paper does
+ *               not use: A is complex symmetric, so the bilinear form u^T v
+ *               gives a basis V_k with V_k^T V_k = 1, the tridiagonal
+ *               T_k = V_k^T A V_k and the action V_k e^{T_k} e_1 beta,
+ *               beta = (psi^T psi)^{1/2}; three vectors read per step
+ *               instead of the k of Arnoldi's Gram-Schmidt, no
+ *               re-orthogonalisation, the recurrence stops when
+ *               |beta_j| <= 1e-12 ||A||_F),
  *               AFQMC_EXPM_CHEBYSHEV (order = expansion order 0 <= k <= 64,
  *               Sec. IV.B: sum_n c_n T_n(A) Psi with c_0 = I_0(1),
  *               c_n = 2 I_n(1) and the recurrence of Eq. chebpoly, A not

@@ -13,7 +13,7 @@ LIB_PATH = os.path.join(HERE, "libafqmc.so")
 
 AFQMC_OK, AFQMC_EINVAL, AFQMC_EDOM, AFQMC_ENOMEM, AFQMC_ECUDA, AFQMC_ENOTSUP, AFQMC_ESTATE = range(7)
 AFQMC_SPLIT2, AFQMC_SPLIT1, AFQMC_TAYLORPROP, AFQMC_CN = 0, 1, 2, 3
-AFQMC_EXPM_TAYLOR, AFQMC_EXPM_KRYLOV, AFQMC_EXPM_BLOCK_KRYLOV, AFQMC_EXPM_CHEBYSHEV = 0, 1, 2, 3
+AFQMC_EXPM_TAYLOR, AFQMC_EXPM_KRYLOV, AFQMC_EXPM_BLOCK_KRYLOV, AFQMC_EXPM_CHEBYSHEV, AFQMC_EXPM_LANCZOS = 0, 1, 2, 3, 4
 AFQMC_FP64, AFQMC_MIXED = 0, 1
 W_FCAP, W_REWEIGHT, W_PHASE, W_NONFINITE, W_SINGULAR = 0x1, 0x2, 0x4, 0x8, 0x10
 STATIC_SCRATCH_BYTES = 32 << 20

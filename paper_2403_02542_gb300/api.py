@@ -17,7 +17,7 @@ PROPAGATORS = {"split2": L.AFQMC_SPLIT2, "split1": L.AFQMC_SPLIT1, "taylor": L.A
                "cn": L.AFQMC_CN}
 # actions of the one-body exponential of Sec. IV built in the library
 EXPMS = {"taylor": L.AFQMC_EXPM_TAYLOR, "krylov": L.AFQMC_EXPM_KRYLOV, "bkrylov": L.AFQMC_EXPM_BLOCK_KRYLOV,
-         "chebyshev": L.AFQMC_EXPM_CHEBYSHEV}
+         "chebyshev": L.AFQMC_EXPM_CHEBYSHEV, "lanczos": L.AFQMC_EXPM_LANCZOS}
 
 
 def _ptr(t: torch.Tensor | None) -> int | None:

@@ -140,7 +140,7 @@ static bool small_inverse(int n, std::vector<double> m, std::vector<double>& inv
 // ---------------------------------------------------------------- workspace
 static void ws_free(Workspace& ws) {
   void* ptrs[] = {ws.theta, ws.t, ws.c, ws.A, ws.psi_b, ws.term0, ws.term1, ws.acc, ws.psi_new, ws.splitk, ws.basis,
-                  ws.hess, ws.beta, ws.scal, ws.logdet, ws.epart, ws.eloc, ws.ecap, ws.emix, ws.alive,
+                  ws.hess, ws.beta, ws.cbeta, ws.scal, ws.logdet, ws.epart, ws.eloc, ws.ecap, ws.emix, ws.alive,
                   ws.bk, ws.bk_keff};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -171,6 +171,7 @@ static afqmc_status ws_ensure(afqmc_ctx* c, int Nw, int kmax) {
     CK(dmalloc(&ws.basis, (size_t)km * nw * per * cs));
     CK(dmalloc(&ws.hess, (size_t)nw * c->nc * km * km * 2 * sizeof(double)));
     CK(dmalloc(&ws.beta, (size_t)nw * c->nc * sizeof(double)));
+    CK(dmalloc(&ws.cbeta, (size_t)nw * c->nc * sizeof(double2)));
   }
   CK(dmalloc(&ws.scal, (size_t)nw * SC_COUNT * sizeof(double)));
   CK(dmalloc(&ws.logdet, (size_t)nw * 4 * sizeof(double)));
@@ -595,20 +596,23 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
     PK(AFQMC_K_OTHER, launch_bk_finish<R>(c, Nw, s));
     c->launches += 2 + jmax * (tc_av ? 3 : 2) + 2;
   } else {
+    // Krylov (Eq. krylov): Arnoldi with modified Gram-Schmidt, or the
+    // complex-symmetric Lanczos recurrence on the same space
     const int k = p->order;
+    const bool lz = p->expm == AFQMC_EXPM_LANCZOS;
     const size_t bstride = (size_t)ws.n_walkers * per;
     if (tc_av)
       PK(AFQMC_K_OTHER, tc_av_normA(c, Nw, s));
     else
       PK(AFQMC_K_OTHER, launch_normA<R>(c, Nw, s));
-    PK(AFQMC_K_OTHER, launch_krylov_init<R>(c, Nw, s));
+    PK(AFQMC_K_OTHER, lz ? launch_lanczos_init<R>(c, Nw, s) : launch_krylov_init<R>(c, Nw, s));
     for (int it = 0; it < k; ++it) {
       // tensor-core products read b_it from the planes the Arnoldi kernels wrote
       PK(AFQMC_K_EXPM, av(tc_av ? nullptr : static_cast<char*>(ws.basis) + it * bstride * cs, ws.term0, nullptr,
                           1.0));
-      PK(AFQMC_K_OTHER, launch_krylov_orth<R>(c, Nw, it, k, s));
+      PK(AFQMC_K_OTHER, lz ? launch_lanczos_step<R>(c, Nw, it, k, s) : launch_krylov_orth<R>(c, Nw, it, k, s));
     }
-    PK(AFQMC_K_OTHER, launch_krylov_finish<R>(c, Nw, k, s));
+    PK(AFQMC_K_OTHER, launch_krylov_finish<R>(c, Nw, k, s, lz));
     c->launches += 2 + 2 * k + 2;
   }
   // psi_new = B acc (Split-2); B B acc = e^{-tau h''} acc (Split-1); acc itself
@@ -1293,7 +1297,7 @@ afqmc_status afqmc_step(afqmc_ctx* c, const afqmc_walkers* w, const double* fiel
   if (p->propagator == AFQMC_TAYLORPROP && p->expm != AFQMC_EXPM_TAYLOR) return AFQMC_ENOTSUP;
   if (p->expm == AFQMC_EXPM_TAYLOR || p->expm == AFQMC_EXPM_CHEBYSHEV) {
     if (p->order < 0 || p->order > 64) return AFQMC_ENOTSUP;
-  } else if (p->expm == AFQMC_EXPM_KRYLOV) {
+  } else if (p->expm == AFQMC_EXPM_KRYLOV || p->expm == AFQMC_EXPM_LANCZOS) {
     if (p->order < 1 || p->order > 32) return AFQMC_ENOTSUP;
   } else if (p->expm == AFQMC_EXPM_BLOCK_KRYLOV) {
     if (p->order < 1 || p->order > 16 || !bk_fits(c, p->order)) return AFQMC_ENOTSUP;
@@ -1305,7 +1309,8 @@ afqmc_status afqmc_step(afqmc_ctx* c, const afqmc_walkers* w, const double* fiel
     st = afqmc_set_tau(c, p->tau);
     if (st != AFQMC_OK) return st;
   }
-  const bool kry = p->expm == AFQMC_EXPM_KRYLOV || p->expm == AFQMC_EXPM_BLOCK_KRYLOV;
+  const bool kry = p->expm == AFQMC_EXPM_KRYLOV || p->expm == AFQMC_EXPM_LANCZOS ||
+                   p->expm == AFQMC_EXPM_BLOCK_KRYLOV;
   const int k = kry ? (p->order < c->N ? p->order : c->N) : 0;
   st = ws_ensure(c, w->n_walkers, k);
   if (st != AFQMC_OK) return st;
@@ -1574,7 +1579,7 @@ static afqmc_status step_checks(afqmc_ctx* c, const afqmc_walkers* w, const doub
   if (p->propagator == AFQMC_TAYLORPROP && p->expm != AFQMC_EXPM_TAYLOR) return AFQMC_ENOTSUP;
   if (p->expm == AFQMC_EXPM_TAYLOR || p->expm == AFQMC_EXPM_CHEBYSHEV) {
     if (p->order < 0 || p->order > 64) return AFQMC_ENOTSUP;
-  } else if (p->expm == AFQMC_EXPM_KRYLOV) {
+  } else if (p->expm == AFQMC_EXPM_KRYLOV || p->expm == AFQMC_EXPM_LANCZOS) {
     if (p->order < 1 || p->order > 32) return AFQMC_ENOTSUP;
   } else if (p->expm == AFQMC_EXPM_BLOCK_KRYLOV) {
     if (p->order < 1 || p->order > 16 || !bk_fits(c, p->order)) return AFQMC_ENOTSUP;
@@ -1599,7 +1604,7 @@ afqmc_status afqmc_batch_step(afqmc_batch* b, const afqmc_walkers* ws, const dou
     afqmc_ctx* c = b->ctxs[i];
     afqmc_status st = step_checks(c, &ws[i], fields[i], &p[i]);
     if (st != AFQMC_OK) return st;
-    if (p[i].expm == AFQMC_EXPM_KRYLOV || p[i].expm == AFQMC_EXPM_BLOCK_KRYLOV)
+    if (p[i].expm == AFQMC_EXPM_KRYLOV || p[i].expm == AFQMC_EXPM_LANCZOS || p[i].expm == AFQMC_EXPM_BLOCK_KRYLOV)
       q[i].order = p[i].order < c->N ? p[i].order : c->N;
     double* el = e_loc ? e_loc[i] : nullptr;
     double* em = e_mix ? e_mix[i] : nullptr;
@@ -1622,7 +1627,8 @@ afqmc_status afqmc_batch_step(afqmc_batch* b, const afqmc_walkers* ws, const dou
         afqmc_status st = afqmc_set_tau(c, p[i].tau);
         if (st != AFQMC_OK) return st;
       }
-      const bool kry = q[i].expm == AFQMC_EXPM_KRYLOV || q[i].expm == AFQMC_EXPM_BLOCK_KRYLOV;
+      const bool kry = q[i].expm == AFQMC_EXPM_KRYLOV || q[i].expm == AFQMC_EXPM_LANCZOS ||
+                       q[i].expm == AFQMC_EXPM_BLOCK_KRYLOV;
       afqmc_status st = ws_ensure(c, ws[i].n_walkers, kry ? q[i].order : 0);
       if (st != AFQMC_OK) return st;
       if (q[i].expm == AFQMC_EXPM_BLOCK_KRYLOV)

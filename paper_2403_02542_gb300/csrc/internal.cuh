@@ -97,6 +97,7 @@ struct Workspace {
   void* basis = nullptr;     // [kmax][Nw][nc][N]
   double* hess = nullptr;    // [Nw*nc][kmax][kmax][2]
   double* beta = nullptr;    // [Nw*nc]
+  double2* cbeta = nullptr;  // [Nw*nc] (psi^T psi)^{1/2} of the Lanczos action
   double* scal = nullptr;    // [Nw][16] per-walker scalars (see SC_*)
   double* logdet = nullptr;  // [Nw][2 spins][2]
   double* epart = nullptr;   // [Nw][G][2 spins][4]  (tr re, tr im, exch re, exch im)
@@ -201,6 +202,7 @@ namespace afq {
 struct TgPlan {
   bool ok = false;
   int Kp = 0, m_cap = 0;
+  int Nq = 0;  // N rounded up to a multiple of 8: q stride of the column space and Im offset of the planes
   size_t Np = 0;
   void* l_hi = nullptr;  // [Np][Kp] bf16: L^T split hi/lo
   void* l_lo = nullptr;
@@ -334,8 +336,16 @@ cudaError_t launch_krylov_init(const afqmc_ctx* c, int Nw, cudaStream_t s);
 // Arnoldi step `it` with the product A b_it in wv (NULL: ws.term0)
 template <typename R>
 cudaError_t launch_krylov_orth(const afqmc_ctx* c, int Nw, int it, int k, cudaStream_t s, const void* wv = nullptr);
+// small exponential y = beta e^{H} e_1 (beta = cbeta for the Lanczos action)
+// and the combination acc = sum_i y_i b_i
 template <typename R>
-cudaError_t launch_krylov_finish(const afqmc_ctx* c, int Nw, int k, cudaStream_t s);
+cudaError_t launch_krylov_finish(const afqmc_ctx* c, int Nw, int k, cudaStream_t s, bool lanczos = false);
+// complex-symmetric Lanczos: v_0 = psi_b / (psi_b^T psi_b)^{1/2}, then per
+// step the three-term recurrence on the product A v_it (wv, NULL: ws.term0)
+template <typename R>
+cudaError_t launch_lanczos_init(const afqmc_ctx* c, int Nw, cudaStream_t s);
+template <typename R>
+cudaError_t launch_lanczos_step(const afqmc_ctx* c, int Nw, int it, int k, cudaStream_t s, const void* wv = nullptr);
 template <typename R>
 cudaError_t launch_weights(const afqmc_ctx* c, const afqmc_walkers* w, double tau, double e0,
                            cudaStream_t s);

@@ -3,7 +3,10 @@
 // A_w = i sqrt(tau) sum_g c_wg L_g (Eq. heffTOT) for every walker is one dense
 // contraction over g with a real right operand:
 //   rows    m = 2w + part : X[2w] = -sqrt(tau) Im c_w,  X[2w+1] = sqrt(tau) Re c_w
-//   columns e = (p, q)    : L^T, the Cholesky vectors with g contiguous
+//   columns e = p Nq + q  : L^T, the Cholesky vectors with g contiguous; q
+//                           runs to Nq = N rounded up to a multiple of 8 (the
+//                           rows q >= N are zero), so that every run of eight
+//                           columns lies in one row p of A_w
 //   K       g
 // so D[2w][e] = Re A_w[e] and D[2w+1][e] = Im A_w[e].  Both operands are split
 // x = hi + lo into bfloat16 pairs and D = X_hi L_hi + X_hi L_lo + X_lo L_hi is
@@ -30,7 +33,9 @@
 //
 // When the products A_w V of the exponential also run on the tensor cores,
 // the field epilogue writes A_w instead as bfloat16 hi/lo planes
-// A'[w][p][k] = [Re A_w[p][q] | Im A_w[p][q]] (k = q, N + q), and
+// A'[w][p][k] = [Re A_w[p][q] | Im A_w[p][q]] (k = q, Nq + q; the columns
+// N..Nq of each half are the zero accumulators of the zero rows of L^T, stored
+// with the rest in 16-byte runs), and
 //   (A V)_re = A' [Re V; -Im V],  (A V)_im = A' [Im V; Re V]
 // is one real contraction per walker with K = 2N and 2 nc output columns
 // (av_tc_kernel: rows p in tiles of 128, the whole V' of the walker as the
@@ -56,11 +61,11 @@ constexpr uint32_t TG_STAGE_BYTES = 2 * TG_A_BYTES + 2 * TG_B_BYTES;
 
 struct TgArgs {
   int mt, nt, KC, n_items;
-  int M, Nn;           // valid rows (2 Nw; mode 2: N) and columns (N^2; mode 2: 2 Nw nc)
-  float* out;          // mode 0: A as interleaved complex [Nw][Nn]
+  int M, Nn;           // valid rows (2 Nw; mode 2: N) and columns (N Nq; mode 2: 2 Nw nc)
+  float* out;          // mode 0: A as interleaved complex [Nw][N][N]
   __nv_bfloat16* a_hi;  // mode 1: A' planes [Nw * N][KA]
   __nv_bfloat16* a_lo;
-  int N, KA;
+  int N, KA, Nq;
   const float2* hs_in;  // mode 2: walkers in [Nw nc][N] complex64
   float2* hs_out;       // mode 2: walkers out, same layout
   int* err;
@@ -193,7 +198,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
       const int m = mt * TG_BM + r;
       const int w = m >> 1;
       const bool row_ok = m < p.M;
-      float* orow = MODE == 2 ? nullptr : p.out + (size_t)w * p.Nn * 2;
+      float* orow = MODE == 2 ? nullptr : p.out + (size_t)w * p.N * p.N * 2;
       const int e_base = nt * TG_BN;
       if constexpr (MODE == 2) {
         // row m = p; columns (Re, Im) of 128 orbitals, in chunks of 32
@@ -228,32 +233,22 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
         tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * TG_BN + c0), v);
         tmem_wait_ld();
         if constexpr (MODE == 1) {
-          // row 2w + part -> plane column part * N + q of row p of walker w
+          // row 2w + part -> plane columns part * Nq + q .. q + 7 of row p of
+          // walker w (e0 and Nq are multiples of 8: one aligned 16-byte run)
           const int e0 = e_base + c0;
           if (!row_ok || e0 >= p.Nn) continue;
           const int part = m & 1;
-          if ((p.N & 7) == 0 && e0 + 8 <= p.Nn) {
-            const int pr = e0 / p.N, q = e0 - pr * p.N;
-            const size_t o = ((size_t)w * p.N + pr) * p.KA + (size_t)part * p.N + q;
-            __align__(16) __nv_bfloat16 h[8], l[8];
+          const int pr = e0 / p.Nq, q = e0 - pr * p.Nq;
+          const size_t o = ((size_t)w * p.N + pr) * p.KA + (size_t)part * p.Nq + q;
+          __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
-            for (int t = 0; t < 8; ++t) {
-              const float x = __uint_as_float(v[t]);
-              h[t] = __float2bfloat16(x);
-              l[t] = __float2bfloat16(x - __bfloat162float(h[t]));
-            }
-            *reinterpret_cast<uint4*>(p.a_hi + o) = *reinterpret_cast<const uint4*>(h);
-            *reinterpret_cast<uint4*>(p.a_lo + o) = *reinterpret_cast<const uint4*>(l);
-          } else {
-            for (int t = 0; t < 8 && e0 + t < p.Nn; ++t) {
-              const int e = e0 + t, pr = e / p.N, q = e - pr * p.N;
-              const size_t o = ((size_t)w * p.N + pr) * p.KA + (size_t)part * p.N + q;
-              const float x = __uint_as_float(v[t]);
-              const __nv_bfloat16 h = __float2bfloat16(x);
-              p.a_hi[o] = h;
-              p.a_lo[o] = __float2bfloat16(x - __bfloat162float(h));
-            }
+          for (int t = 0; t < 8; ++t) {
+            const float x = __uint_as_float(v[t]);
+            h[t] = __float2bfloat16(x);
+            l[t] = __float2bfloat16(x - __bfloat162float(h[t]));
           }
+          *reinterpret_cast<uint4*>(p.a_hi + o) = *reinterpret_cast<const uint4*>(h);
+          *reinterpret_cast<uint4*>(p.a_lo + o) = *reinterpret_cast<const uint4*>(l);
         } else {
           // even lane (row 2w = Re A) keeps columns c0..c0+3, odd lane (Im A) c0+4..c0+7
           float mine[4], other[4];
@@ -265,12 +260,14 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
             other[t] = recv;
           }
           if (row_ok) {
+            // four columns in one row p (e0 and Nq are multiples of 4)
             const int e0 = e_base + c0 + (odd ? 4 : 0);
+            const int pr = e0 / p.Nq, q0 = e0 - pr * p.Nq;
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-              if (e0 + t < p.Nn) {
+              if (pr < p.N && q0 + t < p.N) {
                 const float re = odd ? other[t] : mine[t], im = odd ? mine[t] : other[t];
-                *reinterpret_cast<float2*>(orow + (size_t)(e0 + t) * 2) = make_float2(re, im);
+                *reinterpret_cast<float2*>(orow + ((size_t)pr * p.N + q0 + t) * 2) = make_float2(re, im);
               }
             }
           }
@@ -466,10 +463,11 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
 }
 
 // V'_w from V (complex64 [w][j][q], walker stride vs): rows j < nc hold
-// [Re v_j | -Im v_j], rows nc + j hold [Im v_j | Re v_j]; rows >= 2 nc and
-// columns >= 2N are zero.  Split into hi/lo.
+// [Re v_j | -Im v_j], rows nc + j hold [Im v_j | Re v_j] (the second half
+// from column Nq); rows >= 2 nc, columns q >= N of each half and columns
+// >= 2 Nq are zero.  Split into hi/lo.
 __global__ void build_v_kernel(const float2* __restrict__ V, long long vs, __nv_bfloat16* __restrict__ hi,
-                               __nv_bfloat16* __restrict__ lo, int Nw, int N, int nc, int NBp, int KA) {
+                               __nv_bfloat16* __restrict__ lo, int Nw, int N, int Nq, int nc, int NBp, int KA) {
   const size_t total = (size_t)Nw * NBp * KA;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(e % KA);
@@ -477,12 +475,13 @@ __global__ void build_v_kernel(const float2* __restrict__ V, long long vs, __nv_
     const int row = (int)(rw % NBp);
     const size_t w = rw / NBp;
     float x = 0.f;
-    if (row < 2 * nc && k < 2 * N) {
+    const bool first = k < Nq;
+    const int q = first ? k : k - Nq;
+    if (row < 2 * nc && k < 2 * Nq && q < N) {
       const int j = row < nc ? row : row - nc;
-      const int q = k < N ? k : k - N;
       const float2 v = V[w * vs + (size_t)j * N + q];
-      if (row < nc) x = k < N ? v.x : -v.y;
-      else x = k < N ? v.y : v.x;
+      if (row < nc) x = first ? v.x : -v.y;
+      else x = first ? v.y : v.x;
     }
     const __nv_bfloat16 h = __float2bfloat16(x);
     hi[e] = h;
@@ -516,16 +515,19 @@ __global__ void __launch_bounds__(256) normA_planes_kernel(const __nv_bfloat16* 
   }
 }
 
-// Right operand, once per context: LT[e][g] = L[g][e] split into hi/lo,
-// rows e < Np (zero beyond N^2), g < Kp (zero beyond G).
+// Right operand, once per context: LT[p Nq + q][g] = L[g][p][q] split into
+// hi/lo, rows up to Np (zero for q >= N and beyond N Nq), g < Kp (zero
+// beyond G).
 __global__ void build_lt_kernel(const double* __restrict__ L, __nv_bfloat16* __restrict__ hi,
-                                __nv_bfloat16* __restrict__ lo, size_t NN, int G, size_t Np, int Kp) {
-  const size_t total = Np * Kp;
+                                __nv_bfloat16* __restrict__ lo, int N, int Nq, int G, size_t Np, int Kp) {
+  const size_t total = Np * Kp, NN = (size_t)N * N;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int g = (int)(e % Kp);
     const size_t row = e / Kp;
+    const size_t pr = row / Nq;
+    const int q = (int)(row - pr * Nq);
     double x = 0.0;
-    if (g < G && row < NN) x = L[(size_t)g * NN + row];
+    if (g < G && pr < (size_t)N && q < N) x = L[(size_t)g * NN + pr * N + q];
     split_bf16(x, hi[e], lo[e]);
   }
 }
@@ -616,9 +618,10 @@ cudaError_t tc_field_setup(afqmc_ctx* c, cudaStream_t s) {
   P = TgPlan();
   if (c->prec != AFQMC_MIXED) return cudaSuccess;
   if (tg_smem_bytes() > (size_t)max_dyn_smem()) return cudaSuccess;
-  const size_t NN = (size_t)c->N * c->N;
+  P.Nq = ((c->N + 7) / 8) * 8;
+  const size_t NNq = (size_t)c->N * P.Nq;
   P.Kp = ((c->G + 63) / 64) * 64;
-  P.Np = ((NN + TG_BN - 1) / TG_BN) * TG_BN;
+  P.Np = ((NNq + TG_BN - 1) / TG_BN) * TG_BN;
   if (P.Np / TG_BN > (size_t)(1 << 20)) return cudaSuccess;
   cudaError_t e = dmalloc(&P.l_hi, P.Np * P.Kp * 2);
   if (e != cudaSuccess) return e;
@@ -629,7 +632,8 @@ cudaError_t tc_field_setup(afqmc_ctx* c, cudaStream_t s) {
   e = cudaMemsetAsync(P.err, 0, sizeof(int), s);
   if (e != cudaSuccess) return e;
   build_lt_kernel<<<grid_for(P.Np * P.Kp), 256, 0, s>>>(c->d_L, static_cast<__nv_bfloat16*>(P.l_hi),
-                                                        static_cast<__nv_bfloat16*>(P.l_lo), NN, c->G, P.Np, P.Kp);
+                                                        static_cast<__nv_bfloat16*>(P.l_lo), c->N, P.Nq, c->G, P.Np,
+                                                        P.Kp);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (!make_map(reinterpret_cast<CUtensorMap*>(P.map_l_hi), P.l_hi, P.Np, P.Kp, TG_BN) ||
@@ -659,7 +663,7 @@ cudaError_t tc_field_setup(afqmc_ctx* c, cudaStream_t s) {
       P.av_ok = true;
       P.NBp = nbp;
       P.S_av = S;
-      P.KA = ((2 * c->N + 63) / 64) * 64;
+      P.KA = ((2 * P.Nq + 63) / 64) * 64;
     }
   }
   return cudaSuccess;
@@ -710,7 +714,7 @@ cudaError_t tc_field_ws(afqmc_ctx* c) {
     if (e != cudaSuccess) return e;
     e = dmalloc(&P.a_lo, arows * P.KA * 2);
     if (e != cudaSuccess) return e;
-    // the K padding columns 2N..KA stay zero (the field epilogue writes k < 2N only)
+    // the K padding columns 2 Nq..KA stay zero (the field epilogue writes k < 2 Nq only)
     e = cudaMemset(P.a_hi, 0, arows * P.KA * 2);
     if (e != cudaSuccess) return e;
     e = cudaMemset(P.a_lo, 0, arows * P.KA * 2);
@@ -719,7 +723,8 @@ cudaError_t tc_field_ws(afqmc_ctx* c) {
     if (e != cudaSuccess) return e;
     e = dmalloc(&P.v_lo, vrows * P.KA * 2);
     if (e != cudaSuccess) return e;
-    // rows 2 nc..NBp and columns 2N..KA stay zero when the Arnoldi kernels fill the planes
+    // rows 2 nc..NBp and the columns q >= N of each half stay zero when the
+    // Krylov kernels fill the planes
     e = cudaMemset(P.v_hi, 0, vrows * P.KA * 2);
     if (e != cudaSuccess) return e;
     e = cudaMemset(P.v_lo, 0, vrows * P.KA * 2);
@@ -770,7 +775,8 @@ cudaError_t tc_field_launch(afqmc_ctx* c, int Nw, double sqrt_tau, cudaStream_t 
   a.KC = P.Kp / 64;
   a.n_items = a.mt * a.nt;
   a.M = 2 * Nw;
-  a.Nn = c->N * c->N;
+  a.Nn = c->N * P.Nq;
+  a.Nq = P.Nq;
   a.out = static_cast<float*>(c->ws.A);
   a.a_hi = static_cast<__nv_bfloat16*>(P.a_hi);
   a.a_lo = static_cast<__nv_bfloat16*>(P.a_lo);
@@ -804,7 +810,8 @@ cudaError_t tc_av_launch(afqmc_ctx* c, int Nw, const void* V, long long v_stride
     const size_t elems = (size_t)Nw * P.NBp * P.KA;
     build_v_kernel<<<grid_for(elems), 256, 0, s>>>(static_cast<const float2*>(V), v_stride,
                                                    static_cast<__nv_bfloat16*>(P.v_hi),
-                                                   static_cast<__nv_bfloat16*>(P.v_lo), Nw, c->N, c->nc, P.NBp, P.KA);
+                                                   static_cast<__nv_bfloat16*>(P.v_lo), Nw, c->N, P.Nq, c->nc, P.NBp,
+                                                   P.KA);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -610,25 +610,26 @@ __global__ void mgs_kernel(typename C2<R>::t* __restrict__ psi, int N, int na, i
 // col = w * nc + j and all column vectors are contiguous [N].
 // Basis vector element p of column col = (w, j) into the split right operand
 // of the tensor-core products A V: row j = [Re v | -Im v], row nc + j =
-// [Im v | Re v] of walker w (bf16 hi/lo planes, row length KA).
+// [Im v | Re v] of walker w, the second half from column Nq (bf16 hi/lo
+// planes, row length KA).
 struct VPlanes {
   __nv_bfloat16* hi = nullptr;
   __nv_bfloat16* lo = nullptr;
-  int NBp = 0, KA = 0;
+  int NBp = 0, KA = 0, Nq = 0;
 };
-__device__ __forceinline__ void put_vplanes(const VPlanes& P, int col, int nc, int N, int p, float vr, float vi) {
+__device__ __forceinline__ void put_vplanes(const VPlanes& P, int col, int nc, int p, float vr, float vi) {
   const int w = col / nc, j = col - (col / nc) * nc;
   const size_t ra = ((size_t)w * P.NBp + j) * P.KA, rb = ((size_t)w * P.NBp + nc + j) * P.KA;
   const __nv_bfloat16 hr = __float2bfloat16(vr), hi = __float2bfloat16(vi);
   const __nv_bfloat16 lr = __float2bfloat16(vr - __bfloat162float(hr)), li = __float2bfloat16(vi - __bfloat162float(hi));
   P.hi[ra + p] = hr;
   P.lo[ra + p] = lr;
-  P.hi[ra + N + p] = __hneg(hi);
-  P.lo[ra + N + p] = __hneg(li);
+  P.hi[ra + P.Nq + p] = __hneg(hi);
+  P.lo[ra + P.Nq + p] = __hneg(li);
   P.hi[rb + p] = hi;
   P.lo[rb + p] = li;
-  P.hi[rb + N + p] = hr;
-  P.lo[rb + N + p] = lr;
+  P.hi[rb + P.Nq + p] = hr;
+  P.lo[rb + P.Nq + p] = lr;
 }
 
 // Hessenberg storage: entry (column col, row i, column j) of H_k at
@@ -665,7 +666,7 @@ __global__ void krylov_init_kernel(const typename C2<R>::t* __restrict__ x, type
     v.x *= inv;
     v.y *= inv;
     v0[(size_t)col * N + p] = v;
-    if (vp.hi) put_vplanes(vp, col, nc, N, p, (float)v.x, (float)v.y);
+    if (vp.hi) put_vplanes(vp, col, nc, p, (float)v.x, (float)v.y);
   }
   if (lane == 0) beta[col] = (double)b;
 }
@@ -738,7 +739,7 @@ __global__ void krylov_orth_kernel(const typename C2<R>::t* __restrict__ wv, typ
         o.x = inv * wr[e];
         o.y = inv * wi[e];
         Vn[p] = o;
-        if (vp.hi) put_vplanes(vp, col, nc, N, p, (float)o.x, (float)o.y);
+        if (vp.hi) put_vplanes(vp, col, nc, p, (float)o.x, (float)o.y);
       }
     }
     if (lane == 0) {
@@ -750,7 +751,177 @@ __global__ void krylov_orth_kernel(const typename C2<R>::t* __restrict__ wv, typ
   }
 }
 
-// y = beta e^{H_k} e_1 in FP64 by sub-stepping: (e^{H/m})^m e_1, each factor
+// ---------------------------------------------------------------- Lanczos
+// Complex-symmetric Lanczos (the field matrix A is complex symmetric): the
+// three-term recurrence with the bilinear form u^T v.  The tridiagonal T_k
+// is kept in the Hessenberg storage above (diagonal alpha_j, both
+// off-diagonals beta_j; the rest stays zero), so the small exponential and
+// the combination are those of the Arnoldi action.  One warp per column, the
+// arithmetic in the walkers' precision; (psi^T psi)^{1/2} and every beta_j
+// is the principal complex square root.
+
+// principal square root of z = x + i y: with r = |z|, t = sqrt((r + |x|) / 2),
+// the root is (t, y / 2t) for x >= 0 and (|y| / 2t, +-t) otherwise (the sign
+// of y), from (a + i b)^2 = a^2 - b^2 + 2 i a b.  In the walkers' precision:
+// FP32 for complex64 walkers (an FP64 instruction occupies the narrow FP64
+// pipe for the whole warp, even on one lane), FP64 for complex128 ones.
+__device__ __forceinline__ void csqrt_principal(float x, float y, float& a, float& b) {
+  const float r = hypotf(x, y);
+  if (r == 0.f) { a = 0.f; b = 0.f; return; }
+  const float t = sqrtf(0.5f * (r + fabsf(x)));
+  if (x >= 0.f) { a = t; b = y / (2.f * t); }
+  else { a = fabsf(y) / (2.f * t); b = copysignf(t, y); }
+}
+__device__ __forceinline__ void csqrt_principal(double x, double y, double& a, double& b) {
+  const double r = hypot(x, y);
+  if (r == 0.0) { a = 0.0; b = 0.0; return; }
+  const double t = sqrt(0.5 * (r + fabs(x)));
+  if (x >= 0.0) { a = t; b = y / (2.0 * t); }
+  else { a = fabs(y) / (2.0 * t); b = copysign(t, y); }
+}
+
+template <typename R>
+__global__ void lanczos_init_kernel(const typename C2<R>::t* __restrict__ x, typename C2<R>::t* __restrict__ v0,
+                                    double* __restrict__ beta, double2* __restrict__ cbeta,
+                                    typename C2<R>::t* __restrict__ hess, size_t hs, int kmax, int N, int ncols,
+                                    int nc, VPlanes vp) {
+  typedef typename C2<R>::t cplx;
+  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (col >= ncols) return;
+  for (int e = lane; e < kmax * kmax; e += 32) {
+    cplx z;
+    z.x = R(0);
+    z.y = R(0);
+    hess[(size_t)e * hs + col] = z;
+  }
+  const cplx* X = x + (size_t)col * N;
+  R sr = R(0), si = R(0);  // x^T x
+  for (int p = lane; p < N; p += 32) {
+    const cplx v = X[p];
+    sr += v.x * v.x - v.y * v.y;
+    si += R(2) * v.x * v.y;
+  }
+  R br, bi;
+  csqrt_principal(warp_sum(sr), warp_sum(si), br, bi);
+  const R m2 = br * br + bi * bi;
+  const R ir = m2 > R(0) ? br / m2 : R(0), ii = m2 > R(0) ? -bi / m2 : R(0);
+  if (lane == 0) {
+    beta[col] = 1.0;
+    cbeta[col] = make_double2((double)br, (double)bi);
+  }
+  for (int p = lane; p < N; p += 32) {
+    const cplx v = X[p];
+    cplx o;
+    o.x = v.x * ir - v.y * ii;
+    o.y = v.x * ii + v.y * ir;
+    v0[(size_t)col * N + p] = o;
+    if (vp.hi) put_vplanes(vp, col, nc, p, (float)o.x, (float)o.y);
+  }
+}
+
+// Step `it`: w = A v_it is in `wv`; w -= beta_{it-1} v_{it-1};
+// alpha_it = v_it^T w; w -= alpha_it v_it; then (it + 1 < k)
+// beta_it = (w^T w)^{1/2} and v_{it+1} = w / beta_it, or zero when
+// |beta_it| <= 1e-12 ||A||_F (the space is exhausted; the later steps then
+// see zero vectors).
+template <typename R, int EPL>
+__global__ void lanczos_step_kernel(const typename C2<R>::t* __restrict__ wv, typename C2<R>::t* __restrict__ basis,
+                                    typename C2<R>::t* __restrict__ hess, size_t hs, const double* __restrict__ scal,
+                                    int N, int nc, int ncols, int it, int k, int kmax, size_t bstride, VPlanes vp) {
+  typedef typename C2<R>::t cplx;
+  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (col >= ncols) return;
+  const cplx* W = wv + (size_t)col * N;
+  R wr[EPL], wi[EPL];
+#pragma unroll
+  for (int e = 0; e < EPL; ++e) {
+    const int p = lane + 32 * e;
+    wr[e] = R(0);
+    wi[e] = R(0);
+    if (p < N) {
+      const cplx v = W[p];
+      wr[e] = v.x;
+      wi[e] = v.y;
+    }
+  }
+  if (it > 0) {
+    const cplx bp = hess[(size_t)(it * kmax + it - 1) * hs + col];
+    const cplx* Vp = basis + (it - 1) * bstride + (size_t)col * N;
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      const int p = lane + 32 * e;
+      if (p < N) {
+        const cplx v = Vp[p];
+        wr[e] -= bp.x * v.x - bp.y * v.y;
+        wi[e] -= bp.x * v.y + bp.y * v.x;
+      }
+    }
+  }
+  const cplx* V = basis + it * bstride + (size_t)col * N;
+  cplx vv[EPL];
+  R pr = R(0), pi = R(0);  // v_it^T w
+#pragma unroll
+  for (int e = 0; e < EPL; ++e) {
+    const int p = lane + 32 * e;
+    vv[e].x = R(0);
+    vv[e].y = R(0);
+    if (p < N) vv[e] = V[p];
+    pr += vv[e].x * wr[e] - vv[e].y * wi[e];
+    pi += vv[e].x * wi[e] + vv[e].y * wr[e];
+  }
+  const R ar = warp_sum(pr), ai = warp_sum(pi);
+#pragma unroll
+  for (int e = 0; e < EPL; ++e) {
+    wr[e] -= ar * vv[e].x - ai * vv[e].y;
+    wi[e] -= ar * vv[e].y + ai * vv[e].x;
+  }
+  if (lane == 0) {
+    cplx a;
+    a.x = ar;
+    a.y = ai;
+    hess[(size_t)(it * kmax + it) * hs + col] = a;
+  }
+  if (it + 1 < k) {
+    R sr = R(0), si = R(0);  // w^T w
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      sr += wr[e] * wr[e] - wi[e] * wi[e];
+      si += R(2) * wr[e] * wi[e];
+    }
+    R br, bi;
+    csqrt_principal(warp_sum(sr), warp_sum(si), br, bi);
+    const R thr = (R)(1e-12 * scal[(size_t)(col / nc) * SC_COUNT + SC_NORMA]);
+    const R m2 = br * br + bi * bi;
+    const bool brk = !(sqrt(m2) > thr);
+    if (brk) {
+      br = R(0);
+      bi = R(0);
+    }
+    const R ir = brk ? R(0) : br / m2, ii = brk ? R(0) : -bi / m2;
+    cplx* Vn = basis + (it + 1) * bstride + (size_t)col * N;
+#pragma unroll
+    for (int e = 0; e < EPL; ++e) {
+      const int p = lane + 32 * e;
+      if (p < N) {
+        cplx o;
+        o.x = wr[e] * ir - wi[e] * ii;
+        o.y = wr[e] * ii + wi[e] * ir;
+        Vn[p] = o;
+        if (vp.hi) put_vplanes(vp, col, nc, p, (float)o.x, (float)o.y);
+      }
+    }
+    if (lane == 0) {
+      cplx h;
+      h.x = br;
+      h.y = bi;
+      hess[(size_t)((it + 1) * kmax + it) * hs + col] = h;
+      hess[(size_t)(it * kmax + it + 1) * hs + col] = h;
+    }
+  }
+}
+
+// y = beta e^{H_k} e_1 (beta the real norm of the Arnoldi start, or the
+// complex (psi^T psi)^{1/2} of the Lanczos one) in FP64 by sub-stepping: (e^{H/m})^m e_1, each factor
 // a Taylor series on the vector summed until its terms fall below a relative
 // 1e-10 (complex64 walkers) or 1e-18 (FP64 walkers) of the sum; m chosen so
 // that ||H/m||_1 <= 4 (complex64; the partial sums cancel at most e^4 of FP64
@@ -760,7 +931,8 @@ __global__ void krylov_orth_kernel(const typename C2<R>::t* __restrict__ wv, typ
 // false (large k): H is read from global memory at every use instead.
 template <typename R, int KM, bool SM>
 __global__ void __launch_bounds__(64) krylov_expm_kernel(typename C2<R>::t* __restrict__ hess, size_t hs,
-                                                         const double* __restrict__ beta, int ncols, int k,
+                                                         const double* __restrict__ beta,
+                                                         const double2* __restrict__ cbeta, int ncols, int k,
                                                          int kmax) {
   extern __shared__ double2 hsm[];  // [npk][64]: packed rows i, columns j >= max(i - 1, 0)
   const int t = threadIdx.x;
@@ -840,13 +1012,88 @@ __global__ void __launch_bounds__(64) krylov_expm_kernel(typename C2<R>::t* __re
       if (tn <= tol * an) break;
     }
   }
-  const double b = beta[col];
+  const cd b = cbeta ? ld(cbeta + col) : mk(beta[col], 0.0);
 #pragma unroll
   for (int i = 0; i < KM; ++i)
     if (i < k) {
+      const cd yv = b * v[i];
       typename C2<R>::t y;
-      y.x = (R)(b * v[i].re);
-      y.y = (R)(b * v[i].im);
+      y.x = (R)yv.re;
+      y.y = (R)yv.im;
+      hess[(size_t)(i * kmax) * hs + col] = y;
+    }
+}
+
+// The same y = beta e^{T_k} e_1 for the symmetric tridiagonal T_k of the
+// Lanczos action (diagonal alpha_i at (i, i), off-diagonal beta_i at
+// (i + 1, i) = (i, i + 1)): three entries per row instead of the Hessenberg
+// row, held in registers; sub-steps, stopping rule and FP64 arithmetic as
+// above (the 1-norm of T_k is its infinity-norm).
+template <typename R, int KM>
+__global__ void __launch_bounds__(64) lanczos_expm_kernel(typename C2<R>::t* __restrict__ hess, size_t hs,
+                                                          const double2* __restrict__ cbeta, int ncols, int k,
+                                                          int kmax) {
+  const int col = blockIdx.x * 64 + threadIdx.x;
+  if (col >= ncols) return;
+  cd a[KM], b[KM];  // b[i] couples i and i + 1
+  double n1 = 0.0;
+#pragma unroll
+  for (int i = 0; i < KM; ++i) {
+    a[i] = mk(0.0, 0.0);
+    b[i] = mk(0.0, 0.0);
+    if (i < k) {
+      a[i] = ld(hess + (size_t)(i * kmax + i) * hs + col);
+      if (i + 1 < k) b[i] = ld(hess + (size_t)((i + 1) * kmax + i) * hs + col);
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < KM; ++i) {
+    double r = sqrt(abs2(a[i])) + sqrt(abs2(b[i]));
+    if (i > 0) r += sqrt(abs2(b[i - 1]));
+    n1 = fmax(n1, r);
+  }
+  const bool f32 = std::is_same<R, float>::value;
+  const double X = f32 ? 4.0 : 2.0;
+  int m = 1;
+  if (n1 < 1e30) m = (int)ceil(n1 / X);
+  if (m < 1) m = 1;
+  if (m > 4096) m = 4096;
+  const double sc = 1.0 / m;
+  const double tol = f32 ? 1e-20 : 1e-36;  // on squared norms
+  cd v[KM], tv[KM], u[KM];
+#pragma unroll
+  for (int i = 0; i < KM; ++i) v[i] = mk(i == 0 ? 1.0 : 0.0, 0.0);
+  for (int s = 0; s < m; ++s) {
+#pragma unroll
+    for (int i = 0; i < KM; ++i) tv[i] = v[i];
+    for (int d = 1; d <= 60; ++d) {
+      const double f = sc / d;
+#pragma unroll
+      for (int i = 0; i < KM; ++i) {
+        cd t = a[i] * tv[i];
+        if (i + 1 < KM) t = t + b[i] * tv[i + 1];
+        if (i > 0) t = t + b[i - 1] * tv[i - 1];
+        u[i] = f * t;
+      }
+      double tn = 0.0, an = 0.0;
+#pragma unroll
+      for (int i = 0; i < KM; ++i) {
+        tv[i] = u[i];
+        v[i] = v[i] + u[i];
+        tn += abs2(u[i]);
+        an += abs2(v[i]);
+      }
+      if (tn <= tol * an) break;
+    }
+  }
+  const cd bb = ld(cbeta + col);
+#pragma unroll
+  for (int i = 0; i < KM; ++i)
+    if (i < k) {
+      const cd yv = bb * v[i];
+      typename C2<R>::t y;
+      y.x = (R)yv.re;
+      y.y = (R)yv.im;
       hess[(size_t)(i * kmax) * hs + col] = y;
     }
 }
@@ -1034,6 +1281,7 @@ VPlanes vplanes(const afqmc_ctx* c) {
     v.lo = static_cast<__nv_bfloat16*>(c->tg.v_lo);
     v.NBp = c->tg.NBp;
     v.KA = c->tg.KA;
+    v.Nq = c->tg.Nq;
   }
   return v;
 }
@@ -1074,8 +1322,41 @@ cudaError_t launch_krylov_orth(const afqmc_ctx* c, int Nw, int it, int k, cudaSt
 // packed upper-Hessenberg entries of a k x k matrix
 inline int hess_packed(int k) { return k + k * (k + 1) / 2 - 1; }
 
+template <typename R>
+cudaError_t launch_lanczos_init(const afqmc_ctx* c, int Nw, cudaStream_t s) {
+  const int ncols = Nw * c->nc;
+  const size_t hs = (size_t)c->ws.n_walkers * c->nc;
+  lanczos_init_kernel<R><<<(ncols + 7) / 8, 256, 0, s>>>(
+      static_cast<const typename C2<R>::t*>(c->ws.psi_b), static_cast<typename C2<R>::t*>(c->ws.basis),
+      c->ws.beta, c->ws.cbeta, reinterpret_cast<typename C2<R>::t*>(c->ws.hess), hs, c->ws.kmax, c->N, ncols, c->nc,
+      vplanes<R>(c));
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_lanczos_step(const afqmc_ctx* c, int Nw, int it, int k, cudaStream_t s, const void* wv) {
+  const int ncols = Nw * c->nc;
+  const size_t bstride = (size_t)c->ws.n_walkers * c->nc * c->N;
+  const size_t hs = (size_t)c->ws.n_walkers * c->nc;
+  const typename C2<R>::t* W = static_cast<const typename C2<R>::t*>(wv ? wv : c->ws.term0);
+  typename C2<R>::t* Bs = static_cast<typename C2<R>::t*>(c->ws.basis);
+  typename C2<R>::t* H = reinterpret_cast<typename C2<R>::t*>(c->ws.hess);
+  const dim3 grid((ncols + 7) / 8);
+  const VPlanes vp = vplanes<R>(c);
+  if (c->N <= 128)
+    lanczos_step_kernel<R, 4><<<grid, 256, 0, s>>>(W, Bs, H, hs, c->ws.scal, c->N, c->nc, ncols, it, k, c->ws.kmax,
+                                                   bstride, vp);
+  else if (c->N <= 256)
+    lanczos_step_kernel<R, 8><<<grid, 256, 0, s>>>(W, Bs, H, hs, c->ws.scal, c->N, c->nc, ncols, it, k, c->ws.kmax,
+                                                   bstride, vp);
+  else
+    lanczos_step_kernel<R, 16><<<grid, 256, 0, s>>>(W, Bs, H, hs, c->ws.scal, c->N, c->nc, ncols, it, k,
+                                                    c->ws.kmax, bstride, vp);
+  return cudaGetLastError();
+}
+
 template <typename R, int KM>
-cudaError_t expm_launch(const afqmc_ctx* c, int ncols, int k, cudaStream_t s) {
+cudaError_t expm_launch(const afqmc_ctx* c, int ncols, int k, cudaStream_t s, const double2* cbeta) {
   typename C2<R>::t* H = reinterpret_cast<typename C2<R>::t*>(c->ws.hess);
   const size_t hs = (size_t)c->ws.n_walkers * c->nc;
   const size_t shm = (size_t)hess_packed(k) * 64 * sizeof(double2);
@@ -1085,22 +1366,37 @@ cudaError_t expm_launch(const afqmc_ctx* c, int ncols, int k, cudaStream_t s) {
       cudaError_t e = raise_smem_limit(krylov_expm_kernel<R, KM, true>);
       if (e != cudaSuccess) return e;
     }
-    krylov_expm_kernel<R, KM, true><<<grid, 64, shm, s>>>(H, hs, c->ws.beta, ncols, k, c->ws.kmax);
+    krylov_expm_kernel<R, KM, true><<<grid, 64, shm, s>>>(H, hs, c->ws.beta, cbeta, ncols, k, c->ws.kmax);
   } else {
-    krylov_expm_kernel<R, KM, false><<<grid, 64, 0, s>>>(H, hs, c->ws.beta, ncols, k, c->ws.kmax);
+    krylov_expm_kernel<R, KM, false><<<grid, 64, 0, s>>>(H, hs, c->ws.beta, cbeta, ncols, k, c->ws.kmax);
   }
   return cudaGetLastError();
 }
 
 template <typename R>
-cudaError_t launch_krylov_finish(const afqmc_ctx* c, int Nw, int k, cudaStream_t s) {
+cudaError_t launch_krylov_finish(const afqmc_ctx* c, int Nw, int k, cudaStream_t s, bool lanczos) {
   const int ncols = Nw * c->nc;
   const size_t bstride = (size_t)c->ws.n_walkers * c->nc * c->N;
   const size_t hs = (size_t)c->ws.n_walkers * c->nc;
-  cudaError_t e = k <= 8 ? expm_launch<R, 8>(c, ncols, k, s)
-                  : k <= 12 ? expm_launch<R, 12>(c, ncols, k, s)
-                  : k <= 16 ? expm_launch<R, 16>(c, ncols, k, s)
-                            : expm_launch<R, 32>(c, ncols, k, s);
+  cudaError_t e = cudaSuccess;
+  if (lanczos) {
+    typename C2<R>::t* H = reinterpret_cast<typename C2<R>::t*>(c->ws.hess);
+    const dim3 grid((ncols + 63) / 64);
+    if (k <= 8)
+      lanczos_expm_kernel<R, 8><<<grid, 64, 0, s>>>(H, hs, c->ws.cbeta, ncols, k, c->ws.kmax);
+    else if (k <= 12)
+      lanczos_expm_kernel<R, 12><<<grid, 64, 0, s>>>(H, hs, c->ws.cbeta, ncols, k, c->ws.kmax);
+    else if (k <= 16)
+      lanczos_expm_kernel<R, 16><<<grid, 64, 0, s>>>(H, hs, c->ws.cbeta, ncols, k, c->ws.kmax);
+    else
+      lanczos_expm_kernel<R, 32><<<grid, 64, 0, s>>>(H, hs, c->ws.cbeta, ncols, k, c->ws.kmax);
+    e = cudaGetLastError();
+  } else {
+    e = k <= 8 ? expm_launch<R, 8>(c, ncols, k, s, nullptr)
+        : k <= 12 ? expm_launch<R, 12>(c, ncols, k, s, nullptr)
+        : k <= 16 ? expm_launch<R, 16>(c, ncols, k, s, nullptr)
+                  : expm_launch<R, 32>(c, ncols, k, s, nullptr);
+  }
   if (e != cudaSuccess) return e;
   krylov_combine_kernel<R><<<(ncols + 7) / 8, 256, 0, s>>>(
       reinterpret_cast<const typename C2<R>::t*>(c->ws.hess), hs,
@@ -1147,7 +1443,9 @@ cudaError_t launch_cn_solve(const afqmc_ctx* c, int Nw, void* X, void* Y, cudaSt
   template cudaError_t launch_mgs<R>(const afqmc_ctx*, int, void*, const uint8_t*, double*, cudaStream_t);  \
   template cudaError_t launch_krylov_init<R>(const afqmc_ctx*, int, cudaStream_t);                         \
   template cudaError_t launch_krylov_orth<R>(const afqmc_ctx*, int, int, int, cudaStream_t, const void*);  \
-  template cudaError_t launch_krylov_finish<R>(const afqmc_ctx*, int, int, cudaStream_t);                  \
+  template cudaError_t launch_krylov_finish<R>(const afqmc_ctx*, int, int, cudaStream_t, bool);                \
+  template cudaError_t launch_lanczos_init<R>(const afqmc_ctx*, int, cudaStream_t);                               \
+  template cudaError_t launch_lanczos_step<R>(const afqmc_ctx*, int, int, int, cudaStream_t, const void*);      \
   template cudaError_t launch_init_walkers<R>(const afqmc_ctx*, const afqmc_walkers*, cudaStream_t);
 AFQ_INST(double)
 AFQ_INST(float)

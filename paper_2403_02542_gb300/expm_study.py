@@ -19,7 +19,7 @@ and compares their energies.
 from __future__ import annotations
 
 # largest order each action accepts (afqmc_step)
-K_MAX = {"taylor": 64, "chebyshev": 64, "krylov": 32, "bkrylov": 16}
+K_MAX = {"taylor": 64, "chebyshev": 64, "krylov": 32, "bkrylov": 16, "lanczos": 32}
 REFERENCE = ("taylor", 64)
 
 
@@ -58,7 +58,7 @@ def k_min(ctx, nw: int, n_steps: int, fields, tau: float, e0: float, expm: str, 
 
 
 def sweep(ctx, nw: int, n_steps: int, fields_for_tau, taus, e0: float,
-          methods=("taylor", "chebyshev", "krylov", "bkrylov"), eps: float = 1e-5,
+          methods=("taylor", "chebyshev", "krylov", "bkrylov", "lanczos"), eps: float = 1e-5,
           k_max: int | None = None) -> dict:
     """k_min of every method at every time step (the rows of Fig. 1 for one
     system).  fields_for_tau(tau) returns the fields callable of that tau's runs;

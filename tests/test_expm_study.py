@@ -28,7 +28,7 @@ def test_order_limits_match_the_header():
     hdr = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
                             "include", "afqmc.h")).read()
     for name, macro in (("taylor", "TAYLOR"), ("krylov", "KRYLOV"), ("chebyshev", "CHEBYSHEV"),
-                        ("bkrylov", "BLOCK_KRYLOV")):
+                        ("bkrylov", "BLOCK_KRYLOV"), ("lanczos", "LANCZOS")):
         m = re.search(r"AFQMC_EXPM_" + macro + r" \(order = [^)]*?(\d+) <= k <= (\d+)", hdr)
         assert m is not None, name
         assert S.K_MAX[name] == int(m.group(2)), name
