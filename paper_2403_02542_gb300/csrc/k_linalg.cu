@@ -249,7 +249,8 @@ __global__ void __launch_bounds__(256) overlap_kernel(const typename C2<R>::t* _
 //   O = trial_s^T Psi_s in FP32, p in tiles of 32 staged through shared
 //     memory (each thread owns 2 x 5 blocks of O in registers);
 //   the LU of O with partial pivoting and log det O in FP64 (rows stay in
-//     place; each warp owns rows i = warp (mod 8), its lanes the columns j);
+//     place; the trailing update of each step runs over the flat range of
+//     remaining rows x columns);
 //   O^{-1} in FP32 from the rounded factors, one thread per column
 //     (P O = L U, so column j of O^{-1} is U^{-1} L^{-1} P e_j);
 //   Theta = Psi O^{-1}: threads over (p, block of OV_JB columns j), the
@@ -288,10 +289,10 @@ __global__ void __launch_bounds__(256) overlap_c64_kernel(const float2* __restri
   float* Ts = reinterpret_cast<float*>(Rg);                // [OV_TP][n] (before the LU)
   float2* Ps = reinterpret_cast<float2*>(Ts + OV_TP * n);  // [OV_TP][n] (before the LU)
   float2* Inv = Rg;                                        // [n][n] O^{-1} (after the factors moved)
-  __shared__ int perm[128], rank[128], cand_r[8];
-  __shared__ double cand_v[8];
-  __shared__ int s_swaps, s_sing;
-  __shared__ cd s_rpk;
+  __shared__ int perm[128], rank[128], rem[128];
+  __shared__ double cand[128];
+  __shared__ cd lik[128];
+  __shared__ int s_swaps, s_sing, s_nrem;
   const float2* P = psi + ((size_t)w * nc + off) * N;
   const float* T = trial_f + (size_t)off * N;
   const int nn = n * n;
@@ -347,86 +348,82 @@ __global__ void __launch_bounds__(256) overlap_c64_kernel(const float2* __restri
         }
     }
   }
-  // rank[i]: the step at which row i became the pivot (n: not yet)
-  if (tid < n) rank[tid] = n;
-  if (tid == 0) s_sing = 0;
+  // rank[i]: the step at which row i became the pivot (n: not yet); rem[0..nrem)
+  // the rows not chosen yet (in no particular order)
+  for (int i = tid; i < n; i += 256) {
+    rank[i] = n;
+    rem[i] = i;
+    cand[i] = abs2(LU[i * n]);
+  }
+  if (tid == 0) {
+    s_sing = 0;
+    s_nrem = n;
+  }
   __syncthreads();
 
   // LU with partial pivoting in FP64, rows left in place (implicit pivoting):
   // at step k the pivot is the largest |LU[i][k]| among the rows not chosen
-  // yet (ties keep the smaller row); every other remaining row i gets
-  // l_ik = LU[i][k] / LU[piv][k] and LU[i][j] -= l_ik LU[piv][j] for j > k.
-  // perm[k] = piv, so row k of P O is row perm[k] of O.  Each warp owns rows
-  // i = warp (mod 8), its lanes the columns; the complex update is four FMAs.
-  // The pivot search of step k + 1 rides on the update of step k: every warp
-  // leaves the best candidate among its rows (column k + 1 after the update)
-  // and one thread picks among the eight.
-  auto pick = [&](int kk) {  // thread 0: pivot of step kk from the warps' candidates
-    int piv = n;
-    double best = -1.0;
-    for (int q = 0; q < 8; ++q)
-      if (cand_r[q] < n && (cand_v[q] > best || (cand_v[q] == best && cand_r[q] < piv))) {
-        best = cand_v[q];
-        piv = cand_r[q];
-      }
-    perm[kk] = piv;
-    rank[piv] = kk;
-    if (!(best > 0.0)) s_sing = 1;
-    s_rpk = crecip(LU[piv * n + kk]);
-  };
-  auto warp_best = [&](double v, int row) {  // reduce (value, row) over the warp, ties to the smaller row
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
-      const int orow = __shfl_xor_sync(0xffffffffu, row, o);
-      if (ov > v || (ov == v && orow < row)) { v = ov; row = orow; }
-    }
-    if (lane == 0) { cand_v[wid] = v; cand_r[wid] = row; }
-  };
-  {  // candidates of step 0: every row
-    double v = -1.0;
-    int row = n;
-    for (int i = tid; i < n; i += 256) {
-      const double a2 = abs2(LU[i * n]);
-      const double vv = a2 >= 0.0 ? a2 : 0.0;  // NaN counts as a zero pivot (the walker is then singular)
-      if (vv > v || (vv == v && i < row)) { v = vv; row = i; }
-    }
-    warp_best(v, row);
-  }
-  __syncthreads();
-  if (tid == 0) pick(0);
-  __syncthreads();
+  // yet (ties keep the smaller row; NaN counts as zero, and a zero pivot marks
+  // the walker singular); every other remaining row i gets
+  // l_ik = LU[i][k] / LU[piv][k] (stored in place of LU[i][k]) and
+  // LU[i][j] -= l_ik LU[piv][j] for j > k.  perm[k] = piv, so row k of P O is
+  // row perm[k] of O.  Warp 0 picks the pivot from the candidates |LU[i][k]|^2
+  // left by the previous update, drops it from the list of remaining rows and
+  // forms the multipliers (one per row, lanes over rows); then all threads run
+  // the trailing update over the flat range (remaining row, column j > k), so
+  // that the FP64 warp instructions run with full warps (the FP64 pipe costs
+  // the same for a partly active warp), and leave the candidates of step k + 1.
   for (int k = 0; k < n; ++k) {
-    const int piv = perm[k];
-    const cd rpk = s_rpk;
-    const cd* up = LU + piv * n;
-    double cv = -1.0;  // this lane's best candidate for step k + 1
-    int crow = n;
-    for (int i = wid; i < n; i += 8) {
-      if (rank[i] <= k) continue;  // chosen rows (the pivot included) are final
-      cd* row = LU + i * n;
-      const cd lik = row[k] * rpk;
-      for (int j = k + 1 + lane; j < n; j += 32) {
-        const cd u = up[j];
-        cd v = row[j];
-        v.re = fma(-lik.re, u.re, fma(lik.im, u.im, v.re));
-        v.im = fma(-lik.re, u.im, fma(-lik.im, u.re, v.im));
-        row[j] = v;
-        if (j == k + 1) {
-          const double a2 = abs2(v);
-          const double vv = a2 >= 0.0 ? a2 : 0.0;
-          if (vv > cv || (vv == cv && i < crow)) { cv = vv; crow = i; }
-        }
+    if (wid == 0) {
+      const int nr = s_nrem;
+      double v = -1.0;
+      int row = n, slot = 0;
+      for (int r = lane; r < nr; r += 32) {
+        const double a2 = cand[r];
+        const double vv = a2 >= 0.0 ? a2 : 0.0;  // NaN counts as a zero pivot
+        const int i = rem[r];
+        if (vv > v || (vv == v && i < row)) { v = vv; row = i; slot = r; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+        const int orow = __shfl_xor_sync(0xffffffffu, row, o);
+        const int oslot = __shfl_xor_sync(0xffffffffu, slot, o);
+        if (ov > v || (ov == v && orow < row)) { v = ov; row = orow; slot = oslot; }
+      }
+      const int piv = row;
+      if (lane == 0) {
+        perm[k] = piv;
+        rank[piv] = k;
+        if (!(v > 0.0)) s_sing = 1;
+        rem[slot] = rem[nr - 1];  // drop the pivot from the remaining rows
+        s_nrem = nr - 1;
       }
       __syncwarp();
-      if (lane == 0) row[k] = lik;
+      const cd rpk = crecip(LU[piv * n + k]);
+      for (int r = lane; r < nr - 1; r += 32) {
+        const int i = rem[r];
+        const cd l = LU[i * n + k] * rpk;
+        LU[i * n + k] = l;
+        lik[r] = l;
+      }
     }
-    if (k + 1 < n) warp_best(cv, crow);
     __syncthreads();
-    if (k + 1 < n) {
-      if (tid == 0) pick(k + 1);
-      __syncthreads();
+    const int nr = s_nrem, cols = n - k - 1;
+    if (cols > 0) {
+      const cd* up = LU + perm[k] * n + k + 1;
+      for (int e = tid; e < nr * cols; e += 256) {
+        const int r = e / cols, jj = e - r * cols;
+        cd* x = LU + rem[r] * n + k + 1 + jj;
+        const cd l = lik[r], u = up[jj];
+        cd v = *x;
+        v.re = fma(-l.re, u.re, fma(l.im, u.im, v.re));
+        v.im = fma(-l.re, u.im, fma(-l.im, u.re, v.im));
+        *x = v;
+        if (jj == 0) cand[r] = abs2(v);
+      }
     }
+    __syncthreads();
   }
   // sign of the permutation: parity of n minus its number of cycles
   if (tid == 0) {
