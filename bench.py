@@ -210,6 +210,35 @@ def oracle_rate(system, n_walkers: int, n_steps: int, tau: float = TAU):
                        f"walker-by-walker Krylov, E_L every step), {dt:.1f} s"), per_step
 
 
+def batched_cpu_rate(system, n_walkers: int, n_steps: int, tau: float = TAU):
+    """Time the batched FP64 CPU variant of the step (oracle/batched_cpu.py:
+    the same arithmetic as the oracle, batched over walkers and orbital
+    columns, half-rotated Cholesky contractions) on a bounded sample of the
+    workload: n_walkers walkers for n_steps steps with E_L every step."""
+    import torch
+
+    from oracle import afqmc_ref as R
+    from oracle.batched_cpu import BatchedStep
+    from paper_2403_02542_gb300.inputs import make_fields
+
+    ham = R.make_hamiltonian(system.h1, system.L, system.trial, system.na, system.nb)
+    bs = BatchedStep(ham, tau)
+    psi, _, W = R.init_walkers(ham, n_walkers)
+    lo = bs.log_overlap(psi)
+    e0 = float(bs.local_energy(psi[:1]).real[0])
+    t0 = time.perf_counter()
+    for k in range(n_steps):
+        x = make_fields(99, k, n_walkers, ham.G)
+        psi, lo, W = bs.step(psi, lo, W, x, e0, k=KDIM, reortho=(k + 1) % REORTHO == 0)
+        El = bs.local_energy(psi)
+        R.mixed_energy(W, R.energy_window(El, e0, tau, ham.na + ham.nb))
+    dt = time.perf_counter() - t0
+    return dict(value=n_walkers * n_steps / dt, unit="walker-steps/s", cores=torch.get_num_threads(),
+                host_cores=os.cpu_count(), cpu_model=cpu_model(), kind="batched (FP64, batched over walkers)",
+                sample=f"{n_walkers} walkers x {n_steps} steps of the same workload (FP64, batched over walkers "
+                       f"and orbital columns, half-rotated Cholesky contractions, E_L every step), {dt:.1f} s")
+
+
 def config_dict(precision: str, world: int, nw: int):
     wl = WORKLOAD if nw == NW else WORKLOAD.replace(f"{NW} walkers/GPU", f"{nw} walkers/GPU (reduced)")
     return {"workload": wl, "walkers_per_gpu": nw, "N": 300, "na": 50, "nb": 50, "G": 1500,
@@ -1085,6 +1114,10 @@ def run_ours(args):
     cpu = None
     if world == 1 and not args.no_cpu_baseline and not args.only_headline:
         cpu, _ = oracle_rate(system, args.cpu_sample_walkers, 2)
+        try:
+            cpu["batched"] = batched_cpu_rate(system, 16, 2)
+        except Exception as exc:  # noqa: BLE001 - the second CPU number must not end the bench line
+            cpu["batched"] = {"error": f"{type(exc).__name__}: {exc}"}
     line = {
         "metric": METRIC, "value": value, "unit": "walker-steps/s", "n_gpus": world,
         "steps": K, "warmup": Wm, "ms_per_step": ms / K, "higher_is_better": True,
