@@ -763,6 +763,39 @@ def batched_rate(dev, steps=3, warmup=2):
     return out
 
 
+# DRAM bytes (read + write) of one exchange_tc_kernel launch on the headline
+# workload at 2048 walkers, from one single-pass ncu capture (command and
+# figures in profiles/exchange_tc_kernel_precision_2048walkers_dram.txt), valid
+# while the kernel's sources are the ones captured (sha256 below).
+EXCHANGE_TRAFFIC = {
+    "bytes": 2.38e9 + 198.56e6,
+    "walkers": 2048,
+    "source": "profiles/exchange_tc_kernel_precision_2048walkers_dram.txt",
+    "sha256": {"paper_2403_02542_gb300/csrc/k_exchange_tc.cu":
+               "a86febb3905dde7f6f0de6e3a9183fac1236d5cc746f6dcf0130592e22973d24",
+               "paper_2403_02542_gb300/csrc/tc_common.cuh":
+               "17add56279122795b8af511ad3d8faaf192d72127be1b26c8b888975eed98633"},
+}
+
+
+def exchange_traffic(precision: str, nw: int):
+    """(bytes per launch, note) of the captured exchange launch, or (None,
+    reason) when the workload or the kernel's sources differ from the capture."""
+    import hashlib
+    if precision != "mixed" or nw != EXCHANGE_TRAFFIC["walkers"]:
+        return None, "no capture for this precision / walker count"
+    root = os.path.dirname(os.path.abspath(__file__))
+    for rel, digest in EXCHANGE_TRAFFIC["sha256"].items():
+        try:
+            with open(os.path.join(root, rel), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != digest:
+                    return None, f"{rel} changed since the capture"
+        except OSError:
+            return None, f"{rel} not found"
+    return EXCHANGE_TRAFFIC["bytes"], ("ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch at full size, "
+                                       + EXCHANGE_TRAFFIC["source"])
+
+
 def exchange_flop_per_walker(system) -> int:
     """Algorithmic flops of the Coulomb + exchange contraction per walker:
     T_gs = Lh_gs Theta_s for every g and spin, G * 4 (na^2 + nb^2) * N real
@@ -1088,7 +1121,7 @@ def run_ours(args):
     kname = "exchange_kernel<double> (SIMT FP64)" if args.precision == "fp64" else "exchange_tc_kernel (tcgen05 BF16x3)"
     # DRAM bytes of one exchange launch (read + write) from ncu, when taken on
     # the current kernel (None otherwise)
-    traffic, traffic_note = None, None
+    traffic, traffic_note = exchange_traffic(args.precision, NW)
     total_split = sum(split.values())
     extras = {}
     if world == 1 and not args.only_headline:
@@ -1115,7 +1148,7 @@ def run_ours(args):
     if world == 1 and not args.no_cpu_baseline and not args.only_headline:
         cpu, _ = oracle_rate(system, args.cpu_sample_walkers, 2)
         try:
-            cpu["batched"] = batched_cpu_rate(system, 16, 2)
+            cpu["batched"] = batched_cpu_rate(system, 64, 3)
         except Exception as exc:  # noqa: BLE001 - the second CPU number must not end the bench line
             cpu["batched"] = {"error": f"{type(exc).__name__}: {exc}"}
     line = {
