@@ -85,12 +85,14 @@ enum {
  * AFQMC_MIXED: complex64 walkers.  On the tensor cores in split BF16 (three
  *              bf16 products per FP32 operand pair, FP32 accumulation): the
  *              field assembly A = i sqrt(tau) sum_g c_g L_g, the products A*V
- *              of the Taylor and Krylov actions and the Coulomb + exchange
- *              contraction of E_L (whose Coulomb traces also give the force
- *              bias of the next step when reuse_bias is set).  In FP32: the
- *              overlap products trial^T Psi, Theta's triangular solves, the
- *              half steps B*Psi, the force-bias contraction when it is
- *              recomputed, the Arnoldi inner products and norms and the
+ *              of the Taylor and Krylov actions, the Split-2 half steps
+ *              (Psi + (B - I) Psi, the identity part added in FP32) and the
+ *              Coulomb + exchange contraction of E_L (whose Coulomb traces
+ *              also give the force bias of the next step when reuse_bias is
+ *              set).  In FP32: the overlap products trial^T Psi, O^{-1} from
+ *              the rounded LU factors and Theta = Psi O^{-1}, the force-bias
+ *              contraction when it is recomputed, the Arnoldi and Lanczos
+ *              inner products, norms and square roots and the
  *              Gram-Schmidt projections of the re-orthonormalisation (the
  *              walkers are stored in FP32; every result that depends on them
  *              is invariant under Psi -> Psi M, so the orthonormality of Q
