@@ -249,7 +249,7 @@ static void ctx_free(afqmc_ctx* c) {
   tc_field_free(c);
   ws_free(c->ws);
   void* ptrs[] = {c->d_L, c->d_Lh,  c->d_trial, c->d_hhalf,    c->d_Lbar,     c->d_thT,
-                  c->d_B, c->f_L,   c->f_Lh,    c->f_B,        c->f_trial,    c->d_bias_key,
+                  c->d_B, c->f_L,   c->f_Lh,    c->f_B,        c->f_trial,    c->f_hh2,      c->d_bias_key,
                   c->d_bias_skip, c->d_hpp};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -279,6 +279,7 @@ static afqmc_status ctx_setup(afqmc_ctx* c, const double* h1, const double* L, c
     CK(dmalloc(&c->f_Lh, (size_t)G * nc * N * sizeof(float)));
     CK(dmalloc(&c->f_B, NN * sizeof(float)));
     CK(dmalloc(&c->f_trial, (size_t)nc * N * sizeof(float)));
+    CK(dmalloc(&c->f_hh2, (size_t)nc * N * sizeof(float2)));
   }
   CK(cudaMemcpyAsync(c->d_L, L, (size_t)G * NN * sizeof(double), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(c->d_trial, trial, (size_t)nc * N * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -292,6 +293,14 @@ static afqmc_status ctx_setup(afqmc_ctx* c, const double* h1, const double* L, c
       for (int q = 0; q < N; ++q) hh[(size_t)j * N + q] += t * h1[(size_t)p * N + q];
     }
   CK(cudaMemcpyAsync(c->d_hhalf, hh.data(), hh.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+  if (c->prec == AFQMC_MIXED) {  // h_half = hi + lo in FP32 for the complex64 one-body trace
+    std::vector<float2> hh2(hh.size());
+    for (size_t e = 0; e < hh.size(); ++e) {
+      const float hi = (float)hh[e];
+      hh2[e] = make_float2(hi, (float)(hh[e] - (double)hi));
+    }
+    CK(cudaMemcpy(c->f_hh2, hh2.data(), hh2.size() * sizeof(float2), cudaMemcpyHostToDevice));
+  }
 
   // Theta_T = trial (trial_s^T trial_s)^{-1} per spin (orthonormal trial: Theta_T = trial)
   std::vector<double> thT((size_t)nc * N, 0.0);

@@ -221,6 +221,7 @@ struct TgPlan {
   void* a_lo = nullptr;
   void* v_hi = nullptr;  // [cap * NBp][KA]: rows j [Re v_j | -Im v_j], rows nc + j [Im v_j | Re v_j]
   void* v_lo = nullptr;
+  void* nrm = nullptr;   // [m_cap][Np / 256] float: sum of squares of each field tile row (||A_w||_F)
   alignas(64) unsigned char map_a_hi[128];
   alignas(64) unsigned char map_a_lo[128];
   alignas(64) unsigned char map_v_hi[128];
@@ -265,6 +266,7 @@ struct afqmc_ctx {
   float* f_Lh = nullptr;
   float* f_B = nullptr;
   float* f_trial = nullptr;  // [nc][N]
+  float2* f_hh2 = nullptr;   // [nc][N] h_half split into FP32 (hi, lo)
   // eigendecomposition of h'' (host, for B at any tau)
   double* h_evals = nullptr;  // [N]
   double* h_evecs = nullptr;  // [N][N], column k is eigenvector k

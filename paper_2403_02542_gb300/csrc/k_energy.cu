@@ -192,6 +192,44 @@ __global__ void __launch_bounds__(256) onebody_kernel(const typename C2<R>::t* _
   }
 }
 
+// The same trace for complex64 walkers without an FP64 instruction per
+// element (the FP64 pipe is narrow): h_half = hi + lo in FP32, each product
+// hi * theta split error-free into its rounded value and the FMA residual,
+// the rounded values summed per thread by TwoSum (Knuth) into a
+// (sum, compensation) pair that also collects the residuals and the lo
+// products; the per-thread pairs are then added in FP64.  The intrinsics keep
+// the compiler from contracting the products into the sums.
+__device__ __forceinline__ void acc_prod(float a, float b, float& s, float& c) {
+  const float p = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -p);
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float te = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(te, pe));
+}
+__global__ void __launch_bounds__(256) onebody_c64_kernel(const float2* __restrict__ theta,
+                                                          const float2* __restrict__ hh2, double* scal,
+                                                          size_t per) {
+  __shared__ double sh[16];
+  const int w = blockIdx.x;
+  float sr = 0.f, cr = 0.f, si = 0.f, ci = 0.f;
+  for (size_t e = threadIdx.x; e < per; e += 256) {
+    const float2 th = theta[(size_t)w * per + e];
+    const float2 h = hh2[e];
+    acc_prod(h.x, th.x, sr, cr);
+    acc_prod(h.x, th.y, si, ci);
+    cr = __fmaf_rn(h.y, th.x, cr);
+    ci = __fmaf_rn(h.y, th.y, ci);
+  }
+  double v[2] = {(double)sr + (double)cr, (double)si + (double)ci};
+  block_sum<2>(v, sh);
+  if (threadIdx.x == 0) {
+    scal[(size_t)w * SC_COUNT + SC_E1_RE] = v[0];
+    scal[(size_t)w * SC_COUNT + SC_E1_IM] = v[1];
+  }
+}
+
 // Coulomb and exchange contractions per (walker, spin, g-chunk).
 // T[i][j] = sum_q Lh[g][off+i][q] Theta[w][off+j][q]; each thread owns up to
 // MAXE entries of T in registers; q is staged through shared memory in
@@ -511,8 +549,11 @@ cudaError_t launch_energy(afqmc_ctx* c, int Nw, const double* weight, double e0,
                           double* e_mix, cudaStream_t s, int* n_launch) {
   const size_t per = (size_t)c->nc * c->N;
   prof_mark(c, AFQMC_K_OTHER, true, s);
-  onebody_kernel<R><<<Nw, 256, 0, s>>>(static_cast<const typename C2<R>::t*>(c->ws.theta), c->d_hhalf,
-                                       c->ws.scal, per);
+  if constexpr (std::is_same<R, float>::value)
+    onebody_c64_kernel<<<Nw, 256, 0, s>>>(static_cast<const float2*>(c->ws.theta), c->f_hh2, c->ws.scal, per);
+  else
+    onebody_kernel<R><<<Nw, 256, 0, s>>>(static_cast<const typename C2<R>::t*>(c->ws.theta), c->d_hhalf,
+                                         c->ws.scal, per);
   cudaError_t e = cudaGetLastError();
   prof_mark(c, AFQMC_K_OTHER, false, s);
   if (e != cudaSuccess) return e;

@@ -68,6 +68,7 @@ struct TgArgs {
   int N, KA, Nq;
   const float2* hs_in;  // mode 2: walkers in [Nw nc][N] complex64
   float2* hs_out;       // mode 2: walkers out, same layout
+  float* nrm;           // mode 1: [rows][nt] sum of squares of each tile row (NULL: none)
   int* err;
 };
 
@@ -228,6 +229,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
           }
         }
       }
+      float ss = 0.f;  // mode 1: sum of squares of this row of the tile
       for (int c0 = 0; MODE != 2 && c0 < TG_BN; c0 += 8) {
         uint32_t v[8];
         tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * TG_BN + c0), v);
@@ -246,6 +248,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
             const float x = __uint_as_float(v[t]);
             h[t] = __float2bfloat16(x);
             l[t] = __float2bfloat16(x - __bfloat162float(h[t]));
+            ss = fmaf(x, x, ss);
           }
           *reinterpret_cast<uint4*>(p.a_hi + o) = *reinterpret_cast<const uint4*>(h);
           *reinterpret_cast<uint4*>(p.a_lo + o) = *reinterpret_cast<const uint4*>(l);
@@ -273,6 +276,7 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
           }
         }
       }
+      if (MODE == 1 && p.nrm && row_ok) p.nrm[(size_t)m * p.nt + nt] = ss;
       tc_fence_before();
       mbar_arrive(tempty + buf);
       tph[buf] ^= 1;
@@ -489,30 +493,18 @@ __global__ void build_v_kernel(const float2* __restrict__ V, long long vs, __nv_
   }
 }
 
-// ||A_w||_F^2 = sum over the planes of (hi + lo)^2 (one block per walker, fixed tree)
-__global__ void __launch_bounds__(256) normA_planes_kernel(const __nv_bfloat16* __restrict__ hi,
-                                                           const __nv_bfloat16* __restrict__ lo,
-                                                           double* __restrict__ scal, int N, int KA) {
-  __shared__ double sh[8];
-  const int w = blockIdx.x;
-  const size_t per = (size_t)N * KA;
-  const __nv_bfloat16* h = hi + (size_t)w * per;
-  const __nv_bfloat16* l = lo + (size_t)w * per;
-  float part = 0.f;
-  for (size_t e = threadIdx.x; e < per; e += 256) {
-    const float x = __bfloat162float(h[e]) + __bfloat162float(l[e]);
-    part = fmaf(x, x, part);
-  }
-  double v = part;
+// ||A_w||_F from the field epilogue's per-tile row sums of squares (rows 2w
+// and 2w + 1 of every column tile), one warp per walker, summed in a fixed
+// order (lane-strided FP64 partials, then a fixed shuffle tree).
+__global__ void normA_rows_kernel(const float* __restrict__ nrm, double* __restrict__ scal, int Nw, int nt) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= Nw) return;
+  const float* r = nrm + (size_t)(2 * w) * nt;
+  double v = 0.0;
+  for (int e = lane; e < 2 * nt; e += 32) v += (double)r[e];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int i = 0; i < 8; ++i) t += sh[i];
-    scal[(size_t)w * SC_COUNT + SC_NORMA] = sqrt(t);
-  }
+  if (lane == 0) scal[(size_t)w * SC_COUNT + SC_NORMA] = sqrt(v);
 }
 
 // Right operand, once per context: LT[p Nq + q][g] = L[g][p][q] split into
@@ -674,10 +666,10 @@ cudaError_t tc_field_ws(afqmc_ctx* c) {
   AllocScope alloc_scope(AG_PLANES);
   TgPlan& P = c->tg;
   if (!P.ok) return cudaSuccess;
-  void* old[] = {P.x_hi, P.x_lo, P.a_hi, P.a_lo, P.v_hi, P.v_lo, P.p_hi, P.p_lo};
+  void* old[] = {P.x_hi, P.x_lo, P.a_hi, P.a_lo, P.v_hi, P.v_lo, P.p_hi, P.p_lo, P.nrm};
   for (void* q : old)
     if (q) cudaFree(q);
-  P.x_hi = P.x_lo = P.a_hi = P.a_lo = P.v_hi = P.v_lo = P.p_hi = P.p_lo = nullptr;
+  P.x_hi = P.x_lo = P.a_hi = P.a_lo = P.v_hi = P.v_lo = P.p_hi = P.p_lo = P.nrm = nullptr;
   P.m_cap = 0;
   P.av_cap = 0;
   P.hs_rows = 0;
@@ -709,6 +701,10 @@ cudaError_t tc_field_ws(afqmc_ctx* c) {
     return cudaErrorInvalidValue;
   P.m_cap = mp;
   if (P.av_ok) {
+    // row sums of squares of the field tiles: every row 2w, 2w + 1 (w < Nw) of every
+    // column tile is written by each launch before it is read
+    e = dmalloc(&P.nrm, (size_t)mp * (P.Np / TG_BN) * sizeof(float));
+    if (e != cudaSuccess) return e;
     const size_t arows = (size_t)cap * c->N, vrows = (size_t)cap * P.NBp;
     e = dmalloc(&P.a_hi, arows * P.KA * 2);
     if (e != cudaSuccess) return e;
@@ -751,7 +747,7 @@ cudaError_t tc_field_prepare(const afqmc_ctx* c) {
 void tc_field_free(afqmc_ctx* c) {
   TgPlan& P = c->tg;
   void* ptrs[] = {P.l_hi, P.l_lo, P.x_hi, P.x_lo, P.a_hi, P.a_lo, P.v_hi, P.v_lo,
-                  P.d_hi, P.d_lo, P.p_hi, P.p_lo, P.err};
+                  P.d_hi, P.d_lo, P.p_hi, P.p_lo, P.nrm, P.err};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   P = TgPlan();
@@ -769,7 +765,7 @@ cudaError_t tc_field_launch(afqmc_ctx* c, int Nw, double sqrt_tau, cudaStream_t 
                                                             (float)sqrt_tau);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  TgArgs a;
+  TgArgs a{};
   a.mt = mp / TG_BM;
   a.nt = (int)(P.Np / TG_BN);
   a.KC = P.Kp / 64;
@@ -782,6 +778,7 @@ cudaError_t tc_field_launch(afqmc_ctx* c, int Nw, double sqrt_tau, cudaStream_t 
   a.a_lo = static_cast<__nv_bfloat16*>(P.a_lo);
   a.N = c->N;
   a.KA = P.KA;
+  a.nrm = P.av_ok ? static_cast<float*>(P.nrm) : nullptr;
   a.err = static_cast<int*>(P.err);
   if (!capturing(c)) {
     e = P.av_ok ? raise_smem_limit(field_tc_kernel<1>) : raise_smem_limit(field_tc_kernel<0>);
@@ -889,10 +886,11 @@ cudaError_t tc_halfstep_launch(afqmc_ctx* c, int Nw, const void* in, void* out, 
   return cudaGetLastError();
 }
 
+// ||A_w||_F of the last field assembly (its epilogue left the row sums)
 cudaError_t tc_av_normA(afqmc_ctx* c, int Nw, cudaStream_t s) {
   const TgPlan& P = c->tg;
-  normA_planes_kernel<<<Nw, 256, 0, s>>>(static_cast<const __nv_bfloat16*>(P.a_hi),
-                                         static_cast<const __nv_bfloat16*>(P.a_lo), c->ws.scal, c->N, P.KA);
+  normA_rows_kernel<<<(Nw + 7) / 8, 256, 0, s>>>(static_cast<const float*>(P.nrm), c->ws.scal, Nw,
+                                                 (int)(P.Np / TG_BN));
   return cudaGetLastError();
 }
 
