@@ -92,8 +92,10 @@ enum {
  *              set).  In FP32: the overlap products trial^T Psi, O^{-1} from
  *              the rounded LU factors and Theta = Psi O^{-1}, the force-bias
  *              contraction when it is recomputed, the Arnoldi and Lanczos
- *              inner products, norms and square roots and the
- *              Gram-Schmidt projections of the re-orthonormalisation (the
+ *              inner products, norms and square roots, the one-body trace
+ *              tr(h_half Theta) (error-free products and compensated
+ *              TwoSum sums in FP32, per-thread partials added in FP64) and
+ *              the Gram-Schmidt projections of the re-orthonormalisation (the
  *              walkers are stored in FP32; every result that depends on them
  *              is invariant under Psi -> Psi M, so the orthonormality of Q
  *              affects no energy or weight).  In FP64: the LU of the overlap
