@@ -1450,7 +1450,8 @@ afqmc_status afqmc_sync(afqmc_ctx* c) {
     CK(cudaMemcpy(&flag, f.flag, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) {
       // reported once: the flag is cleared, so the context stays usable
-      CK(cudaMemset(f.flag, 0, sizeof(int)));
+      CK(cudaMemsetAsync(f.flag, 0, sizeof(int), c->stream));
+      CK(cudaStreamSynchronize(c->stream));
       snprintf(g_cuda_err, sizeof g_cuda_err, "%s: pipeline wait timed out (code %d)", f.what, flag);
       return AFQMC_ECUDA;
     }

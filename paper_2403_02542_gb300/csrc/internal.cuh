@@ -202,7 +202,8 @@ namespace afq {
 struct TgPlan {
   bool ok = false;
   int Kp = 0, m_cap = 0;
-  int Nq = 0;  // N rounded up to a multiple of 8: q stride of the column space and Im offset of the planes
+  int Nq = 0;  // N rounded up to a multiple of 8: q stride of the field's column space
+  int Kh = 0;  // Nq rounded up to a multiple of 64: offset of the Im half in the A' and X planes
   size_t Np = 0;
   void* l_hi = nullptr;  // [Np][Kp] bf16: L^T split hi/lo
   void* l_lo = nullptr;
@@ -214,12 +215,13 @@ struct TgPlan {
   alignas(64) unsigned char map_x_hi[128];
   alignas(64) unsigned char map_x_lo[128];
   // products A_w V on the tensor cores: the field kernel then writes A_w as
-  // bf16 hi/lo planes A'[w][p][KA] = [Re A_w[p][:] | Im A_w[p][:]]
+  // bf16 hi/lo planes A'[w][p][KA] = [Re A_w[p][:] | Im A_w[p][:]] (Im from
+  // column Kh, KA = 2 Kh)
   bool av_ok = false;
   int KA = 0, NBp = 0, S_av = 0, av_cap = 0;
   void* a_hi = nullptr;  // [cap * N][KA]
   void* a_lo = nullptr;
-  void* v_hi = nullptr;  // [cap * NBp][KA]: rows j [Re v_j | -Im v_j], rows nc + j [Im v_j | Re v_j]
+  void* v_hi = nullptr;  // [cap * NBp][KA]: rows j [Re v_j | Im v_j] (Im from column Kh), rows >= nc zero
   void* v_lo = nullptr;
   void* nrm = nullptr;   // [m_cap][Np / 256] float: sum of squares of each field tile row (||A_w||_F)
   alignas(64) unsigned char map_a_hi[128];

@@ -33,13 +33,16 @@
 //
 // When the products A_w V of the exponential also run on the tensor cores,
 // the field epilogue writes A_w instead as bfloat16 hi/lo planes
-// A'[w][p][k] = [Re A_w[p][q] | Im A_w[p][q]] (k = q, Nq + q; the columns
-// N..Nq of each half are the zero accumulators of the zero rows of L^T, stored
-// with the rest in 16-byte runs), and
-//   (A V)_re = A' [Re V; -Im V],  (A V)_im = A' [Im V; Re V]
-// is one real contraction per walker with K = 2N and 2 nc output columns
-// (av_tc_kernel: rows p in tiles of 128, the whole V' of the walker as the
-// right operand, same three-MMA split, pipeline and bounded waits).
+// A'[w][p][k] = [Re A_w[p][q] | Im A_w[p][q]] (k = q, Kh + q with Kh = Nq
+// rounded up to 64; the columns N..Nq of each half are the zero accumulators
+// of the zero rows of L^T, stored with the rest in 16-byte runs, and N..Kh
+// stay zero), and the basis vectors sit once in planes X[w][j][k] =
+// [Re v_j | Im v_j] (same halves).  With X* = X with its halves swapped,
+//   (A V)_re = A' [Re V; -Im V] = A' X with B negated on the Im half,
+//   (A V)_im = A' [Im V;  Re V] = A' X*,
+// so av_tc_kernel (rows p in tiles of 128, K = 2 Kh in slabs of 64, same
+// three-MMA split, pipeline and bounded waits) pairs every A' slab with its
+// own X slab and the X slab of the other half, into two accumulators.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -65,7 +68,7 @@ struct TgArgs {
   float* out;          // mode 0: A as interleaved complex [Nw][N][N]
   __nv_bfloat16* a_hi;  // mode 1: A' planes [Nw * N][KA]
   __nv_bfloat16* a_lo;
-  int N, KA, Nq;
+  int N, KA, Nq, Kh;
   const float2* hs_in;  // mode 2: walkers in [Nw nc][N] complex64
   float2* hs_out;       // mode 2: walkers out, same layout
   float* nrm;           // mode 1: [rows][nt] sum of squares of each tile row (NULL: none)
@@ -235,13 +238,13 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
         tmem_ld8(tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * TG_BN + c0), v);
         tmem_wait_ld();
         if constexpr (MODE == 1) {
-          // row 2w + part -> plane columns part * Nq + q .. q + 7 of row p of
-          // walker w (e0 and Nq are multiples of 8: one aligned 16-byte run)
+          // row 2w + part -> plane columns part * Kh + q .. q + 7 of row p of
+          // walker w (e0, Nq and Kh are multiples of 8: one aligned 16-byte run)
           const int e0 = e_base + c0;
           if (!row_ok || e0 >= p.Nn) continue;
           const int part = m & 1;
           const int pr = e0 / p.Nq, q = e0 - pr * p.Nq;
-          const size_t o = ((size_t)w * p.N + pr) * p.KA + (size_t)part * p.Nq + q;
+          const size_t o = ((size_t)w * p.N + pr) * p.KA + (size_t)part * p.Kh + q;
           __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
           for (int t = 0; t < 8; ++t) {
@@ -294,7 +297,8 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
 }
 
 // Products A_w V for every walker: items (walker, 128-row tile of p), K = KA
-// in slabs of 64, the right operand V'_w (NBp rows) streamed with each slab.
+// in slabs of 64; each stage carries the A' slab, the walker's X slab (NBp
+// rows) and the X slab of the other half (slab kc +- KC/2).
 struct AvArgs {
   int N, nc, NBp, KC, MT, n_items, S;
   uint32_t stage_bytes, b_bytes;
@@ -357,14 +361,18 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
       for (int item = blockIdx.x; item < p.n_items && !*abort_flag; item += gridDim.x) {
         const int w = item / p.MT, mt = item - (item / p.MT) * p.MT;
         const int arow = w * p.N + mt * TG_BM, vrow = w * p.NBp;
+        const int half = p.KC >> 1;
         for (int kc = 0; kc < p.KC; ++kc) {
           if (!mbar_wait(empty + stage, ph ^ 1)) { atomicOr(p.err, 1); *abort_flag = 1; break; }
           mbar_expect_tx(full + stage, p.stage_bytes);
           unsigned char* dst = base + (size_t)stage * p.stage_bytes;
+          const int pk = kc < half ? kc + half : kc - half;  // the slab of the other half
           tma_load_2d(dst, &tmA_hi, kc * 64, arow, full + stage);
           tma_load_2d(dst + TG_A_BYTES, &tmA_lo, kc * 64, arow, full + stage);
           tma_load_2d(dst + 2 * TG_A_BYTES, &tmV_hi, kc * 64, vrow, full + stage);
           tma_load_2d(dst + 2 * TG_A_BYTES + p.b_bytes, &tmV_lo, kc * 64, vrow, full + stage);
+          tma_load_2d(dst + 2 * TG_A_BYTES + 2 * p.b_bytes, &tmV_hi, pk * 64, vrow, full + stage);
+          tma_load_2d(dst + 2 * TG_A_BYTES + 3 * p.b_bytes, &tmV_lo, pk * 64, vrow, full + stage);
           issued[stage] = true;
           last_ph[stage] = ph;
           if (++stage == p.S) { stage = 0; ph ^= 1; }
@@ -379,23 +387,32 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
       int stage = 0, buf = 0;
       uint32_t ph = 0, tph[2] = {0, 0};
       const uint32_t idesc = idesc_bf16(TG_BM, p.NBp);
+      const uint32_t idesc_neg = idesc | (1u << 14);  // B negated: the -Im A Im V term of the real part
+      const int half = p.KC >> 1;
       for (int item = blockIdx.x; item < p.n_items && !*abort_flag; item += gridDim.x) {
         if (!mbar_wait(tempty + buf, tph[buf] ^ 1)) { atomicOr(p.err, 2); *abort_flag = 1; break; }
         tc_fence_after();
-        const uint32_t d = tmem + (uint32_t)(buf * p.NBp);
+        const uint32_t d_re = tmem + (uint32_t)(buf * 2 * p.NBp), d_im = d_re + (uint32_t)p.NBp;
         for (int kc = 0; kc < p.KC; ++kc) {
           if (!mbar_wait(full + stage, ph)) { atomicOr(p.err, 4); *abort_flag = 1; break; }
           tc_fence_after();
           const uint32_t a_hi = sa(base + (size_t)stage * p.stage_bytes);
           const uint32_t a_lo = a_hi + TG_A_BYTES;
-          const uint32_t b_hi = a_hi + 2 * TG_A_BYTES;
-          const uint32_t b_lo = b_hi + p.b_bytes;
+          const uint32_t x_hi = a_hi + 2 * TG_A_BYTES;  // X slab kc
+          const uint32_t x_lo = x_hi + p.b_bytes;
+          const uint32_t y_hi = x_lo + p.b_bytes;       // X slab of the other half
+          const uint32_t y_lo = y_hi + p.b_bytes;
+          const uint32_t id_re = kc < half ? idesc : idesc_neg;
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             const uint32_t off = k * 32;
-            umma(d, sw128_desc(a_hi + off), sw128_desc(b_hi + off), idesc, (kc > 0 || k > 0) ? 1u : 0u);
-            umma(d, sw128_desc(a_hi + off), sw128_desc(b_lo + off), idesc, 1u);
-            umma(d, sw128_desc(a_lo + off), sw128_desc(b_hi + off), idesc, 1u);
+            const uint32_t first = (kc > 0 || k > 0) ? 1u : 0u;
+            umma(d_re, sw128_desc(a_hi + off), sw128_desc(x_hi + off), id_re, first);
+            umma(d_re, sw128_desc(a_hi + off), sw128_desc(x_lo + off), id_re, 1u);
+            umma(d_re, sw128_desc(a_lo + off), sw128_desc(x_hi + off), id_re, 1u);
+            umma(d_im, sw128_desc(a_hi + off), sw128_desc(y_hi + off), idesc, first);
+            umma(d_im, sw128_desc(a_hi + off), sw128_desc(y_lo + off), idesc, 1u);
+            umma(d_im, sw128_desc(a_lo + off), sw128_desc(y_hi + off), idesc, 1u);
           }
           umma_commit(empty + stage);
           if (++stage == p.S) { stage = 0; ph ^= 1; }
@@ -429,11 +446,11 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
       const bool row_ok = pr < p.N;
       float2* o = p.out + (size_t)w * p.c_stride + pr;
       float2* dd = p.add ? p.add + (size_t)w * p.c_stride + pr : nullptr;
-      const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * p.NBp);
+      const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(buf * 2 * p.NBp);
       for (int j0 = 0; j0 < p.nc; j0 += 8) {
         uint32_t vr[8], vi[8];
-        tmem_ld8(tbase + (uint32_t)j0, vr);                 // columns j: Re (A V)
-        tmem_ld8(tbase + (uint32_t)(p.nc + j0), vi);        // columns nc + j: Im (A V)
+        tmem_ld8(tbase + (uint32_t)j0, vr);                 // real accumulator, column j
+        tmem_ld8(tbase + (uint32_t)(p.NBp + j0), vi);       // imaginary accumulator, column j
         tmem_wait_ld();
         if (!row_ok) continue;
 #pragma unroll
@@ -466,26 +483,24 @@ __global__ void __launch_bounds__(TG_THREADS, 1)
   }
 }
 
-// V'_w from V (complex64 [w][j][q], walker stride vs): rows j < nc hold
-// [Re v_j | -Im v_j], rows nc + j hold [Im v_j | Re v_j] (the second half
-// from column Nq); rows >= 2 nc, columns q >= N of each half and columns
-// >= 2 Nq are zero.  Split into hi/lo.
+// X_w from V (complex64 [w][j][q], walker stride vs): row j < nc holds
+// [Re v_j | Im v_j] (the second half from column Kh = KA / 2); rows >= nc and
+// columns q >= N of each half are zero.  Split into hi/lo.
 __global__ void build_v_kernel(const float2* __restrict__ V, long long vs, __nv_bfloat16* __restrict__ hi,
-                               __nv_bfloat16* __restrict__ lo, int Nw, int N, int Nq, int nc, int NBp, int KA) {
+                               __nv_bfloat16* __restrict__ lo, int Nw, int N, int nc, int NBp, int KA) {
   const size_t total = (size_t)Nw * NBp * KA;
+  const int Kh = KA >> 1;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const int k = (int)(e % KA);
     const size_t rw = e / KA;
     const int row = (int)(rw % NBp);
     const size_t w = rw / NBp;
     float x = 0.f;
-    const bool first = k < Nq;
-    const int q = first ? k : k - Nq;
-    if (row < 2 * nc && k < 2 * Nq && q < N) {
-      const int j = row < nc ? row : row - nc;
-      const float2 v = V[w * vs + (size_t)j * N + q];
-      if (row < nc) x = first ? v.x : -v.y;
-      else x = first ? v.y : v.x;
+    const bool first = k < Kh;
+    const int q = first ? k : k - Kh;
+    if (row < nc && q < N) {
+      const float2 v = V[w * vs + (size_t)row * N + q];
+      x = first ? v.x : v.y;
     }
     const __nv_bfloat16 h = __float2bfloat16(x);
     hi[e] = h;
@@ -592,7 +607,8 @@ inline int grid_for(size_t n) {
 }
 
 size_t tg_smem_bytes() { return 1024 + (size_t)TG_S * TG_STAGE_BYTES + (2 * TG_S + 5) * 8 + 16; }
-size_t av_stage_bytes(int NBp) { return 2 * (size_t)TG_A_BYTES + 2 * (size_t)NBp * 128; }
+// A' slab (hi, lo) and two X slabs (hi, lo each)
+size_t av_stage_bytes(int NBp) { return 2 * (size_t)TG_A_BYTES + 4 * (size_t)NBp * 128; }
 size_t av_smem_bytes(int NBp, int S) { return 1024 + (size_t)S * av_stage_bytes(NBp) + (2 * S + 5) * 8 + 16; }
 
 int sm_count() {
@@ -604,7 +620,7 @@ int sm_count() {
 }  // namespace
 
 // Plan and right operand of the tensor-core field assembly (mixed contexts);
-// the products A V go to the tensor cores as well when 2 nc <= 240.
+// the products A V go to the tensor cores as well when nc <= 128.
 cudaError_t tc_field_setup(afqmc_ctx* c, cudaStream_t s) {
   TgPlan& P = c->tg;
   P = TgPlan();
@@ -647,21 +663,25 @@ cudaError_t tc_field_setup(afqmc_ctx* c, cudaStream_t s) {
       !make_map(reinterpret_cast<CUtensorMap*>(P.map_d_lo), P.d_lo, P.hs_Mp, P.hs_Kp, TG_BM))
     return cudaErrorInvalidValue;
   P.hs_ok = true;
-  const int nbp = ((2 * c->nc + 15) / 16) * 16;
-  if (nbp <= 240) {
+  // X rows: the nc columns of a walker, padded to the MMA's N granularity;
+  // two accumulators of nbp columns, double-buffered, in the 512 TMEM columns
+  const int nbp = ((c->nc + 15) / 16) * 16;
+  if (nbp <= 128) {
     int S = 4;
     while (S > 2 && av_smem_bytes(nbp, S) > (size_t)max_dyn_smem()) --S;
     if (av_smem_bytes(nbp, S) <= (size_t)max_dyn_smem()) {
       P.av_ok = true;
       P.NBp = nbp;
       P.S_av = S;
-      P.KA = ((2 * P.Nq + 63) / 64) * 64;
+      P.Kh = ((P.Nq + 63) / 64) * 64;
+      P.KA = 2 * P.Kh;
     }
   }
   return cudaSuccess;
 }
 
-// Operand planes sized for the workspace's walker capacity.
+// Operand planes sized for the workspace's walker capacity (zeroed on the
+// context's stream, which is then synchronised).
 cudaError_t tc_field_ws(afqmc_ctx* c) {
   AllocScope alloc_scope(AG_PLANES);
   TgPlan& P = c->tg;
@@ -682,9 +702,9 @@ cudaError_t tc_field_ws(afqmc_ctx* c) {
     if (e != cudaSuccess) return e;
     e = dmalloc(&P.p_lo, rows * P.hs_Kp * 2);
     if (e != cudaSuccess) return e;
-    e = cudaMemset(P.p_hi, 0, rows * P.hs_Kp * 2);
+    e = cudaMemsetAsync(P.p_hi, 0, rows * P.hs_Kp * 2, c->stream);
     if (e != cudaSuccess) return e;
-    e = cudaMemset(P.p_lo, 0, rows * P.hs_Kp * 2);
+    e = cudaMemsetAsync(P.p_lo, 0, rows * P.hs_Kp * 2, c->stream);
     if (e != cudaSuccess) return e;
     if (!make_map(reinterpret_cast<CUtensorMap*>(P.map_p_hi), P.p_hi, rows, P.hs_Kp, TG_BN) ||
         !make_map(reinterpret_cast<CUtensorMap*>(P.map_p_lo), P.p_lo, rows, P.hs_Kp, TG_BN))
@@ -710,20 +730,20 @@ cudaError_t tc_field_ws(afqmc_ctx* c) {
     if (e != cudaSuccess) return e;
     e = dmalloc(&P.a_lo, arows * P.KA * 2);
     if (e != cudaSuccess) return e;
-    // the K padding columns 2 Nq..KA stay zero (the field epilogue writes k < 2 Nq only)
-    e = cudaMemset(P.a_hi, 0, arows * P.KA * 2);
+    // the columns Nq..Kh of each half stay zero (the field epilogue writes q < Nq only)
+    e = cudaMemsetAsync(P.a_hi, 0, arows * P.KA * 2, c->stream);
     if (e != cudaSuccess) return e;
-    e = cudaMemset(P.a_lo, 0, arows * P.KA * 2);
+    e = cudaMemsetAsync(P.a_lo, 0, arows * P.KA * 2, c->stream);
     if (e != cudaSuccess) return e;
     e = dmalloc(&P.v_hi, vrows * P.KA * 2);
     if (e != cudaSuccess) return e;
     e = dmalloc(&P.v_lo, vrows * P.KA * 2);
     if (e != cudaSuccess) return e;
-    // rows 2 nc..NBp and the columns q >= N of each half stay zero when the
+    // rows nc..NBp and the columns q >= N of each half stay zero when the
     // Krylov kernels fill the planes
-    e = cudaMemset(P.v_hi, 0, vrows * P.KA * 2);
+    e = cudaMemsetAsync(P.v_hi, 0, vrows * P.KA * 2, c->stream);
     if (e != cudaSuccess) return e;
-    e = cudaMemset(P.v_lo, 0, vrows * P.KA * 2);
+    e = cudaMemsetAsync(P.v_lo, 0, vrows * P.KA * 2, c->stream);
     if (e != cudaSuccess) return e;
     if (!make_map(reinterpret_cast<CUtensorMap*>(P.map_a_hi), P.a_hi, arows, P.KA, TG_BM) ||
         !make_map(reinterpret_cast<CUtensorMap*>(P.map_a_lo), P.a_lo, arows, P.KA, TG_BM) ||
@@ -732,7 +752,9 @@ cudaError_t tc_field_ws(afqmc_ctx* c) {
       return cudaErrorInvalidValue;
     P.av_cap = cap;
   }
-  return cudaSuccess;
+  // the zero padding is in place before any stream (the context's, or the
+  // non-blocking streams of a batch graph) reads the planes
+  return cudaStreamSynchronize(c->stream);
 }
 
 cudaError_t tc_field_prepare(const afqmc_ctx* c) {
@@ -773,6 +795,7 @@ cudaError_t tc_field_launch(afqmc_ctx* c, int Nw, double sqrt_tau, cudaStream_t 
   a.M = 2 * Nw;
   a.Nn = c->N * P.Nq;
   a.Nq = P.Nq;
+  a.Kh = P.Kh;
   a.out = static_cast<float*>(c->ws.A);
   a.a_hi = static_cast<__nv_bfloat16*>(P.a_hi);
   a.a_lo = static_cast<__nv_bfloat16*>(P.a_lo);
@@ -807,8 +830,7 @@ cudaError_t tc_av_launch(afqmc_ctx* c, int Nw, const void* V, long long v_stride
     const size_t elems = (size_t)Nw * P.NBp * P.KA;
     build_v_kernel<<<grid_for(elems), 256, 0, s>>>(static_cast<const float2*>(V), v_stride,
                                                    static_cast<__nv_bfloat16*>(P.v_hi),
-                                                   static_cast<__nv_bfloat16*>(P.v_lo), Nw, c->N, P.Nq, c->nc, P.NBp,
-                                                   P.KA);
+                                                   static_cast<__nv_bfloat16*>(P.v_lo), Nw, c->N, c->nc, P.NBp, P.KA);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

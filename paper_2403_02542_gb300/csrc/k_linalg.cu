@@ -606,27 +606,22 @@ __global__ void mgs_kernel(typename C2<R>::t* __restrict__ psi, int N, int na, i
 // One warp per orbital column (walker w, column j); columns are numbered
 // col = w * nc + j and all column vectors are contiguous [N].
 // Basis vector element p of column col = (w, j) into the split right operand
-// of the tensor-core products A V: row j = [Re v | -Im v], row nc + j =
-// [Im v | Re v] of walker w, the second half from column Nq (bf16 hi/lo
-// planes, row length KA).
+// of the tensor-core products A V: row j of walker w = [Re v | Im v], the
+// second half from column Kh (bf16 hi/lo planes, row length KA = 2 Kh).
 struct VPlanes {
   __nv_bfloat16* hi = nullptr;
   __nv_bfloat16* lo = nullptr;
-  int NBp = 0, KA = 0, Nq = 0;
+  int NBp = 0, KA = 0, Kh = 0;
 };
 __device__ __forceinline__ void put_vplanes(const VPlanes& P, int col, int nc, int p, float vr, float vi) {
   const int w = col / nc, j = col - (col / nc) * nc;
-  const size_t ra = ((size_t)w * P.NBp + j) * P.KA, rb = ((size_t)w * P.NBp + nc + j) * P.KA;
+  const size_t ra = ((size_t)w * P.NBp + j) * P.KA;
   const __nv_bfloat16 hr = __float2bfloat16(vr), hi = __float2bfloat16(vi);
   const __nv_bfloat16 lr = __float2bfloat16(vr - __bfloat162float(hr)), li = __float2bfloat16(vi - __bfloat162float(hi));
   P.hi[ra + p] = hr;
   P.lo[ra + p] = lr;
-  P.hi[ra + P.Nq + p] = __hneg(hi);
-  P.lo[ra + P.Nq + p] = __hneg(li);
-  P.hi[rb + p] = hi;
-  P.lo[rb + p] = li;
-  P.hi[rb + P.Nq + p] = hr;
-  P.lo[rb + P.Nq + p] = lr;
+  P.hi[ra + P.Kh + p] = hi;
+  P.lo[ra + P.Kh + p] = li;
 }
 
 // Hessenberg storage: entry (column col, row i, column j) of H_k at
@@ -1278,7 +1273,7 @@ VPlanes vplanes(const afqmc_ctx* c) {
     v.lo = static_cast<__nv_bfloat16*>(c->tg.v_lo);
     v.NBp = c->tg.NBp;
     v.KA = c->tg.KA;
-    v.Nq = c->tg.Nq;
+    v.Kh = c->tg.Kh;
   }
   return v;
 }
