@@ -803,6 +803,19 @@ def exchange_flop_per_walker(system) -> int:
     return system.G * 4 * (system.na * system.na + system.nb * system.nb) * system.N
 
 
+def step_flop_per_walker(system, k: int = KDIM) -> int:
+    """Algorithmic flops of one Split-2 + Krylov-k step with E_L, per walker:
+    exchange + Coulomb 4 G (na^2 + nb^2) N, the k products A v over the
+    nc = na + nb orbitals 8 k N^2 nc, the field assembly 2 G N^2 (the
+    independent half of the symmetric A), the force bias 2 G nc N, the two
+    half steps 8 N^2 nc, the Arnoldi projections 8 nc N k (k + 1) and the
+    overlap, ratio and one-body terms 20 N (na^2 + nb^2)."""
+    N, G, na, nb = system.N, system.G, system.na, system.nb
+    nc, n2 = na + nb, na * na + nb * nb
+    return (4 * G * n2 * N + 8 * k * N * N * nc + 2 * G * N * N + 2 * G * nc * N + 8 * N * N * nc
+            + 8 * nc * N * k * (k + 1) + 20 * N * n2)
+
+
 def exchange_peak(precision: str):
     """Roofline denominator of the exchange kernel: (peak, bound, note)."""
     if precision == "fp64":
@@ -1166,6 +1179,11 @@ def run_ours(args):
                      "launches_timed": ex_n, "peak_source": peak_note,
                      "share_of_step": (split.get("exchange", 0.0) / total_split) if total_split else None},
         "kernel_ms_per_step": split,
+        # the whole step against the same roofline: algorithmic flops of all its parts
+        "step_roofline": {"flop_per_walker_step": step_flop_per_walker(system),
+                          "achieved": step_flop_per_walker(system) * NW * world / (ms / K / 1000.0) / 1e12,
+                          "peak": peak, "unit": "TFLOP/s",
+                          "frac": step_flop_per_walker(system) * NW * world / (ms / K / 1000.0) / 1e12 / peak},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e, "unit": "walker-steps/s",
                 "h2d_bytes_per_step": NW * G * 8, "d2h_bytes_per_step": 4 * 8},
