@@ -322,8 +322,8 @@ afqmc_status afqmc_energy_backward(afqmc_ctx* ctx, const afqmc_walkers* w, doubl
  * J = E_n = sum_w W_n Ebar_L(Psi_n) / sum_w W_n (Sec. II.A), with respect to h1
  * and every L_g, through every step of the walk (Split-2 propagator, Sec. III.B,
  * with the Taylor exponential of Eq. taylor or the Krylov action of Eqs.
- * krylovsub-krylov, differentiated through its Arnoldi steps, norms and
- * small exponential).  The paper has no gradients; the
+ * krylovsub-krylov, differentiated through its Arnoldi (or complex-symmetric
+ * Lanczos) steps, norms and small exponential).  The paper has no gradients; the
  * readings taken are: the auxiliary fields are fixed inputs; every threshold
  * decision of the forward walk (force-bias removal |f_g| >= 1, reweighting cap,
  * cos(dtheta) <= 0, energy window) is held fixed, so a removed component or a
@@ -340,10 +340,12 @@ afqmc_status afqmc_energy_backward(afqmc_ctx* ctx, const afqmc_walkers* w, doubl
  *             log <Psi_T|Psi_0>, as afqmc_walkers_init leaves it)
  *   fields    device [n_steps][Nw][G] double, the fields of each step
  *   p         n_steps >= 1; expm = AFQMC_EXPM_TAYLOR (order = Taylor order
- *             1..32) or AFQMC_EXPM_KRYLOV (order = Krylov dimension 1..32,
- *             taken as min(order, N); an invariant subspace found by a
- *             column ends its basis as in the step, the threshold held
- *             fixed), other values AFQMC_ENOTSUP; reortho_every r:
+ *             1..32), AFQMC_EXPM_KRYLOV or AFQMC_EXPM_LANCZOS (order =
+ *             Krylov dimension 1..32, taken as min(order, N); an invariant
+ *             subspace found by a column ends its basis as in the step, the
+ *             threshold held fixed; the Lanczos recurrence is holomorphic,
+ *             so its square roots are differentiated on their principal
+ *             branch), other values AFQMC_ENOTSUP; reortho_every r:
  *             re-orthonormalise after step k when (k+1) % r == 0 (0: never);
  *             ckpt_every >= 1; tau > 0; e0; dJ scales every output gradient
  *   J_out     device [4] double or NULL: {sum W Ebar_L, sum W, J, live
@@ -370,7 +372,7 @@ afqmc_status afqmc_energy_backward(afqmc_ctx* ctx, const afqmc_walkers* w, doubl
  * and, in mixed contexts, G N^2 + G (na+nb) N complex floats; the Krylov
  * action adds Nw (na+nb) N more of the walkers' type and, for each of the
  * Nw (na+nb) columns, a copy of its k x k Hessenberg block in the walkers'
- * type plus k^2 + k complex doubles for the block's adjoint).
+ * type plus k^2 + k + 2 complex doubles for the block's adjoint).
  * AFQMC_ENOTSUP when max(na, nb) > 64.  Synchronises the stream.
  * Errors: EINVAL, EDOM, ENOTSUP, ENOMEM, ECUDA. */
 typedef struct {

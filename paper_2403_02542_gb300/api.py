@@ -172,8 +172,8 @@ class Context:
 
         `w` holds the walkers at step 0 (left unchanged); `fields` is a device
         tensor [n_steps, Nw, G] of the walk's auxiliary fields; `expm` is
-        "taylor" (order = Taylor order) or "krylov" (order = Krylov
-        dimension), the action of e^A in every step.  Returns
+        "taylor" (order = Taylor order), "krylov" (Arnoldi) or "lanczos"
+        (order = Krylov dimension), the action of e^A in every step.  Returns
         (e_mix [4], dJ/dh1 [N,N], dJ/dL [G,N,N]) and, with grad_psi0=True, the
         derivative G [Nw, na+nb, N] (the walkers' complex type) with
         dJ = Re sum G * dPsi_0 as well.  In a mixed context the walk and its
@@ -183,8 +183,8 @@ class Context:
         f = fields.to(device=self.device, dtype=torch.float64).contiguous()
         if f.dim() != 3 or f.shape[1] != w.n or f.shape[2] != self.G:
             raise ValueError("fields must be [n_steps, n_walkers, G]")
-        if expm not in ("taylor", "krylov"):
-            raise ValueError("the walk adjoint takes expm='taylor' or 'krylov'")
+        if expm not in ("taylor", "krylov", "lanczos"):
+            raise ValueError("the walk adjoint takes expm='taylor', 'krylov' or 'lanczos'")
         p = L.WalkAdjointParams(int(f.shape[0]), int(order), int(reortho_every), int(ckpt_every),
                                 float(tau), float(e0), float(dJ), EXPMS[expm])
         J = torch.empty(4, dtype=torch.float64, device=self.device)
@@ -358,8 +358,8 @@ class WalkEnergy(torch.autograd.Function):
     """J(h1, L) = E_n, the mixed estimator after an n-step fixed-field walk
     from walkers at the trial, as a differentiable function (the energy
     derivatives of a bond-length scan).  The forward is the walk itself
-    (afqmc_step, Split-2 + Taylor of the given order or Krylov of that
-    dimension, re-orthonormalisation every reortho_every steps); the
+    (afqmc_step, Split-2 + Taylor of the given order or Krylov (Arnoldi or
+    Lanczos) of that dimension, re-orthonormalisation every reortho_every steps); the
     backward is afqmc_walk_backward on a
     context built from the same (h1, L), which recomputes the walk from
     checkpoints every ckpt_every steps and returns dJ/dh1 and dJ/dL scaled by
@@ -368,8 +368,8 @@ class WalkEnergy(torch.autograd.Function):
 
     apply(h1 [N,N] float64, L [G,N,N] float64, fields [n, Nw, G] float64 on
           the device, trial [N, na+nb], na, nb, e0, tau, order, reortho_every,
-          ckpt_every, precision ("fp64" or "mixed"), e_const, expm ("taylor" or
-          "krylov")) -> J (0-dim)"""
+          ckpt_every, precision ("fp64" or "mixed"), e_const, expm ("taylor",
+          "krylov" or "lanczos")) -> J (0-dim)"""
 
     @staticmethod
     def forward(ctx, h1, chol, fields, trial, na, nb, e0, tau, order=6, reortho_every=0, ckpt_every=10,

@@ -769,10 +769,10 @@ struct AdjBufs {
   uint8_t* keep;
   int skc, skb;  // split-K factors of the two long-K contractions
   // Krylov action (NULL for the Taylor one): the Hessenberg block before the
-  // small exponential, its adjoint, g_y, Gamma_beta and the adjoint U_j of A b_j
+  // small exponential, its adjoint, g_y, the start-norm adjoint, the adjoint
+  // U_j of A b_j and the Lanczos recurrence's per-column carry
   P *Hs, *kU;
-  double2 *GH, *gy;
-  double* gbeta;
+  double2 *GH, *gy, *gbeta, *carry;
 };
 
 int pick_splitk(long long M, long long Nn, long long K, int cap) {
@@ -859,13 +859,15 @@ static void adj_carve(Arena& a, AdjBufs<R>& b, const afqmc_ctx* c, int Nw, int K
   b.Hs = krylov ? a.take<P>(km * km * hs) : nullptr;
   b.GH = krylov ? a.take<double2>(km * km * hs) : nullptr;
   b.gy = krylov ? a.take<double2>(km * hs) : nullptr;
-  b.gbeta = krylov ? a.take<double>(hs) : nullptr;
+  b.gbeta = krylov ? a.take<double2>(hs) : nullptr;
+  b.carry = krylov ? a.take<double2>(hs) : nullptr;
   b.kU = krylov ? a.take<P>(nw * per) : nullptr;
 }
 
 // One reverse step k of the walk: recompute Theta_k, f, c, A, the action of
-// e^A (Taylor terms, or the Arnoldi basis, Hessenberg matrix and products
-// A b_j when kry > 0 is the Krylov dimension) and Psi3 from the stored Psi_k,
+// e^A (Taylor terms, or the Krylov basis, Hessenberg (or Lanczos tridiagonal,
+// lz) matrix and products A b_j when kry > 0 is the Krylov dimension) and
+// Psi3 from the stored Psi_k,
 // then pull the adjoint Psi_bar_{k+1} (in b.pb) back to Psi_bar_k (in b.pb)
 // and accumulate the parameter adjoints.  With complex64 walkers the
 // contractions run in FP32 and the parameter adjoints of the step are added
@@ -873,7 +875,7 @@ static void adj_carve(Arena& a, AdjBufs<R>& b, const afqmc_ctx* c, int Nw, int K
 template <typename R>
 static afqmc_status adj_step(afqmc_ctx* c, const AdjBufs<R>& b, int Nw, const double* x,
                              const typename C2<R>::t* psik, const double* lok, const typename C2<R>::t* psinext, int qr,
-                             int K, int kry, double tau) {
+                             int K, int kry, bool lz, double tau) {
   typedef typename C2<R>::t P;
   constexpr bool split = std::is_same<R, float>::value;
   cudaStream_t s = c->stream;
@@ -908,19 +910,21 @@ static afqmc_status adj_step(afqmc_ctx* c, const AdjBufs<R>& b, int Nw, const do
   if (kry > 0) {
     CKW(gm(site_args<R>(c, SITE_HALFSTEP, Nw, st, b.P0, ws.psi_b), false, EPI_STORE), "adjoint: half step");
     CKW(launch_normA<R>(c, Nw, s), "adjoint: norm of A");
-    CKW(launch_krylov_init<R>(c, Nw, s), "adjoint: Krylov start");
+    CKW(lz ? launch_lanczos_init<R>(c, Nw, s) : launch_krylov_init<R>(c, Nw, s), "adjoint: Krylov start");
     GemmArgs ga = site_args<R>(c, SITE_EXPM, Nw, st, nullptr, nullptr);
     const size_t bstride = (size_t)ws.n_walkers * per;
     for (int j = 0; j < kry; ++j) {
       ga.B = static_cast<const P*>(ws.basis) + j * bstride;
       ga.C = b.Tb + j * kp;
       CKW(gm(ga, true, EPI_STORE), "adjoint: Krylov product");
-      CKW(launch_krylov_orth<R>(c, Nw, j, kry, s, b.Tb + j * kp), "adjoint: Arnoldi step");
+      CKW(lz ? launch_lanczos_step<R>(c, Nw, j, kry, s, b.Tb + j * kp)
+             : launch_krylov_orth<R>(c, Nw, j, kry, s, b.Tb + j * kp),
+          "adjoint: Krylov step");
     }
     const size_t hs = (size_t)ws.n_walkers * nc;
     CKW(cudaMemcpyAsync(b.Hs, ws.hess, (size_t)ws.kmax * ws.kmax * hs * cs, cudaMemcpyDeviceToDevice, s),
         "adjoint: Hessenberg copy");
-    CKW(launch_krylov_finish<R>(c, Nw, kry, s), "adjoint: Krylov finish");
+    CKW(launch_krylov_finish<R>(c, Nw, kry, s, lz), "adjoint: Krylov finish");
     CKW(cudaMemcpyAsync(b.psi2, ws.acc, (size_t)Nw * per * cs, cudaMemcpyDeviceToDevice, s), "adjoint: copy");
     nl += kry + 3;  // norm, start, Arnoldi steps, small exponential and combination; no Taylor sum
   } else {
@@ -954,20 +958,22 @@ static afqmc_status adj_step(afqmc_ctx* c, const AdjBufs<R>& b, int Nw, const do
   CKW(gm(gb, true, bb.second), "adjoint: B adjoint");
   if (kry > 0) {
     // Krylov action: seed from out = sum_i y_i b_i, the adjoint of the small
-    // exponential, then the Arnoldi steps in reverse; per step j the adjoint
-    // U_j of A b_j gives g_b_j += A U_j and A_bar += U_j b_j^T
+    // exponential, then the Arnoldi (or Lanczos) steps in reverse; per step j
+    // the adjoint U_j of A b_j gives g_b_j += A U_j and A_bar += U_j b_j^T
     CKW(kadj_seed<R>(c, Nw, kry, b.p2, b.Ub, kp, b.gy, s), "adjoint: Krylov seed");
-    CKW(kadj_expm<R>(c, Nw, kry, b.Hs, b.gy, b.GH, b.gbeta, s), "adjoint: small exponential");
+    CKW(kadj_expm<R>(c, Nw, kry, b.Hs, b.gy, b.GH, b.gbeta, lz, s), "adjoint: small exponential");
     const size_t bstride = (size_t)ws.n_walkers * per;
     for (int j = kry - 1; j >= 0; --j) {
-      CKW(kadj_orth<R>(c, Nw, j, kry, b.Tb + j * kp, b.Hs, b.GH, b.Ub, kp, b.kU, s), "adjoint: Arnoldi step");
+      CKW(lz ? lzadj_step<R>(c, Nw, j, kry, b.Tb + j * kp, b.Hs, b.GH, b.Ub, kp, b.kU, b.carry, s)
+             : kadj_orth<R>(c, Nw, j, kry, b.Tb + j * kp, b.Hs, b.GH, b.Ub, kp, b.kU, s),
+          "adjoint: Krylov step");
       CKW(gm(site_args<R>(c, SITE_EXPM, Nw, st, b.kU, b.Ub + j * kp), true, EPI_ACC), "adjoint: Krylov product");
       CKW(gm(gargs(N, N, nc, Nw, b.kU, 1, N, perl, static_cast<const P*>(ws.basis) + j * bstride, 1, N, perl, b.Abar,
                    N, 1, NNl),
              true, j == kry - 1 ? EPI_STORE : EPI_ACC),
           "adjoint: A adjoint");
     }
-    CKW(kadj_input<R>(c, Nw, b.Ub, b.gbeta, b.p1, s), "adjoint: Krylov start");
+    CKW(kadj_input<R>(c, Nw, b.Ub, b.gbeta, b.p1, lz, s), "adjoint: Krylov start");
     nl += kry + 3;  // seed, small exponential, Arnoldi steps, start
   } else {
     // Taylor action: U_j = T_bar_j / j in Ub slot j-1, T_bar_{j-1} = Psi2_bar + A U_j
@@ -1065,9 +1071,11 @@ static afqmc_status walk_backward_run(afqmc_ctx* c, const afqmc_walkers* w0, con
   sp.tau = p->tau;
   sp.e0 = p->e0;
   sp.propagator = AFQMC_SPLIT2;
-  // Taylor action of order K, or the Krylov one of dimension kry = min(K, N)
-  const int kry = p->expm == AFQMC_EXPM_KRYLOV ? (K < N ? K : N) : 0;
-  sp.expm = kry > 0 ? AFQMC_EXPM_KRYLOV : AFQMC_EXPM_TAYLOR;
+  // Taylor action of order K, or the Krylov (Arnoldi or Lanczos) one of
+  // dimension kry = min(K, N)
+  const bool lz = p->expm == AFQMC_EXPM_LANCZOS;
+  const int kry = (p->expm == AFQMC_EXPM_KRYLOV || lz) ? (K < N ? K : N) : 0;
+  sp.expm = kry > 0 ? p->expm : AFQMC_EXPM_TAYLOR;
   sp.order = kry > 0 ? kry : K;
   sp.measure = 0;
   auto qr_at = [&](int k) { return (p->reortho_every > 0 && (k + 1) % p->reortho_every == 0) ? 1 : 0; };
@@ -1134,7 +1142,7 @@ static afqmc_status walk_backward_run(afqmc_ctx* c, const afqmc_walkers* w0, con
     for (int k = k1 - 1; k >= k0; --k) {
       const size_t i = (size_t)(k - k0);
       rc = adj_step<R>(c, b, Nw, fields + (size_t)k * fstride, b.seg_psi + i * nw * per, b.seg_lo + i * nw * 2,
-                    b.seg_psi + (i + 1) * nw * per, qr_at(k), K, kry, p->tau);
+                    b.seg_psi + (i + 1) * nw * per, qr_at(k), K, kry, lz, p->tau);
       if (rc != AFQMC_OK) return rc;
     }
   }
@@ -1164,7 +1172,7 @@ static afqmc_status walk_backward_alloc(afqmc_ctx* c, const afqmc_walkers* w0, c
   b.skc = pick_splitk(c->G, Nw, (long long)NN, 32);
   b.skb = pick_splitk(c->N, c->N, (long long)Nw * c->nc, 64);
   Arena a;
-  adj_carve<R>(a, b, c, Nw, q->order, q->ckpt_every, nck, q->expm == AFQMC_EXPM_KRYLOV);
+  adj_carve<R>(a, b, c, Nw, q->order, q->ckpt_every, nck, q->expm != AFQMC_EXPM_TAYLOR);
   CK(cudaStreamSynchronize(c->stream));
   char* base = nullptr;
   cudaError_t e = dmalloc(&base, a.used);
@@ -1173,7 +1181,7 @@ static afqmc_status walk_backward_alloc(afqmc_ctx* c, const afqmc_walkers* w0, c
     return cuda_fail(e, "adjoint workspace");
   }
   a = Arena{base, 0};
-  adj_carve<R>(a, b, c, Nw, q->order, q->ckpt_every, nck, q->expm == AFQMC_EXPM_KRYLOV);
+  adj_carve<R>(a, b, c, Nw, q->order, q->ckpt_every, nck, q->expm != AFQMC_EXPM_TAYLOR);
   afqmc_status st = walk_backward_run<R>(c, w0, fields, q, J_out, grad_h1, grad_L, grad_psi0, b);
   e = cudaStreamSynchronize(c->stream);
   cudaFree(base);
@@ -1408,7 +1416,8 @@ afqmc_status afqmc_walk_backward(afqmc_ctx* c, const afqmc_walkers* w0, const do
   if (!std::isfinite(p->tau) || !std::isfinite(p->e0) || !std::isfinite(p->dJ)) return AFQMC_EDOM;
   if (!(p->tau > 0.0) || p->n_steps < 1 || p->ckpt_every < 1 || p->reortho_every < 0) return AFQMC_EINVAL;
   if (p->order < 1 || p->order > 32) return AFQMC_ENOTSUP;
-  if (p->expm != AFQMC_EXPM_TAYLOR && p->expm != AFQMC_EXPM_KRYLOV) return AFQMC_ENOTSUP;
+  if (p->expm != AFQMC_EXPM_TAYLOR && p->expm != AFQMC_EXPM_KRYLOV && p->expm != AFQMC_EXPM_LANCZOS)
+    return AFQMC_ENOTSUP;
   const int nmax = c->na > c->nb ? c->na : c->nb;
   if (nmax > 64 || w0->n_walkers > 65535) return AFQMC_ENOTSUP;
   if ((size_t)(nmax * nmax + nmax * c->N) * 16 > (size_t)max_dyn_smem() - 1024) return AFQMC_ENOTSUP;
@@ -1426,7 +1435,8 @@ afqmc_status afqmc_walk_backward(afqmc_ctx* c, const afqmc_walkers* w0, const do
     st = afqmc_set_tau(c, p->tau);
     if (st != AFQMC_OK) return st;
   }
-  const int kry = p->expm == AFQMC_EXPM_KRYLOV ? (p->order < c->N ? p->order : c->N) : 0;
+  const int kry =
+      (p->expm == AFQMC_EXPM_KRYLOV || p->expm == AFQMC_EXPM_LANCZOS) ? (p->order < c->N ? p->order : c->N) : 0;
   st = ws_ensure(c, Nw, kry > c->ws.kmax ? kry : c->ws.kmax);
   if (st != AFQMC_OK) return st;
   const int C = p->ckpt_every < p->n_steps ? p->ckpt_every : p->n_steps;

@@ -433,20 +433,28 @@ cudaError_t adj_seed_coef(int Nw, const double* wfin, const double* ecap, const 
 // Krylov-action reverse (basis, Hessenberg and beta of the forward in the
 // workspace; Hs a copy of the Hessenberg block taken before the small
 // exponential overwrote its first column; Gb the basis adjoints, planes
-// gstride apart, stored as holomorphic-style adjoints g = conj(Gamma))
+// gstride apart, stored as holomorphic-style adjoints g = conj(Gamma)).
+// `lanczos` selects the complex start norm gamma (ws.cbeta) and writes the
+// start-norm adjoint as a complex g_gamma; Arnoldi's is (Gamma_beta, 0).
 template <typename R>
 cudaError_t kadj_seed(const afqmc_ctx* c, int Nw, int k, const typename C2<R>::t* gout, typename C2<R>::t* Gb,
                       size_t gstride, double2* gy, cudaStream_t s);
 template <typename R>
 cudaError_t kadj_expm(const afqmc_ctx* c, int Nw, int k, const typename C2<R>::t* Hs, const double2* gy, double2* GH,
-                      double* gbeta, cudaStream_t s);
+                      double2* gbeta, bool lanczos, cudaStream_t s);
 template <typename R>
 cudaError_t kadj_orth(const afqmc_ctx* c, int Nw, int j, int k, const typename C2<R>::t* wj,
                       const typename C2<R>::t* Hs, const double2* GH, typename C2<R>::t* Gb, size_t gstride,
                       typename C2<R>::t* U, cudaStream_t s);
 template <typename R>
-cudaError_t kadj_input(const afqmc_ctx* c, int Nw, const typename C2<R>::t* Gb0, const double* gbeta,
-                       typename C2<R>::t* gx, cudaStream_t s);
+cudaError_t kadj_input(const afqmc_ctx* c, int Nw, const typename C2<R>::t* Gb0, const double2* gbeta,
+                       typename C2<R>::t* gx, bool lanczos, cudaStream_t s);
+// reverse of Lanczos step j; carry: one double2 per column, written by step j
+// for step j - 1 (read only where j + 1 < k, so it needs no initial value)
+template <typename R>
+cudaError_t lzadj_step(const afqmc_ctx* c, int Nw, int j, int k, const typename C2<R>::t* wj,
+                       const typename C2<R>::t* Hs, const double2* GH, typename C2<R>::t* Gb, size_t gstride,
+                       typename C2<R>::t* U, double2* carry, cudaStream_t s);
 template <typename R>
 cudaError_t adj_eloc_seed(const afqmc_ctx* c, int Nw, const typename C2<R>::t* theta, const typename C2<R>::t* t,
                           const double* ecoef, typename C2<R>::t* thbar, cudaStream_t s);

@@ -677,41 +677,49 @@ __global__ void kadj_seed_kernel(const typename C2<R>::t* __restrict__ gout, con
   }
 }
 
-// Adjoint of y = beta e^{H} e_1 (FP64, one thread per column).  With
-// Gamma_y = conj(g_y) and u = beta Gamma_y:
+// Adjoint of y = beta e^{H} e_1 (FP64, one thread per column; beta is the
+// real norm of the Arnoldi start, or the complex gamma = (psi^T psi)^{1/2}
+// of the Lanczos one when cbeta is given).  With Gamma_y = conj(g_y) and
+// u = conj(beta g_y):
 //   Gamma_H = L(H^H, u e_1^T), the Frechet derivative of exp at H^H in the
 //   direction u e_1^T; its column m is the top half of exp(M) [0; e_m] for
 //   M = [[H^H, u e_1^T], [0, H^H]] (block-triangular exponential), taken by
 //   sub-steps of a Taylor series on the 2k-vector (u scaled to unit norm,
 //   the result scaled back: L is linear in its direction);
-//   Gamma_beta = Re sum_i conj(Gamma_y_i) v_i = Re sum_i g_y_i y_i / beta.
+//   the start-norm adjoint, written to gbeta: Arnoldi Gamma_beta =
+//   Re sum_i g_y_i y_i / beta (real part only), Lanczos g_gamma =
+//   sum_i g_y_i y_i / gamma (holomorphic).
 // Only the upper-Hessenberg entries of Gamma_H are written (the others are
 // constant zeros of H).
 template <typename R, int KM>
 __global__ void __launch_bounds__(64) kadj_expm_kernel(const typename C2<R>::t* __restrict__ Hs,
                                                        const typename C2<R>::t* __restrict__ hy, size_t hs, int kmax,
                                                        const double* __restrict__ beta,
+                                                       const double2* __restrict__ cbeta,
                                                        const double2* __restrict__ gy, double2* __restrict__ GH,
-                                                       double* __restrict__ gbeta, int ncols, int k) {
+                                                       double2* __restrict__ gbeta, int ncols, int k) {
   const int col = blockIdx.x * 64 + threadIdx.x;
   if (col >= ncols) return;
   auto H = [&](int i, int j) -> cd { return ld(Hs + (size_t)(i * kmax + j) * hs + col); };
-  const double b = beta[col];
+  const cd bc = cbeta ? ld(cbeta + col) : mk(beta[col], 0.0);
+  const double bm2 = abs2(bc);
   cd u[KM];
-  double gb = 0.0, un = 0.0;
+  cd gsum = mk(0.0, 0.0);
+  double un = 0.0;
 #pragma unroll
   for (int i = 0; i < KM; ++i) {
     u[i] = mk(0.0, 0.0);
     if (i < k) {
       const cd g = ldc(gy[(size_t)i * hs + col]);
-      gb += (g * ld(hy + (size_t)(i * kmax) * hs + col)).re;
-      u[i] = b * conj(g);
+      gsum = gsum + g * ld(hy + (size_t)(i * kmax) * hs + col);
+      u[i] = conj(bc * g);
       un += abs2(u[i]);
     }
   }
-  gbeta[col] = b > 0.0 ? gb / b : 0.0;
+  const cd gb = bm2 > 0.0 ? (1.0 / bm2) * (gsum * conj(bc)) : mk(0.0, 0.0);
+  gbeta[col] = make_double2(gb.re, cbeta ? gb.im : 0.0);
   un = sqrt(un);
-  if (!(un > 0.0) || !(b > 0.0)) {
+  if (!(un > 0.0) || !(bm2 > 0.0)) {
     for (int m = 0; m < k; ++m)
       for (int i = 0; i <= m + 1 && i < k; ++i) GH[(size_t)(i * kmax + m) * hs + col] = make_double2(0.0, 0.0);
     return;
@@ -905,7 +913,7 @@ __global__ void kadj_orth_kernel(const typename C2<R>::t* __restrict__ basis, si
 // (g_x = 0 for a zero column, whose forward output is identically zero).
 template <typename R>
 __global__ void kadj_input_kernel(const typename C2<R>::t* __restrict__ basis, const typename C2<R>::t* __restrict__ Gb0,
-                                  const double* __restrict__ beta, const double* __restrict__ gbeta,
+                                  const double* __restrict__ beta, const double2* __restrict__ gbeta,
                                   typename C2<R>::t* __restrict__ gx, int N, int ncols) {
   const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (col >= ncols) return;
@@ -921,10 +929,160 @@ __global__ void kadj_input_kernel(const typename C2<R>::t* __restrict__ basis, c
     dot += g.re * v.re - g.im * v.im;
   }
   dot = wsum(dot);
-  const R gbt = (R)(gbeta[col] - (double)dot / b), inv = (R)(1.0 / b);
+  const R gbt = (R)(gbeta[col].x - (double)dot / b), inv = (R)(1.0 / b);
   for (int p = lane; p < N; p += 32) {
     const cx<R> g = ldx(Gb0[co + p]), v = ldx(basis[co + p]);
     gx[co + p] = stx(cx<R>{g.re * inv + gbt * v.re, g.im * inv - gbt * v.im});
+  }
+}
+
+// Reverse of Lanczos step j (one warp per column).  The three-term
+// recurrence uses bilinear forms and principal square roots, both
+// holomorphic, so here every adjoint is the g of dJ = Re sum g dz and the
+// small exponential's Gamma_T enters as g_T = conj(Gamma_T):
+//   forward  w1 = A v_j - beta_{j-1} v_{j-1},  alpha_j = v_j^T w1,
+//            w2 = w1 - alpha_j v_j,  beta_j = (w2^T w2)^{1/2},
+//            v_{j+1} = w2 / beta_j  (j + 1 < k; zero after a breakdown)
+//   reverse  g_beta_j = g_T[j+1][j] + g_T[j][j+1] + carry
+//                       - (g_v_{j+1}^T v_{j+1}) / beta_j
+//            g_w2 = g_v_{j+1} / beta_j + g_beta_j v_{j+1}   (0 if beta_j = 0)
+//            g_alpha = g_T[j][j] - g_w2^T v_j
+//            g_v_j += -alpha_j g_w2 + g_alpha w1
+//            U_j = g_w1 = g_w2 + g_alpha v_j
+//            g_v_{j-1} += -beta_{j-1} U_j,  carry <- -U_j^T v_{j-1}
+// The per-column carry passes the part of g_beta_{j-1} that the term
+// -beta_{j-1} v_{j-1} of w1 contributes from step j to step j - 1.  The
+// caller adds A U_j to g_v_j and U_j v_j^T to the adjoint of A.  w1 is
+// rebuilt from the stored product A v_j; the scalar arithmetic runs in the
+// walkers' precision, as in the forward.
+template <typename R, int EPL>
+__global__ void lzadj_step_kernel(const typename C2<R>::t* __restrict__ basis, size_t bstride,
+                                  const typename C2<R>::t* __restrict__ wj, const typename C2<R>::t* __restrict__ Hs,
+                                  size_t hs, int kmax, const double2* __restrict__ GH,
+                                  typename C2<R>::t* __restrict__ Gb, size_t gstride, typename C2<R>::t* __restrict__ U,
+                                  double2* __restrict__ carry, int N, int ncols, int j, int k) {
+  typedef typename C2<R>::t P;
+  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (col >= ncols) return;
+  const size_t co = (size_t)col * N;
+  auto T = [&](int r, int q) { return ldx(Hs[(size_t)(r * kmax + q) * hs + col]); };
+  auto gT = [&](int r, int q) {
+    const double2 g = GH[(size_t)(r * kmax + q) * hs + col];
+    return cx<R>{(R)g.x, (R)(-g.y)};
+  };
+  const cx<R> zero{R(0), R(0)};
+  const cx<R> bp = j > 0 ? T(j, j - 1) : zero, al = T(j, j);
+  const double2 cj = carry[col];
+  const P* vj = basis + j * bstride + co;
+  const P* vm = basis + (j > 0 ? j - 1 : 0) * bstride + co;
+  cx<R> w1[EPL], v[EPL], gw[EPL];
+#pragma unroll
+  for (int e = 0; e < EPL; ++e) {
+    const int p = lane + 32 * e;
+    w1[e] = zero;
+    v[e] = zero;
+    gw[e] = zero;
+    if (p < N) {
+      w1[e] = ldx(wj[co + p]);
+      v[e] = ldx(vj[p]);
+      if (j > 0) w1[e] = w1[e] - bp * ldx(vm[p]);
+    }
+  }
+  if (j + 1 < k) {
+    const cx<R> be = T(j + 1, j);
+    const R m2 = be.re * be.re + be.im * be.im;
+    if (m2 > R(0)) {
+      const P* vn = basis + (j + 1) * bstride + co;
+      const P* gn = Gb + (j + 1) * gstride + co;
+      cx<R> vv[EPL], gv[EPL];
+      R dr = R(0), di = R(0);  // g_v_{j+1}^T v_{j+1}
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) {
+        const int p = lane + 32 * e;
+        vv[e] = zero;
+        gv[e] = zero;
+        if (p < N) {
+          vv[e] = ldx(vn[p]);
+          gv[e] = ldx(gn[p]);
+        }
+        dr += gv[e].re * vv[e].re - gv[e].im * vv[e].im;
+        di += gv[e].re * vv[e].im + gv[e].im * vv[e].re;
+      }
+      dr = wsum(dr);
+      di = wsum(di);
+      const cx<R> ib{be.re / m2, -be.im / m2};
+      const cx<R> gb = gT(j + 1, j) + gT(j, j + 1) + cx<R>{(R)cj.x, (R)cj.y} - ib * cx<R>{dr, di};
+#pragma unroll
+      for (int e = 0; e < EPL; ++e) gw[e] = ib * gv[e] + gb * vv[e];
+    }
+  }
+  R sr = R(0), si = R(0);  // g_w2^T v_j
+#pragma unroll
+  for (int e = 0; e < EPL; ++e) {
+    sr += gw[e].re * v[e].re - gw[e].im * v[e].im;
+    si += gw[e].re * v[e].im + gw[e].im * v[e].re;
+  }
+  sr = wsum(sr);
+  si = wsum(si);
+  const cx<R> ga = gT(j, j) - cx<R>{sr, si};
+  P* gj = Gb + j * gstride + co;
+  P* gm = Gb + (j > 0 ? j - 1 : 0) * gstride + co;
+  R cr = R(0), ci = R(0);  // U_j^T v_{j-1}
+#pragma unroll
+  for (int e = 0; e < EPL; ++e) {
+    const int p = lane + 32 * e;
+    if (p < N) {
+      const cx<R> u = gw[e] + ga * v[e];
+      gj[p] = stx(ldx(gj[p]) - al * gw[e] + ga * w1[e]);
+      U[co + p] = stx(u);
+      if (j > 0) {
+        const cx<R> vp = ldx(vm[p]);
+        cr += u.re * vp.re - u.im * vp.im;
+        ci += u.re * vp.im + u.im * vp.re;
+        gm[p] = stx(ldx(gm[p]) - bp * u);
+      }
+    }
+  }
+  if (j > 0) {
+    cr = wsum(cr);
+    ci = wsum(ci);
+    if (lane == 0) carry[col] = make_double2(-(double)cr, -(double)ci);
+  }
+}
+
+// Adjoint of the Lanczos start v_0 = x / gamma, gamma = (x^T x)^{1/2}:
+//   g_gamma_tot = g_gamma - (g_v0^T v_0) / gamma
+//   g_x = g_v0 / gamma + g_gamma_tot v_0
+// with g_gamma from the small exponential's adjoint (y = gamma e^{T} e_1);
+// g_x = 0 for a column with gamma = 0, whose output is identically zero.
+template <typename R>
+__global__ void lzadj_input_kernel(const typename C2<R>::t* __restrict__ basis,
+                                   const typename C2<R>::t* __restrict__ Gb0, const double2* __restrict__ cbeta,
+                                   const double2* __restrict__ ggam, typename C2<R>::t* __restrict__ gx, int N,
+                                   int ncols) {
+  const int col = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (col >= ncols) return;
+  const size_t co = (size_t)col * N;
+  const double2 gm = cbeta[col];
+  const R m2 = (R)gm.x * (R)gm.x + (R)gm.y * (R)gm.y;
+  if (!(m2 > R(0))) {
+    for (int p = lane; p < N; p += 32) gx[co + p] = stx(cx<R>{R(0), R(0)});
+    return;
+  }
+  R dr = R(0), di = R(0);
+  for (int p = lane; p < N; p += 32) {
+    const cx<R> g = ldx(Gb0[co + p]), v = ldx(basis[co + p]);
+    dr += g.re * v.re - g.im * v.im;
+    di += g.re * v.im + g.im * v.re;
+  }
+  dr = wsum(dr);
+  di = wsum(di);
+  const cx<R> ig{(R)gm.x / m2, -(R)gm.y / m2};
+  const double2 gg = ggam[col];
+  const cx<R> gt = cx<R>{(R)gg.x, (R)gg.y} - ig * cx<R>{dr, di};
+  for (int p = lane; p < N; p += 32) {
+    const cx<R> g = ldx(Gb0[co + p]), v = ldx(basis[co + p]);
+    gx[co + p] = stx(ig * g + gt * v);
   }
 }
 
@@ -1070,20 +1228,21 @@ cudaError_t kadj_seed(const afqmc_ctx* c, int Nw, int k, const typename C2<R>::t
 
 template <typename R, int KM>
 static cudaError_t kadj_expm_k(const afqmc_ctx* c, int ncols, int k, const typename C2<R>::t* Hs, const double2* gy,
-                               double2* GH, double* gbeta, cudaStream_t s) {
+                               double2* GH, double2* gbeta, bool lanczos, cudaStream_t s) {
   const size_t hs = (size_t)c->ws.n_walkers * c->nc;
   kadj_expm_kernel<R, KM><<<(ncols + 63) / 64, 64, 0, s>>>(
-      Hs, reinterpret_cast<const typename C2<R>::t*>(c->ws.hess), hs, c->ws.kmax, c->ws.beta, gy, GH, gbeta, ncols, k);
+      Hs, reinterpret_cast<const typename C2<R>::t*>(c->ws.hess), hs, c->ws.kmax, c->ws.beta,
+      lanczos ? c->ws.cbeta : nullptr, gy, GH, gbeta, ncols, k);
   return cudaGetLastError();
 }
 
 template <typename R>
 cudaError_t kadj_expm(const afqmc_ctx* c, int Nw, int k, const typename C2<R>::t* Hs, const double2* gy, double2* GH,
-                      double* gbeta, cudaStream_t s) {
+                      double2* gbeta, bool lanczos, cudaStream_t s) {
   const int ncols = Nw * c->nc;
-  return k <= 8 ? kadj_expm_k<R, 8>(c, ncols, k, Hs, gy, GH, gbeta, s)
-         : k <= 16 ? kadj_expm_k<R, 16>(c, ncols, k, Hs, gy, GH, gbeta, s)
-                   : kadj_expm_k<R, 32>(c, ncols, k, Hs, gy, GH, gbeta, s);
+  return k <= 8 ? kadj_expm_k<R, 8>(c, ncols, k, Hs, gy, GH, gbeta, lanczos, s)
+         : k <= 16 ? kadj_expm_k<R, 16>(c, ncols, k, Hs, gy, GH, gbeta, lanczos, s)
+                   : kadj_expm_k<R, 32>(c, ncols, k, Hs, gy, GH, gbeta, lanczos, s);
 }
 
 template <typename R>
@@ -1107,23 +1266,48 @@ cudaError_t kadj_orth(const afqmc_ctx* c, int Nw, int j, int k, const typename C
 }
 
 template <typename R>
-cudaError_t kadj_input(const afqmc_ctx* c, int Nw, const typename C2<R>::t* Gb0, const double* gbeta,
-                       typename C2<R>::t* gx, cudaStream_t s) {
+cudaError_t kadj_input(const afqmc_ctx* c, int Nw, const typename C2<R>::t* Gb0, const double2* gbeta,
+                       typename C2<R>::t* gx, bool lanczos, cudaStream_t s) {
   const int ncols = Nw * c->nc;
-  kadj_input_kernel<R><<<(ncols + 7) / 8, 256, 0, s>>>(static_cast<const typename C2<R>::t*>(c->ws.basis), Gb0,
-                                                       c->ws.beta, gbeta, gx, c->N, ncols);
+  const typename C2<R>::t* B = static_cast<const typename C2<R>::t*>(c->ws.basis);
+  if (lanczos)
+    lzadj_input_kernel<R><<<(ncols + 7) / 8, 256, 0, s>>>(B, Gb0, c->ws.cbeta, gbeta, gx, c->N, ncols);
+  else
+    kadj_input_kernel<R><<<(ncols + 7) / 8, 256, 0, s>>>(B, Gb0, c->ws.beta, gbeta, gx, c->N, ncols);
+  return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t lzadj_step(const afqmc_ctx* c, int Nw, int j, int k, const typename C2<R>::t* wj,
+                       const typename C2<R>::t* Hs, const double2* GH, typename C2<R>::t* Gb, size_t gstride,
+                       typename C2<R>::t* U, double2* carry, cudaStream_t s) {
+  const int ncols = Nw * c->nc;
+  const size_t hs = (size_t)c->ws.n_walkers * c->nc, bstride = hs * c->N;
+  const typename C2<R>::t* B = static_cast<const typename C2<R>::t*>(c->ws.basis);
+  const dim3 grid((ncols + 7) / 8);
+  if (c->N <= 128)
+    lzadj_step_kernel<R, 4><<<grid, 256, 0, s>>>(B, bstride, wj, Hs, hs, c->ws.kmax, GH, Gb, gstride, U, carry, c->N,
+                                                 ncols, j, k);
+  else if (c->N <= 256)
+    lzadj_step_kernel<R, 8><<<grid, 256, 0, s>>>(B, bstride, wj, Hs, hs, c->ws.kmax, GH, Gb, gstride, U, carry, c->N,
+                                                 ncols, j, k);
+  else
+    lzadj_step_kernel<R, 16><<<grid, 256, 0, s>>>(B, bstride, wj, Hs, hs, c->ws.kmax, GH, Gb, gstride, U, carry,
+                                                  c->N, ncols, j, k);
   return cudaGetLastError();
 }
 
 #define AFQ_ADJ_INST(R)                                                                                            \
   template cudaError_t kadj_seed<R>(const afqmc_ctx*, int, int, const C2<R>::t*, C2<R>::t*, size_t, double2*,      \
                                     cudaStream_t);                                                                 \
-  template cudaError_t kadj_expm<R>(const afqmc_ctx*, int, int, const C2<R>::t*, const double2*, double2*, double*, \
-                                    cudaStream_t);                                                                 \
+  template cudaError_t kadj_expm<R>(const afqmc_ctx*, int, int, const C2<R>::t*, const double2*, double2*,        \
+                                    double2*, bool, cudaStream_t);                                                 \
   template cudaError_t kadj_orth<R>(const afqmc_ctx*, int, int, int, const C2<R>::t*, const C2<R>::t*,              \
                                     const double2*, C2<R>::t*, size_t, C2<R>::t*, cudaStream_t);                   \
-  template cudaError_t kadj_input<R>(const afqmc_ctx*, int, const C2<R>::t*, const double*, C2<R>::t*,             \
+  template cudaError_t kadj_input<R>(const afqmc_ctx*, int, const C2<R>::t*, const double2*, C2<R>::t*, bool,      \
                                      cudaStream_t);                                                                \
+  template cudaError_t lzadj_step<R>(const afqmc_ctx*, int, int, int, const C2<R>::t*, const C2<R>::t*,             \
+                                     const double2*, C2<R>::t*, size_t, C2<R>::t*, double2*, cudaStream_t);        \
   template cudaError_t adj_sanitize<R>(const C2<R>::t*, C2<R>::t*, const double*, const double*, size_t, int,     \
                                        cudaStream_t);                                                              \
   template cudaError_t adj_sum_terms<R>(const C2<R>::t*, C2<R>::t*, int, size_t, int, cudaStream_t);               \

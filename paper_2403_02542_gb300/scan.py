@@ -8,7 +8,8 @@ dJ/ds = sum dJ/dh1 * dH1 + sum dJ/dL * dL from the walk adjoint
 (afqmc_walk_backward).  Central differences of J along the path are taken
 beside it as a check.  The paper has no gradients; this uses the library's
 adjoint of the fixed-field walk (Split-2 with the Taylor action, Sec. III.B,
-Eq. taylor, or the Krylov action, Eqs. krylovsub-krylov).
+Eq. taylor, or the Krylov action of Eqs. krylovsub-krylov by Arnoldi or by
+the complex-symmetric Lanczos recurrence).
 """
 from __future__ import annotations
 

@@ -198,6 +198,48 @@ def test_walk_adjoint_krylov_is_independent_of_checkpoint_spacing():
         assert torch.equal(x, y)
 
 
+@pytest.mark.parametrize("N,na,nb,G,nw,steps,r,ckpt,dead,k", [
+    (10, 2, 2, 12, 5, 6, 2, 3, (1,), 4),
+    (14, 3, 2, 20, 6, 5, 3, 2, (), 10),
+    (10, 2, 1, 12, 3, 4, 0, 10, (), 12),     # dimension above N: k = N
+    (24, 3, 3, 40, 4, 4, 1, 1, (2,), 5),
+])
+def test_walk_adjoint_lanczos_matches_oracle_autograd(N, na, nb, G, nw, steps, r, ckpt, dead, k):
+    """The complex-symmetric Lanczos action in every step: FP64 gradients
+    entry by entry against autograd through the oracle's three-term
+    recurrence (bilinear forms, principal square roots) and small
+    exponential.  In the first case the Lanczos gradient differs from the
+    Arnoldi one by far more than the bar, so the comparison sees which
+    reverse pass ran."""
+    s = _Sys(N, na, nb, G, seed=5 * N + steps)
+    tau = 0.05
+    e0 = _e0(s)
+    fields = [make_fields(N, 90 + kk, nw, G) for kk in range(steps)]
+    J_ref, gh_ref, gL_ref, gp_ref, W_ref = _oracle(s, nw, fields, tau, e0, k, r, dead, method="lanczos")
+    assert int((W_ref > 0).sum()) == nw - len(dead)
+    J, gh, gL, gp = _gpu(s, nw, fields, tau, e0, k, r, ckpt, dead, psi_grad=True, expm="lanczos")
+    assert abs(float(J[2]) - J_ref) <= 1e-10 * abs(J_ref)
+    _close_entrywise(gh, gh_ref, "dJ/dh1")
+    _close_entrywise(gL, gL_ref, "dJ/dL")
+    _close_entrywise(gp, gp_ref.transpose(1, 2), "dJ/dPsi0")
+    assert torch.equal(gh, gh.T) and torch.equal(gL, gL.transpose(1, 2))
+    if k == 4:
+        _, gh_a, _, _, _ = _oracle(s, nw, fields, tau, e0, k, r, dead, method="krylov")
+        assert float((gh_a - gh_ref).abs().max()) > 1e3 * GRAD_RTOL * float(gh_ref.abs().max())
+
+
+def test_walk_adjoint_lanczos_is_independent_of_checkpoint_spacing():
+    """Recomputing the Lanczos steps from checkpoints changes no bit."""
+    s = _Sys(14, 3, 2, 20, seed=1402)
+    tau, nw, steps, k = 0.05, 6, 6, 8
+    e0 = _e0(s)
+    fields = [make_fields(14, 170 + kk, nw, s.G) for kk in range(steps)]
+    a = _gpu(s, nw, fields, tau, e0, k, 2, 1, psi_grad=True, expm="lanczos")
+    b = _gpu(s, nw, fields, tau, e0, k, 2, 4, psi_grad=True, expm="lanczos")
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
 def test_walk_adjoint_matches_oracle_autograd_mid_size():
     """N = 48, 8+8 electrons, 160 vectors, 16 walkers, 10 steps, QR every 5,
     checkpoints every 5: FP64 gradients entry by entry against autograd
@@ -356,6 +398,28 @@ def test_walk_adjoint_mixed_matches_oracle_autograd(N, na, nb, G, nw, steps, r, 
     _close(gL, gL_ref, MIXED_GRAD_RTOL)
     _close(gp.to(CT), gp_ref.transpose(1, 2), MIXED_GRAD_RTOL)
     assert torch.equal(gh, gh.T) and torch.equal(gL, gL.transpose(1, 2))
+
+
+@pytest.mark.parametrize("N,na,nb,G,nw,steps,r,ckpt,dead,k", [
+    (10, 2, 2, 12, 5, 6, 2, 3, (1,), 6),
+    (24, 3, 3, 40, 4, 4, 1, 2, (), 8),
+])
+def test_walk_adjoint_lanczos_mixed_matches_oracle_autograd(N, na, nb, G, nw, steps, r, ckpt, dead, k):
+    """Complex64 walkers with the Lanczos action: the recurrence's scalars in
+    FP32 forward and reverse, the gradient sums in FP64."""
+    s = _Sys(N, na, nb, G, seed=5 * N + steps)
+    tau = 0.05
+    e0 = _e0(s)
+    fields = [make_fields(N, 90 + kk, nw, G) for kk in range(steps)]
+    J_ref, gh_ref, gL_ref, gp_ref, W_ref = _oracle(s, nw, fields, tau, e0, k, r, dead, method="lanczos")
+    assert int((W_ref > 0).sum()) == nw - len(dead)
+    J, gh, gL, gp = _gpu(s, nw, fields, tau, e0, k, r, ckpt, dead, psi_grad=True, precision="mixed",
+                         expm="lanczos")
+    assert gp.dtype == torch.complex64
+    assert abs(float(J[2]) - J_ref) <= MIXED_J_TOL
+    _close(gh, gh_ref, MIXED_GRAD_RTOL)
+    _close(gL, gL_ref, MIXED_GRAD_RTOL)
+    _close(gp.to(CT), gp_ref.transpose(1, 2), MIXED_GRAD_RTOL)
 
 
 def test_walk_adjoint_mixed_is_independent_of_checkpoint_spacing():
