@@ -118,7 +118,10 @@ def test_lanczos_argument_checks():
             ctx.step(w, x, 0.05, -1.0, expm="lanczos", order=order)
     with pytest.raises(Lb.AfqmcError):
         ctx.step(w, x, 0.05, -1.0, expm="lanczos", order=4, propagator="taylor")
-    with pytest.raises(ValueError):
-        ctx.walk_backward(w, x[None], 0.05, -1.0, order=4, expm="lanczos")
+    for expm in ("bkrylov", "chebyshev"):   # the walk adjoint takes taylor, krylov and lanczos
+        with pytest.raises(ValueError):
+            ctx.walk_backward(w, x[None], 0.05, -1.0, order=4, expm=expm)
+    J, gh, gL = ctx.walk_backward(w, x[None], 0.05, -1.0, order=4, expm="lanczos")
+    assert bool(torch.isfinite(gh).all()) and bool(torch.isfinite(gL).all())
     ctx.step(w, x, 0.05, -1.0, expm="lanczos", order=32)
     ctx.close()
