@@ -1305,6 +1305,9 @@ cudaError_t launch_krylov_orth(const afqmc_ctx* c, int Nw, int it, int k, cudaSt
   else if (c->N <= 256)
     krylov_orth_kernel<R, 8><<<grid, 256, 0, s>>>(W, Bs, H, hs, c->ws.scal, c->N, c->nc, ncols, it, k, c->ws.kmax,
                                                   bstride, vp);
+  else if (c->N <= 320)  // 10 elements per lane: fewer registers, more warps in flight than 16
+    krylov_orth_kernel<R, 10><<<grid, 256, 0, s>>>(W, Bs, H, hs, c->ws.scal, c->N, c->nc, ncols, it, k, c->ws.kmax,
+                                                   bstride, vp);
   else
     krylov_orth_kernel<R, 16><<<grid, 256, 0, s>>>(W, Bs, H, hs, c->ws.scal, c->N, c->nc, ncols, it, k,
                                                    c->ws.kmax, bstride, vp);
@@ -1341,6 +1344,9 @@ cudaError_t launch_lanczos_step(const afqmc_ctx* c, int Nw, int it, int k, cudaS
   else if (c->N <= 256)
     lanczos_step_kernel<R, 8><<<grid, 256, 0, s>>>(W, Bs, H, hs, c->ws.scal, c->N, c->nc, ncols, it, k, c->ws.kmax,
                                                    bstride, vp);
+  else if (c->N <= 320)
+    lanczos_step_kernel<R, 10><<<grid, 256, 0, s>>>(W, Bs, H, hs, c->ws.scal, c->N, c->nc, ncols, it, k,
+                                                    c->ws.kmax, bstride, vp);
   else
     lanczos_step_kernel<R, 16><<<grid, 256, 0, s>>>(W, Bs, H, hs, c->ws.scal, c->N, c->nc, ncols, it, k,
                                                     c->ws.kmax, bstride, vp);
