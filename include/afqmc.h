@@ -265,8 +265,9 @@ afqmc_status afqmc_population_control(afqmc_ctx* ctx, const afqmc_walkers* w, do
  * (one warm-up, three timed launches, minimum kept) for n_walkers walkers on
  * the context's workspace and keeps the fastest.  Tile shape does not change
  * the summation order, so results are bit-identical for every choice.  (Mixed
- * contexts with N <= 128 run their half steps in a dedicated kernel that keeps
- * B in shared memory; the half-step site's choice then serves the adjoint.)
+ * contexts run their half steps on the tensor cores, or, where that plan is
+ * unavailable and N <= 128, in a dedicated kernel that keeps B in shared
+ * memory; the half-step site's choice then serves the adjoint.)
  * Synchronises the context's stream.
  *   table_out  host [4] int32 or NULL: the chosen variant per call site.
  * afqmc_tune_set / afqmc_tune_get write / read that table (e.g. from a cache
