@@ -132,3 +132,26 @@ def test_binding_constants_match_the_header():
     assert values["AFQMC_K_COUNT"] == len(L.KERNEL_CLASSES)
     m = re.search(r"AFQMC_STATIC_SCRATCH_BYTES\s*\(\(unsigned long long\)(\d+)\s*<<\s*(\d+)\)", text)
     assert m and L.STATIC_SCRATCH_BYTES == int(m.group(1)) << int(m.group(2))
+
+
+def test_binding_structs_match_the_header():
+    """The ctypes mirrors of the header's parameter structs list the same
+    fields, in the same order, with the same C types (so the offsets agree)."""
+    text = open(os.path.join(ROOT, "include", "afqmc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    ctype = {"int": ctypes.c_int, "double": ctypes.c_double, "void*": ctypes.c_void_p,
+             "uint32_t*": ctypes.c_void_p, "double*": ctypes.c_void_p}
+    for cname, pyname in (("afqmc_walkers", "Walkers"), ("afqmc_step_params", "StepParams"),
+                          ("afqmc_walk_adjoint_params", "WalkAdjointParams")):
+        m = re.search(r"typedef struct\s*\{([^}]*)\}\s*" + cname + r"\s*;", text)
+        assert m, cname
+        fields = []
+        for decl in m.group(1).split(";"):
+            decl = " ".join(decl.split())
+            if not decl:
+                continue
+            mm = re.match(r"(?:const )?(\w+)\s*(\**)\s*(\w+)$", decl)
+            assert mm, (cname, decl)
+            fields.append((mm.group(3), ctype[mm.group(1) + mm.group(2)]))
+        assert [(n, t) for n, t in getattr(L, pyname)._fields_] == fields, cname
