@@ -422,35 +422,42 @@ __global__ void to_float_kernel(const double* __restrict__ a, float* __restrict_
 
 // A_w <- A_w - tau h'' for every walker: the exponent -tau H_eff = A - tau h''
 // of the Taylor propagator (Sec. III); h'' is real and shared by the walkers,
-// so only the real parts change
+// so only the real parts change.  Threads over the N^2 entries (x) and walker
+// groups (y): tau h''_pq is formed once per entry and subtracted in the
+// walkers' precision from that entry of each walker of the group.
 template <typename R>
 __global__ void shift_field_kernel(typename C2<R>::t* __restrict__ A, const double* __restrict__ hpp, double tau,
-                                   size_t NN, size_t total) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x)
-    A[e].x = (R)((double)A[e].x - tau * hpp[e % NN]);
+                                   size_t NN, int Nw) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= NN) return;
+  const R hv = (R)(tau * hpp[i]);
+  for (int w = blockIdx.y; w < Nw; w += gridDim.y) A[(size_t)w * NN + i].x -= hv;
 }
 
 // One step of the Chebyshev recurrence (Eq. chebpoly) over `total` complex
 // entries.  first: acc = a t + b prod (t = T_0 Psi, prod = T_1 Psi; prod may be
 // t when b = 0).  Otherwise t <- prod - t (prod = 2 A T_{n-1} Psi and
-// t = T_{n-2} Psi, so t becomes T_n Psi) and acc += b t.
+// t = T_{n-2} Psi, so t becomes T_n Psi) and acc += b t.  The arithmetic is in
+// the walkers' precision (FP32 for complex64 walkers: an FP64 operation per
+// element would bind the kernel to the narrow FP64 pipe instead of HBM).
 template <typename R>
 __global__ void cheb_step_kernel(const typename C2<R>::t* prod, typename C2<R>::t* t,
                                  typename C2<R>::t* __restrict__ acc, double a, double b, int first, size_t total) {
+  const R ra = (R)a, rb = (R)b;
   for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
     const auto pv = prod[e];
     const auto tv = t[e];
     auto av = acc[e];
     if (first) {
-      av.x = (R)(a * (double)tv.x + b * (double)pv.x);
-      av.y = (R)(a * (double)tv.y + b * (double)pv.y);
+      av.x = ra * tv.x + rb * pv.x;
+      av.y = ra * tv.y + rb * pv.y;
     } else {
       auto nv = tv;
-      nv.x = (R)((double)pv.x - (double)tv.x);
-      nv.y = (R)((double)pv.y - (double)tv.y);
+      nv.x = pv.x - tv.x;
+      nv.y = pv.y - tv.y;
       t[e] = nv;
-      av.x = (R)((double)av.x + b * (double)nv.x);
-      av.y = (R)((double)av.y + b * (double)nv.y);
+      av.x = av.x + rb * nv.x;
+      av.y = av.y + rb * nv.y;
     }
     acc[e] = av;
   }
@@ -650,8 +657,8 @@ template <typename R>
 cudaError_t launch_shift_field(const afqmc_ctx* c, int Nw, double tau, cudaStream_t s) {
   const size_t NN = (size_t)c->N * c->N, total = (size_t)Nw * NN;
   if (total == 0) return cudaSuccess;
-  shift_field_kernel<R><<<grid_for(total), 256, 0, s>>>(static_cast<typename C2<R>::t*>(c->ws.A), c->d_hpp, tau,
-                                                        NN, total);
+  const dim3 grid((unsigned)((NN + 255) / 256), (unsigned)(Nw < 64 ? Nw : 64));
+  shift_field_kernel<R><<<grid, 256, 0, s>>>(static_cast<typename C2<R>::t*>(c->ws.A), c->d_hpp, tau, NN, Nw);
   return cudaGetLastError();
 }
 
