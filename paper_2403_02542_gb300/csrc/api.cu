@@ -518,12 +518,13 @@ static afqmc_status run_step(afqmc_ctx* c, const afqmc_walkers* w, const double*
   PK(AFQMC_K_FORCEBIAS, gemm<R>(gfb, false, EPI_STORE, s));
   PK(AFQMC_K_OTHER, launch_bias_finalize<R>(c, Nw, x, st, s, nullptr, skip));
   // A_w = i sqrt(tau) sum_g c_wg L_g (Eq. heffTOT); complex64 walkers: on the
-  // tensor cores, except for the Taylor and Crank-Nicolson propagators, which
-  // need X_w = A_w - tau h'' in memory (the field GEMM, then the shift)
+  // tensor cores, into the A' operand planes, or for the Taylor and
+  // Crank-Nicolson propagators, which need X_w = A_w - tau h'' in memory, into
+  // ws.A (then the shift)
   const bool split1 = p->propagator == AFQMC_SPLIT1, tprop = p->propagator == AFQMC_TAYLORPROP,
              cn = p->propagator == AFQMC_CN, xmat = tprop || cn;
-  if (std::is_same<R, float>::value && c->tg.ok && !xmat) {
-    PK(AFQMC_K_FIELD, tc_field_launch(c, Nw, st, s));
+  if (std::is_same<R, float>::value && c->tg.ok) {
+    PK(AFQMC_K_FIELD, tc_field_launch(c, Nw, st, s, xmat));
     c->launches += 1;
   } else {
     PK(AFQMC_K_FIELD, gemm<R>(site_args<R>(c, SITE_FIELD, Nw, st, ws.c, ws.A), false, EPI_STORE, s));

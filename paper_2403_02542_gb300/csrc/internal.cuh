@@ -479,7 +479,9 @@ cudaError_t tc_field_setup(afqmc_ctx* c, cudaStream_t s);
 cudaError_t tc_field_ws(afqmc_ctx* c);
 cudaError_t tc_field_prepare(const afqmc_ctx* c);
 void tc_field_free(afqmc_ctx* c);
-cudaError_t tc_field_launch(afqmc_ctx* c, int Nw, double sqrt_tau, cudaStream_t s);
+// to_memory: write A_w as interleaved complex [Nw][N][N] to ws.A instead of the
+// split-bf16 A' planes (for the propagators that shift A_w in memory)
+cudaError_t tc_field_launch(afqmc_ctx* c, int Nw, double sqrt_tau, cudaStream_t s, bool to_memory = false);
 // C[w][j][p] = alpha sum_q A_w[p][q] V[w][j][q] (D[w] += C[w] when D is given),
 // complex64, walker batch strides in complex elements; A_w from the planes.
 // V == NULL: the V planes were already written (by the Arnoldi kernels).

@@ -777,8 +777,9 @@ void tc_field_free(afqmc_ctx* c) {
 
 // A_w = i sqrt(tau) sum_g c_wg L_g for Nw walkers from ws.c: into ws.A
 // (complex64), or into the A' planes when the products A V use them.
-cudaError_t tc_field_launch(afqmc_ctx* c, int Nw, double sqrt_tau, cudaStream_t s) {
+cudaError_t tc_field_launch(afqmc_ctx* c, int Nw, double sqrt_tau, cudaStream_t s, bool to_memory) {
   TgPlan& P = c->tg;
+  const bool planes = P.av_ok && !to_memory;
   const int mp = ((2 * Nw + TG_BM - 1) / TG_BM) * TG_BM;
   if (mp > P.m_cap || (P.av_ok && Nw > P.av_cap)) return cudaErrorInvalidValue;
   build_x_kernel<<<grid_for((size_t)mp * P.Kp), 256, 0, s>>>(static_cast<const float2*>(c->ws.c),
@@ -801,10 +802,10 @@ cudaError_t tc_field_launch(afqmc_ctx* c, int Nw, double sqrt_tau, cudaStream_t 
   a.a_lo = static_cast<__nv_bfloat16*>(P.a_lo);
   a.N = c->N;
   a.KA = P.KA;
-  a.nrm = P.av_ok ? static_cast<float*>(P.nrm) : nullptr;
+  a.nrm = planes ? static_cast<float*>(P.nrm) : nullptr;
   a.err = static_cast<int*>(P.err);
   if (!capturing(c)) {
-    e = P.av_ok ? raise_smem_limit(field_tc_kernel<1>) : raise_smem_limit(field_tc_kernel<0>);
+    e = planes ? raise_smem_limit(field_tc_kernel<1>) : raise_smem_limit(field_tc_kernel<0>);
     if (e != cudaSuccess) return e;
   }
   const int sms = sm_count();
@@ -814,7 +815,7 @@ cudaError_t tc_field_launch(afqmc_ctx* c, int Nw, double sqrt_tau, cudaStream_t 
   memcpy(&mxl, P.map_x_lo, sizeof(CUtensorMap));
   memcpy(&mlh, P.map_l_hi, sizeof(CUtensorMap));
   memcpy(&mll, P.map_l_lo, sizeof(CUtensorMap));
-  if (P.av_ok)
+  if (planes)
     field_tc_kernel<1><<<grid, TG_THREADS, tg_smem_bytes(), s>>>(mxh, mxl, mlh, mll, a);
   else
     field_tc_kernel<0><<<grid, TG_THREADS, tg_smem_bytes(), s>>>(mxh, mxl, mlh, mll, a);
