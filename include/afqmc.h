@@ -92,7 +92,9 @@ enum {
  *              set).  In FP32: the overlap products trial^T Psi, O^{-1} from
  *              the rounded LU factors and Theta = Psi O^{-1}, the force-bias
  *              contraction when it is recomputed, the Arnoldi and Lanczos
- *              inner products, norms and square roots, the one-body trace
+ *              inner products, norms and square roots, the combinations of
+ *              the Chebyshev recurrence, the shift A_w - tau h'' of the Taylor
+ *              and Crank-Nicolson propagators, the one-body trace
  *              tr(h_half Theta) (error-free products and compensated
  *              TwoSum sums in FP32, per-thread partials added in FP64) and
  *              the Gram-Schmidt projections of the re-orthonormalisation (the
@@ -100,7 +102,8 @@ enum {
  *              is invariant under Psi -> Psi M, so the orthonormality of Q
  *              affects no energy or weight).  In FP64: the LU of the overlap
  *              matrices and their log-determinants, the small exponential
- *              e^{A_k} e_1 of the Krylov action, the hybrid energy, the
+ *              e^{A_k} e_1 of the Krylov action, the Crank-Nicolson
+ *              elimination, the hybrid energy, the
  *              phaseless weights, population control, and every sum over
  *              Cholesky vectors or walkers of the energies. */
 enum { AFQMC_FP64 = 0, AFQMC_MIXED = 1 };
