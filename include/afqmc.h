@@ -333,8 +333,11 @@ afqmc_status afqmc_energy_backward(afqmc_ctx* ctx, const afqmc_walkers* w, doubl
  * cos(dtheta) <= 0, energy window) is held fixed, so a removed component or a
  * capped quantity carries no derivative, and d max(0, cos dtheta) =
  * -sin(dtheta) d(dtheta) where cos > 0; the re-orthonormalisation is a fixed
- * right multiplication Psi <- Psi R^{-1} (exact here: E_L, the force bias,
- * the overlap ratio and the Taylor action are invariant under Psi -> Psi M);
+ * right multiplication Psi <- Psi R^{-1} (exact for the Taylor action: E_L,
+ * the force bias, the overlap ratio and that action are invariant under
+ * Psi -> Psi M; a column-wise Krylov or Lanczos action of dimension k < N is
+ * not, so with re-orthonormalisation the gradient leaves out the part of dJ
+ * that flows through R, a term of the order of the Krylov truncation);
  * the trial is held fixed; the dependence of e^{-tau h''/2} on h'' is taken
  * through the eigendecomposition (Daleckii-Krein divided differences).  The
  * mean-field shift L_bar_g = <Psi_T|L_g|Psi_T>, h'' and E_c' are functions of

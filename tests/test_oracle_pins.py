@@ -1122,3 +1122,83 @@ def test_krylov_walk_gradient_matches_central_differences_and_exact_at_full_dime
     assert float((gLk - gLe).abs().max()) <= 1e-8 * float(gLe.abs().max())
     # and the dimension-4 gradient differs from the exact one (the test sees the truncation)
     assert float((gh - ghe).abs().max()) > 1e-10
+
+
+def test_lanczos_walk_gradient_matches_central_differences_and_exact_at_full_dimension():
+    """The walk objective with the complex-symmetric Lanczos action (reading
+    R30, dimension 4 < N = 7), no re-orthonormalisation: autograd through the
+    three-term recurrence (bilinear forms, principal square roots) and the
+    small exponential against central differences along random symmetric
+    dH, dL and along a random complex direction of Psi_0 (G = conj(torch's
+    .grad)); at dimension N the Lanczos action is the exact e^A psi, so J and
+    its gradients equal those of the exact action (matrix_exp), QR included."""
+    s, e0, fields, tau = _walk_setup(steps=4, seed=14)
+    nw = fields[0].shape[0]
+    g = torch.Generator().manual_seed(5)
+    psi0 = (torch.as_tensor(s.trial, dtype=RT).to(CT).unsqueeze(0).repeat(nw, 1, 1)
+            + 0.1 * _rand_c(g, nw, s.trial.shape[0], s.trial.shape[1]))
+    rng = np.random.default_rng(7)
+    dH = rng.standard_normal(s.h1.shape); dH = 0.5 * (dH + dH.T)
+    dL = rng.standard_normal(s.L.shape); dL = 0.5 * (dL + dL.transpose(0, 2, 1))
+    h1 = torch.tensor(s.h1, dtype=RT, requires_grad=True)
+    L = torch.tensor(s.L, dtype=RT, requires_grad=True)
+    p0 = psi0.clone().requires_grad_(True)
+    J = _walk_J(s, h1, L, p0, fields, tau, e0, r=0, method="lanczos", k=4)
+    gh, gL, tg = torch.autograd.grad(J, [h1, L, p0])
+    G = tg.conj()
+    eps = 1e-5
+    with torch.no_grad():
+        def Jl(hh, LL, pp):
+            return float(_walk_J(s, hh, LL, pp, fields, tau, e0, r=0, method="lanczos", k=4))
+        fd_h = (Jl(s.h1 + eps * dH, s.L, psi0) - Jl(s.h1 - eps * dH, s.L, psi0)) / (2 * eps)
+        fd_L = (Jl(s.h1, s.L + eps * dL, psi0) - Jl(s.h1, s.L - eps * dL, psi0)) / (2 * eps)
+        dP = _rand_c(g, *psi0.shape)
+        fd_p = (Jl(s.h1, s.L, psi0 + eps * dP) - Jl(s.h1, s.L, psi0 - eps * dP)) / (2 * eps)
+    assert abs(fd_h - float((gh * torch.as_tensor(dH)).sum())) <= 1e-6 * max(1.0, abs(fd_h))
+    assert abs(fd_L - float((gL * torch.as_tensor(dL)).sum())) <= 1e-6 * max(1.0, abs(fd_L))
+    assert abs(fd_p - float((G * dP).sum().real)) <= 1e-8 * max(1.0, abs(fd_p))
+    N = s.h1.shape[0]
+    grads = {}
+    for method, k in (("lanczos", N), ("exact", 0)):
+        h1 = torch.tensor(s.h1, dtype=RT, requires_grad=True)
+        L = torch.tensor(s.L, dtype=RT, requires_grad=True)
+        Jm = _walk_J(s, h1, L, psi0, fields, tau, e0, method=method, k=k)
+        grads[method] = (float(Jm.detach()),) + tuple(torch.autograd.grad(Jm, [h1, L]))
+    (Jn, ghn, gLn), (Je, ghe, gLe) = grads["lanczos"], grads["exact"]
+    assert abs(Jn - Je) <= 1e-10 * abs(Je)
+    assert float((ghn - ghe).abs().max()) <= 1e-7 * float(ghe.abs().max())
+    assert float((gLn - gLe).abs().max()) <= 1e-7 * float(gLe.abs().max())
+    # the dimension-4 gradient differs from the exact one (the test sees the truncation)
+    assert float((gh - ghe).abs().max()) > 1e-10
+
+
+@pytest.mark.parametrize("method", ["krylov", "lanczos"])
+def test_qr_as_fixed_factor_is_exact_only_for_actions_linear_in_psi(method):
+    """Reading R10 holds the re-orthonormalisation Psi <- Psi R^{-1} as a
+    fixed right factor.  That is exact where everything downstream is
+    invariant under Psi -> Psi M, which holds for the Taylor action (linear in
+    Psi) but not for a column-wise Krylov action of dimension k < N (each
+    column has its own Krylov space): there the gradient drops the part of
+    dJ that flows through R, a term of the order of the Krylov truncation.
+    Measured here against central differences with QR every 2 steps: the
+    Taylor gradient is exact, the Krylov ones differ by less than 1e-4 of the
+    derivative but by more than the differences' own error."""
+    s, e0, fields, tau = _walk_setup(steps=4, seed=14)
+    nw = fields[0].shape[0]
+    g = torch.Generator().manual_seed(5)
+    psi0 = (torch.as_tensor(s.trial, dtype=RT).to(CT).unsqueeze(0).repeat(nw, 1, 1)
+            + 0.1 * _rand_c(g, nw, s.trial.shape[0], s.trial.shape[1]))
+    dP = _rand_c(torch.Generator().manual_seed(99), *psi0.shape)
+    eps = 1e-5
+
+    def gap(m, k):
+        p0 = psi0.clone().requires_grad_(True)
+        J = _walk_J(s, s.h1, s.L, p0, fields, tau, e0, r=2, method=m, k=k)
+        (tg,) = torch.autograd.grad(J, [p0])
+        with torch.no_grad():
+            fd = (float(_walk_J(s, s.h1, s.L, psi0 + eps * dP, fields, tau, e0, r=2, method=m, k=k))
+                  - float(_walk_J(s, s.h1, s.L, psi0 - eps * dP, fields, tau, e0, r=2, method=m, k=k))) / (2 * eps)
+        return abs(fd - float((tg.conj() * dP).sum().real)) / abs(fd)
+
+    assert gap("taylor", 6) <= 1e-8
+    assert 1e-8 < gap(method, 4) <= 1e-4
